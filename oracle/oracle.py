@@ -1,0 +1,253 @@
+"""Python front end of the FP64 CPU oracle (``paw_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and by the
+CPU-baseline leg of the benchmark, never by the library itself.  The C source is compiled
+here with gcc (``build()``), IEEE semantics kept (no fast-math, no FMA contraction, so the
+oracle gives the same bits on x86-64 and aarch64).
+
+Every function takes numpy arrays in the layouts of ``paw_oracle.c`` and a
+``paper_2310_14776_gb300.synth.System`` describing the cell, grid, potential, projector
+boxes and PAW correction matrices.  Passages followed: Eq. (dh) and the overlap operator
+(PAW section), the projector overlaps entering the atomic density matrix (same section),
+SCF step 1 of the Kohn-Sham section (subspace diagonalization), and the dense Cholesky +
+diagonalization of the parallelization section.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "paw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libpaw_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``paw_oracle.c`` into ``_build/libpaw_oracle.so`` (OpenMP if the compiler has it)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", _SRC,
+            "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i, l, d = ctypes.c_int, ctypes.c_long, ctypes.c_double
+            sig = {
+                "oracle_fd6_coefficients": [P],
+                "oracle_kinetic_local_real": [P, P, P, P, l, P],
+                "oracle_kinetic_local_bloch": [P, P, P, P, P, l, P],
+                "oracle_project": [P, P, P, i, i, P, P, P, P, P, P, l, P],
+                "oracle_apply": [i, P, P, P, i, P, i, P, P, P, P, P, P, P, P, l, P, P],
+                "oracle_gram": [i, P, P, l, l, d, P],
+                "oracle_subspace_diag": [i, l, P, P, P, P, P],
+                "oracle_cholesky": [i, l, P, P],
+                "oracle_jacobi_eigh": [i, l, P, P, P, P],
+                "oracle_rotate": [i, P, l, l, P, P],
+                "oracle_num_threads": [],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _c(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+def fd6_coefficients() -> np.ndarray:
+    out = np.zeros(4)
+    lib().oracle_fd6_coefficients(_ptr(out))
+    return out
+
+
+class _Geometry:
+    """Keeps the marshalled system arrays alive for the duration of a call."""
+
+    def __init__(self, system):
+        self.n = _c(system.n, np.int32)
+        self.L = _c(system.cell, np.float64)
+        self.k = _c(system.k, np.float64)
+        self.v = _c(system.vloc, np.float64)
+        self.nproj = _c(system.nproj, np.int32)
+        self.box_lo = _c(system.box_lo, np.int32)
+        self.box_n = _c(system.box_n, np.int32)
+        self.proj = _c(system.proj, np.float64)
+        self.proj_off = _c(system.proj_off, np.int64)
+        self.dH = _c(system.dH, np.float64)
+        self.dS = _c(system.dS, np.float64)
+        self.dmat_off = _c(system.dmat_off, np.int64)
+        self.natoms = int(system.natoms)
+        self.cplx = bool(system.complex_wf)
+        self.Ip = int(system.nproj_total)
+
+
+def _psi_in(system, psi) -> Tuple[np.ndarray, int]:
+    dt = np.complex128 if system.complex_wf else np.float64
+    psi = _c(psi, dt)
+    nb = psi.size // system.npoints
+    return psi, nb
+
+
+def kinetic_local(system, psi: np.ndarray) -> np.ndarray:
+    """-1/2 Lap_FD psi + v psi (the kinetic and local-potential terms of Eq. (dh))."""
+    g = _Geometry(system)
+    psi, nb = _psi_in(system, psi)
+    out = np.empty_like(psi)
+    if g.cplx:
+        rc = lib().oracle_kinetic_local_bloch(_ptr(g.n), _ptr(g.L), _ptr(g.k), _ptr(g.v), _ptr(psi), nb, _ptr(out))
+    else:
+        rc = lib().oracle_kinetic_local_real(_ptr(g.n), _ptr(g.L), _ptr(g.v), _ptr(psi), nb, _ptr(out))
+    assert rc == 0
+    return out
+
+
+def project(system, psi: np.ndarray) -> np.ndarray:
+    """P [Ip][nb] = <p_i^a | psi_n>."""
+    g = _Geometry(system)
+    psi, nb = _psi_in(system, psi)
+    P = np.zeros((g.Ip, nb), dtype=psi.dtype)
+    rc = lib().oracle_project(_ptr(g.n), _ptr(g.L), _ptr(g.k), int(g.cplx), g.natoms, _ptr(g.nproj), _ptr(g.box_lo),
+                              _ptr(g.box_n), _ptr(g.proj), _ptr(g.proj_off), _ptr(psi), nb, _ptr(P))
+    assert rc == 0
+    return P
+
+
+def _apply(which: int, system, psi: np.ndarray):
+    g = _Geometry(system)
+    psi, nb = _psi_in(system, psi)
+    out = np.empty_like(psi)
+    P = np.zeros((g.Ip, nb), dtype=psi.dtype)
+    dmat = g.dH if which == 0 else g.dS
+    rc = lib().oracle_apply(which, _ptr(g.n), _ptr(g.L), _ptr(g.k), int(g.cplx), _ptr(g.v), g.natoms, _ptr(g.nproj),
+                            _ptr(g.box_lo), _ptr(g.box_n), _ptr(g.proj), _ptr(g.proj_off), _ptr(dmat),
+                            _ptr(g.dmat_off), _ptr(psi), nb, _ptr(out), _ptr(P))
+    assert rc == 0
+    return out, P
+
+
+def apply_H(system, psi: np.ndarray):
+    """(H psi, P): Eq. (dh) applied to every band."""
+    return _apply(0, system, psi)
+
+
+def apply_S(system, psi: np.ndarray):
+    """(S psi, P): the PAW overlap operator applied to every band."""
+    return _apply(1, system, psi)
+
+
+def gram(A: np.ndarray, B: np.ndarray, dV: float, nb: int) -> np.ndarray:
+    """M[n][m] = dV sum_r conj(A_n(r)) B_m(r)."""
+    cplx = np.iscomplexobj(A) or np.iscomplexobj(B)
+    dt = np.complex128 if cplx else np.float64
+    A = _c(A, dt)
+    B = _c(B, dt)
+    K = A.size // nb
+    M = np.zeros((nb, nb), dtype=dt)
+    rc = lib().oracle_gram(int(cplx), _ptr(A), _ptr(B), K, nb, float(dV), _ptr(M))
+    assert rc == 0
+    return M
+
+
+class SubspaceError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__("Cholesky failed at column %d" % (-code - 1) if code > -1000000 else "Jacobi did not converge")
+        self.code = code
+
+
+def subspace_diag(Hnm: np.ndarray, Snm: np.ndarray):
+    """(eps ascending, C) with H C = S C diag(eps), C^H S C = I; plus the Jacobi sweep count."""
+    cplx = np.iscomplexobj(Hnm) or np.iscomplexobj(Snm)
+    dt = np.complex128 if cplx else np.float64
+    H = _c(Hnm, dt)
+    S = _c(Snm, dt)
+    n = H.shape[0]
+    eps = np.zeros(n)
+    C = np.zeros((n, n), dtype=dt)
+    sweeps = ctypes.c_int(0)
+    rc = lib().oracle_subspace_diag(int(cplx), n, _ptr(H), _ptr(S), _ptr(eps), _ptr(C), ctypes.byref(sweeps))
+    if rc != 0:
+        raise SubspaceError(rc)
+    return eps, C, int(sweeps.value)
+
+
+def cholesky(S: np.ndarray) -> np.ndarray:
+    cplx = np.iscomplexobj(S)
+    S = _c(S, np.complex128 if cplx else np.float64)
+    L = np.zeros_like(S)
+    rc = lib().oracle_cholesky(int(cplx), S.shape[0], _ptr(S), _ptr(L))
+    if rc != 0:
+        raise SubspaceError(rc)
+    return L
+
+
+def jacobi_eigh(A: np.ndarray):
+    """(eigenvalues in Jacobi order, V, sweeps) with A = V diag V^H."""
+    cplx = np.iscomplexobj(A)
+    A = _c(A, np.complex128 if cplx else np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros_like(A)
+    sweeps = ctypes.c_int(0)
+    rc = lib().oracle_jacobi_eigh(int(cplx), n, _ptr(A), _ptr(w), _ptr(V), ctypes.byref(sweeps))
+    if rc != 0:
+        raise SubspaceError(-1000000)
+    return w, V, int(sweeps.value)
+
+
+def rotate(psi: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """psi'_m = sum_n psi_n C[n][m]."""
+    cplx = np.iscomplexobj(psi) or np.iscomplexobj(C)
+    dt = np.complex128 if cplx else np.float64
+    psi = _c(psi, dt)
+    C = _c(C, dt)
+    nb = C.shape[0]
+    K = psi.size // nb
+    out = np.empty_like(psi)
+    rc = lib().oracle_rotate(int(cplx), _ptr(psi), K, nb, _ptr(C), _ptr(out))
+    assert rc == 0
+    return out
+
+
+def rayleigh_ritz(system, psi: np.ndarray) -> dict:
+    """One eigensolver step: H psi, S psi, H_nm, S_nm, subspace diag, rotation (SCF step 1)."""
+    psi, nb = _psi_in(system, psi)
+    Hpsi, P = apply_H(system, psi)
+    Spsi, _ = apply_S(system, psi)
+    Hnm = gram(psi, Hpsi, system.dV, nb)
+    Snm = gram(psi, Spsi, system.dV, nb)
+    eps, C, sweeps = subspace_diag(Hnm, Snm)
+    psi_rot = rotate(psi, C)
+    return {"Hpsi": Hpsi, "Spsi": Spsi, "P": P, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "sweeps": sweeps,
+            "psi_rot": psi_rot}
