@@ -1,0 +1,139 @@
+/*
+ * pawfd.h -- C ABI of the GB300 (sm_103a) real-space PAW eigensolver-step library.
+ *
+ * The library applies the PAW Hamiltonian and overlap operators of Eq. (dh) of the PAW
+ * section of the paper (arXiv 2310.14776),
+ *
+ *     H = -1/2 nabla^2 + v(r) + sum_a sum_ii' |p_i^a> dH^a_ii' <p_i'^a|
+ *     S = 1               + sum_a sum_ii' |p_i^a> dS^a_ii' <p_i'^a|,
+ *
+ * to a block of wave functions on a uniform periodic grid (the finite-difference mode of
+ * the wave-function section: the kinetic operator is a stencil on a uniform Cartesian
+ * grid, here the order-6 central second difference), and performs the subspace
+ * diagonalization that opens each SCF step (Kohn-Sham section, step 1) with a dense
+ * Cholesky and eigensolver (parallelization section).  The generalized eigenproblem is
+ * H psi = eps S psi (PAW section, the PAW form of the Kohn-Sham equations).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: PAWFD_OK (0) or a negative PAWFD_E* code; pawfd_last_error() gives text.
+ *     No exception crosses this boundary.
+ *   - Grid arrays are [band][i3][i2][i1] with i1 (x) fastest, bands contiguous with stride
+ *     K = N1*N2*N3 elements.  Complex data is interleaved (re, im).
+ *   - Array arguments are DEVICE pointers owned by the caller unless marked "host".  The
+ *     library never frees caller memory.  It owns only what pawfd_create allocates
+ *     (projector tables, the shifted local potential, scratch), released by pawfd_destroy.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous; a device-side
+ *     failure (Cholesky pivot, eigensolver sweep cap, bounded wait) is recorded in the
+ *     context and returned by pawfd_sync() (and by the next call that synchronizes).
+ *   - Inputs and outputs may not alias unless stated.
+ */
+#ifndef PAWFD_H
+#define PAWFD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pawfd_ctx pawfd_ctx;
+
+/* wave-function storage / arithmetic type */
+enum {
+  PAWFD_R64 = 0,  /* real double, Gamma point (k must be 0)         */
+  PAWFD_C128 = 1  /* complex double, Bloch vector k                  */
+};
+
+/* error codes */
+enum {
+  PAWFD_OK = 0,
+  PAWFD_EINVAL = -1,    /* bad argument (size, pointer, layout)                          */
+  PAWFD_ENOMEM = -2,    /* device allocation in pawfd_create failed                       */
+  PAWFD_ENOTPD = -3,    /* S_nm not positive definite: Cholesky pivot <= 0 (column in text) */
+  PAWFD_ENOCONV = -4,   /* Jacobi eigensolver hit its sweep cap                           */
+  PAWFD_ETIMEDOUT = -5, /* a bounded device-side wait gave up                             */
+  PAWFD_EDEVICE = -6    /* CUDA runtime error (text from the runtime)                     */
+};
+
+/* One periodic orthorhombic cell.  All pointers here are HOST pointers, read during
+ * pawfd_create only (the library copies what it needs to the device).
+ *
+ * Projector p_i^a sampled on its box: the box of atom a covers the unwrapped grid indices
+ * box_lo[a][c] .. box_lo[a][c] + box_n[a][c] - 1 along axis c (x, y, z); an unwrapped index
+ * u stands for grid point u mod N_c in the cell translated by floor(u / N_c) * L_c, so boxes
+ * may cross faces and may even be larger than the cell.  proj holds, for atom a starting
+ * at proj_off[a], the values [I_a][box_n z][box_n y][box_n x].  dH and dS hold, for atom a
+ * starting at dmat_off[a], the real symmetric I_a x I_a matrices dH^a and dS^a (row-major). */
+typedef struct {
+  int n[3];                 /* grid points N1, N2, N3 (x, y, z), each >= 1                   */
+  double cell[3];           /* cell lengths L_c (bohr); spacing h_c = L_c / N_c              */
+  double k[3];              /* Bloch vector (1/bohr); must be 0 for PAWFD_R64                */
+  int dtype;                /* PAWFD_R64 or PAWFD_C128                                       */
+  int max_bands;            /* largest nb any later call will use (sizes the scratch)        */
+  int natoms;               /* A >= 0                                                        */
+  const int* nproj;         /* [A] I_a >= 1                                                  */
+  const int* box_lo;        /* [A][3]                                                        */
+  const int* box_n;         /* [A][3], each >= 1                                             */
+  const double* proj;       /* concatenated projector boxes                                  */
+  const long long* proj_off;/* [A+1]                                                         */
+  const double* dH;         /* concatenated dH^a                                             */
+  const double* dS;         /* concatenated dS^a                                             */
+  const long long* dmat_off;/* [A+1]                                                         */
+  const double* vloc;       /* [N3][N2][N1] local potential v(r) (Hartree)                   */
+} pawfd_system_desc;
+
+/* Create a context for one system; stream is a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns device tables sized for max_bands bands. */
+int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* desc, void* stream);
+int pawfd_destroy(pawfd_ctx* ctx);
+int pawfd_set_stream(pawfd_ctx* ctx, void* stream);
+
+/* Wait for the context's stream; returns the first device-side error recorded since the
+ * last pawfd_sync (and clears it), or PAWFD_OK. */
+int pawfd_sync(pawfd_ctx* ctx);
+const char* pawfd_last_error(const pawfd_ctx* ctx);
+
+/* number of projector rows Ip = sum_a I_a */
+int pawfd_nproj_total(const pawfd_ctx* ctx);
+
+/* number of CUDA kernels this context has launched so far (host-side counter) */
+long long pawfd_launch_count(const pawfd_ctx* ctx);
+
+/* Projector overlaps P[i][n] = <p_i^a | psi_n> = dV sum_r conj(p_i^a(r)) psi_n(r), for
+ * every atom a and projector i (global row i), n < nb.  Bloch phases exp(i k.T) of the
+ * lattice translation T of each box point are applied (projector overlaps of the PAW
+ * section; the atomic density matrix is built from them).
+ *   psi: [nb][K] (dtype of the context);  P: [Ip][nb] (same dtype). */
+int pawfd_project(pawfd_ctx* ctx, const void* psi, int nb, void* P);
+
+/* hpsi = H psi for nb bands (Eq. (dh)).  If P_out is not NULL it receives the projections
+ * of psi ([Ip][nb]); otherwise the context's scratch holds them.  psi, hpsi: [nb][K]. */
+int pawfd_apply_H(pawfd_ctx* ctx, const void* psi, int nb, void* hpsi, void* P_out);
+
+/* spsi = S psi for nb bands (PAW overlap operator).  P_out as for pawfd_apply_H. */
+int pawfd_apply_S(pawfd_ctx* ctx, const void* psi, int nb, void* spsi, void* P_out);
+
+/* The kinetic + local part alone: out = -1/2 Lap_FD psi + v psi (the finite-difference
+ * stencil hot spot of the development section, fused with the local potential). */
+int pawfd_apply_kinetic_local(pawfd_ctx* ctx, const void* psi, int nb, void* out);
+
+/* Gram matrix M[n][m] = dV sum_r conj(A_n(r)) B_m(r), n, m < nb; M is [nb][nb] of the
+ * context's dtype (double or interleaved complex double).  With B = H psi this is the
+ * subspace Hamiltonian H_nm, with B = S psi the subspace overlap S_nm. */
+int pawfd_gram(pawfd_ctx* ctx, const void* A, const void* B, int nb, void* M);
+
+/* Subspace diagonalization: given Hermitian H_nm and positive definite S_nm ([nb][nb],
+ * context dtype), solve H C = S C diag(eps): symmetrize, S = L L^H, A = L^-1 H L^-H,
+ * Jacobi A = U diag(eps) U^H, C = L^-H U.  eps (double [nb]) ascending with stable ties;
+ * each column of C (context dtype, [nb][nb], column m = eigenvector m) is S-normalized and
+ * multiplied by a unit phase that makes its largest-magnitude entry (first on ties) real
+ * and positive.  Hnm and Snm are overwritten (workspace).  Failures (PAWFD_ENOTPD with the
+ * failing column, PAWFD_ENOCONV) are reported by pawfd_sync. */
+int pawfd_subspace_diag(pawfd_ctx* ctx, int nb, void* Hnm, void* Snm, double* eps, void* C);
+
+/* Band rotation psi_out_m = sum_n psi_n C[n][m] (the rotation that completes the subspace
+ * diagonalization).  psi, psi_out: [nb][K]; C: [nb][nb]; psi_out must not alias psi. */
+int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* psi_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAWFD_H */

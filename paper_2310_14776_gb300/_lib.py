@@ -1,0 +1,68 @@
+"""ctypes binding of libpawfd.so (include/pawfd.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpawfd.so")
+
+PAWFD_R64 = 0
+PAWFD_C128 = 1
+ERRORS = {0: "PAWFD_OK", -1: "PAWFD_EINVAL", -2: "PAWFD_ENOMEM", -3: "PAWFD_ENOTPD", -4: "PAWFD_ENOCONV",
+          -5: "PAWFD_ETIMEDOUT", -6: "PAWFD_EDEVICE"}
+
+# every symbol include/pawfd.h declares, with its argument types
+VP, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+
+class SystemDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("cell", ctypes.c_double * 3), ("k", ctypes.c_double * 3),
+                ("dtype", ctypes.c_int), ("max_bands", ctypes.c_int), ("natoms", ctypes.c_int),
+                ("nproj", VP), ("box_lo", VP), ("box_n", VP), ("proj", VP), ("proj_off", VP),
+                ("dH", VP), ("dS", VP), ("dmat_off", VP), ("vloc", VP)]
+
+
+SIGNATURES = {
+    "pawfd_create": ([ctypes.POINTER(VP), ctypes.POINTER(SystemDesc), VP], I),
+    "pawfd_destroy": ([VP], I),
+    "pawfd_set_stream": ([VP, VP], I),
+    "pawfd_sync": ([VP], I),
+    "pawfd_last_error": ([VP], ctypes.c_char_p),
+    "pawfd_nproj_total": ([VP], I),
+    "pawfd_launch_count": ([VP], ctypes.c_longlong),
+    "pawfd_project": ([VP, VP, I, VP], I),
+    "pawfd_apply_H": ([VP, VP, I, VP, VP], I),
+    "pawfd_apply_S": ([VP, VP, I, VP, VP], I),
+    "pawfd_apply_kinetic_local": ([VP, VP, I, VP], I),
+    "pawfd_gram": ([VP, VP, VP, I, VP], I),
+    "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
+    "pawfd_rotate": ([VP, VP, I, VP, VP], I),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PawFDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library; raises if it has not been built (there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError("libpawfd.so not built: run paper_2310_14776_gb300.build.build() "
+                                   "(needs nvcc); the library has no CPU fallback")
+            L = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib

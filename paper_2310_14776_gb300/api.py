@@ -1,0 +1,189 @@
+"""Python front end of the C ABI: torch tensors in, device pointers out.
+
+PyTorch provides device memory and the current CUDA stream; every step of the eigensolver
+step runs in the CUDA kernels of libpawfd.so.  This module only checks shapes, dtypes and
+devices and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import PawFDError
+
+
+def _np_ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Context:
+    """One system (cell, grid, local potential, projector boxes, dH/dS) resident on the GPU.
+
+    ``system`` is a ``synth.System`` or any object with the same fields.  All band arrays are
+    torch tensors on the context's device, shaped [nb, N3, N2, N1] (float64 at the Gamma
+    point, complex128 with a Bloch vector), contiguous.
+    """
+
+    def __init__(self, system, max_bands: int, device: Optional[torch.device] = None):
+        self.lib = _lib.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if self.device.type != "cuda":
+            raise ValueError("the PAW library runs on CUDA devices only")
+        self.n = tuple(int(v) for v in system.n)
+        self.K = self.n[0] * self.n[1] * self.n[2]
+        self.complex = bool(system.complex_wf)
+        self.dtype = torch.complex128 if self.complex else torch.float64
+        self.max_bands = int(max_bands)
+        h = [system.cell[c] / self.n[c] for c in range(3)]
+        self.dV = h[0] * h[1] * h[2]
+        keep = dict(
+            nproj=np.ascontiguousarray(system.nproj, np.int32), box_lo=np.ascontiguousarray(system.box_lo, np.int32),
+            box_n=np.ascontiguousarray(system.box_n, np.int32), proj=np.ascontiguousarray(system.proj, np.float64),
+            proj_off=np.ascontiguousarray(system.proj_off, np.int64), dH=np.ascontiguousarray(system.dH, np.float64),
+            dS=np.ascontiguousarray(system.dS, np.float64), dmat_off=np.ascontiguousarray(system.dmat_off, np.int64),
+            vloc=np.ascontiguousarray(system.vloc, np.float64).reshape(-1))
+        d = _lib.SystemDesc()
+        d.n[:] = list(self.n)
+        d.cell[:] = [float(v) for v in system.cell]
+        d.k[:] = [float(v) for v in system.k]
+        d.dtype = _lib.PAWFD_C128 if self.complex else _lib.PAWFD_R64
+        d.max_bands = self.max_bands
+        d.natoms = int(len(keep["nproj"]))
+        for name in ("nproj", "box_lo", "box_n", "proj", "proj_off", "dH", "dS", "dmat_off", "vloc"):
+            setattr(d, name, _np_ptr(keep[name]) if keep[name].size else None)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.pawfd_create(ctypes.byref(self._h), ctypes.byref(d), self._stream())
+        if rc != 0:
+            raise PawFDError(rc, "pawfd_create failed (see stderr)")
+        self.Ip = int(self.lib.pawfd_nproj_total(self._h))
+
+    # ------------------------------------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _call(self, fn, *args):
+        self.lib.pawfd_set_stream(self._h, self._stream())
+        rc = fn(self._h, *args)
+        if rc != 0:
+            raise PawFDError(rc, self.lib.pawfd_last_error(self._h).decode())
+
+    def _bands(self, t: torch.Tensor, name: str) -> int:
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous %s tensor on %s" % (name, self.dtype, self.device))
+        if t.numel() % self.K:
+            raise ValueError("%s size is not a multiple of the grid size" % name)
+        return t.numel() // self.K
+
+    def _mat(self, t: torch.Tensor, nb: int, name: str):
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != nb * nb:
+            raise ValueError("%s must be a contiguous [%d, %d] %s tensor on %s" % (name, nb, nb, self.dtype, self.device))
+
+    def empty_bands(self, nb: int) -> torch.Tensor:
+        return torch.empty((nb,) + self.n[::-1], dtype=self.dtype, device=self.device)
+
+    # ------------------------------------------------------------------------------------
+    def sync(self):
+        """Wait for the context's work; raise the first device-side error (Cholesky, Jacobi, timeout)."""
+        rc = self.lib.pawfd_sync(self._h)
+        if rc != 0:
+            raise PawFDError(rc, self.lib.pawfd_last_error(self._h).decode())
+
+    def launch_count(self) -> int:
+        """CUDA kernels this context has launched (counted by the library)."""
+        return int(self.lib.pawfd_launch_count(self._h))
+
+    def kinetic_local(self, psi, out=None):
+        nb = self._bands(psi, "psi")
+        out = self.empty_bands(nb) if out is None else out
+        self._bands(out, "out")
+        self._call(self.lib.pawfd_apply_kinetic_local, ctypes.c_void_p(psi.data_ptr()), nb,
+                   ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def project(self, psi, P=None):
+        nb = self._bands(psi, "psi")
+        P = torch.empty((self.Ip, nb), dtype=self.dtype, device=self.device) if P is None else P
+        self._call(self.lib.pawfd_project, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(P.data_ptr()))
+        return P
+
+    def _apply(self, fn, psi, out, P):
+        nb = self._bands(psi, "psi")
+        out = self.empty_bands(nb) if out is None else out
+        self._bands(out, "out")
+        if P is not None and (P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous()):
+            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        self._call(fn, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(out.data_ptr()),
+                   ctypes.c_void_p(P.data_ptr()) if P is not None else None)
+        return out
+
+    def apply_H(self, psi, out=None, P=None):
+        return self._apply(self.lib.pawfd_apply_H, psi, out, P)
+
+    def apply_S(self, psi, out=None, P=None):
+        return self._apply(self.lib.pawfd_apply_S, psi, out, P)
+
+    def gram(self, A, B, M=None):
+        nb = self._bands(A, "A")
+        if self._bands(B, "B") != nb:
+            raise ValueError("A and B must hold the same number of bands")
+        M = torch.empty((nb, nb), dtype=self.dtype, device=self.device) if M is None else M
+        self._mat(M, nb, "M")
+        self._call(self.lib.pawfd_gram, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), nb,
+                   ctypes.c_void_p(M.data_ptr()))
+        return M
+
+    def subspace_diag(self, Hnm, Snm, eps=None, C=None, overwrite: bool = False, check: bool = True):
+        """(eps, C) of H C = S C diag(eps).  Inputs are copied unless ``overwrite``."""
+        nb = Hnm.shape[0]
+        self._mat(Hnm, nb, "Hnm")
+        self._mat(Snm, nb, "Snm")
+        if not overwrite:
+            Hnm, Snm = Hnm.clone(), Snm.clone()
+        eps = torch.empty(nb, dtype=torch.float64, device=self.device) if eps is None else eps
+        C = torch.empty((nb, nb), dtype=self.dtype, device=self.device) if C is None else C
+        self._mat(C, nb, "C")
+        self._call(self.lib.pawfd_subspace_diag, nb, ctypes.c_void_p(Hnm.data_ptr()), ctypes.c_void_p(Snm.data_ptr()),
+                   ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(C.data_ptr()))
+        if check:
+            self.sync()
+        return eps, C
+
+    def rotate(self, psi, C, out=None):
+        nb = self._bands(psi, "psi")
+        self._mat(C, nb, "C")
+        out = self.empty_bands(nb) if out is None else out
+        self._bands(out, "out")
+        self._call(self.lib.pawfd_rotate, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(C.data_ptr()),
+                   ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def rayleigh_ritz(self, psi, work: Optional[dict] = None, check: bool = True, keep_matrices: bool = False) -> dict:
+        """One eigensolver step: H psi, S psi, H_nm, S_nm, subspace diag, rotation.
+
+        ``work`` may hold preallocated outputs under the result's keys.  Unless
+        ``keep_matrices`` the returned Hnm / Snm are the solver's workspace after the solve."""
+        nb = self._bands(psi, "psi")
+        w = work if work is not None else {}
+        Hpsi = self.apply_H(psi, out=w.get("Hpsi"))
+        Spsi = self.apply_S(psi, out=w.get("Spsi"))
+        Hnm = self.gram(psi, Hpsi, M=w.get("Hnm"))
+        Snm = self.gram(psi, Spsi, M=w.get("Snm"))
+        eps, C = self.subspace_diag(Hnm, Snm, eps=w.get("eps"), C=w.get("C"), overwrite=not keep_matrices, check=check)
+        psi_rot = self.rotate(psi, C, out=w.get("psi_rot"))
+        return {"Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.pawfd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,337 @@
+// context.cu -- context creation: validates the system description and builds the device
+// tables (shifted local potential, folded projector boxes, atom colouring, scratch).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "pawfd_internal.cuh"
+
+namespace pawfd {
+
+int fail(pawfd_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int check_cuda(pawfd_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PAWFD_OK;
+  return fail(c, PAWFD_EDEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+template <class T>
+T* dev_alloc(pawfd_ctx* c, size_t count, int* rc) {
+  if (*rc != PAWFD_OK) return nullptr;
+  T* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sizeof(T) * (count ? count : 1));
+  if (e != cudaSuccess) {
+    *rc = fail(c, PAWFD_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  return p;
+}
+
+template <class T>
+void upload(pawfd_ctx* c, T* dst, const T* src, size_t count, int* rc) {
+  if (*rc != PAWFD_OK || count == 0) return;
+  *rc = check_cuda(c, cudaMemcpy(dst, src, sizeof(T) * count, cudaMemcpyHostToDevice), "cudaMemcpy H2D");
+}
+
+long long floor_div(long long u, long long n) { return (u >= 0) ? u / n : -((-u + n - 1) / n); }
+
+struct BoxPoint {
+  long long grid;   // wrapped grid index
+  long long j;      // index inside the box
+  double kt;        // k . T of the image this point belongs to
+};
+
+// Fold atom a's box onto the grid: G[i][q] = sum over box points j that wrap onto the q-th
+// unique grid point of p_i(j) * exp(-i k.T_j).  The projection uses conj(G), the back-add G.
+void fold_atom(const pawfd_system_desc* d, int a, std::vector<int>& pts, std::vector<double>& g_re,
+               std::vector<double>& g_im) {
+  const int* lo = d->box_lo + 3 * a;
+  const int* bn = d->box_n + 3 * a;
+  const long long bsize = (long long)bn[0] * bn[1] * bn[2];
+  const int I = d->nproj[a];
+  std::vector<BoxPoint> bp;
+  bp.reserve(bsize);
+  for (int j3 = 0; j3 < bn[2]; ++j3)
+    for (int j2 = 0; j2 < bn[1]; ++j2)
+      for (int j1 = 0; j1 < bn[0]; ++j1) {
+        long long u[3] = {(long long)lo[0] + j1, (long long)lo[1] + j2, (long long)lo[2] + j3};
+        long long w[3];
+        double kt = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          long long t = floor_div(u[c], d->n[c]);
+          w[c] = u[c] - t * d->n[c];
+          kt += d->k[c] * d->cell[c] * (double)t;
+        }
+        long long grid = (w[2] * d->n[1] + w[1]) * d->n[0] + w[0];
+        bp.push_back(BoxPoint{grid, ((long long)j3 * bn[1] + j2) * bn[0] + j1, kt});
+      }
+  std::stable_sort(bp.begin(), bp.end(), [](const BoxPoint& x, const BoxPoint& y) { return x.grid < y.grid; });
+  pts.clear();
+  std::vector<size_t> first;
+  for (size_t q = 0; q < bp.size(); ++q)
+    if (q == 0 || bp[q].grid != bp[q - 1].grid) {
+      pts.push_back((int)bp[q].grid);
+      first.push_back(q);
+    }
+  first.push_back(bp.size());
+  const size_t np = pts.size();
+  g_re.assign((size_t)I * np, 0.0);
+  g_im.assign((size_t)I * np, 0.0);
+  const double* p = d->proj + d->proj_off[a];
+  for (size_t q = 0; q < np; ++q)
+    for (size_t e = first[q]; e < first[q + 1]; ++e) {
+      const double cr = std::cos(bp[e].kt), ci = -std::sin(bp[e].kt);
+      for (int i = 0; i < I; ++i) {
+        const double val = p[(size_t)i * bsize + bp[e].j];
+        g_re[(size_t)i * np + q] += val * cr;
+        g_im[(size_t)i * np + q] += val * ci;
+      }
+    }
+}
+
+int validate(const pawfd_system_desc* d, std::string& why) {
+  if (!d) return why = "desc is NULL", PAWFD_EINVAL;
+  for (int c = 0; c < 3; ++c) {
+    if (d->n[c] < 1) return why = "grid size must be >= 1", PAWFD_EINVAL;
+    if (!(d->cell[c] > 0.0)) return why = "cell lengths must be > 0", PAWFD_EINVAL;
+  }
+  if ((long long)d->n[0] * d->n[1] * d->n[2] > (1ll << 31) - 1) return why = "grid too large", PAWFD_EINVAL;
+  if (d->dtype != PAWFD_R64 && d->dtype != PAWFD_C128) return why = "unsupported dtype", PAWFD_EINVAL;
+  if (d->dtype == PAWFD_R64 && (d->k[0] != 0.0 || d->k[1] != 0.0 || d->k[2] != 0.0))
+    return why = "real wave functions need k = 0", PAWFD_EINVAL;
+  if (d->max_bands < 1) return why = "max_bands must be >= 1", PAWFD_EINVAL;
+  if (!d->vloc) return why = "vloc is NULL", PAWFD_EINVAL;
+  if (d->natoms < 0) return why = "natoms < 0", PAWFD_EINVAL;
+  if (d->natoms > 0) {
+    if (!d->nproj || !d->box_lo || !d->box_n || !d->proj || !d->proj_off || !d->dH || !d->dS || !d->dmat_off)
+      return why = "atom arrays missing", PAWFD_EINVAL;
+    for (int a = 0; a < d->natoms; ++a) {
+      if (d->nproj[a] < 1 || d->nproj[a] > 32) return why = "nproj must be in 1..32", PAWFD_EINVAL;
+      for (int c = 0; c < 3; ++c)
+        if (d->box_n[3 * a + c] < 1) return why = "box sizes must be >= 1", PAWFD_EINVAL;
+      const long long bsize = (long long)d->box_n[3 * a] * d->box_n[3 * a + 1] * d->box_n[3 * a + 2];
+      if (d->proj_off[a + 1] - d->proj_off[a] != bsize * d->nproj[a])
+        return why = "proj_off inconsistent with box sizes", PAWFD_EINVAL;
+      if (d->dmat_off[a + 1] - d->dmat_off[a] != (long long)d->nproj[a] * d->nproj[a])
+        return why = "dmat_off inconsistent with nproj", PAWFD_EINVAL;
+    }
+  }
+  return PAWFD_OK;
+}
+
+}  // namespace
+
+int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
+  int rc = PAWFD_OK;
+  AtomTables& at = c->at;
+  at.natoms = d->natoms;
+  const bool cplx = c->dtype == PAWFD_C128;
+  std::vector<int> all_pts;
+  std::vector<double> all_re, all_im;
+  at.pt_off.assign(1, 0);
+  at.g_off.assign(1, 0);
+  at.row_off.assign(1, 0);
+  at.dmat_off.assign(d->dmat_off, d->dmat_off + d->natoms + 1);
+  for (int a = 0; a < d->natoms; ++a) {
+    std::vector<int> pts;
+    std::vector<double> re, im;
+    fold_atom(d, a, pts, re, im);
+    at.nproj.push_back(d->nproj[a]);
+    at.npts.push_back((int)pts.size());
+    all_pts.insert(all_pts.end(), pts.begin(), pts.end());
+    all_re.insert(all_re.end(), re.begin(), re.end());
+    all_im.insert(all_im.end(), im.begin(), im.end());
+    at.pt_off.push_back(at.pt_off.back() + (long long)pts.size());
+    at.g_off.push_back(at.g_off.back() + (long long)re.size());
+    at.row_off.push_back(at.row_off.back() + d->nproj[a]);
+    at.Imax = std::max(at.Imax, d->nproj[a]);
+  }
+  at.Ip = at.row_off.back();
+
+  // colouring: atoms whose folded boxes share a grid point get different colours
+  std::vector<uint64_t> used((size_t)c->K, 0);
+  std::vector<int> color_of(d->natoms, 0);
+  int ncolors = 0;
+  for (int a = 0; a < d->natoms; ++a) {
+    uint64_t forbidden = 0;
+    for (long long q = at.pt_off[a]; q < at.pt_off[a + 1]; ++q) forbidden |= used[all_pts[q]];
+    int col = 0;
+    while (col < 64 && (forbidden >> col) & 1ull) ++col;
+    if (col == 64) return fail(c, PAWFD_EINVAL, "more than 64 mutually overlapping projector boxes");
+    color_of[a] = col;
+    ncolors = std::max(ncolors, col + 1);
+    for (long long q = at.pt_off[a]; q < at.pt_off[a + 1]; ++q) used[all_pts[q]] |= (1ull << col);
+  }
+  std::vector<int> color_atoms;
+  at.color_off.assign(1, 0);
+  at.colors.assign(ncolors, {});
+  for (int col = 0; col < ncolors; ++col) {
+    for (int a = 0; a < d->natoms; ++a)
+      if (color_of[a] == col) {
+        color_atoms.push_back(a);
+        at.colors[col].push_back(a);
+      }
+    at.color_off.push_back((int)color_atoms.size());
+  }
+
+  const int A = d->natoms;
+  at.d_nproj = dev_alloc<int>(c, A, &rc);
+  at.d_row_off = dev_alloc<int>(c, A + 1, &rc);
+  at.d_npts = dev_alloc<int>(c, A, &rc);
+  at.d_pt_off = dev_alloc<long long>(c, A + 1, &rc);
+  at.d_pts = dev_alloc<int>(c, all_pts.size(), &rc);
+  at.d_g_off = dev_alloc<long long>(c, A + 1, &rc);
+  at.d_dmat_off = dev_alloc<long long>(c, A + 1, &rc);
+  const long long ndm = A ? d->dmat_off[A] : 0;
+  at.d_dH = dev_alloc<double>(c, ndm, &rc);
+  at.d_dS = dev_alloc<double>(c, ndm, &rc);
+  at.d_color_atoms = dev_alloc<int>(c, color_atoms.size(), &rc);
+  upload(c, at.d_nproj, at.nproj.data(), A, &rc);
+  upload(c, at.d_row_off, at.row_off.data(), A + 1, &rc);
+  upload(c, at.d_npts, at.npts.data(), A, &rc);
+  upload(c, at.d_pt_off, at.pt_off.data(), A + 1, &rc);
+  upload(c, at.d_pts, all_pts.data(), all_pts.size(), &rc);
+  upload(c, at.d_g_off, at.g_off.data(), A + 1, &rc);
+  upload(c, at.d_dmat_off, at.dmat_off.data(), A + 1, &rc);
+  upload(c, at.d_dH, d->dH, ndm, &rc);
+  upload(c, at.d_dS, d->dS, ndm, &rc);
+  upload(c, at.d_color_atoms, color_atoms.data(), color_atoms.size(), &rc);
+  if (cplx) {
+    std::vector<zd> g(all_re.size());
+    for (size_t q = 0; q < g.size(); ++q) g[q] = zd{all_re[q], all_im[q]};
+    zd* dg = dev_alloc<zd>(c, g.size(), &rc);
+    upload(c, dg, g.data(), g.size(), &rc);
+    at.d_g = dg;
+  } else {
+    double* dg = dev_alloc<double>(c, all_re.size(), &rc);
+    upload(c, dg, all_re.data(), all_re.size(), &rc);
+    at.d_g = dg;
+  }
+  return rc;
+}
+
+void free_ctx(pawfd_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
+                  c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
+                  c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_status) cudaFreeHost(c->h_status);
+  delete c;
+}
+
+}  // namespace pawfd
+
+using namespace pawfd;
+
+extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* stream) {
+  if (!out) return PAWFD_EINVAL;
+  *out = nullptr;
+  pawfd_ctx* c = new pawfd_ctx();
+  std::string why;
+  int rc = validate(d, why);
+  if (rc != PAWFD_OK) {
+    delete c;
+    fprintf(stderr, "pawfd_create: %s\n", why.c_str());
+    return rc;
+  }
+  for (int i = 0; i < 3; ++i) {
+    c->n[i] = d->n[i];
+    c->cell[i] = d->cell[i];
+    c->k[i] = d->k[i];
+    c->h[i] = d->cell[i] / d->n[i];
+  }
+  c->dV = c->h[0] * c->h[1] * c->h[2];
+  c->dtype = d->dtype;
+  c->max_bands = d->max_bands;
+  c->K = (size_t)d->n[0] * d->n[1] * d->n[2];
+  c->stream = (cudaStream_t)stream;
+  int dev = 0;
+  rc = check_cuda(c, cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev), "attr");
+
+  // shifted local potential: the centre weight of the three 1-D stencils folded into v
+  if (rc == PAWFD_OK) {
+    std::vector<double> vs(c->K);
+    const double centre = -0.5 * FD6_W0 * (1.0 / (c->h[0] * c->h[0]) + 1.0 / (c->h[1] * c->h[1]) +
+                                           1.0 / (c->h[2] * c->h[2]));
+    for (size_t r = 0; r < c->K; ++r) vs[r] = d->vloc[r] + centre;
+    c->d_vshift = dev_alloc<double>(c, c->K, &rc);
+    upload(c, c->d_vshift, vs.data(), c->K, &rc);
+  }
+  if (rc == PAWFD_OK) rc = build_tables(c, d);
+  const size_t ss = scalar_size(c);
+  const size_t nb = (size_t)c->max_bands;
+  if (rc == PAWFD_OK) {
+    c->d_P = dev_alloc<char>(c, ss * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
+    // split-K partials: enough for ~2 waves of 64x64 tiles at max_bands, capped at 256 MB
+    const size_t tiles = ((nb + 63) / 64) * ((nb + 63) / 64);
+    size_t nsplit = std::max<size_t>(1, std::min<size_t>(64, (2 * (size_t)c->num_sms + tiles - 1) / tiles));
+    while (nsplit > 1 && nsplit * nb * nb * ss > (256ull << 20)) --nsplit;
+    c->gram_part_bytes = nsplit * nb * nb * ss;
+    c->d_gram_part = dev_alloc<char>(c, c->gram_part_bytes, &rc);
+    c->d_work = dev_alloc<char>(c, 7 * nb * nb * ss, &rc);
+    c->d_evals = dev_alloc<double>(c, nb, &rc);
+    c->d_barrier = dev_alloc<unsigned>(c, 4, &rc);
+    c->d_status = dev_alloc<DeviceStatus>(c, 1, &rc);
+    c->d_reduce = dev_alloc<double>(c, 4096, &rc);
+  }
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMallocHost(&c->h_status, sizeof(DeviceStatus)), "cudaMallocHost");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_barrier, 0, 4 * sizeof(unsigned)), "memset");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_status, 0, sizeof(DeviceStatus)), "memset");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaDeviceSynchronize(), "create sync");
+  if (rc != PAWFD_OK) {
+    fprintf(stderr, "pawfd_create: %s\n", c->err.c_str());
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return PAWFD_OK;
+}
+
+extern "C" int pawfd_destroy(pawfd_ctx* c) {
+  if (!c) return PAWFD_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  free_ctx(c);
+  return PAWFD_OK;
+}
+
+extern "C" int pawfd_set_stream(pawfd_ctx* c, void* stream) {
+  if (!c) return PAWFD_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return PAWFD_OK;
+}
+
+extern "C" const char* pawfd_last_error(const pawfd_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+extern "C" int pawfd_nproj_total(const pawfd_ctx* c) { return c ? c->at.Ip : PAWFD_EINVAL; }
+
+extern "C" long long pawfd_launch_count(const pawfd_ctx* c) { return c ? c->launches : PAWFD_EINVAL; }
+
+extern "C" int pawfd_sync(pawfd_ctx* c) {
+  if (!c) return PAWFD_EINVAL;
+  int rc = check_cuda(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost,
+                                         c->stream), "status copy");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamSynchronize(c->stream), "cudaStreamSynchronize");
+  if (rc != PAWFD_OK) return rc;
+  const DeviceStatus st = *c->h_status;
+  if (st.code == 0) return PAWFD_OK;
+  cudaMemsetAsync(c->d_status, 0, sizeof(DeviceStatus), c->stream);
+  cudaStreamSynchronize(c->stream);
+  char buf[160];
+  switch (st.code) {
+    case PAWFD_ENOTPD: snprintf(buf, sizeof buf, "S_nm not positive definite: Cholesky pivot <= 0 at column %d", st.detail); break;
+    case PAWFD_ENOCONV: snprintf(buf, sizeof buf, "Jacobi eigensolver did not converge within %d sweeps", st.detail); break;
+    case PAWFD_ETIMEDOUT: snprintf(buf, sizeof buf, "device barrier wait gave up (barrier %d)", st.detail); break;
+    default: snprintf(buf, sizeof buf, "device error %d (detail %d)", st.code, st.detail); break;
+  }
+  return fail(c, st.code, buf);
+}

@@ -1,0 +1,237 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (FP64 path): H psi, S psi, projections, Gram matrices and rotations agree to
+1e-12 relative (per band 2-norm, and max-abs relative to the largest entry); eigenvalues
+agree to 1e-10 Ha.  Eigenvectors are compared through C^H S C = I and C^H H C = diag(eps)
+and the phase rule, never element by element (degenerate and near-degenerate pairs make
+them non-unique).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2310_14776_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+EPS_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def ctx_for(system, nb, dev):
+    from paper_2310_14776_gb300 import api
+    return api.Context(system, max_bands=nb, device=dev)
+
+
+def to_dev(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def assert_close_bands(got, ref, nb, rel=REL):
+    got = got.reshape(nb, -1)
+    ref = ref.reshape(nb, -1)
+    err = np.linalg.norm(got - ref, axis=1)
+    nrm = np.linalg.norm(ref, axis=1)
+    assert np.all(err <= rel * np.maximum(nrm, 1e-300)), (err / nrm).max()
+    assert np.max(np.abs(got - ref)) <= rel * max(np.max(np.abs(ref)), 1e-300)
+
+
+def assert_close_matrix(got, ref, rel=REL):
+    assert np.max(np.abs(got - ref)) <= rel * max(np.max(np.abs(ref)), 1e-300), np.max(np.abs(got - ref))
+
+
+def check_subspace(eps, C, Hnm, Snm, ref_eps, tol=EPS_TOL):
+    nb = len(eps)
+    assert np.all(np.diff(eps) >= 0)
+    assert np.max(np.abs(eps - ref_eps)) <= tol, np.max(np.abs(eps - ref_eps))
+    Sh = 0.5 * (Snm + Snm.conj().T)
+    Hh = 0.5 * (Hnm + Hnm.conj().T)
+    assert np.allclose(C.conj().T @ Sh @ C, np.eye(nb), rtol=0, atol=1e-11)
+    assert np.allclose(C.conj().T @ Hh @ C, np.diag(eps), rtol=0, atol=1e-11 * max(1.0, np.max(np.abs(eps))))
+    for m in range(nb):
+        i = np.argmax(np.abs(C[:, m]))
+        assert abs(np.imag(C[i, m])) <= 1e-14 * abs(C[i, m]) and np.real(C[i, m]) > 0
+
+
+def full_step_parity(system, nb, seed, dev):
+    psi = synth.make_psi(system, nb, seed)
+    ctx = ctx_for(system, nb, dev)
+    psi_d = to_dev(psi, dev)
+    res = ctx.rayleigh_ritz(psi_d, keep_matrices=True)
+    P = ctx.project(psi_d).cpu().numpy()
+    T = ctx.kinetic_local(psi_d).cpu().numpy()
+    torch.cuda.synchronize(dev)
+    ref = O.rayleigh_ritz(system, psi)
+    assert_close_bands(T, O.kinetic_local(system, psi), nb)
+    assert_close_bands(res["Hpsi"].cpu().numpy(), ref["Hpsi"], nb)
+    assert_close_bands(res["Spsi"].cpu().numpy(), ref["Spsi"], nb)
+    if system.natoms:
+        assert_close_matrix(P, ref["P"])
+    Hnm = res["Hnm"].cpu().numpy()
+    Snm = res["Snm"].cpu().numpy()
+    assert_close_matrix(Hnm, ref["Hnm"])
+    assert_close_matrix(Snm, ref["Snm"])
+    eps = res["eps"].cpu().numpy()
+    C = res["C"].cpu().numpy()
+    check_subspace(eps, C, ref["Hnm"], ref["Snm"], ref["eps"])
+    # rotation with the GPU's own C against the oracle's rotation of the same C
+    assert_close_bands(res["psi_rot"].cpu().numpy(), O.rotate(psi, C), nb)
+    ctx.close()
+
+
+def test_gamma_24c_16b_full_step(dev):
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    full_step_parity(w.system(), w.nbands, w.seed, dev)
+
+
+def test_bloch_small_full_step(dev):
+    s = synth.make_system((20, 18, 16), (8.0, 7.2, 6.4), 3, synth.PSET_SPD2, seed=201, k=(0.31, -0.22, 0.47),
+                          complex_wf=True)
+    full_step_parity(s, 12, 202, dev)
+
+
+@pytest.mark.parametrize("case", [
+    # ragged grid: no axis a multiple of the 32 x 8 tile, several tiles along each axis
+    dict(n=(45, 19, 13), cell=(9.0, 7.6, 5.2), natoms=4, pset=synth.PSET_SPD2, nb=5, cplx=False),
+    # the same with a Bloch vector
+    dict(n=(45, 19, 13), cell=(9.0, 7.6, 5.2), natoms=4, pset=synth.PSET_SPD2, nb=5, cplx=True),
+    # grid axes shorter than the stencil reach, boxes larger than the cell (self-wrapping)
+    dict(n=(5, 6, 4), cell=(2.5, 3.0, 2.0), natoms=2, pset=synth.PSET_SP, nb=3, cplx=True),
+    # one band, no atoms
+    dict(n=(16, 9, 7), cell=(6.0, 4.0, 3.0), natoms=0, pset=synth.PSET_SP, nb=1, cplx=False),
+    # odd band count (Jacobi pads the pairing), many overlapping boxes
+    dict(n=(24, 20, 18), cell=(6.0, 5.0, 4.5), natoms=12, pset=synth.PSET_SPD2, nb=17, cplx=True),
+])
+def test_edge_cases(dev, case):
+    k = (0.4, -0.3, 0.2) if case["cplx"] else (0.0, 0.0, 0.0)
+    s = synth.make_system(case["n"], case["cell"], case["natoms"], case["pset"], seed=300, k=k,
+                          complex_wf=case["cplx"])
+    full_step_parity(s, case["nb"], 301, dev)
+
+
+def test_repeatable_bitwise(dev):
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    s = w.system()
+    ctx = ctx_for(s, w.nbands, dev)
+    psi_d = to_dev(w.psi(s), dev)
+    a = ctx.rayleigh_ritz(psi_d, keep_matrices=True)
+    a = {k: v.clone() for k, v in a.items()}
+    b = ctx.rayleigh_ritz(psi_d, keep_matrices=True)
+    for key in ("Hpsi", "Spsi", "Hnm", "Snm", "eps", "C", "psi_rot"):
+        assert torch.equal(a[key], b[key]), key
+    ctx.close()
+
+
+def test_band_subset_equals_full_block(dev):
+    # bands are independent in apply_H: a sub-block gives the same numbers as the full block
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    s = w.system()
+    ctx = ctx_for(s, w.nbands, dev)
+    psi_d = to_dev(w.psi(s), dev)
+    full = ctx.apply_H(psi_d)
+    part = ctx.apply_H(psi_d[3:8].contiguous())
+    assert torch.equal(full[3:8], part)
+    ctx.close()
+
+
+def test_argument_errors(dev):
+    from paper_2310_14776_gb300 import api
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    s = w.system()
+    ctx = ctx_for(s, 4, dev)
+    psi_d = to_dev(w.psi(s, nb=8), dev)
+    with pytest.raises(api.PawFDError) as e:
+        ctx.apply_H(psi_d)                      # 8 bands > max_bands = 4
+    assert e.value.code == -1
+    with pytest.raises(ValueError):
+        ctx.apply_H(psi_d[:2].float())          # wrong dtype
+    ctx.close()
+
+
+def test_not_positive_definite_is_reported(dev):
+    from paper_2310_14776_gb300 import api
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    ctx = ctx_for(w.system(), 8, dev)
+    H = torch.eye(8, dtype=torch.float64, device=dev)
+    S = torch.eye(8, dtype=torch.float64, device=dev)
+    S[5, 5] = -1.0
+    with pytest.raises(api.PawFDError) as e:
+        ctx.subspace_diag(H, S)
+    assert e.value.code == -3 and "column 5" in str(e.value)
+    # the context stays usable after the reported failure
+    eps, C = ctx.subspace_diag(H, torch.eye(8, dtype=torch.float64, device=dev))
+    assert torch.allclose(eps, torch.ones(8, dtype=torch.float64, device=dev))
+    ctx.close()
+
+
+def test_subspace_against_oracle_random(dev):
+    # Hermitian H, positive definite S of several sizes, real and complex
+    from paper_2310_14776_gb300 import api
+    s = synth.WORKLOADS["gamma-24c-16b"].system()
+    for cplx in (False, True):
+        sysm = synth.make_system((8, 8, 8), (4.0, 4.0, 4.0), 0, synth.PSET_SP, 1, k=(0.1, 0.0, 0.0) if cplx else
+                                 (0.0, 0.0, 0.0), complex_wf=cplx)
+        ctx = ctx_for(sysm, 200, dev)
+        for n in (1, 2, 3, 31, 64, 200):
+            A = synth.uniform(n, 1, n * n, -1, 1).reshape(n, n)
+            B = synth.uniform(n, 2, n * n, -1, 1).reshape(n, n)
+            if cplx:
+                A = A + 1j * synth.uniform(n, 3, n * n, -1, 1).reshape(n, n)
+                B = B + 1j * synth.uniform(n, 4, n * n, -1, 1).reshape(n, n)
+            H = 0.5 * (A + A.conj().T) * 30
+            S = B @ B.conj().T / n + np.eye(n)
+            ref_eps, _, _ = O.subspace_diag(H, S)
+            eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
+            check_subspace(eps.cpu().numpy(), C.cpu().numpy(), H, S, ref_eps)
+        ctx.close()
+    del s, api
+
+
+@pytest.mark.slow
+def test_gamma_96c_256b_full_size(dev):
+    """The benchmark workload at full size, in the benchmark's launch configuration."""
+    w = synth.WORKLOADS["gamma-96c-256b"]
+    s = w.system()
+    psi = w.psi(s)
+    nb = w.nbands
+    ctx = ctx_for(s, nb, dev)
+    psi_d = to_dev(psi, dev)
+    res = ctx.rayleigh_ritz(psi_d, keep_matrices=True)
+    torch.cuda.synchronize(dev)
+    # sampled bands for the grid operators (bands are independent)
+    idx = [0, 1, 77, 128, 255]
+    ref_H, ref_P = O.apply_H(s, psi[idx])
+    ref_S, _ = O.apply_S(s, psi[idx])
+    assert_close_bands(res["Hpsi"][idx].cpu().numpy(), ref_H, len(idx))
+    assert_close_bands(res["Spsi"][idx].cpu().numpy(), ref_S, len(idx))
+    P = ctx.project(psi_d).cpu().numpy()
+    assert_close_matrix(P[:, idx], ref_P)
+    # sampled Gram entries
+    Hnm = res["Hnm"].cpu().numpy()
+    sub = O.gram(psi[idx], ref_H, s.dV, len(idx))
+    assert_close_matrix(Hnm[np.ix_(idx, idx)], sub)
+    # full eigenvalue parity against the oracle's full step
+    ref = O.rayleigh_ritz(s, psi)
+    check_subspace(res["eps"].cpu().numpy(), res["C"].cpu().numpy(), ref["Hnm"], ref["Snm"], ref["eps"])
+    rot = res["psi_rot"][idx].cpu().numpy()
+    C = res["C"].cpu().numpy()
+    ref_rot = np.einsum("nm,nk->mk", C[:, idx], psi.reshape(nb, -1))
+    assert_close_bands(rot, ref_rot, len(idx))
+    # the ten repeated iterations of the workload reproduce the first eigenvalues
+    eps0 = res["eps"].clone()
+    cur = res["psi_rot"]
+    for _ in range(2):
+        r2 = ctx.rayleigh_ritz(cur)
+        assert torch.max(torch.abs(r2["eps"] - eps0)).item() <= 1e-10
+        cur = r2["psi_rot"].clone()
+    ctx.close()
