@@ -133,6 +133,29 @@ int pawfd_subspace_diag(pawfd_ctx* ctx, int nb, void* Hnm, void* Snm, double* ep
  * diagonalization).  psi, psi_out: [nb][K]; C: [nb][nb]; psi_out must not alias psi. */
 int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* psi_out);
 
+/* Gram matrix for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this is a packaging variant of pawfd_gram.  It is for code
+ * that must not call cudaMalloc where it needs the Gram matrix -- for example an application
+ * whose device memory is wholly owned by its own pool allocator, or a serving loop that
+ * cannot afford cudaMalloc's device synchronization and unbounded latency -- and which
+ * therefore cannot create a pawfd context either.  It needs no context and allocates
+ * nothing: M[n][m] = dV sum_r conj(A_n(r)) B_m(r) for n, m < nb, exactly as pawfd_gram,
+ * with the split-K partial tiles kept in a fixed 8 MiB array that lives in the library's
+ * device image.
+ *   A, B:   device [nb][K] arrays of dtype (PAWFD_R64 or PAWFD_C128); M: device [nb][nb].
+ *   stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Returns PAWFD_EINVAL for null pointers, K < 1, nb < 1, an unknown dtype, or when one
+ * nb x nb partial does not fit in the 8 MiB array (nb > 1024 real, nb > 724 complex);
+ * PAWFD_EDEVICE for a CUDA runtime failure.
+ * Notes: every GPU that loads the library holds the 8 MiB array until the process exits.
+ * The first call on each device looks up the array's device address (once per device, with
+ * that device current); make that first call before any stream capture.  All calls share
+ * the one array: calls whose work overlaps on the GPU race on it.  Each call overwrites all
+ * the partial entries it reads, so no clearing between calls is needed. */
+int pawfd_gram_noalloc(const void* A, const void* B, long long K, int nb, int dtype, double dV, void* M,
+                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

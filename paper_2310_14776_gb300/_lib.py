@@ -39,6 +39,7 @@ SIGNATURES = {
     "pawfd_gram": ([VP, VP, VP, I, VP], I),
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
+    "pawfd_gram_noalloc": ([VP, VP, ctypes.c_longlong, I, I, D, VP, VP], I),
 }
 
 _lock = threading.Lock()

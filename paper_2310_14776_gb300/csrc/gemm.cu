@@ -10,6 +10,7 @@
 // The Gram kernel splits the long grid dimension across CTAs and reduces the partial
 // tiles in a fixed order, so the result is deterministic.
 #include <algorithm>
+#include <mutex>
 
 #include "pawfd_internal.cuh"
 
@@ -167,3 +168,91 @@ int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* ou
 }
 
 }  // namespace pawfd
+
+// ------------------------------------------------------------------------------------------
+// Gram matrix without any device allocation (pawfd_gram_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a Gram matrix:
+// an application whose device memory is entirely claimed by its own pool allocator, or a
+// latency-bound serving loop that must never call cudaMalloc (which can synchronize the
+// device and has no bounded latency).  They cannot create a pawfd context either, since
+// pawfd_create allocates.  This entry point runs the same split-K kernels as pawfd_gram but
+// keeps the partial tiles in a fixed, file-scope device array instead of context scratch.
+//
+// Cost of that choice: every GPU that loads this library holds NOALLOC_SCRATCH_BYTES for the
+// array until the process exits, and all calls share the one array, so calls whose work
+// overlaps on the GPU (different streams, threads or processes sharing a context) race on
+// it.  Each call writes every partial entry it later reads, so nothing has to be cleared
+// between calls; the array simply keeps the last call's partials.
+// ------------------------------------------------------------------------------------------
+namespace pawfd {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 8u << 20;   // 8 MiB of split-K partials
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the array's name
+// only stands for the device symbol; its address must be asked from the runtime, once per
+// device, with that device current.
+int noalloc_scratch(void** out, int* sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PAWFD_EDEVICE;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PAWFD_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PAWFD_EDEVICE;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAWFD_EDEVICE;
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_sms[dev] = n;
+  }
+  *out = g_noalloc_ptr[dev];
+  *sms = g_noalloc_sms[dev];
+  return PAWFD_OK;
+}
+
+template <class T>
+int gram_noalloc_impl(const T* A, const T* B, long long K, int nb, double dV, T* M, cudaStream_t stream,
+                      T* part, int num_sms) {
+  const int tiles = ((nb + TM - 1) / TM) * ((nb + TM - 1) / TM);
+  const long long per = (long long)nb * nb * (long long)sizeof(T);
+  long long nsplit = std::max<long long>(1, (2ll * num_sms + tiles - 1) / tiles);
+  nsplit = std::min<long long>(nsplit, (long long)NOALLOC_SCRATCH_BYTES / per);
+  nsplit = std::min<long long>(nsplit, std::max<long long>(1, K / (4 * TK)));
+  long long kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + TK - 1) / TK * TK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  dim3 grid((nb + TM - 1) / TM, (nb + TM - 1) / TM, (unsigned)nsplit);
+  gram_partial_kernel<T><<<grid, NT, 0, stream>>>(A, B, nb, K, kchunk, part);
+  const long long nn = (long long)nb * nb;
+  gram_reduce_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(part, (int)nsplit, nb, dV, M);
+  return cudaGetLastError() == cudaSuccess ? PAWFD_OK : PAWFD_EDEVICE;
+}
+
+}  // namespace
+}  // namespace pawfd
+
+extern "C" int pawfd_gram_noalloc(const void* A, const void* B, long long K, int nb, int dtype, double dV, void* M,
+                                  void* stream) {
+  using namespace pawfd;
+  if (!A || !B || !M || K < 1 || nb < 1) return PAWFD_EINVAL;
+  if (dtype != PAWFD_R64 && dtype != PAWFD_C128) return PAWFD_EINVAL;
+  const size_t elem = dtype == PAWFD_C128 ? sizeof(zd) : sizeof(double);
+  if ((size_t)nb * (size_t)nb * elem > NOALLOC_SCRATCH_BYTES) return PAWFD_EINVAL;   // one partial must fit
+  void* scratch = nullptr;
+  int sms = 0;
+  const int rc = noalloc_scratch(&scratch, &sms);
+  if (rc != PAWFD_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dtype == PAWFD_C128)
+    return gram_noalloc_impl<zd>((const zd*)A, (const zd*)B, K, nb, dV, (zd*)M, s, (zd*)scratch, sms);
+  return gram_noalloc_impl<double>((const double*)A, (const double*)B, K, nb, dV, (double*)M, s,
+                                   (double*)scratch, sms);
+}
