@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 from paper_2310_14776_gb300 import synth  # noqa: E402
 
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe kernel on this machine
 
 
 def parse_args():
@@ -44,6 +45,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     return p.parse_args()
 
 
@@ -133,13 +135,15 @@ def run_gpu(args):
     nb, K = w.nbands, system.npoints
     psi_host = w.psi(system)
     cplx = system.complex_wf
-    ctx = api.Context(system, max_bands=nb, device=dev)
+    if args.precision == "mixed":
+        psi_host = psi_host.astype(np.complex64 if cplx else np.float32)
+    ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
     psi = [torch.from_numpy(psi_host).to(dev), torch.empty_like(torch.from_numpy(psi_host), device=dev)]
     work = {"Hpsi": ctx.empty_bands(nb), "Spsi": ctx.empty_bands(nb),
-            "Hnm": torch.empty((nb, nb), dtype=ctx.dtype, device=dev),
-            "Snm": torch.empty((nb, nb), dtype=ctx.dtype, device=dev),
+            "Hnm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
+            "Snm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
             "eps": torch.empty(nb, dtype=torch.float64, device=dev),
-            "C": torch.empty((nb, nb), dtype=ctx.dtype, device=dev)}
+            "C": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev)}
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -152,10 +156,10 @@ def run_gpu(args):
         ctx.apply_S(cur, out=work["Spsi"])
         if marks is not None:
             marks[2].record(stream)
-        ctx.gram(cur, work["Hpsi"], M=work["Hnm"])
+        ctx.gram(cur, work["Hpsi"], M=work["Hnm"], hermitian=True)
         if marks is not None:
             marks[3].record(stream)
-        ctx.gram(cur, work["Spsi"], M=work["Snm"])
+        ctx.gram(cur, work["Spsi"], M=work["Snm"], hermitian=True)
         ctx.subspace_diag(work["Hnm"], work["Snm"], eps=work["eps"], C=work["C"], overwrite=True, check=False)
         ctx.rotate(cur, work["C"], out=nxt)
         if marks is not None:
@@ -197,10 +201,13 @@ def run_gpu(args):
     units = float(nb) * K * args.steps * world
     value = units / elapsed / 1e9
     flop_scale = 8.0 if cplx else 2.0
-    gram_flops = flop_scale * nb * nb * K
+    gram_flops = flop_scale * nb * (nb + 1) / 2 * K     # unique entries of the Hermitian H_nm
     gram_s = statistics.mean(gram_ms) * 1e-3
     gram_tflops = gram_flops / gram_s / 1e12
-    bytes_ptband = 32 if cplx else 16
+    esize = psi_host.itemsize
+    bytes_ptband = 2 * esize
+    mixed = args.precision == "mixed"
+    alu_peak = FP32_PROBE_TFLOPS if mixed else FP64_NOMINAL_TFLOPS
     applyH_s = statistics.mean(applyH_ms) * 1e-3
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -209,20 +216,24 @@ def run_gpu(args):
         "metric": "H|psi> Gpt.band/s over whole Rayleigh-Ritz steps (apply_H + apply_S + Gram + subspace diag + rotate)",
         "value": value, "unit": "Gpt.band/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c128" if cplx else "f64", "data": "synthetic (seeded)",
+        "vs_baseline": None, "dtype": {8: "f64", 16: "c128", 4: "f32"}[esize] if not (mixed and cplx) else "c64",
+        "data": "synthetic (seeded)",
         "config": {"workload": w.name, "grid": list(system.n), "bands": nb, "atoms": system.natoms,
                    "projectors_per_atom": int(system.nproj[0]) if system.natoms else 0,
-                   "precision": "fp64", "parallelism": "replicas" if world > 1 else "single-gpu",
-                   "l2": "inputs larger than L2 (%.2f GB of bands per step)" % (2 * nb * K * 8 * (2 if cplx else 1) / 1e9)},
+                   "precision": args.precision, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (%.2f GB of bands per step)" % (2 * nb * K * esize / 1e9)},
         "rr_steps_per_s": args.steps * world / elapsed,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "apply_H_gptband_s": nb * K / applyH_s / 1e9,
         "eig_drift_ha": drift,
-        "roofline": {"kernel": "gram_partial_kernel (FP64 DFMA GEMM, H_nm)", "bound": "alu",
-                     "achieved": gram_tflops, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": gram_tflops / FP64_NOMINAL_TFLOPS, "traffic": None,
-                     "peak_source": "nominal GB300 FP64 rate (not in MEASURED_PEAKS.json; probe measured 1.198)"},
-        "stencil_roofline": {"kernel": "apply_H (stencil + projections + back-add)", "bound": "alu",
+        "roofline": {"kernel": ("gram_partial_mixed_kernel (FP32 FMA, FP64 fold)" if mixed else
+                                "gram_partial_kernel (FP64 DFMA GEMM)") + ", Hermitian H_nm: upper tiles only",
+                     "bound": "alu", "achieved": gram_tflops, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": gram_tflops / alu_peak, "traffic": None,
+                     "peak_source": ("FP32 FMA rate measured by a probe kernel (not in MEASURED_PEAKS.json)" if mixed
+                                     else "nominal GB300 FP64 rate (not in MEASURED_PEAKS.json; probe measured 1.198)")},
+        "stencil_roofline": {"kernel": "apply_H (stencil + projections + back-add)",
+                             "bound": "hbm" if mixed else "alu",
                              "achieved_gptband_s": nb * K / applyH_s / 1e9,
                              "hbm_achieved_gbs": bytes_ptband * nb * K / applyH_s / 1e9, "hbm_peak_gbs": hbm,
                              "hbm_frac": bytes_ptband * nb * K / applyH_s / 1e9 / hbm},
@@ -258,8 +269,8 @@ def e2e_gpu(ctx, psi_host, work, args, dev):
         d_in.copy_(h_in, non_blocking=True)
         ctx.apply_H(d_in, out=work["Hpsi"])
         ctx.apply_S(d_in, out=work["Spsi"])
-        ctx.gram(d_in, work["Hpsi"], M=work["Hnm"])
-        ctx.gram(d_in, work["Spsi"], M=work["Snm"])
+        ctx.gram(d_in, work["Hpsi"], M=work["Hnm"], hermitian=True)
+        ctx.gram(d_in, work["Spsi"], M=work["Snm"], hermitian=True)
         ctx.subspace_diag(work["Hnm"], work["Snm"], eps=work["eps"], C=work["C"], overwrite=True, check=False)
         ctx.rotate(d_in, work["C"], out=d_out)
         h_eps.copy_(work["eps"], non_blocking=True)

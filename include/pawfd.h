@@ -36,10 +36,16 @@ extern "C" {
 
 typedef struct pawfd_ctx pawfd_ctx;
 
-/* wave-function storage / arithmetic type */
+/* wave-function storage / arithmetic type of the band arrays and projections.
+ * Gram matrices, eigenvalues and eigenvectors (C) are always FP64: double for the real
+ * types, interleaved complex double for the complex types.  The FP32 types are the mixed
+ * form: stencil, projections and back-add in FP32 arithmetic, Gram sums in FP32 within
+ * chunks of at most 4096 grid points and FP64 across chunks, subspace solve in FP64. */
 enum {
   PAWFD_R64 = 0,  /* real double, Gamma point (k must be 0)         */
-  PAWFD_C128 = 1  /* complex double, Bloch vector k                  */
+  PAWFD_C128 = 1, /* complex double, Bloch vector k                  */
+  PAWFD_R32 = 2,  /* real float, Gamma point (k must be 0)          */
+  PAWFD_C64 = 3   /* complex float, Bloch vector k                   */
 };
 
 /* error codes */
@@ -115,22 +121,31 @@ int pawfd_apply_S(pawfd_ctx* ctx, const void* psi, int nb, void* spsi, void* P_o
  * stencil hot spot of the development section, fused with the local potential). */
 int pawfd_apply_kinetic_local(pawfd_ctx* ctx, const void* psi, int nb, void* out);
 
-/* Gram matrix M[n][m] = dV sum_r conj(A_n(r)) B_m(r), n, m < nb; M is [nb][nb] of the
- * context's dtype (double or interleaved complex double).  With B = H psi this is the
+/* Gram matrix M[n][m] = dV sum_r conj(A_n(r)) B_m(r), n, m < nb; A, B band arrays of the
+ * context's dtype; M is [nb][nb] FP64 (double, or interleaved complex double for the complex
+ * dtypes).  With B = H psi this is the
  * subspace Hamiltonian H_nm, with B = S psi the subspace overlap S_nm. */
 int pawfd_gram(pawfd_ctx* ctx, const void* A, const void* B, int nb, void* M);
 
+/* Hermitian Gram matrix for B = X A with X Hermitian (X = H or S, so that A^H X A is
+ * Hermitian): computes M[n][m] = dV sum_r conj(A_n(r)) B_m(r) for n <= m only (tiles on or
+ * above the diagonal, about half the work of pawfd_gram), sets M[m][n] = conj(M[n][m]) and
+ * makes the diagonal exactly real.  Arguments and layout as pawfd_gram. */
+int pawfd_gram_hermitian(pawfd_ctx* ctx, const void* A, const void* B, int nb, void* M);
+
 /* Subspace diagonalization: given Hermitian H_nm and positive definite S_nm ([nb][nb],
- * context dtype), solve H C = S C diag(eps): symmetrize, S = L L^H, A = L^-1 H L^-H,
+ * FP64 of the context's kind: double or interleaved complex double), solve H C = S C diag(eps): symmetrize, S = L L^H, A = L^-1 H L^-H,
  * Jacobi A = U diag(eps) U^H, C = L^-H U.  eps (double [nb]) ascending with stable ties;
- * each column of C (context dtype, [nb][nb], column m = eigenvector m) is S-normalized and
+ * each column of C (FP64 of the same kind, [nb][nb], column m = eigenvector m) is S-normalized and
  * multiplied by a unit phase that makes its largest-magnitude entry (first on ties) real
  * and positive.  Hnm and Snm are overwritten (workspace).  Failures (PAWFD_ENOTPD with the
  * failing column, PAWFD_ENOCONV) are reported by pawfd_sync. */
 int pawfd_subspace_diag(pawfd_ctx* ctx, int nb, void* Hnm, void* Snm, double* eps, void* C);
 
 /* Band rotation psi_out_m = sum_n psi_n C[n][m] (the rotation that completes the subspace
- * diagonalization).  psi, psi_out: [nb][K]; C: [nb][nb]; psi_out must not alias psi. */
+ * diagonalization).  psi, psi_out: [nb][K] of the context's dtype; C: [nb][nb] FP64 (as
+ * returned by pawfd_subspace_diag; the FP32 dtypes round it to FP32 and accumulate in FP32);
+ * psi_out must not alias psi. */
 int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* psi_out);
 
 /* Gram matrix for callers that cannot allocate device memory.

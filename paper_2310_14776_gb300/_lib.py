@@ -10,6 +10,8 @@ LIB_PATH = os.path.join(HERE, "libpawfd.so")
 
 PAWFD_R64 = 0
 PAWFD_C128 = 1
+PAWFD_R32 = 2
+PAWFD_C64 = 3
 ERRORS = {0: "PAWFD_OK", -1: "PAWFD_EINVAL", -2: "PAWFD_ENOMEM", -3: "PAWFD_ENOTPD", -4: "PAWFD_ENOCONV",
           -5: "PAWFD_ETIMEDOUT", -6: "PAWFD_EDEVICE"}
 
@@ -37,6 +39,7 @@ SIGNATURES = {
     "pawfd_apply_S": ([VP, VP, I, VP, VP], I),
     "pawfd_apply_kinetic_local": ([VP, VP, I, VP], I),
     "pawfd_gram": ([VP, VP, VP, I, VP], I),
+    "pawfd_gram_hermitian": ([VP, VP, VP, I, VP], I),
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
     "pawfd_gram_noalloc": ([VP, VP, ctypes.c_longlong, I, I, D, VP, VP], I),

@@ -24,11 +24,12 @@ class Context:
     """One system (cell, grid, local potential, projector boxes, dH/dS) resident on the GPU.
 
     ``system`` is a ``synth.System`` or any object with the same fields.  All band arrays are
-    torch tensors on the context's device, shaped [nb, N3, N2, N1] (float64 at the Gamma
-    point, complex128 with a Bloch vector), contiguous.
+    torch tensors on the context's device, shaped [nb, N3, N2, N1], contiguous: float64 /
+    complex128 (Gamma point / Bloch vector) for ``precision="fp64"``, float32 / complex64
+    for ``precision="mixed"``.  Gram matrices, eigenvalues and C are always FP64.
     """
 
-    def __init__(self, system, max_bands: int, device: Optional[torch.device] = None):
+    def __init__(self, system, max_bands: int, device: Optional[torch.device] = None, precision: str = "fp64"):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if self.device.type != "cuda":
@@ -36,7 +37,14 @@ class Context:
         self.n = tuple(int(v) for v in system.n)
         self.K = self.n[0] * self.n[1] * self.n[2]
         self.complex = bool(system.complex_wf)
-        self.dtype = torch.complex128 if self.complex else torch.float64
+        if precision not in ("fp64", "mixed"):
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        self.precision = precision
+        self.mat_dtype = torch.complex128 if self.complex else torch.float64
+        if precision == "fp64":
+            self.dtype = self.mat_dtype
+        else:
+            self.dtype = torch.complex64 if self.complex else torch.float32
         self.max_bands = int(max_bands)
         h = [system.cell[c] / self.n[c] for c in range(3)]
         self.dV = h[0] * h[1] * h[2]
@@ -50,7 +58,8 @@ class Context:
         d.n[:] = list(self.n)
         d.cell[:] = [float(v) for v in system.cell]
         d.k[:] = [float(v) for v in system.k]
-        d.dtype = _lib.PAWFD_C128 if self.complex else _lib.PAWFD_R64
+        d.dtype = {("fp64", False): _lib.PAWFD_R64, ("fp64", True): _lib.PAWFD_C128,
+                   ("mixed", False): _lib.PAWFD_R32, ("mixed", True): _lib.PAWFD_C64}[(precision, self.complex)]
         d.max_bands = self.max_bands
         d.natoms = int(len(keep["nproj"]))
         for name in ("nproj", "box_lo", "box_n", "proj", "proj_off", "dH", "dS", "dmat_off", "vloc"):
@@ -80,8 +89,9 @@ class Context:
         return t.numel() // self.K
 
     def _mat(self, t: torch.Tensor, nb: int, name: str):
-        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous() or t.numel() != nb * nb:
-            raise ValueError("%s must be a contiguous [%d, %d] %s tensor on %s" % (name, nb, nb, self.dtype, self.device))
+        if t.device != self.device or t.dtype != self.mat_dtype or not t.is_contiguous() or t.numel() != nb * nb:
+            raise ValueError("%s must be a contiguous [%d, %d] %s tensor on %s" % (name, nb, nb, self.mat_dtype,
+                                                                                   self.device))
 
     def empty_bands(self, nb: int) -> torch.Tensor:
         return torch.empty((nb,) + self.n[::-1], dtype=self.dtype, device=self.device)
@@ -127,14 +137,16 @@ class Context:
     def apply_S(self, psi, out=None, P=None):
         return self._apply(self.lib.pawfd_apply_S, psi, out, P)
 
-    def gram(self, A, B, M=None):
+    def gram(self, A, B, M=None, hermitian: bool = False):
+        """M = dV A^H B.  ``hermitian``: B = X A for a Hermitian X; only the upper half is
+        computed and mirrored (pawfd_gram_hermitian)."""
         nb = self._bands(A, "A")
         if self._bands(B, "B") != nb:
             raise ValueError("A and B must hold the same number of bands")
-        M = torch.empty((nb, nb), dtype=self.dtype, device=self.device) if M is None else M
+        M = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if M is None else M
         self._mat(M, nb, "M")
-        self._call(self.lib.pawfd_gram, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), nb,
-                   ctypes.c_void_p(M.data_ptr()))
+        fn = self.lib.pawfd_gram_hermitian if hermitian else self.lib.pawfd_gram
+        self._call(fn, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()), nb, ctypes.c_void_p(M.data_ptr()))
         return M
 
     def subspace_diag(self, Hnm, Snm, eps=None, C=None, overwrite: bool = False, check: bool = True):
@@ -145,7 +157,7 @@ class Context:
         if not overwrite:
             Hnm, Snm = Hnm.clone(), Snm.clone()
         eps = torch.empty(nb, dtype=torch.float64, device=self.device) if eps is None else eps
-        C = torch.empty((nb, nb), dtype=self.dtype, device=self.device) if C is None else C
+        C = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if C is None else C
         self._mat(C, nb, "C")
         self._call(self.lib.pawfd_subspace_diag, nb, ctypes.c_void_p(Hnm.data_ptr()), ctypes.c_void_p(Snm.data_ptr()),
                    ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(C.data_ptr()))
@@ -171,8 +183,8 @@ class Context:
         w = work if work is not None else {}
         Hpsi = self.apply_H(psi, out=w.get("Hpsi"))
         Spsi = self.apply_S(psi, out=w.get("Spsi"))
-        Hnm = self.gram(psi, Hpsi, M=w.get("Hnm"))
-        Snm = self.gram(psi, Spsi, M=w.get("Snm"))
+        Hnm = self.gram(psi, Hpsi, M=w.get("Hnm"), hermitian=True)
+        Snm = self.gram(psi, Spsi, M=w.get("Snm"), hermitian=True)
         eps, C = self.subspace_diag(Hnm, Snm, eps=w.get("eps"), C=w.get("C"), overwrite=not keep_matrices, check=check)
         psi_rot = self.rotate(psi, C, out=w.get("psi_rot"))
         return {"Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}

@@ -20,7 +20,7 @@ int apply_X(pawfd_ctx* c, int which, const void* psi, int nb, void* out, void* P
   if (which == 0) {
     rc = launch_kinetic_local(c, psi, nb, out);
   } else {
-    rc = check_cuda(c, cudaMemcpyAsync(out, psi, scalar_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
+    rc = check_cuda(c, cudaMemcpyAsync(out, psi, band_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
                                        c->stream), "copy psi");
   }
   if (rc != PAWFD_OK) return rc;
@@ -57,7 +57,14 @@ extern "C" int pawfd_gram(pawfd_ctx* c, const void* A, const void* B, int nb, vo
   int rc = check_bands(c, nb);
   if (rc != PAWFD_OK) return rc;
   if (!A || !B || !M) return fail(c, PAWFD_EINVAL, "null array");
-  return launch_gram(c, A, B, nb, M);
+  return launch_gram(c, A, B, nb, M, false);
+}
+
+extern "C" int pawfd_gram_hermitian(pawfd_ctx* c, const void* A, const void* B, int nb, void* M) {
+  int rc = check_bands(c, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (!A || !B || !M) return fail(c, PAWFD_EINVAL, "null array");
+  return launch_gram(c, A, B, nb, M, true);
 }
 
 extern "C" int pawfd_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C) {

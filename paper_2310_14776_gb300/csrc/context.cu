@@ -103,8 +103,8 @@ int validate(const pawfd_system_desc* d, std::string& why) {
     if (!(d->cell[c] > 0.0)) return why = "cell lengths must be > 0", PAWFD_EINVAL;
   }
   if ((long long)d->n[0] * d->n[1] * d->n[2] > (1ll << 31) - 1) return why = "grid too large", PAWFD_EINVAL;
-  if (d->dtype != PAWFD_R64 && d->dtype != PAWFD_C128) return why = "unsupported dtype", PAWFD_EINVAL;
-  if (d->dtype == PAWFD_R64 && (d->k[0] != 0.0 || d->k[1] != 0.0 || d->k[2] != 0.0))
+  if (d->dtype < PAWFD_R64 || d->dtype > PAWFD_C64) return why = "unsupported dtype", PAWFD_EINVAL;
+  if ((d->dtype == PAWFD_R64 || d->dtype == PAWFD_R32) && (d->k[0] != 0.0 || d->k[1] != 0.0 || d->k[2] != 0.0))
     return why = "real wave functions need k = 0", PAWFD_EINVAL;
   if (d->max_bands < 1) return why = "max_bands must be >= 1", PAWFD_EINVAL;
   if (!d->vloc) return why = "vloc is NULL", PAWFD_EINVAL;
@@ -132,7 +132,8 @@ int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
   int rc = PAWFD_OK;
   AtomTables& at = c->at;
   at.natoms = d->natoms;
-  const bool cplx = c->dtype == PAWFD_C128;
+  const bool cplx = is_complex(c);
+  const bool fp32 = is_fp32(c);
   std::vector<int> all_pts;
   std::vector<double> all_re, all_im;
   at.pt_off.assign(1, 0);
@@ -190,8 +191,6 @@ int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
   at.d_g_off = dev_alloc<long long>(c, A + 1, &rc);
   at.d_dmat_off = dev_alloc<long long>(c, A + 1, &rc);
   const long long ndm = A ? d->dmat_off[A] : 0;
-  at.d_dH = dev_alloc<double>(c, ndm, &rc);
-  at.d_dS = dev_alloc<double>(c, ndm, &rc);
   at.d_color_atoms = dev_alloc<int>(c, color_atoms.size(), &rc);
   upload(c, at.d_nproj, at.nproj.data(), A, &rc);
   upload(c, at.d_row_off, at.row_off.data(), A + 1, &rc);
@@ -200,13 +199,38 @@ int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
   upload(c, at.d_pts, all_pts.data(), all_pts.size(), &rc);
   upload(c, at.d_g_off, at.g_off.data(), A + 1, &rc);
   upload(c, at.d_dmat_off, at.dmat_off.data(), A + 1, &rc);
-  upload(c, at.d_dH, d->dH, ndm, &rc);
-  upload(c, at.d_dS, d->dS, ndm, &rc);
+  if (fp32) {
+    std::vector<float> h(d->dH, d->dH + ndm), s(d->dS, d->dS + ndm);
+    float* dh = dev_alloc<float>(c, ndm, &rc);
+    float* ds = dev_alloc<float>(c, ndm, &rc);
+    upload(c, dh, h.data(), ndm, &rc);
+    upload(c, ds, s.data(), ndm, &rc);
+    at.d_dH = dh;
+    at.d_dS = ds;
+  } else {
+    double* dh = dev_alloc<double>(c, ndm, &rc);
+    double* ds = dev_alloc<double>(c, ndm, &rc);
+    upload(c, dh, d->dH, ndm, &rc);
+    upload(c, ds, d->dS, ndm, &rc);
+    at.d_dH = dh;
+    at.d_dS = ds;
+  }
   upload(c, at.d_color_atoms, color_atoms.data(), color_atoms.size(), &rc);
-  if (cplx) {
+  if (cplx && !fp32) {
     std::vector<zd> g(all_re.size());
     for (size_t q = 0; q < g.size(); ++q) g[q] = zd{all_re[q], all_im[q]};
     zd* dg = dev_alloc<zd>(c, g.size(), &rc);
+    upload(c, dg, g.data(), g.size(), &rc);
+    at.d_g = dg;
+  } else if (cplx) {
+    std::vector<zf> g(all_re.size());
+    for (size_t q = 0; q < g.size(); ++q) g[q] = zf{(float)all_re[q], (float)all_im[q]};
+    zf* dg = dev_alloc<zf>(c, g.size(), &rc);
+    upload(c, dg, g.data(), g.size(), &rc);
+    at.d_g = dg;
+  } else if (fp32) {
+    std::vector<float> g(all_re.begin(), all_re.end());
+    float* dg = dev_alloc<float>(c, g.size(), &rc);
     upload(c, dg, g.data(), g.size(), &rc);
     at.d_g = dg;
   } else {
@@ -264,17 +288,26 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     const double centre = -0.5 * FD6_W0 * (1.0 / (c->h[0] * c->h[0]) + 1.0 / (c->h[1] * c->h[1]) +
                                            1.0 / (c->h[2] * c->h[2]));
     for (size_t r = 0; r < c->K; ++r) vs[r] = d->vloc[r] + centre;
-    c->d_vshift = dev_alloc<double>(c, c->K, &rc);
-    upload(c, c->d_vshift, vs.data(), c->K, &rc);
+    if (is_fp32(c)) {
+      std::vector<float> vf(vs.begin(), vs.end());
+      float* p = dev_alloc<float>(c, c->K, &rc);
+      upload(c, p, vf.data(), c->K, &rc);
+      c->d_vshift = p;
+    } else {
+      double* p = dev_alloc<double>(c, c->K, &rc);
+      upload(c, p, vs.data(), c->K, &rc);
+      c->d_vshift = p;
+    }
   }
   if (rc == PAWFD_OK) rc = build_tables(c, d);
-  const size_t ss = scalar_size(c);
+  const size_t ss = mat_size(c);
   const size_t nb = (size_t)c->max_bands;
   if (rc == PAWFD_OK) {
-    c->d_P = dev_alloc<char>(c, ss * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
-    // split-K partials: enough for ~2 waves of 64x64 tiles at max_bands, capped at 256 MB
-    const size_t tiles = ((nb + 63) / 64) * ((nb + 63) / 64);
-    size_t nsplit = std::max<size_t>(1, std::min<size_t>(64, (2 * (size_t)c->num_sms + tiles - 1) / tiles));
+    c->d_P = dev_alloc<char>(c, band_size(c) * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
+    // split-K partials: about eight 64 x 64 tiles per SM at max_bands (Hermitian tiling),
+    // capped at 256 MB
+    const size_t t1 = (nb + 63) / 64, tiles = t1 * (t1 + 1) / 2;
+    size_t nsplit = std::max<size_t>(1, std::min<size_t>(256, (8 * (size_t)c->num_sms + tiles - 1) / tiles));
     while (nsplit > 1 && nsplit * nb * nb * ss > (256ull << 20)) --nsplit;
     c->gram_part_bytes = nsplit * nb * nb * ss;
     c->d_gram_part = dev_alloc<char>(c, c->gram_part_bytes, &rc);

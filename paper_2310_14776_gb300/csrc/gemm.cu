@@ -19,12 +19,32 @@ namespace {
 
 constexpr int TM = 64, TK = 16, NT = 256;
 
-template <class T>
+// Output tile of this CTA.  HERM: only tiles on or above the diagonal are computed, listed
+// row by row in blockIdx.x; otherwise blockIdx.y / blockIdx.x give the tile row / column.
+template <bool HERM>
+__device__ __forceinline__ void gram_tile(int nb, int* n0, int* m0) {
+  if (!HERM) {
+    *n0 = blockIdx.y * TM;
+    *m0 = blockIdx.x * TM;
+    return;
+  }
+  const int T = (nb + TM - 1) / TM;
+  int t = blockIdx.x, row = 0;
+  while (t >= T - row) {
+    t -= T - row;
+    ++row;
+  }
+  *n0 = row * TM;
+  *m0 = (row + t) * TM;
+}
+
+template <class T, bool HERM = false>
 __global__ void __launch_bounds__(NT) gram_partial_kernel(const T* __restrict__ A, const T* __restrict__ B, int nb,
                                                           long long K, long long kchunk, T* __restrict__ part) {
   __shared__ T As[TK][TM];
   __shared__ T Bs[TK][TM];
-  const int n0 = blockIdx.y * TM, m0 = blockIdx.x * TM;
+  int n0, m0;
+  gram_tile<HERM>(nb, &n0, &m0);
   const long long k0 = (long long)blockIdx.z * kchunk;
   const long long k1 = min(K, k0 + kchunk);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -70,6 +90,103 @@ __global__ void __launch_bounds__(NT) gram_partial_kernel(const T* __restrict__ 
     }
 }
 
+// Mixed-precision Gram partial for FP32 band arrays: products and sums in FP32 over runs of
+// at most MIX_RUN grid points, then folded into FP64; partials written in FP64.
+constexpr long long MIX_RUN = 4096;
+
+template <class T, bool HERM>
+__global__ void __launch_bounds__(NT) gram_partial_mixed_kernel(const T* __restrict__ A, const T* __restrict__ B,
+                                                                int nb, long long K, long long kchunk,
+                                                                wide_t<T>* __restrict__ part) {
+  using W = wide_t<T>;
+  __shared__ T As[TK][TM];
+  __shared__ T Bs[TK][TM];
+  int n0, m0;
+  gram_tile<HERM>(nb, &n0, &m0);
+  const long long k0 = (long long)blockIdx.z * kchunk;
+  const long long k1 = min(K, k0 + kchunk);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int lrow = tid / 4, lk = (tid % 4) * 4;
+  T acc[4][4];
+  W wacc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = zero<T>();
+      wacc[i][j] = zero<W>();
+    }
+  const T* __restrict__ arow = A + (long long)(n0 + lrow) * K;
+  const T* __restrict__ brow = B + (long long)(m0 + lrow) * K;
+  const bool aok = n0 + lrow < nb, bok = m0 + lrow < nb;
+  long long run_end = k0 + MIX_RUN;
+  for (long long kk = k0; kk < k1; kk += TK) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const long long k = kk + lk + e;
+      As[lk + e][lrow] = (aok && k < k1) ? conjx(arow[k]) : zero<T>();
+      Bs[lk + e][lrow] = (bok && k < k1) ? brow[k] : zero<T>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < TK; ++j) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = As[j][ty + 16 * i];
+        b[i] = Bs[j][tx + 16 * i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) fma_plain(acc[i][l], a[i], b[l]);
+    }
+    __syncthreads();
+    if (kk + TK >= run_end || kk + TK >= k1) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          wacc[i][l] += widen(acc[i][l]);
+          acc[i][l] = zero<T>();
+        }
+      run_end += MIX_RUN;
+    }
+  }
+  W* __restrict__ out = part + (long long)blockIdx.z * nb * nb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int n = n0 + ty + 16 * i, m = m0 + tx + 16 * l;
+      if (n < nb && m < nb) out[(long long)n * nb + m] = wacc[i][l];
+    }
+}
+
+// Hermitian result from the upper-triangular partials: M[n][m] for n <= m, mirrored below,
+// diagonal made exactly real.
+__device__ __forceinline__ double herm_diag(double v) { return v; }
+__device__ __forceinline__ zd herm_diag(zd v) { return zd{v.re, 0.0}; }
+
+template <class T>
+__global__ void gram_reduce_herm_kernel(const T* __restrict__ part, int nsplit, int nb, double dV,
+                                        T* __restrict__ M) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nn = (long long)nb * nb;
+  if (e >= nn) return;
+  const int n = (int)(e / nb), m = (int)(e % nb);
+  if (m < n) return;
+  T s = zero<T>();
+  for (int p = 0; p < nsplit; ++p) s += part[p * nn + e];
+  s = dV * s;
+  if (m == n) {
+    M[e] = herm_diag(s);
+  } else {
+    M[e] = s;
+    M[(long long)m * nb + n] = conjx(s);
+  }
+}
+
 template <class T>
 __global__ void gram_reduce_kernel(const T* __restrict__ part, int nsplit, int nb, double dV, T* __restrict__ M) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,8 +198,8 @@ __global__ void gram_reduce_kernel(const T* __restrict__ part, int nsplit, int n
 }
 
 template <class T>
-__global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, const T* __restrict__ C, int nb,
-                                                    long long K, T* __restrict__ out) {
+__global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, const wide_t<T>* __restrict__ C,
+                                                    int nb, long long K, T* __restrict__ out) {
   __shared__ T Cs[TK][TM];
   __shared__ T Ps[TK][TM];
   const long long r0 = (long long)blockIdx.x * TM;
@@ -97,7 +214,7 @@ __global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, c
     for (int s = tid; s < TK * TM; s += NT) {
       const int j = s / TM, i = s - j * TM;
       const int n = n0 + j;
-      Cs[j][i] = (n < nb && m0 + i < nb) ? C[(long long)n * nb + m0 + i] : zero<T>();
+      Cs[j][i] = (n < nb && m0 + i < nb) ? narrow<T>(C[(long long)n * nb + m0 + i]) : zero<T>();
       Ps[j][i] = (n < nb && r0 + i < K) ? psi[(long long)n * K + r0 + i] : zero<T>();
     }
     __syncthreads();
@@ -127,27 +244,35 @@ __global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, c
 }
 
 template <class T>
-int gram_impl(pawfd_ctx* c, const T* A, const T* B, int nb, T* M) {
+int gram_impl(pawfd_ctx* c, const T* A, const T* B, int nb, T* M, bool herm) {
   const long long K = (long long)c->K;
-  const int tiles = ((nb + TM - 1) / TM) * ((nb + TM - 1) / TM);
+  const int T1 = (nb + TM - 1) / TM;
+  const int tiles = herm ? T1 * (T1 + 1) / 2 : T1 * T1;
   const size_t per = (size_t)nb * nb * sizeof(T);
-  long long nsplit = std::max<long long>(1, (2ll * c->num_sms + tiles - 1) / tiles);
+  // about eight CTAs per SM, so that the split work spreads evenly over the SMs
+  long long nsplit = std::max<long long>(1, (8ll * c->num_sms + tiles - 1) / tiles);
   nsplit = std::min<long long>(nsplit, std::max<long long>(1, (long long)(c->gram_part_bytes / per)));
   nsplit = std::min<long long>(nsplit, std::max<long long>(1, K / (4 * TK)));
   long long kchunk = (K + nsplit - 1) / nsplit;
   kchunk = (kchunk + TK - 1) / TK * TK;
   nsplit = (K + kchunk - 1) / kchunk;
-  dim3 grid((nb + TM - 1) / TM, (nb + TM - 1) / TM, (unsigned)nsplit);
   T* part = (T*)c->d_gram_part;
-  gram_partial_kernel<T><<<grid, NT, 0, c->stream>>>(A, B, nb, K, kchunk, part);
   const long long nn = (long long)nb * nb;
-  gram_reduce_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(part, (int)nsplit, nb, c->dV, M);
+  if (herm) {
+    gram_partial_kernel<T, true><<<dim3(tiles, 1, (unsigned)nsplit), NT, 0, c->stream>>>(A, B, nb, K, kchunk, part);
+    gram_reduce_herm_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(part, (int)nsplit, nb, c->dV,
+                                                                                     M);
+  } else {
+    dim3 grid(T1, T1, (unsigned)nsplit);
+    gram_partial_kernel<T><<<grid, NT, 0, c->stream>>>(A, B, nb, K, kchunk, part);
+    gram_reduce_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(part, (int)nsplit, nb, c->dV, M);
+  }
   c->launches += 2;
   return check_cuda(c, cudaGetLastError(), "gram launch");
 }
 
 template <class T>
-int rotate_impl(pawfd_ctx* c, const T* psi, int nb, const T* C, T* out) {
+int rotate_impl(pawfd_ctx* c, const T* psi, int nb, const wide_t<T>* C, T* out) {
   const long long K = (long long)c->K;
   dim3 grid((unsigned)((K + TM - 1) / TM), (nb + TM - 1) / TM);
   rotate_kernel<T><<<grid, NT, 0, c->stream>>>(psi, C, nb, K, out);
@@ -155,16 +280,53 @@ int rotate_impl(pawfd_ctx* c, const T* psi, int nb, const T* C, T* out) {
   return check_cuda(c, cudaGetLastError(), "rotate launch");
 }
 
+template <class T>
+int gram_mixed_impl(pawfd_ctx* c, const T* A, const T* B, int nb, wide_t<T>* M, bool herm) {
+  using W = wide_t<T>;
+  const long long K = (long long)c->K;
+  const int T1 = (nb + TM - 1) / TM;
+  const int tiles = herm ? T1 * (T1 + 1) / 2 : T1 * T1;
+  const size_t per = (size_t)nb * nb * sizeof(W);
+  // about eight CTAs per SM, so that the split work spreads evenly over the SMs
+  long long nsplit = std::max<long long>(1, (8ll * c->num_sms + tiles - 1) / tiles);
+  nsplit = std::min<long long>(nsplit, std::max<long long>(1, (long long)(c->gram_part_bytes / per)));
+  nsplit = std::min<long long>(nsplit, std::max<long long>(1, K / (4 * TK)));
+  long long kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + TK - 1) / TK * TK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  W* part = (W*)c->d_gram_part;
+  const long long nn = (long long)nb * nb;
+  if (herm) {
+    gram_partial_mixed_kernel<T, true><<<dim3(tiles, 1, (unsigned)nsplit), NT, 0, c->stream>>>(A, B, nb, K, kchunk,
+                                                                                               part);
+    gram_reduce_herm_kernel<W><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(part, (int)nsplit, nb, c->dV,
+                                                                                     M);
+  } else {
+    gram_partial_mixed_kernel<T, false><<<dim3(T1, T1, (unsigned)nsplit), NT, 0, c->stream>>>(A, B, nb, K, kchunk,
+                                                                                              part);
+    gram_reduce_kernel<W><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(part, (int)nsplit, nb, c->dV, M);
+  }
+  c->launches += 2;
+  return check_cuda(c, cudaGetLastError(), "gram launch");
+}
+
 }  // namespace
 
-int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M) {
-  if (c->dtype == PAWFD_C128) return gram_impl<zd>(c, (const zd*)A, (const zd*)B, nb, (zd*)M);
-  return gram_impl<double>(c, (const double*)A, (const double*)B, nb, (double*)M);
+int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
+  switch (c->dtype) {
+    case PAWFD_C128: return gram_impl<zd>(c, (const zd*)A, (const zd*)B, nb, (zd*)M, hermitian);
+    case PAWFD_R64: return gram_impl<double>(c, (const double*)A, (const double*)B, nb, (double*)M, hermitian);
+    case PAWFD_C64: return gram_mixed_impl<zf>(c, (const zf*)A, (const zf*)B, nb, (zd*)M, hermitian);
+    case PAWFD_R32: return gram_mixed_impl<float>(c, (const float*)A, (const float*)B, nb, (double*)M, hermitian);
+  }
+  return fail(c, PAWFD_EINVAL, "unsupported dtype");
 }
 
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
-  if (c->dtype == PAWFD_C128) return rotate_impl<zd>(c, (const zd*)psi, nb, (const zd*)C, (zd*)out);
-  return rotate_impl<double>(c, (const double*)psi, nb, (const double*)C, (double*)out);
+  return dispatch_band(c, [&](auto tag) {
+    using T = decltype(tag);
+    return rotate_impl<T>(c, (const T*)psi, nb, (const wide_t<T>*)C, (T*)out);
+  });
 }
 
 }  // namespace pawfd

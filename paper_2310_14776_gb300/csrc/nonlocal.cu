@@ -74,13 +74,13 @@ __global__ void __launch_bounds__(NT) project_kernel(const T* __restrict__ psi, 
   for (int e = 0; e < MAXPAIRS; ++e) {
     const int pair = tid + e * NT;
     const int i = pair / BT, bl = pair - i * BT;
-    if (i < I && b0 + bl < nb) P[(long long)(row + i) * nb + b0 + bl] = dV * acc[e];
+    if (i < I && b0 + bl < nb) P[(long long)(row + i) * nb + b0 + bl] = (real_t<T>)dV * acc[e];
   }
 }
 
 template <class T>
 __global__ void __launch_bounds__(NT) nonlocal_add_kernel(const T* __restrict__ P, int nb, long long K,
-                                                          const double* __restrict__ dmat, const T* __restrict__ g,
+                                                          const real_t<T>* __restrict__ dmat, const T* __restrict__ g,
                                                           AtomArgs at, const int* __restrict__ atoms,
                                                           T* __restrict__ out) {
   __shared__ T Qs[IMAX][BT];
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(NT) nonlocal_add_kernel(const T* __restrict__ 
   const int I = at.nproj[a], np = at.npts[a], row = at.row_off[a];
   const int* __restrict__ pts = at.pts + at.pt_off[a];
   const T* __restrict__ ga = g + at.g_off[a];
-  const double* __restrict__ dX = dmat + at.dmat_off[a];
+  const real_t<T>* __restrict__ dX = dmat + at.dmat_off[a];
   const int tid = threadIdx.x;
   // Q[i][bl] = sum_i' dX[i][i'] P[row + i'][b0 + bl]
   for (int s = tid; s < I * BT; s += NT) {
@@ -139,30 +139,30 @@ int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P) {
   if (c->at.natoms == 0) return PAWFD_OK;
   if (c->at.Imax > IMAX) return fail(c, PAWFD_EINVAL, "more than 32 projectors on one atom");
   dim3 grid(c->at.natoms, (nb + BT - 1) / BT);
-  if (c->dtype == PAWFD_C128)
-    project_kernel<zd><<<grid, NT, 0, c->stream>>>((const zd*)psi, (zd*)P, nb, (long long)c->K, c->dV,
-                                                    (const zd*)c->at.d_g, atom_args(c));
-  else
-    project_kernel<double><<<grid, NT, 0, c->stream>>>((const double*)psi, (double*)P, nb, (long long)c->K, c->dV,
-                                                        (const double*)c->at.d_g, atom_args(c));
+  dispatch_band(c, [&](auto tag) {
+    using T = decltype(tag);
+    project_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)psi, (T*)P, nb, (long long)c->K, c->dV,
+                                                   (const T*)c->at.d_g, atom_args(c));
+    return 0;
+  });
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "project launch");
 }
 
-int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const double* d_dmat, void* out) {
+int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out) {
   if (c->at.natoms == 0) return PAWFD_OK;
   if (c->at.Imax > IMAX) return fail(c, PAWFD_EINVAL, "more than 32 projectors on one atom");
   for (size_t col = 0; col + 1 < c->at.color_off.size(); ++col) {
     const int first = c->at.color_off[col], count = c->at.color_off[col + 1] - first;
     dim3 grid(count, (nb + BT - 1) / BT);
     const int* atoms = c->at.d_color_atoms + first;
-    if (c->dtype == PAWFD_C128)
-      nonlocal_add_kernel<zd><<<grid, NT, 0, c->stream>>>((const zd*)P, nb, (long long)c->K, d_dmat,
-                                                           (const zd*)c->at.d_g, atom_args(c), atoms, (zd*)out);
-    else
-      nonlocal_add_kernel<double><<<grid, NT, 0, c->stream>>>((const double*)P, nb, (long long)c->K, d_dmat,
-                                                               (const double*)c->at.d_g, atom_args(c), atoms,
-                                                               (double*)out);
+    dispatch_band(c, [&](auto tag) {
+      using T = decltype(tag);
+      nonlocal_add_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)P, nb, (long long)c->K,
+                                                          (const real_t<T>*)d_dmat, (const T*)c->at.d_g,
+                                                          atom_args(c), atoms, (T*)out);
+      return 0;
+    });
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "nonlocal_add launch");

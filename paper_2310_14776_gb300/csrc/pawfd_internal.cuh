@@ -12,53 +12,79 @@
 namespace pawfd {
 
 // ------------------------------------------------------------------------------------------
-// complex double with the few operations the kernels need
+// scalars: double / float (real, Gamma point) and zd / zf (complex, Bloch), with the few
+// operations the kernels need
 // ------------------------------------------------------------------------------------------
-struct alignas(16) zd {
-  double re, im;
+template <class R>
+struct alignas(2 * sizeof(R)) cplx {
+  R re, im;
 };
+using zd = cplx<double>;
+using zf = cplx<float>;
 
-__host__ __device__ inline zd make_zd(double r, double i) { return zd{r, i}; }
-__host__ __device__ inline zd operator+(zd a, zd b) { return zd{a.re + b.re, a.im + b.im}; }
-__host__ __device__ inline zd operator-(zd a, zd b) { return zd{a.re - b.re, a.im - b.im}; }
-__host__ __device__ inline zd operator*(zd a, zd b) { return zd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-__host__ __device__ inline zd operator*(double s, zd a) { return zd{s * a.re, s * a.im}; }
-__host__ __device__ inline zd operator*(zd a, double s) { return zd{s * a.re, s * a.im}; }
-__host__ __device__ inline zd& operator+=(zd& a, zd b) { a.re += b.re; a.im += b.im; return a; }
-__host__ __device__ inline zd& operator-=(zd& a, zd b) { a.re -= b.re; a.im -= b.im; return a; }
+template <class R> __host__ __device__ inline cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator*(cplx<R> a, cplx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> __host__ __device__ inline cplx<R> operator*(R s, cplx<R> a) { return {s * a.re, s * a.im}; }
+template <class R> __host__ __device__ inline cplx<R> operator*(cplx<R> a, R s) { return {s * a.re, s * a.im}; }
+template <class R> __host__ __device__ inline cplx<R>& operator+=(cplx<R>& a, cplx<R> b) { a.re += b.re; a.im += b.im; return a; }
+template <class R> __host__ __device__ inline cplx<R>& operator-=(cplx<R>& a, cplx<R> b) { a.re -= b.re; a.im -= b.im; return a; }
 
-// scalar traits: T is double (real, Gamma point) or zd (complex, Bloch)
+template <class T> struct Traits;
+template <> struct Traits<double> { using R = double; using D = double; static constexpr bool complex = false; };
+template <> struct Traits<float> { using R = float; using D = double; static constexpr bool complex = false; };
+template <> struct Traits<zd> { using R = double; using D = zd; static constexpr bool complex = true; };
+template <> struct Traits<zf> { using R = float; using D = zd; static constexpr bool complex = true; };
+template <class T> using real_t = typename Traits<T>::R;
+template <class T> using wide_t = typename Traits<T>::D;   // the FP64 type of the same kind
+
 __host__ __device__ inline double conjx(double x) { return x; }
-__host__ __device__ inline zd conjx(zd x) { return zd{x.re, -x.im}; }
+__host__ __device__ inline float conjx(float x) { return x; }
+template <class R> __host__ __device__ inline cplx<R> conjx(cplx<R> x) { return {x.re, -x.im}; }
 __host__ __device__ inline double absx2(double x) { return x * x; }
-__host__ __device__ inline double absx2(zd x) { return x.re * x.re + x.im * x.im; }
+__host__ __device__ inline float absx2(float x) { return x * x; }
+template <class R> __host__ __device__ inline R absx2(cplx<R> x) { return x.re * x.re + x.im * x.im; }
 __host__ __device__ inline double realx(double x) { return x; }
-__host__ __device__ inline double realx(zd x) { return x.re; }
-template <class T> __host__ __device__ inline T zero();
-template <> __host__ __device__ inline double zero<double>() { return 0.0; }
-template <> __host__ __device__ inline zd zero<zd>() { return zd{0.0, 0.0}; }
-template <class T> __host__ __device__ inline T from_real(double x);
+__host__ __device__ inline float realx(float x) { return x; }
+template <class R> __host__ __device__ inline R realx(cplx<R> x) { return x.re; }
+template <class T> __host__ __device__ inline T zero() { return T{}; }
+template <class T> __host__ __device__ inline T from_real(real_t<T> x);
 template <> __host__ __device__ inline double from_real<double>(double x) { return x; }
+template <> __host__ __device__ inline float from_real<float>(float x) { return x; }
 template <> __host__ __device__ inline zd from_real<zd>(double x) { return zd{x, 0.0}; }
+template <> __host__ __device__ inline zf from_real<zf>(float x) { return zf{x, 0.0f}; }
+// widening / narrowing conversions between the FP32 and FP64 scalar of the same kind
+__host__ __device__ inline double widen(float x) { return (double)x; }
+__host__ __device__ inline double widen(double x) { return x; }
+__host__ __device__ inline zd widen(zf x) { return zd{(double)x.re, (double)x.im}; }
+__host__ __device__ inline zd widen(zd x) { return x; }
+template <class T> __host__ __device__ inline T narrow(wide_t<T> x);
+template <> __host__ __device__ inline double narrow<double>(double x) { return x; }
+template <> __host__ __device__ inline float narrow<float>(double x) { return (float)x; }
+template <> __host__ __device__ inline zd narrow<zd>(zd x) { return x; }
+template <> __host__ __device__ inline zf narrow<zf>(zd x) { return zf{(float)x.re, (float)x.im}; }
+
 // acc += conj(a) * b
-__host__ __device__ inline void fma_conj(double& acc, double a, double b) { acc = fma(a, b, acc); }
-__host__ __device__ inline void fma_conj(zd& acc, zd a, zd b) {
+template <class R> __host__ __device__ inline void fma_conj(R& acc, R a, R b) { acc = fma(a, b, acc); }
+template <class R> __host__ __device__ inline void fma_conj(cplx<R>& acc, cplx<R> a, cplx<R> b) {
   acc.re = fma(a.re, b.re, acc.re);
   acc.re = fma(a.im, b.im, acc.re);
   acc.im = fma(a.re, b.im, acc.im);
   acc.im = fma(-a.im, b.re, acc.im);
 }
 // acc += a * b
-__host__ __device__ inline void fma_plain(double& acc, double a, double b) { acc = fma(a, b, acc); }
-__host__ __device__ inline void fma_plain(zd& acc, zd a, zd b) {
+template <class R> __host__ __device__ inline void fma_plain(R& acc, R a, R b) { acc = fma(a, b, acc); }
+template <class R> __host__ __device__ inline void fma_plain(cplx<R>& acc, cplx<R> a, cplx<R> b) {
   acc.re = fma(a.re, b.re, acc.re);
   acc.re = fma(-a.im, b.im, acc.re);
   acc.im = fma(a.re, b.im, acc.im);
   acc.im = fma(a.im, b.re, acc.im);
 }
 // acc += s * a (s real)
-__host__ __device__ inline void fma_real(double& acc, double s, double a) { acc = fma(s, a, acc); }
-__host__ __device__ inline void fma_real(zd& acc, double s, zd a) {
+template <class R> __host__ __device__ inline void fma_real(R& acc, R s, R a) { acc = fma(s, a, acc); }
+template <class R> __host__ __device__ inline void fma_real(cplx<R>& acc, R s, cplx<R> a) {
   acc.re = fma(s, a.re, acc.re);
   acc.im = fma(s, a.im, acc.im);
 }
@@ -93,10 +119,10 @@ struct AtomTables {
   long long* d_pt_off = nullptr;
   int* d_pts = nullptr;              // wrapped grid index of every box point (unique per atom)
   long long* d_g_off = nullptr;
-  void* d_g = nullptr;               // folded projector values [I_a][npts_a], scalar type of the context
+  void* d_g = nullptr;               // folded projector values [I_a][npts_a], band scalar type
   long long* d_dmat_off = nullptr;
-  double* d_dH = nullptr;
-  double* d_dS = nullptr;
+  void* d_dH = nullptr;              // dH^a, real type of the band arithmetic (double or float)
+  void* d_dS = nullptr;
   int* d_color_atoms = nullptr;      // atoms listed color by color
   std::vector<int> color_off;        // [ncolors+1] into d_color_atoms
 };
@@ -110,7 +136,7 @@ struct pawfd_ctx {
   int max_bands;
   size_t K;
   cudaStream_t stream;
-  double* d_vshift = nullptr;                 // v(r) - 1/2 c0 sum_c 1/h_c^2
+  void* d_vshift = nullptr;                   // v(r) - 1/2 c0 sum_c 1/h_c^2 (double or float)
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_gram_part = nullptr;                // split-K partial Gram matrices
@@ -128,7 +154,25 @@ struct pawfd_ctx {
 
 namespace pawfd {
 
-inline size_t scalar_size(const pawfd_ctx* c) { return c->dtype == PAWFD_C128 ? 16 : 8; }
+inline bool is_complex(const pawfd_ctx* c) { return c->dtype == PAWFD_C128 || c->dtype == PAWFD_C64; }
+inline bool is_fp32(const pawfd_ctx* c) { return c->dtype == PAWFD_R32 || c->dtype == PAWFD_C64; }
+// bytes of one band-array element / of one subspace-matrix element (always FP64)
+inline size_t band_size(const pawfd_ctx* c) {
+  return c->dtype == PAWFD_C128 ? 16 : (c->dtype == PAWFD_R32 ? 4 : 8);
+}
+inline size_t mat_size(const pawfd_ctx* c) { return is_complex(c) ? 16 : 8; }
+
+// Call f(T{}) with T the band scalar type of the context (double, zd, float, zf).
+template <class F>
+int dispatch_band(const pawfd_ctx* c, F&& f) {
+  switch (c->dtype) {
+    case PAWFD_R64: return f(double{});
+    case PAWFD_C128: return f(zd{});
+    case PAWFD_R32: return f(float{});
+    case PAWFD_C64: return f(zf{});
+  }
+  return PAWFD_EINVAL;
+}
 
 int fail(pawfd_ctx* c, int code, const std::string& msg);
 int check_cuda(pawfd_ctx* c, cudaError_t e, const char* what);
@@ -136,8 +180,8 @@ int check_cuda(pawfd_ctx* c, cudaError_t e, const char* what);
 // kernels (launchers), each enqueued on c->stream; return PAWFD_OK or an error code
 int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out);
 int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P);
-int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const double* d_dmat, void* out);
-int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M);
+int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out);
+int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
 

@@ -16,25 +16,30 @@
 namespace pawfd {
 namespace {
 
+// R: real type of the arithmetic (double for the FP64 dtypes, float for the FP32 ones)
+template <class R>
 struct StencilArgs {
   int n1, n2, n3;
   long long K;
-  double wx[3], wy[3], wz[3];   // -1/2 w_m / h_c^2 for m = 1..3
-  zd ph[3];                     // exp(i k_c L_c)
-  const double* vshift;         // v(r) - 1/2 w_0 sum_c 1/h_c^2
+  R wx[3], wy[3], wz[3];        // -1/2 w_m / h_c^2 for m = 1..3
+  cplx<R> ph[3];                // exp(i k_c L_c)
+  const R* vshift;              // v(r) - 1/2 w_0 sum_c 1/h_c^2
   int zchunk, nzc;
 };
 
-__device__ __forceinline__ double phased(double v, int, int, int, const StencilArgs&) { return v; }
+template <class R>
+__device__ __forceinline__ R phased(R v, int, int, int, const StencilArgs<R>&) { return v; }
 
-__device__ __forceinline__ zd pow_phase(zd ph, int t) {
-  zd r = zd{1.0, 0.0};
-  const zd f = t > 0 ? ph : conjx(ph);
+template <class R>
+__device__ __forceinline__ cplx<R> pow_phase(cplx<R> ph, int t) {
+  cplx<R> r = {R(1), R(0)};
+  const cplx<R> f = t > 0 ? ph : conjx(ph);
   for (int i = 0; i < (t > 0 ? t : -t); ++i) r = r * f;
   return r;
 }
 
-__device__ __forceinline__ zd phased(zd v, int t1, int t2, int t3, const StencilArgs& a) {
+template <class R>
+__device__ __forceinline__ cplx<R> phased(cplx<R> v, int t1, int t2, int t3, const StencilArgs<R>& a) {
   if (t1) v = v * pow_phase(a.ph[0], t1);
   if (t2) v = v * pow_phase(a.ph[1], t2);
   if (t3) v = v * pow_phase(a.ph[2], t3);
@@ -43,7 +48,8 @@ __device__ __forceinline__ zd phased(zd v, int t1, int t2, int t3, const Stencil
 
 // psi at unwrapped grid index (u1, u2, u3) of one band, Bloch phase included
 template <class T>
-__device__ __forceinline__ T load_wrapped(const T* __restrict__ src, int u1, int u2, int u3, const StencilArgs& a) {
+__device__ __forceinline__ T load_wrapped(const T* __restrict__ src, int u1, int u2, int u3,
+                                          const StencilArgs<real_t<T>>& a) {
   int t1 = 0, t2 = 0, t3 = 0;
   while (u1 < 0) { u1 += a.n1; --t1; }
   while (u1 >= a.n1) { u1 -= a.n1; ++t1; }
@@ -60,7 +66,7 @@ constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
 
 template <class T>
 __global__ void __launch_bounds__(TX * TY) kinetic_local_kernel(const T* __restrict__ psi, T* __restrict__ out,
-                                                                StencilArgs a) {
+                                                                StencilArgs<real_t<T>> a) {
   __shared__ T tile[SY][SX];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
@@ -104,25 +110,25 @@ __global__ void __launch_bounds__(TX * TY) kinetic_local_kernel(const T* __restr
   }
 }
 
-}  // namespace
-
-int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
-  StencilArgs a;
+template <class T>
+int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
+  using R = real_t<T>;
+  StencilArgs<R> a;
   a.n1 = c->n[0];
   a.n2 = c->n[1];
   a.n3 = c->n[2];
   a.K = (long long)c->K;
   const double wm[3] = {FD6_W1, FD6_W2, FD6_W3};
   for (int m = 0; m < 3; ++m) {
-    a.wx[m] = -0.5 * wm[m] / (c->h[0] * c->h[0]);
-    a.wy[m] = -0.5 * wm[m] / (c->h[1] * c->h[1]);
-    a.wz[m] = -0.5 * wm[m] / (c->h[2] * c->h[2]);
+    a.wx[m] = (R)(-0.5 * wm[m] / (c->h[0] * c->h[0]));
+    a.wy[m] = (R)(-0.5 * wm[m] / (c->h[1] * c->h[1]));
+    a.wz[m] = (R)(-0.5 * wm[m] / (c->h[2] * c->h[2]));
   }
   for (int cc = 0; cc < 3; ++cc) {
     const double kl = c->k[cc] * c->cell[cc];
-    a.ph[cc] = zd{cos(kl), sin(kl)};
+    a.ph[cc] = cplx<R>{(R)cos(kl), (R)sin(kl)};
   }
-  a.vshift = c->d_vshift;
+  a.vshift = (const R*)c->d_vshift;
   const int gx = (a.n1 + TX - 1) / TX, gy = (a.n2 + TY - 1) / TY;
   const long long tiles = (long long)gx * gy;
   // split z so that one launch has at least ~4 CTAs per SM
@@ -131,19 +137,22 @@ int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
   a.zchunk = (a.n3 + nzc - 1) / nzc;
   a.nzc = (a.n3 + a.zchunk - 1) / a.zchunk;
   const int bands_per_launch = std::max(1, 65535 / a.nzc);
-  const size_t ss = scalar_size(c);
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gx, gy, nbl * a.nzc), block(TX, TY);
-    const char* src = (const char*)psi + (size_t)b0 * c->K * ss;
-    char* dst = (char*)out + (size_t)b0 * c->K * ss;
-    if (c->dtype == PAWFD_C128)
-      kinetic_local_kernel<zd><<<grid, block, 0, c->stream>>>((const zd*)src, (zd*)dst, a);
-    else
-      kinetic_local_kernel<double><<<grid, block, 0, c->stream>>>((const double*)src, (double*)dst, a);
+    kinetic_local_kernel<T><<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K, out + (size_t)b0 * c->K, a);
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "kinetic_local launch");
+}
+
+}  // namespace
+
+int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
+  return dispatch_band(c, [&](auto tag) {
+    using T = decltype(tag);
+    return kinetic_local_impl<T>(c, (const T*)psi, nb, (T*)out);
+  });
 }
 
 }  // namespace pawfd

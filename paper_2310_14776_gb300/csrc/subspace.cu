@@ -479,7 +479,7 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
 
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C) {
   if (nb > 3072) return fail(c, PAWFD_EINVAL, "subspace_diag supports at most 3072 bands");
-  if (c->dtype == PAWFD_C128) return subspace_impl<zd>(c, nb, (zd*)Hnm, (zd*)Snm, eps, (zd*)C);
+  if (is_complex(c)) return subspace_impl<zd>(c, nb, (zd*)Hnm, (zd*)Snm, eps, (zd*)C);
   return subspace_impl<double>(c, nb, (double*)Hnm, (double*)Snm, eps, (double*)C);
 }
 

@@ -313,6 +313,9 @@ WORKLOADS = {
     # 96^3 grid at 0.2 Angstrom, 256 real bands, 32 atoms x 18 projectors, ten iterations
     "gamma-96c-256b": Workload("gamma-96c-256b", (96, 96, 96), (96 * H_02A,) * 3, 256, 32, PSET_SPD2, seed=1,
                                iterations=10),
+    # 64^3 grid at 0.2 Angstrom, 128 real bands, 8 atoms x 18 projectors: the small case for
+    # profiler captures (band arrays of 268 MB, larger than L2)
+    "gamma-64c-128b": Workload("gamma-64c-128b", (64, 64, 64), (64 * H_02A,) * 3, 128, 8, PSET_SPD2, seed=5),
     # 144^3 grid at 0.2 Angstrom, 1024 complex bands at one Bloch k-point, 128 atoms x 18 projectors
     "bloch-144c-1024b": Workload("bloch-144c-1024b", (144, 144, 144), (144 * H_02A,) * 3, 1024, 128, PSET_SPD2,
                                  seed=2, complex_wf=True, k=_bloch_k((144 * H_02A,) * 3)),

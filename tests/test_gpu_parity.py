@@ -119,6 +119,23 @@ def test_edge_cases(dev, case):
     full_step_parity(s, case["nb"], 301, dev)
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_hermitian_gram_equals_full_gram(dev, cplx):
+    k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=501, k=k, complex_wf=cplx)
+    nb = 150                                  # three 64-wide tiles, ragged last one
+    ctx = ctx_for(s, nb, dev)
+    psi = to_dev(synth.make_psi(s, nb, 502), dev)
+    hpsi = ctx.apply_H(psi)
+    full = ctx.gram(psi, hpsi).cpu().numpy()
+    herm = ctx.gram(psi, hpsi, hermitian=True).cpu().numpy()
+    assert np.array_equal(herm, herm.conj().T)
+    assert_close_matrix(herm, full)
+    ref = O.gram(synth.make_psi(s, nb, 502), O.apply_H(s, synth.make_psi(s, nb, 502))[0], s.dV, nb)
+    assert_close_matrix(herm, ref)
+    ctx.close()
+
+
 def test_repeatable_bitwise(dev):
     w = synth.WORKLOADS["gamma-24c-16b"]
     s = w.system()
