@@ -249,6 +249,7 @@ void free_ctx(pawfd_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
+  free_tc(c);
   delete c;
 }
 
@@ -318,6 +319,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     c->d_reduce = dev_alloc<double>(c, 4096, &rc);
   }
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMallocHost(&c->h_status, sizeof(DeviceStatus)), "cudaMallocHost");
+  if (rc == PAWFD_OK && c->use_tc) rc = setup_tc(c);
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_barrier, 0, 4 * sizeof(unsigned)), "memset");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_status, 0, sizeof(DeviceStatus)), "memset");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaDeviceSynchronize(), "create sync");

@@ -313,6 +313,7 @@ int gram_mixed_impl(pawfd_ctx* c, const T* A, const T* B, int nb, wide_t<T>* M, 
 }  // namespace
 
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
+  if (c->use_tc) return launch_gram_tc(c, A, B, nb, M, hermitian);
   switch (c->dtype) {
     case PAWFD_C128: return gram_impl<zd>(c, (const zd*)A, (const zd*)B, nb, (zd*)M, hermitian);
     case PAWFD_R64: return gram_impl<double>(c, (const double*)A, (const double*)B, nb, (double*)M, hermitian);

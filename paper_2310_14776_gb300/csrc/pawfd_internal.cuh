@@ -1,6 +1,7 @@
 // pawfd_internal.cuh -- shared definitions of the CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -127,6 +128,24 @@ struct AtomTables {
   std::vector<int> color_off;        // [ncolors+1] into d_color_atoms
 };
 
+// Scratch of the tensor-core Gram: digit slices of one K block of each operand, their scale
+// exponents, FP64 split-K partials, and the TMA descriptors of the slice buffers.
+struct TcScratch {
+  bool ready = false;
+  long long kblk = 0;          // real-view values per K block (multiple of the exactness chunk)
+  int rowsA_alloc = 0, rowsB_alloc = 0;
+  void* slicesA = nullptr;
+  void* slicesB = nullptr;
+  int* sigA = nullptr;
+  int* sigB = nullptr;
+  int* maxA = nullptr;         // per-row largest scale exponent of the current K block
+  int* maxB = nullptr;
+  void* part = nullptr;
+  size_t part_bytes = 0;
+  CUtensorMap mapA;
+  CUtensorMap mapB;
+};
+
 }  // namespace pawfd
 
 struct pawfd_ctx {
@@ -149,6 +168,8 @@ struct pawfd_ctx {
   double* d_reduce = nullptr;                 // [max grid] partial sums for in-kernel reductions
   int num_sms = 0;
   long long launches = 0;                     // kernels this context has launched
+  bool use_tc = true;                         // Gram matrices on the tensor cores (sliced digits)
+  pawfd::TcScratch tc;
   std::string err;
 };
 
@@ -182,6 +203,9 @@ int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out);
 int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P);
 int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out);
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
+int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
+int setup_tc(pawfd_ctx* c);
+void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
 

@@ -1,0 +1,375 @@
+// sliced_gram.cuh -- Gram matrices on the BF16 tensor cores with exact integer slices.
+//
+// Each real input value x (FP64 or FP32) of a row-chunk of KC grid values is written, relative
+// to the chunk's largest binary exponent, as S balanced base-128 digits d_i in [-64, 64]:
+//     x ~= 2^sigma * sum_i d_i 2^(-7 i),       sigma = E - bias - 5   (per row and chunk)
+// The scaled digits d_i 2^(-7i) are exact in BF16, every digit product is exact in FP32, and
+// the tcgen05 tensor core sums them in FP32.  Four TMEM accumulators per output element, one
+// per digit order o = i + j (scaled digit products of order o are multiples of 2^(-7o) and at
+// most 2^(12 - 7o) in magnitude, so a sum of n of them is exact while n 2^12 <= 2^24):
+//     D0 = order 0 (1 product per grid value)   exact while KC <= 4096
+//     D1 = order 1 (2 products)                 exact while KC <= 2048
+//     D2 = order 2 (3 products)                 exact while KC <= 1365
+//     D3 = orders 3 .. ORD, rounded in FP32 (each term is already 2^-21 below order 0)
+// Chunks are KC = 256 values long, which keeps the FP32 drift of D3 small.  After every chunk
+// the epilogue adds 2^(sigma_a + sigma_b) (D0 + D1 + D2 + D3) to a double-float (two FP32)
+// accumulator with error-free transformations (Knuth's TwoSum), so the FP64 pipe is not
+// needed per chunk; the scale is taken relative to the row's largest sigma of the K block.
+// S = 7 digits and orders up to ORD = 6 keep 48 bits of each FP64 value (products accurate to
+// ~2^-45 of the chunk maxima); S = 4 and ORD = 4 keep all 24 bits of an FP32 value.  Rounding
+// to the digit grid may lift the top digit to 65; the exactness bounds above have room for it.  Digits are extracted from the IEEE bit fields with
+// integer operations, so slicing needs no FP64 arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "pawfd_internal.cuh"
+#include "tc_common.cuh"
+
+namespace pawfd {
+namespace sg {
+
+constexpr int KC = 256;           // grid values per exactness chunk
+constexpr int BM = 128;           // output rows per CTA (TMEM lanes)
+constexpr int BN = 128;           // output columns per CTA
+constexpr int BK = 16;            // K per stage = one MMA (32-byte rows, 32B swizzle)
+constexpr int STAGES = 3;
+// Two epilogue warps per TMEM lane quarter (64 columns each) plus the TMA and MMA warps: ten
+// warps, three on some SM sub-partitions, which caps registers at 168 per thread.
+constexpr int EPI_WARPS = 8;
+constexpr int NTHREADS = (EPI_WARPS + 2) * 32;
+constexpr int TMEM_COLS = 512;    // D0, D1, D2, D3 at columns 0, 128, 256, 384
+
+template <int S>
+__host__ __device__ constexpr int stage_bytes() {
+  static_assert(S >= 4 && S <= 7, "four to seven digits");
+  return 2 * S * BM * BK * 2;
+}
+template <int S>
+__host__ __device__ constexpr int smem_bytes() { return STAGES * stage_bytes<S>() + 1024; }
+
+// ------------------------------------------------------------------------------------------
+// slicing
+// ------------------------------------------------------------------------------------------
+struct Fields {
+  int exp;                 // biased exponent (0 for zero / subnormal, treated as zero)
+  unsigned long long mant; // significand with the implicit bit
+  bool neg;
+};
+__device__ __forceinline__ Fields fields(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  Fields f;
+  f.exp = (int)((b >> 52) & 0x7FF);
+  f.mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  f.neg = (b >> 63) != 0;
+  return f;
+}
+__device__ __forceinline__ Fields fields(float x) {
+  const unsigned b = __float_as_uint(x);
+  Fields f;
+  f.exp = (int)((b >> 23) & 0xFF);
+  f.mant = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  f.neg = (b >> 31) != 0;
+  return f;
+}
+template <class R> struct FloatBits;
+template <> struct FloatBits<double> { static constexpr int bias = 1023, nb = 52; };
+template <> struct FloatBits<float> { static constexpr int bias = 127, nb = 23; };
+
+// x = src[r][k] of the real view, or for the "swapped" operand of a complex Gram the pair
+// (re, im) -> (im, -re), so that sum_k a_k b''_k = Im(conj(a) . b).
+template <class R>
+__device__ __forceinline__ R slice_input(const R* __restrict__ src, long long ld, long long len, int r, long long k,
+                                        bool swapped) {
+  if (k >= len) return R(0);
+  const R* row = src + (long long)r * ld;
+  if (!swapped) return row[k];
+  return (k & 1) ? -row[k - 1] : row[k + 1];
+}
+
+// One warp per (row, chunk) of a K block: src points at the block's first value of row 0, rows
+// are ld apart, len values per row are valid (the rest of the Lp-long block is zero).
+// out: [S][out_rows][Lp] bf16 scaled digits (rows placed at row_offset); sig: [nchunks][sig_ld];
+// sigmax[row] (reset by the caller for every block) receives the largest sigma of the row.
+template <class R, int S>
+__global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
+                                                    int nchunks, long long Lp, bool swapped, int row_offset,
+                                                    int out_rows, __nv_bfloat16* __restrict__ out,
+                                                    int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= rows * nchunks) return;
+  const int r = warp / nchunks;
+  const long long c = warp % nchunks;
+  const long long k0 = c * KC;
+  int emax = 0;
+  for (int t = lane; t < KC; t += 32) emax = max(emax, fields(slice_input(src, ld, len, r, k0 + t, swapped)).exp);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  constexpr int bias = FloatBits<R>::bias, nbits = FloatBits<R>::nb;
+  constexpr int g = 7 * S - 1 - nbits;   // shift that leaves 7S-1 bits (top digit below 64)
+  const int orow = row_offset + r;
+  if (lane == 0) {
+    sig[c * sig_ld + orow] = emax - bias - 5;
+    atomicMax(sigmax + orow, emax - bias - 5);
+  }
+  for (int t = lane; t < KC; t += 32) {
+    const Fields f = fields(slice_input(src, ld, len, r, k0 + t, swapped));
+    // G = mant * 2^(g - sh) rounded to nearest (ties up): the value on a grid of 7S-1 bits
+    // below the chunk maximum; FP32 inputs keep every mantissa bit (g - sh >= 0 for sh <= 4)
+    unsigned long long G = 0;
+    const int sh = emax - f.exp + 1;
+    const int rs = sh - g;
+    if (f.exp != 0 && rs < 64) G = rs > 0 ? (f.mant + (1ull << (rs - 1))) >> rs : f.mant << (-rs);
+    int d[S + 1];
+#pragma unroll
+    for (int i = 0; i < S; ++i) d[i] = (int)((G >> (7 * (S - 1 - i))) & 127ull);
+#pragma unroll
+    for (int i = S - 1; i >= 1; --i)
+      if (d[i] >= 64) {
+        d[i] -= 128;
+        d[i - 1] += 1;
+      }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      const float v = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
+      out[((long long)i * out_rows + orow) * Lp + k0 + t] = __float2bfloat16_rn(v);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Gram kernel
+// ------------------------------------------------------------------------------------------
+struct GramArgs {
+  const int* sigA;      // [nchunks][sig_ldA]  (chunks of this K block)
+  const int* sigB;      // [nchunks][sig_ldB]
+  const int* maxA;      // [rows] largest sigma of each row in this K block
+  const int* maxB;
+  int sig_ldA, sig_ldB;
+  int rowsA, rowsB;     // valid rows of the two operands
+  int tilesN;           // column tiles (ceil(rowsB / BN))
+  int herm;             // only tiles with tile row <= tile column (within each half of B if halves > 1)
+  int halves;           // 2 for complex (B = [B'; B'']): tiles are enumerated per half
+  int half_rows;        // rows per half of B (complex: nb)
+  int chunks_per_cta;
+  int nchunks;          // chunks in this K block
+  int accumulate;       // add to part instead of overwriting it (second and later K blocks)
+  double* part;         // [nsplit][rowsA][rowsB]
+  DeviceStatus* st;
+};
+
+// 2^e for the product scale; below the normal range the chunk contributes nothing (its
+// digits are all zero) and 0 is returned
+__device__ __forceinline__ double pow2(int e) {
+  return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// tile index -> (tile row, tile col) over the output [rowsA][rowsB]
+__device__ __forceinline__ void gram_tile(const GramArgs& a, int t, int* tr, int* tc_) {
+  if (!a.herm) {
+    *tr = t / a.tilesN;
+    *tc_ = t % a.tilesN;
+    return;
+  }
+  const int T = (a.half_rows + BN - 1) / BN;     // tiles per half side
+  const int per_half = T * (T + 1) / 2;
+  const int h = t / per_half;
+  int u = t % per_half, row = 0;
+  while (u >= T - row) {
+    u -= T - row;
+    ++row;
+  }
+  *tr = row;
+  *tc_ = h * T + row + u;
+}
+
+// float 2^e for e <= 0 (0 below the normal range)
+__device__ __forceinline__ float pow2f_nonpos(int e) { return e < -126 ? 0.0f : __int_as_float((e + 127) << 23); }
+
+// error-free a + b = s + e (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// (hi, lo) += (xh, xl), double-float accumulation
+__device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl) {
+  float s, e;
+  two_sum(hi, xh, s, e);
+  e += lo + xl;
+  two_sum(s, e, hi, lo);
+}
+
+template <int S, int ORD>
+__global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
+                                                                  const __grid_constant__ CUtensorMap tB, GramArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full[STAGES], empty[STAGES], dfull, dempty;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int tr, tcol;
+  gram_tile(a, blockIdx.x, &tr, &tcol);
+  const int row0 = tr * BM;
+  // column tiles of the complex second half start at half_rows, not at a multiple of BN
+  const int T = (a.half_rows + BN - 1) / BN;
+  const int col0 = (tcol / T) * a.half_rows + (tcol % T) * BN;
+  const int c_begin = blockIdx.y * a.chunks_per_cta;
+  const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
+  const int nch = max(0, c_end - c_begin);
+  const int steps_per_chunk = KC / BK;
+  const int total_steps = nch * steps_per_chunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&dfull, 1);
+    tc::mbar_init(&dempty, EPI_WARPS);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    tc::mbar_fence_init();
+  }
+  if (warp == EPI_WARPS) tc::tmem_alloc(&tmem_base, TMEM_COLS);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+
+  if (warp == EPI_WARPS) {
+    if (lane == 0) {   // TMA producer: S slices of A and S slices of B per stage
+      for (int g = 0; g < total_steps && !abort_flag; ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !tc::mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
+          abort_flag = 1;
+          set_status(a.st, PAWFD_ETIMEDOUT, 1001);
+          break;
+        }
+        const int kx = (c_begin + g / steps_per_chunk) * KC + (g % steps_per_chunk) * BK;
+        unsigned char* sa = smem + s * stage_bytes<S>();
+        unsigned char* sb = sa + S * BM * BK * 2;
+        tc::mbar_expect_tx(&full[s], stage_bytes<S>());
+        tc::tma_load_3d(sa, &tA, &full[s], kx, row0, 0);
+        tc::tma_load_3d(sb, &tB, &full[s], kx, col0, 0);
+        issued = g + 1;
+      }
+    }
+  } else if (warp == EPI_WARPS + 1) {
+    if (lane == 0) {   // MMA issuer
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      for (int c = 0; c < nch && !abort_flag; ++c) {
+        if (c > 0 && !tc::mbar_wait(&dempty, (c - 1) & 1)) {
+          abort_flag = 1;
+          set_status(a.st, PAWFD_ETIMEDOUT, 1002);
+          break;
+        }
+        tc::fence_after_sync();
+        for (int q = 0; q < steps_per_chunk && !abort_flag; ++q) {
+          const int g = c * steps_per_chunk + q;
+          const int s = g % STAGES;
+          if (!tc::mbar_wait(&full[s], (g / STAGES) & 1)) {
+            abort_flag = 1;
+            set_status(a.st, PAWFD_ETIMEDOUT, 1003);
+            break;
+          }
+          tc::fence_after_sync();
+          unsigned char* sa = smem + s * stage_bytes<S>();
+          unsigned char* sb = sa + S * BM * BK * 2;
+#pragma unroll
+          for (int i = 0; i < S; ++i)
+#pragma unroll
+            for (int j = 0; j < S && i + j <= ORD; ++j) {
+              const int o = i + j;
+              const uint32_t d = tmem + (uint32_t)((o < 3 ? o : 3) * BN);
+              // the first product written into an accumulator in this chunk overwrites it
+              // (loop order: (0,0) (0,1) (0,2) (0,3) ... so each order first appears with i = 0)
+              const bool first = (q == 0) && (i == 0) && (j <= 3);
+              tc::mma_bf16(d, tc::smem_desc(sa + i * BM * BK * 2, BK * 2), tc::smem_desc(sb + j * BM * BK * 2, BK * 2),
+                           idesc, first ? 0u : 1u);
+            }
+          tc::mma_commit(&empty[s]);
+          consumed = g + 1;
+        }
+        tc::mma_commit(&dfull);
+      }
+    }
+  } else {
+    // epilogue warps: lane quarter (warp % 4), column half (warp / 4)
+    const int quarter = warp & 3, chalf = warp >> 2;
+    const int row = row0 + quarter * 32 + lane;
+    const int cbase = chalf * 64;
+    float ahi[64], alo[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      ahi[j] = 0.0f;
+      alo[j] = 0.0f;
+    }
+    const int ra = (row < a.rowsA) ? __ldg(a.maxA + row) : 0;
+    for (int c = 0; c < nch; ++c) {
+      bool ok = tc::mbar_wait(&dfull, c & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_flag = 1;
+          set_status(a.st, PAWFD_ETIMEDOUT, 1004);
+        }
+        break;
+      }
+      tc::fence_after_sync();
+      const int chunk = c_begin + c;
+      const int sa = (row < a.rowsA) ? __ldg(a.sigA + (long long)chunk * a.sig_ldA + row) - ra : 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        uint32_t d0[8], d1[8], d2[8], d3[8];
+        const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + b * 8);
+        tc::tmem_ld8(base, d0);
+        tc::tmem_ld8(base + BN, d1);
+        tc::tmem_ld8(base + 2 * BN, d2);
+        tc::tmem_ld8(base + 3 * BN, d3);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int col = col0 + cbase + b * 8 + j;
+          const int sb = (col < a.rowsB) ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + col) - __ldg(a.maxB + col)
+                                         : 0;
+          const float scale = pow2f_nonpos(sa + sb);
+          // D0 + D1 + D2 exactly as a double-float, then D3
+          float s1, e1, s2, e2, vh, vl;
+          two_sum(__uint_as_float(d0[j]), __uint_as_float(d1[j]), s1, e1);
+          two_sum(s1, __uint_as_float(d2[j]), s2, e2);
+          two_sum(s2, (e1 + e2) + __uint_as_float(d3[j]), vh, vl);
+          df_add(ahi[b * 8 + j], alo[b * 8 + j], vh * scale, vl * scale);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&dempty);
+    }
+    // columns beyond this tile's half of B belong to the other half's tiles
+    const int col_lim = min(a.rowsB, (tcol / T + 1) * a.half_rows);
+    if (row < a.rowsA && !abort_flag) {
+      double* out = a.part + ((long long)blockIdx.y * a.rowsA + row) * a.rowsB;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int col = col0 + cbase + j;
+        if (col < col_lim) {
+          const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
+          out[col] = a.accumulate ? out[col] + v : v;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0)   // let issued copies land before the CTA exits (bounded)
+    for (int g = consumed; g < issued; ++g) tc::mbar_wait(&full[g % STAGES], (g / STAGES) & 1);
+  __syncthreads();
+  if (warp == EPI_WARPS) tc::tmem_free(tmem, TMEM_COLS);
+}
+
+}  // namespace sg
+}  // namespace pawfd

@@ -1,0 +1,216 @@
+// tc_gram.cu -- Gram matrices on the tensor cores (sliced_gram.cuh) for every band dtype.
+//
+// Real inputs: M = dV A^T B over K.  Complex inputs: the interleaved arrays are read as real
+// rows of length 2K; Re(conj(a).b) is the real dot product of the two rows and Im(conj(a).b) the
+// dot product of a with the "swapped" row (im, -re) of b, so the complex Gram is one real
+// Gram of A (nb rows) against B_ext = [B; B''] (2 nb rows).  K is processed in blocks whose
+// slices fit the context's scratch; every block adds into FP64 split-K partials, and one
+// reduce kernel sums the partials in a fixed order, applies dV and (for the Hermitian form)
+// mirrors the upper triangle.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "pawfd_internal.cuh"
+#include "sliced_gram.cuh"
+
+namespace pawfd {
+namespace {
+
+template <class W>
+__global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV, bool herm,
+                                 W* __restrict__ M);
+
+// real: part [nsplit][nb][nb]
+template <>
+__global__ void tc_reduce_kernel<double>(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV,
+                                         bool herm, double* __restrict__ M) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nb * nb) return;
+  const int n = (int)(e / nb), m = (int)(e % nb);
+  if (herm && m < n) return;
+  double s = 0.0;
+  for (int p = 0; p < nsplit; ++p) s += part[((long long)p * nb + n) * rowsB + m];
+  s *= dV;
+  M[e] = s;
+  if (herm && m != n) M[(long long)m * nb + n] = s;
+}
+
+// complex: part [nsplit][nb][2 nb], real part in columns [0, nb), imaginary in [nb, 2 nb)
+template <>
+__global__ void tc_reduce_kernel<zd>(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV,
+                                     bool herm, zd* __restrict__ M) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nb * nb) return;
+  const int n = (int)(e / nb), m = (int)(e % nb);
+  if (herm && m < n) return;
+  double re = 0.0, im = 0.0;
+  for (int p = 0; p < nsplit; ++p) {
+    const double* row = part + ((long long)p * nb + n) * rowsB;
+    re += row[m];
+    im += row[nb + m];
+  }
+  re *= dV;
+  im *= dV;
+  if (herm && m == n) im = 0.0;
+  M[e] = zd{re, im};
+  if (herm && m != n) M[(long long)m * nb + n] = zd{re, -im};
+}
+
+template <class R, int S, int ORD>
+int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool herm) {
+  TcScratch& t = c->tc;
+  const bool cplx = is_complex(c);
+  const long long L = (long long)c->K * (cplx ? 2 : 1);            // real-view row length
+  const int rowsB = cplx ? 2 * nb : nb;
+  const int T = (nb + sg::BN - 1) / sg::BN;
+  const int halves = cplx ? 2 : 1;
+  const int tiles = herm ? halves * T * (T + 1) / 2 : halves * T * T;
+  const long long Kblk = t.kblk;
+  const int max_chunks = (int)(Kblk / sg::KC);
+  // splits per K block: fill the SMs once (one CTA per SM), at least one chunk per CTA
+  int nsplit = std::max(1, std::min(max_chunks, (c->num_sms + tiles - 1) / tiles));
+  while (nsplit > 1 && (size_t)nsplit * nb * rowsB * sizeof(double) > t.part_bytes) --nsplit;
+  __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
+  __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
+  const int blocks_of_rows = 256 / 32;
+  int blk = 0;
+  for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
+    const long long len = std::min(Kblk, L - k0);
+    const int nch = (int)((len + sg::KC - 1) / sg::KC);
+    const int cpc = (nch + nsplit - 1) / nsplit;
+    const int ns = (nch + cpc - 1) / cpc;
+    const long long warpsA = (long long)nb * nch;
+    // per-row largest sigma of this block: start from a very negative value
+    cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+    cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
+    sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
+        A + k0, nb, L, len, nch, Kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
+    sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
+        B + k0, nb, L, len, nch, Kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+    c->launches += 2;
+    if (cplx) {
+      sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
+          B + k0, nb, L, len, nch, Kblk, true, nb, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+      c->launches += 1;
+    }
+    sg::GramArgs a;
+    a.sigA = t.sigA;
+    a.sigB = t.sigB;
+    a.sig_ldA = t.rowsA_alloc;
+    a.sig_ldB = t.rowsB_alloc;
+    a.maxA = t.maxA;
+    a.maxB = t.maxB;
+    a.rowsA = nb;
+    a.rowsB = rowsB;
+    a.tilesN = halves * T;
+    a.herm = herm;
+    a.halves = halves;
+    a.half_rows = nb;
+    a.chunks_per_cta = cpc;
+    a.nchunks = nch;
+    a.accumulate = blk > 0;
+    a.part = (double*)t.part;
+    a.st = c->d_status;
+    // slots written by the first block must cover every split later blocks add into
+    if (blk == 0 && ns < nsplit) nsplit = ns;
+    sg::sliced_gram_kernel<S, ORD><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.mapA, t.mapB, a);
+    c->launches += 1;
+  }
+  const long long nn = (long long)nb * nb;
+  if (cplx)
+    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB,
+                                                                              c->dV, herm, (zd*)M);
+  else
+    tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB,
+                                                                                  c->dV, herm, (double*)M);
+  c->launches += 1;
+  return check_cuda(c, cudaGetLastError(), "tensor-core gram launch");
+}
+
+}  // namespace
+
+int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
+  if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core Gram scratch not set up");
+  if (is_fp32(c)) return tc_gram_impl<float, 4, 4>(c, (const float*)A, (const float*)B, nb, M, hermitian);
+  return tc_gram_impl<double, 7, 6>(c, (const double*)A, (const double*)B, nb, M, hermitian);
+}
+
+// TMA descriptor of a slice buffer [S][rows][Lp] bf16: boxes of 16 values x 128 rows x S slices,
+// 32-byte swizzle (the layout the tensor core reads through smem_desc(..., 32)).
+int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled not available");
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  cuuint64_t dims[3] = {(cuuint64_t)Lp, (cuuint64_t)rows, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)Lp * 2, (cuuint64_t)rows * (cuuint64_t)Lp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)sg::BK, (cuuint32_t)sg::BM, (cuuint32_t)S};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled failed");
+  return PAWFD_OK;
+}
+
+// Scratch and TMA descriptors, sized for max_bands and one K block.
+int setup_tc(pawfd_ctx* c) {
+  TcScratch& t = c->tc;
+  const int nb = c->max_bands;
+  const bool cplx = is_complex(c);
+  const int S = is_fp32(c) ? 4 : 7;
+  const long long L = (long long)c->K * (cplx ? 2 : 1);
+  // K block: up to 512 chunks, no longer than the padded row
+  const long long Lpad = (L + sg::KC - 1) / sg::KC * sg::KC;
+  t.kblk = std::min<long long>(512LL * sg::KC, Lpad);
+  t.rowsA_alloc = (nb + sg::BM - 1) / sg::BM * sg::BM;
+  t.rowsB_alloc = ((cplx ? 2 * nb : nb) + sg::BN - 1) / sg::BN * sg::BN;
+  const size_t sa = (size_t)S * t.rowsA_alloc * t.kblk * 2, sb = (size_t)S * t.rowsB_alloc * t.kblk * 2;
+  const int nchunks = (int)(t.kblk / sg::KC);
+  const int rowsB = cplx ? 2 * nb : nb;
+  const int T = (nb + sg::BN - 1) / sg::BN;
+  const int tiles_min = (cplx ? 2 : 1) * T * (T + 1) / 2;
+  const int nsplit = std::max(1, std::min(nchunks, (c->num_sms + tiles_min - 1) / tiles_min));
+  t.part_bytes = (size_t)nsplit * nb * rowsB * sizeof(double);
+  int rc = check_cuda(c, cudaMalloc(&t.slicesA, sa), "cudaMalloc tc slices");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.slicesB, sb), "cudaMalloc tc slices");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.sigA, sizeof(int) * nchunks * t.rowsA_alloc), "cudaMalloc");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.sigB, sizeof(int) * nchunks * t.rowsB_alloc), "cudaMalloc");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.part, t.part_bytes), "cudaMalloc tc partials");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.maxA, sizeof(int) * t.rowsA_alloc), "cudaMalloc");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.maxB, sizeof(int) * t.rowsB_alloc), "cudaMalloc");
+  if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  // rows beyond nb (and the imaginary half's padding) are never sliced: keep them zero
+  rc = check_cuda(c, cudaMemset(t.slicesA, 0, sa), "memset");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.slicesB, 0, sb), "memset");
+  if (rc != PAWFD_OK) return rc;
+  rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S);
+  if (rc == PAWFD_OK) {
+    if (S == 7)
+      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              sg::smem_bytes<7>()), "smem attribute");
+    else
+      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              sg::smem_bytes<4>()), "smem attribute");
+  }
+  t.ready = rc == PAWFD_OK;
+  return rc;
+}
+
+void free_tc(pawfd_ctx* c) {
+  TcScratch& t = c->tc;
+  void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.maxA, t.maxB};
+  for (void* q : p)
+    if (q) cudaFree(q);
+  t = TcScratch();
+}
+
+}  // namespace pawfd
