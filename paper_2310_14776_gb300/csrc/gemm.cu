@@ -324,6 +324,7 @@ int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, boo
 }
 
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
+  if (c->use_tc) return launch_rotate_tc(c, psi, nb, C, out);
   return dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
     return rotate_impl<T>(c, (const T*)psi, nb, (const wide_t<T>*)C, (T*)out);

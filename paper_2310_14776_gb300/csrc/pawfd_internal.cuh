@@ -144,6 +144,19 @@ struct TcScratch {
   size_t part_bytes = 0;
   CUtensorMap mapA;
   CUtensorMap mapB;
+  // band rotation
+  long long rot_Lc = 0;        // contraction length (bands, x2 for complex) padded to chunks
+  int rot_rowsA_alloc = 0;
+  long long rot_rblk = 0;      // grid points per block
+  void* rotA = nullptr;        // FP64 operand built from C
+  void* rotSlicesA = nullptr;
+  void* rotSlicesB = nullptr;
+  int* rotSigA = nullptr;
+  int* rotSigB = nullptr;
+  int* rotMaxA = nullptr;
+  int* rotMaxB = nullptr;
+  CUtensorMap rotMapA;
+  CUtensorMap rotMapB;
 };
 
 }  // namespace pawfd
@@ -204,6 +217,7 @@ int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P);
 int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out);
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
+int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);

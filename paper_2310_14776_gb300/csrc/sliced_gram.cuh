@@ -4,15 +4,17 @@
 // to the chunk's largest binary exponent, as S balanced base-128 digits d_i in [-64, 64]:
 //     x ~= 2^sigma * sum_i d_i 2^(-7 i),       sigma = E - bias - 5   (per row and chunk)
 // The scaled digits d_i 2^(-7i) are exact in BF16, every digit product is exact in FP32, and
-// the tcgen05 tensor core sums them in FP32.  Four TMEM accumulators per output element, one
+// the tcgen05 tensor core sums them in FP32.  Five TMEM accumulators per output element, one
 // per digit order o = i + j (scaled digit products of order o are multiples of 2^(-7o) and at
 // most 2^(12 - 7o) in magnitude, so a sum of n of them is exact while n 2^12 <= 2^24):
 //     D0 = order 0 (1 product per grid value)   exact while KC <= 4096
 //     D1 = order 1 (2 products)                 exact while KC <= 2048
 //     D2 = order 2 (3 products)                 exact while KC <= 1365
-//     D3 = orders 3 .. ORD, rounded in FP32 (each term is already 2^-21 below order 0)
-// Chunks are KC = 256 values long, which keeps the FP32 drift of D3 small.  After every chunk
-// the epilogue adds 2^(sigma_a + sigma_b) (D0 + D1 + D2 + D3) to a double-float (two FP32)
+//     D3 = order 3 (4 products)                 exact while KC <= 1024
+//     D4 = orders 4 .. ORD, rounded in FP32 (each term is already 2^-28 below order 0)
+// Five accumulators of BN = 96 columns use 480 of the 512 TMEM columns.  Chunks are KC = 256
+// values long, which also keeps the FP32 drift of D4 small.  After every chunk
+// the epilogue adds 2^(sigma_a + sigma_b) (D0 + ... + D4) to a double-float (two FP32)
 // accumulator with error-free transformations (Knuth's TwoSum), so the FP64 pipe is not
 // needed per chunk; the scale is taken relative to the row's largest sigma of the K block.
 // S = 7 digits and orders up to ORD = 6 keep 48 bits of each FP64 value (products accurate to
@@ -31,19 +33,34 @@ namespace sg {
 
 constexpr int KC = 256;           // grid values per exactness chunk
 constexpr int BM = 128;           // output rows per CTA (TMEM lanes)
-constexpr int BN = 128;           // output columns per CTA
+constexpr int BN = 96;            // output columns per CTA (MMA N)
 constexpr int BK = 16;            // K per stage = one MMA (32-byte rows, 32B swizzle)
-constexpr int STAGES = 3;
-// Two epilogue warps per TMEM lane quarter (64 columns each) plus the TMA and MMA warps: ten
+constexpr int STAGES = 4;
+constexpr int NACC = 5;           // accumulators D0 .. D4 at columns 0, 96, 192, 288, 384
+// Two epilogue warps per TMEM lane quarter (48 columns each) plus the TMA and MMA warps: ten
 // warps, three on some SM sub-partitions, which caps registers at 168 per thread.
 constexpr int EPI_WARPS = 8;
+constexpr int EPI_COLS = BN / 2;
 constexpr int NTHREADS = (EPI_WARPS + 2) * 32;
-constexpr int TMEM_COLS = 512;    // D0, D1, D2, D3 at columns 0, 128, 256, 384
+constexpr int TMEM_COLS = 512;
 
+template <int S>
+__host__ __device__ constexpr int a_slice_bytes() { return BM * BK * 2; }
+__host__ __device__ constexpr int b_slice_bytes() { return BN * BK * 2; }
 template <int S>
 __host__ __device__ constexpr int stage_bytes() {
   static_assert(S >= 4 && S <= 7, "four to seven digits");
-  return 2 * S * BM * BK * 2;
+  return S * (BM + BN) * BK * 2;
+}
+
+// Hermitian tiling: tile rows of BM, tile columns of BN; a tile is needed when it holds an
+// element with row <= column, i.e. column tile tc >= (BM tr) / BN.
+__host__ __device__ inline int herm_first_col(int tr) { return (BM * tr) / BN; }
+__host__ __device__ inline int herm_tiles(int n) {
+  const int Tr = (n + BM - 1) / BM, Tc = (n + BN - 1) / BN;
+  int t = 0;
+  for (int r = 0; r < Tr; ++r) t += Tc > herm_first_col(r) ? Tc - herm_first_col(r) : 0;
+  return t;
 }
 template <int S>
 __host__ __device__ constexpr int smem_bytes() { return STAGES * stage_bytes<S>() + 1024; }
@@ -137,25 +154,107 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
   }
 }
 
+// Transposing slicer for the band rotation: operand rows are grid points r, the contraction
+// index k runs over the bands (real: k = n; complex: k = 2 n + c, c = 0 real / 1 imaginary
+// part).  One CTA per (16 grid points, chunk of KC contraction values): the [KC][16] tile is
+// read along r, the largest exponent of every grid point's chunk found, and the digits
+// written along k.  out: [S][out_rows][Lp]; sig: [nchunks][sig_ld] (sig_ld >= rows).
+constexpr int RT = 16;
+
+template <class R, int S>
+__global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
+                                                      long long r0, int rcount, long long Lp, int out_rows,
+                                                      __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
+                                                      int sig_ld, int* __restrict__ sigmax) {
+  __shared__ R tile[KC][RT + 1];
+  __shared__ int pmax[16][RT];
+  const int rt = blockIdx.x, c = blockIdx.y;
+  const int tid = threadIdx.x, lr = tid % RT, kq = tid / RT;
+  const long long Lk = (long long)nb * (cplx ? 2 : 1);
+  const int rl0 = rt * RT;   // first local grid point of this CTA
+  for (int kk = kq; kk < KC; kk += 16) {
+    const long long k = (long long)c * KC + kk;
+    R v = R(0);
+    if (k < Lk && rl0 + lr < rcount) {
+      const long long n = cplx ? (k >> 1) : k;
+      const long long e = (n * K + r0 + rl0 + lr) * (cplx ? 2 : 1) + (cplx ? (k & 1) : 0);
+      v = psi[e];
+    }
+    tile[kk][lr] = v;
+  }
+  __syncthreads();
+  int em = 0;
+  for (int kk = kq; kk < KC; kk += 16) em = max(em, fields(tile[kk][lr]).exp);
+  pmax[kq][lr] = em;
+  __syncthreads();
+  constexpr int bias = FloatBits<R>::bias, nbits = FloatBits<R>::nb;
+  constexpr int g = 7 * S - 1 - nbits;
+  if (tid < RT) {
+    int m = 0;
+    for (int q = 0; q < 16; ++q) m = max(m, pmax[q][tid]);
+    pmax[0][tid] = m;
+    if (rl0 + tid < rcount) {
+      sig[(long long)c * sig_ld + rl0 + tid] = m - bias - 5;
+      atomicMax(sigmax + rl0 + tid, m - bias - 5);
+    }
+  }
+  __syncthreads();
+  const int w = tid >> 5, lane = tid & 31;
+  for (int q = w; q < RT; q += 8) {
+    if (rl0 + q >= rcount) break;
+    const int emax = pmax[0][q];
+    for (int kk = lane; kk < KC; kk += 32) {
+      const Fields f = fields(tile[kk][q]);
+      unsigned long long G = 0;
+      const int sh = emax - f.exp + 1;
+      const int rs = sh - g;
+      if (f.exp != 0 && rs < 64) G = rs > 0 ? (f.mant + (1ull << (rs - 1))) >> rs : f.mant << (-rs);
+      int d[S];
+#pragma unroll
+      for (int i = 0; i < S; ++i) d[i] = (int)((G >> (7 * (S - 1 - i))) & 127ull);
+#pragma unroll
+      for (int i = S - 1; i >= 1; --i)
+        if (d[i] >= 64) {
+          d[i] -= 128;
+          d[i - 1] += 1;
+        }
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        const float v = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
+        out[((long long)i * out_rows + rl0 + q) * Lp + (long long)c * KC + kk] = __float2bfloat16_rn(v);
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Gram kernel
 // ------------------------------------------------------------------------------------------
 struct GramArgs {
-  const int* sigA;      // [nchunks][sig_ldA]  (chunks of this K block)
-  const int* sigB;      // [nchunks][sig_ldB]
-  const int* maxA;      // [rows] largest sigma of each row in this K block
-  const int* maxB;
-  int sig_ldA, sig_ldB;
-  int rowsA, rowsB;     // valid rows of the two operands
-  int tilesN;           // column tiles (ceil(rowsB / BN))
-  int herm;             // only tiles with tile row <= tile column (within each half of B if halves > 1)
-  int halves;           // 2 for complex (B = [B'; B'']): tiles are enumerated per half
-  int half_rows;        // rows per half of B (complex: nb)
-  int chunks_per_cta;
-  int nchunks;          // chunks in this K block
-  int accumulate;       // add to part instead of overwriting it (second and later K blocks)
-  double* part;         // [nsplit][rowsA][rowsB]
-  DeviceStatus* st;
+  const int* sigA = nullptr;      // [nchunks][sig_ldA]  (chunks of this K block)
+  const int* sigB = nullptr;      // [nchunks][sig_ldB]
+  const int* maxA = nullptr;      // [rows] largest sigma of each row in this K block
+  const int* maxB = nullptr;
+  int sig_ldA = 0, sig_ldB = 0;
+  int rowsA = 0, rowsB = 0;     // valid rows of the two operands
+  int tilesN = 0;           // column tiles (ceil(rowsB / BN))
+  int herm = 0;             // only tiles with tile row <= tile column (within each half of B if halves > 1)
+  int halves = 0;           // 2 for complex (B = [B'; B'']): tiles are enumerated per half
+  int half_rows = 0;        // rows per half of B (complex: nb)
+  int chunks_per_cta = 0;
+  int nchunks = 0;          // chunks in this K block
+  int accumulate = 0;       // add to part instead of overwriting it (second and later K blocks)
+  double* part = nullptr;         // [nsplit][rowsA][rowsB]
+  DeviceStatus* st = nullptr;
+  // band rotation: write every output value straight to the band array instead of partials.
+  // Row `row` of the product is band row % rot_nb, real part for row < rot_nb and imaginary
+  // part otherwise (complex); column `col` is grid point col of the block starting at rot_out.
+  int rotation = 0;
+  int rot_nb = 0;
+  int rot_cplx = 0;
+  int rot_fp32 = 0;
+  long long rot_K = 0;  // grid points per band
+  void* rot_out = nullptr;        // band array, already offset to the first grid point of the block
 };
 
 // 2^e for the product scale; below the normal range the chunk contributes nothing (its
@@ -164,23 +263,28 @@ __device__ __forceinline__ double pow2(int e) {
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
-// tile index -> (tile row, tile col) over the output [rowsA][rowsB]
+// tile index -> (tile row, tile col) over the output [rowsA][rowsB]; tile columns are numbered
+// per half of B (Tc = ceil(half_rows / BN) each)
 __device__ __forceinline__ void gram_tile(const GramArgs& a, int t, int* tr, int* tc_) {
   if (!a.herm) {
     *tr = t / a.tilesN;
     *tc_ = t % a.tilesN;
     return;
   }
-  const int T = (a.half_rows + BN - 1) / BN;     // tiles per half side
-  const int per_half = T * (T + 1) / 2;
+  const int Tc = (a.half_rows + BN - 1) / BN;
+  const int per_half = herm_tiles(a.half_rows);
   const int h = t / per_half;
   int u = t % per_half, row = 0;
-  while (u >= T - row) {
-    u -= T - row;
+  while (true) {
+    const int first = herm_first_col(row), cnt = Tc > first ? Tc - first : 0;
+    if (u < cnt) {
+      *tr = row;
+      *tc_ = h * Tc + first + u;
+      return;
+    }
+    u -= cnt;
     ++row;
   }
-  *tr = row;
-  *tc_ = h * T + row + u;
 }
 
 // float 2^e for e <= 0 (0 below the normal range)
@@ -251,7 +355,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         }
         const int kx = (c_begin + g / steps_per_chunk) * KC + (g % steps_per_chunk) * BK;
         unsigned char* sa = smem + s * stage_bytes<S>();
-        unsigned char* sb = sa + S * BM * BK * 2;
+        unsigned char* sb = sa + S * a_slice_bytes<S>();
         tc::mbar_expect_tx(&full[s], stage_bytes<S>());
         tc::tma_load_3d(sa, &tA, &full[s], kx, row0, 0);
         tc::tma_load_3d(sb, &tB, &full[s], kx, col0, 0);
@@ -278,18 +382,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           }
           tc::fence_after_sync();
           unsigned char* sa = smem + s * stage_bytes<S>();
-          unsigned char* sb = sa + S * BM * BK * 2;
+          unsigned char* sb = sa + S * a_slice_bytes<S>();
+          bool touched[NACC] = {false, false, false, false, false};
 #pragma unroll
           for (int i = 0; i < S; ++i)
 #pragma unroll
-            for (int j = 0; j < S && i + j <= ORD; ++j) {
-              const int o = i + j;
-              const uint32_t d = tmem + (uint32_t)((o < 3 ? o : 3) * BN);
+            for (int j = 0; j < S; ++j) {
+              if (i + j > ORD) continue;
+              const int slot = (i + j) < NACC - 1 ? (i + j) : NACC - 1;
+              const uint32_t d = tmem + (uint32_t)(slot * BN);
               // the first product written into an accumulator in this chunk overwrites it
-              // (loop order: (0,0) (0,1) (0,2) (0,3) ... so each order first appears with i = 0)
-              const bool first = (q == 0) && (i == 0) && (j <= 3);
-              tc::mma_bf16(d, tc::smem_desc(sa + i * BM * BK * 2, BK * 2), tc::smem_desc(sb + j * BM * BK * 2, BK * 2),
-                           idesc, first ? 0u : 1u);
+              const bool first = (q == 0) && !touched[slot];
+              touched[slot] = true;
+              tc::mma_bf16(d, tc::smem_desc(sa + i * a_slice_bytes<S>(), BK * 2),
+                           tc::smem_desc(sb + j * b_slice_bytes(), BK * 2), idesc, first ? 0u : 1u);
             }
           tc::mma_commit(&empty[s]);
           consumed = g + 1;
@@ -301,10 +407,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     // epilogue warps: lane quarter (warp % 4), column half (warp / 4)
     const int quarter = warp & 3, chalf = warp >> 2;
     const int row = row0 + quarter * 32 + lane;
-    const int cbase = chalf * 64;
-    float ahi[64], alo[64];
+    const int cbase = chalf * EPI_COLS;
+    float ahi[EPI_COLS], alo[EPI_COLS];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
+    for (int j = 0; j < EPI_COLS; ++j) {
       ahi[j] = 0.0f;
       alo[j] = 0.0f;
     }
@@ -323,13 +429,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       const int chunk = c_begin + c;
       const int sa = (row < a.rowsA) ? __ldg(a.sigA + (long long)chunk * a.sig_ldA + row) - ra : 0;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) {
-        uint32_t d0[8], d1[8], d2[8], d3[8];
+      for (int b = 0; b < EPI_COLS / 8; ++b) {
+        uint32_t d[NACC][8];
         const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + b * 8);
-        tc::tmem_ld8(base, d0);
-        tc::tmem_ld8(base + BN, d1);
-        tc::tmem_ld8(base + 2 * BN, d2);
-        tc::tmem_ld8(base + 3 * BN, d3);
+#pragma unroll
+        for (int o = 0; o < NACC; ++o) tc::tmem_ld8(base + o * BN, d[o]);
         tc::tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -337,11 +441,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           const int sb = (col < a.rowsB) ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + col) - __ldg(a.maxB + col)
                                          : 0;
           const float scale = pow2f_nonpos(sa + sb);
-          // D0 + D1 + D2 exactly as a double-float, then D3
-          float s1, e1, s2, e2, vh, vl;
-          two_sum(__uint_as_float(d0[j]), __uint_as_float(d1[j]), s1, e1);
-          two_sum(s1, __uint_as_float(d2[j]), s2, e2);
-          two_sum(s2, (e1 + e2) + __uint_as_float(d3[j]), vh, vl);
+          // D0 + D1 + D2 + D3 exactly as a double-float, then D4
+          float s1, e1, s2, e2, s3, e3, vh, vl;
+          two_sum(__uint_as_float(d[0][j]), __uint_as_float(d[1][j]), s1, e1);
+          two_sum(s1, __uint_as_float(d[2][j]), s2, e2);
+          two_sum(s2, __uint_as_float(d[3][j]), s3, e3);
+          two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][j]), vh, vl);
           df_add(ahi[b * 8 + j], alo[b * 8 + j], vh * scale, vl * scale);
         }
       }
@@ -351,10 +456,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     }
     // columns beyond this tile's half of B belong to the other half's tiles
     const int col_lim = min(a.rowsB, (tcol / T + 1) * a.half_rows);
-    if (row < a.rowsA && !abort_flag) {
+    if (a.rotation) {
+      if (row < a.rowsA && !abort_flag) {
+        const int band = row % a.rot_nb, part = row / a.rot_nb;
+        const long long base = (long long)band * a.rot_K;
+#pragma unroll
+        for (int j = 0; j < EPI_COLS; ++j) {
+          const int col = col0 + cbase + j;
+          if (col < a.rowsB) {
+            const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
+            const long long idx = a.rot_cplx ? 2 * (base + col) + part : base + col;
+            if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v;
+            else ((double*)a.rot_out)[idx] = v;
+          }
+        }
+      }
+    } else if (row < a.rowsA && !abort_flag) {
       double* out = a.part + ((long long)blockIdx.y * a.rowsA + row) * a.rowsB;
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
+      for (int j = 0; j < EPI_COLS; ++j) {
         const int col = col0 + cbase + j;
         if (col < col_lim) {
           const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));

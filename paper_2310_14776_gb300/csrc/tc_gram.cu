@@ -63,9 +63,9 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   const bool cplx = is_complex(c);
   const long long L = (long long)c->K * (cplx ? 2 : 1);            // real-view row length
   const int rowsB = cplx ? 2 * nb : nb;
-  const int T = (nb + sg::BN - 1) / sg::BN;
+  const int Tr = (nb + sg::BM - 1) / sg::BM, Tc = (nb + sg::BN - 1) / sg::BN;
   const int halves = cplx ? 2 : 1;
-  const int tiles = herm ? halves * T * (T + 1) / 2 : halves * T * T;
+  const int tiles = herm ? halves * sg::herm_tiles(nb) : Tr * halves * Tc;
   const long long Kblk = t.kblk;
   const int max_chunks = (int)(Kblk / sg::KC);
   // splits per K block: fill the SMs once (one CTA per SM), at least one chunk per CTA
@@ -94,7 +94,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
           B + k0, nb, L, len, nch, Kblk, true, nb, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
       c->launches += 1;
     }
-    sg::GramArgs a;
+    sg::GramArgs a = {};
     a.sigA = t.sigA;
     a.sigB = t.sigB;
     a.sig_ldA = t.rowsA_alloc;
@@ -103,7 +103,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     a.maxB = t.maxB;
     a.rowsA = nb;
     a.rowsB = rowsB;
-    a.tilesN = halves * T;
+    a.tilesN = halves * Tc;
     a.herm = herm;
     a.halves = halves;
     a.half_rows = nb;
@@ -129,7 +129,93 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   return check_cuda(c, cudaGetLastError(), "tensor-core gram launch");
 }
 
+// The rotation's first operand: A_ext[row][k] with k the contraction index.  Real:
+// A[m][n] = C[n][m].  Complex (C interleaved): rows m < nb give the real part of the output,
+// A[m][2n] = Re C[n][m], A[m][2n+1] = -Im C[n][m]; rows nb + m the imaginary part,
+// A[nb+m][2n] = Im C[n][m], A[nb+m][2n+1] = Re C[n][m].  Columns beyond the contraction are 0.
+__global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int cplx, double* __restrict__ A,
+                                   long long Lc, int rows) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * Lc) return;
+  const int row = (int)(e / Lc);
+  const long long k = e % Lc;
+  double v = 0.0;
+  if (!cplx) {
+    if (row < nb && k < nb) v = C[k * nb + row];
+  } else if (row < 2 * nb && k < 2 * nb) {
+    const int m = row % nb, n = (int)(k >> 1), re = (k & 1) == 0;
+    const double cr = C[2 * ((long long)n * nb + m)], ci = C[2 * ((long long)n * nb + m) + 1];
+    v = row < nb ? (re ? cr : -ci) : (re ? ci : cr);
+  }
+  A[e] = v;
+}
+
+template <class R, int S, int ORD>
+int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) {
+  TcScratch& t = c->tc;
+  const bool cplx = is_complex(c);
+  const int rowsA = cplx ? 2 * nb : nb;
+  const long long Lk = (long long)nb * (cplx ? 2 : 1);
+  const long long Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
+  const int nch = (int)(Lc / sg::KC);
+  if (Lc > t.rot_Lc) return fail(c, PAWFD_EINVAL, "rotation scratch too small");
+  const long long K = (long long)c->K;
+  // operand A from C, then its digits
+  rot_operand_kernel<<<(unsigned)((t.rot_rowsA_alloc * t.rot_Lc + 255) / 256), 256, 0, c->stream>>>(
+      C, nb, cplx, (double*)t.rotA, t.rot_Lc, t.rot_rowsA_alloc);
+  cudaMemsetAsync(t.rotMaxA, 0x80, sizeof(int) * t.rot_rowsA_alloc, c->stream);
+  {
+    const long long warps = (long long)rowsA * nch;
+    sg::slice_kernel<double, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+        (const double*)t.rotA, rowsA, t.rot_Lc, Lk, nch, t.rot_Lc, false, 0, t.rot_rowsA_alloc,
+        (__nv_bfloat16*)t.rotSlicesA, t.rotSigA, t.rot_rowsA_alloc, t.rotMaxA);
+  }
+  c->launches += 2;
+  const int tilesM = (rowsA + sg::BM - 1) / sg::BM;
+  for (long long r0 = 0; r0 < K; r0 += t.rot_rblk) {
+    const int rcount = (int)std::min<long long>(t.rot_rblk, K - r0);
+    cudaMemsetAsync(t.rotMaxB, 0x80, sizeof(int) * t.rot_rblk, c->stream);
+    sg::slice_t_kernel<R, S><<<dim3((rcount + sg::RT - 1) / sg::RT, nch), 256, 0, c->stream>>>(
+        psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
+        (int)t.rot_rblk, t.rotMaxB);
+    sg::GramArgs a = {};
+    a.sigA = t.rotSigA;
+    a.sigB = t.rotSigB;
+    a.sig_ldA = t.rot_rowsA_alloc;
+    a.sig_ldB = (int)t.rot_rblk;
+    a.maxA = t.rotMaxA;
+    a.maxB = t.rotMaxB;
+    a.rowsA = rowsA;
+    a.rowsB = rcount;
+    a.tilesN = (rcount + sg::BN - 1) / sg::BN;
+    a.herm = 0;
+    a.halves = 1;
+    a.half_rows = rcount;
+    a.chunks_per_cta = nch;
+    a.nchunks = nch;
+    a.accumulate = 0;
+    a.part = nullptr;
+    a.st = c->d_status;
+    a.rotation = 1;
+    a.rot_nb = nb;
+    a.rot_cplx = cplx;
+    a.rot_fp32 = sizeof(R) == 4;
+    a.rot_K = K;
+    a.rot_out = out + r0 * (cplx ? 2 : 1);
+    sg::sliced_gram_kernel<S, ORD><<<dim3(tilesM * a.tilesN, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.rotMapA, t.rotMapB, a);
+    c->launches += 2;
+  }
+  return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
+}
+
 }  // namespace
+
+int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
+  if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core scratch not set up");
+  if (is_fp32(c)) return tc_rotate_impl<float, 4, 4>(c, (const float*)psi, nb, (const double*)C, (float*)out);
+  return tc_rotate_impl<double, 7, 6>(c, (const double*)psi, nb, (const double*)C, (double*)out);
+}
 
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
   if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core Gram scratch not set up");
@@ -137,9 +223,9 @@ int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, 
   return tc_gram_impl<double, 7, 6>(c, (const double*)A, (const double*)B, nb, M, hermitian);
 }
 
-// TMA descriptor of a slice buffer [S][rows][Lp] bf16: boxes of 16 values x 128 rows x S slices,
+// TMA descriptor of a slice buffer [S][rows][Lp] bf16: boxes of 16 values x box_rows x S slices,
 // 32-byte swizzle (the layout the tensor core reads through smem_desc(..., 32)).
-int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S) {
+int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -151,7 +237,7 @@ int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long 
   }
   cuuint64_t dims[3] = {(cuuint64_t)Lp, (cuuint64_t)rows, (cuuint64_t)S};
   cuuint64_t strides[2] = {(cuuint64_t)Lp * 2, (cuuint64_t)rows * (cuuint64_t)Lp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)sg::BK, (cuuint32_t)sg::BM, (cuuint32_t)S};
+  cuuint32_t box[3] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows, (cuuint32_t)S};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -175,8 +261,7 @@ int setup_tc(pawfd_ctx* c) {
   const size_t sa = (size_t)S * t.rowsA_alloc * t.kblk * 2, sb = (size_t)S * t.rowsB_alloc * t.kblk * 2;
   const int nchunks = (int)(t.kblk / sg::KC);
   const int rowsB = cplx ? 2 * nb : nb;
-  const int T = (nb + sg::BN - 1) / sg::BN;
-  const int tiles_min = (cplx ? 2 : 1) * T * (T + 1) / 2;
+  const int tiles_min = (cplx ? 2 : 1) * sg::herm_tiles(nb);
   const int nsplit = std::max(1, std::min(nchunks, (c->num_sms + tiles_min - 1) / tiles_min));
   t.part_bytes = (size_t)nsplit * nb * rowsB * sizeof(double);
   int rc = check_cuda(c, cudaMalloc(&t.slicesA, sa), "cudaMalloc tc slices");
@@ -191,8 +276,8 @@ int setup_tc(pawfd_ctx* c) {
   rc = check_cuda(c, cudaMemset(t.slicesA, 0, sa), "memset");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.slicesB, 0, sb), "memset");
   if (rc != PAWFD_OK) return rc;
-  rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S);
-  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S);
+  rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BM);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) {
     if (S == 7)
       rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -201,13 +286,40 @@ int setup_tc(pawfd_ctx* c) {
       rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               sg::smem_bytes<4>()), "smem attribute");
   }
+  // rotation scratch: operand A (from C) and its digits, digits of a block of grid points
+  if (rc == PAWFD_OK) {
+    const long long Lk = (long long)nb * (cplx ? 2 : 1);
+    t.rot_Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
+    t.rot_rowsA_alloc = ((cplx ? 2 * nb : nb) + sg::BM - 1) / sg::BM * sg::BM;
+    const long long Kpad = ((long long)c->K + sg::BN - 1) / sg::BN * sg::BN;
+    const long long budget = 512ll << 20;   // bytes of grid-point digits per block
+    long long rblk = budget / ((long long)S * t.rot_Lc * 2) / sg::BN * sg::BN;
+    t.rot_rblk = std::max<long long>(sg::BN, std::min(rblk, Kpad));
+    const int nchr = (int)(t.rot_Lc / sg::KC);
+    const size_t a_bytes = sizeof(double) * t.rot_rowsA_alloc * t.rot_Lc;
+    const size_t sa_bytes = (size_t)S * t.rot_rowsA_alloc * t.rot_Lc * 2;
+    const size_t sb_bytes = (size_t)S * t.rot_rblk * t.rot_Lc * 2;
+    rc = check_cuda(c, cudaMalloc(&t.rotA, a_bytes), "cudaMalloc rot");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotSlicesA, sa_bytes), "cudaMalloc rot");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotSlicesB, sb_bytes), "cudaMalloc rot");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotSigA, sizeof(int) * nchr * t.rot_rowsA_alloc), "cudaMalloc");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotSigB, sizeof(int) * nchr * t.rot_rblk), "cudaMalloc");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotMaxA, sizeof(int) * t.rot_rowsA_alloc), "cudaMalloc");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotMaxB, sizeof(int) * t.rot_rblk), "cudaMalloc");
+    if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+    rc = check_cuda(c, cudaMemset(t.rotSlicesA, 0, sa_bytes), "memset");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesB, 0, sb_bytes), "memset");
+    if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapA, t.rotSlicesA, t.rot_rowsA_alloc, t.rot_Lc, S, sg::BM);
+    if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapB, t.rotSlicesB, (int)t.rot_rblk, t.rot_Lc, S, sg::BN);
+  }
   t.ready = rc == PAWFD_OK;
   return rc;
 }
 
 void free_tc(pawfd_ctx* c) {
   TcScratch& t = c->tc;
-  void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.maxA, t.maxB};
+  void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.maxA, t.maxB,
+               t.rotA, t.rotSlicesA, t.rotSlicesB, t.rotSigA, t.rotSigB, t.rotMaxA, t.rotMaxB};
   for (void* q : p)
     if (q) cudaFree(q);
   t = TcScratch();
