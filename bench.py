@@ -148,22 +148,23 @@ def run_gpu(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def step(cur, nxt, marks=None):
-        if marks is not None:
-            marks[0].record(stream)
+        # marks: events between the stages apply_H | apply_S | Gram H | Gram S | subspace | rotate
+        def mark(i):
+            if marks is not None:
+                marks[i].record(stream)
+        mark(0)
         ctx.apply_H(cur, out=work["Hpsi"])
-        if marks is not None:
-            marks[1].record(stream)
+        mark(1)
         ctx.apply_S(cur, out=work["Spsi"])
-        if marks is not None:
-            marks[2].record(stream)
+        mark(2)
         ctx.gram(cur, work["Hpsi"], M=work["Hnm"], hermitian=True)
-        if marks is not None:
-            marks[3].record(stream)
+        mark(3)
         ctx.gram(cur, work["Spsi"], M=work["Snm"], hermitian=True)
+        mark(4)
         ctx.subspace_diag(work["Hnm"], work["Snm"], eps=work["eps"], C=work["C"], overwrite=True, check=False)
+        mark(5)
         ctx.rotate(cur, work["C"], out=nxt)
-        if marks is not None:
-            marks[4].record(stream)
+        mark(6)
 
     for i in range(args.warmup):
         step(psi[i % 2], psi[(i + 1) % 2])
@@ -176,7 +177,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
-    marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
+    marks = [[ev() for _ in range(7)] for _ in range(args.steps)]
     t0, t1 = ev(), ev()
     t0.record(stream)
     for i in range(args.steps):
@@ -193,24 +194,40 @@ def run_gpu(args):
         tt = torch.tensor([elapsed], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = tt.item()
-    step_ms = [m[0].elapsed_time(m[4]) for m in marks]
-    applyH_ms = [m[0].elapsed_time(m[1]) for m in marks]
-    gram_ms = [m[2].elapsed_time(m[3]) for m in marks]
+    step_ms = [m[0].elapsed_time(m[6]) for m in marks]
+    names = ["apply_H", "apply_S", "gram_H", "gram_S", "subspace_diag", "rotate"]
+    stages = {nm: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks) for i, nm in enumerate(names)}
     drift = float(torch.max(torch.abs(work["eps"] - eps_first)).item())
 
     units = float(nb) * K * args.steps * world
     value = units / elapsed / 1e9
-    flop_scale = 8.0 if cplx else 2.0
-    gram_flops = flop_scale * nb * (nb + 1) / 2 * K     # unique entries of the Hermitian H_nm
-    gram_s = statistics.mean(gram_ms) * 1e-3
-    gram_tflops = gram_flops / gram_s / 1e12
     esize = psi_host.itemsize
-    bytes_ptband = 2 * esize
     mixed = args.precision == "mixed"
-    alu_peak = FP32_PROBE_TFLOPS if mixed else FP64_NOMINAL_TFLOPS
-    applyH_s = statistics.mean(applyH_ms) * 1e-3
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    # digit products per real multiply-add of the tensor-core kernels (orders <= 6 of 7 digits
+    # for FP64 data, <= 4 of 4 digits for FP32 data) and real multiply-adds per complex one
+    products = 13 if mixed else 28
+    cfac = 4 if cplx else 1
+    # algorithmic work per stage (see the roofline table of the design notes)
+    work_units = {
+        # FP64: 19 FP64 instructions per point-band (9 add, 9 FMA, 1 mul), vs the FP64 issue rate
+        "apply_H": ("alu", 19.0 * nb * K * (2 if cplx else 1), FP64_NOMINAL_TFLOPS / 2 * 1e12, "FP64 instr/s")
+        if not mixed else ("hbm", 2.0 * esize * nb * K, hbm * 1e9, "B/s"),
+        "gram_H": ("tensor", 2.0 * products * cfac * nb * (nb + 1) / 2 * K, bf16 * 1e12, "BF16 FLOP/s"),
+        "gram_S": ("tensor", 2.0 * products * cfac * nb * (nb + 1) / 2 * K, bf16 * 1e12, "BF16 FLOP/s"),
+        "rotate": ("tensor", 2.0 * products * cfac * nb * nb * K, bf16 * 1e12, "BF16 FLOP/s"),
+    }
+    dom = max((k for k in stages if k in work_units), key=lambda k: stages[k])
+    bound, amount, peak, unit = work_units[dom]
+    achieved = amount / (stages[dom] * 1e-3)
+    kernel_of = {"apply_H": "kinetic_local_kernel + project_kernel + nonlocal_add_kernel",
+                 "gram_H": "slice_kernel + sliced_gram_kernel (digit-product Gram)",
+                 "gram_S": "slice_kernel + sliced_gram_kernel (digit-product Gram)",
+                 "rotate": "slice_t_kernel + sliced_gram_kernel (digit-product rotation)"}
+    scale = 1e12 if unit.endswith("FLOP/s") or unit == "FP64 instr/s" else 1e9
+    roof_unit = {"BF16 FLOP/s": "TFLOP/s", "FP64 instr/s": "Tinstr/s", "B/s": "GB/s"}[unit]
 
     result = {
         "metric": "H|psi> Gpt.band/s over whole Rayleigh-Ritz steps (apply_H + apply_S + Gram + subspace diag + rotate)",
@@ -224,19 +241,14 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (%.2f GB of bands per step)" % (2 * nb * K * esize / 1e9)},
         "rr_steps_per_s": args.steps * world / elapsed,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
-        "apply_H_gptband_s": nb * K / applyH_s / 1e9,
+        "stages_ms": stages,
+        "apply_H_gptband_s": nb * K / (stages["apply_H"] * 1e-3) / 1e9,
         "eig_drift_ha": drift,
-        "roofline": {"kernel": ("gram_partial_mixed_kernel (FP32 FMA, FP64 fold)" if mixed else
-                                "gram_partial_kernel (FP64 DFMA GEMM)") + ", Hermitian H_nm: upper tiles only",
-                     "bound": "alu", "achieved": gram_tflops, "peak": alu_peak, "unit": "TFLOP/s",
-                     "frac": gram_tflops / alu_peak, "traffic": None,
-                     "peak_source": ("FP32 FMA rate measured by a probe kernel (not in MEASURED_PEAKS.json)" if mixed
-                                     else "nominal GB300 FP64 rate (not in MEASURED_PEAKS.json; probe measured 1.198)")},
-        "stencil_roofline": {"kernel": "apply_H (stencil + projections + back-add)",
-                             "bound": "hbm" if mixed else "alu",
-                             "achieved_gptband_s": nb * K / applyH_s / 1e9,
-                             "hbm_achieved_gbs": bytes_ptband * nb * K / applyH_s / 1e9, "hbm_peak_gbs": hbm,
-                             "hbm_frac": bytes_ptband * nb * K / applyH_s / 1e9 / hbm},
+        "roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
+                     "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak, "traffic": None,
+                     "peak_source": {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                                     "hbm": "MEASURED_PEAKS.json hbm_gbs",
+                                     "alu": "nominal GB300 FP64 rate 1.25 TFLOP/s / 2 (FMA)"}[bound]},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
