@@ -103,6 +103,14 @@ int pawfd_nproj_total(const pawfd_ctx* ctx);
 /* number of CUDA kernels this context has launched so far (host-side counter) */
 long long pawfd_launch_count(const pawfd_ctx* ctx);
 
+/* Select among equivalent implementations (for tests and measurements):
+ *   "tensor_cores"    1 (default): Gram matrices and rotations on the tensor cores with exact
+ *                     digit slices; 0: FP64 / FP32 FMA kernels on the CUDA cores.
+ *   "stencil_variant" 0 (default): fastest kernel that applies to the shape; 1: skip the
+ *                     bulk-copy ring kernel; 2: always the general kernel.
+ * Returns PAWFD_EINVAL for an unknown name or value. */
+int pawfd_set_option(pawfd_ctx* ctx, const char* name, int value);
+
 /* Projector overlaps P[i][n] = <p_i^a | psi_n> = dV sum_r conj(p_i^a(r)) psi_n(r), for
  * every atom a and projector i (global row i), n < nb.  Bloch phases exp(i k.T) of the
  * lattice translation T of each box point are applied (projector overlaps of the PAW

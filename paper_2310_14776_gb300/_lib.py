@@ -34,6 +34,7 @@ SIGNATURES = {
     "pawfd_last_error": ([VP], ctypes.c_char_p),
     "pawfd_nproj_total": ([VP], I),
     "pawfd_launch_count": ([VP], ctypes.c_longlong),
+    "pawfd_set_option": ([VP, ctypes.c_char_p, I], I),
     "pawfd_project": ([VP, VP, I, VP], I),
     "pawfd_apply_H": ([VP, VP, I, VP, VP], I),
     "pawfd_apply_S": ([VP, VP, I, VP, VP], I),

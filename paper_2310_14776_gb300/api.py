@@ -103,6 +103,12 @@ class Context:
         if rc != 0:
             raise PawFDError(rc, self.lib.pawfd_last_error(self._h).decode())
 
+    def set_option(self, name: str, value: int):
+        """Choose among equivalent implementations (see pawfd_set_option in include/pawfd.h)."""
+        rc = self.lib.pawfd_set_option(self._h, name.encode(), int(value))
+        if rc != 0:
+            raise PawFDError(rc, self.lib.pawfd_last_error(self._h).decode())
+
     def launch_count(self) -> int:
         """CUDA kernels this context has launched (counted by the library)."""
         return int(self.lib.pawfd_launch_count(self._h))

@@ -351,6 +351,22 @@ extern "C" int pawfd_nproj_total(const pawfd_ctx* c) { return c ? c->at.Ip : PAW
 
 extern "C" long long pawfd_launch_count(const pawfd_ctx* c) { return c ? c->launches : PAWFD_EINVAL; }
 
+extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
+  if (!c || !name) return PAWFD_EINVAL;
+  const std::string n(name);
+  if (n == "tensor_cores" && (value == 0 || value == 1)) {
+    if (value == 1 && !c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core scratch not set up");
+    c->use_tc = value == 1;
+    return PAWFD_OK;
+  }
+  if (n == "stencil_variant" && value >= 0 && value <= 2) {
+    c->stencil_variant = value;
+    c->fast_stencil = value != 2;
+    return PAWFD_OK;
+  }
+  return fail(c, PAWFD_EINVAL, "unknown option or value");
+}
+
 extern "C" int pawfd_sync(pawfd_ctx* c) {
   if (!c) return PAWFD_EINVAL;
   int rc = check_cuda(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(DeviceStatus), cudaMemcpyDeviceToHost,

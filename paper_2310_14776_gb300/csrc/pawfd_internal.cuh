@@ -182,6 +182,8 @@ struct pawfd_ctx {
   int num_sms = 0;
   long long launches = 0;                     // kernels this context has launched
   bool use_tc = true;                         // Gram matrices on the tensor cores (sliced digits)
+  bool fast_stencil = true;                   // shape-specialised stencil kernels where they apply
+  int stencil_variant = 0;                    // 0: ring (bulk copies) first, 1: register float4 kernel
   pawfd::TcScratch tc;
   std::string err;
 };

@@ -148,7 +148,15 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
 
 }  // namespace
 
+int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out);
+int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out);
+
 int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
+  if (c->dtype == PAWFD_R32 && c->fast_stencil) {
+    if (c->stencil_variant != 1 && launch_kinetic_local_ring(c, (const float*)psi, nb, (float*)out) == PAWFD_OK)
+      return PAWFD_OK;
+    if (launch_kinetic_local_f32x4(c, (const float*)psi, nb, (float*)out) == PAWFD_OK) return PAWFD_OK;
+  }
   return dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
     return kinetic_local_impl<T>(c, (const T*)psi, nb, (T*)out);

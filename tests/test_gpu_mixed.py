@@ -69,6 +69,11 @@ CASES = {
     "gamma": dict(n=(24, 24, 24), cell=(10.0, 10.0, 10.0), natoms=2, pset=synth.PSET_SP, nb=16, cplx=False),
     "bloch": dict(n=(36, 30, 28), cell=(13.6, 11.3, 10.6), natoms=6, pset=synth.PSET_SPD2, nb=40, cplx=True),
     "ragged": dict(n=(45, 19, 13), cell=(9.0, 7.6, 5.2), natoms=4, pset=synth.PSET_SPD2, nb=9, cplx=True),
+    # FP32 real with N1 % 4 == 0 (the float4 stencil): fewer rows than one y tile, odd N3
+    "f32x4-small": dict(n=(28, 9, 11), cell=(7.0, 3.5, 4.4), natoms=3, pset=synth.PSET_SP, nb=7, cplx=False),
+    # two x tiles (the second ragged) and three y tiles (the last ragged)
+    "f32x4-ragged": dict(n=(132, 37, 10), cell=(26.0, 7.4, 4.0), natoms=5, pset=synth.PSET_SPD2, nb=3,
+                         cplx=False),
 }
 
 
