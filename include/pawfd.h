@@ -108,6 +108,9 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *                     digit slices; 0: FP64 / FP32 FMA kernels on the CUDA cores.
  *   "stencil_variant" 0 (default): fastest kernel that applies to the shape; 1: skip the
  *                     bulk-copy ring kernel; 2: always the general kernel.
+ *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,
+ *                     at most 64 (clamped further by the kernel's thread and memory limits).
+ *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
  * Returns PAWFD_EINVAL for an unknown name or value. */
 int pawfd_set_option(pawfd_ctx* ctx, const char* name, int value);
 

@@ -364,6 +364,14 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->fast_stencil = value != 2;
     return PAWFD_OK;
   }
+  if (n == "stencil_rows" && value >= 0 && value <= 64) {
+    c->stencil_rows = value;
+    return PAWFD_OK;
+  }
+  if (n == "stencil_yblock" && value >= 0 && value <= 3) {
+    c->stencil_yblock = value;
+    return PAWFD_OK;
+  }
   return fail(c, PAWFD_EINVAL, "unknown option or value");
 }
 

@@ -184,6 +184,8 @@ struct pawfd_ctx {
   bool use_tc = true;                         // Gram matrices on the tensor cores (sliced digits)
   bool fast_stencil = true;                   // shape-specialised stencil kernels where they apply
   int stencil_variant = 0;                    // 0: ring (bulk copies) first, 1: register float4 kernel
+  int stencil_rows = 0;                       // y rows per CTA of the ring kernel (0: automatic)
+  int stencil_yblock = 0;                     // y rows per thread of the ring kernel (0: automatic)
   pawfd::TcScratch tc;
   std::string err;
 };

@@ -35,18 +35,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Wait until the phase of the given parity has completed; false after WAIT_NS.
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// Wait until the phase of the given parity has completed; false after WAIT_NS.  The timer is
+// read only once the first try_wait has failed, so a phase that has already completed costs
+// one instruction.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_addr(bar);
+  if (mbar_try_wait(a, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try_wait(a, parity)) return true;
     if (now_ns() - t0 > WAIT_NS) return false;
   }
 }
