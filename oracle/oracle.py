@@ -251,3 +251,36 @@ def rayleigh_ritz(system, psi: np.ndarray) -> dict:
     psi_rot = rotate(psi, C)
     return {"Hpsi": Hpsi, "Spsi": Spsi, "P": P, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "sweeps": sweeps,
             "psi_rot": psi_rot}
+
+
+def residual_norms(Hpsi: np.ndarray, Spsi: np.ndarray, eps: np.ndarray, dV: float) -> np.ndarray:
+    """||r_n|| = sqrt(dV sum_r |(H psi)_n(r) - eps_n (S psi)_n(r)|^2) for every band n.
+
+    The residual of the generalized eigenproblem H psi = eps S psi of the PAW section, the
+    quantity an iterative eigensolver drives to zero (Kohn-Sham section, step 1)."""
+    nb = len(eps)
+    r = Hpsi.reshape(nb, -1) - np.asarray(eps, np.float64)[:, None] * Spsi.reshape(nb, -1)
+    return np.sqrt(dV * np.sum(np.abs(r) ** 2, axis=1))
+
+
+def refine(system, psi_lo: np.ndarray) -> dict:
+    """Final refinement of the mixed form, in the order of its reading (the paper is silent):
+
+    1. the FP32 / complex64 bands psi' are promoted to FP64 (exactly);
+    2. H psi' and S psi' are applied in FP64 (Eq. (dh) and the overlap operator);
+    3. FP64 Gram matrices H'_nm, S'_nm are formed;
+    4. the Rayleigh quotients theta_n = H'_nn / S'_nn are taken from their diagonals;
+    5. a second FP64 subspace diagonalization gives the refined eps (ascending) and C;
+    6. the residual norms ||H psi'_n - eps_n S psi'_n|| are reported.
+    """
+    psi = np.asarray(psi_lo).astype(np.complex128 if system.complex_wf else np.float64)
+    psi, nb = _psi_in(system, psi)
+    Hpsi, P = apply_H(system, psi)
+    Spsi, _ = apply_S(system, psi)
+    Hnm = gram(psi, Hpsi, system.dV, nb)
+    Snm = gram(psi, Spsi, system.dV, nb)
+    theta = np.real(np.diag(Hnm)) / np.real(np.diag(Snm))
+    eps, C, sweeps = subspace_diag(Hnm, Snm)
+    resid = residual_norms(Hpsi, Spsi, eps, system.dV)
+    return {"psi": psi, "Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "theta": theta, "eps": eps, "C": C,
+            "resid": resid}

@@ -467,3 +467,63 @@ def test_projector_functions_orthonormal():
     p = synth.projector_values(pset, x, y, z).reshape(pset.count, -1)
     ov = h ** 3 * p @ p.T
     assert np.allclose(ov, np.eye(pset.count), rtol=0, atol=2e-3)
+
+
+# ------------------------------------------------------------------------------------------
+# Final refinement of the mixed form (residual norms, Rayleigh quotients, second RR)
+# ------------------------------------------------------------------------------------------
+
+def test_refine_exact_eigenvectors_have_zero_residual():
+    # real plane waves cos(G.r) of a free system are exact eigenvectors (I1): the refinement
+    # returns their closed-form eigenvalues as eps and theta, and residuals at rounding level
+    s = free_system((10, 9, 8), (5.0, 4.6, 4.1))
+    x, y, z = grid_coords(s)
+    V = s.cell[0] * s.cell[1] * s.cell[2]
+    js = [(1, 0, 0), (0, 1, 1), (2, -1, 0), (1, 2, 3)]
+    psi, lams = [], []
+    for j in js:
+        q = [2 * math.pi * j[c] / s.cell[c] for c in range(3)]
+        psi.append(np.sqrt(2.0 / V) * np.cos(q[0] * x + q[1] * y + q[2] * z))
+        lams.append(plane_wave_eigenvalue(s, q))
+    order = np.argsort(lams)
+    psi = np.array(psi)[order]
+    lams = np.array(lams)[order]
+    res = O.refine(s, psi)
+    assert np.allclose(res["eps"], lams, rtol=0, atol=1e-11)
+    assert np.allclose(res["theta"], lams, rtol=0, atol=1e-11)
+    assert np.all(res["resid"] <= 1e-11 * lams.max())
+
+
+def test_refine_residual_of_mixed_plane_waves():
+    # psi_1,2 = (w_a +- w_b)/sqrt(2) for orthonormal eigenvectors w_a, w_b with eigenvalues
+    # l_a < l_b: both Rayleigh quotients are (l_a + l_b)/2, the second RR recovers l_a, l_b,
+    # and the residuals taken with eps_n are |l_b - l_a|/sqrt(2) for both bands
+    s = free_system((12, 10, 9), (6.0, 5.0, 4.5))
+    x, y, z = grid_coords(s)
+    V = s.cell[0] * s.cell[1] * s.cell[2]
+    qa = [2 * math.pi * j / s.cell[c] for c, j in enumerate((1, 0, 0))]
+    qb = [2 * math.pi * j / s.cell[c] for c, j in enumerate((1, 2, -1))]
+    wa = np.sqrt(2.0 / V) * np.cos(qa[0] * x + qa[1] * y + qa[2] * z)
+    wb = np.sqrt(2.0 / V) * np.cos(qb[0] * x + qb[1] * y + qb[2] * z)
+    la, lb = plane_wave_eigenvalue(s, qa), plane_wave_eigenvalue(s, qb)
+    assert la < lb
+    psi = np.array([(wa + wb) / np.sqrt(2.0), (wa - wb) / np.sqrt(2.0)])
+    res = O.refine(s, psi)
+    assert np.allclose(res["theta"], [(la + lb) / 2] * 2, rtol=0, atol=1e-11)
+    assert np.allclose(res["eps"], [la, lb], rtol=0, atol=1e-11)
+    assert np.allclose(res["resid"], [(lb - la) / np.sqrt(2.0)] * 2, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("complex_wf", [False, True])
+def test_refine_of_ritz_vectors_is_a_fixed_point(complex_wf):
+    # a second RR on the (FP64) Ritz vectors of a first one reproduces its eigenvalues, and each
+    # Rayleigh quotient equals its eigenvalue (the Ritz vectors diagonalize the projected pencil)
+    s = small_system(complex_wf=complex_wf)
+    first = O.rayleigh_ritz(s, rand_psi(s, 6, 21))
+    res = O.refine(s, first["psi_rot"])
+    assert np.allclose(res["eps"], first["eps"], rtol=0, atol=1e-11)
+    assert np.allclose(res["theta"], first["eps"], rtol=0, atol=1e-11)
+    # residual norms are those of the Ritz pairs: check one against the definition via H, S
+    n = 3
+    r = res["Hpsi"][n] - first["eps"][n] * res["Spsi"][n]
+    assert abs(res["resid"][n] - math.sqrt(s.dV) * np.linalg.norm(r)) <= 1e-12 * res["resid"][n]
