@@ -155,9 +155,30 @@ int pawfd_subspace_diag(pawfd_ctx* ctx, int nb, void* Hnm, void* Snm, double* ep
 
 /* Band rotation psi_out_m = sum_n psi_n C[n][m] (the rotation that completes the subspace
  * diagonalization).  psi, psi_out: [nb][K] of the context's dtype; C: [nb][nb] FP64 (as
- * returned by pawfd_subspace_diag; the FP32 dtypes round it to FP32 and accumulate in FP32);
- * psi_out must not alias psi. */
+ * returned by pawfd_subspace_diag); psi_out must not alias psi.  With the tensor-core path
+ * (the default) psi and C enter as exact sums of scaled BF16 digits (all 53 / 24 bits of
+ * psi, C to at least 26 bits for the FP32 dtypes) and each output is accumulated to about
+ * FP64 accuracy before the final rounding to the context's dtype. */
 int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* psi_out);
+
+/* Final refinement of the mixed form (the paper is silent on it; this is the reading that
+ * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
+ * PAWFD_C128) of the same system as the mixed context whose rotated bands psi_lo (PAWFD_R32
+ * or PAWFD_C64 of the same kind, [nb][K], 16-byte aligned) are refined:
+ *   1. psi = psi_lo promoted to FP64 (exact);
+ *   2. hpsi = H psi and spsi = S psi in FP64 (Eq. (dh) and the overlap operator of the PAW
+ *      section; one set of projections serves both);
+ *   3. Hnm = dV psi^H hpsi, Snm = dV psi^H spsi (Hermitian Gram matrices, FP64);
+ *   4. theta[n] = Re Hnm[n][n] / Re Snm[n][n] (FP64 Rayleigh quotients of the bands psi_lo);
+ *   5. a second subspace diagonalization of (Hnm, Snm) gives eps (ascending) and C, as
+ *      pawfd_subspace_diag (Hnm and Snm are overwritten);
+ *   6. resid[n] = sqrt(dV sum_r |hpsi_n(r) - eps[n] spsi_n(r)|^2).
+ * psi, hpsi, spsi: caller-owned FP64 device work arrays [nb][K] (on return they hold steps
+ * 1-2); Hnm, Snm, C: [nb][nb] of the context's kind; eps, theta, resid: device [nb] doubles.
+ * Returns PAWFD_EINVAL for a mixed context, nb outside 1..max_bands, null or aliased arrays,
+ * or misaligned band arrays; device-side failures of step 5 are reported by pawfd_sync. */
+int pawfd_refine(pawfd_ctx* ctx, const void* psi_lo, int nb, void* psi, void* hpsi, void* spsi, void* Hnm,
+                 void* Snm, double* eps, double* theta, double* resid, void* C);
 
 /* Gram matrix for callers that cannot allocate device memory.
  *

@@ -43,6 +43,7 @@ SIGNATURES = {
     "pawfd_gram_hermitian": ([VP, VP, VP, I, VP], I),
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
+    "pawfd_refine": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
     "pawfd_gram_noalloc": ([VP, VP, ctypes.c_longlong, I, I, D, VP, VP], I),
 }
 

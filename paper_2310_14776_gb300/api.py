@@ -195,6 +195,38 @@ class Context:
         psi_rot = self.rotate(psi, C, out=w.get("psi_rot"))
         return {"Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}
 
+    def refine(self, psi_lo, work: Optional[dict] = None, check: bool = True) -> dict:
+        """Final refinement of mixed-form bands on this FP64 context (pawfd_refine): FP64
+        H psi', S psi', Gram matrices, Rayleigh quotients ``theta``, a second subspace solve
+        (``eps``, ``C``) and residual norms ``resid``.  ``psi_lo`` is the float32 / complex64
+        output of a mixed context of the same system."""
+        if self.precision != "fp64":
+            raise ValueError("refine runs on an fp64 context")
+        lo = torch.complex64 if self.complex else torch.float32
+        if psi_lo.device != self.device or psi_lo.dtype != lo or not psi_lo.is_contiguous():
+            raise ValueError("psi_lo must be a contiguous %s tensor on %s" % (lo, self.device))
+        if psi_lo.numel() % self.K:
+            raise ValueError("psi_lo size is not a multiple of the grid size")
+        nb = psi_lo.numel() // self.K
+        w = work if work is not None else {}
+        out = {}
+        for key in ("psi", "Hpsi", "Spsi"):
+            out[key] = w.get(key) if w.get(key) is not None else self.empty_bands(nb)
+            self._bands(out[key], key)
+        for key in ("Hnm", "Snm", "C"):
+            out[key] = w.get(key) if w.get(key) is not None else torch.empty((nb, nb), dtype=self.mat_dtype,
+                                                                             device=self.device)
+            self._mat(out[key], nb, key)
+        for key in ("eps", "theta", "resid"):
+            out[key] = w.get(key) if w.get(key) is not None else torch.empty(nb, dtype=torch.float64,
+                                                                             device=self.device)
+        p = lambda t: ctypes.c_void_p(t.data_ptr())
+        self._call(self.lib.pawfd_refine, p(psi_lo), nb, p(out["psi"]), p(out["Hpsi"]), p(out["Spsi"]),
+                   p(out["Hnm"]), p(out["Snm"]), p(out["eps"]), p(out["theta"]), p(out["resid"]), p(out["C"]))
+        if check:
+            self.sync()
+        return out
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self.lib.pawfd_destroy(self._h)
