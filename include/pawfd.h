@@ -111,6 +111,9 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,
  *                     at most 64 (clamped further by the kernel's thread and memory limits).
  *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
+ *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
+ *                     cooperative grids with a bounded software grid barrier; 1: on one
+ *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
  * Returns PAWFD_EINVAL for an unknown name or value. */
 int pawfd_set_option(pawfd_ctx* ctx, const char* name, int value);
 

@@ -316,7 +316,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     c->d_evals = dev_alloc<double>(c, nb, &rc);
     c->d_barrier = dev_alloc<unsigned>(c, 4, &rc);
     c->d_status = dev_alloc<DeviceStatus>(c, 1, &rc);
-    c->d_reduce = dev_alloc<double>(c, 4096, &rc);
+    c->d_reduce = dev_alloc<double>(c, 8192, &rc);   // [0, 2048): partial sums; then Jacobi round flags
   }
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMallocHost(&c->h_status, sizeof(DeviceStatus)), "cudaMallocHost");
   if (rc == PAWFD_OK && c->use_tc) rc = setup_tc(c);
@@ -366,6 +366,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
   }
   if (n == "stencil_rows" && value >= 0 && value <= 64) {
     c->stencil_rows = value;
+    return PAWFD_OK;
+  }
+  if (n == "jacobi_cluster" && (value == 0 || value == 1)) {
+    c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
   if (n == "stencil_yblock" && value >= 0 && value <= 3) {

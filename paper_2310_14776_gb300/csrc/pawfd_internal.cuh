@@ -178,7 +178,7 @@ struct pawfd_ctx {
   unsigned* d_barrier = nullptr;              // grid-barrier counters
   pawfd::DeviceStatus* d_status = nullptr;
   pawfd::DeviceStatus* h_status = nullptr;    // pinned mirror
-  double* d_reduce = nullptr;                 // [max grid] partial sums for in-kernel reductions
+  double* d_reduce = nullptr;                 // [8192]: in-kernel partial sums, Jacobi round flags
   int num_sms = 0;
   long long launches = 0;                     // kernels this context has launched
   bool use_tc = true;                         // Gram matrices on the tensor cores (sliced digits)
@@ -186,6 +186,7 @@ struct pawfd_ctx {
   int stencil_variant = 0;                    // 0: ring (bulk copies) first, 1: register float4 kernel
   int stencil_rows = 0;                       // y rows per CTA of the ring kernel (0: automatic)
   int stencil_yblock = 0;                     // y rows per thread of the ring kernel (0: automatic)
+  bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   pawfd::TcScratch tc;
   std::string err;
 };

@@ -65,6 +65,25 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, DeviceStatus* st, 
   return s_ok != 0;
 }
 
+// Cluster-wide barrier (hardware).  Every CTA of the cluster reaches every call: the callers'
+// control flow depends only on values that all CTAs compute identically.  The fence makes
+// this CTA's global-memory writes visible before the arrive; readers use L2-only loads.
+__device__ __forceinline__ void cluster_barrier() {
+  __threadfence();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// MODE 0: cooperative grid launch, software grid barrier (bounded); MODE 1: one thread-block
+// cluster, hardware cluster barrier.  Returns false if the kernel must stop.
+template <int MODE>
+__device__ __forceinline__ bool all_barrier(unsigned* bar, unsigned nblocks, DeviceStatus* st, int id) {
+  if (MODE == 1) {
+    cluster_barrier();
+    return true;
+  }
+  return grid_barrier(bar, nblocks, st, id);
+}
+
 // L2-only loads: data written by other CTAs of the same launch must not come from a stale L1
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ zd ldcg(const zd* p) {
@@ -83,46 +102,100 @@ __global__ void symmetrize_kernel(const T* __restrict__ H, const T* __restrict__
   Ss[e] = 0.5 * (S[e] + conjx(S[t]));
 }
 
-// Right-looking Cholesky of the lower triangle of S (in place, one CTA).  Strict upper zeroed.
-template <class T>
-__global__ void __launch_bounds__(1024) cholesky_kernel(T* __restrict__ S, int n, DeviceStatus* st) {
+// ------------------------------------------------------------------------------------------
+// Blocked right-looking Cholesky S = L L^H of the lower triangle (in place; strict upper
+// zeroed), Golub & Van Loan's outer-product form by panels of CH_NB columns:
+//   (a) every CTA loads the panel's diagonal block and factors it with one warp in shared
+//       memory (identical arithmetic in every CTA, so every CTA takes the same decision on a
+//       pivot <= 0; CTA 0 writes the block back);
+//   (b) the rows below solve x L11^H = a, one warp per row;
+//   (c) the trailing lower triangle is updated, S22 -= L21 L21^H.
+// Two all-CTA barriers per panel.
+// ------------------------------------------------------------------------------------------
+constexpr int CH_NB = 32;
+constexpr int CH_NT = 512;
+
+__device__ __forceinline__ double shfl_x(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ zd shfl_x(zd v, int src) {
+  return zd{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(CH_NT) cholesky_kernel(T* __restrict__ S, int n, unsigned* bar, DeviceStatus* st) {
+  __shared__ T L11[CH_NB][CH_NB + 1];
+  __shared__ double inv_d[CH_NB];
   __shared__ int s_fail;
-  __shared__ double s_ljj;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) s_fail = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const double d = realx(S[(long long)j * n + j]);
-      if (!(d > 0.0)) {
-        s_fail = 1;
-        set_status(st, PAWFD_ENOTPD, j);
-      } else {
-        s_ljj = sqrt(d);
-        S[(long long)j * n + j] = from_real<T>(s_ljj);
+  const unsigned G = gridDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int gthreads = (int)G * CH_NT, gtid = (int)blockIdx.x * CH_NT + tid;
+  if (ld_volatile(&st->code) != 0) return;   // uniform: set before this launch
+  for (int k0 = 0; k0 < n; k0 += CH_NB) {
+    const int nb = min(CH_NB, n - k0);
+    // (a) diagonal block
+    for (int e = tid; e < nb * nb; e += CH_NT) L11[e / nb][e % nb] = ldcg(S + (long long)(k0 + e / nb) * n + k0 + e % nb);
+    __syncthreads();
+    if (warp == 0) {
+      int fail = -1;
+      for (int j = 0; j < nb; ++j) {
+        const double d = realx(L11[j][j]);
+        if (!(d > 0.0)) {
+          fail = j;
+          break;
+        }
+        const double ljj = sqrt(d), inv = 1.0 / ljj;
+        __syncwarp();
+        if (lane == j) {
+          L11[j][j] = from_real<T>(ljj);
+          inv_d[j] = inv;
+        }
+        if (lane > j && lane < nb) L11[lane][j] = inv * L11[lane][j];
+        __syncwarp();
+        if (lane > j && lane < nb) {
+          const T lij = L11[lane][j];
+          for (int k = j + 1; k <= lane; ++k) L11[lane][k] -= lij * conjx(L11[k][j]);
+        }
+        __syncwarp();
       }
+      if (lane == 0) s_fail = fail;
     }
     __syncthreads();
-    if (s_fail) return;
-    const double inv = 1.0 / s_ljj;
-    for (int i = j + 1 + tid; i < n; i += nt) S[(long long)i * n + j] = inv * S[(long long)i * n + j];
-    __syncthreads();
-    const int m = n - j - 1;
-    for (long long e = tid; e < (long long)m * m; e += nt) {
-      const int r = (int)(e / m), q = (int)(e % m);
+    if (s_fail >= 0) {
+      if (blockIdx.x == 0 && tid == 0) set_status(st, PAWFD_ENOTPD, k0 + s_fail);
+      return;
+    }
+    // (b) rows below the block, one warp per row: x_j = (a_j - sum_{l<j} x_l conj(L_jl)) / L_jj
+    const int m = n - k0 - nb;
+    for (int r = (int)blockIdx.x * (CH_NT / 32) + warp; r < m; r += (int)G * (CH_NT / 32)) {
+      const long long row = (long long)(k0 + nb + r) * n + k0;
+      const T a = lane < nb ? ldcg(S + row + lane) : zero<T>();
+      T sacc = zero<T>(), x = zero<T>();
+      for (int j = 0; j < nb; ++j) {
+        const T xj = shfl_x(inv_d[j] * (a - sacc), j);
+        if (lane == j) x = xj;
+        if (lane > j && lane < nb) sacc += xj * conjx(L11[lane][j]);
+      }
+      if (lane < nb) S[row + lane] = x;
+    }
+    if (!all_barrier<MODE>(bar, G, st, 700)) return;
+    // every CTA has read the unfactored diagonal block: CTA 0 writes the factor back
+    if (blockIdx.x == 0)
+      for (int e = tid; e < nb * nb; e += CH_NT) {
+        const int i = e / nb, k = e % nb;
+        S[(long long)(k0 + i) * n + k0 + k] = k <= i ? L11[i][k] : zero<T>();
+      }
+    // (c) trailing lower triangle
+    for (int e = gtid; e < m * m; e += gthreads) {
+      const int r = e / m, q = e - r * m;
       if (q > r) continue;
-      const int i = j + 1 + r, k = j + 1 + q;
-      T v = S[(long long)i * n + k];
-      const T lij = S[(long long)i * n + j], lkj = S[(long long)k * n + j];
-      v -= lij * conjx(lkj);
-      S[(long long)i * n + k] = v;
+      const long long i = k0 + nb + r, k = k0 + nb + q;
+      T acc = ldcg(S + i * n + k);
+      for (int j = 0; j < nb; ++j) acc -= ldcg(S + i * n + k0 + j) * conjx(ldcg(S + k * n + k0 + j));
+      S[i * n + k] = acc;
     }
-    __syncthreads();
+    if (!all_barrier<MODE>(bar, G, st, 701)) return;
   }
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = (int)(e / n), k = (int)(e % n);
-    if (k > i) S[e] = zero<T>();
-  }
+  for (int e = gtid; e < n * n; e += gthreads)
+    if (e % n > e / n) S[e] = zero<T>();
 }
 
 // Linv column j = L^-1 e_j by forward substitution (one CTA per column).
@@ -145,15 +218,22 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const T* __restrict__ 
   for (int k = tid; k < n; k += blockDim.x) Linv[(long long)k * n + j] = x[k];
 }
 
-// C = op(A) op(B), n x n, op = identity or conjugate transpose
+// C = op(A) op(B) (+ D), n x n, op = identity or conjugate transpose.  With `skip` set on the
+// device, C is a copy of `src` instead (the product is known to be that matrix).
 template <class T>
 __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A, bool ha, const T* __restrict__ B,
-                                                         bool hb, int n, T* __restrict__ C, const DeviceStatus* st) {
+                                                         bool hb, int n, T* __restrict__ C, const DeviceStatus* st,
+                                                         const T* __restrict__ D = nullptr,
+                                                         const int* skip = nullptr, const T* __restrict__ src = nullptr) {
   __shared__ T As[16][17];
   __shared__ T Bs[16][17];
   if (ld_volatile(&st->code) != 0) return;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  if (skip && ld_volatile(skip)) {
+    if (row < n && col < n) C[(long long)row * n + col] = src[(long long)row * n + col];
+    return;
+  }
   T acc = zero<T>();
   for (int k0 = 0; k0 < n; k0 += 16) {
     {
@@ -171,7 +251,7 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A
     for (int k = 0; k < 16; ++k) fma_plain(acc, As[ty][k], Bs[k][tx]);
     __syncthreads();
   }
-  if (row < n && col < n) C[(long long)row * n + col] = acc;
+  if (row < n && col < n) C[(long long)row * n + col] = D ? acc + D[(long long)row * n + col] : acc;
 }
 
 template <class T>
@@ -202,12 +282,54 @@ __device__ __forceinline__ zd phase_of(zd apq, double mag) { return zd{apq.re / 
 __device__ __forceinline__ double absx(double x) { return fabs(x); }
 __device__ __forceinline__ double absx(zd x) { return hypot(x.re, x.im); }
 
+// Jacobi rotation of the pair (p, q) (p < q) that annihilates a_pq of a Hermitian matrix
+template <class T>
+__device__ __forceinline__ Rot make_rot(int p, int q, T apq, double app, double aqq) {
+  Rot R;
+  R.c = 1.0; R.s = 0.0; R.e = zd{1.0, 0.0}; R.p = p; R.q = q;
+  const double mag = absx(apq);
+  if (mag > 0.0) {
+    const double tau = (aqq - app) / (2.0 * mag);
+    const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+    R.c = 1.0 / sqrt(1.0 + t * t);
+    R.s = t * R.c;
+    R.e = phase_of(apq, mag);
+  }
+  return R;
+}
+
+// A'[P,Q] = J_P^H A[P,Q] J_Q on one 2x2 block with J = [[c, s], [-s e, c e]] on (p, q);
+// a diagonal block (P == Q) comes out exactly diagonal with a real diagonal
+template <class T>
+__device__ __forceinline__ void rotate_block(const Rot& rp, const Rot& rq, bool diag, T& b00, T& b01, T& b10,
+                                             T& b11) {
+  if (rq.q >= 0) {
+    const T x0 = rq.c * b00 - rq.s * mul_e(b01, rq.e);
+    const T x1 = rq.s * b00 + rq.c * mul_e(b01, rq.e);
+    const T y0 = rq.c * b10 - rq.s * mul_e(b11, rq.e);
+    const T y1 = rq.s * b10 + rq.c * mul_e(b11, rq.e);
+    b00 = x0; b01 = x1; b10 = y0; b11 = y1;
+  }
+  if (rp.q >= 0) {
+    const T x0 = rp.c * b00 - rp.s * mul_ce(b10, rp.e);
+    const T y0 = rp.s * b00 + rp.c * mul_ce(b10, rp.e);
+    const T x1 = rp.c * b01 - rp.s * mul_ce(b11, rp.e);
+    const T y1 = rp.s * b01 + rp.c * mul_ce(b11, rp.e);
+    b00 = x0; b10 = y0; b01 = x1; b11 = y1;
+  }
+  if (diag && rp.q >= 0) {
+    b01 = zero<T>();
+    b10 = zero<T>();
+    b00 = from_real<T>(realx(b00));
+    b11 = from_real<T>(realx(b11));
+  }
+}
+
 // player at position pos of round r of the circle (round-robin) schedule over npad players
 __device__ __forceinline__ int rr_player(int pos, int r, int npad) {
   return pos == 0 ? 0 : ((pos - 1 + r) % (npad - 1)) + 1;
 }
 
-template <class T>
 __device__ double block_reduce_sum(double v, double* s_red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -220,12 +342,95 @@ __device__ double block_reduce_sum(double v, double* s_red) {
   return s;   // valid in thread 0
 }
 
+// One step of the Ogita-Aishima refinement of an approximate eigenvector basis X of the
+// Hermitian A (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
+// 2018): with S = X^H A X, R = I - X^H X, lambda_i = Re s_ii / (1 - Re r_ii),
+//   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)  for |lambda_j - lambda_i| > delta,
+//   e_ij = r_ij / 2                                          otherwise (and e_ii = r_ii / 2),
+// X' = X + X E is orthonormal and diagonalizes A to second order in the error of X.  delta =
+// 2 (||S - diag S||_F + ||S||_F ||R||_F) separates clusters; their coupling is left to the
+// Jacobi sweeps, and so is every pair whose |e_ij| would exceed 1e-4 in the first step or
+// 1e-7 in a later one (a first-order correction made only in the second step would leave a
+// non-orthogonality of its square).  XtX = null means X = I (R = 0, S = A).  In the first step (XtX = null) *skip is
+// set when S is already diagonal to tol or when more than 2n coupled pairs would be left (far
+// from diagonal); every later step and product then copies instead.  One CTA.
+template <class T>
+__global__ void __launch_bounds__(1024) refine_step_kernel(const T* __restrict__ S, const T* __restrict__ XtX, int n,
+                                                          T* __restrict__ E, int* skip, double tol,
+                                                          const DeviceStatus* st) {
+  __shared__ double s_red[32];
+  __shared__ double s_v[3];
+  if (ld_volatile(&st->code) != 0) return;
+  if (XtX && ld_volatile(skip)) return;
+  const int tid = threadIdx.x;
+  const int nn = n * n;
+  auto r_of = [&](int e) -> T {   // R = I - X^H X
+    if (!XtX) return zero<T>();
+    return from_real<T>(e / n == e % n ? 1.0 : 0.0) - XtX[e];
+  };
+  double off2 = 0.0, fro2 = 0.0, r2 = 0.0;
+  for (int e = tid; e < nn; e += blockDim.x) {
+    const double a2 = absx2(S[e]);
+    fro2 += a2;
+    if (e / n != e % n) off2 += a2;
+    r2 += absx2(r_of(e));
+  }
+  off2 = block_reduce_sum(off2, s_red);
+  if (tid == 0) s_v[0] = off2;
+  fro2 = block_reduce_sum(fro2, s_red);
+  if (tid == 0) s_v[1] = fro2;
+  r2 = block_reduce_sum(r2, s_red);
+  if (tid == 0) s_v[2] = r2;
+  __syncthreads();
+  off2 = s_v[0];
+  fro2 = s_v[1];
+  r2 = s_v[2];
+  if (!XtX && off2 <= tol * tol * fro2) {
+    if (tid == 0) *skip = 1;
+    return;
+  }
+  const double delta = fmax(2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
+  const double thr2 = tol * tol * fro2 / ((double)n * n);   // a coupling the Jacobi would rotate
+  auto lam = [&](int i) -> double {
+    const int d = i * n + i;
+    return realx(S[d]) / (1.0 - realx(r_of(d)));
+  };
+  double coupled = 0.0;   // pairs left to the Jacobi sweeps with a coupling above threshold
+  for (int e = tid; e < nn; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    T v = 0.5 * r_of(e);
+    if (i != j) {
+      const double li = lam(i), lj = lam(j);
+      bool cluster = fabs(lj - li) <= delta;
+      if (!cluster) {
+        const T w = (1.0 / (lj - li)) * (S[e] + lj * r_of(e));
+        // first step: |e_ij| <= 1e-4; later steps take only corrections that are already of
+        // second order (<= 1e-7), so that the orthogonality error they leave is O(1e-14)
+        if (absx2(w) <= (XtX ? 1e-14 : 1e-8)) v = w;
+        else cluster = true;
+      }
+      if (cluster && absx2(S[e]) > thr2) coupled += 1.0;
+    }
+    E[e] = v;
+  }
+  coupled = block_reduce_sum(coupled, s_red);
+  // too many coupled pairs: the matrix is far from diagonal, leave it all to the Jacobi sweeps
+  if (tid == 0 && !XtX) *skip = coupled > 2.0 * n ? 1 : 0;
+}
+
+template <class T>
+__global__ void identity_kernel(T* __restrict__ X, int n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n * n) X[e] = from_real<T>((e / n) == (e % n) ? 1.0 : 0.0);
+}
+
 // sum over all CTAs of per-CTA partials, identical (same order) in every CTA
+template <int MODE>
 __device__ double grid_sum(double mine, double* red, double* s_red, double* s_bcast, unsigned* bar, unsigned G,
                            DeviceStatus* st, int id, bool* ok) {
-  const double b = block_reduce_sum<double>(mine, s_red);
+  const double b = block_reduce_sum(mine, s_red);
   if (threadIdx.x == 0) red[blockIdx.x] = b;
-  if (!grid_barrier(bar, G, st, id)) {
+  if (!all_barrier<MODE>(bar, G, st, id)) {
     *ok = false;
     return 0.0;
   }
@@ -237,14 +442,15 @@ __device__ double grid_sum(double mine, double* red, double* s_red, double* s_bc
   __syncthreads();
   const double s = *s_bcast;
   // everyone has read red[] before anyone may overwrite it in the next reduction
-  if (!grid_barrier(bar, G, st, id + 1)) *ok = false;
+  if (!all_barrier<MODE>(bar, G, st, id + 1)) *ok = false;
   return s;
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) jacobi_kernel(T* __restrict__ A0, T* __restrict__ A1, T* __restrict__ V,
-                                                     int n, double tol, int max_sweeps, unsigned* bar,
-                                                     DeviceStatus* st, double* red) {
+template <class T, int MODE>
+__global__ void __launch_bounds__(MODE == 1 ? 1024 : 256)
+    jacobi_kernel(T* __restrict__ A0, T* __restrict__ A1, T* __restrict__ V, int n, double tol, int max_sweeps,
+                  unsigned* bar, DeviceStatus* st, double* red) {
+  // V holds the caller's starting basis; the rotations accumulate onto it
   extern __shared__ unsigned char smem_raw[];
   Rot* rot = (Rot*)smem_raw;
   __shared__ double s_red[32];
@@ -261,20 +467,26 @@ __global__ void __launch_bounds__(256) jacobi_kernel(T* __restrict__ A0, T* __re
   T* Anext = A1;
   if (ld_volatile(&st->code) != 0) return;   // an earlier step (Cholesky) failed
 
-  // V = I
-  for (long long e = gtid; e < (long long)n * n; e += gthreads) V[e] = from_real<T>((e / n) == (e % n) ? 1.0 : 0.0);
 
   double fro2 = 0.0;
   for (long long e = gtid; e < (long long)n * n; e += gthreads) fro2 += absx2(ldcg(A + e));
-  fro2 = grid_sum(fro2, red, s_red, &s_bcast, bar, G, st, 1, &ok);
+  fro2 = grid_sum<MODE>(fro2, red, s_red, &s_bcast, bar, G, st, 1, &ok);
   if (!ok) return;
   const double limit2 = tol * tol * fro2;
 
+  // Threshold Jacobi: a pair is rotated only if |a_pq|^2 > thr2 (all off-diagonal entries at
+  // that level would add up to the convergence limit), and a round whose pairs all fall below
+  // it at the start of the sweep is skipped without a barrier.
+  // The flags alternate between two arrays by sweep: a CTA may still read the flags of the
+  // last rounds of sweep s while another clears those of sweep s + 1 (no barrier between them).
+  const double thr2 = limit2 / ((double)n * n);
   for (int sweep = 0;; ++sweep) {
+    unsigned* rflag = (unsigned*)(red + 2048) + (sweep & 1) * 3072;
+    for (long long e = gtid; e < npad - 1; e += gthreads) rflag[e] = 0u;
     double off2 = 0.0;
     for (long long e = gtid; e < (long long)n * n; e += gthreads)
       if ((e / n) != (e % n)) off2 += absx2(ldcg(A + e));
-    off2 = grid_sum(off2, red, s_red, &s_bcast, bar, G, st, 3, &ok);
+    off2 = grid_sum<MODE>(off2, red, s_red, &s_bcast, bar, G, st, 3, &ok);
     if (!ok) return;
     if (off2 <= limit2 || sweep == max_sweeps) {
       if (off2 > limit2 && blockIdx.x == 0 && threadIdx.x == 0) set_status(st, PAWFD_ENOCONV, max_sweeps);
@@ -282,26 +494,27 @@ __global__ void __launch_bounds__(256) jacobi_kernel(T* __restrict__ A0, T* __re
         for (long long e = gtid; e < (long long)n * n; e += gthreads) A0[e] = ldcg(A + e);
       return;
     }
+    for (long long w = gtid; w < (long long)(npad - 1) * np; w += gthreads) {
+      const int r = (int)(w / np), k = (int)(w % np);
+      int p = rr_player(k, r, npad), q = rr_player(npad - 1 - k, r, npad);
+      if (p > q) { const int t = p; p = q; q = t; }
+      if (q < n && absx2(ldcg(A + (long long)p * n + q)) > thr2) rflag[r] = 1u;
+    }
+    if (!all_barrier<MODE>(bar, G, st, 5)) return;
     for (int r = 0; r < npad - 1; ++r) {
+      if (__ldcg(rflag + r) == 0u) continue;   // identical in every CTA
       // rotation parameters of this round's n/2 disjoint pairs, computed by every CTA
       for (int k = threadIdx.x; k < np; k += blockDim.x) {
         int p = rr_player(k, r, npad), q = rr_player(npad - 1 - k, r, npad);
         if (p > q) { const int t = p; p = q; q = t; }
         Rot R;
-        R.c = 1.0; R.s = 0.0; R.e = zd{1.0, 0.0}; R.p = p; R.q = q;
+        const T apq = q < n ? ldcg(A + (long long)p * n + q) : zero<T>();
         if (q >= n) {
-          R.q = -1;
+          R.c = 1.0; R.s = 0.0; R.e = zd{1.0, 0.0}; R.p = p; R.q = -1;
+        } else if (absx2(apq) <= thr2) {
+          R.c = 1.0; R.s = 0.0; R.e = zd{1.0, 0.0}; R.p = p; R.q = q;
         } else {
-          const T apq = ldcg(A + (long long)p * n + q);
-          const double mag = absx(apq);
-          if (mag > 0.0) {
-            const double app = realx(ldcg(A + (long long)p * n + p)), aqq = realx(ldcg(A + (long long)q * n + q));
-            const double tau = (aqq - app) / (2.0 * mag);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            R.c = 1.0 / sqrt(1.0 + t * t);
-            R.s = t * R.c;
-            R.e = phase_of(apq, mag);
-          }
+          R = make_rot<T>(p, q, apq, realx(ldcg(A + (long long)p * n + p)), realx(ldcg(A + (long long)q * n + q)));
         }
         rot[k] = R;
       }
@@ -315,28 +528,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(T* __restrict__ A0, T* __re
         T b01 = j1 >= 0 ? ldcg(A + (long long)i0 * n + j1) : zero<T>();
         T b10 = i1 >= 0 ? ldcg(A + (long long)i1 * n + j0) : zero<T>();
         T b11 = (i1 >= 0 && j1 >= 0) ? ldcg(A + (long long)i1 * n + j1) : zero<T>();
-        // columns: B J_Q
-        if (j1 >= 0) {
-          const T x0 = rq.c * b00 - rq.s * mul_e(b01, rq.e);
-          const T x1 = rq.s * b00 + rq.c * mul_e(b01, rq.e);
-          const T y0 = rq.c * b10 - rq.s * mul_e(b11, rq.e);
-          const T y1 = rq.s * b10 + rq.c * mul_e(b11, rq.e);
-          b00 = x0; b01 = x1; b10 = y0; b11 = y1;
-        }
-        // rows: J_P^H (.)
-        if (i1 >= 0) {
-          const T x0 = rp.c * b00 - rp.s * mul_ce(b10, rp.e);
-          const T y0 = rp.s * b00 + rp.c * mul_ce(b10, rp.e);
-          const T x1 = rp.c * b01 - rp.s * mul_ce(b11, rp.e);
-          const T y1 = rp.s * b01 + rp.c * mul_ce(b11, rp.e);
-          b00 = x0; b10 = y0; b01 = x1; b11 = y1;
-        }
-        if (P == Q && i1 >= 0) {
-          b01 = zero<T>();
-          b10 = zero<T>();
-          b00 = from_real<T>(realx(b00));
-          b11 = from_real<T>(realx(b11));
-        }
+        rotate_block<T>(rp, rq, P == Q, b00, b01, b10, b11);
         Anext[(long long)i0 * n + j0] = b00;
         if (j1 >= 0) Anext[(long long)i0 * n + j1] = b01;
         if (i1 >= 0) Anext[(long long)i1 * n + j0] = b10;
@@ -351,7 +543,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(T* __restrict__ A0, T* __re
         V[(long long)row * n + rq.p] = rq.c * v0 - rq.s * mul_e(v1, rq.e);
         V[(long long)row * n + rq.q] = rq.s * v0 + rq.c * mul_e(v1, rq.e);
       }
-      if (!grid_barrier(bar, G, st, 100 + r)) return;
+      if (!all_barrier<MODE>(bar, G, st, 100 + r)) return;
       T* t = A; A = Anext; Anext = t;
     }
   }
@@ -418,6 +610,138 @@ __global__ void phase_fix_kernel(T* __restrict__ C, int n, const DeviceStatus* s
   }
 }
 
+// Jacobi on A (n x n, in place) accumulating V.  When one round's 2x2 blocks fit the threads
+// of one thread-block cluster, the kernel runs as a single cluster and every round ends on a
+// hardware cluster barrier; otherwise as a cooperative grid with a software grid barrier.
+template <class T>
+int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm) {
+  cudaStream_t s = c->stream;
+  const int npad = n + (n & 1), np = npad / 2;
+  const size_t rot_bytes = sizeof(Rot) * np;
+  double tol = 1e-14;
+  int max_sweeps = 60;
+  unsigned* bar = c->d_barrier;
+  DeviceStatus* st = c->d_status;
+  double* red = c->d_reduce;
+  int rc;
+  const long long blocks = (long long)np * np;
+  if (c->jacobi_cluster && blocks <= 16ll * 1024 * 2) {
+    // one cluster of G CTAs x 1024 threads, G <= 16 (non-portable sizes above 8 when allowed)
+    int G = (int)std::max(1ll, std::min<long long>(16, (blocks + 1023) / 1024));
+    if (rot_bytes > 48 * 1024) {
+      rc = check_cuda(c, cudaFuncSetAttribute(jacobi_kernel<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)rot_bytes), "jacobi smem attribute");
+      if (rc != PAWFD_OK) return rc;
+    }
+    if (G > 8) {
+      if (cudaFuncSetAttribute(jacobi_kernel<T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        G = 8;
+      }
+    }
+    for (;; G /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(G);
+      cfg.blockDim = dim3(1024);
+      cfg.dynamicSmemBytes = rot_bytes;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = G;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, jacobi_kernel<T, 1>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nclusters = 0;
+      }
+      if (nclusters >= 1) {
+        rc = check_cuda(c, cudaLaunchKernelEx(&cfg, jacobi_kernel<T, 1>, Am, A2, Vm, n, tol, max_sweeps, bar, st, red),
+                        "jacobi cluster launch");
+        c->launches += 1;
+        return rc;
+      }
+      if (G == 1) break;
+    }
+  }
+  // cooperative grid sized to the work of one round and to co-residency
+  if (rot_bytes > 48 * 1024) {
+    rc = check_cuda(c, cudaFuncSetAttribute(jacobi_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)rot_bytes), "jacobi smem attribute");
+    if (rc != PAWFD_OK) return rc;
+  }
+  int per_sm = 0;
+  rc = check_cuda(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T, 0>, 256, rot_bytes),
+                  "occupancy");
+  if (rc != PAWFD_OK) return rc;
+  long long want = (blocks + 255) / 256;
+  int G = (int)std::max(1ll, std::min<long long>(want, (long long)per_sm * c->num_sms));
+  G = std::min(G, 2048);   // grid_sum partials live in red[0, 2048)
+  rc = check_cuda(c, cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), s), "barrier reset");
+  if (rc != PAWFD_OK) return rc;
+  void* args[] = {&Am, &A2, &Vm, &n, &tol, &max_sweeps, &bar, &st, &red};
+  rc = check_cuda(c, cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T, 0>, dim3(G), dim3(256), args,
+                                                 rot_bytes, s),
+                  "jacobi cooperative launch");
+  c->launches += 1;
+  return rc;
+}
+
+// Launch a kernel of the MODE 1 / MODE 0 pair: one thread-block cluster of up to `want` CTAs
+// (non-portable sizes above 8 when allowed) when `cluster` is set and a cluster fits, else a
+// cooperative grid of up to `want` co-resident CTAs.
+template <class K1, class K0, class... Args>
+int launch_cluster_or_grid(pawfd_ctx* c, K1 kernel1, K0 kernel0, int nthreads, size_t smem, int want, bool cluster,
+                           const char* what, Args... args) {
+  cudaStream_t s = c->stream;
+  int rc;
+  if (cluster) {
+    int G = std::max(1, std::min(16, want));
+    if (G > 8 && cudaFuncSetAttribute(kernel1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      G = 8;
+    }
+    for (;; G = (G + 1) / 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(G);
+      cfg.blockDim = dim3(nthreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = G;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kernel1, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nclusters = 0;
+      }
+      if (nclusters >= 1) {
+        rc = check_cuda(c, cudaLaunchKernelEx(&cfg, kernel1, args...), what);
+        c->launches += 1;
+        return rc;
+      }
+      if (G == 1) break;
+    }
+  }
+  int per_sm = 0;
+  rc = check_cuda(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel0, nthreads, smem), "occupancy");
+  if (rc != PAWFD_OK) return rc;
+  const int G = std::max(1, std::min(want, per_sm * c->num_sms));
+  rc = check_cuda(c, cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), s), "barrier reset");
+  if (rc != PAWFD_OK) return rc;
+  void* argv[] = {&args...};
+  rc = check_cuda(c, cudaLaunchCooperativeKernel((const void*)kernel0, dim3(G), dim3(nthreads), argv, smem, s), what);
+  c->launches += 1;
+  return rc;
+}
+
 template <class T>
 int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   const long long nn = (long long)n * n;
@@ -432,46 +756,57 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   cudaStream_t s = c->stream;
   const unsigned eb = (unsigned)((nn + 255) / 256);
   symmetrize_kernel<T><<<eb, 256, 0, s>>>(H, S, n, Hs, Lm);
-  cholesky_kernel<T><<<1, 1024, 0, s>>>(Lm, n, c->d_status);
+  c->launches += 1;
+  int rc = check_cuda(c, cudaGetLastError(), "symmetrize launch");
+  if (rc != PAWFD_OK) return rc;
+  // Cholesky: one cluster up to n = 256 (its flops fit 16 SMs), the whole GPU above
+  {
+    unsigned* bar = c->d_barrier;
+    DeviceStatus* st = c->d_status;
+    const int want = n <= 256 ? 16 : c->num_sms;
+    rc = launch_cluster_or_grid(c, cholesky_kernel<T, 1>, cholesky_kernel<T, 0>, CH_NT, 0, want, c->jacobi_cluster,
+                                "cholesky launch", Lm, n, bar, st);
+    if (rc != PAWFD_OK) return rc;
+  }
   tri_inverse_kernel<T><<<n, 256, sizeof(T) * n, s>>>(Lm, n, Li, c->d_status);
   dim3 gg((n + 15) / 16, (n + 15) / 16);
   small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, false, Hs, false, n, T1, c->d_status);
   small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Li, true, n, Am, c->d_status);
   hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, c->d_status);
-  c->launches += 6;
-  int rc = check_cuda(c, cudaGetLastError(), "subspace launch");
+  c->launches += 4;
+  rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
 
-  // Jacobi: cooperative launch sized to the work of one round and to co-residency
-  const int npad = n + (n & 1), np = npad / 2;
-  const size_t rot_bytes = sizeof(Rot) * np;
-  if (rot_bytes > 48 * 1024) {
-    rc = check_cuda(c, cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)rot_bytes), "jacobi smem attribute");
+  // Two Ogita-Aishima steps from X = I (skipped on the device when A is already diagonal or
+  // far from it), then A <- X^H A X and the Jacobi sweeps, which accumulate onto X
+  {
+    identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n);
+    c->launches += 1;
+    int* skip = (int*)(c->d_barrier + 2);
+    const double tol = 1e-14;
+    const DeviceStatus* st = c->d_status;
+    // step 1: S = A, R = 0; X1 = I + E into Hs (the symmetrized H is no longer needed)
+    refine_step_kernel<T><<<1, 1024, 0, s>>>(Am, nullptr, n, T1, skip, tol, st);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, T1, false, n, Hs, st, Vm, skip, Vm);
+    // step 2: S = X1^H A X1 (into Lm, no longer needed), X1^H X1 (into A2), X2 = X1 + X1 E into Vm
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Hs, false, n, T1, st, nullptr, skip, Am);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, T1, false, n, Lm, st, nullptr, skip, T1);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, Hs, false, n, A2, st, nullptr, skip, Vm);
+    refine_step_kernel<T><<<1, 1024, 0, s>>>(Lm, A2, n, T1, skip, tol, st);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, T1, false, n, Vm, st, Hs, skip, Hs);
+    // A <- X2^H A X2
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, skip, Am);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, skip, T1);
+    c->launches += 9;
+    rc = check_cuda(c, cudaGetLastError(), "refinement steps");
     if (rc != PAWFD_OK) return rc;
   }
-  int per_sm = 0;
-  rc = check_cuda(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel<T>, 256, rot_bytes),
-                  "occupancy");
-  if (rc != PAWFD_OK) return rc;
-  long long want = ((long long)np * np + 255) / 256;
-  int G = (int)std::max(1ll, std::min<long long>(want, (long long)per_sm * c->num_sms));
-  G = std::min(G, 4096);
-  rc = check_cuda(c, cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), s), "barrier reset");
-  if (rc != PAWFD_OK) return rc;
-  double tol = 1e-14;
-  int max_sweeps = 60;
-  unsigned* bar = c->d_barrier;
-  DeviceStatus* st = c->d_status;
-  double* red = c->d_reduce;
-  void* args[] = {&Am, &A2, &Vm, &n, &tol, &max_sweeps, &bar, &st, &red};
-  rc = check_cuda(c, cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T>, dim3(G), dim3(256), args, rot_bytes, s),
-                  "jacobi cooperative launch");
+  rc = launch_jacobi<T>(c, n, Am, A2, Vm);
   if (rc != PAWFD_OK) return rc;
   sort_kernel<T><<<n, 128, 0, s>>>(Am, Vm, n, eps, T1, c->d_status);
   small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, true, T1, false, n, C, c->d_status);
   phase_fix_kernel<T><<<n, 256, 0, s>>>(C, n, c->d_status);
-  c->launches += 4;
+  c->launches += 3;
   return check_cuda(c, cudaGetLastError(), "subspace launch");
 }
 
