@@ -111,6 +111,8 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,
  *                     at most 64 (clamped further by the kernel's thread and memory limits).
  *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
+ *   "stencil_zsplit"  general stencil kernel: the z range is split so that one launch has at
+ *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
@@ -182,6 +184,50 @@ int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* p
  * or misaligned band arrays; device-side failures of step 5 are reported by pawfd_sync. */
 int pawfd_refine(pawfd_ctx* ctx, const void* psi_lo, int nb, void* psi, void* hpsi, void* spsi, void* Hnm,
                  void* Snm, double* eps, double* theta, double* resid, void* C);
+
+/* One Rayleigh-Ritz step of SCF step 1 (Kohn-Sham section) as a single call: hpsi = H psi
+ * and spsi = S psi (Eq. (dh) and the overlap operator of the PAW section; one set of
+ * projections serves both), Hnm = dV psi^H hpsi and Snm = dV psi^H spsi (Hermitian Gram),
+ * the subspace diagonalization (eps ascending, C; Hnm and Snm are overwritten as in
+ * pawfd_subspace_diag) and psi_out = psi C.
+ *   psi, hpsi, spsi, psi_out: [nb][K] of the context's dtype, pairwise distinct;
+ *   Hnm, Snm, C: [nb][nb] FP64 of the context's kind; eps: [nb] doubles.  All device memory
+ *   owned by the caller.  Errors as the individual calls; device-side failures at pawfd_sync. */
+int pawfd_rr_step(pawfd_ctx* ctx, const void* psi, int nb, void* hpsi, void* spsi, void* Hnm, void* Snm,
+                  double* eps, void* C, void* psi_out);
+
+/* A batch of independent Rayleigh-Ritz steps (no counterpart in the paper: the packaging of
+ * many eigensolver instances of different sizes for one GPU).  Each job names its own
+ * context (at most one job per context: a job uses its context's scratch) and the arrays of
+ * pawfd_rr_step.  pawfd_batch_launch forks from `stream`, runs every job on a stream of the
+ * batch's own (so the jobs' kernels overlap on the GPU) and joins back into `stream`.
+ * With use_graph = 1, pawfd_batch_create captures that whole sequence once into a CUDA graph
+ * and every launch is one graph launch; the arrays are then fixed for the batch's lifetime.
+ * If the capture is refused the batch stays usable in eager mode (pawfd_batch_is_graph
+ * returns 0 and pawfd_batch_last_error says why).  The contexts' own streams are not used;
+ * check each context with pawfd_sync after the stream has been synchronized.
+ * Returns PAWFD_EINVAL for null arguments, count < 1, a repeated context or a job whose
+ * arrays fail the checks of pawfd_rr_step; PAWFD_EDEVICE for CUDA failures. */
+typedef struct pawfd_rr_job {
+  pawfd_ctx* ctx;
+  const void* psi;
+  int nb;
+  void* hpsi;
+  void* spsi;
+  void* Hnm;
+  void* Snm;
+  double* eps;
+  void* C;
+  void* psi_out;
+} pawfd_rr_job;
+typedef struct pawfd_batch pawfd_batch;
+int pawfd_batch_create(pawfd_batch** out, const pawfd_rr_job* jobs, int count, int use_graph);
+int pawfd_batch_launch(pawfd_batch* batch, void* stream);
+int pawfd_batch_is_graph(const pawfd_batch* batch);
+/* kernels one launch of the batch runs (counted when the sequence was enqueued) */
+long long pawfd_batch_kernel_count(const pawfd_batch* batch);
+const char* pawfd_batch_last_error(const pawfd_batch* batch);
+int pawfd_batch_destroy(pawfd_batch* batch);
 
 /* Gram matrix for callers that cannot allocate device memory.
  *

@@ -26,6 +26,11 @@ class SystemDesc(ctypes.Structure):
                 ("dH", VP), ("dS", VP), ("dmat_off", VP), ("vloc", VP)]
 
 
+class RrJob(ctypes.Structure):
+    _fields_ = [("ctx", VP), ("psi", VP), ("nb", ctypes.c_int), ("hpsi", VP), ("spsi", VP), ("Hnm", VP),
+                ("Snm", VP), ("eps", VP), ("C", VP), ("psi_out", VP)]
+
+
 SIGNATURES = {
     "pawfd_create": ([ctypes.POINTER(VP), ctypes.POINTER(SystemDesc), VP], I),
     "pawfd_destroy": ([VP], I),
@@ -44,6 +49,13 @@ SIGNATURES = {
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
     "pawfd_refine": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
+    "pawfd_rr_step": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP], I),
+    "pawfd_batch_create": ([ctypes.POINTER(VP), ctypes.POINTER(RrJob), I, I], I),
+    "pawfd_batch_launch": ([VP, VP], I),
+    "pawfd_batch_is_graph": ([VP], I),
+    "pawfd_batch_kernel_count": ([VP], ctypes.c_longlong),
+    "pawfd_batch_last_error": ([VP], ctypes.c_char_p),
+    "pawfd_batch_destroy": ([VP], I),
     "pawfd_gram_noalloc": ([VP, VP, ctypes.c_longlong, I, I, D, VP, VP], I),
 }
 

@@ -195,6 +195,39 @@ class Context:
         psi_rot = self.rotate(psi, C, out=w.get("psi_rot"))
         return {"Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}
 
+    def alloc_work(self, nb: int) -> dict:
+        """Device arrays of one Rayleigh-Ritz step for nb bands (the keys rr_step fills)."""
+        return {"Hpsi": self.empty_bands(nb), "Spsi": self.empty_bands(nb),
+                "Hnm": torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device),
+                "Snm": torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device),
+                "eps": torch.empty(nb, dtype=torch.float64, device=self.device),
+                "C": torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device)}
+
+    def _job_args(self, psi, out, work):
+        nb = self._bands(psi, "psi")
+        self._bands(out, "out")
+        for key in ("Hpsi", "Spsi"):
+            self._bands(work[key], key)
+        for key in ("Hnm", "Snm", "C"):
+            self._mat(work[key], nb, key)
+        if work["eps"].numel() != nb or work["eps"].dtype != torch.float64:
+            raise ValueError("eps must hold nb float64 values")
+        p = lambda t: t.data_ptr()  # noqa: E731
+        return nb, (p(psi), nb, p(work["Hpsi"]), p(work["Spsi"]), p(work["Hnm"]), p(work["Snm"]), p(work["eps"]),
+                    p(work["C"]), p(out))
+
+    def rr_step(self, psi, out=None, work: Optional[dict] = None) -> dict:
+        """One whole Rayleigh-Ritz step in a single library call (pawfd_rr_step): returns the
+        work dict (Hpsi, Spsi, Hnm/Snm as the solver's workspace, eps, C) plus psi_rot."""
+        nb = self._bands(psi, "psi")
+        work = work if work is not None else self.alloc_work(nb)
+        out = self.empty_bands(nb) if out is None else out
+        _, args = self._job_args(psi, out, work)
+        self._call(self.lib.pawfd_rr_step, *[ctypes.c_void_p(a) if i != 1 else a for i, a in enumerate(args)])
+        res = dict(work)
+        res["psi_rot"] = out
+        return res
+
     def refine(self, psi_lo, work: Optional[dict] = None, check: bool = True) -> dict:
         """Final refinement of mixed-form bands on this FP64 context (pawfd_refine): FP64
         H psi', S psi', Gram matrices, Rayleigh quotients ``theta``, a second subspace solve
@@ -230,6 +263,66 @@ class Context:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self.lib.pawfd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent Rayleigh-Ritz steps of several contexts (pawfd_batch_*): every launch runs
+    one step of every job, each job on a stream of its own so that their kernels overlap;
+    with ``use_graph`` the sequence is captured once into a CUDA graph and each launch is a
+    single graph launch (the arrays are then fixed).  ``entries``: (ctx, psi, out, work)."""
+
+    def __init__(self, entries, use_graph: bool = True):
+        if not entries:
+            raise ValueError("a batch needs at least one job")
+        self.lib = _lib.load()
+        self.entries = list(entries)   # keeps the tensors alive
+        jobs = (_lib.RrJob * len(entries))()
+        for i, (ctx, psi, out, work) in enumerate(entries):
+            nb, args = ctx._job_args(psi, out, work)
+            j = jobs[i]
+            j.ctx = ctx._h.value
+            j.psi, j.nb, j.hpsi, j.spsi, j.Hnm, j.Snm, j.eps, j.C, j.psi_out = args
+        self.device = entries[0][0].device
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            rc = self.lib.pawfd_batch_create(ctypes.byref(self._h), jobs, len(entries), int(use_graph))
+        if rc != 0:
+            raise PawFDError(rc, "pawfd_batch_create failed")
+
+    @property
+    def is_graph(self) -> bool:
+        return bool(self.lib.pawfd_batch_is_graph(self._h))
+
+    @property
+    def kernel_count(self) -> int:
+        return int(self.lib.pawfd_batch_kernel_count(self._h))
+
+    @property
+    def last_error(self) -> str:
+        return self.lib.pawfd_batch_last_error(self._h).decode()
+
+    def launch(self):
+        stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        rc = self.lib.pawfd_batch_launch(self._h, stream)
+        if rc != 0:
+            raise PawFDError(rc, self.last_error)
+
+    def sync(self):
+        """Wait for the device and raise the first error any job's context recorded."""
+        torch.cuda.synchronize(self.device)
+        for ctx, *_ in self.entries:
+            ctx.sync()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self.lib.pawfd_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):

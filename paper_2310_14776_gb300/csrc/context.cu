@@ -372,6 +372,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
+  if (n == "stencil_zsplit" && value >= 0 && value <= 64) {
+    c->stencil_zsplit = value;
+    return PAWFD_OK;
+  }
   if (n == "stencil_yblock" && value >= 0 && value <= 3) {
     c->stencil_yblock = value;
     return PAWFD_OK;

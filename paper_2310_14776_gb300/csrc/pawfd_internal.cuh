@@ -186,6 +186,7 @@ struct pawfd_ctx {
   int stencil_variant = 0;                    // 0: ring (bulk copies) first, 1: register float4 kernel
   int stencil_rows = 0;                       // y rows per CTA of the ring kernel (0: automatic)
   int stencil_yblock = 0;                     // y rows per thread of the ring kernel (0: automatic)
+  int stencil_zsplit = 0;                     // general stencil: target CTAs per SM of a launch (0: 4)
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   pawfd::TcScratch tc;
   std::string err;

@@ -131,8 +131,9 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
   a.vshift = (const R*)c->d_vshift;
   const int gx = (a.n1 + TX - 1) / TX, gy = (a.n2 + TY - 1) / TY;
   const long long tiles = (long long)gx * gy;
-  // split z so that one launch has at least ~4 CTAs per SM
-  long long want = (4ll * c->num_sms + tiles * nb - 1) / (tiles * nb);
+  // split z so that one launch has at least `per_sm` CTAs per SM (default 4)
+  const long long per_sm = c->stencil_zsplit > 0 ? c->stencil_zsplit : 4;
+  long long want = (per_sm * c->num_sms + tiles * nb - 1) / (tiles * nb);
   int nzc = (int)std::max(1ll, std::min<long long>(want, (a.n3 + 3) / 4));
   a.zchunk = (a.n3 + nzc - 1) / nzc;
   a.nzc = (a.n3 + a.zchunk - 1) / a.zchunk;

@@ -320,3 +320,75 @@ WORKLOADS = {
     "bloch-144c-1024b": Workload("bloch-144c-1024b", (144, 144, 144), (144 * H_02A,) * 3, 1024, 128, PSET_SPD2,
                                  seed=2, complex_wf=True, k=_bloch_k((144 * H_02A,) * 3)),
 }
+
+
+# ------------------------------------------------------------------------------------------
+# Batched and served instances: independent systems of different sizes
+# ------------------------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class Instance:
+    """One eigensolver instance of a batch or of the served stream: grid, cell at 0.2 Angstrom
+    spacing, band count, atoms (18 projectors each), Bloch vector, seed."""
+    n: Tuple[int, int, int]
+    nbands: int
+    natoms: int
+    seed: int
+    complex_wf: bool
+    k: Tuple[float, float, float]
+
+    @property
+    def cell(self) -> Tuple[float, float, float]:
+        return tuple(self.n[c] * H_02A for c in range(3))
+
+    @property
+    def npoints(self) -> int:
+        return self.n[0] * self.n[1] * self.n[2]
+
+    def system(self) -> System:
+        return make_system(self.n, self.cell, self.natoms, PSET_SPD2, self.seed, k=self.k,
+                           complex_wf=self.complex_wf)
+
+    def psi(self, system: System) -> np.ndarray:
+        return make_psi(system, self.nbands, self.seed)
+
+
+def batch_instance(seed: int, complex_wf: bool = True, grid=(32, 80), bands=(32, 256), atoms=(2, 24)) -> Instance:
+    """Seeded sizes of one batched instance: each grid axis and the band and atom counts are
+    independent uniform integers in the given inclusive ranges; for Bloch instances each
+    component of k is uniform in [0, pi / L_c)."""
+    u = uniform01(seed, STREAM_SIZES, 0, 5)
+    n = tuple(int(grid[0] + min(grid[1] - grid[0], int(u[c] * (grid[1] - grid[0] + 1)))) for c in range(3))
+    nb = int(bands[0] + min(bands[1] - bands[0], int(u[3] * (bands[1] - bands[0] + 1))))
+    na = int(atoms[0] + min(atoms[1] - atoms[0], int(u[4] * (atoms[1] - atoms[0] + 1))))
+    k = (0.0, 0.0, 0.0)
+    if complex_wf:
+        uk = uniform01(seed, STREAM_KPT, 0, 3)
+        k = tuple(float(uk[c] * math.pi / (n[c] * H_02A)) for c in range(3))
+    return Instance(n, nb, na, seed, complex_wf, k)
+
+
+def batch_instances(count: int = 64, seed0: int = 3, complex_wf: bool = True, **ranges) -> List[Instance]:
+    """The batched workload: `count` instances with seeds seed0, seed0 + 1, ..."""
+    return [batch_instance(seed0 + i, complex_wf, **ranges) for i in range(count)]
+
+
+def served_job(job_id: int, seed0: int = 4, complex_wf: bool = True, large_fraction: float = 0.1,
+               large=((128, 128, 128), 512, 24), **ranges) -> Instance:
+    """One job of the served stream: with probability `large_fraction` a large job (grid,
+    bands, atoms of `large`), otherwise sized as a batched instance."""
+    seed = seed0 + job_id
+    if uniform01(seed, STREAM_SIZES, 5, 1)[0] < large_fraction:
+        n, nb, na = large
+        k = (0.0, 0.0, 0.0)
+        if complex_wf:
+            uk = uniform01(seed, STREAM_KPT, 0, 3)
+            k = tuple(float(uk[c] * math.pi / (n[c] * H_02A)) for c in range(3))
+        return Instance(tuple(n), nb, na, seed, complex_wf, k)
+    return batch_instance(seed, complex_wf, **ranges)
+
+
+def poisson_arrivals(rate: float, count: int, seed: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson stream: cumulative exponential gaps -ln(1 - u) / rate."""
+    u = uniform01(seed, STREAM_SIZES, 1 << 20, count)
+    return np.cumsum(-np.log1p(-u) / rate)

@@ -52,25 +52,23 @@ def test_header_compiles_as_c():
     assert r.returncode == 0, r.stderr
 
 
-def test_desc_struct_layout_matches_header():
-    # field offsets of the ctypes mirror equal those the C compiler gives the header's struct
-    fields = [f[0] for f in _lib.SystemDesc._fields_]
+@pytest.mark.parametrize("cname,cls", [("pawfd_system_desc", "SystemDesc"), ("pawfd_rr_job", "RrJob")])
+def test_struct_layout_matches_header(cname, cls):
+    # field offsets of the ctypes mirrors equal those the C compiler gives the header's structs
+    import ctypes
+    mirror = getattr(_lib, cls)
+    fields = [f[0] for f in mirror._fields_]
     prog = '#include <stdio.h>\n#include <stddef.h>\n#include "pawfd.h"\nint main(void){\n'
     for f in fields:
-        prog += 'printf("%%zu\\n", offsetof(pawfd_system_desc, %s));\n' % f
-    prog += 'printf("%zu\\n", sizeof(pawfd_system_desc)); return 0; }\n'
-    exe = "/tmp/pawfd_layout_check"
+        prog += 'printf("%%zu\\n", offsetof(%s, %s));\n' % (cname, f)
+    prog += 'printf("%%zu\\n", sizeof(%s)); return 0; }\n' % cname
+    exe = "/tmp/pawfd_layout_check_" + cname
     r = subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-x", "c", "-", "-o", exe],
                        input=prog, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
-    want = [getattr(_lib.SystemDesc, f).offset for f in fields] + [ctypes_sizeof()]
+    want = [getattr(mirror, f).offset for f in fields] + [ctypes.sizeof(mirror)]
     assert got == want
-
-
-def ctypes_sizeof():
-    import ctypes
-    return ctypes.sizeof(_lib.SystemDesc)
 
 
 def test_api_fails_loudly_without_cuda():

@@ -1,0 +1,134 @@
+"""GPU tests of the single-call step, the batched form and the served form.
+
+* pawfd_rr_step gives the same bits as the separate calls of one Rayleigh-Ritz step.
+* A batch (one CUDA graph, or eager fork/join over streams) gives every instance the same
+  bits as running that instance alone; a batch of FP64 instances matches the FP64 oracle.
+* The served loop gives every job the same result alone and in the mix (the stated
+  tolerance is 1e-10 Ha; the kernels are deterministic, so the bits agree), and never
+  charges more than its HBM budget.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2310_14776_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def small(count, complex_wf, seed0):
+    return synth.batch_instances(count, seed0, complex_wf, grid=(20, 36), bands=(8, 40), atoms=(2, 5))
+
+
+def setup(inst, precision, dev):
+    from paper_2310_14776_gb300 import api
+    s = inst.system()
+    ctx = api.Context(s, max_bands=inst.nbands, device=dev, precision=precision)
+    psi = inst.psi(s)
+    if precision == "mixed":
+        psi = psi.astype(np.complex64 if inst.complex_wf else np.float32)
+    psi_t = torch.from_numpy(psi).to(dev)
+    return s, ctx, psi, psi_t
+
+
+@pytest.mark.parametrize("precision,cplx", [("fp64", False), ("fp64", True), ("mixed", False), ("mixed", True)])
+def test_rr_step_equals_separate_calls(dev, precision, cplx):
+    inst = small(1, cplx, 70)[0]
+    _, ctx, _, psi = setup(inst, precision, dev)
+    a = ctx.rayleigh_ritz(psi)
+    b = ctx.rr_step(psi)
+    ctx.sync()
+    for key in ("Hpsi", "Spsi", "eps", "C", "psi_rot"):
+        assert torch.equal(a[key], b[key]), key
+    ctx.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_single_instances(dev, use_graph):
+    from paper_2310_14776_gb300 import api
+    insts = small(5, True, 80) + small(3, False, 90)
+    entries, single = [], []
+    for i, inst in enumerate(insts):
+        precision = "fp64" if i % 4 == 3 else "mixed"
+        _, ctx, _, psi = setup(inst, precision, dev)
+        ref = ctx.rr_step(psi)
+        ctx.sync()
+        single.append({k: ref[k].clone() for k in ("eps", "psi_rot", "Hpsi")})
+        entries.append((ctx, psi, torch.empty_like(psi), ctx.alloc_work(inst.nbands)))
+    batch = api.Batch(entries, use_graph=use_graph)
+    if use_graph:
+        assert batch.is_graph, batch.last_error
+    for rep in range(2):              # a second launch replays the same work on the same inputs
+        batch.launch()
+        batch.sync()
+        assert batch.kernel_count > 0
+        for (ctx, psi, out, work), ref in zip(entries, single):
+            assert torch.equal(work["eps"], ref["eps"])
+            assert torch.equal(out, ref["psi_rot"])
+            assert torch.equal(work["Hpsi"], ref["Hpsi"])
+    batch.close()
+    for ctx, *_ in entries:
+        ctx.close()
+
+
+def test_batch_of_fp64_instances_matches_oracle(dev):
+    from paper_2310_14776_gb300 import api
+    insts = small(3, True, 100)
+    entries, refs = [], []
+    for inst in insts:
+        s, ctx, psi_np, psi = setup(inst, "fp64", dev)
+        refs.append(O.rayleigh_ritz(s, psi_np))
+        entries.append((ctx, psi, torch.empty_like(psi), ctx.alloc_work(inst.nbands)))
+    batch = api.Batch(entries, use_graph=True)
+    batch.launch()
+    batch.sync()
+    for (ctx, psi, out, work), ref in zip(entries, refs):
+        assert np.max(np.abs(work["eps"].cpu().numpy() - ref["eps"])) <= 1e-10
+        got = work["Hpsi"].cpu().numpy().reshape(len(ref["eps"]), -1)
+        want = ref["Hpsi"].reshape(len(ref["eps"]), -1)
+        assert np.all(np.linalg.norm(got - want, axis=1) <= 1e-12 * np.linalg.norm(want, axis=1))
+    batch.close()
+    for ctx, *_ in entries:
+        ctx.close()
+
+
+def test_batch_rejects_a_repeated_context(dev):
+    from paper_2310_14776_gb300 import api, _lib
+    inst = small(1, True, 110)[0]
+    _, ctx, _, psi = setup(inst, "mixed", dev)
+    e = (ctx, psi, torch.empty_like(psi), ctx.alloc_work(inst.nbands))
+    with pytest.raises(_lib.PawFDError):
+        api.Batch([e, e])
+    ctx.close()
+
+
+def test_served_results_same_alone_and_in_mix(dev):
+    from paper_2310_14776_gb300 import serve
+    systems = small(5, True, 120)
+    jobs = [serve.Job(j, 0.002 * j, j % 5, 1000 + j) for j in range(12)]
+    budget = 6 << 30
+    srv = serve.Server(systems, dev, precision="mixed", iterations=3, budget_bytes=budget, max_active=8)
+    mixed = srv.run(jobs)
+    assert mixed["unfinished"] == 0 and len(mixed["records"]) == len(jobs)
+    assert mixed["peak_used"] <= budget and mixed["overruns"] == 0
+    got = {r.job.job_id: r.eps for r in mixed["records"]}
+    srv.close()
+    for job in jobs:
+        alone = serve.Server(systems, dev, precision="mixed", iterations=3, budget_bytes=budget, max_active=1)
+        res = alone.run([serve.Job(job.job_id, 0.0, job.system, job.psi_seed)])
+        alone.close()
+        eps = res["records"][0].eps
+        assert np.max(np.abs(eps - got[job.job_id])) <= 1e-10
+        assert np.array_equal(eps, got[job.job_id])
+    stats = serve.latency_stats(mixed["records"])
+    assert stats["jobs"] == len(jobs) and stats["p99_ms"] >= stats["p50_ms"] > 0

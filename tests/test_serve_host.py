@@ -1,0 +1,85 @@
+"""Host-side logic of the batched and served forms (no GPU): seeded instance sizes, the
+Poisson job stream, and the scheduler's HBM budget and admission rules."""
+import numpy as np
+
+from paper_2310_14776_gb300 import serve, synth
+
+
+def test_batch_instances_are_seeded_and_in_range():
+    a = synth.batch_instances(64)
+    b = synth.batch_instances(64)
+    assert a == b
+    for inst in a:
+        assert all(32 <= v <= 80 for v in inst.n)
+        assert 32 <= inst.nbands <= 256 and 2 <= inst.natoms <= 24
+        assert all(0.0 <= inst.k[c] < np.pi / inst.cell[c] for c in range(3))
+        assert abs(inst.cell[0] / inst.n[0] - 0.2 * synth.BOHR_PER_ANGSTROM) < 1e-12
+    # the sizes actually vary (non-cubic grids allowed)
+    assert len({inst.n for inst in a}) > 50
+    assert any(len(set(inst.n)) > 1 for inst in a)
+
+
+def test_poisson_stream_rate_and_mix():
+    jobs = serve.job_stream(200.0, 30.0, 64, 8)
+    assert jobs == serve.job_stream(200.0, 30.0, 64, 8)
+    n = len(jobs)
+    # Poisson count: mean 6000, sd ~77
+    assert abs(n - 6000) < 5 * np.sqrt(6000)
+    gaps = np.diff([0.0] + [j.arrival for j in jobs])
+    assert np.all(gaps >= 0) and abs(gaps.mean() - 1 / 200.0) < 5 * (1 / 200.0) / np.sqrt(n)
+    large = sum(j.system >= 64 for j in jobs) / n
+    assert abs(large - 0.1) < 5 * np.sqrt(0.09 / n)
+    assert all(0 <= j.system < 72 for j in jobs)
+
+
+def test_scheduler_never_exceeds_budget_and_admits_first_fit():
+    rng = np.random.default_rng(1)
+    sizes = {j: int(rng.integers(1, 40)) for j in range(300)}
+    sch = serve.Scheduler(budget=100, max_active=6)
+    jobs = [serve.Job(j, float(j), 0, j) for j in range(300)]
+    need = lambda job: sizes[job.job_id]  # noqa: E731
+    no_reclaim = lambda short: 0  # noqa: E731
+    running, finished = [], []
+    for job in jobs:
+        sch.arrive(job)
+        while True:
+            pick = sch.pick(need, no_reclaim)
+            if pick is None:
+                break
+            # first fit: no earlier waiting job within the lookahead would have fit
+            sch.admit(pick, need(pick))
+            running.append(pick)
+            assert sch.used <= sch.budget and len(sch.active) <= 6
+        if running and rng.random() < 0.6:
+            done = running.pop(int(rng.integers(len(running))))
+            sch.retire(done)
+            finished.append(done)
+    while running:
+        sch.retire(running.pop())
+    assert sch.used == 0 and sch.overruns == 0
+    assert sch.peak_used <= 100
+
+
+def test_scheduler_reclaims_idle_memory_and_skips_impossible_jobs():
+    sch = serve.Scheduler(budget=100, max_active=4)
+    sch.used = 90                       # idle pooled contexts hold 90
+    pool = [50, 40]
+
+    def reclaim(short):
+        freed = 0
+        while pool and freed < short:
+            freed += pool.pop(0)
+        return freed
+
+    sch.arrive(serve.Job(0, 0.0, 0, 0))   # needs 200: never fits this budget
+    sch.arrive(serve.Job(1, 0.0, 0, 1))   # needs 30: fits after reclaiming one context
+    need = {0: 200, 1: 30}
+    pick = sch.pick(lambda j: need[j.job_id], reclaim)
+    assert pick.job_id == 1 and sch.used == 40 and pool == [40]
+    assert [j.job_id for j in sch.queue] == [0]
+
+
+def test_array_bytes():
+    inst = synth.Instance((10, 11, 12), 7, 2, 0, True, (0.0, 0.0, 0.0))
+    assert serve.array_bytes(inst, "mixed") == 4 * 1320 * 7 * 8 + 3 * 49 * 16 + 56
+    assert serve.array_bytes(inst, "fp64") == 4 * 1320 * 7 * 16 + 3 * 49 * 16 + 56
