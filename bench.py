@@ -31,6 +31,11 @@ sys.path.insert(0, ROOT)
 
 from paper_2310_14776_gb300 import synth  # noqa: E402
 
+METRIC = "H|psi> Gpt\u00b7band/s; Rayleigh-Ritz steps/s and p50/p99 latency vs plain FP64"
+UNIT = "Gpt\u00b7band/s"
+VALUE_DEF = ("grid points x bands of whole Rayleigh-Ritz steps (apply_H, apply_S, Hermitian Gram H and S, "
+             "subspace diag, rotation) per second / 1e9, inputs resident in HBM")
+HOST_PSI_MAX = 3e8           # larger band blocks are generated on the device (seeded torch RNG)
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe kernel on this machine
 
@@ -41,12 +46,20 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="pawfd", choices=["pawfd", "reference"])
-    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS))
+    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS) + ["batch64", "served"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    return p.parse_args()
+    p.add_argument("--precision", default=None, choices=["fp64", "mixed"],
+                   help="fp64 (default for single workloads) or mixed (default for batch64 / served)")
+    p.add_argument("--rate", type=float, default=200.0, help="served: arrivals per second")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="served: length of the arrival stream")
+    p.add_argument("--serve-warmup", type=float, default=5.0, help="served: arrivals before this are excluded")
+    p.add_argument("--real", action="store_true", help="batch64 / served: real (Gamma) instead of Bloch instances")
+    a = p.parse_args()
+    if a.precision is None:
+        a.precision = "mixed" if a.workload in ("batch64", "served") else "fp64"
+    return a
 
 
 def dist_env():
@@ -83,7 +96,7 @@ class ClockSampler:
             os.close(fd)
             self.out = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.out,
                                          stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -133,12 +146,21 @@ def run_gpu(args):
     w = synth.WORKLOADS[args.workload]
     system = w.system()
     nb, K = w.nbands, system.npoints
-    psi_host = w.psi(system)
     cplx = system.complex_wf
-    if args.precision == "mixed":
-        psi_host = psi_host.astype(np.complex64 if cplx else np.float32)
     ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
-    psi = [torch.from_numpy(psi_host).to(dev), torch.empty_like(torch.from_numpy(psi_host), device=dev)]
+    if nb * K <= HOST_PSI_MAX:
+        psi_host = w.psi(system)
+        if args.precision == "mixed":
+            psi_host = psi_host.astype(np.complex64 if cplx else np.float32)
+        psi0 = torch.from_numpy(psi_host).to(dev)
+        psi_src = "seeded SplitMix64 on the host"
+    else:
+        psi_host = None
+        psi0 = device_bands(ctx, nb, w.seed)
+        psi_src = "seeded torch generator on the device (uniform(-1, 1))"
+        args.no_e2e = True
+    esize = psi0.element_size()
+    psi = [psi0, torch.empty_like(psi0)]
     work = {"Hpsi": ctx.empty_bands(nb), "Spsi": ctx.empty_bands(nb),
             "Hnm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
             "Snm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
@@ -201,7 +223,6 @@ def run_gpu(args):
 
     units = float(nb) * K * args.steps * world
     value = units / elapsed / 1e9
-    esize = psi_host.itemsize
     mixed = args.precision == "mixed"
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -230,11 +251,11 @@ def run_gpu(args):
     roof_unit = {"BF16 FLOP/s": "TFLOP/s", "FP64 instr/s": "Tinstr/s", "B/s": "GB/s"}[unit]
 
     result = {
-        "metric": "H|psi> Gpt.band/s over whole Rayleigh-Ritz steps (apply_H + apply_S + Gram + subspace diag + rotate)",
-        "value": value, "unit": "Gpt.band/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "metric": METRIC, "value_definition": VALUE_DEF,
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {8: "f64", 16: "c128", 4: "f32"}[esize] if not (mixed and cplx) else "c64",
-        "data": "synthetic (seeded)",
+        "data": "synthetic (seeded; bands: %s)" % psi_src,
         "config": {"workload": w.name, "grid": list(system.n), "bands": nb, "atoms": system.natoms,
                    "projectors_per_atom": int(system.nproj[0]) if system.natoms else 0,
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single-gpu",
@@ -256,7 +277,7 @@ def run_gpu(args):
     if not args.no_e2e:
         result["e2e"] = e2e_gpu(ctx, psi_host, work, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(system, psi_host, w)
+        result["cpu_baseline"] = cpu_baseline(system, w, args.precision)
     if world > 1:
         dist.barrier()
     ctx.close()
@@ -264,6 +285,20 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def device_bands(ctx, nb, seed):
+    """uniform(-1, 1) bands generated on the device by a seeded torch generator."""
+    import torch
+    g = torch.Generator(device=ctx.device)
+    g.manual_seed(int(seed))
+    shape = (nb,) + tuple(ctx.n[::-1])
+    rdt = torch.float32 if ctx.precision == "mixed" else torch.float64
+    re = torch.rand(shape, generator=g, device=ctx.device, dtype=rdt) * 2 - 1
+    if not ctx.complex:
+        return re
+    im = torch.rand(shape, generator=g, device=ctx.device, dtype=rdt) * 2 - 1
+    return torch.complex(re, im)
 
 
 def e2e_gpu(ctx, psi_host, work, args, dev):
@@ -279,12 +314,7 @@ def e2e_gpu(ctx, psi_host, work, args, dev):
 
     def one():
         d_in.copy_(h_in, non_blocking=True)
-        ctx.apply_H(d_in, out=work["Hpsi"])
-        ctx.apply_S(d_in, out=work["Spsi"])
-        ctx.gram(d_in, work["Hpsi"], M=work["Hnm"], hermitian=True)
-        ctx.gram(d_in, work["Spsi"], M=work["Snm"], hermitian=True)
-        ctx.subspace_diag(work["Hnm"], work["Snm"], eps=work["eps"], C=work["C"], overwrite=True, check=False)
-        ctx.rotate(d_in, work["C"], out=d_out)
+        ctx.rr_step(d_in, out=d_out, work=work)      # the single public call of one step
         h_eps.copy_(work["eps"], non_blocking=True)
         h_out.copy_(d_out, non_blocking=True)
 
@@ -300,8 +330,211 @@ def e2e_gpu(ctx, psi_host, work, args, dev):
     el = e0.elapsed_time(e1) * 1e-3
     K = psi_host[0].size
     per_step_bytes = h_in.numel() * h_in.element_size()
-    return {"value": nb * K * args.e2e_steps / el / 1e9, "unit": "Gpt.band/s", "steps": args.e2e_steps,
+    return {"value": nb * K * args.e2e_steps / el / 1e9, "unit": UNIT, "steps": args.e2e_steps,
+            "api": "Context.rr_step (pawfd_rr_step) with pinned host buffers",
             "h2d_bytes_per_step": per_step_bytes, "d2h_bytes_per_step": per_step_bytes + nb * 8}
+
+
+# ------------------------------------------------------------------------------------------
+# Batched and served forms
+# ------------------------------------------------------------------------------------------
+def contraction_bf16_flops(inst, precision):
+    """BF16 digit-product FLOP of one instance step's Hermitian Gram pair and rotation."""
+    products = 13 if precision == "mixed" else 28
+    cfac = 4 if inst.complex_wf else 1
+    nb, K = inst.nbands, inst.npoints
+    return 2.0 * products * cfac * (2 * nb * (nb + 1) / 2 + nb * nb) * K
+
+
+def fp64_step_seconds(inst, dev, system=None, reps=1):
+    """One plain FP64 single-instance step (pawfd_rr_step, eager), timed after one warm-up step."""
+    import torch
+    from paper_2310_14776_gb300 import api
+    s = system if system is not None else inst.system()
+    ctx = api.Context(s, max_bands=inst.nbands, device=dev, precision="fp64")
+    psi = device_bands(ctx, inst.nbands, inst.seed)
+    out = torch.empty_like(psi)
+    work = ctx.alloc_work(inst.nbands)
+    ctx.rr_step(psi, out=out, work=work)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ctx.rr_step(psi, out=out, work=work)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ctx.sync()
+    t = e0.elapsed_time(e1) * 1e-3 / reps
+    ctx.close()
+    del psi, out, work
+    torch.cuda.empty_cache()
+    return t
+
+
+def run_batch(args):
+    """64 independent instances (seeded sizes), one RR step of all of them per graph launch."""
+    import torch
+    import torch.distributed as dist
+    from paper_2310_14776_gb300 import api, autotune
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    insts = synth.batch_instances(64, complex_wf=not args.real)
+    ent_a, ent_b, tuned = [], [], {}
+    for inst in insts:
+        ctx = api.Context(inst.system(), max_bands=inst.nbands, device=dev, precision=args.precision)
+        psi_a = device_bands(ctx, inst.nbands, inst.seed)
+        psi_b = torch.empty_like(psi_a)
+        work = ctx.alloc_work(inst.nbands)
+        work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=dev))
+        opts = autotune.tune(ctx, psi_a, work)
+        tuned[str(autotune.shape_key(ctx, inst.nbands))] = opts
+        ent_a.append((ctx, psi_a, psi_b, work))
+        ent_b.append((ctx, psi_b, psi_a, work))
+    batches = [api.Batch(ent_a, use_graph=True), api.Batch(ent_b, use_graph=True)]
+    for i in range(args.warmup):
+        batches[i % 2].launch()
+    for b in batches:
+        b.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record()
+    for i in range(args.steps):
+        batches[(args.warmup + i) % 2].launch()
+        evs[i + 1].record()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    for b in batches:
+        b.sync()
+    elapsed = evs[0].elapsed_time(evs[-1]) * 1e-3
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = tt.item()
+    per_launch = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    units = sum(inst.npoints * inst.nbands for inst in insts)
+    value = units * args.steps * world / elapsed / 1e9
+    rr = len(insts) * args.steps * world / elapsed
+    flops = sum(contraction_bf16_flops(inst, args.precision) for inst in insts)
+    peaks = load_peaks()
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    achieved = flops * args.steps / elapsed
+    graph = all(b.is_graph for b in batches)
+    kernels = batches[0].kernel_count
+    for b in batches:
+        b.close()
+    for ctx, *_ in ent_a:
+        ctx.close()
+    del ent_a, ent_b, batches
+    torch.cuda.empty_cache()
+    # the plain FP64 single-instance path on the same instances, one after another
+    fp64_total = 0.0
+    if rank == 0:
+        fp64_total = sum(fp64_step_seconds(inst, dev) for inst in insts)
+    result = {
+        "metric": METRIC, "value_definition": VALUE_DEF + " (summed over the batch's instances)",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": ("c64" if not args.real else "f32") if args.precision == "mixed"
+        else ("c128" if not args.real else "f64"),
+        "data": "synthetic (seeded sizes; bands from a seeded torch generator on the device)",
+        "config": {"workload": "batch64: 64 instances, grids 32-80 per axis, 32-256 bands, 2-24 atoms x 18 "
+                               "projectors, %s" % ("Bloch k" if not args.real else "Gamma"),
+                   "instances": len(insts), "points_x_bands": units, "precision": args.precision,
+                   "launch": "one CUDA graph launch per batch step" if graph else "eager streams",
+                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (%.1f GB of bands per step)" % (
+                       2 * units * (8 if not args.real else 4) * (2 if args.precision == "fp64" else 1) / 1e9)},
+        "rr_steps_per_s": rr,
+        "latency_ms": {"p50": float(np.percentile(per_launch, 50)), "p99": float(np.percentile(per_launch, 99))},
+        "fp64_sequential": {"rr_steps_per_s": len(insts) / fp64_total if fp64_total else None,
+                            "seconds_per_batch_step": fp64_total,
+                            "how": "each instance alone, plain FP64 pawfd_rr_step, one after another"},
+        "speedup_vs_fp64_sequential": (rr / world) / (len(insts) / fp64_total) if fp64_total else None,
+        "autotuned": tuned,
+        "roofline": {"stage": "whole batch step", "kernel": "sliced_gram_kernel (Gram pair + rotation of all "
+                     "instances)", "bound": "tensor", "achieved": achieved / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                     "frac": achieved / (bf16 * 1e12), "traffic": None,
+                     "note": "BF16 digit-product work of all contractions / whole batch step time (a lower bound "
+                             "on the contraction kernels' own rate)"},
+        "gpu_launches": int(kernels * args.steps), "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_served(args):
+    """Poisson stream of eigensolver jobs through the continuous-batching server."""
+    import torch
+    from paper_2310_14776_gb300 import serve
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    systems = serve.catalogue(complex_wf=not args.real)
+    jobs = serve.job_stream(args.rate, args.serve_seconds, 64, 8, seed=4 + rank)
+    srv = serve.Server(systems, dev, precision=args.precision, iterations=5)
+    srv.prepare(sorted({j.system for j in jobs}))
+    clocks = ClockSampler(local)
+    clocks.start()
+    out = srv.run(jobs, duration=args.serve_seconds * 1.25 + 5.0)
+    clk = clocks.stop()
+    srv.close()
+    recs = out["records"]
+    steps_done = 5 * len(recs)
+    lat = serve.latency_stats(recs, warmup=args.serve_warmup)
+    lat_note = "jobs arriving after the warm-up window"
+    if not lat.get("jobs"):
+        # saturated stream served in arrival order: no job after the warm-up window finished
+        lat = serve.latency_stats(recs, warmup=0.0)
+        lat_note = "all completed jobs (none arriving after the warm-up window finished: the queue only grew)"
+    arrived = [j for j in jobs if j.arrival <= out["elapsed"]]
+    saturated = out["unfinished"] > 0
+    # plain FP64 sequential on a sample of the same mix: 8 small systems and 1 large one
+    small = [systems[i] for i in sorted({j.system for j in jobs if j.system < 64})[:8]]
+    large = [systems[i] for i in sorted({j.system for j in jobs if j.system >= 64})[:1]]
+    t_small = [fp64_step_seconds(inst, dev, srv.system(systems.index(inst))) for inst in small]
+    t_large = [fp64_step_seconds(inst, dev, srv.system(systems.index(inst))) for inst in large]
+    frac_large = sum(j.system >= 64 for j in jobs) / max(1, len(jobs))
+    t_job = 5 * ((1 - frac_large) * float(np.mean(t_small)) + (frac_large * float(np.mean(t_large)) if t_large else 0))
+    result = {
+        "metric": METRIC, "value_definition": "grid points x bands of completed Rayleigh-Ritz steps per second / 1e9",
+        "value": sum(5 * systems[r.job.system].npoints * systems[r.job.system].nbands for r in recs) / out["elapsed"] / 1e9,
+        "unit": UNIT, "n_gpus": 1, "steps": steps_done, "warmup": 0, "ms_per_step": out["elapsed"] / max(1, steps_done) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64" if (args.precision == "mixed" and not args.real) else "mixed",
+        "data": "synthetic (seeded catalogue of 72 systems; bands seeded per job on the device)",
+        "config": {"workload": "served: Poisson %.0f jobs/s for %.0f s, 5 RR iterations per job, 90%% batched-size "
+                               "systems and 10%% 128^3 x 512-band systems" % (args.rate, args.serve_seconds),
+                   "precision": args.precision, "hbm_budget_gb": out["budget"] / 1e9, "max_active": srv.sched.max_active,
+                   "parallelism": "single-gpu"},
+        "rr_steps_per_s": steps_done / out["elapsed"],
+        "latency_ms": {"p50": lat.get("p50_ms"), "p99": lat.get("p99_ms"), "jobs": lat.get("jobs"),
+                       "over": lat_note, "warmup_s": args.serve_warmup},
+        "jobs": {"arrived": len(arrived), "completed": len(recs), "unfinished_at_stop": out["unfinished"],
+                 "max_queue": out["max_queue"], "peak_hbm_gb": out["peak_used"] / 1e9,
+                 "budget_overruns": out["overruns"]},
+        "saturated": saturated,
+        "max_sustainable_jobs_per_s": len(recs) / out["elapsed"] if saturated else ">= %.0f" % args.rate,
+        "fp64_sequential": {"rr_steps_per_s": 5.0 / t_job if t_job else None, "seconds_per_job": t_job,
+                            "how": "plain FP64 pawfd_rr_step, one job at a time, on 8 small and %d large systems "
+                                   "of the stream, weighted by its large fraction %.3f" % (len(large), frac_large)},
+        "speedup_vs_fp64_sequential": (steps_done / out["elapsed"]) / (5.0 / t_job) if t_job else None,
+        "roofline": None, "gpu_launches": None, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
 
 
 # ------------------------------------------------------------------------------------------
@@ -314,14 +547,28 @@ def oracle_step_time(system, psi):
     return time.perf_counter() - t
 
 
-def cpu_baseline(system, psi, w):
+def oracle_sample(system, w, precision, budget=2.3e8):
+    """The bounded CPU sample of a workload: one full oracle Rayleigh-Ritz step on the first
+    nb_s bands, nb_s = all bands when K * nb <= budget (2.3e8 is the 96^3 x 256 workload,
+    about 20 s on 16 cores), else the most bands within the budget (at least 8)."""
+    nb_s = w.nbands if system.npoints * w.nbands <= budget else max(8, int(budget // system.npoints))
+    psi = w.psi(system, nb=nb_s)
+    if precision == "mixed":
+        psi = psi.astype(np.complex64 if system.complex_wf else np.float32)
+    psi = psi.astype(np.complex128 if system.complex_wf else np.float64)
+    return nb_s, psi
+
+
+def cpu_baseline(system, w, precision):
     from oracle import oracle as O
     O.build()
+    nb_s, psi = oracle_sample(system, w, precision)
     t = oracle_step_time(system, psi)
-    return {"value": system.npoints * w.nbands / t / 1e9, "unit": "Gpt.band/s", "cores": O.num_threads(),
+    return {"value": system.npoints * nb_s / t / 1e9, "unit": UNIT, "cores": O.num_threads(),
             "kind": "oracle", "seconds": t,
-            "sample": "one full Rayleigh-Ritz step of the %s workload (apply_H, apply_S, two Gram matrices, "
-                      "subspace diag, rotation) on the host cores" % w.name}
+            "sample": "one full FP64 Rayleigh-Ritz step (apply_H, apply_S, two Gram matrices, subspace diag, "
+                      "rotation) of the %s workload on %d of its %d bands, on the host cores"
+                      % (w.name, nb_s, w.nbands)}
 
 
 def run_reference(args):
@@ -330,25 +577,33 @@ def run_reference(args):
         return
     from oracle import oracle as O
     O.build()
+    if args.workload not in synth.WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the single-system workloads; "
+                          "%s is timed against sequential plain FP64 on the GPU inside its own line"
+                          % args.workload}), flush=True)
+        return
     w = synth.WORKLOADS[args.workload]
     system = w.system()
-    psi = w.psi(system)
+    # each reference step is a bounded sample (about 4 s on 16 cores at 96^3) so that the
+    # driver's warm-up + timed steps end within a few minutes
+    nb_s, psi = oracle_sample(system, w, args.precision, budget=5e7)
     for _ in range(args.warmup):
         oracle_step_time(system, psi)
     times = [oracle_step_time(system, psi) for _ in range(args.steps)]
     el = sum(times)
-    value = system.npoints * w.nbands * args.steps / el / 1e9
-    cb = {"value": value, "unit": "Gpt.band/s", "cores": O.num_threads(), "kind": "oracle",
-          "sample": "one full Rayleigh-Ritz step of the %s workload per step" % w.name}
+    value = system.npoints * nb_s * args.steps / el / 1e9
+    sample = ("one full FP64 Rayleigh-Ritz step of the %s workload on %d of its %d bands per step"
+              % (w.name, nb_s, w.nbands))
+    cb = {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample}
     print(json.dumps({
-        "impl": "reference", "metric": "H|psi> Gpt.band/s over whole Rayleigh-Ritz steps (apply_H + apply_S + "
-                                       "Gram + subspace diag + rotate)",
-        "value": value, "unit": "Gpt.band/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "impl": "reference", "metric": METRIC, "value_definition": VALUE_DEF,
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c128" if system.complex_wf else "f64", "data": "synthetic (seeded)",
         "config": {"workload": w.name, "grid": list(system.n), "bands": w.nbands, "atoms": system.natoms,
-                   "precision": "fp64"},
-        "cpu_baseline": cb, "e2e": {"value": value, "unit": "Gpt.band/s", "h2d_bytes_per_step": 0,
+                   "projectors_per_atom": int(system.nproj[0]) if system.natoms else 0,
+                   "precision": args.precision, "parallelism": "single-gpu"},
+        "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                                     "d2h_bytes_per_step": 0}}), flush=True)
 
 
@@ -356,6 +611,10 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_gpu(args)
 

@@ -105,7 +105,8 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
 
 /* Select among equivalent implementations (for tests and measurements):
  *   "tensor_cores"    1 (default): Gram matrices and rotations on the tensor cores with exact
- *                     digit slices; 0: FP64 / FP32 FMA kernels on the CUDA cores.
+ *                     digit slices; 0: FMA kernels on the CUDA cores (FP64 products for the FP64
+ *                     dtypes; FP32 products, about 1e-7 relative, for the FP32 dtypes).
  *   "stencil_variant" 0 (default): fastest kernel that applies to the shape; 1: skip the
  *                     bulk-copy ring kernel; 2: always the general kernel.
  *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,

@@ -1,11 +1,12 @@
 """Per-shape autotuner for the kernel choices of a context.
 
-Each candidate is a setting of ``pawfd_set_option`` that computes the same result (a
-different stencil tiling, or the tensor-core digit-product Gram and rotation against the
-FMA kernels).  Candidates are timed with CUDA events on the instance's own arrays, on the
-current stream, after one untimed call; the fastest setting is applied to the context and
-remembered per shape key (precision, kind, grid, bands, projector rows), so that instances
-of one shape are tuned once.
+Each candidate is a setting of ``pawfd_set_option`` that computes the same result to the
+context's tolerance: a different stencil tiling (bitwise the same output), or, for FP64
+data, the tensor-core digit-product Gram and rotation against the FP64 FMA kernels.
+Candidates are timed with CUDA events on the instance's own arrays, on the current stream,
+after one untimed call; the fastest setting is applied to the context and remembered per
+shape key (precision, kind, grid, bands, projector rows), so that instances of one shape are
+tuned once.
 """
 from __future__ import annotations
 
@@ -34,7 +35,13 @@ def stencil_candidates(ctx) -> List[Dict[str, int]]:
 
 
 def contraction_candidates(ctx) -> List[Dict[str, int]]:
-    return [{"tensor_cores": 1}, {"tensor_cores": 0}]
+    """Gram / rotation variants of equal accuracy.  For FP64 data both the digit-product
+    tensor-core kernels and the FP64 FMA kernels meet the FP64 tolerance.  For FP32 data the FMA
+    kernels form FP32 products (about 1e-7 relative), far less accurate than the exact digit
+    products, so the mixed form keeps the tensor-core path."""
+    if ctx.precision == "fp64":
+        return [{"tensor_cores": 1}, {"tensor_cores": 0}]
+    return []
 
 
 def _time(fn, reps: int) -> float:
@@ -84,9 +91,11 @@ def tune(ctx, psi: torch.Tensor, work: dict, reps: int = 2, use_cache: bool = Tr
             ctx.gram(psi, work["Hpsi"], M=work["Hnm"], hermitian=True)
             ctx.rotate(psi, work["C"], out=tmp)
 
-        g, _ = _best(ctx, contraction_candidates(ctx), contraction, reps)
-        if g:
-            best.update(g)
+        cands = contraction_candidates(ctx)
+        if cands:
+            g, _ = _best(ctx, cands, contraction, reps)
+            if g:
+                best.update(g)
         _CACHE[key] = best
     for k, v in best.items():
         ctx.set_option(k, v)

@@ -322,7 +322,9 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
   if (rc == PAWFD_OK && c->use_tc) rc = setup_tc(c);
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_barrier, 0, 4 * sizeof(unsigned)), "memset");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_status, 0, sizeof(DeviceStatus)), "memset");
-  if (rc == PAWFD_OK) rc = check_cuda(c, cudaDeviceSynchronize(), "create sync");
+  // the uploads and memsets above ran on the legacy default stream: wait for those only, not
+  // for other work on the device (a server creates contexts while jobs run on their streams)
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamSynchronize(cudaStreamLegacy), "create sync");
   if (rc != PAWFD_OK) {
     fprintf(stderr, "pawfd_create: %s\n", c->err.c_str());
     free_ctx(c);

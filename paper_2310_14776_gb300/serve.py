@@ -178,10 +178,32 @@ class Server:
             self._sys_cache[sysid] = self.systems[sysid].system()
         return self._sys_cache[sysid]
 
-    def prepare(self, sysids: Sequence[int]):
-        """Build the host-side systems ahead of time (not part of any job's latency)."""
+    def prepare(self, sysids: Sequence[int], contexts: bool = True):
+        """Ahead of the stream (not part of any job's latency): build the host-side systems
+        and, with `contexts`, one pooled context per system, tuned for its shape, while the
+        budget allows (smallest first)."""
+        torch = self.torch
         for s in sysids:
             self.system(s)
+        if not contexts:
+            return
+        for s in sorted(sysids, key=lambda i: array_bytes(self.systems[i], self.precision)):
+            inst = self.systems[s]
+            if self._ctx_estimate(s) + array_bytes(inst, self.precision) > self.sched.free_bytes():
+                continue
+            ctx, cbytes, _ = self._get_ctx(s)
+            if self.tune:
+                from . import autotune
+                psi = self._bands(inst, inst.seed, torch.cuda.current_stream(self.device))
+                work = ctx.alloc_work(inst.nbands)
+                work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=self.device))
+                autotune.tune(ctx, psi, work)
+                del psi, work
+            self.pool[s].append((ctx, cbytes))
+            self.idle_lru[(s, id(ctx))] = True
+            self.sched.used += cbytes
+        torch.cuda.synchronize(self.device)
+        torch.cuda.empty_cache()
 
     def _ctx_estimate(self, sysid: int) -> int:
         if sysid in self.ctx_bytes:
@@ -219,9 +241,14 @@ class Server:
             self.idle_lru.pop((sysid, id(ctx)), None)
             return ctx, nbytes, False
         inst = self.systems[sysid]
-        torch.cuda.synchronize(self.device)
         f0, _ = torch.cuda.mem_get_info(self.device)
-        ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
+        try:
+            ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
+        except api.PawFDError:
+            # the library allocates with cudaMalloc: give back what torch's cache holds, once
+            torch.cuda.empty_cache()
+            f0, _ = torch.cuda.mem_get_info(self.device)
+            ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
         f1, _ = torch.cuda.mem_get_info(self.device)
         nbytes = max(0, f0 - f1)
         self.ctx_bytes[sysid] = max(nbytes, self.ctx_bytes.get(sysid, 0))
@@ -252,7 +279,8 @@ class Server:
             work = ctx.alloc_work(inst.nbands)
             if self.tune:
                 from . import autotune
-                work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=self.device))
+                if autotune.shape_key(ctx, inst.nbands) not in autotune._CACHE:
+                    work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=self.device))
                 autotune.tune(ctx, psi, work)
             bufs = [psi, out]
             for it in range(self.iterations):
