@@ -40,6 +40,30 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe kernel on this machine
 
 
+# Measured DRAM traffic per unit of the dominant stage's kernels (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum on a small case, profiles/dram_apply_H_fp64_64c_128b.md), valid only
+# while the kernels' sources are the ones that were measured.
+TRAFFIC = {
+    ("apply_H", "fp64", False): {
+        "per_point_band": 15.89, "per_atom_band": 38585.0,
+        "sources": {"paper_2310_14776_gb300/csrc/stencil.cu": "9aee46d1fbc4aa43a9d6ab9eafebff03b565df86",
+                    "paper_2310_14776_gb300/csrc/nonlocal.cu": "6322b1ed8ccada121d05dbddc6446954e8a3cab2"}},
+}
+
+
+def stage_traffic(stage, precision, cplx, K, nb, natoms):
+    """DRAM bytes of one launch of the stage, scaled from the measured small case, or None."""
+    import hashlib
+    t = TRAFFIC.get((stage, precision, cplx))
+    if t is None:
+        return None
+    for path, sha in t["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    return t["per_point_band"] * K * nb + t["per_atom_band"] * natoms * nb
+
+
 def parse_args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -56,6 +80,7 @@ def parse_args():
     p.add_argument("--serve-seconds", type=float, default=60.0, help="served: length of the arrival stream")
     p.add_argument("--serve-warmup", type=float, default=5.0, help="served: arrivals before this are excluded")
     p.add_argument("--real", action="store_true", help="batch64 / served: real (Gamma) instead of Bloch instances")
+    p.add_argument("--no-refine", action="store_true", help="mixed: skip the final FP64 refinement measurement")
     a = p.parse_args()
     if a.precision is None:
         a.precision = "mixed" if a.workload in ("batch64", "served") else "fp64"
@@ -266,7 +291,9 @@ def run_gpu(args):
         "apply_H_gptband_s": nb * K / (stages["apply_H"] * 1e-3) / 1e9,
         "eig_drift_ha": drift,
         "roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
-                     "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak, "traffic": None,
+                     "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,
+                     "traffic": stage_traffic(dom, args.precision, cplx, K, nb, system.natoms),
+                     "traffic_unit": "DRAM bytes per stage launch (ncu, scaled from 64^3 x 128)",
                      "peak_source": {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst)",
                                      "hbm": "MEASURED_PEAKS.json hbm_gbs",
                                      "alu": "nominal GB300 FP64 rate 1.25 TFLOP/s / 2 (FMA)"}[bound]},
@@ -276,6 +303,15 @@ def run_gpu(args):
 
     if not args.no_e2e:
         result["e2e"] = e2e_gpu(ctx, psi_host, work, args, dev)
+    if mixed and not args.no_refine:
+        latest = psi[(args.warmup + args.steps) % 2]
+        eps_mixed = work["eps"].clone()
+        # room for the FP64 arrays: drop the mixed step's own H psi, S psi and the other buffer
+        for key in ("Hpsi", "Spsi"):
+            work[key] = None
+        psi[(args.warmup + args.steps + 1) % 2] = None
+        torch.cuda.empty_cache()
+        result["refine"] = refine_gpu(system, nb, latest, eps_mixed, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, w, args.precision)
     if world > 1:
@@ -285,6 +321,31 @@ def run_gpu(args):
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def refine_gpu(system, nb, psi_lo, eps_mixed, dev):
+    """The final FP64 refinement (pawfd_refine) of the last rotated mixed-form bands, timed."""
+    import torch
+    from paper_2310_14776_gb300 import api
+    fp = api.Context(system, max_bands=nb, device=dev, precision="fp64")
+    fp.refine(psi_lo)              # untimed first call
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fp.refine(psi_lo, check=False)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    fp.sync()
+    eps = out["eps"]
+    res = {"ms": e0.elapsed_time(e1), "max_abs_eps_refined_minus_mixed_ha": float((eps - eps_mixed).abs().max()),
+           "max_abs_theta_minus_eps_ha": float((out["theta"] - eps).abs().max()),
+           "max_residual_norm": float(out["resid"].max()), "median_residual_norm": float(out["resid"].median()),
+           "what": "promote psi' to FP64, FP64 H psi' and S psi', Hermitian Grams, Rayleigh quotients, second "
+                   "subspace solve, residual norms ||H psi'_n - eps_n S psi'_n||"}
+    fp.close()
+    del out
+    torch.cuda.empty_cache()
+    return res
 
 
 def device_bands(ctx, nb, seed):
