@@ -114,6 +114,11 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
  *   "stencil_zsplit"  general stencil kernel: the z range is split so that one launch has at
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
+ *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 256 (0: the whole
+ *                     slice buffer, 512 units); shorter blocks keep the digit slices in L2.
+ *   "tc_fused"        0 (default): digit planes are sliced to memory, then multiplied; 1: the
+ *                     tensor-core Gram makes its digits inside the MMA kernel from the raw
+ *                     operands (when their rows are 16-byte aligned).  Same digits, same products.
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.

@@ -374,6 +374,14 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
+  if (n == "tc_fused" && (value == 0 || value == 1)) {
+    c->tc_fused = value == 1;
+    return PAWFD_OK;
+  }
+  if (n == "tc_kblk" && value >= 0 && value <= 4096) {
+    c->tc_kblk_chunks = value;
+    return PAWFD_OK;
+  }
   if (n == "stencil_zsplit" && value >= 0 && value <= 64) {
     c->stencil_zsplit = value;
     return PAWFD_OK;

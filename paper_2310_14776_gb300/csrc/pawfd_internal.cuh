@@ -157,6 +157,12 @@ struct TcScratch {
   int* rotMaxB = nullptr;
   CUtensorMap rotMapA;
   CUtensorMap rotMapB;
+  // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
+  long long fnch = 0;          // chunks per row
+  int* fsigA = nullptr;        // [fnch][max_bands]
+  int* fsigB = nullptr;
+  int* fmaxA = nullptr;        // [max_bands] largest exponent of each row
+  int* fmaxB = nullptr;
 };
 
 }  // namespace pawfd
@@ -188,6 +194,8 @@ struct pawfd_ctx {
   int stencil_yblock = 0;                     // y rows per thread of the ring kernel (0: automatic)
   int stencil_zsplit = 0;                     // general stencil: target CTAs per SM of a launch (0: 4)
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
+  int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 256-value chunks (0: allocation)
+  bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   pawfd::TcScratch tc;
   std::string err;
 };

@@ -156,55 +156,24 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
 
 // Transposing slicer for the band rotation: operand rows are grid points r, the contraction
 // index k runs over the bands (real: k = n; complex: k = 2 n + c, c = 0 real / 1 imaginary
-// part).  One CTA per (16 grid points, chunk of KC contraction values): the [KC][16] tile is
-// read along r, the largest exponent of every grid point's chunk found, and the digits
-// written along k.  out: [S][out_rows][Lp]; sig: [nchunks][sig_ld] (sig_ld >= rows).
+// part).  One CTA per (16 grid points, chunk of KC contraction values): the tile is read along
+// r (coalesced), kept transposed in shared memory, the largest exponent of every grid point's
+// chunk found, and each thread turns 8 consecutive k of one grid point into S 16-byte digit
+// groups (a warp writes 512 contiguous bytes of a plane).  out: [S][out_rows][Lp];
+// sig: [nchunks][sig_ld] (sig_ld >= rows).
 constexpr int RT = 16;
 
-template <class R, int S>
-__global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
-                                                      long long r0, int rcount, long long Lp, int out_rows,
-                                                      __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
-                                                      int sig_ld, int* __restrict__ sigmax) {
-  __shared__ R tile[KC][RT + 1];
-  __shared__ int pmax[16][RT];
-  const int rt = blockIdx.x, c = blockIdx.y;
-  const int tid = threadIdx.x, lr = tid % RT, kq = tid / RT;
-  const long long Lk = (long long)nb * (cplx ? 2 : 1);
-  const int rl0 = rt * RT;   // first local grid point of this CTA
-  for (int kk = kq; kk < KC; kk += 16) {
-    const long long k = (long long)c * KC + kk;
-    R v = R(0);
-    if (k < Lk && rl0 + lr < rcount) {
-      const long long n = cplx ? (k >> 1) : k;
-      const long long e = (n * K + r0 + rl0 + lr) * (cplx ? 2 : 1) + (cplx ? (k & 1) : 0);
-      v = psi[e];
-    }
-    tile[kk][lr] = v;
-  }
-  __syncthreads();
-  int em = 0;
-  for (int kk = kq; kk < KC; kk += 16) em = max(em, fields(tile[kk][lr]).exp);
-  pmax[kq][lr] = em;
-  __syncthreads();
-  constexpr int bias = FloatBits<R>::bias, nbits = FloatBits<R>::nb;
-  constexpr int g = 7 * S - 1 - nbits;
-  if (tid < RT) {
-    int m = 0;
-    for (int q = 0; q < 16; ++q) m = max(m, pmax[q][tid]);
-    pmax[0][tid] = m;
-    if (rl0 + tid < rcount) {
-      sig[(long long)c * sig_ld + rl0 + tid] = m - bias - 5;
-      atomicMax(sigmax + rl0 + tid, m - bias - 5);
-    }
-  }
-  __syncthreads();
-  const int w = tid >> 5, lane = tid & 31;
-  for (int q = w; q < RT; q += 8) {
-    if (rl0 + q >= rcount) break;
-    const int emax = pmax[0][q];
-    for (int kk = lane; kk < KC; kk += 32) {
-      const Fields f = fields(tile[kk][q]);
+// 8 values -> S planes of 8 bf16 digits (out[i][j]: plane i, values 2j, 2j+1), relative to the
+// chunk's largest biased exponent emax (the digit scale of slice_kernel).
+template <int S>
+__device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32_t (&out)[S][4]) {
+  constexpr int nbits = 52, g = 7 * S - 1 - nbits;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    float dv[S][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const Fields f = fields(x[2 * p + u]);
       unsigned long long G = 0;
       const int sh = emax - f.exp + 1;
       const int rs = sh - g;
@@ -219,11 +188,102 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
           d[i - 1] += 1;
         }
 #pragma unroll
-      for (int i = 0; i < S; ++i) {
-        const float v = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
-        out[((long long)i * out_rows + rl0 + q) * Lp + (long long)c * KC + kk] = __float2bfloat16_rn(v);
+      for (int i = 0; i < S; ++i) dv[i][u] = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      uint32_t r;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(dv[i][1]), "f"(dv[i][0]));
+      out[i][p] = r;
+    }
+  }
+}
+
+// FP32 values: y = x 2^-sigma (|y| < 64), d_i = rint(y_i), y_{i+1} = 128 (y_i - d_i), all exact
+// in FP32; the digits are balanced by construction.
+template <int S>
+__device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_t (&out)[S][4]) {
+  const int sigma = emax - 127 - 5;
+  const float scale = (sigma > 126 || sigma < -126) ? 0.0f : __int_as_float((127 - sigma) << 23);
+  float y[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) y[v] = x[v] * scale;
+#pragma unroll
+  for (int i = 0; i < S; ++i) {
+    float d[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      d[v] = rintf(y[v]);
+      y[v] = (y[v] - d[v]) * 128.0f;
+    }
+    const float w = __int_as_float((127 - 7 * i) << 23);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t r;
+      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(d[2 * j + 1] * w), "f"(d[2 * j] * w));
+      out[i][j] = r;
+    }
+  }
+}
+
+template <class R, int S>
+__global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
+                                                      long long r0, int rcount, long long Lp, int out_rows,
+                                                      __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
+                                                      int sig_ld, int* __restrict__ sigmax) {
+  constexpr int PITCH = KC + 16 / (int)sizeof(R);   // 16-byte aligned rows: vector reads, few conflicts
+  __shared__ __align__(16) R tile[RT][PITCH];     // [grid point][k]
+  __shared__ int pmax[16][RT];
+  const int rt = blockIdx.x, c = blockIdx.y;
+  const int tid = threadIdx.x, lr = tid % RT, kq = tid / RT;
+  const long long Lk = (long long)nb * (cplx ? 2 : 1);
+  const int rl0 = rt * RT;   // first local grid point of this CTA
+  int em = 0;
+  for (int kk = kq; kk < KC; kk += 16) {
+    const long long k = (long long)c * KC + kk;
+    R v = R(0);
+    if (k < Lk && rl0 + lr < rcount) {
+      const long long n = cplx ? (k >> 1) : k;
+      const long long e = (n * K + r0 + rl0 + lr) * (cplx ? 2 : 1) + (cplx ? (k & 1) : 0);
+      v = psi[e];
+    }
+    tile[lr][kk] = v;
+    em = max(em, fields(v).exp);
+  }
+  pmax[kq][lr] = em;
+  __syncthreads();
+  if (tid < RT) {
+    int m = 0;
+    for (int q = 0; q < 16; ++q) m = max(m, pmax[q][tid]);
+    pmax[0][tid] = m;
+    if (rl0 + tid < rcount) {
+      sig[(long long)c * sig_ld + rl0 + tid] = m - FloatBits<R>::bias - 5;
+      atomicMax(sigmax + rl0 + tid, m - FloatBits<R>::bias - 5);
+    }
+  }
+  __syncthreads();
+  // items: (grid point q, 8 consecutive k); consecutive threads take consecutive k groups
+  for (int item = tid; item < RT * (KC / 8); item += 256) {
+    const int q = item / (KC / 8), k8 = (item % (KC / 8)) * 8;
+    if (rl0 + q >= rcount) continue;
+    R x[8];
+    if constexpr (sizeof(R) == 4) {
+      const float4 a0 = *(const float4*)&tile[q][k8], a1 = *(const float4*)&tile[q][k8 + 4];
+      x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w; x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
+    } else {
+#pragma unroll
+      for (int v = 0; v < 8; v += 2) {
+        const double2 a2 = *(const double2*)&tile[q][k8 + v];
+        x[v] = a2.x;
+        x[v + 1] = a2.y;
       }
     }
+    uint32_t o[S][4];
+    digits8_t<S>(x, pmax[0][q], o);
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      *(uint4*)(out + ((long long)i * out_rows + rl0 + q) * Lp + (long long)c * KC + k8) =
+          make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
   }
 }
 
@@ -243,6 +303,7 @@ struct GramArgs {
   int half_rows = 0;        // rows per half of B (complex: nb)
   int chunks_per_cta = 0;
   int nchunks = 0;          // chunks in this K block
+  long long klen = 0;       // valid contraction values in this K block (0: all full chunks)
   int accumulate = 0;       // add to part instead of overwriting it (second and later K blocks)
   double* part = nullptr;         // [nsplit][rowsA][rowsB]
   DeviceStatus* st = nullptr;
@@ -255,6 +316,7 @@ struct GramArgs {
   int rot_fp32 = 0;
   long long rot_K = 0;  // grid points per band
   void* rot_out = nullptr;        // band array, already offset to the first grid point of the block
+  int rot_vec = 0;                // real bands with 16-byte aligned rows: vector stores
 };
 
 // 2^e for the product scale; below the normal range the chunk contributes nothing (its
@@ -324,7 +386,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
   const int nch = max(0, c_end - c_begin);
   const int steps_per_chunk = KC / BK;
-  const int total_steps = nch * steps_per_chunk;
+  // stages of chunk c (the last chunk of a block may hold fewer than KC valid values: no MMAs
+  // on its zero padding)
+  auto steps_of = [&](int c) {
+    if (a.klen <= 0) return steps_per_chunk;
+    const long long left = a.klen - (long long)(c_begin + c) * KC;
+    return (int)max(1ll, min((long long)steps_per_chunk, (left + BK - 1) / BK));
+  };
+  int total_steps = 0;
+  for (int c = 0; c < nch; ++c) total_steps += steps_of(c);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -346,6 +416,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
 
   if (warp == EPI_WARPS) {
     if (lane == 0) {   // TMA producer: S slices of A and S slices of B per stage
+      int c = 0, q = 0;
       for (int g = 0; g < total_steps && !abort_flag; ++g) {
         const int s = g % STAGES;
         if (g >= STAGES && !tc::mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
@@ -353,7 +424,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           set_status(a.st, PAWFD_ETIMEDOUT, 1001);
           break;
         }
-        const int kx = (c_begin + g / steps_per_chunk) * KC + (g % steps_per_chunk) * BK;
+        const int kx = (c_begin + c) * KC + q * BK;
+        if (++q == steps_of(c)) {
+          q = 0;
+          ++c;
+        }
         unsigned char* sa = smem + s * stage_bytes<S>();
         unsigned char* sb = sa + S * a_slice_bytes<S>();
         tc::mbar_expect_tx(&full[s], stage_bytes<S>());
@@ -365,6 +440,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   } else if (warp == EPI_WARPS + 1) {
     if (lane == 0) {   // MMA issuer
       constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+      int g = 0;
       for (int c = 0; c < nch && !abort_flag; ++c) {
         if (c > 0 && !tc::mbar_wait(&dempty, (c - 1) & 1)) {
           abort_flag = 1;
@@ -372,8 +448,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           break;
         }
         tc::fence_after_sync();
-        for (int q = 0; q < steps_per_chunk && !abort_flag; ++q) {
-          const int g = c * steps_per_chunk + q;
+        const int steps = steps_of(c);
+        for (int q = 0; q < steps && !abort_flag; ++q, ++g) {
           const int s = g % STAGES;
           if (!tc::mbar_wait(&full[s], (g / STAGES) & 1)) {
             abort_flag = 1;
@@ -460,14 +536,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       if (row < a.rowsA && !abort_flag) {
         const int band = row % a.rot_nb, part = row / a.rot_nb;
         const long long base = (long long)band * a.rot_K;
+        if (a.rot_vec) {
+          // real bands, 16-byte aligned rows: 4 (FP32) or 2 (FP64) values per store
 #pragma unroll
-        for (int j = 0; j < EPI_COLS; ++j) {
-          const int col = col0 + cbase + j;
-          if (col < a.rowsB) {
-            const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
-            const long long idx = a.rot_cplx ? 2 * (base + col) + part : base + col;
-            if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v;
-            else ((double*)a.rot_out)[idx] = v;
+          for (int j = 0; j < EPI_COLS; j += 4) {
+            const int col = col0 + cbase + j;
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              v[u] = col + u < a.rowsB ? ((double)ahi[j + u] + (double)alo[j + u]) * pow2(ra + __ldg(a.maxB + col + u))
+                                       : 0.0;
+            if (col + 3 < a.rowsB) {
+              if (a.rot_fp32) {
+                *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+              } else {
+                *(double2*)((double*)a.rot_out + base + col) = make_double2(v[0], v[1]);
+                *(double2*)((double*)a.rot_out + base + col + 2) = make_double2(v[2], v[3]);
+              }
+            } else {
+              for (int u = 0; u < 4 && col + u < a.rowsB; ++u) {
+                if (a.rot_fp32) ((float*)a.rot_out)[base + col + u] = (float)v[u];
+                else ((double*)a.rot_out)[base + col + u] = v[u];
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < EPI_COLS; ++j) {
+            const int col = col0 + cbase + j;
+            if (col < a.rowsB) {
+              const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
+              const long long idx = a.rot_cplx ? 2 * (base + col) + part : base + col;
+              if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v;
+              else ((double*)a.rot_out)[idx] = v;
+            }
           }
         }
       }
