@@ -116,6 +116,9 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
  *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 256 (0: the whole
  *                     slice buffer, 512 units); shorter blocks keep the digit slices in L2.
+ *   "stencil_df"      1 (default): the real FP64 stencil computes in double-float FP32 pairs
+ *                     (about 48 bits, well inside the FP64 tolerance; far faster than the FP64
+ *                     pipe); 0: FP64 arithmetic.  "stencil_variant" 2 also selects FP64.
  *   "tc_fused"        0 (default): digit planes are sliced to memory, then multiplied; 1: the
  *                     tensor-core Gram makes its digits inside the MMA kernel from the raw
  *                     operands (when their rows are 16-byte aligned).  Same digits, same products.

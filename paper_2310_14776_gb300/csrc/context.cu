@@ -245,7 +245,8 @@ void free_ctx(pawfd_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
-                  c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce};
+                  c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
+                  c->d_vshift_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -298,6 +299,17 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
       double* p = dev_alloc<double>(c, c->K, &rc);
       upload(c, p, vs.data(), c->K, &rc);
       c->d_vshift = p;
+      if (c->dtype == PAWFD_R64) {
+        // the same values as (hi, lo) FP32 pairs for the double-float stencil
+        std::vector<float> df(2 * c->K);
+        for (size_t r = 0; r < c->K; ++r) {
+          df[2 * r] = (float)vs[r];
+          df[2 * r + 1] = (float)(vs[r] - (double)df[2 * r]);
+        }
+        float* q = dev_alloc<float>(c, 2 * c->K, &rc);
+        upload(c, q, df.data(), 2 * c->K, &rc);
+        c->d_vshift_df = q;
+      }
     }
   }
   if (rc == PAWFD_OK) rc = build_tables(c, d);
@@ -372,6 +384,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
   }
   if (n == "jacobi_cluster" && (value == 0 || value == 1)) {
     c->jacobi_cluster = value == 1;
+    return PAWFD_OK;
+  }
+  if (n == "stencil_df" && (value == 0 || value == 1)) {
+    c->stencil_df = value == 1;
     return PAWFD_OK;
   }
   if (n == "tc_fused" && (value == 0 || value == 1)) {

@@ -175,6 +175,7 @@ struct pawfd_ctx {
   size_t K;
   cudaStream_t stream;
   void* d_vshift = nullptr;                   // v(r) - 1/2 c0 sum_c 1/h_c^2 (double or float)
+  void* d_vshift_df = nullptr;                // real FP64: the same as (hi, lo) FP32 pairs
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_gram_part = nullptr;                // split-K partial Gram matrices
@@ -196,6 +197,7 @@ struct pawfd_ctx {
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 256-value chunks (0: allocation)
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
+  bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
   pawfd::TcScratch tc;
   std::string err;
 };

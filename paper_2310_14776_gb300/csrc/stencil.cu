@@ -151,8 +151,12 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
 
 int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out);
 int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out);
+int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out);
 
 int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
+  if (c->dtype == PAWFD_R64 && c->stencil_df && c->fast_stencil &&
+      launch_kinetic_local_df(c, (const double*)psi, nb, (double*)out) == PAWFD_OK)
+    return PAWFD_OK;
   if (c->dtype == PAWFD_R32 && c->fast_stencil) {
     if (c->stencil_variant != 1 && launch_kinetic_local_ring(c, (const float*)psi, nb, (float*)out) == PAWFD_OK)
       return PAWFD_OK;

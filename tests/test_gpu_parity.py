@@ -109,6 +109,9 @@ def test_bloch_small_full_step(dev):
     dict(n=(5, 6, 4), cell=(2.5, 3.0, 2.0), natoms=2, pset=synth.PSET_SP, nb=3, cplx=True),
     # one band, no atoms
     dict(n=(16, 9, 7), cell=(6.0, 4.0, 3.0), natoms=0, pset=synth.PSET_SP, nb=1, cplx=False),
+    # real FP64 grid served by the double-float stencil: three x tiles (the last ragged), y and
+    # z wrapping inside the tile loop
+    dict(n=(77, 30, 9), cell=(15.0, 6.0, 1.9), natoms=3, pset=synth.PSET_SPD2, nb=4, cplx=False),
     # odd band count (Jacobi pads the pairing), many overlapping boxes
     dict(n=(24, 20, 18), cell=(6.0, 5.0, 4.5), natoms=12, pset=synth.PSET_SPD2, nb=17, cplx=True),
 ])
@@ -133,6 +136,28 @@ def test_hermitian_gram_equals_full_gram(dev, cplx):
     assert_close_matrix(herm, full)
     ref = O.gram(synth.make_psi(s, nb, 502), O.apply_H(s, synth.make_psi(s, nb, 502))[0], s.dV, nb)
     assert_close_matrix(herm, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [(45, 19, 13), (96, 40, 10), (40, 14, 3)])
+def test_double_float_stencil_matches_fp64_arithmetic(dev, n):
+    # the real FP64 stencil in double-float FP32 pairs against the FP64-pipe kernel: per band
+    # within 1e-13 of the band norm (the pairs carry about 48 bits)
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system(n, tuple(0.21 * v for v in n), 2, synth.PSET_SP, seed=330)
+    nb = 6
+    ctx = api.Context(s, max_bands=nb, device=dev, precision="fp64")
+    psi = to_dev(synth.make_psi(s, nb, 331), dev)
+    ctx.set_option("stencil_df", 1)
+    a = ctx.kinetic_local(psi).clone()
+    ctx.set_option("stencil_df", 0)
+    b = ctx.kinetic_local(psi).clone()
+    ctx.sync()
+    d = (a - b).reshape(nb, -1).norm(dim=1) / b.reshape(nb, -1).norm(dim=1)
+    assert d.max().item() <= 1e-13, d.max().item()
+    ref = O.kinetic_local(s, synth.make_psi(s, nb, 331))
+    e = np.linalg.norm((a.cpu().numpy() - ref).reshape(nb, -1), axis=1) / np.linalg.norm(ref.reshape(nb, -1), axis=1)
+    assert e.max() <= 1e-13
     ctx.close()
 
 
