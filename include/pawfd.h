@@ -112,6 +112,7 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,
  *                     at most 64 (clamped further by the kernel's thread and memory limits).
  *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
+ *   "stencil_ring"    ring stencil: planes in flight + in use, 0 (default 8), 8, 10 or 12.
  *   "stencil_zsplit"  general stencil kernel: the z range is split so that one launch has at
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
  *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 256 (0: the whole

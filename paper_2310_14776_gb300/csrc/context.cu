@@ -398,6 +398,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->tc_kblk_chunks = value;
     return PAWFD_OK;
   }
+  if (n == "stencil_ring" && (value == 0 || value == 8 || value == 10 || value == 12)) {
+    c->stencil_ring = value;
+    return PAWFD_OK;
+  }
   if (n == "stencil_zsplit" && value >= 0 && value <= 64) {
     c->stencil_zsplit = value;
     return PAWFD_OK;

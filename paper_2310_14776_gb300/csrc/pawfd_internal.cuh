@@ -194,6 +194,7 @@ struct pawfd_ctx {
   int stencil_rows = 0;                       // y rows per CTA of the ring kernel (0: automatic)
   int stencil_yblock = 0;                     // y rows per thread of the ring kernel (0: automatic)
   int stencil_zsplit = 0;                     // general stencil: target CTAs per SM of a launch (0: 4)
+  int stencil_ring = 0;                       // ring stencil: planes in the ring (0: 8; 8, 10 or 12)
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 256-value chunks (0: allocation)
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel

@@ -27,7 +27,6 @@
 namespace pawfd {
 namespace {
 
-constexpr int RING = 8;          // planes in the shared-memory ring
 constexpr int PAD = 4;           // floats of padding after each staged row
 
 struct RingArgs {
@@ -73,7 +72,7 @@ struct Consumer {
 
 // One z step for ring plane j (the queue's new entry z + 3); the centre plane is j - 3.
 // Queue rotation B: q[(B + i) % 7][r] holds row r of plane z - 3 + i.
-template <int B, int R>
+template <int B, int R, int RING>
 __device__ __forceinline__ bool consume(Consumer<R>& c, const RingArgs& a, int j, int jend, float4 (&q)[7][R]) {
   const int s = (unsigned)j % RING, sc = (unsigned)(j - 3) % RING;
   // the potential of the next z step is loaded one step ahead (an L2 round trip per step)
@@ -148,7 +147,7 @@ constexpr int max_threads() {
 // 1-D block: a.ncw consumer warps (thread t -> rows R (t / N1v) .. + R - 1, float4 column
 // t % N1v) and one producer warp.  Dynamic shared memory: RING planes of (BY + 6) rows x
 // pitch floats.  BY is a multiple of R.
-template <int R>
+template <int R, int RING>
 __global__ void __launch_bounds__(max_threads<R>(), 1)
     kinetic_local_ring_kernel(const float* __restrict__ psi, float* __restrict__ out, RingArgs a) {
   extern __shared__ __align__(128) float ring[];
@@ -252,7 +251,7 @@ __global__ void __launch_bounds__(max_threads<R>(), 1)
   const int jend = nplanes;
 #define PAWFD_RING_STEP(B)                     \
   if (ok && j < jend) {                        \
-    ok = consume<B, R>(c, a, j, jend, q);            \
+    ok = consume<B, R, RING>(c, a, j, jend, q);      \
     ++j;                                       \
   }
   while (ok && j < jend) {
@@ -268,7 +267,7 @@ __global__ void __launch_bounds__(max_threads<R>(), 1)
   if (!ok && (tid & 31) == 0) set_status(a.st, PAWFD_ETIMEDOUT, 2001);
 }
 
-template <int R>
+template <int R, int RING>
 int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, int rows_hint) {
   // rows per CTA: a multiple of R within the thread limit and ~100 KB of ring
   const int max_rows = R * ((max_threads<R>() - 32) / a.n1v);
@@ -286,7 +285,7 @@ int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, 
   int nzc = (int)std::max(1ll, std::min<long long>(want, (a.n3 + 15) / 16));
   a.zchunk = (a.n3 + nzc - 1) / nzc;
   a.nzc = (a.n3 + a.zchunk - 1) / a.zchunk;
-  int rc = check_cuda(c, cudaFuncSetAttribute(kinetic_local_ring_kernel<R>,
+  int rc = check_cuda(c, cudaFuncSetAttribute(kinetic_local_ring_kernel<R, RING>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                       "ring smem attribute");
   if (rc != PAWFD_OK) return rc;
@@ -294,7 +293,7 @@ int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, 
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gy, nbl * a.nzc), block(32 * (a.ncw + 1));
-    kinetic_local_ring_kernel<R><<<grid, block, smem, c->stream>>>(psi + (size_t)b0 * c->K,
+    kinetic_local_ring_kernel<R, RING><<<grid, block, smem, c->stream>>>(psi + (size_t)b0 * c->K,
                                                                     out + (size_t)b0 * c->K, a);
     c->launches += 1;
   }
@@ -327,10 +326,25 @@ int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out
   // (several CTAs per SM, each with deep register reuse) beat every other combination
   const int yb = c->stencil_yblock > 0 ? c->stencil_yblock : 3;
   const int rows = c->stencil_rows > 0 ? c->stencil_rows : yb * std::max(1, (96 + a.n1v / 2) / a.n1v);
+  const int depth = c->stencil_ring > 0 ? c->stencil_ring : 8;
+  if (depth == 10) {
+    switch (yb) {
+      case 1: return launch_ring<1, 10>(c, psi, nb, out, a, rows);
+      case 2: return launch_ring<2, 10>(c, psi, nb, out, a, rows);
+      default: return launch_ring<3, 10>(c, psi, nb, out, a, rows);
+    }
+  }
+  if (depth == 12) {
+    switch (yb) {
+      case 1: return launch_ring<1, 12>(c, psi, nb, out, a, rows);
+      case 2: return launch_ring<2, 12>(c, psi, nb, out, a, rows);
+      default: return launch_ring<3, 12>(c, psi, nb, out, a, rows);
+    }
+  }
   switch (yb) {
-    case 1: return launch_ring<1>(c, psi, nb, out, a, rows);
-    case 2: return launch_ring<2>(c, psi, nb, out, a, rows);
-    default: return launch_ring<3>(c, psi, nb, out, a, rows);
+    case 1: return launch_ring<1, 8>(c, psi, nb, out, a, rows);
+    case 2: return launch_ring<2, 8>(c, psi, nb, out, a, rows);
+    default: return launch_ring<3, 8>(c, psi, nb, out, a, rows);
   }
 }
 
