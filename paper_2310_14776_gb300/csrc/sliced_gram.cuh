@@ -108,6 +108,12 @@ __device__ __forceinline__ R slice_input(const R* __restrict__ src, long long ld
 // are ld apart, len values per row are valid (the rest of the Lp-long block is zero).
 // out: [S][out_rows][Lp] bf16 scaled digits (rows placed at row_offset); sig: [nchunks][sig_ld];
 // sigmax[row] (reset by the caller for every block) receives the largest sigma of the row.
+// Each lane takes 8 consecutive values of the 256-value chunk and writes 16 bytes per plane.
+template <int S>
+__device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32_t (&out)[S][4]);
+template <int S>
+__device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_t (&out)[S][4]);
+
 template <class R, int S>
 __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
                                                     int nchunks, long long Lp, bool swapped, int row_offset,
@@ -117,41 +123,49 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
   if (warp >= rows * nchunks) return;
   const int r = warp / nchunks;
   const long long c = warp % nchunks;
-  const long long k0 = c * KC;
-  int emax = 0;
-  for (int t = lane; t < KC; t += 32) emax = max(emax, fields(slice_input(src, ld, len, r, k0 + t, swapped)).exp);
+  const long long k0 = c * KC + lane * 8;
+  R x[8];
+  const R* row = src + (long long)r * ld;
+  if (k0 + 8 <= len && ((((uintptr_t)(row + k0)) & 15) == 0)) {
+    if constexpr (sizeof(R) == 8) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  constexpr int bias = FloatBits<R>::bias, nbits = FloatBits<R>::nb;
-  constexpr int g = 7 * S - 1 - nbits;   // shift that leaves 7S-1 bits (top digit below 64)
-  const int orow = row_offset + r;
-  if (lane == 0) {
-    sig[c * sig_ld + orow] = emax - bias - 5;
-    atomicMax(sigmax + orow, emax - bias - 5);
-  }
-  for (int t = lane; t < KC; t += 32) {
-    const Fields f = fields(slice_input(src, ld, len, r, k0 + t, swapped));
-    // G = mant * 2^(g - sh) rounded to nearest (ties up): the value on a grid of 7S-1 bits
-    // below the chunk maximum; FP32 inputs keep every mantissa bit (g - sh >= 0 for sh <= 4)
-    unsigned long long G = 0;
-    const int sh = emax - f.exp + 1;
-    const int rs = sh - g;
-    if (f.exp != 0 && rs < 64) G = rs > 0 ? (f.mant + (1ull << (rs - 1))) >> rs : f.mant << (-rs);
-    int d[S + 1];
-#pragma unroll
-    for (int i = 0; i < S; ++i) d[i] = (int)((G >> (7 * (S - 1 - i))) & 127ull);
-#pragma unroll
-    for (int i = S - 1; i >= 1; --i)
-      if (d[i] >= 64) {
-        d[i] -= 128;
-        d[i - 1] += 1;
+      for (int v = 0; v < 8; v += 2) {
+        const double2 t = __ldg((const double2*)(row + k0 + v));
+        x[v] = t.x;
+        x[v + 1] = t.y;
       }
+    } else {
+      const float4 t0 = __ldg((const float4*)(row + k0)), t1 = __ldg((const float4*)(row + k0 + 4));
+      x[0] = t0.x; x[1] = t0.y; x[2] = t0.z; x[3] = t0.w; x[4] = t1.x; x[5] = t1.y; x[6] = t1.z; x[7] = t1.w;
+    }
+  } else {
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      const float v = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
-      out[((long long)i * out_rows + orow) * Lp + k0 + t] = __float2bfloat16_rn(v);
+    for (int v = 0; v < 8; ++v) x[v] = k0 + v < len ? row[k0 + v] : R(0);
+  }
+  if (swapped) {
+    // (re, im) -> (im, -re): pairs start at even k, and k0 is a multiple of 8
+#pragma unroll
+    for (int v = 0; v < 8; v += 2) {
+      const R re = x[v], im = x[v + 1];
+      x[v] = im;
+      x[v + 1] = -re;
     }
   }
+  int emax = 0;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) emax = max(emax, fields(x[v]).exp);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  const int orow = row_offset + r;
+  if (lane == 0) {
+    sig[c * sig_ld + orow] = emax - FloatBits<R>::bias - 5;
+    atomicMax(sigmax + orow, emax - FloatBits<R>::bias - 5);
+  }
+  uint32_t o[S][4];
+  digits8_t<S>(x, emax, o);
+#pragma unroll
+  for (int i = 0; i < S; ++i)
+    *(uint4*)(out + ((long long)i * out_rows + orow) * Lp + c * KC + lane * 8) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
 }
 
 // Transposing slicer for the band rotation: operand rows are grid points r, the contraction
