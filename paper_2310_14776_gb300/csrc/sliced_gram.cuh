@@ -35,7 +35,6 @@ constexpr int KC = 256;           // grid values per exactness chunk
 constexpr int BM = 128;           // output rows per CTA (TMEM lanes)
 constexpr int BN = 96;            // output columns per CTA (MMA N)
 constexpr int BK = 16;            // K per stage = one MMA (32-byte rows, 32B swizzle)
-constexpr int STAGES = 4;
 constexpr int NACC = 5;           // accumulators D0 .. D4 at columns 0, 96, 192, 288, 384
 // Two epilogue warps per TMEM lane quarter (48 columns each) plus the TMA and MMA warps: ten
 // warps, three on some SM sub-partitions, which caps registers at 168 per thread.
@@ -62,8 +61,11 @@ __host__ __device__ inline int herm_tiles(int n) {
   for (int r = 0; r < Tr; ++r) t += Tc > herm_first_col(r) ? Tc - herm_first_col(r) : 0;
   return t;
 }
+// pipeline depth: as many stages as fit in 200 KB of shared memory (4 for FP64, 7 for FP32)
 template <int S>
-__host__ __device__ constexpr int smem_bytes() { return STAGES * stage_bytes<S>() + 1024; }
+__host__ __device__ constexpr int stages() { return (200 * 1024) / stage_bytes<S>() < 8 ? (200 * 1024) / stage_bytes<S>() : 8; }
+template <int S>
+__host__ __device__ constexpr int smem_bytes() { return stages<S>() * stage_bytes<S>() + 1024; }
 
 // ------------------------------------------------------------------------------------------
 // slicing
@@ -104,11 +106,20 @@ __device__ __forceinline__ R slice_input(const R* __restrict__ src, long long ld
   return (k & 1) ? -row[k - 1] : row[k + 1];
 }
 
+// Digit planes are stored in K steps: plane i, K step s (values 16 s .. 16 s + 15 of a row),
+// row r at element ((i * (Lp / 16) + s) * rows + r) * 16.  The 16 values of one row and step
+// are 32 contiguous bytes, and the BK x box_rows operand box of one plane that a pipeline
+// stage loads is one contiguous block of box_rows * 32 bytes.
+__device__ __forceinline__ long long plane_offset(int i, long long k, int r, int rows, long long Lp) {
+  return (((long long)i * (Lp / BK) + (k >> 4)) * rows + r) * BK + (k & 15);
+}
+
 // One warp per (row, chunk) of a K block: src points at the block's first value of row 0, rows
 // are ld apart, len values per row are valid (the rest of the Lp-long block is zero).
-// out: [S][out_rows][Lp] bf16 scaled digits (rows placed at row_offset); sig: [nchunks][sig_ld];
-// sigmax[row] (reset by the caller for every block) receives the largest sigma of the row.
-// Each lane takes 8 consecutive values of the 256-value chunk and writes 16 bytes per plane.
+// out: S digit planes of out_rows rows and Lp values (layout above; rows placed at row_offset);
+// sig: [nchunks][sig_ld]; sigmax[row] (reset by the caller for every block) receives the
+// largest sigma of the row.  Consecutive warps take consecutive rows of one chunk; each lane
+// takes 8 consecutive values of the 256-value chunk and writes 16 bytes per plane.
 template <int S>
 __device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32_t (&out)[S][4]);
 template <int S>
@@ -121,8 +132,8 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
                                                     int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= rows * nchunks) return;
-  const int r = warp / nchunks;
-  const long long c = warp % nchunks;
+  const int r = warp % rows;
+  const long long c = warp / rows;
   const long long k0 = c * KC + lane * 8;
   R x[8];
   const R* row = src + (long long)r * ld;
@@ -165,7 +176,7 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
   digits8_t<S>(x, emax, o);
 #pragma unroll
   for (int i = 0; i < S; ++i)
-    *(uint4*)(out + ((long long)i * out_rows + orow) * Lp + c * KC + lane * 8) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+    *(uint4*)(out + plane_offset(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
 }
 
 // Transposing slicer for the band rotation: operand rows are grid points r, the contraction
@@ -173,7 +184,7 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
 // part).  One CTA per (16 grid points, chunk of KC contraction values): the tile is read along
 // r (coalesced), kept transposed in shared memory, the largest exponent of every grid point's
 // chunk found, and each thread turns 8 consecutive k of one grid point into S 16-byte digit
-// groups (a warp writes 512 contiguous bytes of a plane).  out: [S][out_rows][Lp];
+// groups (a warp writes 512 contiguous bytes of a plane).  out: digit planes of out_rows rows (plane_offset);
 // sig: [nchunks][sig_ld] (sig_ld >= rows).
 constexpr int RT = 16;
 
@@ -276,9 +287,10 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
     }
   }
   __syncthreads();
-  // items: (grid point q, 8 consecutive k); consecutive threads take consecutive k groups
+  // items: (K step j, half h, grid point q); the 32 threads of a warp cover the 16 grid points
+  // and both halves of one K step, i.e. 512 contiguous bytes of a digit plane
   for (int item = tid; item < RT * (KC / 8); item += 256) {
-    const int q = item / (KC / 8), k8 = (item % (KC / 8)) * 8;
+    const int q = item % RT, k8 = (item / (2 * RT)) * 16 + ((item / RT) & 1) * 8;
     if (rl0 + q >= rcount) continue;
     R x[8];
     if constexpr (sizeof(R) == 4) {
@@ -296,7 +308,7 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
     digits8_t<S>(x, pmax[0][q], o);
 #pragma unroll
     for (int i = 0; i < S; ++i)
-      *(uint4*)(out + ((long long)i * out_rows + rl0 + q) * Lp + (long long)c * KC + k8) =
+      *(uint4*)(out + plane_offset(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
           make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
   }
 }
@@ -331,6 +343,7 @@ struct GramArgs {
   long long rot_K = 0;  // grid points per band
   void* rot_out = nullptr;        // band array, already offset to the first grid point of the block
   int rot_vec = 0;                // real bands with 16-byte aligned rows: vector stores
+  int rot_tiles = 0;              // output tiles of the rotation, shared out over the persistent CTAs
 };
 
 // 2^e for the product scale; below the normal range the chunk contributes nothing (its
@@ -343,8 +356,10 @@ __device__ __forceinline__ double pow2(int e) {
 // per half of B (Tc = ceil(half_rows / BN) each)
 __device__ __forceinline__ void gram_tile(const GramArgs& a, int t, int* tr, int* tc_) {
   if (!a.herm) {
-    *tr = t / a.tilesN;
-    *tc_ = t % a.tilesN;
+    // tile rows fastest: the CTAs that share a B tile run together and read it once from DRAM
+    const int Tr = (a.rowsA + BM - 1) / BM;
+    *tr = t % Tr;
+    *tc_ = t / Tr;
     return;
   }
   const int Tc = (a.half_rows + BN - 1) / BN;
@@ -380,9 +395,10 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
   two_sum(s, e, hi, lo);
 }
 
-template <int S, int ORD>
+template <int S, int ORD, bool ONE>
 __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
                                                                   const __grid_constant__ CUtensorMap tB, GramArgs a) {
+  constexpr int STAGES = stages<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t full[STAGES], empty[STAGES], dfull, dempty;
@@ -390,12 +406,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   __shared__ volatile int abort_flag;
   __shared__ int issued, consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tr, tcol;
-  gram_tile(a, blockIdx.x, &tr, &tcol);
-  const int row0 = tr * BM;
   // column tiles of the complex second half start at half_rows, not at a multiple of BN
   const int T = (a.half_rows + BN - 1) / BN;
-  const int col0 = (tcol / T) * a.half_rows + (tcol % T) * BN;
+  // Output tiles of this CTA: tile blockIdx.x; with ONE (a rotation whose contraction is one
+  // chunk) every gridDim.x-th tile from blockIdx.x (a persistent CTA: the copies for the next
+  // tile run while the epilogue of the last one drains TMEM and stores).
+  const int ntiles = !ONE ? 1 : ((int)blockIdx.x < a.rot_tiles ? (a.rot_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
+  auto tile_at = [&](int i, int& row0, int& col0, int& tcol) {
+    int tr;
+    gram_tile(a, (int)blockIdx.x + i * (int)gridDim.x, &tr, &tcol);
+    row0 = tr * BM;
+    col0 = (tcol / T) * a.half_rows + (tcol % T) * BN;
+  };
   const int c_begin = blockIdx.y * a.chunks_per_cta;
   const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
   const int nch = max(0, c_end - c_begin);
@@ -407,8 +429,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     const long long left = a.klen - (long long)(c_begin + c) * KC;
     return (int)max(1ll, min((long long)steps_per_chunk, (left + BK - 1) / BK));
   };
-  int total_steps = 0;
-  for (int c = 0; c < nch; ++c) total_steps += steps_of(c);
+  int steps_tile = 0;
+  for (int c = 0; c < nch; ++c) steps_tile += steps_of(c);
+  const int total_steps = steps_tile * ntiles;
+  const int items = nch * ntiles;   // (tile, chunk) pairs, chunk fastest: one TMEM round each
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -429,8 +453,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   const uint32_t tmem = tmem_base;
 
   if (warp == EPI_WARPS) {
-    if (lane == 0) {   // TMA producer: S slices of A and S slices of B per stage
-      int c = 0, q = 0;
+    if (lane == 0 && items > 0) {   // TMA producer: S slices of A and S slices of B per stage
+      int c = 0, q = 0, i = 0, row0, col0, tcol;
+      tile_at(0, row0, col0, tcol);
       for (int g = 0; g < total_steps && !abort_flag; ++g) {
         const int s = g % STAGES;
         if (g >= STAGES && !tc::mbar_wait(&empty[s], ((g / STAGES) - 1) & 1)) {
@@ -439,30 +464,33 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           break;
         }
         const int kx = (c_begin + c) * KC + q * BK;
-        if (++q == steps_of(c)) {
-          q = 0;
-          ++c;
-        }
         unsigned char* sa = smem + s * stage_bytes<S>();
         unsigned char* sb = sa + S * a_slice_bytes<S>();
         tc::mbar_expect_tx(&full[s], stage_bytes<S>());
-        tc::tma_load_3d(sa, &tA, &full[s], kx, row0, 0);
-        tc::tma_load_3d(sb, &tB, &full[s], kx, col0, 0);
+        tc::tma_load_4d(sa, &tA, &full[s], 0, row0, kx / BK, 0);
+        tc::tma_load_4d(sb, &tB, &full[s], 0, col0, kx / BK, 0);
         issued = g + 1;
+        if (++q == steps_of(c)) {
+          q = 0;
+          if (++c == nch) {
+            c = 0;
+            if (++i < ntiles) tile_at(i, row0, col0, tcol);
+          }
+        }
       }
     }
   } else if (warp == EPI_WARPS + 1) {
     if (lane == 0) {   // MMA issuer
       constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
       int g = 0;
-      for (int c = 0; c < nch && !abort_flag; ++c) {
-        if (c > 0 && !tc::mbar_wait(&dempty, (c - 1) & 1)) {
+      for (int it = 0; it < items && !abort_flag; ++it) {
+        if (it > 0 && !tc::mbar_wait(&dempty, (it - 1) & 1)) {
           abort_flag = 1;
           set_status(a.st, PAWFD_ETIMEDOUT, 1002);
           break;
         }
         tc::fence_after_sync();
-        const int steps = steps_of(c);
+        const int steps = steps_of(it % nch);
         for (int q = 0; q < steps && !abort_flag; ++q, ++g) {
           const int s = g % STAGES;
           if (!tc::mbar_wait(&full[s], (g / STAGES) & 1)) {
@@ -494,8 +522,88 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       }
     }
   } else {
+    if constexpr (ONE) {
+    // One chunk per tile (the rotation of real bands with nb <= KC): 16-column groups go from
+    // TMEM straight to the band array; the value is (D0 + ... + D4) 2^(sigma_a + sigma_b),
+    // summed exactly as a double-float and converted to FP64.  The chunk exponents of the
+    // tile's rows and columns are loaded while the tile's MMAs run (the columns' in two
+    // registers per lane, handed to the column's threads by shuffles), and TMEM is released to
+    // the MMA warp as soon as the last group is loaded.
+    static_assert(EPI_COLS % 16 == 0 && EPI_COLS <= 64, "16-column groups, two exponent registers per lane");
+    const int quarter = warp & 3, chalf = warp >> 2;
+    const int cbase = chalf * EPI_COLS;
+    for (int i = 0; i < ntiles; ++i) {
+      int row0, col0, tcol;
+      tile_at(i, row0, col0, tcol);
+      const int row = row0 + quarter * 32 + lane;
+      const bool rv = row < a.rowsA;
+      const int sga = rv ? __ldg(a.sigA + (long long)c_begin * a.sig_ldA + row) : 0;
+      const int cl0 = col0 + cbase + lane, cl1 = cl0 + 32;
+      const int sgb0 = cl0 < a.rowsB ? __ldg(a.sigB + (long long)c_begin * a.sig_ldB + cl0) : 0;
+      const int sgb1 = (lane + 32 < EPI_COLS && cl1 < a.rowsB) ? __ldg(a.sigB + (long long)c_begin * a.sig_ldB + cl1) : 0;
+      bool ok = tc::mbar_wait(&dfull, i & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_flag = 1;
+          set_status(a.st, PAWFD_ETIMEDOUT, 1004);
+        }
+        break;
+      }
+      tc::fence_after_sync();
+      const bool live = rv && !abort_flag;
+      const int band = row % a.rot_nb, part = row / a.rot_nb;
+      const long long base = (long long)band * a.rot_K;
+#pragma unroll 1
+      for (int g = 0; g < EPI_COLS / 16; ++g) {
+        uint32_t d[NACC][16];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + g * 16);
+#pragma unroll
+        for (int o = 0; o < NACC; ++o) tc::tmem_ld16(taddr + o * BN, d[o]);
+        tc::tmem_wait_ld();
+        if (g == EPI_COLS / 16 - 1) {
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&dempty);
+        }
+#pragma unroll
+        for (int j4 = 0; j4 < 16; j4 += 4) {
+          const int col = col0 + cbase + g * 16 + j4;
+          double v[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int cj = g * 16 + j4 + j;   // column within this warp's part
+            const int sgb = __shfl_sync(0xffffffffu, cj < 32 ? sgb0 : sgb1, cj & 31);
+            float s1, e1, s2, e2, s3, e3, vh, vl;
+            two_sum(__uint_as_float(d[0][j4 + j]), __uint_as_float(d[1][j4 + j]), s1, e1);
+            two_sum(s1, __uint_as_float(d[2][j4 + j]), s2, e2);
+            two_sum(s2, __uint_as_float(d[3][j4 + j]), s3, e3);
+            two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][j4 + j]), vh, vl);
+            v[j] = col + j < a.rowsB ? ((double)vh + (double)vl) * pow2(sga + sgb) : 0.0;
+          }
+          if (!live) continue;
+          if (a.rot_vec && col + 3 < a.rowsB) {
+            if (a.rot_fp32) {
+              *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+            } else {
+              *(double2*)((double*)a.rot_out + base + col) = make_double2(v[0], v[1]);
+              *(double2*)((double*)a.rot_out + base + col + 2) = make_double2(v[2], v[3]);
+            }
+          } else {
+            for (int j = 0; j < 4 && col + j < a.rowsB; ++j) {
+              const long long idx = a.rot_cplx ? 2 * (base + col + j) + part : base + col + j;
+              if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v[j];
+              else ((double*)a.rot_out)[idx] = v[j];
+            }
+          }
+        }
+      }
+    }
+    } else {
     // epilogue warps: lane quarter (warp % 4), column half (warp / 4)
     const int quarter = warp & 3, chalf = warp >> 2;
+    int row0, col0, tcol;
+    tile_at(0, row0, col0, tcol);
     const int row = row0 + quarter * 32 + lane;
     const int cbase = chalf * EPI_COLS;
     float ahi[EPI_COLS], alo[EPI_COLS];
@@ -505,7 +613,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       alo[j] = 0.0f;
     }
     const int ra = (row < a.rowsA) ? __ldg(a.maxA + row) : 0;
+    // column exponents: two registers per lane (columns cbase + lane, cbase + 32 + lane), handed
+    // to the column's threads by shuffles; the chunk's exponents are loaded before its MMAs end
+    const int cl0 = col0 + cbase + lane, cl1 = cl0 + 32;
+    const bool cv0 = cl0 < a.rowsB, cv1 = lane + 32 < EPI_COLS && cl1 < a.rowsB;
+    const int mb0 = cv0 ? __ldg(a.maxB + cl0) : 0, mb1 = cv1 ? __ldg(a.maxB + cl1) : 0;
     for (int c = 0; c < nch; ++c) {
+      const int chunk = c_begin + c;
+      const int sa = (row < a.rowsA) ? __ldg(a.sigA + (long long)chunk * a.sig_ldA + row) - ra : 0;
+      const int sb0 = cv0 ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + cl0) - mb0 : 0;
+      const int sb1 = cv1 ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + cl1) - mb1 : 0;
       bool ok = tc::mbar_wait(&dfull, c & 1);
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) {
@@ -516,8 +633,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         break;
       }
       tc::fence_after_sync();
-      const int chunk = c_begin + c;
-      const int sa = (row < a.rowsA) ? __ldg(a.sigA + (long long)chunk * a.sig_ldA + row) - ra : 0;
 #pragma unroll
       for (int b = 0; b < EPI_COLS / 8; ++b) {
         uint32_t d[NACC][8];
@@ -527,9 +642,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         tc::tmem_wait_ld();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int col = col0 + cbase + b * 8 + j;
-          const int sb = (col < a.rowsB) ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + col) - __ldg(a.maxB + col)
-                                         : 0;
+          const int cj = b * 8 + j;
+          const int sb = __shfl_sync(0xffffffffu, cj < 32 ? sb0 : sb1, cj & 31);
           const float scale = pow2f_nonpos(sa + sb);
           // D0 + D1 + D2 + D3 exactly as a double-float, then D4
           float s1, e1, s2, e2, s3, e3, vh, vl;
@@ -597,6 +711,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           out[col] = a.accumulate ? out[col] + v : v;
         }
       }
+    }
     }
   }
   tc::fence_before_sync();

@@ -122,7 +122,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     a.st = c->d_status;
     // slots written by the first block must cover every split later blocks add into
     if (blk == 0 && ns < nsplit) nsplit = ns;
-    sg::sliced_gram_kernel<S, ORD><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
     c->launches += 1;
   }
@@ -212,8 +212,14 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
     a.rot_out = out + r0 * (cplx ? 2 : 1);
     a.rot_vec = !cplx && ((uintptr_t)a.rot_out % 16 == 0) && ((K * sizeof(R)) % 16 == 0);
     a.klen = Lk;
-    sg::sliced_gram_kernel<S, ORD><<<dim3(tilesM * a.tilesN, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.rotMapA, t.rotMapB, a);
+    a.rot_tiles = tilesM * a.tilesN;
+    if (nch == 1)   // persistent CTAs, one per SM (the kernel's shared memory admits one)
+      sg::sliced_gram_kernel<S, ORD, true>
+          <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+              t.rotMapA, t.rotMapB, a);
+    else
+      sg::sliced_gram_kernel<S, ORD, false><<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+          t.rotMapA, t.rotMapB, a);
     c->launches += 2;
   }
   return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
@@ -340,11 +346,13 @@ int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long 
       return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled not available");
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  cuuint64_t dims[3] = {(cuuint64_t)Lp, (cuuint64_t)rows, (cuuint64_t)S};
-  cuuint64_t strides[2] = {(cuuint64_t)Lp * 2, (cuuint64_t)rows * (cuuint64_t)Lp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows, (cuuint32_t)S};
-  cuuint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr,
+  // digit planes in K steps (sg::plane_offset): dims (value in step, row, step, plane)
+  const cuuint64_t ks = (cuuint64_t)(Lp / sg::BK);
+  cuuint64_t dims[4] = {(cuuint64_t)sg::BK, (cuuint64_t)rows, ks, (cuuint64_t)S};
+  cuuint64_t strides[3] = {(cuuint64_t)sg::BK * 2, (cuuint64_t)rows * sg::BK * 2, ks * rows * sg::BK * 2};
+  cuuint32_t box[4] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows, 1, (cuuint32_t)S};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled failed");
@@ -384,12 +392,20 @@ int setup_tc(pawfd_ctx* c) {
   rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BM);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) {
-    if (S == 7)
-      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              sg::smem_bytes<7>()), "smem attribute");
-    else
-      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              sg::smem_bytes<4>()), "smem attribute");
+    const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (S == 7) {
+      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6, false>, smem_attr, sg::smem_bytes<7>()),
+                      "smem attribute");
+      if (rc == PAWFD_OK)
+        rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6, true>, smem_attr, sg::smem_bytes<7>()),
+                        "smem attribute");
+    } else {
+      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4, false>, smem_attr, sg::smem_bytes<4>()),
+                      "smem attribute");
+      if (rc == PAWFD_OK)
+        rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4, true>, smem_attr, sg::smem_bytes<4>()),
+                        "smem attribute");
+    }
   }
   // fused Gram: chunk exponents over the whole row
   if (rc == PAWFD_OK) {
