@@ -352,6 +352,27 @@ __device__ __forceinline__ double pow2(int e) {
   return e < -1022 ? 0.0 : __longlong_as_double((long long)(e + 1023) << 52);
 }
 
+// x 2^e as a double, assembled from the bit fields of the float x with integer operations (no
+// FP64 conversion or multiply: the FP64 pipe is narrow); results below the normal FP64
+// range, and float subnormals, give 0.
+__device__ __forceinline__ double f2d_scaled(float x, int e) {
+  const unsigned u = __float_as_uint(x);
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const int ed = ef - 127 + 1023 + e;
+  if (ef == 0 || ed <= 0) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((unsigned)ed << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+// the double-float (xh, xl) times 2^e: both parts exact, one FP64 add
+__device__ __forceinline__ double df_to_double(float xh, float xl, int e) {
+  return f2d_scaled(xh, e) + f2d_scaled(xl, e);
+}
+// x 2^e in FP32 (x is the correctly rounded sum of the double-float pair)
+__device__ __forceinline__ float f2f_scaled(float x, int e) {
+  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
+  return (float)((double)x * pow2(e));
+}
+
 // tile index -> (tile row, tile col) over the output [rowsA][rowsB]; tile columns are numbered
 // per half of B (Tc = ceil(half_rows / BN) each)
 __device__ __forceinline__ void gram_tile(const GramArgs& a, int t, int* tr, int* tc_) {
@@ -523,13 +544,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     }
   } else {
     if constexpr (ONE) {
-    // One chunk per tile (the rotation of real bands with nb <= KC): 16-column groups go from
-    // TMEM straight to the band array; the value is (D0 + ... + D4) 2^(sigma_a + sigma_b),
-    // summed exactly as a double-float and converted to FP64.  The chunk exponents of the
-    // tile's rows and columns are loaded while the tile's MMAs run (the columns' in two
-    // registers per lane, handed to the column's threads by shuffles), and TMEM is released to
-    // the MMA warp as soon as the last group is loaded.
-    static_assert(EPI_COLS % 16 == 0 && EPI_COLS <= 64, "16-column groups, two exponent registers per lane");
+    // One chunk per tile (the rotation of real bands with nb <= KC): the value is (D0 + ... +
+    // D4) 2^(sigma_a + sigma_b), summed exactly as a double-float and converted to the band
+    // dtype.  The chunk exponents of the tile's rows and columns are loaded while the tile's
+    // MMAs run (the columns' in two registers per lane, handed to the column's threads by
+    // shuffles).
+    static_assert(EPI_COLS % 8 == 0 && EPI_COLS <= 64, "8-column groups, two exponent registers per lane");
     const int quarter = warp & 3, chalf = warp >> 2;
     const int cbase = chalf * EPI_COLS;
     for (int i = 0; i < ntiles; ++i) {
@@ -554,47 +574,53 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       const bool live = rv && !abort_flag;
       const int band = row % a.rot_nb, part = row / a.rot_nb;
       const long long base = (long long)band * a.rot_K;
-#pragma unroll 1
-      for (int g = 0; g < EPI_COLS / 16; ++g) {
-        uint32_t d[NACC][16];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + g * 16);
+      // TMEM -> the exact double-float sums (vh, vl) of the five orders, 8 columns at a time;
+      // then TMEM goes back to the MMA warp and the conversion and stores overlap the next tile
+      float vh[EPI_COLS], vl[EPI_COLS];
 #pragma unroll
-        for (int o = 0; o < NACC; ++o) tc::tmem_ld16(taddr + o * BN, d[o]);
+      for (int g = 0; g < EPI_COLS / 8; ++g) {
+        uint32_t d[NACC][8];
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + g * 8);
+#pragma unroll
+        for (int o = 0; o < NACC; ++o) tc::tmem_ld8(taddr + o * BN, d[o]);
         tc::tmem_wait_ld();
-        if (g == EPI_COLS / 16 - 1) {
-          tc::fence_before_sync();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&dempty);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float s1, e1, s2, e2, s3, e3;
+          two_sum(__uint_as_float(d[0][j]), __uint_as_float(d[1][j]), s1, e1);
+          two_sum(s1, __uint_as_float(d[2][j]), s2, e2);
+          two_sum(s2, __uint_as_float(d[3][j]), s3, e3);
+          two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][j]), vh[g * 8 + j], vl[g * 8 + j]);
         }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&dempty);
 #pragma unroll
-        for (int j4 = 0; j4 < 16; j4 += 4) {
-          const int col = col0 + cbase + g * 16 + j4;
-          double v[4];
+      for (int j4 = 0; j4 < EPI_COLS; j4 += 4) {
+        const int col = col0 + cbase + j4;
+        double v[4];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int cj = g * 16 + j4 + j;   // column within this warp's part
-            const int sgb = __shfl_sync(0xffffffffu, cj < 32 ? sgb0 : sgb1, cj & 31);
-            float s1, e1, s2, e2, s3, e3, vh, vl;
-            two_sum(__uint_as_float(d[0][j4 + j]), __uint_as_float(d[1][j4 + j]), s1, e1);
-            two_sum(s1, __uint_as_float(d[2][j4 + j]), s2, e2);
-            two_sum(s2, __uint_as_float(d[3][j4 + j]), s3, e3);
-            two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][j4 + j]), vh, vl);
-            v[j] = col + j < a.rowsB ? ((double)vh + (double)vl) * pow2(sga + sgb) : 0.0;
-          }
-          if (!live) continue;
-          if (a.rot_vec && col + 3 < a.rowsB) {
-            if (a.rot_fp32) {
-              *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
-            } else {
-              *(double2*)((double*)a.rot_out + base + col) = make_double2(v[0], v[1]);
-              *(double2*)((double*)a.rot_out + base + col + 2) = make_double2(v[2], v[3]);
-            }
+        for (int j = 0; j < 4; ++j) {
+          const int cj = j4 + j;   // column within this warp's part
+          const int sgb = __shfl_sync(0xffffffffu, cj < 32 ? sgb0 : sgb1, cj & 31);
+          v[j] = col + j < a.rowsB
+                     ? (a.rot_fp32 ? (double)f2f_scaled(vh[cj], sga + sgb) : df_to_double(vh[cj], vl[cj], sga + sgb))
+                     : 0.0;
+        }
+        if (!live) continue;
+        if (a.rot_vec && col + 3 < a.rowsB) {
+          if (a.rot_fp32) {
+            *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
           } else {
-            for (int j = 0; j < 4 && col + j < a.rowsB; ++j) {
-              const long long idx = a.rot_cplx ? 2 * (base + col + j) + part : base + col + j;
-              if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v[j];
-              else ((double*)a.rot_out)[idx] = v[j];
-            }
+            *(double2*)((double*)a.rot_out + base + col) = make_double2(v[0], v[1]);
+            *(double2*)((double*)a.rot_out + base + col + 2) = make_double2(v[2], v[3]);
+          }
+        } else {
+          for (int j = 0; j < 4 && col + j < a.rowsB; ++j) {
+            const long long idx = a.rot_cplx ? 2 * (base + col + j) + part : base + col + j;
+            if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v[j];
+            else ((double*)a.rot_out)[idx] = v[j];
           }
         }
       }
@@ -672,8 +698,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
             double v[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              v[u] = col + u < a.rowsB ? ((double)ahi[j + u] + (double)alo[j + u]) * pow2(ra + __ldg(a.maxB + col + u))
-                                       : 0.0;
+              v[u] = col + u < a.rowsB ? df_to_double(ahi[j + u], alo[j + u], ra + __ldg(a.maxB + col + u)) : 0.0;
             if (col + 3 < a.rowsB) {
               if (a.rot_fp32) {
                 *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
@@ -693,7 +718,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           for (int j = 0; j < EPI_COLS; ++j) {
             const int col = col0 + cbase + j;
             if (col < a.rowsB) {
-              const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
+              const double v = df_to_double(ahi[j], alo[j], ra + __ldg(a.maxB + col));
               const long long idx = a.rot_cplx ? 2 * (base + col) + part : base + col;
               if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v;
               else ((double*)a.rot_out)[idx] = v;
@@ -707,7 +732,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       for (int j = 0; j < EPI_COLS; ++j) {
         const int col = col0 + cbase + j;
         if (col < col_lim) {
-          const double v = ((double)ahi[j] + (double)alo[j]) * pow2(ra + __ldg(a.maxB + col));
+          const double v = df_to_double(ahi[j], alo[j], ra + __ldg(a.maxB + col));
           out[col] = a.accumulate ? out[col] + v : v;
         }
       }
