@@ -246,7 +246,7 @@ void free_ctx(pawfd_ctx* c) {
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
-                  c->d_vshift_df};
+                  c->d_vshift_df, c->d_flags, c->d_oa};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -329,10 +329,13 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     c->d_barrier = dev_alloc<unsigned>(c, 4, &rc);
     c->d_status = dev_alloc<DeviceStatus>(c, 1, &rc);
     c->d_reduce = dev_alloc<double>(c, 8192, &rc);   // [0, 2048): partial sums; then Jacobi round flags
+    c->d_flags = dev_alloc<int>(c, 16, &rc);
+    c->d_oa = dev_alloc<double>(c, oa_scratch_doubles(nb), &rc);
   }
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMallocHost(&c->h_status, sizeof(DeviceStatus)), "cudaMallocHost");
   if (rc == PAWFD_OK && c->use_tc) rc = setup_tc(c);
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_barrier, 0, 4 * sizeof(unsigned)), "memset");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_flags, 0, 16 * sizeof(int)), "memset");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(c->d_status, 0, sizeof(DeviceStatus)), "memset");
   // the uploads and memsets above ran on the legacy default stream: wait for those only, not
   // for other work on the device (a server creates contexts while jobs run on their streams)

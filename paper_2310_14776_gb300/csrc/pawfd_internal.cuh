@@ -180,7 +180,9 @@ struct pawfd_ctx {
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_gram_part = nullptr;                // split-K partial Gram matrices
   size_t gram_part_bytes = 0;
-  void* d_work = nullptr;                     // subspace workspace (5 matrices of max_bands^2)
+  void* d_work = nullptr;                     // subspace workspace (7 matrices of max_bands^2)
+  int* d_flags = nullptr;                     // [16] subspace-solve path decisions (device-side gates)
+  double* d_oa = nullptr;                     // Ogita-Aishima partial sums and eigenvalue estimates
   double* d_evals = nullptr;                  // [max_bands] unsorted eigenvalues
   unsigned* d_barrier = nullptr;              // grid-barrier counters
   pawfd::DeviceStatus* d_status = nullptr;
@@ -239,6 +241,9 @@ int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
+// CTAs of the Ogita-Aishima element kernels and the doubles of their scratch for nb bands
+constexpr int OA_G = 64;
+inline size_t oa_scratch_doubles(int nb) { return 5 * (size_t)OA_G + (size_t)nb; }
 
 // order-6 central second-difference weights: f'' ~ (1/h^2) sum_m w_|m| f(x + m h)
 constexpr double FD6_W0 = -49.0 / 18.0;

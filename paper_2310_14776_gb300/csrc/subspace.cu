@@ -120,15 +120,20 @@ __device__ __forceinline__ zd shfl_x(zd v, int src) {
   return zd{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
 }
 
+// A kernel given a gate does nothing when the gate word is nonzero (a path of the subspace solve
+// that the device decided against; the word is the same for every CTA of a launch).
+__device__ __forceinline__ bool gated(const int* gate) { return gate && ld_volatile(gate) != 0; }
+
 template <class T, int MODE>
-__global__ void __launch_bounds__(CH_NT) cholesky_kernel(T* __restrict__ S, int n, unsigned* bar, DeviceStatus* st) {
+__global__ void __launch_bounds__(CH_NT) cholesky_kernel(T* __restrict__ S, int n, unsigned* bar, DeviceStatus* st,
+                                                         const int* gate) {
   __shared__ T L11[CH_NB][CH_NB + 1];
   __shared__ double inv_d[CH_NB];
   __shared__ int s_fail;
   const unsigned G = gridDim.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gthreads = (int)G * CH_NT, gtid = (int)blockIdx.x * CH_NT + tid;
-  if (ld_volatile(&st->code) != 0) return;   // uniform: set before this launch
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;   // uniform: set before this launch
   for (int k0 = 0; k0 < n; k0 += CH_NB) {
     const int nb = min(CH_NB, n - k0);
     // (a) diagonal block
@@ -201,11 +206,11 @@ __global__ void __launch_bounds__(CH_NT) cholesky_kernel(T* __restrict__ S, int 
 // Linv column j = L^-1 e_j by forward substitution (one CTA per column).
 template <class T>
 __global__ void __launch_bounds__(256) tri_inverse_kernel(const T* __restrict__ L, int n, T* __restrict__ Linv,
-                                                          const DeviceStatus* st) {
+                                                          const DeviceStatus* st, const int* gate) {
   extern __shared__ unsigned char smem_raw[];
   T* x = (T*)smem_raw;
   const int j = blockIdx.x, tid = threadIdx.x;
-  if (ld_volatile(&st->code) != 0) return;
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
   for (int k = tid; k < n; k += blockDim.x) x[k] = (k == j) ? from_real<T>(1.0) : zero<T>();
   for (int i = j; i < n; ++i) {
     __syncthreads();
@@ -224,10 +229,11 @@ template <class T>
 __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A, bool ha, const T* __restrict__ B,
                                                          bool hb, int n, T* __restrict__ C, const DeviceStatus* st,
                                                          const T* __restrict__ D = nullptr,
-                                                         const int* skip = nullptr, const T* __restrict__ src = nullptr) {
+                                                         const int* skip = nullptr, const T* __restrict__ src = nullptr,
+                                                         const int* gate = nullptr) {
   __shared__ T As[16][17];
   __shared__ T Bs[16][17];
-  if (ld_volatile(&st->code) != 0) return;
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
   if (skip && ld_volatile(skip)) {
@@ -255,8 +261,8 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A
 }
 
 template <class T>
-__global__ void hermitize_kernel(T* __restrict__ A, int n, const DeviceStatus* st) {
-  if (ld_volatile(&st->code) != 0) return;
+__global__ void hermitize_kernel(T* __restrict__ A, int n, const DeviceStatus* st, const int* gate = nullptr) {
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)n * n) return;
   const int i = (int)(e / n), j = (int)(e % n);
@@ -357,10 +363,10 @@ __device__ double block_reduce_sum(double v, double* s_red) {
 template <class T>
 __global__ void __launch_bounds__(1024) refine_step_kernel(const T* __restrict__ S, const T* __restrict__ XtX, int n,
                                                           T* __restrict__ E, int* skip, double tol,
-                                                          const DeviceStatus* st) {
+                                                          const DeviceStatus* st, const int* gate) {
   __shared__ double s_red[32];
   __shared__ double s_v[3];
-  if (ld_volatile(&st->code) != 0) return;
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
   if (XtX && ld_volatile(skip)) return;
   const int tid = threadIdx.x;
   const int nn = n * n;
@@ -419,9 +425,159 @@ __global__ void __launch_bounds__(1024) refine_step_kernel(const T* __restrict__
 }
 
 template <class T>
-__global__ void identity_kernel(T* __restrict__ X, int n) {
+__global__ void identity_kernel(T* __restrict__ X, int n, const int* gate = nullptr) {
+  if (gated(gate)) return;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < (long long)n * n) X[e] = from_real<T>((e / n) == (e % n) ? 1.0 : 0.0);
+}
+
+// ---- Ogita-Aishima steps on many CTAs, for the generalized problem H x = lambda S x ----
+// With an approximate basis X, A = X^H H X and B = X^H S X (B = null: B = I), the step of the
+// single-CTA kernel above with R = I - B:  lambda_i = Re a_ii / Re b_ii,
+//   e_ij = (a_ij + lambda_j r_ij) / (lambda_j - lambda_i)  off clusters, e_ij = r_ij / 2 on them,
+// and X' = X + X E is S-orthonormal and diagonalizes H to second order.  Started from X = I
+// (A = H_nm, B = S_nm), it replaces the Cholesky reduction when the bands are already close
+// to the Ritz vectors (the iterated Rayleigh-Ritz step).
+
+// Gate words of one subspace solve (oa_decide_kernel): a kernel given gate word g does nothing
+// when flags[g] != 0.
+enum { GATE_NEAR = 0, GATE_FAR = 1, GATE_STEP2 = 2, GATE_AM = 3, GATE_JACOBI = 4, GATE_LAMBDA = 5 };
+
+__device__ double block_reduce_max(double v, double* s_red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) s_red[warp] = v;
+  __syncthreads();
+  double m = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmax(m, s_red[w]);
+  return m;   // valid in thread 0
+}
+
+// per-CTA partial sums of ||A - diag A||_F^2, ||A||_F^2, ||I - B||_F^2 into part[3 g + k], and
+// lambda_i = Re a_ii / Re b_ii
+template <class T>
+__global__ void __launch_bounds__(256) oa_stats_kernel(const T* __restrict__ A, const T* __restrict__ B, int n,
+                                                       double* __restrict__ part, double* __restrict__ lam,
+                                                       const int* gate, const DeviceStatus* st) {
+  __shared__ double s_red[32];
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  const long long nn = (long long)n * n;
+  double off2 = 0.0, fro2 = 0.0, r2 = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const bool dg = (e / n) == (e % n);
+    const double a2 = absx2(A[e]);
+    fro2 += a2;
+    if (!dg) off2 += a2;
+    if (B) r2 += absx2(from_real<T>(dg ? 1.0 : 0.0) - B[e]);
+  }
+  off2 = block_reduce_sum(off2, s_red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x] = off2;
+  fro2 = block_reduce_sum(fro2, s_red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 1] = fro2;
+  r2 = block_reduce_sum(r2, s_red);
+  if (threadIdx.x == 0) part[3 * blockIdx.x + 2] = r2;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const long long d = (long long)i * n + i;
+    lam[i] = realx(A[d]) / (B ? realx(B[d]) : 1.0);
+  }
+}
+
+// E of one step (see above).  delta = 2 (||A - diag A|| + ||A|| ||R||) separates clusters;
+// a pair is also left to the Jacobi sweeps when |e_ij|^2 would exceed ebound2.  Partials:
+// part2[2 g] = pairs left coupled above the Jacobi threshold, part2[2 g + 1] = max |e_ij|^2.
+template <class T>
+__global__ void __launch_bounds__(256) oa_update_kernel(const T* __restrict__ A, const T* __restrict__ B, int n,
+                                                        const double* __restrict__ lam, const double* __restrict__ part,
+                                                        double tol, double ebound2, T* __restrict__ E,
+                                                        double* __restrict__ part2, const int* gate,
+                                                        const DeviceStatus* st) {
+  __shared__ double s_red[32];
+  __shared__ double s_v[3];
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  if (threadIdx.x < 3) {   // the same sums, in the same order, in every CTA
+    double v = 0.0;
+    for (int g = 0; g < OA_G; ++g) v += part[3 * g + threadIdx.x];
+    s_v[threadIdx.x] = v;
+  }
+  __syncthreads();
+  const double off2 = s_v[0], fro2 = s_v[1], r2 = s_v[2];
+  const double delta = fmax(2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
+  const double thr2 = tol * tol * fro2 / ((double)n * n);
+  const long long nn = (long long)n * n;
+  double coupled = 0.0, emax2 = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const T r = B ? from_real<T>(i == j ? 1.0 : 0.0) - B[e] : zero<T>();
+    T v = 0.5 * r;
+    if (i != j) {
+      const double li = lam[i], lj = lam[j];
+      bool cluster = fabs(lj - li) <= delta;
+      if (!cluster) {
+        const T w = (1.0 / (lj - li)) * (A[e] + lj * r);
+        if (absx2(w) <= ebound2) v = w;
+        else cluster = true;
+      }
+      if (cluster && absx2(A[e]) > thr2) coupled += 1.0;
+    }
+    emax2 = fmax(emax2, absx2(v));
+    E[e] = v;
+  }
+  coupled = block_reduce_sum(coupled, s_red);
+  if (threadIdx.x == 0) part2[2 * blockIdx.x] = coupled;
+  emax2 = block_reduce_max(emax2, s_red);
+  if (threadIdx.x == 0) part2[2 * blockIdx.x + 1] = emax2;
+}
+
+// Path decision from the first step started at X = I (A = H_nm, B = S_nm): the near path when
+// ||I - S_nm||_F <= 1e-4 and at most 2 n pairs are left coupled.  One step suffices when
+// every |e_ij| <= 1e-8 (the error left is of its square); with no coupled pair either, the
+// Jacobi sweeps are not needed and the eigenvalues are the lambda_i.
+__global__ void oa_decide_kernel(const double* __restrict__ part, const double* __restrict__ part2, int n,
+                                 int* __restrict__ flags) {
+  if (threadIdx.x != 0) return;
+  double r2 = 0.0, coupled = 0.0, emax2 = 0.0;
+  for (int g = 0; g < OA_G; ++g) {
+    r2 += part[3 * g + 2];
+    coupled += part2[2 * g];
+    emax2 = fmax(emax2, part2[2 * g + 1]);
+  }
+  const bool near = r2 <= 1e-8 && coupled <= 2.0 * n;
+  const bool one = emax2 <= 1e-16;
+  const bool nojac = one && coupled == 0.0;
+  flags[GATE_NEAR] = near;
+  flags[GATE_FAR] = !near;
+  flags[GATE_STEP2] = !near || one;
+  flags[GATE_AM] = !near || nojac;
+  flags[GATE_JACOBI] = near && nojac;
+  flags[GATE_LAMBDA] = !(near && nojac);
+}
+
+// X = I + E
+template <class T>
+__global__ void identity_plus_kernel(const T* __restrict__ E, int n, T* __restrict__ X, const int* gate,
+                                     const DeviceStatus* st) {
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n * n) X[e] = E[e] + from_real<T>((e / n) == (e % n) ? 1.0 : 0.0);
+}
+
+template <class T>
+__global__ void copy_kernel(const T* __restrict__ src, long long count, T* __restrict__ dst, const int* gate,
+                            const DeviceStatus* st) {
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) dst[e] = src[e];
+}
+
+// the diagonal of A from lambda (the sort reads only the diagonal)
+template <class T>
+__global__ void lambda_diag_kernel(const double* __restrict__ lam, int n, T* __restrict__ A, const int* gate,
+                                   const DeviceStatus* st) {
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[(long long)i * n + i] = from_real<T>(lam[i]);
 }
 
 // sum over all CTAs of per-CTA partials, identical (same order) in every CTA
@@ -449,7 +605,7 @@ __device__ double grid_sum(double mine, double* red, double* s_red, double* s_bc
 template <class T, int MODE>
 __global__ void __launch_bounds__(MODE == 1 ? 1024 : 256)
     jacobi_kernel(T* __restrict__ A0, T* __restrict__ A1, T* __restrict__ V, int n, double tol, int max_sweeps,
-                  unsigned* bar, DeviceStatus* st, double* red) {
+                  unsigned* bar, DeviceStatus* st, double* red, const int* gate) {
   // V holds the caller's starting basis; the rotations accumulate onto it
   extern __shared__ unsigned char smem_raw[];
   Rot* rot = (Rot*)smem_raw;
@@ -465,7 +621,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 1024 : 256)
   // rotated blocks to the other buffer, so no CTA can see a half-updated round.
   T* A = A0;
   T* Anext = A1;
-  if (ld_volatile(&st->code) != 0) return;   // an earlier step (Cholesky) failed
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;   // an earlier step failed, or no sweeps needed
 
 
   double fro2 = 0.0;
@@ -614,7 +770,7 @@ __global__ void phase_fix_kernel(T* __restrict__ C, int n, const DeviceStatus* s
 // of one thread-block cluster, the kernel runs as a single cluster and every round ends on a
 // hardware cluster barrier; otherwise as a cooperative grid with a software grid barrier.
 template <class T>
-int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm) {
+int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm, const int* gate) {
   cudaStream_t s = c->stream;
   const int npad = n + (n & 1), np = npad / 2;
   const size_t rot_bytes = sizeof(Rot) * np;
@@ -659,7 +815,8 @@ int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm) {
         nclusters = 0;
       }
       if (nclusters >= 1) {
-        rc = check_cuda(c, cudaLaunchKernelEx(&cfg, jacobi_kernel<T, 1>, Am, A2, Vm, n, tol, max_sweeps, bar, st, red),
+        rc = check_cuda(c, cudaLaunchKernelEx(&cfg, jacobi_kernel<T, 1>, Am, A2, Vm, n, tol, max_sweeps, bar, st, red,
+                                              gate),
                         "jacobi cluster launch");
         c->launches += 1;
         return rc;
@@ -682,7 +839,7 @@ int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm) {
   G = std::min(G, 2048);   // grid_sum partials live in red[0, 2048)
   rc = check_cuda(c, cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), s), "barrier reset");
   if (rc != PAWFD_OK) return rc;
-  void* args[] = {&Am, &A2, &Vm, &n, &tol, &max_sweeps, &bar, &st, &red};
+  void* args[] = {&Am, &A2, &Vm, &n, &tol, &max_sweeps, &bar, &st, &red, &gate};
   rc = check_cuda(c, cudaLaunchCooperativeKernel((const void*)jacobi_kernel<T, 0>, dim3(G), dim3(256), args,
                                                  rot_bytes, s),
                   "jacobi cooperative launch");
@@ -747,64 +904,99 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   const long long nn = (long long)n * n;
   T* W = (T*)c->d_work;
   T* Hs = W;            // symmetrized H
-  T* Lm = W + nn;       // symmetrized S, then L
-  T* Li = W + 2 * nn;   // L^-1
-  T* T1 = W + 3 * nn;   // L^-1 H, later U
-  T* Am = W + 4 * nn;   // L^-1 H L^-H, diagonalized in place
-  T* Vm = W + 5 * nn;   // Jacobi rotations
-  T* A2 = W + 6 * nn;   // second Jacobi buffer
+  T* Lm = W + nn;       // symmetrized S; far path: then L
+  T* Li = W + 2 * nn;   // far path: L^-1; near path: E of the first step (and of the second)
+  T* T1 = W + 3 * nn;   // products, later U
+  T* Am = W + 4 * nn;   // the matrix of the Jacobi sweeps, diagonalized in place
+  T* Vm = W + 5 * nn;   // the basis X the rotations accumulate onto
+  T* A2 = W + 6 * nn;   // second Jacobi buffer; near path: X^H H X of the second step
   cudaStream_t s = c->stream;
+  const DeviceStatus* st = c->d_status;
+  const int* flags = c->d_flags;
+  const int* near = flags + GATE_NEAR;      // far-path kernels: skipped on the near path
+  const int* far = flags + GATE_FAR;        // near-path kernels: skipped on the far path
+  double* part = c->d_oa;                   // [3 OA_G] norms
+  double* part2 = c->d_oa + 3 * OA_G;       // [2 OA_G] coupled pairs, max |e|^2
+  double* lam = c->d_oa + 5 * OA_G;         // [n]
+  const double tol = 1e-14;
   const unsigned eb = (unsigned)((nn + 255) / 256);
+  const dim3 gg((n + 15) / 16, (n + 15) / 16);
   symmetrize_kernel<T><<<eb, 256, 0, s>>>(H, S, n, Hs, Lm);
-  c->launches += 1;
-  int rc = check_cuda(c, cudaGetLastError(), "symmetrize launch");
+  // the first Ogita-Aishima step from X = I on (H, S), and the path decision
+  oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, part, lam, nullptr, st);
+  oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, lam, part, tol, 1e-8, Li, part2, nullptr, st);
+  oa_decide_kernel<<<1, 32, 0, s>>>(part, part2, n, c->d_flags);
+  c->launches += 4;
+  int rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
+
+  // ---- far path: Cholesky S = L L^H, A = L^-1 H L^-H, Ogita-Aishima on A from X = I ----
   // Cholesky: one cluster up to n = 256 (its flops fit 16 SMs), the whole GPU above
   {
     unsigned* bar = c->d_barrier;
-    DeviceStatus* st = c->d_status;
+    DeviceStatus* stw = c->d_status;
     const int want = n <= 256 ? 16 : c->num_sms;
     rc = launch_cluster_or_grid(c, cholesky_kernel<T, 1>, cholesky_kernel<T, 0>, CH_NT, 0, want, c->jacobi_cluster,
-                                "cholesky launch", Lm, n, bar, st);
+                                "cholesky launch", Lm, n, bar, stw, near);
     if (rc != PAWFD_OK) return rc;
   }
-  tri_inverse_kernel<T><<<n, 256, sizeof(T) * n, s>>>(Lm, n, Li, c->d_status);
-  dim3 gg((n + 15) / 16, (n + 15) / 16);
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, false, Hs, false, n, T1, c->d_status);
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Li, true, n, Am, c->d_status);
-  hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, c->d_status);
+  tri_inverse_kernel<T><<<n, 256, sizeof(T) * n, s>>>(Lm, n, Li, st, near);
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, false, Hs, false, n, T1, st, nullptr, nullptr, nullptr, near);
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Li, true, n, Am, st, nullptr, nullptr, nullptr, near);
+  hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, near);
   c->launches += 4;
   rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
-
   // Two Ogita-Aishima steps from X = I (skipped on the device when A is already diagonal or
   // far from it), then A <- X^H A X and the Jacobi sweeps, which accumulate onto X
   {
-    identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n);
+    identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n, near);
     c->launches += 1;
     int* skip = (int*)(c->d_barrier + 2);
-    const double tol = 1e-14;
-    const DeviceStatus* st = c->d_status;
     // step 1: S = A, R = 0; X1 = I + E into Hs (the symmetrized H is no longer needed)
-    refine_step_kernel<T><<<1, 1024, 0, s>>>(Am, nullptr, n, T1, skip, tol, st);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, T1, false, n, Hs, st, Vm, skip, Vm);
+    refine_step_kernel<T><<<1, 1024, 0, s>>>(Am, nullptr, n, T1, skip, tol, st, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, T1, false, n, Hs, st, Vm, skip, Vm, near);
     // step 2: S = X1^H A X1 (into Lm, no longer needed), X1^H X1 (into A2), X2 = X1 + X1 E into Vm
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Hs, false, n, T1, st, nullptr, skip, Am);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, T1, false, n, Lm, st, nullptr, skip, T1);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, Hs, false, n, A2, st, nullptr, skip, Vm);
-    refine_step_kernel<T><<<1, 1024, 0, s>>>(Lm, A2, n, T1, skip, tol, st);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, T1, false, n, Vm, st, Hs, skip, Hs);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Hs, false, n, T1, st, nullptr, skip, Am, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, T1, false, n, Lm, st, nullptr, skip, T1, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, Hs, false, n, A2, st, nullptr, skip, Vm, near);
+    refine_step_kernel<T><<<1, 1024, 0, s>>>(Lm, A2, n, T1, skip, tol, st, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, T1, false, n, Vm, st, Hs, skip, Hs, near);
     // A <- X2^H A X2
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, skip, Am);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, skip, T1);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, skip, Am, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, skip, T1, near);
     c->launches += 9;
     rc = check_cuda(c, cudaGetLastError(), "refinement steps");
     if (rc != PAWFD_OK) return rc;
   }
-  rc = launch_jacobi<T>(c, n, Am, A2, Vm);
+
+  // ---- near path: X1 = I + E1; a second step unless the first left |e| <= 1e-8; A = X^H H X
+  // for the Jacobi sweeps unless no pair is left coupled (then the eigenvalues are lambda) ----
+  {
+    const int* step2 = flags + GATE_STEP2;
+    const int* amg = flags + GATE_AM;
+    identity_plus_kernel<T><<<eb, 256, 0, s>>>(Li, n, Vm, far, st);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, A2, st, nullptr, nullptr, nullptr, step2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Lm, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2);
+    oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, part, lam, step2, st);
+    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol, 1e-14, Li, part2, step2, st);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Li, false, n, T1, st, Vm, nullptr, nullptr, step2);
+    copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, step2, st);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, amg);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, amg);
+    hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, amg);
+    lambda_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(lam, n, Am, flags + GATE_LAMBDA, st);
+    c->launches += 13;
+    rc = check_cuda(c, cudaGetLastError(), "near-path launch");
+    if (rc != PAWFD_OK) return rc;
+  }
+  rc = launch_jacobi<T>(c, n, Am, A2, Vm, flags + GATE_JACOBI);
   if (rc != PAWFD_OK) return rc;
   sort_kernel<T><<<n, 128, 0, s>>>(Am, Vm, n, eps, T1, c->d_status);
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, true, T1, false, n, C, c->d_status);
+  // C = L^-H U (far path) or U (near path: a copy)
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, true, T1, false, n, C, st, nullptr, near, T1);
   phase_fix_kernel<T><<<n, 256, 0, s>>>(C, n, c->d_status);
   c->launches += 3;
   return check_cuda(c, cudaGetLastError(), "subspace launch");

@@ -239,6 +239,36 @@ def test_subspace_against_oracle_random(dev):
     del s, api
 
 
+@pytest.mark.parametrize("cplx", [False, True])
+def test_subspace_near_ritz_basis(dev, cplx):
+    """H_nm, S_nm of bands that are already (nearly) Ritz vectors: S close to I, H close to
+    diagonal, as in the iterated Rayleigh-Ritz step.  Exact, slightly and less slightly
+    perturbed, and with degenerate eigenvalues (pairs left to the Jacobi sweeps)."""
+    sysm = synth.make_system((8, 8, 8), (4.0, 4.0, 4.0), 0, synth.PSET_SP, 1, k=(0.1, 0.0, 0.0) if cplx else
+                             (0.0, 0.0, 0.0), complex_wf=cplx)
+    ctx = ctx_for(sysm, 200, dev)
+    for n in (3, 64, 200):
+        def rnd(seed):
+            a = synth.uniform(n, seed, n * n, -1, 1).reshape(n, n)
+            if cplx:
+                a = a + 1j * synth.uniform(n, seed + 50, n * n, -1, 1).reshape(n, n)
+            return 0.5 * (a + a.conj().T)
+        H0 = rnd(11) * 30
+        B = rnd(12)
+        S0 = B @ B.conj().T / n + np.eye(n)
+        _, C0, _ = O.subspace_diag(H0, S0)
+        H1 = C0.conj().T @ H0 @ C0
+        S1 = C0.conj().T @ S0 @ C0
+        Hdeg = np.diag(np.repeat(np.arange(n // 2 + 1, dtype=float), 2)[:n]).astype(H1.dtype)
+        cases = [(H1, S1), (H1 + 1e-9 * rnd(13), S1 + 1e-9 * rnd(14)), (H1 + 1e-6 * rnd(15), S1 + 1e-6 * rnd(16)),
+                 (Hdeg + 1e-9 * rnd(17), np.eye(n) + 1e-10 * rnd(18))]
+        for H, S in cases:
+            ref_eps, _, _ = O.subspace_diag(H, S)
+            eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
+            check_subspace(eps.cpu().numpy(), C.cpu().numpy(), H, S, ref_eps)
+    ctx.close()
+
+
 @pytest.mark.slow
 def test_gamma_96c_256b_full_size(dev):
     """The benchmark workload at full size, in the benchmark's launch configuration."""
