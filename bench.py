@@ -43,12 +43,7 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # Measured DRAM traffic per unit of the dominant stage's kernels (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum on a small case, profiles/dram_apply_H_fp64_64c_128b.md), valid only
 # while the kernels' sources are the ones that were measured.
-TRAFFIC = {
-    ("apply_H", "fp64", False): {
-        "per_point_band": 15.89, "per_atom_band": 38585.0,
-        "sources": {"paper_2310_14776_gb300/csrc/stencil.cu": "9aee46d1fbc4aa43a9d6ab9eafebff03b565df86",
-                    "paper_2310_14776_gb300/csrc/nonlocal.cu": "6322b1ed8ccada121d05dbddc6446954e8a3cab2"}},
-}
+TRAFFIC = {}
 
 
 def stage_traffic(stage, precision, cplx, K, nb, natoms):
@@ -187,6 +182,7 @@ def run_gpu(args):
     esize = psi0.element_size()
     psi = [psi0, torch.empty_like(psi0)]
     work = {"Hpsi": ctx.empty_bands(nb), "Spsi": ctx.empty_bands(nb),
+            "P": torch.empty((max(ctx.Ip, 1), nb), dtype=ctx.dtype, device=dev),
             "Hnm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
             "Snm": torch.empty((nb, nb), dtype=ctx.mat_dtype, device=dev),
             "eps": torch.empty(nb, dtype=torch.float64, device=dev),
@@ -195,23 +191,20 @@ def run_gpu(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def step(cur, nxt, marks=None):
-        # marks: events between the stages apply_H | apply_S | Gram H | Gram S | subspace | rotate
+        # the calls of pawfd_rr_step, one library call per stage; marks: events between the
+        # stages apply_HS | Gram H and S | subspace | rotate
         def mark(i):
             if marks is not None:
                 marks[i].record(stream)
         mark(0)
-        ctx.apply_H(cur, out=work["Hpsi"])
+        ctx.apply_hs(cur, Hpsi=work["Hpsi"], Spsi=work["Spsi"], P=work["P"])
         mark(1)
-        ctx.apply_S(cur, out=work["Spsi"])
+        ctx.gram_hs(cur, work["Hpsi"], work["P"], Hnm=work["Hnm"], Snm=work["Snm"])
         mark(2)
-        ctx.gram(cur, work["Hpsi"], M=work["Hnm"], hermitian=True)
-        mark(3)
-        ctx.gram(cur, work["Spsi"], M=work["Snm"], hermitian=True)
-        mark(4)
         ctx.subspace_diag(work["Hnm"], work["Snm"], eps=work["eps"], C=work["C"], overwrite=True, check=False)
-        mark(5)
+        mark(3)
         ctx.rotate(cur, work["C"], out=nxt)
-        mark(6)
+        mark(4)
 
     for i in range(args.warmup):
         step(psi[i % 2], psi[(i + 1) % 2])
@@ -224,7 +217,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
-    marks = [[ev() for _ in range(7)] for _ in range(args.steps)]
+    marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
     t0, t1 = ev(), ev()
     t0.record(stream)
     for i in range(args.steps):
@@ -241,8 +234,8 @@ def run_gpu(args):
         tt = torch.tensor([elapsed], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         elapsed = tt.item()
-    step_ms = [m[0].elapsed_time(m[6]) for m in marks]
-    names = ["apply_H", "apply_S", "gram_H", "gram_S", "subspace_diag", "rotate"]
+    step_ms = [m[0].elapsed_time(m[4]) for m in marks]
+    names = ["apply_HS", "gram_HS", "subspace_diag", "rotate"]
     stages = {nm: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks) for i, nm in enumerate(names)}
     drift = float(torch.max(torch.abs(work["eps"] - eps_first)).item())
 
@@ -258,19 +251,17 @@ def run_gpu(args):
     cfac = 4 if cplx else 1
     # algorithmic work per stage (see the roofline table of the design notes)
     work_units = {
-        # FP64: 19 FP64 instructions per point-band (9 add, 9 FMA, 1 mul), vs the FP64 issue rate
-        "apply_H": ("alu", 19.0 * nb * K * (2 if cplx else 1), FP64_NOMINAL_TFLOPS / 2 * 1e12, "FP64 instr/s")
-        if not mixed else ("hbm", 2.0 * esize * nb * K, hbm * 1e9, "B/s"),
-        "gram_H": ("tensor", 2.0 * products * cfac * nb * (nb + 1) / 2 * K, bf16 * 1e12, "BF16 FLOP/s"),
-        "gram_S": ("tensor", 2.0 * products * cfac * nb * (nb + 1) / 2 * K, bf16 * 1e12, "BF16 FLOP/s"),
+        # H psi and S psi: psi read twice (stencil, copy), H psi and S psi written once
+        "apply_HS": ("hbm", 4.0 * esize * nb * K, hbm * 1e9, "B/s"),
+        # the two Hermitian Gram matrices (upper triangles), digit products on the tensor cores
+        "gram_HS": ("tensor", 2 * 2.0 * products * cfac * nb * (nb + 1) / 2 * K, bf16 * 1e12, "BF16 FLOP/s"),
         "rotate": ("tensor", 2.0 * products * cfac * nb * nb * K, bf16 * 1e12, "BF16 FLOP/s"),
     }
     dom = max((k for k in stages if k in work_units), key=lambda k: stages[k])
     bound, amount, peak, unit = work_units[dom]
     achieved = amount / (stages[dom] * 1e-3)
-    kernel_of = {"apply_H": "kinetic_local_kernel + project_kernel + nonlocal_add_kernel",
-                 "gram_H": "slice_kernel + sliced_gram_kernel (digit-product Gram)",
-                 "gram_S": "slice_kernel + sliced_gram_kernel (digit-product Gram)",
+    kernel_of = {"apply_HS": "stencil + project_kernel + nonlocal_add_kernel (x2) + copy",
+                 "gram_HS": "slice_kernel (x2) + sliced_gram_kernel (x2) + overlap correction",
                  "rotate": "slice_t_kernel + sliced_gram_kernel (digit-product rotation)"}
     scale = 1e12 if unit.endswith("FLOP/s") or unit == "FP64 instr/s" else 1e9
     roof_unit = {"BF16 FLOP/s": "TFLOP/s", "FP64 instr/s": "Tinstr/s", "B/s": "GB/s"}[unit]
@@ -288,7 +279,7 @@ def run_gpu(args):
         "rr_steps_per_s": args.steps * world / elapsed,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "stages_ms": stages,
-        "apply_H_gptband_s": nb * K / (stages["apply_H"] * 1e-3) / 1e9,
+        "apply_HS_gptband_s": nb * K / (stages["apply_HS"] * 1e-3) / 1e9,
         "eig_drift_ha": drift,
         "roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
                      "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,

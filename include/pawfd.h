@@ -159,6 +159,23 @@ int pawfd_gram(pawfd_ctx* ctx, const void* A, const void* B, int nb, void* M);
  * makes the diagonal exactly real.  Arguments and layout as pawfd_gram. */
 int pawfd_gram_hermitian(pawfd_ctx* ctx, const void* A, const void* B, int nb, void* M);
 
+/* H psi and S psi for nb bands with one set of projections (Eq. (dh) and the PAW overlap
+ * operator; the projections of psi are computed once and serve both nonlocal terms).  If
+ * P_out is not NULL it receives the projections ([Ip][nb]); otherwise the context's scratch
+ * holds them.  psi, hpsi, spsi: [nb][K], pairwise distinct.  Asynchronous like the calls
+ * above. */
+int pawfd_apply_HS(pawfd_ctx* ctx, const void* psi, int nb, void* hpsi, void* spsi, void* P_out);
+
+/* The two Gram matrices of the subspace step (SCF step 1 of the Kohn-Sham section):
+ *   Hnm = dV psi^H (H psi)                         (as pawfd_gram_hermitian with B = H psi)
+ *   Snm = dV psi^H psi + sum_a P_a^H dS^a P_a      (the PAW overlap <psi_n|S|psi_m>, its
+ *                                                    projector term from the projections P)
+ * P: the projections of psi ([Ip][nb], as written by pawfd_project / pawfd_apply_HS; may be
+ * NULL only when the context has no atoms).  With the tensor-core contraction and real bands
+ * the digits of psi are made once and serve both matrices.  Hnm, Snm: [nb][nb] FP64 of the
+ * context's kind, Hermitian (mirrored, real diagonal); they may not alias.  Asynchronous. */
+int pawfd_gram_hs(pawfd_ctx* ctx, const void* psi, const void* hpsi, int nb, const void* P, void* Hnm, void* Snm);
+
 /* Subspace diagonalization: given Hermitian H_nm and positive definite S_nm ([nb][nb],
  * FP64 of the context's kind: double or interleaved complex double), solve H C = S C diag(eps): symmetrize, S = L L^H, A = L^-1 H L^-H,
  * Jacobi A = U diag(eps) U^H, C = L^-H U.  eps (double [nb]) ascending with stable ties;

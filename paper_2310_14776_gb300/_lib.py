@@ -46,6 +46,8 @@ SIGNATURES = {
     "pawfd_apply_kinetic_local": ([VP, VP, I, VP], I),
     "pawfd_gram": ([VP, VP, VP, I, VP], I),
     "pawfd_gram_hermitian": ([VP, VP, VP, I, VP], I),
+    "pawfd_apply_HS": ([VP, VP, I, VP, VP, VP], I),
+    "pawfd_gram_hs": ([VP, VP, VP, I, VP, VP, VP], I),
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
     "pawfd_refine": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),

@@ -143,6 +143,37 @@ class Context:
     def apply_S(self, psi, out=None, P=None):
         return self._apply(self.lib.pawfd_apply_S, psi, out, P)
 
+    def apply_hs(self, psi, Hpsi=None, Spsi=None, P=None):
+        """H psi and S psi with one set of projections (pawfd_apply_HS); returns (Hpsi, Spsi, P)."""
+        nb = self._bands(psi, "psi")
+        Hpsi = self.empty_bands(nb) if Hpsi is None else Hpsi
+        Spsi = self.empty_bands(nb) if Spsi is None else Spsi
+        self._bands(Hpsi, "Hpsi")
+        self._bands(Spsi, "Spsi")
+        P = torch.empty((max(self.Ip, 1), nb), dtype=self.dtype, device=self.device) if P is None else P
+        if P.numel() < self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous():
+            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        self._call(self.lib.pawfd_apply_HS, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(Hpsi.data_ptr()),
+                   ctypes.c_void_p(Spsi.data_ptr()), ctypes.c_void_p(P.data_ptr()))
+        return Hpsi, Spsi, P
+
+    def gram_hs(self, psi, Hpsi, P, Hnm=None, Snm=None):
+        """H_nm = dV psi^H H psi and S_nm = dV psi^H psi + sum_a P_a^H dS^a P_a (pawfd_gram_hs);
+        P holds the projections of psi.  Returns (Hnm, Snm)."""
+        nb = self._bands(psi, "psi")
+        if self._bands(Hpsi, "Hpsi") != nb:
+            raise ValueError("psi and Hpsi must hold the same number of bands")
+        Hnm = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if Hnm is None else Hnm
+        Snm = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if Snm is None else Snm
+        self._mat(Hnm, nb, "Hnm")
+        self._mat(Snm, nb, "Snm")
+        if P is not None and (P.numel() < self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous()):
+            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        self._call(self.lib.pawfd_gram_hs, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(Hpsi.data_ptr()), nb,
+                   ctypes.c_void_p(P.data_ptr()) if P is not None else None, ctypes.c_void_p(Hnm.data_ptr()),
+                   ctypes.c_void_p(Snm.data_ptr()))
+        return Hnm, Snm
+
     def gram(self, A, B, M=None, hermitian: bool = False):
         """M = dV A^H B.  ``hermitian``: B = X A for a Hermitian X; only the upper half is
         computed and mirrored (pawfd_gram_hermitian)."""
@@ -187,13 +218,11 @@ class Context:
         ``keep_matrices`` the returned Hnm / Snm are the solver's workspace after the solve."""
         nb = self._bands(psi, "psi")
         w = work if work is not None else {}
-        Hpsi = self.apply_H(psi, out=w.get("Hpsi"))
-        Spsi = self.apply_S(psi, out=w.get("Spsi"))
-        Hnm = self.gram(psi, Hpsi, M=w.get("Hnm"), hermitian=True)
-        Snm = self.gram(psi, Spsi, M=w.get("Snm"), hermitian=True)
+        Hpsi, Spsi, P = self.apply_hs(psi, Hpsi=w.get("Hpsi"), Spsi=w.get("Spsi"), P=w.get("P"))
+        Hnm, Snm = self.gram_hs(psi, Hpsi, P, Hnm=w.get("Hnm"), Snm=w.get("Snm"))
         eps, C = self.subspace_diag(Hnm, Snm, eps=w.get("eps"), C=w.get("C"), overwrite=not keep_matrices, check=check)
         psi_rot = self.rotate(psi, C, out=w.get("psi_rot"))
-        return {"Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}
+        return {"Hpsi": Hpsi, "Spsi": Spsi, "P": P, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "psi_rot": psi_rot}
 
     def alloc_work(self, nb: int) -> dict:
         """Device arrays of one Rayleigh-Ritz step for nb bands (the keys rr_step fills)."""

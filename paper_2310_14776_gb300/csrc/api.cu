@@ -31,6 +31,36 @@ int apply_X(pawfd_ctx* c, int which, const void* psi, int nb, void* out, void* P
 
 }  // namespace
 
+namespace pawfd {
+int launch_apply_hs(pawfd_ctx* c, const void* psi, int nb, void* hpsi, void* spsi, void* P) {
+  int rc = launch_kinetic_local(c, psi, nb, hpsi);
+  if (rc == PAWFD_OK) rc = launch_project(c, psi, nb, P);
+  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dH, hpsi);
+  if (rc == PAWFD_OK)
+    rc = check_cuda(c, cudaMemcpyAsync(spsi, psi, band_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
+                                       c->stream), "copy psi");
+  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dS, spsi);
+  return rc;
+}
+}  // namespace pawfd
+
+extern "C" int pawfd_apply_HS(pawfd_ctx* c, const void* psi, int nb, void* hpsi, void* spsi, void* P_out) {
+  int rc = check_bands(c, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (!psi || !hpsi || !spsi) return fail(c, PAWFD_EINVAL, "null array");
+  if (psi == hpsi || psi == spsi || hpsi == spsi) return fail(c, PAWFD_EINVAL, "arrays may not alias");
+  return launch_apply_hs(c, psi, nb, hpsi, spsi, P_out ? P_out : c->d_P);
+}
+
+extern "C" int pawfd_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, const void* P, void* Hnm,
+                             void* Snm) {
+  int rc = check_bands(c, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (!psi || !hpsi || !Hnm || !Snm || (!P && c->at.Ip > 0)) return fail(c, PAWFD_EINVAL, "null array");
+  if (Hnm == Snm) return fail(c, PAWFD_EINVAL, "Hnm and Snm may not alias");
+  return launch_gram_hs(c, psi, hpsi, nb, P, Hnm, Snm);
+}
+
 extern "C" int pawfd_apply_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
   int rc = check_bands(c, nb);
   if (rc != PAWFD_OK) return rc;

@@ -2,8 +2,9 @@
 //
 // pawfd_rr_step enqueues the whole eigensolver step of SCF step 1 (Kohn-Sham section) for one
 // context: H psi and S psi (Eq. (dh) and the overlap operator of the PAW section, with one set
-// of projections serving both), the Hermitian Gram matrices, the subspace diagonalization and
-// the band rotation.
+// of projections serving both), the Hermitian Gram matrices (S_nm as dV psi^H psi plus the
+// projector term, from the same slicing of psi as H_nm), the subspace diagonalization and the
+// band rotation.
 //
 // A batch holds many such steps for independent contexts (different grids, band counts and
 // atoms).  Each job runs on a stream of its own, forked from and joined back to the caller's
@@ -36,15 +37,8 @@ int enqueue_rr_step(pawfd_ctx* c, const pawfd_rr_job& j) {
     return fail(c, PAWFD_EINVAL, "null array");
   if (j.psi == j.psi_out || j.psi == j.hpsi || j.psi == j.spsi || j.hpsi == j.spsi || j.Hnm == j.Snm)
     return fail(c, PAWFD_EINVAL, "arrays may not alias");
-  int rc = launch_kinetic_local(c, j.psi, nb, j.hpsi);
-  if (rc == PAWFD_OK) rc = launch_project(c, j.psi, nb, c->d_P);
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, c->d_P, nb, c->at.d_dH, j.hpsi);
-  if (rc == PAWFD_OK)
-    rc = check_cuda(c, cudaMemcpyAsync(j.spsi, j.psi, band_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
-                                       c->stream), "copy psi");
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, c->d_P, nb, c->at.d_dS, j.spsi);
-  if (rc == PAWFD_OK) rc = launch_gram(c, j.psi, j.hpsi, nb, j.Hnm, true);
-  if (rc == PAWFD_OK) rc = launch_gram(c, j.psi, j.spsi, nb, j.Snm, true);
+  int rc = launch_apply_hs(c, j.psi, nb, j.hpsi, j.spsi, c->d_P);
+  if (rc == PAWFD_OK) rc = launch_gram_hs(c, j.psi, j.hpsi, nb, c->d_P, j.Hnm, j.Snm);
   if (rc == PAWFD_OK) rc = launch_subspace_diag(c, nb, j.Hnm, j.Snm, j.eps, j.C);
   if (rc == PAWFD_OK) rc = launch_rotate(c, j.psi, nb, j.C, j.psi_out);
   return rc;

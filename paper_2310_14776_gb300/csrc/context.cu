@@ -246,7 +246,7 @@ void free_ctx(pawfd_ctx* c) {
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
-                  c->d_vshift_df, c->d_flags, c->d_oa};
+                  c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -317,6 +317,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
   const size_t nb = (size_t)c->max_bands;
   if (rc == PAWFD_OK) {
     c->d_P = dev_alloc<char>(c, band_size(c) * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
+    c->d_Q = dev_alloc<char>(c, mat_size(c) * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
     // split-K partials: about eight 64 x 64 tiles per SM at max_bands (Hermitian tiling),
     // capped at 256 MB
     const size_t t1 = (nb + 63) / 64, tiles = t1 * (t1 + 1) / 2;

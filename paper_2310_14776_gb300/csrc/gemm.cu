@@ -323,6 +323,16 @@ int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, boo
   return fail(c, PAWFD_EINVAL, "unsupported dtype");
 }
 
+int launch_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, const void* P, void* Hnm, void* Snm) {
+  int rc = PAWFD_OK;
+  if (!(c->use_tc && gram_pair_tc(c, psi, hpsi, nb, Hnm, Snm, &rc))) {
+    rc = launch_gram(c, psi, hpsi, nb, Hnm, true);
+    if (rc == PAWFD_OK) rc = launch_gram(c, psi, psi, nb, Snm, true);
+  }
+  if (rc != PAWFD_OK) return rc;
+  return launch_overlap_correction(c, P, nb, Snm);
+}
+
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
   if (c->use_tc) return launch_rotate_tc(c, psi, nb, C, out);
   return dispatch_band(c, [&](auto tag) {

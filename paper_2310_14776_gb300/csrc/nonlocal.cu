@@ -121,6 +121,54 @@ __global__ void __launch_bounds__(NT) nonlocal_add_kernel(const T* __restrict__ 
   }
 }
 
+// Q[row_a + i][m] = sum_j dS^a[i][j] P[row_a + j][m] in FP64: one CTA per (atom, 256 bands)
+template <class T>
+__global__ void __launch_bounds__(256) overlap_q_kernel(const T* __restrict__ P, int nb,
+                                                        const real_t<T>* __restrict__ dmat, AtomArgs at,
+                                                        wide_t<T>* __restrict__ Q) {
+  using W = wide_t<T>;
+  const int a = blockIdx.x, m = blockIdx.y * 256 + threadIdx.x;
+  if (m >= nb) return;
+  const int I = at.nproj[a], row = at.row_off[a];
+  const real_t<T>* __restrict__ dX = dmat + at.dmat_off[a];
+  for (int i = 0; i < I; ++i) {
+    W q = zero<W>();
+    for (int j = 0; j < I; ++j) fma_real(q, (double)dX[i * I + j], widen(P[(long long)(row + j) * nb + m]));
+    Q[(long long)(row + i) * nb + m] = q;
+  }
+}
+
+// M[n][m] += sum_r conj(P[r][n]) Q[r][m] for n <= m, mirrored to M[m][n] (M Hermitian; the
+// diagonal keeps its real part).  16 x 16 output tiles on or above the diagonal.
+template <class T>
+__global__ void __launch_bounds__(256) overlap_corr_kernel(const T* __restrict__ P, const wide_t<T>* __restrict__ Q,
+                                                           int nb, int Ip, wide_t<T>* __restrict__ M) {
+  using W = wide_t<T>;
+  if (blockIdx.y > blockIdx.x) return;   // tile (row block y, column block x), y <= x
+  __shared__ W Ps[16][17];
+  __shared__ W Qs[16][17];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int n = blockIdx.y * 16 + ty, m = blockIdx.x * 16 + tx;
+  W acc = zero<W>();
+  for (int r0 = 0; r0 < Ip; r0 += 16) {
+    const int r = r0 + tx, rq = r0 + ty;
+    const int nn = blockIdx.y * 16 + ty, mm = blockIdx.x * 16 + tx;
+    Ps[ty][tx] = (r < Ip && nn < nb) ? conjx(widen(P[(long long)r * nb + nn])) : zero<W>();
+    Qs[ty][tx] = (rq < Ip && mm < nb) ? Q[(long long)rq * nb + mm] : zero<W>();
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) fma_plain(acc, Ps[ty][k], Qs[k][tx]);
+    __syncthreads();
+  }
+  if (n >= nb || m >= nb || n > m) return;
+  if (n == m) {
+    M[(long long)n * nb + n] = M[(long long)n * nb + n] + from_real<W>(realx(acc));
+  } else {
+    M[(long long)n * nb + m] = M[(long long)n * nb + m] + acc;
+    M[(long long)m * nb + n] = M[(long long)m * nb + n] + conjx(acc);
+  }
+}
+
 AtomArgs atom_args(const pawfd_ctx* c) {
   AtomArgs a;
   a.nproj = c->at.d_nproj;
@@ -166,6 +214,24 @@ int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat,
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "nonlocal_add launch");
+}
+
+// S_nm += sum_a P_a^H dS^a P_a (the overlap's nonlocal term of the S Gram matrix); M is the
+// Hermitian FP64 [nb][nb] matrix, P the projections [Ip][nb] of the context's band dtype
+int launch_overlap_correction(pawfd_ctx* c, const void* P, int nb, void* M) {
+  if (c->at.natoms == 0) return PAWFD_OK;
+  if (c->at.Imax > IMAX) return fail(c, PAWFD_EINVAL, "more than 32 projectors on one atom");
+  const int tb = (nb + 15) / 16;
+  dispatch_band(c, [&](auto tag) {
+    using T = decltype(tag);
+    using W = wide_t<T>;
+    overlap_q_kernel<T><<<dim3(c->at.natoms, (nb + 255) / 256), 256, 0, c->stream>>>(
+        (const T*)P, nb, (const real_t<T>*)c->at.d_dS, atom_args(c), (W*)c->d_Q);
+    overlap_corr_kernel<T><<<dim3(tb, tb), 256, 0, c->stream>>>((const T*)P, (const W*)c->d_Q, nb, c->at.Ip, (W*)M);
+    return 0;
+  });
+  c->launches += 2;
+  return check_cuda(c, cudaGetLastError(), "overlap correction launch");
 }
 
 }  // namespace pawfd

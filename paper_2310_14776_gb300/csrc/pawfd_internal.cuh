@@ -144,6 +144,8 @@ struct TcScratch {
   size_t part_bytes = 0;
   CUtensorMap mapA;
   CUtensorMap mapB;
+  CUtensorMap mapAB;           // slicesA with the B operand's box (the Gram of psi with itself)
+  void* part2 = nullptr;       // partials of the second Gram of a pair
   // band rotation
   long long rot_Lc = 0;        // contraction length (bands, x2 for complex) padded to chunks
   int rot_rowsA_alloc = 0;
@@ -178,6 +180,7 @@ struct pawfd_ctx {
   void* d_vshift_df = nullptr;                // real FP64: the same as (hi, lo) FP32 pairs
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
+  void* d_Q = nullptr;                        // [Ip][max_bands] FP64 dS P of the overlap correction
   void* d_gram_part = nullptr;                // split-K partial Gram matrices
   size_t gram_part_bytes = 0;
   void* d_work = nullptr;                     // subspace workspace (7 matrices of max_bands^2)
@@ -241,6 +244,12 @@ int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
+int launch_overlap_correction(pawfd_ctx* c, const void* P, int nb, void* M);
+bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc);
+// H psi and S psi with one set of projections P of psi (written to P)
+int launch_apply_hs(pawfd_ctx* c, const void* psi, int nb, void* hpsi, void* spsi, void* P);
+// H_nm = dV psi^H H psi and S_nm = dV psi^H psi + sum_a P_a^H dS^a P_a (P: projections of psi)
+int launch_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, const void* P, void* Hnm, void* Snm);
 // CTAs of the Ogita-Aishima element kernels and the doubles of their scratch for nb bands
 constexpr int OA_G = 64;
 inline size_t oa_scratch_doubles(int nb) { return 5 * (size_t)OA_G + (size_t)nb; }

@@ -111,16 +111,9 @@ extern "C" int pawfd_refine(pawfd_ctx* c, const void* psi_lo, int nb, void* psi,
   c->launches += 1;
   int rc = check_cuda(c, cudaGetLastError(), "promote launch");
   // 2. H psi' and S psi' in FP64, sharing one set of projections
-  if (rc == PAWFD_OK) rc = launch_kinetic_local(c, psi, nb, hpsi);
-  if (rc == PAWFD_OK) rc = launch_project(c, psi, nb, c->d_P);
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, c->d_P, nb, c->at.d_dH, hpsi);
-  if (rc == PAWFD_OK)
-    rc = check_cuda(c, cudaMemcpyAsync(spsi, psi, band_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
-                                       c->stream), "copy psi");
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, c->d_P, nb, c->at.d_dS, spsi);
+  if (rc == PAWFD_OK) rc = launch_apply_hs(c, psi, nb, hpsi, spsi, c->d_P);
   // 3. FP64 Gram matrices
-  if (rc == PAWFD_OK) rc = launch_gram(c, psi, hpsi, nb, Hnm, true);
-  if (rc == PAWFD_OK) rc = launch_gram(c, psi, spsi, nb, Snm, true);
+  if (rc == PAWFD_OK) rc = launch_gram_hs(c, psi, hpsi, nb, c->d_P, Hnm, Snm);
   if (rc != PAWFD_OK) return rc;
   // 4.-6. Rayleigh quotients, second subspace solve, residual norms
   if (is_complex(c)) return refine_tail<zd>(c, nb, hpsi, spsi, Hnm, Snm, eps, theta, resid, C);

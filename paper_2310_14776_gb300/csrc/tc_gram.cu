@@ -137,6 +137,75 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   return check_cuda(c, cudaGetLastError(), "tensor-core gram launch");
 }
 
+// The two Hermitian Gram matrices of the Rayleigh-Ritz step for real bands from one slicing
+// of psi: M1 = dV psi^T B (B = H psi) and M2 = dV psi^T psi, the second with psi's digit
+// planes as both operands.  Each K block slices psi and B once and runs the two MMA kernels.
+template <class R, int S, int ORD>
+int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, double* M2) {
+  TcScratch& t = c->tc;
+  const long long L = (long long)c->K;
+  const int tiles = sg::herm_tiles(nb);
+  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KC)
+                                                 : t.kblk;
+  const int max_chunks = (int)(Kblk / sg::KC);
+  int nsplit = std::max(1, std::min(max_chunks, c->num_sms / tiles));
+  while (nsplit > 1 && (size_t)nsplit * nb * nb * sizeof(double) > t.part_bytes) --nsplit;
+  __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
+  __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
+  int blk = 0;
+  for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
+    const long long len = std::min(Kblk, L - k0);
+    const int nch = (int)((len + sg::KC - 1) / sg::KC);
+    const int cpc = (nch + nsplit - 1) / nsplit;
+    const int ns = (nch + cpc - 1) / cpc;
+    const long long warps = (long long)nb * nch;
+    cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+    cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
+    sg::slice_kernel<R, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+        A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
+    sg::slice_kernel<R, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+        B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+    sg::GramArgs a = {};
+    a.sigA = t.sigA;
+    a.sigB = t.sigB;
+    a.sig_ldA = t.rowsA_alloc;
+    a.sig_ldB = t.rowsB_alloc;
+    a.maxA = t.maxA;
+    a.maxB = t.maxB;
+    a.rowsA = nb;
+    a.rowsB = nb;
+    a.tilesN = (nb + sg::BN - 1) / sg::BN;
+    a.herm = 1;
+    a.halves = 1;
+    a.half_rows = nb;
+    a.chunks_per_cta = cpc;
+    a.nchunks = nch;
+    a.accumulate = blk > 0;
+    a.klen = len;
+    a.part = (double*)t.part;
+    a.st = c->d_status;
+    if (blk == 0 && ns < nsplit) nsplit = ns;
+    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.mapA, t.mapB, a);
+    // psi^T psi: psi's planes and exponents on both sides
+    sg::GramArgs a2 = a;
+    a2.sigB = t.sigA;
+    a2.sig_ldB = t.rowsA_alloc;
+    a2.maxB = t.maxA;
+    a2.part = (double*)t.part2;
+    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.mapA, t.mapAB, a2);
+    c->launches += 4;
+  }
+  const long long nn = (long long)nb * nb;
+  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, nb,
+                                                                                c->dV, true, M1);
+  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part2, nsplit, nb, nb,
+                                                                                c->dV, true, M2);
+  c->launches += 2;
+  return check_cuda(c, cudaGetLastError(), "tensor-core gram pair launch");
+}
+
 // The rotation's first operand: A_ext[row][k] with k the contraction index.  Real:
 // A[m][n] = C[n][m].  Complex (C interleaved): rows m < nb give the real part of the output,
 // A[m][2n] = Re C[n][m], A[m][2n+1] = -Im C[n][m]; rows nb + m the imaginary part,
@@ -321,6 +390,14 @@ int fused_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool 
   return check_cuda(c, cudaGetLastError(), "fused tensor-core gram launch");
 }
 
+// Hermitian Grams psi^H B and psi^H psi (real bands; false when this form does not apply)
+bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc) {
+  if (!c->tc.ready || is_complex(c) || c->tc_fused) return false;
+  if (is_fp32(c)) *rc = tc_gram_pair_impl<float, 4, 4>(c, (const float*)psi, (const float*)B, nb, (double*)M1, (double*)M2);
+  else *rc = tc_gram_pair_impl<double, 7, 6>(c, (const double*)psi, (const double*)B, nb, (double*)M1, (double*)M2);
+  return true;
+}
+
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
   if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core Gram scratch not set up");
   // the fused kernel reads the operands through TMA: 16-byte aligned base and row stride
@@ -382,6 +459,7 @@ int setup_tc(pawfd_ctx* c) {
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.sigA, sizeof(int) * nchunks * t.rowsA_alloc), "cudaMalloc");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.sigB, sizeof(int) * nchunks * t.rowsB_alloc), "cudaMalloc");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.part, t.part_bytes), "cudaMalloc tc partials");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.part2, t.part_bytes), "cudaMalloc tc partials");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.maxA, sizeof(int) * t.rowsA_alloc), "cudaMalloc");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.maxB, sizeof(int) * t.rowsB_alloc), "cudaMalloc");
   if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
@@ -391,6 +469,7 @@ int setup_tc(pawfd_ctx* c) {
   if (rc != PAWFD_OK) return rc;
   rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BM);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BN);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapAB, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) {
     const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if (S == 7) {
@@ -455,7 +534,7 @@ int setup_tc(pawfd_ctx* c) {
 
 void free_tc(pawfd_ctx* c) {
   TcScratch& t = c->tc;
-  void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.maxA, t.maxB,
+  void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.part2, t.maxA, t.maxB,
                t.rotA, t.rotSlicesA, t.rotSlicesB, t.rotSigA, t.rotSigB, t.rotMaxA, t.rotMaxB,
                t.fsigA, t.fsigB, t.fmaxA, t.fmaxB};
   for (void* q : p)

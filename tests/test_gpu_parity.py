@@ -122,6 +122,41 @@ def test_edge_cases(dev, case):
     full_step_parity(s, case["nb"], 301, dev)
 
 
+@pytest.mark.parametrize("precision,cplx", [("fp64", False), ("fp64", True), ("mixed", False), ("mixed", True)])
+def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx):
+    """pawfd_gram_hs: H_nm from the shared slicing of psi is the same Hermitian Gram as
+    pawfd_gram_hermitian(psi, H psi); S_nm = dV psi^H psi + sum_a P^H dS P agrees with the
+    Gram of psi and S psi (the oracle's form) to the precision of the bands."""
+    from paper_2310_14776_gb300 import api
+    k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=511, k=k, complex_wf=cplx)
+    nb = 150
+    ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+    psi_np = synth.make_psi(s, nb, 512)
+    psi = to_dev(psi_np, dev).to(ctx.dtype)
+    hpsi, spsi, P = ctx.apply_hs(psi)
+    Hnm, Snm = ctx.gram_hs(psi, hpsi, P)
+    Hsep = ctx.gram(psi, hpsi, hermitian=True)
+    Ssep = ctx.gram(psi, spsi, hermitian=True)
+    Hnm, Snm, Hsep, Ssep = (t.cpu().numpy() for t in (Hnm, Snm, Hsep, Ssep))
+    assert np.array_equal(Snm, Snm.conj().T) and np.array_equal(Hnm, Hnm.conj().T)
+    if precision == "fp64":
+        assert np.array_equal(Hnm, Hsep)
+        assert_close_matrix(Snm, Ssep)
+        ref = O.rayleigh_ritz(s, psi_np)
+        assert_close_matrix(Snm, ref["Snm"])
+        assert_close_matrix(Hnm, ref["Hnm"])
+    else:
+        # S psi in FP32 rounds each value once: the two forms differ at the FP32 level
+        assert_close_matrix(Hnm, Hsep, rel=1e-12)
+        assert_close_matrix(Snm, Ssep, rel=1e-6)
+        # against the oracle's FP64 S_nm of the FP32-rounded bands (the projections are FP32)
+        psi32 = psi.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+        ref = O.rayleigh_ritz(s, psi32)
+        assert_close_matrix(Snm, ref["Snm"], rel=1e-6)
+    ctx.close()
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_hermitian_gram_equals_full_gram(dev, cplx):
     k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
