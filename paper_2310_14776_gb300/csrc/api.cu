@@ -33,12 +33,10 @@ int apply_X(pawfd_ctx* c, int which, const void* psi, int nb, void* out, void* P
 
 namespace pawfd {
 int launch_apply_hs(pawfd_ctx* c, const void* psi, int nb, void* hpsi, void* spsi, void* P) {
-  int rc = launch_kinetic_local(c, psi, nb, hpsi);
+  // the stencil pass also writes S psi's first term (psi itself), so psi is read once
+  int rc = launch_kinetic_local(c, psi, nb, hpsi, spsi);
   if (rc == PAWFD_OK) rc = launch_project(c, psi, nb, P);
   if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dH, hpsi);
-  if (rc == PAWFD_OK)
-    rc = check_cuda(c, cudaMemcpyAsync(spsi, psi, band_size(c) * c->K * (size_t)nb, cudaMemcpyDeviceToDevice,
-                                       c->stream), "copy psi");
   if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dS, spsi);
   return rc;
 }

@@ -234,7 +234,7 @@ int fail(pawfd_ctx* c, int code, const std::string& msg);
 int check_cuda(pawfd_ctx* c, cudaError_t e, const char* what);
 
 // kernels (launchers), each enqueued on c->stream; return PAWFD_OK or an error code
-int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out);
+int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out, void* cpy = nullptr);
 int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P);
 int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out);
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);

@@ -25,6 +25,7 @@ struct StencilArgs {
   cplx<R> ph[3];                // exp(i k_c L_c)
   const R* vshift;              // v(r) - 1/2 w_0 sum_c 1/h_c^2
   int zchunk, nzc;
+  void* cpy;                    // optional second output: a copy of psi (the 1 of S = 1 + ...)
 };
 
 template <class R>
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(TX * TY) kinetic_local_kernel(const T* __restr
   const int z1 = min(z0 + a.zchunk, a.n3);
   const T* __restrict__ src = psi + (long long)band * a.K;
   T* __restrict__ dst = out + (long long)band * a.K;
+  T* __restrict__ cp = a.cpy ? (T*)a.cpy + (long long)band * a.K : nullptr;
   const int x = X0 + tx, y = Y0 + ty;
   const bool active = x < a.n1 && y < a.n2;
 
@@ -106,12 +108,13 @@ __global__ void __launch_bounds__(TX * TY) kinetic_local_kernel(const T* __restr
       fma_real(acc, a.wz[1], q[5] + q[1]);
       fma_real(acc, a.wz[2], q[6] + q[0]);
       dst[r] = acc;
+      if (cp) cp[r] = q[3];   // the point itself: no wrap, no phase
     }
   }
 }
 
 template <class T>
-int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
+int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out, T* cpy) {
   using R = real_t<T>;
   StencilArgs<R> a;
   a.n1 = c->n[0];
@@ -141,6 +144,7 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gx, gy, nbl * a.nzc), block(TX, TY);
+    a.cpy = cpy ? (void*)(cpy + (size_t)b0 * c->K) : nullptr;
     kinetic_local_kernel<T><<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K, out + (size_t)b0 * c->K, a);
     c->launches += 1;
   }
@@ -149,22 +153,26 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out) {
 
 }  // namespace
 
-int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out);
-int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out);
-int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out);
+int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy);
+int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy);
+int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out, double* cpy);
 
-int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out) {
+// out = (-1/2 Lap + v) psi; with cpy != null the kernels also write psi to cpy (the first term
+// of S psi = psi + sum |p> dS <p|psi>), which saves the separate copy pass
+int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out, void* cpy) {
   if (c->dtype == PAWFD_R64 && c->stencil_df && c->fast_stencil &&
-      launch_kinetic_local_df(c, (const double*)psi, nb, (double*)out) == PAWFD_OK)
+      launch_kinetic_local_df(c, (const double*)psi, nb, (double*)out, (double*)cpy) == PAWFD_OK)
     return PAWFD_OK;
   if (c->dtype == PAWFD_R32 && c->fast_stencil) {
-    if (c->stencil_variant != 1 && launch_kinetic_local_ring(c, (const float*)psi, nb, (float*)out) == PAWFD_OK)
+    if (c->stencil_variant != 1 &&
+        launch_kinetic_local_ring(c, (const float*)psi, nb, (float*)out, (float*)cpy) == PAWFD_OK)
       return PAWFD_OK;
-    if (launch_kinetic_local_f32x4(c, (const float*)psi, nb, (float*)out) == PAWFD_OK) return PAWFD_OK;
+    if (launch_kinetic_local_f32x4(c, (const float*)psi, nb, (float*)out, (float*)cpy) == PAWFD_OK)
+      return PAWFD_OK;
   }
   return dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
-    return kinetic_local_impl<T>(c, (const T*)psi, nb, (T*)out);
+    return kinetic_local_impl<T>(c, (const T*)psi, nb, (T*)out, (T*)cpy);
   });
 }
 

@@ -8,7 +8,8 @@
 //   * the FP64 input is split into hi (rounded to 24 bits) and lo (the rest, rounded to 24
 //     bits) with integer operations on the IEEE fields, off the FP64 pipe;
 //   * the 19-term sum uses error-free transformations (TwoSum; products with FMA), about 190
-//     FP32 operations per point, with relative error of order 2^-46 of the terms;
+//     FP32 operations per point, with relative error of order 2^-46 of the terms; the x, y
+//     and z terms form three independent chains that are merged at the end;
 //   * only the final hi + lo uses the FP64 pipe (one addition per point; both parts are
 //     widened to FP64 with integer operations).
 // Layout of the work as the general kernel: a CTA owns a 32 x 8 (x, y) column of one band and
@@ -33,6 +34,7 @@ struct DFArgs {
   DF wx[3], wy[3], wz[3];   // -1/2 w_m / h_c^2 as hi + lo
   const float2* vshift;     // v(r) - 1/2 w_0 sum 1/h_c^2 as (hi, lo)
   int zchunk, nzc;
+  double* cpy;              // optional copy of psi (first band of this launch), or null
 };
 
 // x = hi + lo: hi = x rounded to 24 bits, lo = x - hi rounded to 24 bits (so hi + lo equals x
@@ -92,6 +94,26 @@ __device__ __forceinline__ void tap(DF& acc, DF w, DF p, DF m) {
   acc.lo += te + pe;
 }
 
+// w (p + m) as a new pair (hi: the rounded product, lo: every rounding error so far)
+__device__ __forceinline__ DF tap0(DF w, DF p, DF m) {
+  float s, e;
+  two_sum(p.hi, m.hi, s, e);
+  const float slo = e + (p.lo + m.lo);
+  const float ph = s * w.hi;
+  float pe = fmaf(s, w.hi, -ph);
+  pe = fmaf(s, w.lo, pe);
+  pe = fmaf(slo, w.hi, pe);
+  return {ph, pe};
+}
+
+// acc += b (pairs): the high parts added error-free, the low parts and the error summed
+__device__ __forceinline__ void merge(DF& acc, DF b) {
+  float t, te;
+  two_sum(acc.hi, b.hi, t, te);
+  acc.hi = t;
+  acc.lo += te + b.lo;
+}
+
 // wrapped index (|i| at most one period away from the cell, as for a stencil halo)
 __device__ __forceinline__ int wrap1(int i, int n) {
   i = i < 0 ? i + n : i;
@@ -136,6 +158,7 @@ __global__ void __launch_bounds__(TX * TY) kinetic_local_df_kernel(const double*
   const int z1 = min(z0 + a.zchunk, a.n3);
   const double* __restrict__ src = psi + (long long)band * a.K;
   double* __restrict__ dst = out + (long long)band * a.K;
+  double* __restrict__ cp = a.cpy ? a.cpy + (long long)band * a.K : nullptr;
   const int x = X0 + tx, y = Y0 + ty;
   const bool active = x < a.n1 && y < a.n2;
   // this thread's halo cells
@@ -183,17 +206,23 @@ __global__ void __launch_bounds__(TX * TY) kinetic_local_df_kernel(const double*
       float pe = fmaf(v.x, c.hi, -acc.hi);
       pe = fmaf(v.x, c.lo, pe);
       acc.lo = fmaf(v.y, c.hi, pe);
+      // three independent chains (x, y, z terms) for instruction-level parallelism, merged
+      // into the potential term with the same error-free additions
       const DF* row = &T[ty + HALO][tx + HALO];
-      tap(acc, a.wx[0], row[1], row[-1]);
-      tap(acc, a.wx[1], row[2], row[-2]);
-      tap(acc, a.wx[2], row[3], row[-3]);
-      tap(acc, a.wy[0], T[ty + HALO + 1][tx + HALO], T[ty + HALO - 1][tx + HALO]);
-      tap(acc, a.wy[1], T[ty + HALO + 2][tx + HALO], T[ty + HALO - 2][tx + HALO]);
-      tap(acc, a.wy[2], T[ty + HALO + 3][tx + HALO], T[ty + HALO - 3][tx + HALO]);
-      tap(acc, a.wz[0], q[4], q[2]);
-      tap(acc, a.wz[1], q[5], q[1]);
-      tap(acc, a.wz[2], q[6], q[0]);
+      DF ax = tap0(a.wx[0], row[1], row[-1]);
+      DF ay = tap0(a.wy[0], T[ty + HALO + 1][tx + HALO], T[ty + HALO - 1][tx + HALO]);
+      DF az = tap0(a.wz[0], q[4], q[2]);
+      tap(ax, a.wx[1], row[2], row[-2]);
+      tap(ay, a.wy[1], T[ty + HALO + 2][tx + HALO], T[ty + HALO - 2][tx + HALO]);
+      tap(az, a.wz[1], q[5], q[1]);
+      tap(ax, a.wx[2], row[3], row[-3]);
+      tap(ay, a.wy[2], T[ty + HALO + 3][tx + HALO], T[ty + HALO - 3][tx + HALO]);
+      tap(az, a.wz[2], q[6], q[0]);
+      merge(ax, ay);
+      merge(acc, az);
+      merge(acc, ax);
       dst[r] = f2d(acc.hi) + f2d(acc.lo);   // one FP64 operation per point
+      if (cp) cp[r] = src[r];                // exact value (the pair holds 48 bits); L1/L2 hit
     }
     buf ^= 1;
   }
@@ -207,7 +236,7 @@ DF split_host(double w) {
 }  // namespace
 
 // Real FP64 contexts with the double-float potential table; EINVAL otherwise.
-int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out) {
+int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out, double* cpy) {
   if (c->dtype != PAWFD_R64 || !c->d_vshift_df) return PAWFD_EINVAL;
   // one wrap per index must reach every point a tile touches (own points run up to TX - 1 and
   // halos HALO past the tile): smaller grids use the general kernel
@@ -235,6 +264,7 @@ int launch_kinetic_local_df(pawfd_ctx* c, const double* psi, int nb, double* out
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gx, gy, nbl * a.nzc), block(TX, TY);
+    a.cpy = cpy ? cpy + (size_t)b0 * c->K : nullptr;
     kinetic_local_df_kernel<<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K, out + (size_t)b0 * c->K, a);
     c->launches += 1;
   }

@@ -27,6 +27,7 @@ struct F32Args {
   float wx[3], wy[3], wz[3];
   const float* vshift;
   int zchunk, nzc;
+  float* cpy;              // optional copy of psi (first band of this launch), or null
 };
 
 __device__ __forceinline__ float4 ld4(const float* __restrict__ p) { return __ldg((const float4*)p); }
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(BX* BY) kinetic_local_f32x4_kernel(const float
   const int z1 = min(z0 + a.zchunk, a.n3);
   const float* __restrict__ src = psi + (long long)band * a.K;
   float* __restrict__ dst = out + (long long)band * a.K;
+  float* __restrict__ cp = a.cpy ? a.cpy + (long long)band * a.K : nullptr;
   const int x = X0 + 4 * tx, y = Y0 + ty;
   // plane row r holds global row wrap(Y0 - 3 + r); threads past the last row of a ragged tile
   // still load their (wrapped) row so that the y neighbours of the last rows are right
@@ -133,13 +135,14 @@ __global__ void __launch_bounds__(BX* BY) kinetic_local_f32x4_kernel(const float
         r[i] = acc;
       }
       *(float4*)(dst + at(z, y) + x) = make_float4(r[0], r[1], r[2], r[3]);
+      if (cp) *(float4*)(cp + at(z, y) + x) = C;
     }
     buf ^= 1;
   }
 }
 
 template <int BX, int BY>
-void launch_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, const F32Args& a0) {
+void launch_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy, const F32Args& a0) {
   F32Args a = a0;
   const int gx = (a.n1 + 4 * BX - 1) / (4 * BX), gy = (a.n2 + BY - 1) / BY;
   const long long tiles = (long long)gx * gy;
@@ -151,6 +154,7 @@ void launch_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, const F32A
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gx, gy, nbl * a.nzc), block(BX, BY);
+    a.cpy = cpy ? cpy + (size_t)b0 * c->K : nullptr;
     kinetic_local_f32x4_kernel<BX, BY><<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K,
                                                                        out + (size_t)b0 * c->K, a);
     c->launches += 1;
@@ -161,9 +165,9 @@ void launch_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, const F32A
 
 // FP32 real band arrays with N1 a multiple of 4 (16-byte rows); returns PAWFD_EINVAL when the
 // shape does not qualify, so the caller can use the general kernel.
-int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out) {
+int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy) {
   if (c->dtype != PAWFD_R32 || c->n[0] % 4 != 0 || c->n[0] < 4) return PAWFD_EINVAL;
-  if (((uintptr_t)psi | (uintptr_t)out) & 15) return PAWFD_EINVAL;
+  if (((uintptr_t)psi | (uintptr_t)out | (uintptr_t)cpy) & 15) return PAWFD_EINVAL;
   F32Args a;
   a.n1 = c->n[0];
   a.n2 = c->n[1];
@@ -180,10 +184,10 @@ int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* ou
   a.zchunk = a.n3;
   a.nzc = 1;
   const int n1v = a.n1v;
-  if (n1v >= 32) launch_f32x4<32, BYMAX>(c, psi, nb, out, a);
-  else if (n1v >= 24) launch_f32x4<24, BYMAX>(c, psi, nb, out, a);
-  else if (n1v >= 16) launch_f32x4<16, BYMAX>(c, psi, nb, out, a);
-  else launch_f32x4<8, BYMAX>(c, psi, nb, out, a);
+  if (n1v >= 32) launch_f32x4<32, BYMAX>(c, psi, nb, out, cpy, a);
+  else if (n1v >= 24) launch_f32x4<24, BYMAX>(c, psi, nb, out, cpy, a);
+  else if (n1v >= 16) launch_f32x4<16, BYMAX>(c, psi, nb, out, cpy, a);
+  else launch_f32x4<8, BYMAX>(c, psi, nb, out, cpy, a);
   return check_cuda(c, cudaGetLastError(), "kinetic_local f32x4 launch");
 }
 

@@ -36,6 +36,7 @@ struct RingArgs {
   const float* vshift;
   int zchunk, nzc, by, ncw;
   DeviceStatus* st;
+  float* cpy;            // optional copy of psi (first band of this launch), or null
 };
 
 __device__ __forceinline__ int wrapr(int i, int n) {
@@ -65,6 +66,7 @@ struct Consumer {
   bool valid;            // the thread's rows lie inside the CTA's tile
   bool act[R];           // row r of the thread is a grid row (y < N2)
   float* dst;            // output at (z, y, x) of the current step, first row
+  float* cpy;            // copy of psi at the same place, or null
   const float* v;        // shifted potential at (z + 1, y, x), first row (prefetched a step ahead)
   float4 vcur[R];        // shifted potential of the current step
   long long plane_stride;
@@ -127,9 +129,11 @@ __device__ __forceinline__ bool consume(Consumer<R>& c, const RingArgs& a, int j
         acc1 = __ffma2_rn(wz2, __fadd2_rn(hi2(zp), hi2(zm)), acc1);
       }
       *(float4*)(c.dst + r * c.n1) = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+      if (c.cpy) *(float4*)(c.cpy + r * c.n1) = C;
     }
   }
   c.dst += c.plane_stride;
+  if (c.cpy) c.cpy += c.plane_stride;
   c.v += c.plane_stride;
 #pragma unroll
   for (int r = 0; r < R; ++r) c.vcur[r] = vnext[r];
@@ -223,6 +227,7 @@ __global__ void __launch_bounds__(max_threads<R>(), 1)
   c.plane_stride = (long long)a.n1 * a.n2;
   const long long g0 = ((long long)z0 * a.n2 + (c.act[0] ? y : 0)) * a.n1 + x;
   c.dst = out + (long long)band * a.K + g0;
+  c.cpy = a.cpy ? a.cpy + (long long)band * a.K + g0 : nullptr;
 #pragma unroll
   for (int r = 0; r < R; ++r)
     c.vcur[r] = c.act[r] ? __ldg((const float4*)(a.vshift + g0 + r * a.n1)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(max_threads<R>(), 1)
 }
 
 template <int R, int RING>
-int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, int rows_hint) {
+int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy, RingArgs a, int rows_hint) {
   // rows per CTA: a multiple of R within the thread limit and ~100 KB of ring
   const int max_rows = R * ((max_threads<R>() - 32) / a.n1v);
   if (max_rows < R) return PAWFD_EINVAL;
@@ -293,6 +298,7 @@ int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, 
   for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
     const int nbl = std::min(bands_per_launch, nb - b0);
     dim3 grid(gy, nbl * a.nzc), block(32 * (a.ncw + 1));
+    a.cpy = cpy ? cpy + (size_t)b0 * c->K : nullptr;
     kinetic_local_ring_kernel<R, RING><<<grid, block, smem, c->stream>>>(psi + (size_t)b0 * c->K,
                                                                     out + (size_t)b0 * c->K, a);
     c->launches += 1;
@@ -304,9 +310,9 @@ int launch_ring(pawfd_ctx* c, const float* psi, int nb, float* out, RingArgs a, 
 
 // FP32 real band arrays with N1 % 4 == 0 and 8 <= N1 <= 3072; EINVAL when the shape does
 // not qualify (the caller then uses another kernel).
-int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out) {
+int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy) {
   if (c->dtype != PAWFD_R32 || c->n[0] % 4 != 0 || c->n[0] < 8 || c->n[0] > 3072) return PAWFD_EINVAL;
-  if (((uintptr_t)psi | (uintptr_t)out) & 15) return PAWFD_EINVAL;
+  if (((uintptr_t)psi | (uintptr_t)out | (uintptr_t)cpy) & 15) return PAWFD_EINVAL;
   RingArgs a;
   a.n1 = c->n[0];
   a.n2 = c->n[1];
@@ -329,22 +335,22 @@ int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out
   const int depth = c->stencil_ring > 0 ? c->stencil_ring : 8;
   if (depth == 10) {
     switch (yb) {
-      case 1: return launch_ring<1, 10>(c, psi, nb, out, a, rows);
-      case 2: return launch_ring<2, 10>(c, psi, nb, out, a, rows);
-      default: return launch_ring<3, 10>(c, psi, nb, out, a, rows);
+      case 1: return launch_ring<1, 10>(c, psi, nb, out, cpy, a, rows);
+      case 2: return launch_ring<2, 10>(c, psi, nb, out, cpy, a, rows);
+      default: return launch_ring<3, 10>(c, psi, nb, out, cpy, a, rows);
     }
   }
   if (depth == 12) {
     switch (yb) {
-      case 1: return launch_ring<1, 12>(c, psi, nb, out, a, rows);
-      case 2: return launch_ring<2, 12>(c, psi, nb, out, a, rows);
-      default: return launch_ring<3, 12>(c, psi, nb, out, a, rows);
+      case 1: return launch_ring<1, 12>(c, psi, nb, out, cpy, a, rows);
+      case 2: return launch_ring<2, 12>(c, psi, nb, out, cpy, a, rows);
+      default: return launch_ring<3, 12>(c, psi, nb, out, cpy, a, rows);
     }
   }
   switch (yb) {
-    case 1: return launch_ring<1, 8>(c, psi, nb, out, a, rows);
-    case 2: return launch_ring<2, 8>(c, psi, nb, out, a, rows);
-    default: return launch_ring<3, 8>(c, psi, nb, out, a, rows);
+    case 1: return launch_ring<1, 8>(c, psi, nb, out, cpy, a, rows);
+    case 2: return launch_ring<2, 8>(c, psi, nb, out, cpy, a, rows);
+    default: return launch_ring<3, 8>(c, psi, nb, out, cpy, a, rows);
   }
 }
 
