@@ -36,8 +36,7 @@ int launch_apply_hs(pawfd_ctx* c, const void* psi, int nb, void* hpsi, void* sps
   // the stencil pass also writes S psi's first term (psi itself), so psi is read once
   int rc = launch_kinetic_local(c, psi, nb, hpsi, spsi);
   if (rc == PAWFD_OK) rc = launch_project(c, psi, nb, P);
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dH, hpsi);
-  if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, P, nb, c->at.d_dS, spsi);
+  if (rc == PAWFD_OK) rc = launch_nonlocal_add2(c, P, nb, c->at.d_dH, hpsi, c->at.d_dS, spsi);
   return rc;
 }
 }  // namespace pawfd

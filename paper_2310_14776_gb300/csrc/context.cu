@@ -182,7 +182,36 @@ int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
     at.color_off.push_back((int)color_atoms.size());
   }
 
+  // work items: each atom's box points in runs of NL_PCH, so that large boxes spread over
+  // many CTAs (the FP64 rate of one SM would otherwise bound a whole box)
+  std::vector<int2> items, color_items;
+  std::vector<long long> item_row;
+  std::vector<int> atom_items(1, 0);
+  for (int a = 0; a < d->natoms; ++a) {
+    for (int p0 = 0; p0 < at.npts[a]; p0 += NL_PCH) {
+      items.push_back(make_int2(a, p0));
+      item_row.push_back(at.part_rows);
+      at.part_rows += at.nproj[a];
+    }
+    atom_items.push_back((int)items.size());
+  }
+  at.nitems = (int)items.size();
+  at.color_item_off.assign(1, 0);
+  for (int col = 0; col < ncolors; ++col) {
+    for (int a : at.colors[col])
+      for (int p0 = 0; p0 < at.npts[a]; p0 += NL_PCH) color_items.push_back(make_int2(a, p0));
+    at.color_item_off.push_back((int)color_items.size());
+  }
+
   const int A = d->natoms;
+  at.d_items = dev_alloc<int2>(c, std::max<size_t>(1, items.size()), &rc);
+  at.d_item_row = dev_alloc<long long>(c, std::max<size_t>(1, item_row.size()), &rc);
+  at.d_atom_items = dev_alloc<int>(c, atom_items.size(), &rc);
+  at.d_color_items = dev_alloc<int2>(c, std::max<size_t>(1, color_items.size()), &rc);
+  upload(c, at.d_items, items.data(), items.size(), &rc);
+  upload(c, at.d_item_row, item_row.data(), item_row.size(), &rc);
+  upload(c, at.d_atom_items, atom_items.data(), atom_items.size(), &rc);
+  upload(c, at.d_color_items, color_items.data(), color_items.size(), &rc);
   at.d_nproj = dev_alloc<int>(c, A, &rc);
   at.d_row_off = dev_alloc<int>(c, A + 1, &rc);
   at.d_npts = dev_alloc<int>(c, A, &rc);
@@ -246,7 +275,8 @@ void free_ctx(pawfd_ctx* c) {
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
-                  c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q};
+                  c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
+                  c->at.d_atom_items, c->at.d_color_items};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -318,6 +348,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
   if (rc == PAWFD_OK) {
     c->d_P = dev_alloc<char>(c, band_size(c) * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
     c->d_Q = dev_alloc<char>(c, mat_size(c) * std::max<size_t>(1, (size_t)c->at.Ip) * nb, &rc);
+    c->d_Ppart = dev_alloc<char>(c, band_size(c) * std::max<size_t>(1, (size_t)c->at.part_rows) * nb, &rc);
     // split-K partials: about eight 64 x 64 tiles per SM at max_bands (Hermitian tiling),
     // capped at 256 MB
     const size_t t1 = (nb + 63) / 64, tiles = t1 * (t1 + 1) / 2;

@@ -31,14 +31,20 @@ struct AtomArgs {
   const long long* dmat_off;
 };
 
+// Partial projections of one work item (atom a, box points p0 .. p0 + NL_PCH - 1) for BT
+// bands: part[item_row + i][band] = sum_p conj(G_a[i][p]) psi_band(r_p) over the item's points.
 template <class T>
-__global__ void __launch_bounds__(NT) project_kernel(const T* __restrict__ psi, T* __restrict__ P, int nb,
-                                                     long long K, double dV, const T* __restrict__ g, AtomArgs at) {
+__global__ void __launch_bounds__(NT) project_kernel(const T* __restrict__ psi, T* __restrict__ part, int nb,
+                                                     long long K, const T* __restrict__ g, AtomArgs at,
+                                                     const int2* __restrict__ items,
+                                                     const long long* __restrict__ item_row) {
   __shared__ T gs[IMAX][CH];
   __shared__ T ps[BT][CH + 1];
-  const int a = blockIdx.x;
+  const int2 item = items[blockIdx.x];
+  const int a = item.x;
   const int b0 = blockIdx.y * BT;
-  const int I = at.nproj[a], np = at.npts[a], row = at.row_off[a];
+  const int I = at.nproj[a], np = at.npts[a];
+  const int p_end = min(np, item.y + NL_PCH);
   const int* __restrict__ pts = at.pts + at.pt_off[a];
   const T* __restrict__ ga = g + at.g_off[a];
   const int tid = threadIdx.x;
@@ -47,14 +53,14 @@ __global__ void __launch_bounds__(NT) project_kernel(const T* __restrict__ psi, 
   T acc[MAXPAIRS];
 #pragma unroll
   for (int e = 0; e < MAXPAIRS; ++e) acc[e] = zero<T>();
-  for (int pc = 0; pc < np; pc += CH) {
+  for (int pc = item.y; pc < p_end; pc += CH) {
     for (int s = tid; s < I * CH; s += NT) {
       const int i = s / CH, p = s - i * CH;
-      gs[i][p] = (pc + p < np) ? conjx(ga[(long long)i * np + pc + p]) : zero<T>();
+      gs[i][p] = (pc + p < p_end) ? conjx(ga[(long long)i * np + pc + p]) : zero<T>();
     }
     for (int s = tid; s < BT * CH; s += NT) {
       const int bl = s / CH, p = s - bl * CH;
-      ps[bl][p] = (pc + p < np && b0 + bl < nb) ? psi[(long long)(b0 + bl) * K + pts[pc + p]] : zero<T>();
+      ps[bl][p] = (pc + p < p_end && b0 + bl < nb) ? psi[(long long)(b0 + bl) * K + pts[pc + p]] : zero<T>();
     }
     __syncthreads();
 #pragma unroll
@@ -70,52 +76,89 @@ __global__ void __launch_bounds__(NT) project_kernel(const T* __restrict__ psi, 
     }
     __syncthreads();
   }
+  const long long row = item_row[blockIdx.x];
 #pragma unroll
   for (int e = 0; e < MAXPAIRS; ++e) {
     const int pair = tid + e * NT;
     const int i = pair / BT, bl = pair - i * BT;
-    if (i < I && b0 + bl < nb) P[(long long)(row + i) * nb + b0 + bl] = (real_t<T>)dV * acc[e];
+    if (i < I && b0 + bl < nb) part[(row + i) * nb + b0 + bl] = acc[e];
   }
 }
 
+// P[row_a + i][band] = dV sum over the atom's items (in order) of the partials
+template <class T>
+__global__ void __launch_bounds__(256) project_reduce_kernel(const T* __restrict__ part, T* __restrict__ P, int nb,
+                                                             double dV, AtomArgs at,
+                                                             const int* __restrict__ atom_items,
+                                                             const long long* __restrict__ item_row) {
+  using W = wide_t<T>;
+  const int a = blockIdx.x, m = blockIdx.y * 256 + threadIdx.x;
+  if (m >= nb) return;
+  const int I = at.nproj[a], row = at.row_off[a];
+  const int it0 = atom_items[a], it1 = atom_items[a + 1];
+  for (int i = 0; i < I; ++i) {
+    W s = zero<W>();
+    for (int it = it0; it < it1; ++it) s = s + widen(part[(item_row[it] + i) * nb + m]);
+    P[(long long)(row + i) * nb + m] = narrow<T>(dV * s);
+  }
+}
+
+// out1 += sum_i G_a[i] Q1[i] (and out2 with Q2 when out2 is set), Qk = dmat_k^a P_a, over one
+// work item's box points.  Items of one launch belong to atoms of one colour, so no two
+// threads of a launch touch the same grid point.
 template <class T>
 __global__ void __launch_bounds__(NT) nonlocal_add_kernel(const T* __restrict__ P, int nb, long long K,
-                                                          const real_t<T>* __restrict__ dmat, const T* __restrict__ g,
-                                                          AtomArgs at, const int* __restrict__ atoms,
-                                                          T* __restrict__ out) {
-  __shared__ T Qs[IMAX][BT];
+                                                          const real_t<T>* __restrict__ dmat1,
+                                                          const real_t<T>* __restrict__ dmat2,
+                                                          const T* __restrict__ g, AtomArgs at,
+                                                          const int2* __restrict__ items, T* __restrict__ out1,
+                                                          T* __restrict__ out2) {
+  __shared__ T Q1s[IMAX][BT];
+  __shared__ T Q2s[IMAX][BT];
   __shared__ T gs[IMAX][CH];
-  const int a = atoms[blockIdx.x];
+  const int2 item = items[blockIdx.x];
+  const int a = item.x;
   const int b0 = blockIdx.y * BT;
   const int I = at.nproj[a], np = at.npts[a], row = at.row_off[a];
+  const int p_end = min(np, item.y + NL_PCH);
   const int* __restrict__ pts = at.pts + at.pt_off[a];
   const T* __restrict__ ga = g + at.g_off[a];
-  const real_t<T>* __restrict__ dX = dmat + at.dmat_off[a];
+  const long long dmo = at.dmat_off[a];
   const int tid = threadIdx.x;
-  // Q[i][bl] = sum_i' dX[i][i'] P[row + i'][b0 + bl]
+  const bool two = out2 != nullptr;
+  // Qk[i][bl] = sum_i' dmat_k[i][i'] P[row + i'][b0 + bl]
   for (int s = tid; s < I * BT; s += NT) {
     const int i = s / BT, bl = s - i * BT;
-    T q = zero<T>();
+    T q1 = zero<T>(), q2 = zero<T>();
     if (b0 + bl < nb)
-      for (int i2 = 0; i2 < I; ++i2) fma_real(q, dX[i * I + i2], P[(long long)(row + i2) * nb + b0 + bl]);
-    Qs[i][bl] = q;
+      for (int i2 = 0; i2 < I; ++i2) {
+        const T pv = P[(long long)(row + i2) * nb + b0 + bl];
+        fma_real(q1, dmat1[dmo + i * I + i2], pv);
+        if (two) fma_real(q2, dmat2[dmo + i * I + i2], pv);
+      }
+    Q1s[i][bl] = q1;
+    Q2s[i][bl] = q2;
   }
   const int p_local = tid % CH, bsub = tid / CH;   // 8 bands in flight per pass
-  for (int pc = 0; pc < np; pc += CH) {
+  for (int pc = item.y; pc < p_end; pc += CH) {
     __syncthreads();
     for (int s = tid; s < I * CH; s += NT) {
       const int i = s / CH, p = s - i * CH;
-      gs[i][p] = (pc + p < np) ? ga[(long long)i * np + pc + p] : zero<T>();
+      gs[i][p] = (pc + p < p_end) ? ga[(long long)i * np + pc + p] : zero<T>();
     }
     __syncthreads();
     const int p = pc + p_local;
-    if (p < np) {
+    if (p < p_end) {
       const long long r = pts[p];
       for (int bl = bsub; bl < BT && b0 + bl < nb; bl += NT / CH) {
-        T s = zero<T>();
-        for (int i = 0; i < I; ++i) fma_plain(s, gs[i][p_local], Qs[i][bl]);
-        T* o = out + (long long)(b0 + bl) * K + r;
-        *o += s;
+        T s1 = zero<T>(), s2 = zero<T>();
+        for (int i = 0; i < I; ++i) {
+          fma_plain(s1, gs[i][p_local], Q1s[i][bl]);
+          if (two) fma_plain(s2, gs[i][p_local], Q2s[i][bl]);
+        }
+        const long long o = (long long)(b0 + bl) * K + r;
+        out1[o] += s1;
+        if (two) out2[o] += s2;
       }
     }
   }
@@ -186,34 +229,45 @@ AtomArgs atom_args(const pawfd_ctx* c) {
 int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P) {
   if (c->at.natoms == 0) return PAWFD_OK;
   if (c->at.Imax > IMAX) return fail(c, PAWFD_EINVAL, "more than 32 projectors on one atom");
-  dim3 grid(c->at.natoms, (nb + BT - 1) / BT);
+  dim3 grid(c->at.nitems, (nb + BT - 1) / BT), rgrid(c->at.natoms, (nb + 255) / 256);
   dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
-    project_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)psi, (T*)P, nb, (long long)c->K, c->dV,
-                                                   (const T*)c->at.d_g, atom_args(c));
+    if (c->at.nitems > 0)
+      project_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)psi, (T*)c->d_Ppart, nb, (long long)c->K,
+                                                     (const T*)c->at.d_g, atom_args(c), c->at.d_items,
+                                                     c->at.d_item_row);
+    project_reduce_kernel<T><<<rgrid, 256, 0, c->stream>>>((const T*)c->d_Ppart, (T*)P, nb, c->dV, atom_args(c),
+                                                            c->at.d_atom_items, c->at.d_item_row);
     return 0;
   });
-  c->launches += 1;
+  c->launches += 2;
   return check_cuda(c, cudaGetLastError(), "project launch");
 }
 
-int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out) {
+int launch_nonlocal_add2(pawfd_ctx* c, const void* P, int nb, const void* dmat1, void* out1, const void* dmat2,
+                         void* out2) {
   if (c->at.natoms == 0) return PAWFD_OK;
   if (c->at.Imax > IMAX) return fail(c, PAWFD_EINVAL, "more than 32 projectors on one atom");
-  for (size_t col = 0; col + 1 < c->at.color_off.size(); ++col) {
-    const int first = c->at.color_off[col], count = c->at.color_off[col + 1] - first;
+  for (size_t col = 0; col + 1 < c->at.color_item_off.size(); ++col) {
+    const int first = c->at.color_item_off[col], count = c->at.color_item_off[col + 1] - first;
+    if (count == 0) continue;
     dim3 grid(count, (nb + BT - 1) / BT);
-    const int* atoms = c->at.d_color_atoms + first;
+    const int2* items = c->at.d_color_items + first;
     dispatch_band(c, [&](auto tag) {
       using T = decltype(tag);
       nonlocal_add_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)P, nb, (long long)c->K,
-                                                          (const real_t<T>*)d_dmat, (const T*)c->at.d_g,
-                                                          atom_args(c), atoms, (T*)out);
+                                                          (const real_t<T>*)dmat1, (const real_t<T>*)dmat2,
+                                                          (const T*)c->at.d_g, atom_args(c), items, (T*)out1,
+                                                          (T*)out2);
       return 0;
     });
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "nonlocal_add launch");
+}
+
+int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out) {
+  return launch_nonlocal_add2(c, P, nb, d_dmat, out, nullptr, nullptr);
 }
 
 // S_nm += sum_a P_a^H dS^a P_a (the overlap's nonlocal term of the S Gram matrix); M is the

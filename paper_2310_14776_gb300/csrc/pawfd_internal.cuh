@@ -126,7 +126,16 @@ struct AtomTables {
   void* d_dS = nullptr;
   int* d_color_atoms = nullptr;      // atoms listed color by color
   std::vector<int> color_off;        // [ncolors+1] into d_color_atoms
+  // work items of the projector kernels: (atom, first box point) of up to NL_PCH box points
+  int nitems = 0;
+  long long part_rows = 0;           // rows of the projection partials (sum over items of I_a)
+  int2* d_items = nullptr;           // [nitems], atom by atom
+  long long* d_item_row = nullptr;   // [nitems] first partial row of each item
+  int* d_atom_items = nullptr;       // [natoms + 1] item range of each atom
+  int2* d_color_items = nullptr;     // items listed color by color
+  std::vector<int> color_item_off;   // [ncolors+1] into d_color_items
 };
+constexpr int NL_PCH = 256;          // box points per work item of the projector kernels
 
 // Scratch of the tensor-core Gram: digit slices of one K block of each operand, their scale
 // exponents, FP64 split-K partials, and the TMA descriptors of the slice buffers.
@@ -181,6 +190,7 @@ struct pawfd_ctx {
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_Q = nullptr;                        // [Ip][max_bands] FP64 dS P of the overlap correction
+  void* d_Ppart = nullptr;                    // [part_rows][max_bands] projection partials
   void* d_gram_part = nullptr;                // split-K partial Gram matrices
   size_t gram_part_bytes = 0;
   void* d_work = nullptr;                     // subspace workspace (7 matrices of max_bands^2)
@@ -237,6 +247,9 @@ int check_cuda(pawfd_ctx* c, cudaError_t e, const char* what);
 int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out, void* cpy = nullptr);
 int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P);
 int launch_nonlocal_add(pawfd_ctx* c, const void* P, int nb, const void* d_dmat, void* out);
+// out1 += sum |p> dmat1 P and out2 += sum |p> dmat2 P in one pass over the boxes
+int launch_nonlocal_add2(pawfd_ctx* c, const void* P, int nb, const void* dmat1, void* out1, const void* dmat2,
+                         void* out2);
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
