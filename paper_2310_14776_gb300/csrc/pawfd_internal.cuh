@@ -168,6 +168,7 @@ struct TcScratch {
   int* rotMaxB = nullptr;
   CUtensorMap rotMapA;
   CUtensorMap rotMapB;
+  int slice_t_ctas = 0;        // CTAs of the persistent transposing slicer
   // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
   long long fnch = 0;          // chunks per row
   int* fsigA = nullptr;        // [fnch][max_bands]

@@ -251,65 +251,109 @@ __device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_
   }
 }
 
+// Persistent, double-buffered form: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
+// (chunk-major, so that CTAs running together read the same band rows) and copies the next
+// tile into shared memory with cp.async (8 bytes per FP64 value or 4 per FP32 value, zero
+// filled past the bands or the block's grid points) while it slices the current one.  The
+// staged tile is band-major: buf[n][q] (real) or buf[n][2 q + c] (complex), RT grid points q.
+template <class R>
+__host__ __device__ constexpr int slice_t_pitch() { return sizeof(R) == 8 ? 2 * RT + 2 : 2 * RT + 4; }
+// two staged tiles of KC contraction values x RT grid points
+template <class R>
+__host__ __device__ constexpr int slice_t_smem() { return KC * slice_t_pitch<R>() * (int)sizeof(R); }
+
+__device__ __forceinline__ void cp_async_zfill(void* sdst, const void* gsrc, int bytes, bool valid) {
+  const int src_bytes = valid ? bytes : 0;
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(tc::smem_addr(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(sdst)), "l"(gsrc), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 template <class R, int S>
 __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
                                                       long long r0, int rcount, long long Lp, int out_rows,
                                                       __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
-                                                      int sig_ld, int* __restrict__ sigmax) {
-  constexpr int PITCH = KC + 16 / (int)sizeof(R);   // 16-byte aligned rows: vector reads, few conflicts
-  __shared__ __align__(16) R tile[RT][PITCH];     // [grid point][k]
+                                                      int sig_ld, int* __restrict__ sigmax, int nch) {
+  constexpr int PITCH = slice_t_pitch<R>();          // values per staged band row (two of them for real)
+  extern __shared__ __align__(16) unsigned char slice_t_smem_raw[];
+  R* bufs = (R*)slice_t_smem_raw;                    // [2][KC / 2][PITCH]: KC contraction values x RT points
   __shared__ int pmax[16][RT];
-  const int rt = blockIdx.x, c = blockIdx.y;
-  const int tid = threadIdx.x, lr = tid % RT, kq = tid / RT;
-  const long long Lk = (long long)nb * (cplx ? 2 : 1);
-  const int rl0 = rt * RT;   // first local grid point of this CTA
-  int em = 0;
-  for (int kk = kq; kk < KC; kk += 16) {
-    const long long k = (long long)c * KC + kk;
-    R v = R(0);
-    if (k < Lk && rl0 + lr < rcount) {
-      const long long n = cplx ? (k >> 1) : k;
-      const long long e = (n * K + r0 + rl0 + lr) * (cplx ? 2 : 1) + (cplx ? (k & 1) : 0);
-      v = psi[e];
+  const int tid = threadIdx.x;
+  const int nrt = (rcount + RT - 1) / RT;
+  const int ntiles = nrt * nch;
+  const int vals_per_row = cplx ? 2 * RT : RT;        // values of one band row of a tile
+  const int rows_per_chunk = cplx ? KC / 2 : KC;      // band rows of one chunk
+  // staged value (k, q) of a tile: real buf[k][q] (row pitch PITCH / 2), complex buf[k / 2][2 q + k % 2]
+  auto stage = [&](R* buf, int t) {
+    const int rt = t % nrt, c = t / nrt;
+    const int rl0 = rt * RT;
+    const int nfirst = c * rows_per_chunk;
+    const int total = rows_per_chunk * vals_per_row;
+    for (int e = tid; e < total; e += 256) {
+      const int nr = e / vals_per_row, w = e - nr * vals_per_row;
+      const int n = nfirst + nr;
+      const int q = cplx ? w >> 1 : w;
+      const bool ok = n < nb && rl0 + q < rcount;
+      const long long gi = cplx ? (((long long)n * K + r0 + rl0) * 2 + w) : ((long long)n * K + r0 + rl0 + w);
+      R* dst = buf + (cplx ? (long long)nr * PITCH + w : (long long)nr * (PITCH / 2) + w);
+      cp_async_zfill(dst, ok ? psi + gi : psi, (int)sizeof(R), ok);
     }
-    tile[lr][kk] = v;
-    em = max(em, fields(v).exp);
-  }
-  pmax[kq][lr] = em;
-  __syncthreads();
-  if (tid < RT) {
-    int m = 0;
-    for (int q = 0; q < 16; ++q) m = max(m, pmax[q][tid]);
-    pmax[0][tid] = m;
-    if (rl0 + tid < rcount) {
-      sig[(long long)c * sig_ld + rl0 + tid] = m - FloatBits<R>::bias - 5;
-      atomicMax(sigmax + rl0 + tid, m - FloatBits<R>::bias - 5);
+  };
+  auto val = [&](const R* buf, int k, int q) -> R {
+    return cplx ? buf[(k >> 1) * PITCH + 2 * q + (k & 1)] : buf[k * (PITCH / 2) + q];
+  };
+  int it = 0;
+  int t = blockIdx.x;
+  if (t < ntiles) stage(bufs, t);
+  cp_async_commit();
+  for (; t < ntiles; t += gridDim.x, ++it) {
+    R* cur = bufs + (it & 1) * (KC / 2) * PITCH;
+    R* nxt = bufs + ((it + 1) & 1) * (KC / 2) * PITCH;
+    if (t + (int)gridDim.x < ntiles) stage(nxt, t + gridDim.x);
+    cp_async_commit();
+    cp_async_wait1();   // this tile's copies have landed
+    __syncthreads();
+    const int rt = t % nrt, c = t / nrt;
+    const int rl0 = rt * RT;
+    // largest exponent of every grid point's chunk (zero fill beyond the bands contributes 0)
+    {
+      const int lr = tid % RT, kq = tid / RT;
+      int em = 0;
+      for (int kk = kq; kk < KC; kk += 16) em = max(em, fields(val(cur, kk, lr)).exp);
+      pmax[kq][lr] = em;
     }
-  }
-  __syncthreads();
-  // items: (K step j, half h, grid point q); the 32 threads of a warp cover the 16 grid points
-  // and both halves of one K step, i.e. 512 contiguous bytes of a digit plane
-  for (int item = tid; item < RT * (KC / 8); item += 256) {
-    const int q = item % RT, k8 = (item / (2 * RT)) * 16 + ((item / RT) & 1) * 8;
-    if (rl0 + q >= rcount) continue;
-    R x[8];
-    if constexpr (sizeof(R) == 4) {
-      const float4 a0 = *(const float4*)&tile[q][k8], a1 = *(const float4*)&tile[q][k8 + 4];
-      x[0] = a0.x; x[1] = a0.y; x[2] = a0.z; x[3] = a0.w; x[4] = a1.x; x[5] = a1.y; x[6] = a1.z; x[7] = a1.w;
-    } else {
-#pragma unroll
-      for (int v = 0; v < 8; v += 2) {
-        const double2 a2 = *(const double2*)&tile[q][k8 + v];
-        x[v] = a2.x;
-        x[v + 1] = a2.y;
+    __syncthreads();
+    if (tid < RT) {
+      int m = 0;
+      for (int q = 0; q < 16; ++q) m = max(m, pmax[q][tid]);
+      pmax[0][tid] = m;
+      if (rl0 + tid < rcount) {
+        sig[(long long)c * sig_ld + rl0 + tid] = m - FloatBits<R>::bias - 5;
+        atomicMax(sigmax + rl0 + tid, m - FloatBits<R>::bias - 5);
       }
     }
-    uint32_t o[S][4];
-    digits8_t<S>(x, pmax[0][q], o);
+    __syncthreads();
+    // items: (K step j, half h, grid point q); the 32 threads of a warp cover the 16 grid points
+    // and both halves of one K step, i.e. 512 contiguous bytes of a digit plane
+    for (int item = tid; item < RT * (KC / 8); item += 256) {
+      const int q = item % RT, k8 = (item / (2 * RT)) * 16 + ((item / RT) & 1) * 8;
+      if (rl0 + q >= rcount) continue;
+      R x[8];
 #pragma unroll
-    for (int i = 0; i < S; ++i)
-      *(uint4*)(out + plane_offset(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
-          make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+      for (int v = 0; v < 8; ++v) x[v] = val(cur, k8 + v, q);
+      uint32_t o[S][4];
+      digits8_t<S>(x, pmax[0][q], o);
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+        *(uint4*)(out + plane_offset(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
+            make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+    }
+    __syncthreads();   // the buffer and pmax are reused
   }
 }
 

@@ -252,9 +252,10 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
   for (long long r0 = 0; r0 < K; r0 += t.rot_rblk) {
     const int rcount = (int)std::min<long long>(t.rot_rblk, K - r0);
     cudaMemsetAsync(t.rotMaxB, 0x80, sizeof(int) * t.rot_rblk, c->stream);
-    sg::slice_t_kernel<R, S><<<dim3((rcount + sg::RT - 1) / sg::RT, nch), 256, 0, c->stream>>>(
+    const int stiles = (rcount + sg::RT - 1) / sg::RT * nch;
+    sg::slice_t_kernel<R, S><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R>(), c->stream>>>(
         psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
-        (int)t.rot_rblk, t.rotMaxB);
+        (int)t.rot_rblk, t.rotMaxB, nch);
     sg::GramArgs a = {};
     a.sigA = t.rotSigA;
     a.sigB = t.rotSigB;
@@ -523,7 +524,21 @@ int setup_tc(pawfd_ctx* c) {
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotMaxA, sizeof(int) * t.rot_rowsA_alloc), "cudaMalloc");
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.rotMaxB, sizeof(int) * t.rot_rblk), "cudaMalloc");
     if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
-    rc = check_cuda(c, cudaMemset(t.rotSlicesA, 0, sa_bytes), "memset");
+    // persistent transposing slicer: as many CTAs as fit at once
+    if (rc == PAWFD_OK) {
+      const void* fn = S == 7 ? (const void*)sg::slice_t_kernel<double, 7> : (const void*)sg::slice_t_kernel<float, 4>;
+      const int smem = S == 7 ? sg::slice_t_smem<double>() : sg::slice_t_smem<float>();
+      rc = check_cuda(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem attribute");
+      int per_sm = 0;
+      if (rc == PAWFD_OK)
+        rc = check_cuda(c, S == 7 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sg::slice_t_kernel<double, 7>,
+                                                                                  256, smem)
+                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sg::slice_t_kernel<float, 4>,
+                                                                                  256, smem),
+                        "occupancy");
+      t.slice_t_ctas = std::max(1, per_sm) * c->num_sms;
+    }
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesA, 0, sa_bytes), "memset");
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesB, 0, sb_bytes), "memset");
     if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapA, t.rotSlicesA, t.rot_rowsA_alloc, t.rot_Lc, S, sg::BM);
     if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapB, t.rotSlicesB, (int)t.rot_rblk, t.rot_Lc, S, sg::BN);
