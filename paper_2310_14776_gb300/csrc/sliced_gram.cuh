@@ -411,10 +411,12 @@ __device__ __forceinline__ double f2d_scaled(float x, int e) {
 __device__ __forceinline__ double df_to_double(float xh, float xl, int e) {
   return f2d_scaled(xh, e) + f2d_scaled(xl, e);
 }
-// x 2^e in FP32 (x is the correctly rounded sum of the double-float pair)
+// x 2^e in FP32 (x is the correctly rounded sum of the double-float pair).  The rare path is
+// out of line so that it is not evaluated under a predicate for every value (FP64 pipe).
+__device__ __noinline__ float f2f_scaled_slow(float x, int e) { return (float)((double)x * pow2(e)); }
 __device__ __forceinline__ float f2f_scaled(float x, int e) {
   if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
-  return (float)((double)x * pow2(e));
+  return f2f_scaled_slow(x, e);
 }
 
 // tile index -> (tile row, tile col) over the output [rowsA][rowsB]; tile columns are numbered

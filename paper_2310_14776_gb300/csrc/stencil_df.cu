@@ -40,14 +40,19 @@ struct DFArgs {
 // x = hi + lo: hi = x rounded to 24 bits, lo = x - hi rounded to 24 bits (so hi + lo equals x
 // to a relative 2^-48).  The IEEE fields are split with integer operations; values outside
 // the normal FP32 range of both parts take the conversion path.
+// The rare path, kept out of line: inlined, the compiler evaluates it for every value under a
+// predicate, and its three FP64 conversions and one FP64 subtraction per value then fill the
+// narrow FP64 pipe (ncu showed the pipe 75 % busy for what should be one addition per point).
+__device__ __noinline__ DF split64_slow(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - (double)hi)};
+}
+
 __device__ __forceinline__ DF split64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
   const int e = (int)((h >> 20) & 0x7FFu);
-  if (e < 960 || e > 1140) {
-    const float hi = __double2float_rn(x);
-    return {hi, __double2float_rn(x - (double)hi)};
-  }
+  if (e < 960 || e > 1140) return split64_slow(x);
   const unsigned top = (((h & 0xFFFFFu) | 0x100000u) << 3) | (l >> 29);   // 24-bit significand
   const unsigned rem = l & 0x1FFFFFFFu;                                    // the 29 bits below
   const unsigned up = rem >> 28;                                           // round half up
