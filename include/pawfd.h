@@ -120,6 +120,9 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_df"      1 (default): the real FP64 stencil computes in double-float FP32 pairs
  *                     (about 48 bits, well inside the FP64 tolerance; far faster than the FP64
  *                     pipe); 0: FP64 arithmetic.  "stencil_variant" 2 also selects FP64.
+ *   "nonlocal_df"     1 (default): for real FP64 bands the projections and the nonlocal
+ *                     back-add compute in double-float FP32 pairs (runs of 32 terms, then FP64
+ *                     sums); 0: FP64 arithmetic.
  *   "tc_fused"        0 (default): digit planes are sliced to memory, then multiplied; 1: the
  *                     tensor-core Gram makes its digits inside the MMA kernel from the raw
  *                     operands (when their rows are 16-byte aligned).  Same digits, same products.

@@ -266,6 +266,15 @@ int build_tables(pawfd_ctx* c, const pawfd_system_desc* d) {
     double* dg = dev_alloc<double>(c, all_re.size(), &rc);
     upload(c, dg, all_re.data(), all_re.size(), &rc);
     at.d_g = dg;
+    // the same values as (hi, lo) pairs for the double-float projector kernels
+    std::vector<float2> gdf(all_re.size());
+    for (size_t q = 0; q < gdf.size(); ++q) {
+      const float hi = (float)all_re[q];
+      gdf[q] = make_float2(hi, (float)(all_re[q] - (double)hi));
+    }
+    float2* dgdf = dev_alloc<float2>(c, gdf.size(), &rc);
+    upload(c, dgdf, gdf.data(), gdf.size(), &rc);
+    at.d_g_df = dgdf;
   }
   return rc;
 }
@@ -276,7 +285,7 @@ void free_ctx(pawfd_ctx* c) {
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
                   c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
-                  c->at.d_atom_items, c->at.d_color_items};
+                  c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_status) cudaFreeHost(c->h_status);
@@ -423,6 +432,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
   }
   if (n == "stencil_df" && (value == 0 || value == 1)) {
     c->stencil_df = value == 1;
+    return PAWFD_OK;
+  }
+  if (n == "nonlocal_df" && (value == 0 || value == 1)) {
+    c->nonlocal_df = value == 1;
     return PAWFD_OK;
   }
   if (n == "tc_fused" && (value == 0 || value == 1)) {

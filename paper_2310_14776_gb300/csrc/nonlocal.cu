@@ -10,7 +10,9 @@
 // share a grid point, each (point, band) is written by exactly one thread per launch, and
 // colours are applied in a fixed order.
 #include <algorithm>
+#include <type_traits>
 
+#include "df_arith.cuh"
 #include "pawfd_internal.cuh"
 
 namespace pawfd {
@@ -164,6 +166,127 @@ __global__ void __launch_bounds__(NT) nonlocal_add_kernel(const T* __restrict__ 
   }
 }
 
+// ---- real FP64 bands in double-float arithmetic (FP32 pipe) ----
+// The FP64 forms above are bound by GB300's FP64 rate (about two FMAs per SM and clock).
+// Here the operands are pairs hi + lo (the projector values split once at create, psi and
+// Q split on load) and every product-accumulate is dfa::fma_acc, about 15 FP32 operations of
+// relative error ~2^-47; a run of CH terms is summed in pairs and then added to an FP64
+// accumulator, so the pairs' error does not grow with the box size.
+
+template <int I_UNUSED = 0>
+__global__ void __launch_bounds__(NT) project_df_kernel(const double* __restrict__ psi, double* __restrict__ part,
+                                                        int nb, long long K, const float2* __restrict__ gdf,
+                                                        AtomArgs at, const int2* __restrict__ items,
+                                                        const long long* __restrict__ item_row) {
+  using dfa::DF;
+  __shared__ DF gs[IMAX][CH];
+  __shared__ DF ps[BT][CH + 1];
+  const int2 item = items[blockIdx.x];
+  const int a = item.x;
+  const int b0 = blockIdx.y * BT;
+  const int I = at.nproj[a], np = at.npts[a];
+  const int p_end = min(np, item.y + NL_PCH);
+  const int* __restrict__ pts = at.pts + at.pt_off[a];
+  const float2* __restrict__ ga = gdf + at.g_off[a];
+  const int tid = threadIdx.x;
+  constexpr int MAXPAIRS = IMAX * BT / NT;
+  double acc[MAXPAIRS];
+#pragma unroll
+  for (int e = 0; e < MAXPAIRS; ++e) acc[e] = 0.0;
+  for (int pc = item.y; pc < p_end; pc += CH) {
+    for (int s = tid; s < I * CH; s += NT) {
+      const int i = s / CH, p = s - i * CH;
+      const float2 gv = (pc + p < p_end) ? ga[(long long)i * np + pc + p] : make_float2(0.f, 0.f);
+      gs[i][p] = {gv.x, gv.y};
+    }
+    for (int s = tid; s < BT * CH; s += NT) {
+      const int bl = s / CH, p = s - bl * CH;
+      ps[bl][p] = (pc + p < p_end && b0 + bl < nb) ? dfa::split64(psi[(long long)(b0 + bl) * K + pts[pc + p]])
+                                                   : DF{0.f, 0.f};
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < MAXPAIRS; ++e) {
+      const int pair = tid + e * NT;
+      const int i = pair / BT, bl = pair - i * BT;
+      if (i < I) {
+        DF s = {0.f, 0.f};
+#pragma unroll 8
+        for (int p = 0; p < CH; ++p) dfa::fma_acc(s, gs[i][p], ps[bl][p]);
+        acc[e] += dfa::to_double(s);
+      }
+    }
+    __syncthreads();
+  }
+  const long long row = item_row[blockIdx.x];
+#pragma unroll
+  for (int e = 0; e < MAXPAIRS; ++e) {
+    const int pair = tid + e * NT;
+    const int i = pair / BT, bl = pair - i * BT;
+    if (i < I && b0 + bl < nb) part[(row + i) * nb + b0 + bl] = acc[e];
+  }
+}
+
+template <int I_UNUSED = 0>
+__global__ void __launch_bounds__(NT) nonlocal_add_df_kernel(const double* __restrict__ P, int nb, long long K,
+                                                             const double* __restrict__ dmat1,
+                                                             const double* __restrict__ dmat2,
+                                                             const float2* __restrict__ gdf, AtomArgs at,
+                                                             const int2* __restrict__ items,
+                                                             double* __restrict__ out1, double* __restrict__ out2) {
+  using dfa::DF;
+  __shared__ DF Q1s[IMAX][BT];
+  __shared__ DF Q2s[IMAX][BT];
+  __shared__ DF gs[IMAX][CH];
+  const int2 item = items[blockIdx.x];
+  const int a = item.x;
+  const int b0 = blockIdx.y * BT;
+  const int I = at.nproj[a], np = at.npts[a], row = at.row_off[a];
+  const int p_end = min(np, item.y + NL_PCH);
+  const int* __restrict__ pts = at.pts + at.pt_off[a];
+  const float2* __restrict__ ga = gdf + at.g_off[a];
+  const long long dmo = at.dmat_off[a];
+  const int tid = threadIdx.x;
+  const bool two = out2 != nullptr;
+  // Qk[i][bl] = sum_i' dmat_k[i][i'] P[row + i'][b0 + bl] in FP64 (I^2 per band), then split
+  for (int s = tid; s < I * BT; s += NT) {
+    const int i = s / BT, bl = s - i * BT;
+    double q1 = 0.0, q2 = 0.0;
+    if (b0 + bl < nb)
+      for (int i2 = 0; i2 < I; ++i2) {
+        const double pv = P[(long long)(row + i2) * nb + b0 + bl];
+        q1 = fma(dmat1[dmo + i * I + i2], pv, q1);
+        if (two) q2 = fma(dmat2[dmo + i * I + i2], pv, q2);
+      }
+    Q1s[i][bl] = dfa::split64(q1);
+    Q2s[i][bl] = dfa::split64(q2);
+  }
+  const int p_local = tid % CH, bsub = tid / CH;
+  for (int pc = item.y; pc < p_end; pc += CH) {
+    __syncthreads();
+    for (int s = tid; s < I * CH; s += NT) {
+      const int i = s / CH, p = s - i * CH;
+      const float2 gv = (pc + p < p_end) ? ga[(long long)i * np + pc + p] : make_float2(0.f, 0.f);
+      gs[i][p] = {gv.x, gv.y};
+    }
+    __syncthreads();
+    const int p = pc + p_local;
+    if (p < p_end) {
+      const long long r = pts[p];
+      for (int bl = bsub; bl < BT && b0 + bl < nb; bl += NT / CH) {
+        DF s1 = {0.f, 0.f}, s2 = {0.f, 0.f};
+        for (int i = 0; i < I; ++i) {
+          dfa::fma_acc(s1, gs[i][p_local], Q1s[i][bl]);
+          if (two) dfa::fma_acc(s2, gs[i][p_local], Q2s[i][bl]);
+        }
+        const long long o = (long long)(b0 + bl) * K + r;
+        out1[o] += dfa::to_double(s1);
+        if (two) out2[o] += dfa::to_double(s2);
+      }
+    }
+  }
+}
+
 // Q[row_a + i][m] = sum_j dS^a[i][j] P[row_a + j][m] in FP64: one CTA per (atom, 256 bands)
 template <class T>
 __global__ void __launch_bounds__(256) overlap_q_kernel(const T* __restrict__ P, int nb,
@@ -232,10 +355,16 @@ int launch_project(pawfd_ctx* c, const void* psi, int nb, void* P) {
   dim3 grid(c->at.nitems, (nb + BT - 1) / BT), rgrid(c->at.natoms, (nb + 255) / 256);
   dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
-    if (c->at.nitems > 0)
-      project_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)psi, (T*)c->d_Ppart, nb, (long long)c->K,
-                                                     (const T*)c->at.d_g, atom_args(c), c->at.d_items,
-                                                     c->at.d_item_row);
+    if (c->at.nitems > 0) {
+      if (std::is_same<T, double>::value && c->at.d_g_df && c->nonlocal_df)
+        project_df_kernel<><<<grid, NT, 0, c->stream>>>((const double*)psi, (double*)c->d_Ppart, nb, (long long)c->K,
+                                                        (const float2*)c->at.d_g_df, atom_args(c), c->at.d_items,
+                                                        c->at.d_item_row);
+      else
+        project_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)psi, (T*)c->d_Ppart, nb, (long long)c->K,
+                                                       (const T*)c->at.d_g, atom_args(c), c->at.d_items,
+                                                       c->at.d_item_row);
+    }
     project_reduce_kernel<T><<<rgrid, 256, 0, c->stream>>>((const T*)c->d_Ppart, (T*)P, nb, c->dV, atom_args(c),
                                                             c->at.d_atom_items, c->at.d_item_row);
     return 0;
@@ -255,10 +384,16 @@ int launch_nonlocal_add2(pawfd_ctx* c, const void* P, int nb, const void* dmat1,
     const int2* items = c->at.d_color_items + first;
     dispatch_band(c, [&](auto tag) {
       using T = decltype(tag);
-      nonlocal_add_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)P, nb, (long long)c->K,
-                                                          (const real_t<T>*)dmat1, (const real_t<T>*)dmat2,
-                                                          (const T*)c->at.d_g, atom_args(c), items, (T*)out1,
-                                                          (T*)out2);
+      if (std::is_same<T, double>::value && c->at.d_g_df && c->nonlocal_df)
+        nonlocal_add_df_kernel<><<<grid, NT, 0, c->stream>>>((const double*)P, nb, (long long)c->K,
+                                                             (const double*)dmat1, (const double*)dmat2,
+                                                             (const float2*)c->at.d_g_df, atom_args(c), items,
+                                                             (double*)out1, (double*)out2);
+      else
+        nonlocal_add_kernel<T><<<grid, NT, 0, c->stream>>>((const T*)P, nb, (long long)c->K,
+                                                            (const real_t<T>*)dmat1, (const real_t<T>*)dmat2,
+                                                            (const T*)c->at.d_g, atom_args(c), items, (T*)out1,
+                                                            (T*)out2);
       return 0;
     });
     c->launches += 1;

@@ -121,6 +121,7 @@ struct AtomTables {
   int* d_pts = nullptr;              // wrapped grid index of every box point (unique per atom)
   long long* d_g_off = nullptr;
   void* d_g = nullptr;               // folded projector values [I_a][npts_a], band scalar type
+  void* d_g_df = nullptr;            // real FP64: the same values as (hi, lo) FP32 pairs
   long long* d_dmat_off = nullptr;
   void* d_dH = nullptr;              // dH^a, real type of the band arithmetic (double or float)
   void* d_dS = nullptr;
@@ -215,6 +216,7 @@ struct pawfd_ctx {
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 256-value chunks (0: allocation)
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
+  bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic
   pawfd::TcScratch tc;
   std::string err;
 };

@@ -16,14 +16,13 @@
 // marches along z, the z neighbours in a register queue, the plane (with halo) in shared memory.
 #include <algorithm>
 
+#include "df_arith.cuh"
 #include "pawfd_internal.cuh"
 
 namespace pawfd {
 namespace {
 
-struct __align__(8) DF {
-  float hi, lo;
-};
+using namespace dfa;
 
 constexpr int TX = 32, TY = 8, HALO = 3;
 constexpr int SX = TX + 2 * HALO, SY = TY + 2 * HALO;
@@ -36,53 +35,6 @@ struct DFArgs {
   int zchunk, nzc;
   double* cpy;              // optional copy of psi (first band of this launch), or null
 };
-
-// x = hi + lo: hi = x rounded to 24 bits, lo = x - hi rounded to 24 bits (so hi + lo equals x
-// to a relative 2^-48).  The IEEE fields are split with integer operations; values outside
-// the normal FP32 range of both parts take the conversion path.
-// The rare path, kept out of line: inlined, the compiler evaluates it for every value under a
-// predicate, and its three FP64 conversions and one FP64 subtraction per value then fill the
-// narrow FP64 pipe (ncu showed the pipe 75 % busy for what should be one addition per point).
-__device__ __noinline__ DF split64_slow(double x) {
-  const float hi = __double2float_rn(x);
-  return {hi, __double2float_rn(x - (double)hi)};
-}
-
-__device__ __forceinline__ DF split64(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
-  const int e = (int)((h >> 20) & 0x7FFu);
-  if (e < 960 || e > 1140) return split64_slow(x);
-  const unsigned top = (((h & 0xFFFFFu) | 0x100000u) << 3) | (l >> 29);   // 24-bit significand
-  const unsigned rem = l & 0x1FFFFFFFu;                                    // the 29 bits below
-  const unsigned up = rem >> 28;                                           // round half up
-  // exponent (e - 1023 + 127) and the 23 stored bits; a carry of the rounding runs into the
-  // exponent, as it must
-  const unsigned hbits = (h & 0x80000000u) | ((((unsigned)(e - 896)) << 23) + (top & 0x7FFFFFu) + up);
-  // residual in units of 2^(e - 1075): rem - up 2^29, |r| <= 2^28
-  const int r = (int)rem - (int)(up << 29);
-  const float scale = __int_as_float((e - 948) << 23);                     // 2^(e - 1075)
-  float lo = __int2float_rn(r) * scale;
-  if (h & 0x80000000u) lo = -lo;
-  return {__uint_as_float(hbits), lo};
-}
-
-// exact float -> double from the IEEE fields (integer operations only); zero and subnormal
-// inputs give zero (below 2^-126, far under the 2^-48 relative accuracy of the pairs)
-__device__ __forceinline__ double f2d(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0) return 0.0;
-  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)b);
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
 
 // acc += w (p + m), acc kept as (hi exact FP32 sum, lo collecting every rounding error)
 __device__ __forceinline__ void tap(DF& acc, DF w, DF p, DF m) {

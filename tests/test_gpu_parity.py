@@ -196,6 +196,23 @@ def test_double_float_stencil_matches_fp64_arithmetic(dev, n):
     ctx.close()
 
 
+@pytest.mark.parametrize("case", [((45, 19, 13), 6, 5), ((30, 28, 26), 9, 40)])
+def test_double_float_projectors_match_fp64_arithmetic(dev, case):
+    """Real FP64 projections and nonlocal back-adds in double-float pairs (the default) against
+    the same kernels in FP64 arithmetic."""
+    n, natoms, nb = case
+    s = synth.make_system(n, (9.0, 7.6, 5.2), natoms, synth.PSET_SPD2, seed=411)
+    ctx = ctx_for(s, nb, dev)
+    psi = to_dev(synth.make_psi(s, nb, 412), dev)
+    H1, S1, P1 = (t.clone() for t in ctx.apply_hs(psi))
+    ctx.set_option("nonlocal_df", 0)
+    H0, S0, P0 = ctx.apply_hs(psi)
+    for got, ref in ((H1, H0), (S1, S0)):
+        assert_close_bands(got.cpu().numpy(), ref.cpu().numpy(), nb, rel=1e-13)
+    assert_close_matrix(P1.cpu().numpy(), P0.cpu().numpy(), rel=1e-13)
+    ctx.close()
+
+
 def test_repeatable_bitwise(dev):
     w = synth.WORKLOADS["gamma-24c-16b"]
     s = w.system()
