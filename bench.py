@@ -40,23 +40,32 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe kernel on this machine
 
 
-# Measured DRAM traffic per unit of the dominant stage's kernels (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum on a small case, profiles/dram_apply_H_fp64_64c_128b.md), valid only
-# while the kernels' sources are the ones that were measured.
-TRAFFIC = {}
+# Measured DRAM traffic of the dominant stage's kernels (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of every kernel of one pawfd_gram_hs call at 64^3 x 256 bands,
+# profiles/dram_gram_hs_64c_256b.md).  At a fixed band count it grows with the grid points K
+# (slicing and digit-plane reads per K block); valid only for that band count and while the
+# kernels' sources are the ones that were measured.
+_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "ad448c6ea872b883358588f8300a39d6d8c8d8b9",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "44c57458868bf05c9c7e9bead7734471195cee14",
+                 "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
+                 "paper_2310_14776_gb300/csrc/tc_common.cuh": "55d9c2bd5425ee3d0ded06a7ec772b410d3832a8"}
+TRAFFIC = {
+    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21836.3, "sources": _GRAM_SOURCES},
+    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11890.2, "sources": _GRAM_SOURCES},
+}
 
 
 def stage_traffic(stage, precision, cplx, K, nb, natoms):
     """DRAM bytes of one launch of the stage, scaled from the measured small case, or None."""
     import hashlib
     t = TRAFFIC.get((stage, precision, cplx))
-    if t is None:
+    if t is None or t["nb"] != nb:
         return None
     for path, sha in t["sources"].items():
         with open(os.path.join(ROOT, path), "rb") as f:
             if hashlib.sha1(f.read()).hexdigest() != sha:
                 return None
-    return t["per_point_band"] * K * nb + t["per_atom_band"] * natoms * nb
+    return t["per_point"] * K
 
 
 def parse_args():
@@ -76,6 +85,8 @@ def parse_args():
     p.add_argument("--serve-warmup", type=float, default=5.0, help="served: arrivals before this are excluded")
     p.add_argument("--real", action="store_true", help="batch64 / served: real (Gamma) instead of Bloch instances")
     p.add_argument("--no-refine", action="store_true", help="mixed: skip the final FP64 refinement measurement")
+    p.add_argument("--bands", type=int, default=0,
+                   help="single workloads: this many bands instead of the workload's own (profiling cases)")
     a = p.parse_args()
     if a.precision is None:
         a.precision = "mixed" if a.workload in ("batch64", "served") else "fp64"
@@ -165,10 +176,10 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     w = synth.WORKLOADS[args.workload]
     system = w.system()
-    nb, K = w.nbands, system.npoints
+    nb, K = (args.bands or w.nbands), system.npoints
     cplx = system.complex_wf
     ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
-    if nb * K <= HOST_PSI_MAX:
+    if nb * K <= HOST_PSI_MAX and nb == w.nbands:
         psi_host = w.psi(system)
         if args.precision == "mixed":
             psi_host = psi_host.astype(np.complex64 if cplx else np.float32)
@@ -284,7 +295,7 @@ def run_gpu(args):
         "roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
                      "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,
                      "traffic": stage_traffic(dom, args.precision, cplx, K, nb, system.natoms),
-                     "traffic_unit": "DRAM bytes per stage launch (ncu, scaled from 64^3 x 128)",
+                     "traffic_unit": "DRAM bytes per stage call (ncu at 64^3 x 256 bands, scaled by grid points)",
                      "peak_source": {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst)",
                                      "hbm": "MEASURED_PEAKS.json hbm_gbs",
                                      "alu": "nominal GB300 FP64 rate 1.25 TFLOP/s / 2 (FMA)"}[bound]},
