@@ -152,7 +152,7 @@ struct TcScratch {
   int* maxB = nullptr;
   void* part = nullptr;
   size_t part_bytes = 0;
-  CUtensorMap mapA;
+  CUtensorMap mapA;            // row-major planes of the Gram operands (4-D TMA boxes)
   CUtensorMap mapB;
   CUtensorMap mapAB;           // slicesA with the B operand's box (the Gram of psi with itself)
   void* part2 = nullptr;       // partials of the second Gram of a pair
@@ -167,8 +167,6 @@ struct TcScratch {
   int* rotSigB = nullptr;
   int* rotMaxA = nullptr;
   int* rotMaxB = nullptr;
-  CUtensorMap rotMapA;
-  CUtensorMap rotMapB;
   int slice_t_ctas = 0;        // CTAs of the persistent transposing slicer
   // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
   long long fnch = 0;          // chunks per row

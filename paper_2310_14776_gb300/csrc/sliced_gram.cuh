@@ -106,37 +106,31 @@ __device__ __forceinline__ R slice_input(const R* __restrict__ src, long long ld
   return (k & 1) ? -row[k - 1] : row[k + 1];
 }
 
-// Digit planes are stored in K steps: plane i, K step s (values 16 s .. 16 s + 15 of a row),
-// row r at element ((i * (Lp / 16) + s) * rows + r) * 16.  The 16 values of one row and step
-// are 32 contiguous bytes, and the BK x box_rows operand box of one plane that a pipeline
-// stage loads is one contiguous block of box_rows * 32 bytes.
-__device__ __forceinline__ long long plane_offset(int i, long long k, int r, int rows, long long Lp) {
+// Digit planes are stored in K steps: plane i, K step s (values 16 s .. 16 s + 15 of every
+// row) is a slab of rows x 16 values.  Two layouts of a slab:
+//  * row-major (plane_offset_rm): row r at 16 r, 32 contiguous bytes per row.  The Gram reads it
+//    with 4-D TMA boxes (32-byte swizzle), which also zero-fill rows past the allocation.
+//  * core matrices (plane_offset_cm): row group g = r / 8 holds the tensor cores' two K-major
+//    core matrices (values 0-7 and 8-15 of the step) of 8 rows x 8 values (128 bytes each), so
+//    the operand box of one plane (16 values of box_rows rows, box_rows a multiple of 8 from a
+//    multiple of 8) is one contiguous block of box_rows * 32 bytes, copied with one bulk copy
+//    and used as it lands (no swizzle).  The rotation's operands use this layout.
+// rows is a multiple of 8 in both.
+__device__ __forceinline__ long long plane_offset_rm(int i, long long k, int r, int rows, long long Lp) {
   return (((long long)i * (Lp / BK) + (k >> 4)) * rows + r) * BK + (k & 15);
 }
+__device__ __forceinline__ long long plane_offset_cm(int i, long long k, int r, int rows, long long Lp) {
+  return ((long long)i * (Lp / BK) + (k >> 4)) * (long long)rows * BK + (long long)(r >> 3) * 128 +
+         ((k >> 3) & 1) * 64 + (r & 7) * 8 + (k & 7);
+}
 
-// One warp per (row, chunk) of a K block: src points at the block's first value of row 0, rows
-// are ld apart, len values per row are valid (the rest of the Lp-long block is zero).
-// out: S digit planes of out_rows rows and Lp values (layout above; rows placed at row_offset);
-// sig: [nchunks][sig_ld]; sigmax[row] (reset by the caller for every block) receives the
-// largest sigma of the row.  Consecutive warps take consecutive rows of one chunk; each lane
-// takes 8 consecutive values of the 256-value chunk and writes 16 bytes per plane.
 template <int S>
 __device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32_t (&out)[S][4]);
 template <int S>
 __device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_t (&out)[S][4]);
 
-template <class R, int S>
-__global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
-                                                    int nchunks, long long Lp, bool swapped, int row_offset,
-                                                    int out_rows, __nv_bfloat16* __restrict__ out,
-                                                    int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= rows * nchunks) return;
-  const int r = warp % rows;
-  const long long c = warp / rows;
-  const long long k0 = c * KC + lane * 8;
-  R x[8];
-  const R* row = src + (long long)r * ld;
+template <class R>
+__device__ __forceinline__ void load8(const R* __restrict__ row, long long k0, long long len, bool swapped, R (&x)[8]) {
   if (k0 + 8 <= len && ((((uintptr_t)(row + k0)) & 15) == 0)) {
     if constexpr (sizeof(R) == 8) {
 #pragma unroll
@@ -162,6 +156,26 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
       x[v + 1] = -re;
     }
   }
+}
+
+// One warp per (row, chunk) of a K block: src points at the block's first value of row 0, rows
+// are ld apart, len values per row are valid (the rest of the Lp-long block is zero).  out: S
+// row-major digit planes of out_rows rows and Lp values (rows placed at row_offset); sig:
+// [nchunks][sig_ld]; sigmax[row] (reset by the caller for every block) receives the largest
+// sigma of the row.  Consecutive warps take consecutive rows of one chunk; each lane takes 8
+// consecutive values of the 256-value chunk and writes 16 bytes per plane.
+template <class R, int S>
+__global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
+                                                    int nchunks, long long Lp, bool swapped, int row_offset,
+                                                    int out_rows, __nv_bfloat16* __restrict__ out,
+                                                    int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= rows * nchunks) return;
+  const int r = warp % rows;
+  const long long c = warp / rows;
+  const long long k0 = c * KC + lane * 8;
+  R x[8];
+  load8(src + (long long)r * ld, k0, len, swapped, x);
   int emax = 0;
 #pragma unroll
   for (int v = 0; v < 8; ++v) emax = max(emax, fields(x[v]).exp);
@@ -176,7 +190,66 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
   digits8_t<S>(x, emax, o);
 #pragma unroll
   for (int i = 0; i < S; ++i)
-    *(uint4*)(out + plane_offset(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+    *(uint4*)(out + plane_offset_rm(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+}
+
+// The same for core-matrix planes (the rotation's C operand): one warp per (group of 8 rows,
+// chunk) of a K block; src, rows, ld, len, sig and sigmax as above; rows placed at row_offset,
+// a multiple of 8.  Lane (r8, q) = (lane % 8, lane / 8)
+// takes row r8 of the group and, in each of 8 passes j, the 8 values 32 j + 8 q of the chunk,
+// so that one store instruction of the warp fills two whole K-step blocks of the row group's
+// core matrices (2 x 256 contiguous bytes).  The chunk is read twice: once for its largest
+// exponent, once (from L1/L2) for the digits.
+template <class R, int S>
+__global__ void __launch_bounds__(256) slice_rg_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
+                                                       int nchunks, long long Lp, bool swapped, int row_offset,
+                                                       int out_rows, __nv_bfloat16* __restrict__ out,
+                                                       int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
+  const int ngroups = (rows + 7) / 8;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= (long long)ngroups * nchunks) return;
+  const int g = (int)(warp % ngroups);
+  const long long c = warp / ngroups;
+  const int r8 = lane & 7, q = lane >> 3;
+  const int r = g * 8 + r8;
+  const bool valid = r < rows;
+  const R* row = src + (long long)(valid ? r : 0) * ld;
+  int emax = 0;
+#pragma unroll 2
+  for (int j = 0; j < KC / 32; ++j) {
+    R x[8];
+    if (valid) load8(row, c * KC + 32 * j + 8 * q, len, swapped, x);
+    else {
+#pragma unroll
+      for (int v = 0; v < 8; ++v) x[v] = R(0);
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) emax = max(emax, fields(x[v]).exp);
+  }
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 8));
+  emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, 16));
+  const int orow = row_offset + r;
+  if (valid && q == 0) {
+    sig[c * sig_ld + orow] = emax - FloatBits<R>::bias - 5;
+    atomicMax(sigmax + orow, emax - FloatBits<R>::bias - 5);
+  }
+#pragma unroll 1
+  for (int j = 0; j < KC / 32; ++j) {
+    const long long k0 = c * KC + 32 * j + 8 * q;
+    R x[8];
+    uint32_t o[S][4];
+    if (valid) {
+      load8(row, k0, len, swapped, x);
+      digits8_t<S>(x, emax, o);
+    } else {
+#pragma unroll
+      for (int i = 0; i < S; ++i) o[i][0] = o[i][1] = o[i][2] = o[i][3] = 0u;   // padding rows of the group
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      *(uint4*)(out + plane_offset_cm(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+  }
 }
 
 // Transposing slicer for the band rotation: operand rows are grid points r, the contraction
@@ -350,7 +423,7 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
       digits8_t<S>(x, pmax[0][q], o);
 #pragma unroll
       for (int i = 0; i < S; ++i)
-        *(uint4*)(out + plane_offset(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
+        *(uint4*)(out + plane_offset_cm(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
             make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
     }
     __syncthreads();   // the buffer and pmax are reused
@@ -388,6 +461,12 @@ struct GramArgs {
   void* rot_out = nullptr;        // band array, already offset to the first grid point of the block
   int rot_vec = 0;                // real bands with 16-byte aligned rows: vector stores
   int rot_tiles = 0;              // output tiles of the rotation, shared out over the persistent CTAs
+  // digit planes of the two operands (plane_offset layout, slabs of rows_alloc x 16 values)
+  const __nv_bfloat16* gA = nullptr;
+  const __nv_bfloat16* gB = nullptr;
+  int rows_allocA = 0, rows_allocB = 0;
+  long long ksteps = 0;           // K steps per plane (Lp / 16) of both buffers
+  int half_stride = 0;            // B row of the second half's first row (complex; 0: half_rows)
 };
 
 // 2^e for the product scale; below the normal range the chunk contributes nothing (its
@@ -462,9 +541,13 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
   two_sum(s, e, hi, lo);
 }
 
-template <int S, int ORD, bool ONE>
+// BULK: the operands are core-matrix planes (plane_offset_cm), one bulk copy per plane and
+// operand per stage, read by the tensor cores without swizzle; otherwise row-major planes
+// (plane_offset_rm) through the 4-D TMA maps tA and tB with a 32-byte swizzle.
+template <int S, int ORD, bool ONE, bool BULK>
 __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
-                                                                  const __grid_constant__ CUtensorMap tB, GramArgs a) {
+                                                                  const __grid_constant__ CUtensorMap tB,
+                                                                  const __grid_constant__ GramArgs a) {
   constexpr int STAGES = stages<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -473,8 +556,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   __shared__ volatile int abort_flag;
   __shared__ int issued, consumed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // column tiles of the complex second half start at half_rows, not at a multiple of BN
+  // column tiles of the complex second half start at half_stride (a multiple of 8)
   const int T = (a.half_rows + BN - 1) / BN;
+  const int HS = a.half_stride ? a.half_stride : a.half_rows;
   // Output tiles of this CTA: tile blockIdx.x; with ONE (a rotation whose contraction is one
   // chunk) every gridDim.x-th tile from blockIdx.x (a persistent CTA: the copies for the next
   // tile run while the epilogue of the last one drains TMEM and stores).
@@ -483,7 +567,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     int tr;
     gram_tile(a, (int)blockIdx.x + i * (int)gridDim.x, &tr, &tcol);
     row0 = tr * BM;
-    col0 = (tcol / T) * a.half_rows + (tcol % T) * BN;
+    col0 = (tcol / T) * HS + (tcol % T) * BN;
   };
   const int c_begin = blockIdx.y * a.chunks_per_cta;
   const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
@@ -534,8 +618,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         unsigned char* sa = smem + s * stage_bytes<S>();
         unsigned char* sb = sa + S * a_slice_bytes<S>();
         tc::mbar_expect_tx(&full[s], stage_bytes<S>());
-        tc::tma_load_4d(sa, &tA, &full[s], 0, row0, kx / BK, 0);
-        tc::tma_load_4d(sb, &tB, &full[s], 0, col0, kx / BK, 0);
+        const long long ks = kx / BK;
+        if constexpr (BULK) {
+          // one contiguous box per plane and operand (rows row0 .. row0 + BM - 1 of the slab)
+#pragma unroll
+          for (int pl = 0; pl < S; ++pl) {
+            tc::bulk_load(sa + pl * a_slice_bytes<S>(),
+                          a.gA + (pl * a.ksteps + ks) * a.rows_allocA * BK + (long long)row0 * BK, a_slice_bytes<S>(),
+                          &full[s]);
+            tc::bulk_load(sb + pl * b_slice_bytes(),
+                          a.gB + (pl * a.ksteps + ks) * a.rows_allocB * BK + (long long)col0 * BK, b_slice_bytes(),
+                          &full[s]);
+          }
+        } else {
+          tc::tma_load_4d(sa, &tA, &full[s], 0, row0, (int)ks, 0);
+          tc::tma_load_4d(sb, &tB, &full[s], 0, col0, (int)ks, 0);
+        }
         issued = g + 1;
         if (++q == steps_of(c)) {
           q = 0;
@@ -579,8 +677,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
               // the first product written into an accumulator in this chunk overwrites it
               const bool first = (q == 0) && !touched[slot];
               touched[slot] = true;
-              tc::mma_bf16(d, tc::smem_desc(sa + i * a_slice_bytes<S>(), BK * 2),
-                           tc::smem_desc(sb + j * b_slice_bytes(), BK * 2), idesc, first ? 0u : 1u);
+              const uint64_t da = BULK ? tc::smem_desc_nosw(sa + i * a_slice_bytes<S>(), 128, 256)
+                                       : tc::smem_desc(sa + i * a_slice_bytes<S>(), BK * 2);
+              const uint64_t db = BULK ? tc::smem_desc_nosw(sb + j * b_slice_bytes(), 128, 256)
+                                       : tc::smem_desc(sb + j * b_slice_bytes(), BK * 2);
+              tc::mma_bf16(d, da, db, idesc, first ? 0u : 1u);
             }
           tc::mma_commit(&empty[s]);
           consumed = g + 1;
@@ -731,7 +832,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       if (lane == 0) tc::mbar_arrive(&dempty);
     }
     // columns beyond this tile's half of B belong to the other half's tiles
-    const int col_lim = min(a.rowsB, (tcol / T + 1) * a.half_rows);
+    const int col_lim = min(a.rowsB, (tcol / T) * HS + a.half_rows);
     if (a.rotation) {
       if (row < a.rowsA && !abort_flag) {
         const int band = row % a.rot_nb, part = row / a.rot_nb;

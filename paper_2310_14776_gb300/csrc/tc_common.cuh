@@ -77,6 +77,28 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// 1-D bulk copy of `bytes` contiguous bytes (16-byte aligned, a multiple of 16) from global to
+// shared memory, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Descriptor of a K-major operand tile without swizzle, in core matrices of 8 rows x 16 bytes
+// (128 contiguous bytes each): the two core matrices of a row group's K step 16 apart by
+// `lbo` bytes, consecutive row groups `sbo` bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_nosw(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint64_t addr = smem_addr(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;                          // start address
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;            // leading byte offset: next core matrix along K
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;            // stride byte offset: next group of 8 rows
+  d |= (uint64_t)1 << 46;                                // fixed 0b001
+  return d;                                              // layout type 0: no swizzle
+}
+
 // Shared-memory matrix descriptor of a K-major operand tile whose rows are `row_bytes` long
 // (32, 64 or 128, the TMA swizzle width), rows grouped by 8 (stride 8 * row_bytes).
 __device__ __forceinline__ uint64_t smem_desc(const void* p, int row_bytes) {

@@ -19,13 +19,13 @@ namespace pawfd {
 namespace {
 
 template <class W>
-__global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV, bool herm,
-                                 W* __restrict__ M);
+__global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, int im_off, double dV,
+                                 bool herm, W* __restrict__ M);
 
 // real: part [nsplit][nb][nb]
 template <>
-__global__ void tc_reduce_kernel<double>(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV,
-                                         bool herm, double* __restrict__ M) {
+__global__ void tc_reduce_kernel<double>(const double* __restrict__ part, int nsplit, int nb, int rowsB, int,
+                                         double dV, bool herm, double* __restrict__ M) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)nb * nb) return;
   const int n = (int)(e / nb), m = (int)(e % nb);
@@ -37,10 +37,10 @@ __global__ void tc_reduce_kernel<double>(const double* __restrict__ part, int ns
   if (herm && m != n) M[(long long)m * nb + n] = s;
 }
 
-// complex: part [nsplit][nb][2 nb], real part in columns [0, nb), imaginary in [nb, 2 nb)
+// complex: part [nsplit][nb][rowsB], real part in columns [0, nb), imaginary in [im_off, im_off + nb)
 template <>
-__global__ void tc_reduce_kernel<zd>(const double* __restrict__ part, int nsplit, int nb, int rowsB, double dV,
-                                     bool herm, zd* __restrict__ M) {
+__global__ void tc_reduce_kernel<zd>(const double* __restrict__ part, int nsplit, int nb, int rowsB, int im_off,
+                                     double dV, bool herm, zd* __restrict__ M) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)nb * nb) return;
   const int n = (int)(e / nb), m = (int)(e % nb);
@@ -49,7 +49,7 @@ __global__ void tc_reduce_kernel<zd>(const double* __restrict__ part, int nsplit
   for (int p = 0; p < nsplit; ++p) {
     const double* row = part + ((long long)p * nb + n) * rowsB;
     re += row[m];
-    im += row[nb + m];
+    im += row[im_off + m];
   }
   re *= dV;
   im *= dV;
@@ -63,7 +63,9 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   TcScratch& t = c->tc;
   const bool cplx = is_complex(c);
   const long long L = (long long)c->K * (cplx ? 2 : 1);            // real-view row length
-  const int rowsB = cplx ? 2 * nb : nb;
+  // complex: the swapped rows B'' start at a multiple of 8 (whole core-matrix row groups)
+  const int nbp = (nb + 7) / 8 * 8;
+  const int rowsB = cplx ? nbp + nb : nb;
   const int Tr = (nb + sg::BM - 1) / sg::BM, Tc = (nb + sg::BN - 1) / sg::BN;
   const int halves = cplx ? 2 : 1;
   const int tiles = herm ? halves * sg::herm_tiles(nb) : Tr * halves * Tc;
@@ -78,30 +80,34 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   while (nsplit > 1 && (size_t)nsplit * nb * rowsB * sizeof(double) > t.part_bytes) --nsplit;
   __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
   __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
-  const int blocks_of_rows = 256 / 32;
   int blk = 0;
   for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
     const long long len = std::min(Kblk, L - k0);
     const int nch = (int)((len + sg::KC - 1) / sg::KC);
     const int cpc = (nch + nsplit - 1) / nsplit;
     const int ns = (nch + cpc - 1) / cpc;
-    const long long warpsA = (long long)nb * nch;
     // per-row largest sigma of this block: start from a very negative value
     cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
     cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
     // slices keep the allocated row length t.kblk (the tensor maps' layout); a shorter block
     // fills the first Kblk values of each row
-    sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
-    sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
     c->launches += 2;
     if (cplx) {
-      sg::slice_kernel<R, S><<<(unsigned)((warpsA + blocks_of_rows - 1) / blocks_of_rows), 256, 0, c->stream>>>(
-          B + k0, nb, L, len, nch, t.kblk, true, nb, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+      sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+          B + k0, nb, L, len, nch, t.kblk, true, nbp, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
       c->launches += 1;
     }
     sg::GramArgs a = {};
+    a.gA = sA;
+    a.gB = sB;
+    a.rows_allocA = t.rowsA_alloc;
+    a.rows_allocB = t.rowsB_alloc;
+    a.ksteps = t.kblk / sg::BK;
+    a.half_stride = cplx ? nbp : nb;
     a.sigA = t.sigA;
     a.sigB = t.sigB;
     a.sig_ldA = t.rowsA_alloc;
@@ -122,17 +128,17 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     a.st = c->d_status;
     // slots written by the first block must cover every split later blocks add into
     if (blk == 0 && ns < nsplit) nsplit = ns;
-    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
     c->launches += 1;
   }
   const long long nn = (long long)nb * nb;
   if (cplx)
-    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB,
+    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB, nbp,
                                                                               c->dV, herm, (zd*)M);
   else
     tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB,
-                                                                                  c->dV, herm, (double*)M);
+                                                                                  nb, c->dV, herm, (double*)M);
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "tensor-core gram launch");
 }
@@ -158,14 +164,18 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     const int nch = (int)((len + sg::KC - 1) / sg::KC);
     const int cpc = (nch + nsplit - 1) / nsplit;
     const int ns = (nch + cpc - 1) / cpc;
-    const long long warps = (long long)nb * nch;
     cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
     cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
-    sg::slice_kernel<R, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
-    sg::slice_kernel<R, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
     sg::GramArgs a = {};
+    a.gA = sA;
+    a.gB = sB;
+    a.rows_allocA = t.rowsA_alloc;
+    a.rows_allocB = t.rowsB_alloc;
+    a.ksteps = t.kblk / sg::BK;
     a.sigA = t.sigA;
     a.sigB = t.sigB;
     a.sig_ldA = t.rowsA_alloc;
@@ -185,22 +195,25 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a.part = (double*)t.part;
     a.st = c->d_status;
     if (blk == 0 && ns < nsplit) nsplit = ns;
-    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
-    // psi^T psi: psi's planes and exponents on both sides
+    // psi^T psi: psi's planes and exponents on both sides (psi's planes through a map with the
+    // B operand's box)
     sg::GramArgs a2 = a;
+    a2.gB = sA;
+    a2.rows_allocB = t.rowsA_alloc;
     a2.sigB = t.sigA;
     a2.sig_ldB = t.rowsA_alloc;
     a2.maxB = t.maxA;
     a2.part = (double*)t.part2;
-    sg::sliced_gram_kernel<S, ORD, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapAB, a2);
     c->launches += 4;
   }
   const long long nn = (long long)nb * nb;
-  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, nb,
+  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, nb, nb,
                                                                                 c->dV, true, M1);
-  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part2, nsplit, nb, nb,
+  tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part2, nsplit, nb, nb, nb,
                                                                                 c->dV, true, M2);
   c->launches += 2;
   return check_cuda(c, cudaGetLastError(), "tensor-core gram pair launch");
@@ -242,8 +255,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
       C, nb, cplx, (double*)t.rotA, t.rot_Lc, t.rot_rowsA_alloc);
   cudaMemsetAsync(t.rotMaxA, 0x80, sizeof(int) * t.rot_rowsA_alloc, c->stream);
   {
-    const long long warps = (long long)rowsA * nch;
-    sg::slice_kernel<double, S><<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_rg_kernel<double, S><<<(unsigned)(((rowsA + 7) / 8 * (long long)nch + 7) / 8), 256, 0, c->stream>>>(
         (const double*)t.rotA, rowsA, t.rot_Lc, Lk, nch, t.rot_Lc, false, 0, t.rot_rowsA_alloc,
         (__nv_bfloat16*)t.rotSlicesA, t.rotSigA, t.rot_rowsA_alloc, t.rotMaxA);
   }
@@ -257,6 +269,11 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
         psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
         (int)t.rot_rblk, t.rotMaxB, nch);
     sg::GramArgs a = {};
+    a.gA = (const __nv_bfloat16*)t.rotSlicesA;
+    a.gB = (const __nv_bfloat16*)t.rotSlicesB;
+    a.rows_allocA = t.rot_rowsA_alloc;
+    a.rows_allocB = (int)t.rot_rblk;
+    a.ksteps = t.rot_Lc / sg::BK;
     a.sigA = t.rotSigA;
     a.sigB = t.rotSigB;
     a.sig_ldA = t.rot_rowsA_alloc;
@@ -284,12 +301,12 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
     a.klen = Lk;
     a.rot_tiles = tilesM * a.tilesN;
     if (nch == 1)   // persistent CTAs, one per SM (the kernel's shared memory admits one)
-      sg::sliced_gram_kernel<S, ORD, true>
-          <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-              t.rotMapA, t.rotMapB, a);
+      sg::sliced_gram_kernel<S, ORD, true, true>
+          <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB,
+                                                                                                        a);
     else
-      sg::sliced_gram_kernel<S, ORD, false><<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-          t.rotMapA, t.rotMapB, a);
+      sg::sliced_gram_kernel<S, ORD, false, true>
+          <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, a);
     c->launches += 2;
   }
   return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
@@ -382,11 +399,11 @@ int fused_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool 
   c->launches += 1;
   const long long nn = (long long)nb * nb;
   if (cplx)
-    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, ns, nb, rowsB, c->dV,
-                                                                              herm, (zd*)M);
+    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, ns, nb, rowsB, nb,
+                                                                              c->dV, herm, (zd*)M);
   else
     tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, ns, nb, rowsB,
-                                                                                  c->dV, herm, (double*)M);
+                                                                                  nb, c->dV, herm, (double*)M);
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "fused tensor-core gram launch");
 }
@@ -412,8 +429,9 @@ int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, 
   return tc_gram_impl<double, 7, 6>(c, (const double*)A, (const double*)B, nb, M, hermitian);
 }
 
-// TMA descriptor of a slice buffer [S][rows][Lp] bf16: boxes of 16 values x box_rows x S slices,
-// 32-byte swizzle (the layout the tensor core reads through smem_desc(..., 32)).
+// TMA descriptor of a row-major digit-plane buffer (S planes, K steps of rows x 16 values):
+// boxes of 16 values x box_rows x S planes, 32-byte swizzle (the layout the tensor core reads
+// through smem_desc(..., 32)); rows past the allocation read as zero.
 int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S, int box_rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -424,7 +442,7 @@ int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long 
       return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled not available");
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
-  // digit planes in K steps (sg::plane_offset): dims (value in step, row, step, plane)
+  // row-major digit planes in K steps (sg::plane_offset_rm): dims (value in step, row, step, plane)
   const cuuint64_t ks = (cuuint64_t)(Lp / sg::BK);
   cuuint64_t dims[4] = {(cuuint64_t)sg::BK, (cuuint64_t)rows, ks, (cuuint64_t)S};
   cuuint64_t strides[3] = {(cuuint64_t)sg::BK * 2, (cuuint64_t)rows * sg::BK * 2, ks * rows * sg::BK * 2};
@@ -448,10 +466,12 @@ int setup_tc(pawfd_ctx* c) {
   const long long Lpad = (L + sg::KC - 1) / sg::KC * sg::KC;
   t.kblk = std::min<long long>(512LL * sg::KC, Lpad);
   t.rowsA_alloc = (nb + sg::BM - 1) / sg::BM * sg::BM;
-  t.rowsB_alloc = ((cplx ? 2 * nb : nb) + sg::BN - 1) / sg::BN * sg::BN;
+  // complex: the swapped half starts at row nbp (a multiple of 8) and has its own column tiles
+  const int nbp = (nb + 7) / 8 * 8, tcn = (nb + sg::BN - 1) / sg::BN;
+  t.rowsB_alloc = cplx ? nbp + tcn * sg::BN : tcn * sg::BN;
   const size_t sa = (size_t)S * t.rowsA_alloc * t.kblk * 2, sb = (size_t)S * t.rowsB_alloc * t.kblk * 2;
   const int nchunks = (int)(t.kblk / sg::KC);
-  const int rowsB = cplx ? 2 * nb : nb;
+  const int rowsB = cplx ? nbp + nb : nb;
   const int tiles_min = (cplx ? 2 : 1) * sg::herm_tiles(nb);
   const int nsplit = std::max(1, std::min(nchunks, (c->num_sms + tiles_min - 1) / tiles_min));
   t.part_bytes = (size_t)nsplit * nb * rowsB * sizeof(double);
@@ -473,19 +493,18 @@ int setup_tc(pawfd_ctx* c) {
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapAB, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) {
     const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (S == 7) {
-      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6, false>, smem_attr, sg::smem_bytes<7>()),
+    // the Gram (row-major planes, TMA maps) and the rotation (core-matrix planes, bulk copies;
+    // persistent one-chunk form and general form)
+    const void* fns7[] = {(const void*)sg::sliced_gram_kernel<7, 6, false, false>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, true, true>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, true>};
+    const void* fns4[] = {(const void*)sg::sliced_gram_kernel<4, 4, false, false>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, true, true>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, true>};
+    for (int f = 0; f < 3 && rc == PAWFD_OK; ++f)
+      rc = check_cuda(c, cudaFuncSetAttribute(S == 7 ? fns7[f] : fns4[f], smem_attr,
+                                              S == 7 ? sg::smem_bytes<7>() : sg::smem_bytes<4>()),
                       "smem attribute");
-      if (rc == PAWFD_OK)
-        rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<7, 6, true>, smem_attr, sg::smem_bytes<7>()),
-                        "smem attribute");
-    } else {
-      rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4, false>, smem_attr, sg::smem_bytes<4>()),
-                      "smem attribute");
-      if (rc == PAWFD_OK)
-        rc = check_cuda(c, cudaFuncSetAttribute(sg::sliced_gram_kernel<4, 4, true>, smem_attr, sg::smem_bytes<4>()),
-                        "smem attribute");
-    }
   }
   // fused Gram: chunk exponents over the whole row
   if (rc == PAWFD_OK) {
@@ -540,8 +559,6 @@ int setup_tc(pawfd_ctx* c) {
     }
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesA, 0, sa_bytes), "memset");
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesB, 0, sb_bytes), "memset");
-    if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapA, t.rotSlicesA, t.rot_rowsA_alloc, t.rot_Lc, S, sg::BM);
-    if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.rotMapB, t.rotSlicesB, (int)t.rot_rblk, t.rot_Lc, S, sg::BN);
   }
   t.ready = rc == PAWFD_OK;
   return rc;
