@@ -115,8 +115,8 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *   "stencil_ring"    ring stencil: planes in flight + in use, 0 (default 8), 8, 10 or 12.
  *   "stencil_zsplit"  general stencil kernel: the z range is split so that one launch has at
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
- *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 256 (0: the whole
- *                     slice buffer, 512 units); shorter blocks keep the digit slices in L2.
+ *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 512 (0: the whole
+ *                     slice buffer, 256 units); shorter blocks keep the digit slices in L2.
  *   "stencil_df"      1 (default): the real FP64 stencil computes in double-float FP32 pairs
  *                     (about 48 bits, well inside the FP64 tolerance; far faster than the FP64
  *                     pipe); 0: FP64 arithmetic.  "stencil_variant" 2 also selects FP64.

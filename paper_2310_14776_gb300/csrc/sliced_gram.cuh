@@ -12,8 +12,11 @@
 //     D2 = order 2 (3 products)                 exact while KC <= 1365
 //     D3 = order 3 (4 products)                 exact while KC <= 1024
 //     D4 = orders 4 .. ORD, rounded in FP32 (each term is already 2^-28 below order 0)
-// Five accumulators of BN = 96 columns use 480 of the 512 TMEM columns.  Chunks are KC = 256
-// values long, which also keeps the FP32 drift of D4 small.  After every chunk
+// Five accumulators of BN = 96 columns use 480 of the 512 TMEM columns.  Chunks are KCG = 512
+// values long for the Gram matrices (D0 .. D3 stay exact: with |d| <= 65 the order-2 sums
+// reach 3 * 512 * 65^2 * 2^-14 < 2^10, inside the 2^(24-14) that keeps multiples of 2^-14
+// exact, and the others have more room) and KC = 256 for the rotation, whose contraction
+// (the bands) is usually one chunk; the FP32 drift of D4 stays small at either length.  After every chunk
 // the epilogue adds 2^(sigma_a + sigma_b) (D0 + ... + D4) to a double-float (two FP32)
 // accumulator with error-free transformations (Knuth's TwoSum), so the FP64 pipe is not
 // needed per chunk; the scale is taken relative to the row's largest sigma of the K block.
@@ -31,7 +34,8 @@
 namespace pawfd {
 namespace sg {
 
-constexpr int KC = 256;           // grid values per exactness chunk
+constexpr int KC = 256;           // grid values per exactness chunk of the rotation (bands)
+constexpr int KCG = 512;          // grid values per exactness chunk of the Gram matrices
 constexpr int BM = 128;           // output rows per CTA (TMEM lanes)
 constexpr int BN = 96;            // output columns per CTA (MMA N)
 constexpr int BK = 16;            // K per stage = one MMA (32-byte rows, 32B swizzle)
@@ -164,21 +168,24 @@ __device__ __forceinline__ void load8(const R* __restrict__ row, long long k0, l
 // [nchunks][sig_ld]; sigmax[row] (reset by the caller for every block) receives the largest
 // sigma of the row.  Consecutive warps take consecutive rows of one chunk; each lane takes 8
 // consecutive values of the 256-value chunk and writes 16 bytes per plane.
-template <class R, int S>
+template <class R, int S, int KCH>
 __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
                                                     int nchunks, long long Lp, bool swapped, int row_offset,
                                                     int out_rows, __nv_bfloat16* __restrict__ out,
                                                     int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
+  constexpr int NH = KCH / 256;   // runs of 256 values of the chunk: lane takes 8 values of each
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= rows * nchunks) return;
   const int r = warp % rows;
   const long long c = warp / rows;
-  const long long k0 = c * KC + lane * 8;
-  R x[8];
-  load8(src + (long long)r * ld, k0, len, swapped, x);
+  R x[NH][8];
+#pragma unroll
+  for (int h = 0; h < NH; ++h) load8(src + (long long)r * ld, c * KCH + h * 256 + lane * 8, len, swapped, x[h]);
   int emax = 0;
 #pragma unroll
-  for (int v = 0; v < 8; ++v) emax = max(emax, fields(x[v]).exp);
+  for (int h = 0; h < NH; ++h)
+#pragma unroll
+    for (int v = 0; v < 8; ++v) emax = max(emax, fields(x[h][v]).exp);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   const int orow = row_offset + r;
@@ -186,11 +193,15 @@ __global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, i
     sig[c * sig_ld + orow] = emax - FloatBits<R>::bias - 5;
     atomicMax(sigmax + orow, emax - FloatBits<R>::bias - 5);
   }
-  uint32_t o[S][4];
-  digits8_t<S>(x, emax, o);
 #pragma unroll
-  for (int i = 0; i < S; ++i)
-    *(uint4*)(out + plane_offset_rm(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+  for (int h = 0; h < NH; ++h) {
+    uint32_t o[S][4];
+    digits8_t<S>(x[h], emax, o);
+    const long long k0 = c * KCH + h * 256 + lane * 8;
+#pragma unroll
+    for (int i = 0; i < S; ++i)
+      *(uint4*)(out + plane_offset_rm(i, k0, orow, out_rows, Lp)) = make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
+  }
 }
 
 // The same for core-matrix planes (the rotation's C operand): one warp per (group of 8 rows,
@@ -544,7 +555,7 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
 // BULK: the operands are core-matrix planes (plane_offset_cm), one bulk copy per plane and
 // operand per stage, read by the tensor cores without swizzle; otherwise row-major planes
 // (plane_offset_rm) through the 4-D TMA maps tA and tB with a 32-byte swizzle.
-template <int S, int ORD, bool ONE, bool BULK>
+template <int S, int ORD, bool ONE, bool BULK, int KCH>
 __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
                                                                   const __grid_constant__ CUtensorMap tB,
                                                                   const __grid_constant__ GramArgs a) {
@@ -572,12 +583,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   const int c_begin = blockIdx.y * a.chunks_per_cta;
   const int c_end = min(a.nchunks, c_begin + a.chunks_per_cta);
   const int nch = max(0, c_end - c_begin);
-  const int steps_per_chunk = KC / BK;
+  const int steps_per_chunk = KCH / BK;
   // stages of chunk c (the last chunk of a block may hold fewer than KC valid values: no MMAs
   // on its zero padding)
   auto steps_of = [&](int c) {
     if (a.klen <= 0) return steps_per_chunk;
-    const long long left = a.klen - (long long)(c_begin + c) * KC;
+    const long long left = a.klen - (long long)(c_begin + c) * KCH;
     return (int)max(1ll, min((long long)steps_per_chunk, (left + BK - 1) / BK));
   };
   int steps_tile = 0;
@@ -614,7 +625,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           set_status(a.st, PAWFD_ETIMEDOUT, 1001);
           break;
         }
-        const int kx = (c_begin + c) * KC + q * BK;
+        const int kx = (c_begin + c) * KCH + q * BK;
         unsigned char* sa = smem + s * stage_bytes<S>();
         unsigned char* sb = sa + S * a_slice_bytes<S>();
         tc::mbar_expect_tx(&full[s], stage_bytes<S>());

@@ -71,9 +71,9 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   const int tiles = herm ? halves * sg::herm_tiles(nb) : Tr * halves * Tc;
   // K block: the allocated slice length, or fewer chunks (the slices of a short block can stay
   // in L2 between the slicing kernels and the MMA kernel)
-  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KC)
+  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
-  const int max_chunks = (int)(Kblk / sg::KC);
+  const int max_chunks = (int)(Kblk / sg::KCG);
   // splits per K block: fill the SMs once (one CTA per SM), at least one chunk per CTA
   // one CTA per SM: tiles x splits within one wave (a partial second wave doubles the time)
   int nsplit = std::max(1, std::min(max_chunks, c->num_sms / tiles));
@@ -83,7 +83,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   int blk = 0;
   for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
     const long long len = std::min(Kblk, L - k0);
-    const int nch = (int)((len + sg::KC - 1) / sg::KC);
+    const int nch = (int)((len + sg::KCG - 1) / sg::KCG);
     const int cpc = (nch + nsplit - 1) / nsplit;
     const int ns = (nch + cpc - 1) / cpc;
     // per-row largest sigma of this block: start from a very negative value
@@ -91,13 +91,13 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
     // slices keep the allocated row length t.kblk (the tensor maps' layout); a shorter block
     // fills the first Kblk values of each row
-    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
-    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
     c->launches += 2;
     if (cplx) {
-      sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+      sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
           B + k0, nb, L, len, nch, t.kblk, true, nbp, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
       c->launches += 1;
     }
@@ -128,7 +128,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     a.st = c->d_status;
     // slots written by the first block must cover every split later blocks add into
     if (blk == 0 && ns < nsplit) nsplit = ns;
-    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
     c->launches += 1;
   }
@@ -151,9 +151,9 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
   TcScratch& t = c->tc;
   const long long L = (long long)c->K;
   const int tiles = sg::herm_tiles(nb);
-  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KC)
+  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
-  const int max_chunks = (int)(Kblk / sg::KC);
+  const int max_chunks = (int)(Kblk / sg::KCG);
   int nsplit = std::max(1, std::min(max_chunks, c->num_sms / tiles));
   while (nsplit > 1 && (size_t)nsplit * nb * nb * sizeof(double) > t.part_bytes) --nsplit;
   __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
@@ -161,14 +161,14 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
   int blk = 0;
   for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
     const long long len = std::min(Kblk, L - k0);
-    const int nch = (int)((len + sg::KC - 1) / sg::KC);
+    const int nch = (int)((len + sg::KCG - 1) / sg::KCG);
     const int cpc = (nch + nsplit - 1) / nsplit;
     const int ns = (nch + cpc - 1) / cpc;
     cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
     cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
-    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
-    sg::slice_kernel<R, S><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
     sg::GramArgs a = {};
     a.gA = sA;
@@ -195,7 +195,7 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a.part = (double*)t.part;
     a.st = c->d_status;
     if (blk == 0 && ns < nsplit) nsplit = ns;
-    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
     // psi^T psi: psi's planes and exponents on both sides (psi's planes through a map with the
     // B operand's box)
@@ -206,7 +206,7 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a2.sig_ldB = t.rowsA_alloc;
     a2.maxB = t.maxA;
     a2.part = (double*)t.part2;
-    sg::sliced_gram_kernel<S, ORD, false, false><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapAB, a2);
     c->launches += 4;
   }
@@ -301,11 +301,11 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
     a.klen = Lk;
     a.rot_tiles = tilesM * a.tilesN;
     if (nch == 1)   // persistent CTAs, one per SM (the kernel's shared memory admits one)
-      sg::sliced_gram_kernel<S, ORD, true, true>
+      sg::sliced_gram_kernel<S, ORD, true, true, sg::KC>
           <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB,
                                                                                                         a);
     else
-      sg::sliced_gram_kernel<S, ORD, false, true>
+      sg::sliced_gram_kernel<S, ORD, false, true, sg::KC>
           <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, a);
     c->launches += 2;
   }
@@ -463,8 +463,8 @@ int setup_tc(pawfd_ctx* c) {
   const int S = is_fp32(c) ? 4 : 7;
   const long long L = (long long)c->K * (cplx ? 2 : 1);
   // K block: up to 512 chunks, no longer than the padded row
-  const long long Lpad = (L + sg::KC - 1) / sg::KC * sg::KC;
-  t.kblk = std::min<long long>(512LL * sg::KC, Lpad);
+  const long long Lpad = (L + sg::KCG - 1) / sg::KCG * sg::KCG;
+  t.kblk = std::min<long long>(256LL * sg::KCG, Lpad);
   t.rowsA_alloc = (nb + sg::BM - 1) / sg::BM * sg::BM;
   // complex: the swapped half starts at row nbp (a multiple of 8) and has its own column tiles
   const int nbp = (nb + 7) / 8 * 8, tcn = (nb + sg::BN - 1) / sg::BN;
@@ -495,12 +495,12 @@ int setup_tc(pawfd_ctx* c) {
     const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     // the Gram (row-major planes, TMA maps) and the rotation (core-matrix planes, bulk copies;
     // persistent one-chunk form and general form)
-    const void* fns7[] = {(const void*)sg::sliced_gram_kernel<7, 6, false, false>,
-                          (const void*)sg::sliced_gram_kernel<7, 6, true, true>,
-                          (const void*)sg::sliced_gram_kernel<7, 6, false, true>};
-    const void* fns4[] = {(const void*)sg::sliced_gram_kernel<4, 4, false, false>,
-                          (const void*)sg::sliced_gram_kernel<4, 4, true, true>,
-                          (const void*)sg::sliced_gram_kernel<4, 4, false, true>};
+    const void* fns7[] = {(const void*)sg::sliced_gram_kernel<7, 6, false, false, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, true, true, sg::KC>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KC>};
+    const void* fns4[] = {(const void*)sg::sliced_gram_kernel<4, 4, false, false, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, true, true, sg::KC>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KC>};
     for (int f = 0; f < 3 && rc == PAWFD_OK; ++f)
       rc = check_cuda(c, cudaFuncSetAttribute(S == 7 ? fns7[f] : fns4[f], smem_attr,
                                               S == 7 ? sg::smem_bytes<7>() : sg::smem_bytes<4>()),
