@@ -656,27 +656,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       }
     }
   } else if (warp == EPI_WARPS + 1) {
-    if (lane == 0) {   // MMA issuer
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
-      int g = 0;
-      for (int it = 0; it < items && !abort_flag; ++it) {
-        if (it > 0 && !tc::mbar_wait(&dempty, (it - 1) & 1)) {
-          abort_flag = 1;
-          set_status(a.st, PAWFD_ETIMEDOUT, 1002);
+    // MMA issuer: the whole warp runs the loop (the waits, the stage's descriptors), so the
+    // descriptors are warp-uniform values; one elected lane issues the MMAs and the commits.
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    const bool leader = tc::elect_one();
+    int g = 0;
+    for (int it = 0; it < items; ++it) {
+      if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+      if (it > 0) {
+        const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&dempty, (it - 1) & 1));
+        if (!ok) {
+          if (leader) {
+            abort_flag = 1;
+            set_status(a.st, PAWFD_ETIMEDOUT, 1002);
+          }
+          break;
+        }
+      }
+      tc::fence_after_sync();
+      const int steps = steps_of(it % nch);
+      bool failed = false;
+      for (int q = 0; q < steps; ++q, ++g) {
+        const int s = g % STAGES;
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (g / STAGES) & 1))) {
+          if (leader) {
+            abort_flag = 1;
+            set_status(a.st, PAWFD_ETIMEDOUT, 1003);
+          }
+          failed = true;
           break;
         }
         tc::fence_after_sync();
-        const int steps = steps_of(it % nch);
-        for (int q = 0; q < steps && !abort_flag; ++q, ++g) {
-          const int s = g % STAGES;
-          if (!tc::mbar_wait(&full[s], (g / STAGES) & 1)) {
-            abort_flag = 1;
-            set_status(a.st, PAWFD_ETIMEDOUT, 1003);
-            break;
-          }
-          tc::fence_after_sync();
-          unsigned char* sa = smem + s * stage_bytes<S>();
-          unsigned char* sb = sa + S * a_slice_bytes<S>();
+        unsigned char* sa = smem + s * stage_bytes<S>();
+        unsigned char* sb = sa + S * a_slice_bytes<S>();
+        // plane i of a stage starts i slices after the stage's first plane; the start address
+        // field (address / 16, 14 bits) does not overflow inside the 228 KB of shared memory
+        const uint64_t da0 = BULK ? tc::smem_desc_nosw(sa, 128, 256) : tc::smem_desc(sa, BK * 2);
+        const uint64_t db0 = BULK ? tc::smem_desc_nosw(sb, 128, 256) : tc::smem_desc(sb, BK * 2);
+        if (leader) {
           bool touched[NACC] = {false, false, false, false, false};
 #pragma unroll
           for (int i = 0; i < S; ++i)
@@ -686,19 +703,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
               const int slot = (i + j) < NACC - 1 ? (i + j) : NACC - 1;
               const uint32_t d = tmem + (uint32_t)(slot * BN);
               // the first product written into an accumulator in this chunk overwrites it
-              const bool first = (q == 0) && !touched[slot];
+              const uint32_t acc = touched[slot] ? 1u : (q == 0 ? 0u : 1u);
               touched[slot] = true;
-              const uint64_t da = BULK ? tc::smem_desc_nosw(sa + i * a_slice_bytes<S>(), 128, 256)
-                                       : tc::smem_desc(sa + i * a_slice_bytes<S>(), BK * 2);
-              const uint64_t db = BULK ? tc::smem_desc_nosw(sb + j * b_slice_bytes(), 128, 256)
-                                       : tc::smem_desc(sb + j * b_slice_bytes(), BK * 2);
-              tc::mma_bf16(d, da, db, idesc, first ? 0u : 1u);
+              tc::mma_bf16(d, da0 + (uint64_t)((i * a_slice_bytes<S>()) >> 4),
+                           db0 + (uint64_t)((j * b_slice_bytes()) >> 4), idesc, acc);
             }
           tc::mma_commit(&empty[s]);
           consumed = g + 1;
         }
-        tc::mma_commit(&dfull);
+        __syncwarp();
       }
+      if (failed) break;
+      if (leader) tc::mma_commit(&dfull);
+      __syncwarp();
     }
   } else {
     if constexpr (ONE) {
