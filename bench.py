@@ -87,6 +87,9 @@ def parse_args():
     p.add_argument("--no-refine", action="store_true", help="mixed: skip the final FP64 refinement measurement")
     p.add_argument("--bands", type=int, default=0,
                    help="single workloads: this many bands instead of the workload's own (profiling cases)")
+    p.add_argument("--tc-scratch-mb", type=int, default=8192,
+                   help="single workloads: digit-plane scratch of the tensor-core Gram and rotation (MB); "
+                        "0 keeps the library's default block sizes")
     a = p.parse_args()
     if a.precision is None:
         a.precision = "mixed" if a.workload in ("batch64", "served") else "fp64"
@@ -179,6 +182,8 @@ def run_gpu(args):
     nb, K = (args.bands or w.nbands), system.npoints
     cplx = system.complex_wf
     ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
+    if args.tc_scratch_mb:
+        ctx.set_option("tc_scratch_mb", args.tc_scratch_mb)
     if nb * K <= HOST_PSI_MAX and nb == w.nbands:
         psi_host = w.psi(system)
         if args.precision == "mixed":
@@ -286,6 +291,7 @@ def run_gpu(args):
         "config": {"workload": w.name, "grid": list(system.n), "bands": nb, "atoms": system.natoms,
                    "projectors_per_atom": int(system.nproj[0]) if system.natoms else 0,
                    "precision": args.precision, "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "tc_scratch_mb": args.tc_scratch_mb,
                    "l2": "inputs larger than L2 (%.2f GB of bands per step)" % (2 * nb * K * esize / 1e9)},
         "rr_steps_per_s": args.steps * world / elapsed,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
@@ -313,7 +319,7 @@ def run_gpu(args):
             work[key] = None
         psi[(args.warmup + args.steps + 1) % 2] = None
         torch.cuda.empty_cache()
-        result["refine"] = refine_gpu(system, nb, latest, eps_mixed, dev)
+        result["refine"] = refine_gpu(system, nb, latest, eps_mixed, dev, args.tc_scratch_mb)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, w, args.precision)
     if world > 1:
@@ -325,11 +331,13 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def refine_gpu(system, nb, psi_lo, eps_mixed, dev):
+def refine_gpu(system, nb, psi_lo, eps_mixed, dev, tc_scratch_mb=0):
     """The final FP64 refinement (pawfd_refine) of the last rotated mixed-form bands, timed."""
     import torch
     from paper_2310_14776_gb300 import api
     fp = api.Context(system, max_bands=nb, device=dev, precision="fp64")
+    if tc_scratch_mb:
+        fp.set_option("tc_scratch_mb", tc_scratch_mb)
     fp.refine(psi_lo)              # untimed first call
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -117,6 +117,14 @@ long long pawfd_launch_count(const pawfd_ctx* ctx);
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
  *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 512 (0: the whole
  *                     slice buffer, 256 units); shorter blocks keep the digit slices in L2.
+ *   "tc_scratch_mb"   size of the tensor-core digit-plane scratch, in MB: the Gram's K block is
+ *                     as long as the planes of both operands fit in it, and the rotation's block
+ *                     of grid points as long as their planes fit in it (0, the default: K
+ *                     blocks of 256 x 512 values and rotation blocks of 512 MB).  Larger blocks
+ *                     mean fewer launches and better balance across SMs at the cost of memory.
+ *                     Waits for the context's stream, then frees and re-allocates the scratch;
+ *                     on an allocation failure returns PAWFD_ENOMEM and turns the tensor-core
+ *                     path off.
  *   "stencil_df"      1 (default): the real FP64 stencil computes in double-float FP32 pairs
  *                     (about 48 bits, well inside the FP64 tolerance; far faster than the FP64
  *                     pipe); 0: FP64 arithmetic.  "stencil_variant" 2 also selects FP64.

@@ -442,6 +442,20 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->tc_fused = value == 1;
     return PAWFD_OK;
   }
+  if (n == "tc_scratch_mb" && value >= 0 && value <= (1 << 20)) {
+    // re-size the digit-plane scratch: wait for the work in flight, free, allocate again
+    c->tc_scratch_mb = value;
+    if (!c->tc.ready) return PAWFD_OK;
+    int rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (rc != PAWFD_OK) return rc;
+    free_tc(c);
+    rc = setup_tc(c);
+    if (rc != PAWFD_OK) {
+      free_tc(c);
+      c->use_tc = false;
+    }
+    return rc;
+  }
   if (n == "tc_kblk" && value >= 0 && value <= 4096) {
     c->tc_kblk_chunks = value;
     return PAWFD_OK;

@@ -211,7 +211,8 @@ struct pawfd_ctx {
   int stencil_zsplit = 0;                     // general stencil: target CTAs per SM of a launch (0: 4)
   int stencil_ring = 0;                       // ring stencil: planes in the ring (0: 8; 8, 10 or 12)
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
-  int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 256-value chunks (0: allocation)
+  int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 512-value chunks (0: allocation)
+  int tc_scratch_mb = 0;                      // digit-plane scratch per operand set in MB (0: default sizes)
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
   bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic

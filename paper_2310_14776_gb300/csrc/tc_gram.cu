@@ -462,13 +462,19 @@ int setup_tc(pawfd_ctx* c) {
   const bool cplx = is_complex(c);
   const int S = is_fp32(c) ? 4 : 7;
   const long long L = (long long)c->K * (cplx ? 2 : 1);
-  // K block: up to 512 chunks, no longer than the padded row
-  const long long Lpad = (L + sg::KCG - 1) / sg::KCG * sg::KCG;
-  t.kblk = std::min<long long>(256LL * sg::KCG, Lpad);
   t.rowsA_alloc = (nb + sg::BM - 1) / sg::BM * sg::BM;
   // complex: the swapped half starts at row nbp (a multiple of 8) and has its own column tiles
   const int nbp = (nb + 7) / 8 * 8, tcn = (nb + sg::BN - 1) / sg::BN;
   t.rowsB_alloc = cplx ? nbp + tcn * sg::BN : tcn * sg::BN;
+  // K block: 256 chunks by default, or as many as the two operands' digit planes fit in the
+  // requested scratch size; never longer than the padded row
+  const long long Lpad = (L + sg::KCG - 1) / sg::KCG * sg::KCG;
+  long long kblk = 256LL * sg::KCG;
+  if (c->tc_scratch_mb > 0) {
+    const long long per_value = (long long)S * (t.rowsA_alloc + t.rowsB_alloc) * 2;
+    kblk = std::max<long long>(sg::KCG, ((long long)c->tc_scratch_mb << 20) / per_value / sg::KCG * sg::KCG);
+  }
+  t.kblk = std::min<long long>(kblk, Lpad);
   const size_t sa = (size_t)S * t.rowsA_alloc * t.kblk * 2, sb = (size_t)S * t.rowsB_alloc * t.kblk * 2;
   const int nchunks = (int)(t.kblk / sg::KC);
   const int rowsB = cplx ? nbp + nb : nb;
@@ -528,7 +534,8 @@ int setup_tc(pawfd_ctx* c) {
     t.rot_Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
     t.rot_rowsA_alloc = ((cplx ? 2 * nb : nb) + sg::BM - 1) / sg::BM * sg::BM;
     const long long Kpad = ((long long)c->K + sg::BN - 1) / sg::BN * sg::BN;
-    const long long budget = 512ll << 20;   // bytes of grid-point digits per block
+    // bytes of grid-point digits per block
+    const long long budget = c->tc_scratch_mb > 0 ? ((long long)c->tc_scratch_mb << 20) : (512ll << 20);
     long long rblk = budget / ((long long)S * t.rot_Lc * 2) / sg::BN * sg::BN;
     t.rot_rblk = std::max<long long>(sg::BN, std::min(rblk, Kpad));
     const int nchr = (int)(t.rot_Lc / sg::KC);

@@ -157,6 +157,43 @@ def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision,cplx", [("fp64", False), ("fp64", True), ("mixed", False)])
+def test_scratch_size_changes_blocks_not_results(dev, precision, cplx):
+    """tc_scratch_mb re-sizes the digit-plane scratch: 1 MB gives K blocks of one 512-value
+    chunk (dozens of launches, a ragged last block) and rotation blocks of a few hundred grid
+    points; 4096 MB one block for the whole grid.  Gram matrices and rotated bands agree with
+    the default blocking and with the oracle."""
+    from paper_2310_14776_gb300 import api
+    k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=521, k=k, complex_wf=cplx)
+    nb = 100
+    psi_np = synth.make_psi(s, nb, 522)
+    rng = np.random.default_rng(523)
+    C = np.linalg.qr(rng.standard_normal((nb, nb)))[0]
+    if cplx:
+        C = C.astype(np.complex128)
+    out = {}
+    for mb in (0, 1, 4096):
+        ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+        ctx.set_option("tc_scratch_mb", mb)
+        psi = to_dev(psi_np, dev).to(ctx.dtype)
+        hpsi, spsi, P = ctx.apply_hs(psi)
+        Hnm, Snm = ctx.gram_hs(psi, hpsi, P)
+        rot = ctx.rotate(psi, to_dev(C, dev))
+        out[mb] = tuple(t.cpu().numpy() for t in (Hnm, Snm, rot))
+        ctx.close()
+    rel = REL if precision == "fp64" else 1e-12
+    for mb in (1, 4096):
+        for got, ref in zip(out[mb][:2], out[0][:2]):
+            assert_close_matrix(got, ref, rel=rel)
+        assert_close_bands(out[mb][2], out[0][2], nb, rel=rel)
+    if precision == "fp64":
+        ref = O.rayleigh_ritz(s, psi_np)
+        assert_close_matrix(out[1][0], ref["Hnm"])
+        assert_close_matrix(out[1][1], ref["Snm"])
+        assert_close_bands(out[4096][2], O.rotate(psi_np, C), nb)
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_hermitian_gram_equals_full_gram(dev, cplx):
     k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
