@@ -497,9 +497,48 @@ __device__ __forceinline__ double f2d_scaled(float x, int e) {
   const unsigned hi = (u & 0x80000000u) | ((unsigned)ed << 20) | ((u >> 3) & 0xFFFFFu);
   return __hiloint2double((int)hi, (int)(u << 29));
 }
-// the double-float (xh, xl) times 2^e: both parts exact, one FP64 add
-__device__ __forceinline__ double df_to_double(float xh, float xl, int e) {
+// the double-float (xh, xl) times 2^e: both parts exact, one FP64 add (the general path)
+__device__ __noinline__ double df_to_double_slow(float xh, float xl, int e) {
   return f2d_scaled(xh, e) + f2d_scaled(xl, e);
+}
+// The same with integer operations only.  For a normalized pair (|xl| <= ulp(xh) / 2) the
+// 53-bit significand of the result is xh's 24 bits followed by 29 zero bits, plus or minus xl's
+// significand aligned to that last bit (xl's bits below it are dropped), renormalized by at
+// most one bit: within one unit in the last place of the FP64 result.  Zero and subnormal
+// parts, pairs that are not normalized and results outside the normal FP64 range take the
+// FP64 path.
+__device__ __forceinline__ double df_to_double(float xh, float xl, int e) {
+  const unsigned uh = __float_as_uint(xh), ul = __float_as_uint(xl);
+  const int eh = (int)((uh >> 23) & 0xFFu), el = (int)((ul >> 23) & 0xFFu);
+  const int d = eh - el;
+  int ed = eh - 127 + 1023 + e;
+  if (eh == 0 || (el != 0 && d < 21) || ed <= 1 || ed >= 2046) return df_to_double_slow(xh, xl, e);
+  const unsigned mh = (uh & 0x7FFFFFu) | 0x800000u;
+  unsigned hi = mh >> 3, lo = mh << 29;   // mh 2^29 as the high and low words of the significand
+  unsigned L = 0;
+  if (el != 0 && d < 53) {
+    const unsigned ml = (ul & 0x7FFFFFu) | 0x800000u;
+    L = d <= 29 ? ml << (29 - d) : ml >> (d - 29);
+  }
+  if ((uh ^ ul) & 0x80000000u) {
+    const unsigned nlo = lo - L;
+    hi -= nlo > lo ? 1u : 0u;
+    lo = nlo;
+  } else {
+    const unsigned nlo = lo + L;
+    hi += nlo < lo ? 1u : 0u;
+    lo = nlo;
+  }
+  if (hi >= (1u << 21)) {
+    lo = (lo >> 1) | (hi << 31);
+    hi >>= 1;
+    ++ed;
+  } else if (hi < (1u << 20)) {
+    hi = (hi << 1) | (lo >> 31);
+    lo <<= 1;
+    --ed;
+  }
+  return __hiloint2double((int)((uh & 0x80000000u) | ((unsigned)ed << 20) | (hi & 0xFFFFFu)), (int)lo);
 }
 // x 2^e in FP32 (x is the correctly rounded sum of the double-float pair).  The rare path is
 // out of line so that it is not evaluated under a predicate for every value (FP64 pipe).
@@ -705,8 +744,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
               // the first product written into an accumulator in this chunk overwrites it
               const uint32_t acc = touched[slot] ? 1u : (q == 0 ? 0u : 1u);
               touched[slot] = true;
-              tc::mma_bf16(d, da0 + (uint64_t)((i * a_slice_bytes<S>()) >> 4),
-                           db0 + (uint64_t)((j * b_slice_bytes()) >> 4), idesc, acc);
+              // A plane i serves the products (i, 0) .. (i, ORD - i) back to back: read it from
+              // shared memory once and keep it in the collector buffer for the others
+              const uint64_t da = da0 + (uint64_t)((i * a_slice_bytes<S>()) >> 4);
+              const uint64_t db = db0 + (uint64_t)((j * b_slice_bytes()) >> 4);
+              const int jlast = (ORD - i) < (S - 1) ? (ORD - i) : (S - 1);
+              if (jlast == 0)
+                tc::mma_bf16_ca<0>(d, da, db, idesc, acc);
+              else if (j == 0)
+                tc::mma_bf16_ca<1>(d, da, db, idesc, acc);
+              else if (j < jlast)
+                tc::mma_bf16_ca<2>(d, da, db, idesc, acc);
+              else
+                tc::mma_bf16_ca<3>(d, da, db, idesc, acc);
             }
           tc::mma_commit(&empty[s]);
           consumed = g + 1;
@@ -721,18 +771,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     if constexpr (ONE) {
     // One chunk per tile (the rotation of real bands with nb <= KC): the value is (D0 + ... +
     // D4) 2^(sigma_a + sigma_b), summed exactly as a double-float and converted to the band
-    // dtype.  The chunk exponents of the tile's rows and columns are loaded while the tile's
-    // MMAs run (the columns' in two registers per lane, handed to the column's threads by
-    // shuffles).
+    // dtype.  TMEM is read in the 16 x 256-bit shape: in each 16-lane half h of the warp's
+    // lane quarter, thread t holds rows t/4 and t/4 + 8 and columns 2 (t%4), 2 (t%4) + 1 of
+    // each 8-column group, so four threads store four consecutive outputs of one row and a
+    // store instruction writes 8 rows x 4 values (not 32 rows x 1 value).  The chunk
+    // exponents of the tile's rows and columns are loaded while the tile's MMAs run (the
+    // columns' in two registers per lane, handed to the column's threads by shuffles).
     static_assert(EPI_COLS % 8 == 0 && EPI_COLS <= 64, "8-column groups, two exponent registers per lane");
+    constexpr int NG = EPI_COLS / 8;
     const int quarter = warp & 3, chalf = warp >> 2;
     const int cbase = chalf * EPI_COLS;
+    const int trow = lane >> 2, tcol2 = (lane & 3) * 2;
     for (int i = 0; i < ntiles; ++i) {
       int row0, col0, tcol;
       tile_at(i, row0, col0, tcol);
-      const int row = row0 + quarter * 32 + lane;
-      const bool rv = row < a.rowsA;
-      const int sga = rv ? __ldg(a.sigA + (long long)c_begin * a.sig_ldA + row) : 0;
+      // this thread's rows: r = 2 h + p  ->  row0 + 32 quarter + 16 h + 8 p + trow
+      int sga[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = row0 + quarter * 32 + (r >> 1) * 16 + (r & 1) * 8 + trow;
+        sga[r] = row < a.rowsA ? __ldg(a.sigA + (long long)c_begin * a.sig_ldA + row) : 0;
+      }
       const int cl0 = col0 + cbase + lane, cl1 = cl0 + 32;
       const int sgb0 = cl0 < a.rowsB ? __ldg(a.sigB + (long long)c_begin * a.sig_ldB + cl0) : 0;
       const int sgb1 = (lane + 32 < EPI_COLS && cl1 < a.rowsB) ? __ldg(a.sigB + (long long)c_begin * a.sig_ldB + cl1) : 0;
@@ -746,56 +805,70 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         break;
       }
       tc::fence_after_sync();
-      const bool live = rv && !abort_flag;
-      const int band = row % a.rot_nb, part = row / a.rot_nb;
-      const long long base = (long long)band * a.rot_K;
-      // TMEM -> the exact double-float sums (vh, vl) of the five orders, 8 columns at a time;
-      // then TMEM goes back to the MMA warp and the conversion and stores overlap the next tile
-      float vh[EPI_COLS], vl[EPI_COLS];
+      // TMEM -> the exact double-float sums (vh, vl) of the five orders
+      float vh[2][NG][4], vl[2][NG][4];   // [h][group][2 p + c]
 #pragma unroll
-      for (int g = 0; g < EPI_COLS / 8; ++g) {
-        uint32_t d[NACC][8];
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cbase + g * 8);
+      for (int h = 0; h < 2; ++h)
 #pragma unroll
-        for (int o = 0; o < NACC; ++o) tc::tmem_ld8(taddr + o * BN, d[o]);
-        tc::tmem_wait_ld();
+        for (int g = 0; g < NG; ++g) {
+          uint32_t d[NACC][4];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32 + h * 16) << 16) + (uint32_t)(cbase + g * 8);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float s1, e1, s2, e2, s3, e3;
-          two_sum(__uint_as_float(d[0][j]), __uint_as_float(d[1][j]), s1, e1);
-          two_sum(s1, __uint_as_float(d[2][j]), s2, e2);
-          two_sum(s2, __uint_as_float(d[3][j]), s3, e3);
-          two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][j]), vh[g * 8 + j], vl[g * 8 + j]);
+          for (int o = 0; o < NACC; ++o) tc::tmem_ld_16x256b(taddr + o * BN, d[o]);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float s1, e1, s2, e2, s3, e3;
+            two_sum(__uint_as_float(d[0][e]), __uint_as_float(d[1][e]), s1, e1);
+            two_sum(s1, __uint_as_float(d[2][e]), s2, e2);
+            two_sum(s2, __uint_as_float(d[3][e]), s3, e3);
+            two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][e]), vh[h][g][e], vl[h][g][e]);
+          }
         }
-      }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&dempty);
+      // column exponents of this thread's columns 8 g + tcol2 + c (all lanes shuffle)
+      int sgb[NG][2];
 #pragma unroll
-      for (int j4 = 0; j4 < EPI_COLS; j4 += 4) {
-        const int col = col0 + cbase + j4;
-        double v[4];
+      for (int g = 0; g < NG; ++g)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int cj = j4 + j;   // column within this warp's part
-          const int sgb = __shfl_sync(0xffffffffu, cj < 32 ? sgb0 : sgb1, cj & 31);
-          v[j] = col + j < a.rowsB
-                     ? (a.rot_fp32 ? (double)f2f_scaled(vh[cj], sga + sgb) : df_to_double(vh[cj], vl[cj], sga + sgb))
-                     : 0.0;
+        for (int c = 0; c < 2; ++c) {
+          const int cj = g * 8 + tcol2 + c;
+          sgb[g][c] = __shfl_sync(0xffffffffu, g * 8 < 32 ? sgb0 : sgb1, cj & 31);
         }
-        if (!live) continue;
-        if (a.rot_vec && col + 3 < a.rowsB) {
+      if (abort_flag) continue;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int h = r >> 1, p = r & 1;
+        const int row = row0 + quarter * 32 + h * 16 + p * 8 + trow;
+        if (row >= a.rowsA) continue;
+        const int band = row % a.rot_nb, part = row / a.rot_nb;
+        const long long base = (long long)band * a.rot_K;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const int col = col0 + cbase + g * 8 + tcol2;
+          const bool vec = a.rot_vec && col + 1 < a.rowsB;
           if (a.rot_fp32) {
-            *(float4*)((float*)a.rot_out + base + col) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+            const float v0 = f2f_scaled(vh[h][g][2 * p], sga[r] + sgb[g][0]);
+            const float v1 = f2f_scaled(vh[h][g][2 * p + 1], sga[r] + sgb[g][1]);
+            if (vec) {
+              *(float2*)((float*)a.rot_out + base + col) = make_float2(v0, v1);
+            } else {
+              if (col < a.rowsB) ((float*)a.rot_out)[a.rot_cplx ? 2 * (base + col) + part : base + col] = v0;
+              if (col + 1 < a.rowsB)
+                ((float*)a.rot_out)[a.rot_cplx ? 2 * (base + col + 1) + part : base + col + 1] = v1;
+            }
           } else {
-            *(double2*)((double*)a.rot_out + base + col) = make_double2(v[0], v[1]);
-            *(double2*)((double*)a.rot_out + base + col + 2) = make_double2(v[2], v[3]);
-          }
-        } else {
-          for (int j = 0; j < 4 && col + j < a.rowsB; ++j) {
-            const long long idx = a.rot_cplx ? 2 * (base + col + j) + part : base + col + j;
-            if (a.rot_fp32) ((float*)a.rot_out)[idx] = (float)v[j];
-            else ((double*)a.rot_out)[idx] = v[j];
+            const double v0 = df_to_double(vh[h][g][2 * p], vl[h][g][2 * p], sga[r] + sgb[g][0]);
+            const double v1 = df_to_double(vh[h][g][2 * p + 1], vl[h][g][2 * p + 1], sga[r] + sgb[g][1]);
+            if (vec) {
+              *(double2*)((double*)a.rot_out + base + col) = make_double2(v0, v1);
+            } else {
+              if (col < a.rowsB) ((double*)a.rot_out)[a.rot_cplx ? 2 * (base + col) + part : base + col] = v0;
+              if (col + 1 < a.rowsB)
+                ((double*)a.rot_out)[a.rot_cplx ? 2 * (base + col + 1) + part : base + col + 1] = v1;
+            }
           }
         }
       }
