@@ -128,6 +128,19 @@ __device__ __forceinline__ long long plane_offset_cm(int i, long long k, int r, 
          ((k >> 3) & 1) * 64 + (r & 7) * 8 + (k & 7);
 }
 
+// d 2^(-7 i) as a float for an integer |d| < 2^22, exactly, without a conversion instruction:
+// the float 1.5 2^(23 - 7 i) has a unit in the last place of 2^(-7 i), so adding d to its bits
+// and subtracting the float again leaves d 2^(-7 i).
+__device__ __forceinline__ float digit_scaled(int d, int i) {
+  const int m = ((150 - 7 * i) << 23) | 0x400000;
+  return __int_as_float(m + d) - __int_as_float(m);
+}
+// Two floats that bf16 represents exactly (at most 8 significant bits) as a bf16x2 word, lo in
+// the low half: the top 16 bits of each.
+__device__ __forceinline__ uint32_t pack_bf16x2_exact(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
 template <int S>
 __device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32_t (&out)[S][4]);
 template <int S>
@@ -168,8 +181,10 @@ __device__ __forceinline__ void load8(const R* __restrict__ row, long long k0, l
 // [nchunks][sig_ld]; sigmax[row] (reset by the caller for every block) receives the largest
 // sigma of the row.  Consecutive warps take consecutive rows of one chunk; each lane takes 8
 // consecutive values of the 256-value chunk and writes 16 bytes per plane.
+// (Memory-bound: the register cap keeps three CTAs per SM for FP64 values and six for FP32.)
 template <class R, int S, int KCH>
-__global__ void __launch_bounds__(256) slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 6)
+    slice_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
                                                     int nchunks, long long Lp, bool swapped, int row_offset,
                                                     int out_rows, __nv_bfloat16* __restrict__ out,
                                                     int* __restrict__ sig, int sig_ld, int* __restrict__ sigmax) {
@@ -297,14 +312,10 @@ __device__ __forceinline__ void digits8_t(const double (&x)[8], int emax, uint32
           d[i - 1] += 1;
         }
 #pragma unroll
-      for (int i = 0; i < S; ++i) dv[i][u] = (f.neg ? -(float)d[i] : (float)d[i]) * __int_as_float((127 - 7 * i) << 23);
+      for (int i = 0; i < S; ++i) dv[i][u] = digit_scaled(f.neg ? -d[i] : d[i], i);
     }
 #pragma unroll
-    for (int i = 0; i < S; ++i) {
-      uint32_t r;
-      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(dv[i][1]), "f"(dv[i][0]));
-      out[i][p] = r;
-    }
+    for (int i = 0; i < S; ++i) out[i][p] = pack_bf16x2_exact(dv[i][0], dv[i][1]);
   }
 }
 
@@ -322,29 +333,28 @@ __device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_
     float d[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
-      d[v] = rintf(y[v]);
+      // round to the nearest integer (ties to even; |y| <= 64): adding and subtracting
+      // 1.5 2^23 leaves the integer part
+      d[v] = (y[v] + 12582912.0f) - 12582912.0f;
       y[v] = (y[v] - d[v]) * 128.0f;
     }
     const float w = __int_as_float((127 - 7 * i) << 23);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      uint32_t r;
-      asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(d[2 * j + 1] * w), "f"(d[2 * j] * w));
-      out[i][j] = r;
-    }
+    for (int j = 0; j < 4; ++j) out[i][j] = pack_bf16x2_exact(d[2 * j] * w, d[2 * j + 1] * w);
   }
 }
 
 // Persistent, double-buffered form: each CTA walks tiles t = blockIdx.x, + gridDim.x, ...
 // (chunk-major, so that CTAs running together read the same band rows) and copies the next
-// tile into shared memory with cp.async (8 bytes per FP64 value or 4 per FP32 value, zero
-// filled past the bands or the block's grid points) while it slices the current one.  The
-// staged tile is band-major: buf[n][q] (real) or buf[n][2 q + c] (complex), RT grid points q.
+// tile into shared memory with cp.async while it slices the current one: 16 bytes per copy
+// when the band rows and the block start allow it (vec16), else one value per copy; zero
+// filled past the bands or the block's grid points.  The staged tile is dense and band-major:
+// buf[n][q] (real) or buf[n][2 q + c] (complex), RT grid points q per band row.
 template <class R>
-__host__ __device__ constexpr int slice_t_pitch() { return sizeof(R) == 8 ? 2 * RT + 2 : 2 * RT + 4; }
+__host__ __device__ constexpr int slice_t_tile_values() { return KC * RT; }
 // two staged tiles of KC contraction values x RT grid points
 template <class R>
-__host__ __device__ constexpr int slice_t_smem() { return KC * slice_t_pitch<R>() * (int)sizeof(R); }
+__host__ __device__ constexpr int slice_t_smem() { return 2 * slice_t_tile_values<R>() * (int)sizeof(R); }
 
 __device__ __forceinline__ void cp_async_zfill(void* sdst, const void* gsrc, int bytes, bool valid) {
   const int src_bytes = valid ? bytes : 0;
@@ -355,6 +365,11 @@ __device__ __forceinline__ void cp_async_zfill(void* sdst, const void* gsrc, int
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(sdst)), "l"(gsrc), "r"(src_bytes)
                  : "memory");
 }
+// 16 bytes, of which the first src_bytes (0 .. 16) are copied and the rest zero filled
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_addr(sdst)), "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
@@ -362,21 +377,35 @@ template <class R, int S>
 __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
                                                       long long r0, int rcount, long long Lp, int out_rows,
                                                       __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
-                                                      int sig_ld, int* __restrict__ sigmax, int nch) {
-  constexpr int PITCH = slice_t_pitch<R>();          // values per staged band row (two of them for real)
+                                                      int sig_ld, int* __restrict__ sigmax, int nch, int vec16) {
   extern __shared__ __align__(16) unsigned char slice_t_smem_raw[];
-  R* bufs = (R*)slice_t_smem_raw;                    // [2][KC / 2][PITCH]: KC contraction values x RT points
+  R* bufs = (R*)slice_t_smem_raw;                    // [2][KC * RT] staged values
   __shared__ int pmax[16][RT];
   const int tid = threadIdx.x;
   const int nrt = (rcount + RT - 1) / RT;
   const int ntiles = nrt * nch;
   const int vals_per_row = cplx ? 2 * RT : RT;        // values of one band row of a tile
   const int rows_per_chunk = cplx ? KC / 2 : KC;      // band rows of one chunk
-  // staged value (k, q) of a tile: real buf[k][q] (row pitch PITCH / 2), complex buf[k / 2][2 q + k % 2]
+  constexpr int V16 = 16 / (int)sizeof(R);            // values per 16-byte copy
+  // staged value (k, q) of a tile: real buf[k][q], complex buf[k / 2][2 q + k % 2]
   auto stage = [&](R* buf, int t) {
     const int rt = t % nrt, c = t / nrt;
     const int rl0 = rt * RT;
     const int nfirst = c * rows_per_chunk;
+    if (vec16) {
+      const int per_row = vals_per_row / V16;
+      const int total = rows_per_chunk * per_row;
+      for (int e = tid; e < total; e += 256) {
+        const int nr = e / per_row, w = (e - nr * per_row) * V16;
+        const int n = nfirst + nr;
+        // values of this copy that lie inside the block's grid points
+        const int left = cplx ? 2 * (rcount - rl0) - w : rcount - rl0 - w;
+        const int nval = n < nb ? max(0, min(V16, left)) : 0;
+        const long long gi = cplx ? (((long long)n * K + r0 + rl0) * 2 + w) : ((long long)n * K + r0 + rl0 + w);
+        cp_async16(buf + nr * vals_per_row + w, nval > 0 ? psi + gi : psi, nval * (int)sizeof(R));
+      }
+      return;
+    }
     const int total = rows_per_chunk * vals_per_row;
     for (int e = tid; e < total; e += 256) {
       const int nr = e / vals_per_row, w = e - nr * vals_per_row;
@@ -384,20 +413,19 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
       const int q = cplx ? w >> 1 : w;
       const bool ok = n < nb && rl0 + q < rcount;
       const long long gi = cplx ? (((long long)n * K + r0 + rl0) * 2 + w) : ((long long)n * K + r0 + rl0 + w);
-      R* dst = buf + (cplx ? (long long)nr * PITCH + w : (long long)nr * (PITCH / 2) + w);
-      cp_async_zfill(dst, ok ? psi + gi : psi, (int)sizeof(R), ok);
+      cp_async_zfill(buf + nr * vals_per_row + w, ok ? psi + gi : psi, (int)sizeof(R), ok);
     }
   };
   auto val = [&](const R* buf, int k, int q) -> R {
-    return cplx ? buf[(k >> 1) * PITCH + 2 * q + (k & 1)] : buf[k * (PITCH / 2) + q];
+    return cplx ? buf[(k >> 1) * (2 * RT) + 2 * q + (k & 1)] : buf[k * RT + q];
   };
   int it = 0;
   int t = blockIdx.x;
   if (t < ntiles) stage(bufs, t);
   cp_async_commit();
   for (; t < ntiles; t += gridDim.x, ++it) {
-    R* cur = bufs + (it & 1) * (KC / 2) * PITCH;
-    R* nxt = bufs + ((it + 1) & 1) * (KC / 2) * PITCH;
+    R* cur = bufs + (it & 1) * slice_t_tile_values<R>();
+    R* nxt = bufs + ((it + 1) & 1) * slice_t_tile_values<R>();
     if (t + (int)gridDim.x < ntiles) stage(nxt, t + gridDim.x);
     cp_async_commit();
     cp_async_wait1();   // this tile's copies have landed

@@ -554,6 +554,24 @@ __global__ void oa_decide_kernel(const double* __restrict__ part, const double* 
   flags[GATE_LAMBDA] = !(near && nojac);
 }
 
+// After the second step of the near path: when it left every |e_ij| <= 1e-8 and no pair
+// coupled, X2 = X1 (I + E2) is the eigenvector basis to FP64 precision (the error left is of
+// the order of |e|^2), so A = X2^H H X2 and the Jacobi sweeps are skipped and the eigenvalues
+// are the step's lambda_i (Rayleigh quotients of X1, within |e|^2 of those of X2).
+__global__ void oa_decide2_kernel(const double* __restrict__ part2, int* __restrict__ flags, const int* gate) {
+  if (threadIdx.x != 0 || gated(gate)) return;
+  double coupled = 0.0, emax2 = 0.0;
+  for (int g = 0; g < OA_G; ++g) {
+    coupled += part2[2 * g];
+    emax2 = fmax(emax2, part2[2 * g + 1]);
+  }
+  if (emax2 <= 1e-16 && coupled == 0.0) {
+    flags[GATE_AM] = 1;
+    flags[GATE_JACOBI] = 1;
+    flags[GATE_LAMBDA] = 0;
+  }
+}
+
 // X = I + E
 template <class T>
 __global__ void identity_plus_kernel(const T* __restrict__ E, int n, T* __restrict__ X, const int* gate,
@@ -971,7 +989,8 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   }
 
   // ---- near path: X1 = I + E1; a second step unless the first left |e| <= 1e-8; A = X^H H X
-  // for the Jacobi sweeps unless no pair is left coupled (then the eigenvalues are lambda) ----
+  // for the Jacobi sweeps unless a step left every |e| <= 1e-8 and no pair coupled (then the
+  // eigenvalues are that step's lambda) ----
   {
     const int* step2 = flags + GATE_STEP2;
     const int* amg = flags + GATE_AM;
@@ -982,13 +1001,14 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2);
     oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, part, lam, step2, st);
     oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol, 1e-14, Li, part2, step2, st);
+    oa_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Li, false, n, T1, st, Vm, nullptr, nullptr, step2);
     copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, step2, st);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, amg);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, amg);
     hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, amg);
     lambda_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(lam, n, Am, flags + GATE_LAMBDA, st);
-    c->launches += 13;
+    c->launches += 14;
     rc = check_cuda(c, cudaGetLastError(), "near-path launch");
     if (rc != PAWFD_OK) return rc;
   }

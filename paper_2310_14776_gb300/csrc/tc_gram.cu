@@ -265,9 +265,13 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
     const int rcount = (int)std::min<long long>(t.rot_rblk, K - r0);
     cudaMemsetAsync(t.rotMaxB, 0x80, sizeof(int) * t.rot_rblk, c->stream);
     const int stiles = (rcount + sg::RT - 1) / sg::RT * nch;
+    // 16-byte staging copies: band rows and the block start on 16-byte boundaries
+    constexpr int v16 = 16 / (int)sizeof(R);
+    const int per = cplx ? 2 : 1;
+    const int vec16 = (per * K) % v16 == 0 && (per * r0) % v16 == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
     sg::slice_t_kernel<R, S><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R>(), c->stream>>>(
         psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
-        (int)t.rot_rblk, t.rotMaxB, nch);
+        (int)t.rot_rblk, t.rotMaxB, nch, vec16);
     sg::GramArgs a = {};
     a.gA = (const __nv_bfloat16*)t.rotSlicesA;
     a.gB = (const __nv_bfloat16*)t.rotSlicesB;

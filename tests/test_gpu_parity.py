@@ -349,8 +349,10 @@ def test_subspace_near_ritz_basis(dev, cplx):
         H1 = C0.conj().T @ H0 @ C0
         S1 = C0.conj().T @ S0 @ C0
         Hdeg = np.diag(np.repeat(np.arange(n // 2 + 1, dtype=float), 2)[:n]).astype(H1.dtype)
-        cases = [(H1, S1), (H1 + 1e-9 * rnd(13), S1 + 1e-9 * rnd(14)), (H1 + 1e-6 * rnd(15), S1 + 1e-6 * rnd(16)),
-                 (Hdeg + 1e-9 * rnd(17), np.eye(n) + 1e-10 * rnd(18))]
+        # 1e-7 and 1e-6: the first step leaves |e| above 1e-8, the second below it (no Jacobi
+        # sweeps; the eigenvalues are the second step's Rayleigh quotients)
+        cases = [(H1, S1), (H1 + 1e-9 * rnd(13), S1 + 1e-9 * rnd(14)), (H1 + 1e-7 * rnd(19), S1 + 1e-7 * rnd(20)),
+                 (H1 + 1e-6 * rnd(15), S1 + 1e-6 * rnd(16)), (Hdeg + 1e-9 * rnd(17), np.eye(n) + 1e-10 * rnd(18))]
         for H, S in cases:
             ref_eps, _, _ = O.subspace_diag(H, S)
             eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
