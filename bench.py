@@ -45,13 +45,13 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # profiles/dram_gram_hs_64c_256b.md).  At a fixed band count it grows with the grid points K
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
-_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "ad448c6ea872b883358588f8300a39d6d8c8d8b9",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "44c57458868bf05c9c7e9bead7734471195cee14",
+_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "9fbba2e9424e4e6498471fb2c73f3e6161a9c0a4",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "9ce5f1aaf97c12cdb49e6a798566e2917cfc2712",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
-                 "paper_2310_14776_gb300/csrc/tc_common.cuh": "55d9c2bd5425ee3d0ded06a7ec772b410d3832a8"}
+                 "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
-    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21836.3, "sources": _GRAM_SOURCES},
-    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11890.2, "sources": _GRAM_SOURCES},
+    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 22258.9, "sources": _GRAM_SOURCES},
+    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 12194.6, "sources": _GRAM_SOURCES},
 }
 
 
