@@ -373,23 +373,30 @@ def device_bands(ctx, nb, seed):
 
 
 def e2e_gpu(ctx, psi_host, work, args, dev):
-    """Same step through the public API with host buffers: H2D of psi and D2H of eps + rotated bands."""
+    """The same iterated step through the public API with host buffers: every step copies its
+    input bands from pinned host memory to the device, makes one pawfd_rr_step call and copies
+    the eigenvalues and the rotated bands back; the next step's input is that host copy (the
+    bands stay on the host between steps, as in a host-driven loop)."""
     import torch
     nb = psi_host.shape[0]
-    h_in = torch.from_numpy(psi_host).pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
+    h_bufs = [torch.from_numpy(psi_host).pin_memory(), torch.empty_like(torch.from_numpy(psi_host)).pin_memory()]
     h_eps = torch.empty(nb, dtype=torch.float64).pin_memory()
-    d_in = torch.empty_like(h_in, device=dev)
-    d_out = torch.empty_like(h_in, device=dev)
+    d_in = torch.empty_like(h_bufs[0], device=dev)
+    d_out = torch.empty_like(h_bufs[0], device=dev)
     stream = torch.cuda.current_stream(dev)
+    it = [0]
 
     def one():
+        h_in, h_out = h_bufs[it[0] % 2], h_bufs[(it[0] + 1) % 2]
         d_in.copy_(h_in, non_blocking=True)
         ctx.rr_step(d_in, out=d_out, work=work)      # the single public call of one step
         h_eps.copy_(work["eps"], non_blocking=True)
         h_out.copy_(d_out, non_blocking=True)
+        it[0] += 1
 
-    one()
+    # untimed: the first steps from the random start (the Cholesky path and dense Jacobi sweeps)
+    for _ in range(2):
+        one()
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -400,9 +407,10 @@ def e2e_gpu(ctx, psi_host, work, args, dev):
     ctx.sync()
     el = e0.elapsed_time(e1) * 1e-3
     K = psi_host[0].size
-    per_step_bytes = h_in.numel() * h_in.element_size()
+    per_step_bytes = h_bufs[0].numel() * h_bufs[0].element_size()
     return {"value": nb * K * args.e2e_steps / el / 1e9, "unit": UNIT, "steps": args.e2e_steps,
-            "api": "Context.rr_step (pawfd_rr_step) with pinned host buffers",
+            "api": "Context.rr_step (pawfd_rr_step) with pinned host buffers; each step's input is the previous "
+                   "step's rotated bands read back to the host",
             "h2d_bytes_per_step": per_step_bytes, "d2h_bytes_per_step": per_step_bytes + nb * 8}
 
 
