@@ -88,8 +88,8 @@ def parse_args():
     p.add_argument("--bands", type=int, default=0,
                    help="single workloads: this many bands instead of the workload's own (profiling cases)")
     p.add_argument("--tc-scratch-mb", type=int, default=8192,
-                   help="single workloads: digit-plane scratch of the tensor-core Gram and rotation (MB); "
-                        "0 keeps the library's default block sizes")
+                   help="single workloads and batch64: digit-plane scratch of the tensor-core Gram and rotation "
+                        "per context (MB); 0 keeps the library's default block sizes")
     a = p.parse_args()
     if a.precision is None:
         a.precision = "mixed" if a.workload in ("batch64", "served") else "fp64"
@@ -465,6 +465,9 @@ def run_batch(args):
     ent_a, ent_b, tuned = [], [], {}
     for inst in insts:
         ctx = api.Context(inst.system(), max_bands=inst.nbands, device=dev, precision=args.precision)
+        if args.tc_scratch_mb:
+            # the whole grid in one K block (every instance's planes fit in 8 GB)
+            ctx.set_option("tc_scratch_mb", args.tc_scratch_mb)
         psi_a = device_bands(ctx, inst.nbands, inst.seed)
         psi_b = torch.empty_like(psi_a)
         work = ctx.alloc_work(inst.nbands)
@@ -530,7 +533,7 @@ def run_batch(args):
                                "projectors, %s" % ("Bloch k" if not args.real else "Gamma"),
                    "instances": len(insts), "points_x_bands": units, "precision": args.precision,
                    "launch": "one CUDA graph launch per batch step" if graph else "eager streams",
-                   "parallelism": "replicas" if world > 1 else "single-gpu",
+                   "parallelism": "replicas" if world > 1 else "single-gpu", "tc_scratch_mb": args.tc_scratch_mb,
                    "l2": "inputs larger than L2 (%.1f GB of bands per step)" % (
                        2 * units * (8 if not args.real else 4) * (2 if args.precision == "fp64" else 1) / 1e9)},
         "rr_steps_per_s": rr,
