@@ -204,6 +204,44 @@ int pawfd_subspace_diag(pawfd_ctx* ctx, int nb, void* Hnm, void* Snm, double* ep
  * FP64 accuracy before the final rounding to the context's dtype. */
 int pawfd_rotate(pawfd_ctx* ctx, const void* psi, int nb, const void* C, void* psi_out);
 
+/* The band rotation onto the first nout columns of C: psi_out_m = sum_n psi_n C[n][m] for
+ * m < nout (C: [nb][nb] FP64 of the context's kind; psi_out: [nout][K]).  nout = nb is
+ * pawfd_rotate.  Returns PAWFD_EINVAL for nout outside 1..nb and as pawfd_rotate otherwise. */
+int pawfd_rotate_n(pawfd_ctx* ctx, const void* psi, int nb, const void* C, int nout, void* psi_out);
+
+/* Residuals of the generalized eigenproblem H psi = eps S psi (PAW section) and their
+ * preconditioned corrections, as used by the iterative eigensolver (SCF step 2 of the
+ * Kohn-Sham section; the paper names the Davidson method without its steps, so this is a
+ * reading):
+ *   R_n(r) = hpsi_n(r) - eps[n] spsi_n(r)               (the band's arithmetic),
+ *   rnorm[n] = sqrt(dV sum_r |R_n(r)|^2)                  (FP64 sums in a fixed order),
+ *   pr_n(r) = -R_n(r) / max(d(r) - eps[n], d0 / 10)      (weights in FP32),
+ * with d(r) = v(r) + d0 the diagonal of the kinetic + local operator and d0 =
+ * -1/2 c0 sum_c 1/h_c^2 the stencil's centre weight (a Jacobi preconditioner kept positive).
+ * hpsi, spsi, pr: [nb][K] of the context's dtype (pr distinct from both); eps, rnorm: device
+ * [nb] doubles.  Uses the subspace workspace of the context (no other call of the same
+ * context may run concurrently). */
+int pawfd_residual_precond(pawfd_ctx* ctx, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
+                           double* rnorm);
+
+/* One block-Davidson step (the reading of the iterative eigensolver named in the Kohn-Sham
+ * and parallelization sections; needs max_bands >= 2 nb):
+ *   1. HX[0 .. nb) = H psi, SX = S psi for psi = X[0 .. nb) (Ritz vectors with Ritz values
+ *      eps_in, e.g. from pawfd_rr_step or a previous step);
+ *   2. X[nb .. 2nb) = the preconditioned corrections of pawfd_residual_precond, rnorm their
+ *      residual norms;
+ *   3. HX[nb .. 2nb) = H of the corrections; P = the projections of all 2 nb columns of X;
+ *   4. Hnm, Snm = the Hermitian Gram matrices of X (as pawfd_gram_hs), scaled to a unit S
+ *      diagonal (which leaves the Ritz values unchanged and keeps the factorization well
+ *      conditioned when corrections are tiny), eps and C of their subspace diagonalization
+ *      (2 nb Ritz pairs, ascending; C for the unscaled X; Hnm and Snm overwritten);
+ *   5. psi_out = X C[:, 0 .. nb): the nb lowest Ritz vectors, with Ritz values eps[0 .. nb).
+ * X, HX: [2 nb][K]; SX, psi_out: [nb][K] (context dtype, pairwise distinct); P: [Ip][2 nb];
+ * Hnm, Snm, C: [2 nb][2 nb] FP64 of the context's kind; eps: [2 nb], rnorm: [nb] device
+ * doubles.  All memory owned by the caller.  Errors as the individual calls. */
+int pawfd_davidson_step(pawfd_ctx* ctx, void* X, int nb, const double* eps_in, void* HX, void* SX, void* P,
+                        void* Hnm, void* Snm, double* eps, void* C, double* rnorm, void* psi_out);
+
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
  * PAWFD_C128) of the same system as the mixed context whose rotated bands psi_lo (PAWFD_R32

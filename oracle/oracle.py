@@ -263,6 +263,53 @@ def residual_norms(Hpsi: np.ndarray, Spsi: np.ndarray, eps: np.ndarray, dV: floa
     return np.sqrt(dV * np.sum(np.abs(r) ** 2, axis=1))
 
 
+def davidson_weights(system, eps: np.ndarray) -> np.ndarray:
+    """Jacobi preconditioner weights w_n(r) = -1 / max(d(r) - eps_n, d0 / 10) of the block-Davidson
+    step (a reading: the paper names the Davidson eigensolver of the Kohn-Sham and
+    parallelization sections without its steps).  d(r) = v(r) + d0 is the diagonal of the
+    kinetic + local operator, d0 = -1/2 c0 sum_c 1/h_c^2 the stencil's centre weight.  The
+    reading fixes the weights' precision at FP32 (any positive weight gives a valid search
+    direction), so they are formed here in float32 arithmetic from the FP64 d and eps."""
+    c0 = fd6_coefficients()[0]
+    h = system.h
+    d0 = -0.5 * c0 * (1.0 / (h[0] * h[0]) + 1.0 / (h[1] * h[1]) + 1.0 / (h[2] * h[2]))
+    d = (np.asarray(system.vloc, np.float64).reshape(-1) + d0).astype(np.float32)
+    e = np.asarray(eps, np.float64).astype(np.float32)
+    floor = np.float32(0.1 * d0)
+    den = d[None, :] - e[:, None]
+    den = np.where(den > floor, den, floor)
+    return (np.float32(-1.0) / den).astype(np.float64)
+
+
+def davidson_step(system, psi: np.ndarray, eps_in: np.ndarray) -> dict:
+    """One block-Davidson step in the order of its reading:
+
+    1. H psi and S psi for the n input Ritz vectors psi (Ritz values eps_in);
+    2. residuals R_n = H psi_n - eps_n S psi_n and their norms sqrt(dV sum_r |R_n|^2);
+    3. corrections w_n R_n with the Jacobi weights of ``davidson_weights``;
+    4. Rayleigh-Ritz on the 2n columns X = [psi, corrections]: Gram matrices dV X^H H X and
+       dV X^H S X, the subspace diagonalization (2n Ritz pairs, ascending), and the n lowest
+       Ritz vectors X C[:, :n].
+    """
+    psi, nb = _psi_in(system, psi)
+    K = system.npoints
+    Hpsi, _ = apply_H(system, psi)
+    Spsi, _ = apply_S(system, psi)
+    eps_in = np.asarray(eps_in, np.float64)[:nb]
+    R = Hpsi.reshape(nb, K) - eps_in[:, None] * Spsi.reshape(nb, K)
+    rnorm = np.sqrt(system.dV * np.sum(np.abs(R) ** 2, axis=1))
+    corr = R * davidson_weights(system, eps_in)
+    X = np.concatenate([psi.reshape(nb, K), corr.astype(psi.dtype)]).reshape((2 * nb,) + psi.shape[1:])
+    HX, _ = apply_H(system, X)
+    SX, _ = apply_S(system, X)
+    Hnm = gram(X, HX, system.dV, 2 * nb)
+    Snm = gram(X, SX, system.dV, 2 * nb)
+    eps, C, sweeps = subspace_diag(Hnm, Snm)
+    psi_out = rotate(X, C).reshape(2 * nb, K)[:nb].reshape(psi.shape)
+    return {"X": X, "Hnm": Hnm, "Snm": Snm, "eps": eps, "C": C, "rnorm": rnorm, "psi_out": psi_out,
+            "sweeps": sweeps}
+
+
 def refine(system, psi_lo: np.ndarray) -> dict:
     """Final refinement of the mixed form, in the order of its reading (the paper is silent):
 

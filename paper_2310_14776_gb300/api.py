@@ -211,6 +211,66 @@ class Context:
                    ctypes.c_void_p(out.data_ptr()))
         return out
 
+    def rotate_n(self, psi, C, nout: int, out=None):
+        """psi_out_m = sum_n psi_n C[n][m] for m < nout (pawfd_rotate_n)."""
+        nb = self._bands(psi, "psi")
+        self._mat(C, nb, "C")
+        out = self.empty_bands(nout) if out is None else out
+        if self._bands(out, "out") != nout:
+            raise ValueError("out must hold nout bands")
+        self._call(self.lib.pawfd_rotate_n, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(C.data_ptr()),
+                   int(nout), ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def residual_precond(self, Hpsi, Spsi, eps, pr=None, rnorm=None):
+        """Residuals H psi - eps S psi: their norms and the preconditioned corrections
+        (pawfd_residual_precond).  Returns (pr, rnorm)."""
+        nb = self._bands(Hpsi, "Hpsi")
+        self._bands(Spsi, "Spsi")
+        if eps.numel() != nb or eps.dtype != torch.float64 or eps.device != self.device:
+            raise ValueError("eps must hold nb float64 values on the device")
+        pr = self.empty_bands(nb) if pr is None else pr
+        self._bands(pr, "pr")
+        rnorm = torch.empty(nb, dtype=torch.float64, device=self.device) if rnorm is None else rnorm
+        self._call(self.lib.pawfd_residual_precond, ctypes.c_void_p(Hpsi.data_ptr()), ctypes.c_void_p(Spsi.data_ptr()),
+                   nb, ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(pr.data_ptr()),
+                   ctypes.c_void_p(rnorm.data_ptr()))
+        return pr, rnorm
+
+    def alloc_davidson(self, nb: int) -> dict:
+        """Device arrays of one block-Davidson step for nb bands (needs max_bands >= 2 nb)."""
+        m = 2 * nb
+        return {"X": self.empty_bands(m), "HX": self.empty_bands(m), "SX": self.empty_bands(nb),
+                "P": torch.empty((max(self.Ip, 1), m), dtype=self.dtype, device=self.device),
+                "Hnm": torch.empty((m, m), dtype=self.mat_dtype, device=self.device),
+                "Snm": torch.empty((m, m), dtype=self.mat_dtype, device=self.device),
+                "C": torch.empty((m, m), dtype=self.mat_dtype, device=self.device),
+                "eps": torch.empty(m, dtype=torch.float64, device=self.device),
+                "rnorm": torch.empty(nb, dtype=torch.float64, device=self.device),
+                "psi_out": self.empty_bands(nb)}
+
+    def davidson_step(self, work: dict, nb: int, eps_in) -> dict:
+        """One block-Davidson step (pawfd_davidson_step) on work["X"][:nb] (Ritz vectors with
+        Ritz values eps_in); fills the arrays of ``work`` (see alloc_davidson) and returns it.
+        work["psi_out"] holds the nb lowest Ritz vectors, work["eps"][:nb] their Ritz values,
+        work["rnorm"] the residual norms of the input vectors."""
+        w = work
+        for key, count in (("X", 2 * nb), ("HX", 2 * nb), ("SX", nb), ("psi_out", nb)):
+            if self._bands(w[key], key) != count:
+                raise ValueError("%s must hold %d bands" % (key, count))
+        for key in ("Hnm", "Snm", "C"):
+            self._mat(w[key], 2 * nb, key)
+        if eps_in.numel() < nb or eps_in.dtype != torch.float64 or eps_in.device != self.device:
+            raise ValueError("eps_in must hold nb float64 values on the device")
+        if w["eps"].numel() != 2 * nb or w["rnorm"].numel() != nb:
+            raise ValueError("eps must hold 2 nb and rnorm nb float64 values")
+        if w["P"].numel() < self.Ip * 2 * nb or w["P"].dtype != self.dtype:
+            raise ValueError("P must hold [Ip][2 nb] values of the band dtype")
+        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        self._call(self.lib.pawfd_davidson_step, p(w["X"]), nb, p(eps_in), p(w["HX"]), p(w["SX"]), p(w["P"]),
+                   p(w["Hnm"]), p(w["Snm"]), p(w["eps"]), p(w["C"]), p(w["rnorm"]), p(w["psi_out"]))
+        return w
+
     def rayleigh_ritz(self, psi, work: Optional[dict] = None, check: bool = True, keep_matrices: bool = False) -> dict:
         """One eigensolver step: H psi, S psi, H_nm, S_nm, subspace diag, rotation.
 

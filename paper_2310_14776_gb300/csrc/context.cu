@@ -283,7 +283,7 @@ void free_ctx(pawfd_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
-                  c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_barrier, c->d_status, c->d_reduce,
+                  c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_dscale, c->d_barrier, c->d_status, c->d_reduce,
                   c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
                   c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df};
   for (void* p : ptrs)
@@ -367,6 +367,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     c->d_gram_part = dev_alloc<char>(c, c->gram_part_bytes, &rc);
     c->d_work = dev_alloc<char>(c, 7 * nb * nb * ss, &rc);
     c->d_evals = dev_alloc<double>(c, nb, &rc);
+    c->d_dscale = dev_alloc<double>(c, nb, &rc);
     c->d_barrier = dev_alloc<unsigned>(c, 4, &rc);
     c->d_status = dev_alloc<DeviceStatus>(c, 1, &rc);
     c->d_reduce = dev_alloc<double>(c, 8192, &rc);   // [0, 2048): partial sums; then Jacobi round flags

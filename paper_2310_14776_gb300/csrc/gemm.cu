@@ -199,7 +199,7 @@ __global__ void gram_reduce_kernel(const T* __restrict__ part, int nsplit, int n
 
 template <class T>
 __global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, const wide_t<T>* __restrict__ C,
-                                                    int nb, long long K, T* __restrict__ out) {
+                                                    int nb, int nout, long long K, T* __restrict__ out) {
   __shared__ T Cs[TK][TM];
   __shared__ T Ps[TK][TM];
   const long long r0 = (long long)blockIdx.x * TM;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, c
     for (int s = tid; s < TK * TM; s += NT) {
       const int j = s / TM, i = s - j * TM;
       const int n = n0 + j;
-      Cs[j][i] = (n < nb && m0 + i < nb) ? narrow<T>(C[(long long)n * nb + m0 + i]) : zero<T>();
+      Cs[j][i] = (n < nb && m0 + i < nout) ? narrow<T>(C[(long long)n * nb + m0 + i]) : zero<T>();
       Ps[j][i] = (n < nb && r0 + i < K) ? psi[(long long)n * K + r0 + i] : zero<T>();
     }
     __syncthreads();
@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(NT) rotate_kernel(const T* __restrict__ psi, c
     for (int l = 0; l < 4; ++l) {
       const int m = m0 + ty + 16 * i;
       const long long r = r0 + tx + 16 * l;
-      if (m < nb && r < K) out[(long long)m * K + r] = acc[i][l];
+      if (m < nout && r < K) out[(long long)m * K + r] = acc[i][l];
     }
 }
 
@@ -272,10 +272,10 @@ int gram_impl(pawfd_ctx* c, const T* A, const T* B, int nb, T* M, bool herm) {
 }
 
 template <class T>
-int rotate_impl(pawfd_ctx* c, const T* psi, int nb, const wide_t<T>* C, T* out) {
+int rotate_impl(pawfd_ctx* c, const T* psi, int nb, const wide_t<T>* C, int nout, T* out) {
   const long long K = (long long)c->K;
-  dim3 grid((unsigned)((K + TM - 1) / TM), (nb + TM - 1) / TM);
-  rotate_kernel<T><<<grid, NT, 0, c->stream>>>(psi, C, nb, K, out);
+  dim3 grid((unsigned)((K + TM - 1) / TM), (nout + TM - 1) / TM);
+  rotate_kernel<T><<<grid, NT, 0, c->stream>>>(psi, C, nb, nout, K, out);
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "rotate launch");
 }
@@ -333,11 +333,12 @@ int launch_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, cons
   return launch_overlap_correction(c, P, nb, Snm);
 }
 
-int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
-  if (c->use_tc) return launch_rotate_tc(c, psi, nb, C, out);
+int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout) {
+  if (nout < 0) nout = nb;
+  if (c->use_tc) return launch_rotate_tc(c, psi, nb, C, out, nout);
   return dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
-    return rotate_impl<T>(c, (const T*)psi, nb, (const wide_t<T>*)C, (T*)out);
+    return rotate_impl<T>(c, (const T*)psi, nb, (const wide_t<T>*)C, nout, (T*)out);
   });
 }
 

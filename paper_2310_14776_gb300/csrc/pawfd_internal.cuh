@@ -197,6 +197,7 @@ struct pawfd_ctx {
   int* d_flags = nullptr;                     // [16] subspace-solve path decisions (device-side gates)
   double* d_oa = nullptr;                     // Ogita-Aishima partial sums and eigenvalue estimates
   double* d_evals = nullptr;                  // [max_bands] unsorted eigenvalues
+  double* d_dscale = nullptr;                 // [max_bands] column scaling of a Davidson subspace
   unsigned* d_barrier = nullptr;              // grid-barrier counters
   pawfd::DeviceStatus* d_status = nullptr;
   pawfd::DeviceStatus* h_status = nullptr;    // pinned mirror
@@ -254,10 +255,13 @@ int launch_nonlocal_add2(pawfd_ctx* c, const void* P, int nb, const void* dmat1,
                          void* out2);
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
-int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
+int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout);
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
-int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out);
+int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout = -1);
+// residuals H psi - eps S psi, their norms and the preconditioned corrections (davidson.cu)
+int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
+                            double* rnorm);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
 int launch_overlap_correction(pawfd_ctx* c, const void* P, int nb, void* M);
 bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc);

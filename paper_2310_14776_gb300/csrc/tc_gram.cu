@@ -219,11 +219,12 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
   return check_cuda(c, cudaGetLastError(), "tensor-core gram pair launch");
 }
 
-// The rotation's first operand: A_ext[row][k] with k the contraction index.  Real:
-// A[m][n] = C[n][m].  Complex (C interleaved): rows m < nb give the real part of the output,
-// A[m][2n] = Re C[n][m], A[m][2n+1] = -Im C[n][m]; rows nb + m the imaginary part,
-// A[nb+m][2n] = Im C[n][m], A[nb+m][2n+1] = Re C[n][m].  Columns beyond the contraction are 0.
-__global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int cplx, double* __restrict__ A,
+// The rotation's first operand: A_ext[row][k] with k the contraction index, for the first
+// nout columns m of C ([nb][nb]).  Real: A[m][n] = C[n][m].  Complex (C interleaved): rows
+// m < nout give the real part of the output, A[m][2n] = Re C[n][m], A[m][2n+1] = -Im C[n][m];
+// rows nout + m the imaginary part, A[nout+m][2n] = Im C[n][m], A[nout+m][2n+1] = Re C[n][m].
+// Columns beyond the contraction and rows beyond the outputs are 0.
+__global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int nout, int cplx, double* __restrict__ A,
                                    long long Lc, int rows) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long long)rows * Lc) return;
@@ -231,20 +232,20 @@ __global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int cpl
   const long long k = e % Lc;
   double v = 0.0;
   if (!cplx) {
-    if (row < nb && k < nb) v = C[k * nb + row];
-  } else if (row < 2 * nb && k < 2 * nb) {
-    const int m = row % nb, n = (int)(k >> 1), re = (k & 1) == 0;
+    if (row < nout && k < nb) v = C[k * nb + row];
+  } else if (row < 2 * nout && k < 2 * nb) {
+    const int m = row % nout, n = (int)(k >> 1), re = (k & 1) == 0;
     const double cr = C[2 * ((long long)n * nb + m)], ci = C[2 * ((long long)n * nb + m) + 1];
-    v = row < nb ? (re ? cr : -ci) : (re ? ci : cr);
+    v = row < nout ? (re ? cr : -ci) : (re ? ci : cr);
   }
   A[e] = v;
 }
 
 template <class R, int S, int ORD>
-int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) {
+int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, R* out) {
   TcScratch& t = c->tc;
   const bool cplx = is_complex(c);
-  const int rowsA = cplx ? 2 * nb : nb;
+  const int rowsA = cplx ? 2 * nout : nout;
   const long long Lk = (long long)nb * (cplx ? 2 : 1);
   const long long Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
   const int nch = (int)(Lc / sg::KC);
@@ -252,7 +253,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
   const long long K = (long long)c->K;
   // operand A from C, then its digits
   rot_operand_kernel<<<(unsigned)((t.rot_rowsA_alloc * t.rot_Lc + 255) / 256), 256, 0, c->stream>>>(
-      C, nb, cplx, (double*)t.rotA, t.rot_Lc, t.rot_rowsA_alloc);
+      C, nb, nout, cplx, (double*)t.rotA, t.rot_Lc, t.rot_rowsA_alloc);
   cudaMemsetAsync(t.rotMaxA, 0x80, sizeof(int) * t.rot_rowsA_alloc, c->stream);
   {
     sg::slice_rg_kernel<double, S><<<(unsigned)(((rowsA + 7) / 8 * (long long)nch + 7) / 8), 256, 0, c->stream>>>(
@@ -296,7 +297,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
     a.part = nullptr;
     a.st = c->d_status;
     a.rotation = 1;
-    a.rot_nb = nb;
+    a.rot_nb = nout;
     a.rot_cplx = cplx;
     a.rot_fp32 = sizeof(R) == 4;
     a.rot_K = K;
@@ -318,10 +319,10 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, R* out) 
 
 }  // namespace
 
-int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out) {
+int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout) {
   if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core scratch not set up");
-  if (is_fp32(c)) return tc_rotate_impl<float, 4, 4>(c, (const float*)psi, nb, (const double*)C, (float*)out);
-  return tc_rotate_impl<double, 7, 6>(c, (const double*)psi, nb, (const double*)C, (double*)out);
+  if (is_fp32(c)) return tc_rotate_impl<float, 4, 4>(c, (const float*)psi, nb, (const double*)C, nout, (float*)out);
+  return tc_rotate_impl<double, 7, 6>(c, (const double*)psi, nb, (const double*)C, nout, (double*)out);
 }
 
 // TMA descriptor of a raw operand [rows][L] (FP64 or FP32, row stride L values): boxes of

@@ -527,3 +527,72 @@ def test_refine_of_ritz_vectors_is_a_fixed_point(complex_wf):
     n = 3
     r = res["Hpsi"][n] - first["eps"][n] * res["Spsi"][n]
     assert abs(res["resid"][n] - math.sqrt(s.dV) * np.linalg.norm(r)) <= 1e-12 * res["resid"][n]
+
+
+# ------------------------------------------------------------------------------------------
+# f-1: the block-Davidson step (the iterative eigensolver of the Kohn-Sham section; reading)
+# ------------------------------------------------------------------------------------------
+
+def _dense_ritz(s, H, S, X, nb):
+    Y = X.reshape(nb, s.npoints).T
+    return scipy.linalg.eigh(s.dV * Y.conj().T @ H @ Y, s.dV * Y.conj().T @ S @ Y, eigvals_only=True)
+
+
+@pytest.mark.parametrize("case", ["selfwrap", "bloch"])
+def test_davidson_step_against_dense_operators(case):
+    # the corrections are the weights times the dense residual, and the step's 2n Ritz values
+    # are those of the dense pencil projected on X = [psi, corrections]
+    s = small_system(**TINY[case])
+    H, S = dense_operators(s)
+    n, K = 4, s.npoints
+    rr = O.rayleigh_ritz(s, rand_psi(s, n, 7))
+    psi, eps = rr["psi_rot"], rr["eps"]
+    st = O.davidson_step(s, psi, eps)
+    Y = psi.reshape(n, K)
+    R = (H @ Y.T).T - eps[:, None] * (S @ Y.T).T
+    w = O.davidson_weights(s, eps)
+    assert np.all(w < 0)
+    corr = st["X"].reshape(2 * n, K)[n:]
+    assert np.allclose(corr, w * R, rtol=0, atol=1e-11 * np.max(np.abs(w * R)))
+    assert np.allclose(st["rnorm"], np.sqrt(s.dV * np.sum(np.abs(R) ** 2, axis=1)), rtol=1e-10, atol=0)
+    ritz = _dense_ritz(s, H, S, st["X"], 2 * n)
+    assert np.allclose(st["eps"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
+    # the output vectors are the n lowest Ritz vectors: S-orthonormal, with those Ritz values
+    Z = st["psi_out"].reshape(n, K).T
+    assert np.allclose(s.dV * Z.conj().T @ S @ Z, np.eye(n), rtol=0, atol=1e-10)
+    assert np.allclose(s.dV * Z.conj().T @ H @ Z, np.diag(st["eps"][:n]), rtol=0, atol=1e-10 * np.max(np.abs(ritz)))
+
+
+@pytest.mark.parametrize("case", ["selfwrap", "bloch"])
+def test_davidson_iteration_converges_from_above(case):
+    # Ritz values never fall below the exact eigenvalues (interlacing), never rise from one
+    # step to the next (the new subspace contains the old vectors), and approach the exact
+    # lowest eigenvalues while the residuals shrink
+    s = small_system(**TINY[case])
+    H, S = dense_operators(s)
+    exact = scipy.linalg.eigh(H, S, eigvals_only=True)
+    n = 4
+    rr = O.rayleigh_ritz(s, rand_psi(s, n, 5))
+    psi, eps = rr["psi_rot"], rr["eps"]
+    err0 = None
+    for it in range(40):
+        st = O.davidson_step(s, psi, eps)
+        new = st["eps"][:n]
+        assert np.all(new >= exact[:n] - 1e-10)
+        assert np.all(new <= eps + 1e-10)
+        if it == 0:
+            err0, r0 = np.sum(new - exact[:n]), st["rnorm"].max()
+        psi, eps = st["psi_out"], new
+    assert np.sum(eps - exact[:n]) < err0 / 50
+    assert st["rnorm"].max() < r0 / 15
+
+
+def test_davidson_fixed_point_is_exact_eigenvectors():
+    s = small_system(**TINY["bloch"])
+    H, S = dense_operators(s)
+    lam, V = scipy.linalg.eigh(H, S)
+    n = 3
+    psi = (V[:, :n].T / math.sqrt(s.dV)).reshape((n,) + tuple(s.n[::-1]))
+    st = O.davidson_step(s, psi, lam[:n])
+    assert np.max(st["rnorm"]) < 1e-10 * max(1.0, np.max(np.abs(lam[:n])))
+    assert np.allclose(st["eps"][:n], lam[:n], rtol=0, atol=1e-10)
