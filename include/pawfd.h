@@ -242,6 +242,21 @@ int pawfd_residual_precond(pawfd_ctx* ctx, const void* hpsi, const void* spsi, i
 int pawfd_davidson_step(pawfd_ctx* ctx, void* X, int nb, const double* eps_in, void* HX, void* SX, void* P,
                         void* Hnm, void* Snm, double* eps, void* C, double* rnorm, void* psi_out);
 
+/* The reductions that follow the eigensolver in the SCF loop (the density of step 4 of the
+ * Kohn-Sham section; the PAW section's pseudo density and atomic density matrices), for one
+ * spin channel and occupation numbers f (device [nb] doubles):
+ *   rho[r] = sum_n f[n] |psi_n(r)|^2   (device [K] doubles; the pseudo density without
+ *            compensation charges).  Real FP64 bands are summed in double-float FP32 pairs
+ *            (about 2^-46 relative per term), complex FP64 bands in FP64, FP32 bands in FP32
+ *            runs of 16 bands added in FP64.
+ *   D[dmat_off[a] + i I_a + i'] = sum_n f[n] conj(P[row_a + i][n]) P[row_a + i'][n]
+ *            (Eq. (atomicdensitymatrix): <psi_n|p_i^a><p_i'^a|psi_n> with P the projections
+ *            of pawfd_project, row_a the atom's first projector row); FP64 (complex FP64 for
+ *            the complex dtypes) in the packed per-atom layout of dH and dS.
+ * Returns PAWFD_EINVAL for nb outside 1..max_bands or null arrays. */
+int pawfd_density(pawfd_ctx* ctx, const void* psi, int nb, const double* f, double* rho);
+int pawfd_atomic_density(pawfd_ctx* ctx, const void* P, int nb, const double* f, void* D);
+
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
  * PAWFD_C128) of the same system as the mixed context whose rotated bands psi_lo (PAWFD_R32

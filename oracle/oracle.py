@@ -263,6 +263,35 @@ def residual_norms(Hpsi: np.ndarray, Spsi: np.ndarray, eps: np.ndarray, dV: floa
     return np.sqrt(dV * np.sum(np.abs(r) ** 2, axis=1))
 
 
+def density(system, psi: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """The pseudo density rho(r) = sum_n f_n |psi_n(r)|^2 of one spin channel (the PAW
+    section's n~ without compensation charges; the density of step 4 of the Kohn-Sham
+    section), [N3][N2][N1] float64."""
+    psi, nb = _psi_in(system, psi)
+    f = np.asarray(f, np.float64)
+    rho = np.zeros(system.npoints)
+    for n in range(nb):
+        rho += f[n] * np.abs(psi.reshape(nb, -1)[n]) ** 2
+    return rho.reshape(psi.shape[1:])
+
+
+def atomic_density(system, P: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Eq. (atomicdensitymatrix): D^a_ii' = sum_n f_n <psi_n|p_i^a> <p_i'^a|psi_n>
+    = sum_n f_n conj(P[row_a + i][n]) P[row_a + i'][n] (P from ``project``), packed per atom
+    like dH and dS (offsets system.dmat_off)."""
+    f = np.asarray(f, np.float64)
+    cplx = np.iscomplexobj(P)
+    D = np.zeros(int(system.dmat_off[-1]) if system.natoms else 0, np.complex128 if cplx else np.float64)
+    row = 0
+    for a in range(system.natoms):
+        I = int(system.nproj[a])
+        Pa = P[row:row + I]
+        Da = (np.conj(Pa) * f[None, :]) @ Pa.T
+        D[int(system.dmat_off[a]):int(system.dmat_off[a]) + I * I] = Da.reshape(-1)
+        row += I
+    return D
+
+
 def davidson_weights(system, eps: np.ndarray) -> np.ndarray:
     """Jacobi preconditioner weights w_n(r) = -1 / max(d(r) - eps_n, d0 / 10) of the block-Davidson
     step (a reading: the paper names the Davidson eigensolver of the Kohn-Sham and

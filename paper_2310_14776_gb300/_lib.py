@@ -55,6 +55,8 @@ SIGNATURES = {
     "pawfd_rotate_n": ([VP, VP, I, VP, I, VP], I),
     "pawfd_residual_precond": ([VP, VP, VP, I, VP, VP, VP], I),
     "pawfd_davidson_step": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
+    "pawfd_density": ([VP, VP, I, VP, VP], I),
+    "pawfd_atomic_density": ([VP, VP, I, VP, VP], I),
     "pawfd_batch_create": ([ctypes.POINTER(VP), ctypes.POINTER(RrJob), I, I], I),
     "pawfd_batch_launch": ([VP, VP], I),
     "pawfd_batch_is_graph": ([VP], I),

@@ -46,6 +46,7 @@ class Context:
         else:
             self.dtype = torch.complex64 if self.complex else torch.float32
         self.max_bands = int(max_bands)
+        self._dmat_total = int(np.asarray(system.dmat_off)[-1]) if int(system.natoms) > 0 else 0
         h = [system.cell[c] / self.n[c] for c in range(3)]
         self.dV = h[0] * h[1] * h[2]
         keep = dict(
@@ -236,6 +237,29 @@ class Context:
                    nb, ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(pr.data_ptr()),
                    ctypes.c_void_p(rnorm.data_ptr()))
         return pr, rnorm
+
+    def density(self, psi, f, rho=None):
+        """rho(r) = sum_n f_n |psi_n(r)|^2 (pawfd_density); f: device float64 [nb]."""
+        nb = self._bands(psi, "psi")
+        if f.numel() != nb or f.dtype != torch.float64 or f.device != self.device:
+            raise ValueError("f must hold nb float64 values on the device")
+        rho = torch.empty(self.K, dtype=torch.float64, device=self.device) if rho is None else rho
+        if rho.numel() != self.K or rho.dtype != torch.float64 or not rho.is_contiguous():
+            raise ValueError("rho must be a contiguous float64 tensor of K values")
+        self._call(self.lib.pawfd_density, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(f.data_ptr()),
+                   ctypes.c_void_p(rho.data_ptr()))
+        return rho
+
+    def atomic_density(self, P, f, D=None):
+        """D^a = sum_n f_n conj(P_an) P_an^T per atom, packed like dH / dS (pawfd_atomic_density)."""
+        nb = f.numel()
+        if P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous():
+            raise ValueError("P must be a contiguous [Ip, nb] tensor of the band dtype")
+        total = int(self._dmat_total)
+        D = torch.empty(max(total, 1), dtype=self.mat_dtype, device=self.device) if D is None else D
+        self._call(self.lib.pawfd_atomic_density, ctypes.c_void_p(P.data_ptr()), nb, ctypes.c_void_p(f.data_ptr()),
+                   ctypes.c_void_p(D.data_ptr()))
+        return D[:total]
 
     def alloc_davidson(self, nb: int) -> dict:
         """Device arrays of one block-Davidson step for nb bands (needs max_bands >= 2 nb)."""

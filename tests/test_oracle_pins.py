@@ -596,3 +596,45 @@ def test_davidson_fixed_point_is_exact_eigenvectors():
     st = O.davidson_step(s, psi, lam[:n])
     assert np.max(st["rnorm"]) < 1e-10 * max(1.0, np.max(np.abs(lam[:n])))
     assert np.allclose(st["eps"][:n], lam[:n], rtol=0, atol=1e-10)
+
+
+# ------------------------------------------------------------------------------------------
+# f-2: pseudo density and atomic density matrices
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("complex_wf", [False, True])
+def test_density_paw_charge_and_energy_identities(complex_wf):
+    # for S-orthonormal bands, dV sum_r rho + sum_a Tr(D^a dS^a) = sum_n f_n (the PAW norm of
+    # every band is 1), and sum_n f_n <psi_n|H|psi_n> = sum_n f_n dV <psi_n|(T + v) psi_n>
+    # + sum_a Tr(D^a dH^a) (the expectation-value formula of the PAW section)
+    s = small_system(complex_wf=complex_wf, k=(0.3, -0.2, 0.1) if complex_wf else (0.0, 0.0, 0.0))
+    nb = 6
+    rr = O.rayleigh_ritz(s, rand_psi(s, nb, 31))
+    psi = rr["psi_rot"]
+    f = np.linspace(2.0, 0.25, nb)
+    rho = O.density(s, psi, f)
+    P = O.project(s, psi)
+    D = O.atomic_density(s, P, f)
+    blocksD = atom_blocks(s, D)
+    charge = s.dV * np.sum(rho) + sum(np.trace(Da @ dS) for Da, dS in zip(blocksD, atom_blocks(s, s.dS)))
+    assert abs(charge - np.sum(f)) < 1e-12 * np.sum(f)
+    T = O.kinetic_local(s, psi).reshape(nb, -1)
+    local = sum(f[n] * s.dV * np.vdot(psi.reshape(nb, -1)[n], T[n]) for n in range(nb))
+    nonlocal_ = sum(np.trace(Da @ dH) for Da, dH in zip(blocksD, atom_blocks(s, s.dH)))
+    band = np.sum(f * rr["eps"])
+    assert abs(local + nonlocal_ - band) < 1e-11 * max(1.0, abs(band))
+    for Da in blocksD:
+        assert np.allclose(Da, Da.conj().T, rtol=0, atol=1e-15 * max(1.0, np.max(np.abs(Da))))
+        assert np.min(np.linalg.eigvalsh(Da)) > -1e-13 * max(1.0, np.max(np.abs(Da)))
+
+
+def test_density_of_plane_waves_is_uniform():
+    s = free_system((10, 9, 8), (5.0, 4.6, 4.2), complex_wf=True)
+    x, y, z = grid_coords(s)
+    V = s.cell[0] * s.cell[1] * s.cell[2]
+    qs = [(0, 0, 0), (1, 0, 0), (0, -1, 2), (3, 2, -1)]
+    psi = np.array([np.exp(2j * math.pi * (q[0] * x / s.cell[0] + q[1] * y / s.cell[1] + q[2] * z / s.cell[2]))
+                    / math.sqrt(V) for q in qs])
+    f = np.array([2.0, 2.0, 1.0, 0.5])
+    rho = O.density(s, psi, f)
+    assert np.allclose(rho, np.sum(f) / V, rtol=1e-14, atol=0)
