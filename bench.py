@@ -74,7 +74,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="pawfd", choices=["pawfd", "reference"])
-    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS) + ["batch64", "served", "davidson"])
+    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS) + ["batch64", "served", "davidson", "density"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -706,6 +706,83 @@ def run_davidson(args):
 
 
 # ------------------------------------------------------------------------------------------
+# Density reductions after the eigensolver
+# ------------------------------------------------------------------------------------------
+def run_density(args):
+    """The pseudo density (pawfd_density) and the atomic density matrices
+    (pawfd_atomic_density) of the 96^3 x 256-band system's bands, occupations 2."""
+    import torch
+
+    from paper_2310_14776_gb300 import api
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS["gamma-96c-256b"]
+    system = w.system()
+    nb, K = (args.bands or w.nbands), system.npoints
+    ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
+    psi = device_bands(ctx, nb, w.seed)
+    f = torch.full((nb,), 2.0, dtype=torch.float64, device=dev)
+    rho = torch.empty(K, dtype=torch.float64, device=dev)
+    P = ctx.project(psi)
+    D = ctx.atomic_density(P, f)
+    esize = psi.element_size()
+    for _ in range(args.warmup):
+        ctx.density(psi, f, rho=rho)
+        ctx.atomic_density(P, f, D=D)
+    ctx.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    l0 = ctx.launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    evs[0].record()
+    for i in range(args.steps):
+        ctx.density(psi, f, rho=rho)
+        evs[2 * i + 1].record()
+        ctx.atomic_density(P, f, D=D)
+        evs[2 * i + 2].record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ctx.sync()
+    launches = ctx.launch_count() - l0
+    elapsed = evs[0].elapsed_time(evs[-1]) * 1e-3
+    dens_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(args.steps)]
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    bytes_per_launch = nb * K * esize + K * 8
+    achieved = bytes_per_launch / (np.mean(dens_ms) * 1e-3) / 1e9
+    cb = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        nb_s = 64
+        psi_s = w.psi(system, nb=nb_s)
+        t = time.perf_counter()
+        O.density(system, psi_s, np.full(nb_s, 2.0))
+        ts = time.perf_counter() - t
+        cb = {"value": K * nb_s / ts / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "seconds": ts,
+              "sample": "the oracle pseudo density of %d bands of the gamma-96c-256b system (numpy, one core)" % nb_s}
+    result = {
+        "metric": METRIC, "value_definition": "grid points x bands reduced into the pseudo density (plus the atomic "
+                                              "density matrices) per second / 1e9",
+        "value": K * nb * args.steps / elapsed / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {8: "f64", 4: "f32"}[esize],
+        "data": "synthetic (seeded; bands from a seeded torch generator on the device)",
+        "config": {"workload": "density: pseudo density + atomic density matrices of gamma-96c-256b", "grid":
+                   list(system.n), "bands": nb, "precision": args.precision, "parallelism": "single-gpu",
+                   "l2": "inputs larger than L2 (%.2f GB of bands per step)" % (nb * K * esize / 1e9)},
+        "latency_ms": {"p50": float(np.percentile(dens_ms, 50)), "p99": float(np.percentile(dens_ms, 99))},
+        "roofline": {"stage": "pawfd_density", "kernel": "density_kernel", "bound": "hbm", "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "bytes_per_launch": bytes_per_launch, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "gpu_launches": launches, "clocks": clk, "cpu_baseline": cb,
+    }
+    print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # CPU oracle baseline / reference arm
 # ------------------------------------------------------------------------------------------
 def oracle_step_time(system, psi):
@@ -785,6 +862,8 @@ def main():
         run_served(args)
     elif args.workload == "davidson":
         run_davidson(args)
+    elif args.workload == "density":
+        run_density(args)
     else:
         run_gpu(args)
 

@@ -19,7 +19,34 @@ using namespace pawfd;
 namespace {
 
 constexpr int DT = 256;     // threads per density block
-constexpr int DV = 2;       // grid points per thread
+constexpr int DV = 4;       // consecutive grid points per thread
+
+// The DV values of one band at r0 (16-byte vector loads when the whole group is inside the
+// grid and aligned; zero past the end).
+__device__ __forceinline__ void load_group(const double* __restrict__ row, bool vec, long long left,
+                                           double (&x)[DV]) {
+  if (vec) {
+    const double2 a = __ldg((const double2*)row), b = __ldg((const double2*)row + 1);
+    x[0] = a.x; x[1] = a.y; x[2] = b.x; x[3] = b.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < DV; ++v) x[v] = v < left ? row[v] : 0.0;
+  }
+}
+__device__ __forceinline__ void load_group(const float* __restrict__ row, bool vec, long long left, float (&x)[DV]) {
+  if (vec) {
+    const float4 a = __ldg((const float4*)row);
+    x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+  } else {
+#pragma unroll
+    for (int v = 0; v < DV; ++v) x[v] = v < left ? row[v] : 0.0f;
+  }
+}
+template <class R>
+__device__ __forceinline__ void load_group(const cplx<R>* __restrict__ row, bool, long long left, cplx<R> (&x)[DV]) {
+#pragma unroll
+  for (int v = 0; v < DV; ++v) x[v] = v < left ? row[v] : zero<cplx<R>>();
+}
 
 // f_n |x|^2 summed over the bands.  Real FP64 bands: in double-float FP32 pairs (x split into
 // hi + lo with integer operations, x^2 and f_n x^2 as error-free products, about 2^-46 relative
@@ -28,59 +55,59 @@ constexpr int DV = 2;       // grid points per thread
 // FP64.  FP32 bands: products in FP32 within runs of 16 bands, then FP64 (|x|^2 of an FP32
 // value is exact to 2^-24; the sum over bands is the part that needs the wider type).
 template <class T>
-__global__ void __launch_bounds__(DT) density_kernel(const T* __restrict__ psi, int nb, long long K,
+__global__ void __launch_bounds__(DT) density_kernel(const T* __restrict__ psi, int nb, long long K, bool aligned,
                                                      const double* __restrict__ f, double* __restrict__ rho) {
   using R = real_t<T>;
   const long long r0 = ((long long)blockIdx.x * DT + threadIdx.x) * DV;
   if (r0 >= K) return;
+  const long long left = K - r0;
+  const bool vec = aligned && left >= DV;
   if constexpr (std::is_same<T, double>::value) {
     dfa::DF acc[DV];
 #pragma unroll
     for (int v = 0; v < DV; ++v) acc[v] = {0.0f, 0.0f};
-    const bool full2 = r0 + DV <= K;
     for (int n = 0; n < nb; ++n) {
       const dfa::DF fn = dfa::split64(__ldg(f + n));
-      const double* row = psi + (long long)n * K + r0;
+      double x[DV];
+      load_group(psi + (long long)n * K + r0, vec, left, x);
 #pragma unroll
-      for (int v = 0; v < DV; ++v)
-        if (full2 || r0 + v < K) {
-          const dfa::DF x = dfa::split64(row[v]);
-          dfa::DF x2 = {0.0f, 0.0f};
-          dfa::fma_acc(x2, x, x);
-          dfa::fma_acc(acc[v], fn, x2);
-        }
+      for (int v = 0; v < DV; ++v) {
+        const dfa::DF xs = dfa::split64(x[v]);
+        dfa::DF x2 = {0.0f, 0.0f};
+        dfa::fma_acc(x2, xs, xs);
+        dfa::fma_acc(acc[v], fn, x2);
+      }
     }
 #pragma unroll
     for (int v = 0; v < DV; ++v)
-      if (full2 || r0 + v < K) rho[r0 + v] = dfa::to_double(acc[v]);
+      if (v < left) rho[r0 + v] = dfa::to_double(acc[v]);
   } else {
-  double acc[DV];
+    double acc[DV];
 #pragma unroll
-  for (int v = 0; v < DV; ++v) acc[v] = 0.0;
-  const bool full = r0 + DV <= K;
-  for (int n0 = 0; n0 < nb; n0 += 16) {
-    const int n1 = min(nb, n0 + 16);
-    R part[DV];
+    for (int v = 0; v < DV; ++v) acc[v] = 0.0;
+    for (int n0 = 0; n0 < nb; n0 += 16) {
+      const int n1 = min(nb, n0 + 16);
+      R part[DV];
 #pragma unroll
-    for (int v = 0; v < DV; ++v) part[v] = (R)0;
-    for (int n = n0; n < n1; ++n) {
-      const R fn = (R)__ldg(f + n);
-      const T* row = psi + (long long)n * K + r0;
+      for (int v = 0; v < DV; ++v) part[v] = (R)0;
+      for (int n = n0; n < n1; ++n) {
+        const R fn = (R)__ldg(f + n);
+        T x[DV];
+        load_group(psi + (long long)n * K + r0, vec, left, x);
 #pragma unroll
-      for (int v = 0; v < DV; ++v)
-        if (full || r0 + v < K) {
-          if constexpr (sizeof(R) == 8) acc[v] = fma((double)fn, (double)absx2(row[v]), acc[v]);
-          else part[v] = fmaf(fn, absx2(row[v]), part[v]);
+        for (int v = 0; v < DV; ++v) {
+          if constexpr (sizeof(R) == 8) acc[v] = fma((double)fn, (double)absx2(x[v]), acc[v]);
+          else part[v] = fmaf(fn, absx2(x[v]), part[v]);
         }
-    }
-    if constexpr (sizeof(R) == 4) {
+      }
+      if constexpr (sizeof(R) == 4) {
 #pragma unroll
-      for (int v = 0; v < DV; ++v) acc[v] += (double)part[v];
+        for (int v = 0; v < DV; ++v) acc[v] += (double)part[v];
+      }
     }
-  }
 #pragma unroll
-  for (int v = 0; v < DV; ++v)
-    if (full || r0 + v < K) rho[r0 + v] = acc[v];
+    for (int v = 0; v < DV; ++v)
+      if (v < left) rho[r0 + v] = acc[v];
   }
 }
 
@@ -115,9 +142,11 @@ extern "C" int pawfd_density(pawfd_ctx* c, const void* psi, int nb, const double
   if (!psi || !f || !rho) return fail(c, PAWFD_EINVAL, "null array");
   const long long K = (long long)c->K;
   const unsigned blocks = (unsigned)((K + (long long)DT * DV - 1) / ((long long)DT * DV));
+  // 16-byte loads of the real types: band rows and the array start on 16-byte boundaries
+  const bool aligned = (K * (long long)band_size(c)) % 16 == 0 && ((uintptr_t)psi & 15) == 0;
   int rc = dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
-    density_kernel<T><<<blocks, DT, 0, c->stream>>>((const T*)psi, nb, K, f, rho);
+    density_kernel<T><<<blocks, DT, 0, c->stream>>>((const T*)psi, nb, K, aligned, f, rho);
     return 0;
   });
   if (rc != PAWFD_OK) return rc;
