@@ -46,13 +46,42 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
 _GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "9fbba2e9424e4e6498471fb2c73f3e6161a9c0a4",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "9ce5f1aaf97c12cdb49e6a798566e2917cfc2712",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "67b8b680e74ff194fe1827d5b5f1c9146aa063b9",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
                  "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
     ("gram_HS", "fp64", False): {"nb": 256, "per_point": 22258.9, "sources": _GRAM_SOURCES},
     ("gram_HS", "mixed", False): {"nb": 256, "per_point": 12194.6, "sources": _GRAM_SOURCES},
 }
+
+
+# Measured DRAM traffic per launch of the Gram MMA kernel (the mean of the two launches of one
+# pawfd_gram_hs call, ncu at 64^3 x 256 bands, profiles/dram_gram_hs_64c_256b.md), per grid
+# point: FP64 (2026.6 + 0.5 + 940.5 + 0.8) / 2 MB, mixed (1142.2 + 0.6 + 537.6 + 0.5) / 2 MB.
+KERNEL_TRAFFIC = {
+    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1484.2e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 840.45e6 / 262144, "sources": _GRAM_SOURCES},
+}
+
+
+def kernel_traffic(kernel, precision, cplx, K, nb):
+    """DRAM bytes of one launch of the kernel, scaled from the measured small case, or None."""
+    import hashlib
+    t = KERNEL_TRAFFIC.get((kernel, precision, cplx))
+    if t is None or t["nb"] != nb:
+        return None
+    for path, sha in t["sources"].items():
+        with open(os.path.join(ROOT, path), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != sha:
+                return None
+    return t["per_point"] * K
+
+
+def sg_tiles_area(nb):
+    """Output entries the Hermitian Gram kernel computes: 128 x 96 tiles holding an element
+    with row <= column."""
+    tr, tcn = (nb + 127) // 128, (nb + 95) // 96
+    return sum(max(0, tcn - (128 * r) // 96) for r in range(tr)) * 128 * 96
 
 
 def stage_traffic(stage, precision, cplx, K, nb, natoms):
@@ -233,6 +262,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     launches0 = ctx.launch_count()
+    ctx.kernel_timing(True)       # CUDA events around every Gram MMA kernel launch from here
     marks = [[ev() for _ in range(5)] for _ in range(args.steps)]
     t0, t1 = ev(), ev()
     t0.record(stream)
@@ -244,6 +274,7 @@ def run_gpu(args):
         dist.barrier()
     clk = clocks.stop()
     ctx.sync()
+    mma_ms, mma_launches = ctx.kernel_timing(False)
     launches = ctx.launch_count() - launches0
     elapsed = t0.elapsed_time(t1) * 1e-3
     if world > 1:
@@ -281,6 +312,23 @@ def run_gpu(args):
                  "rotate": "slice_t_kernel + sliced_gram_kernel (digit-product rotation)"}
     scale = 1e12 if unit.endswith("FLOP/s") or unit == "FP64 instr/s" else 1e9
     roof_unit = {"BF16 FLOP/s": "TFLOP/s", "FP64 instr/s": "Tinstr/s", "B/s": "GB/s"}[unit]
+    # the dominant kernel: the Gram MMA kernel (two launches per pawfd_gram_hs call), timed by
+    # CUDA events around each launch on the context's stream; algorithmic work per launch = the
+    # digit products of one Hermitian Gram's upper triangle
+    mma_avg_ms = mma_ms / mma_launches if mma_launches and mma_launches > 0 else None
+    gram_launch_flops = 2.0 * products * cfac * nb * (nb + 1) / 2 * K
+    kernel_roof = None
+    if mma_avg_ms:
+        ach = gram_launch_flops / (mma_avg_ms * 1e-3)
+        kernel_roof = {"kernel": "sliced_gram_kernel (Gram mode; %d launches timed)" % mma_launches,
+                       "bound": "tensor", "achieved": ach / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                       "frac": ach / (bf16 * 1e12), "avg_launch_ms": mma_avg_ms,
+                       "traffic": kernel_traffic("gram_mma", args.precision, cplx, K, nb),
+                       "traffic_unit": "DRAM bytes per launch (ncu at 64^3 x 256 bands, mean of the pair's two "
+                                       "launches, scaled by grid points)",
+                       "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                       "work": "useful (Hermitian upper-triangle) BF16 digit products; the kernel executes "
+                               "%.2fx that in 128 x 96 tiles" % (sg_tiles_area(nb) / (nb * (nb + 1) / 2))}
 
     result = {
         "metric": METRIC, "value_definition": VALUE_DEF,
@@ -298,13 +346,15 @@ def run_gpu(args):
         "stages_ms": stages,
         "apply_HS_gptband_s": nb * K / (stages["apply_HS"] * 1e-3) / 1e9,
         "eig_drift_ha": drift,
-        "roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
-                     "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,
-                     "traffic": stage_traffic(dom, args.precision, cplx, K, nb, system.natoms),
-                     "traffic_unit": "DRAM bytes per stage call (ncu at 64^3 x 256 bands, scaled by grid points)",
-                     "peak_source": {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                                     "hbm": "MEASURED_PEAKS.json hbm_gbs",
-                                     "alu": "nominal GB300 FP64 rate 1.25 TFLOP/s / 2 (FMA)"}[bound]},
+        "roofline": kernel_roof,
+        "stage_roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
+                           "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,
+                           "traffic": stage_traffic(dom, args.precision, cplx, K, nb, system.natoms),
+                           "traffic_unit": "DRAM bytes per stage call (ncu at 64^3 x 256 bands, scaled by grid "
+                                           "points)",
+                           "peak_source": {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst)",
+                                           "hbm": "MEASURED_PEAKS.json hbm_gbs",
+                                           "alu": "nominal GB300 FP64 rate 1.25 TFLOP/s / 2 (FMA)"}[bound]},
         "gpu_launches": int(launches),
         "clocks": clk,
     }

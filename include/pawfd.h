@@ -103,6 +103,13 @@ int pawfd_nproj_total(const pawfd_ctx* ctx);
 /* number of CUDA kernels this context has launched so far (host-side counter) */
 long long pawfd_launch_count(const pawfd_ctx* ctx);
 
+/* CUDA-event timing of the tensor-core Gram MMA kernel launches of pawfd_gram_hs (each of its
+ * two MMA kernels per K block is bracketed by a pair of events on the context's stream, up to
+ * 256 launches between two calls).  Returns, through total_ms and launches, the summed device
+ * time and the number of timed launches since the previous call (launches = -1 if more than
+ * 256 were made), waiting for the last one; then turns timing on (enable = 1) or off. */
+int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long* launches);
+
 /* Select among equivalent implementations (for tests and measurements):
  *   "tensor_cores"    1 (default): Gram matrices and rotations on the tensor cores with exact
  *                     digit slices; 0: FMA kernels on the CUDA cores (FP64 products for the FP64

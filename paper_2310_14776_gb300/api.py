@@ -238,6 +238,14 @@ class Context:
                    ctypes.c_void_p(rnorm.data_ptr()))
         return pr, rnorm
 
+    def kernel_timing(self, enable: bool):
+        """Device time of the Gram MMA kernel launches timed since the previous call (ms, count),
+        then timing on or off (pawfd_kernel_timing)."""
+        ms = ctypes.c_double(0.0)
+        n = ctypes.c_longlong(0)
+        self._call(self.lib.pawfd_kernel_timing, int(bool(enable)), ctypes.byref(ms), ctypes.byref(n))
+        return ms.value, n.value
+
     def density(self, psi, f, rho=None):
         """rho(r) = sum_n f_n |psi_n(r)|^2 (pawfd_density); f: device float64 [nb]."""
         nb = self._bands(psi, "psi")

@@ -288,6 +288,10 @@ void free_ctx(pawfd_ctx* c) {
                   c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (int i = 0; i < KernelTimer::CAP; ++i) {
+    if (c->ktimer.start[i]) cudaEventDestroy(c->ktimer.start[i]);
+    if (c->ktimer.stop[i]) cudaEventDestroy(c->ktimer.stop[i]);
+  }
   if (c->h_status) cudaFreeHost(c->h_status);
   free_tc(c);
   delete c;
@@ -474,6 +478,49 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     return PAWFD_OK;
   }
   return fail(c, PAWFD_EINVAL, "unknown option or value");
+}
+
+namespace pawfd {
+void ktimer_begin(pawfd_ctx* c) {
+  KernelTimer& t = c->ktimer;
+  if (!t.on) return;
+  if (t.used >= KernelTimer::CAP) {
+    t.overflow = true;
+    return;
+  }
+  if (!t.start[t.used]) {
+    cudaEventCreate(&t.start[t.used]);
+    cudaEventCreate(&t.stop[t.used]);
+  }
+  cudaEventRecord(t.start[t.used], c->stream);
+}
+void ktimer_end(pawfd_ctx* c) {
+  KernelTimer& t = c->ktimer;
+  if (!t.on || t.used >= KernelTimer::CAP) return;
+  cudaEventRecord(t.stop[t.used], c->stream);
+  ++t.used;
+}
+}  // namespace pawfd
+
+extern "C" int pawfd_kernel_timing(pawfd_ctx* c, int enable, double* total_ms, long long* launches) {
+  if (!c) return PAWFD_EINVAL;
+  KernelTimer& t = c->ktimer;
+  double ms = 0.0;
+  int rc = PAWFD_OK;
+  if (t.used > 0) {
+    rc = check_cuda(c, cudaEventSynchronize(t.stop[t.used - 1]), "timing event");
+    for (int i = 0; i < t.used && rc == PAWFD_OK; ++i) {
+      float e = 0.0f;
+      rc = check_cuda(c, cudaEventElapsedTime(&e, t.start[i], t.stop[i]), "timing event");
+      ms += e;
+    }
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = t.overflow ? -1 : t.used;
+  t.used = 0;
+  t.overflow = false;
+  t.on = enable != 0;
+  return rc;
 }
 
 extern "C" int pawfd_sync(pawfd_ctx* c) {

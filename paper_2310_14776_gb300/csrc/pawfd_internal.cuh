@@ -178,7 +178,17 @@ struct TcScratch {
 
 }  // namespace pawfd
 
+// CUDA-event timing of the Gram MMA kernel launches (off by default; pawfd_kernel_timing)
+struct KernelTimer {
+  static constexpr int CAP = 256;     // launches timed between two reads
+  bool on = false;
+  int used = 0;
+  bool overflow = false;
+  cudaEvent_t start[CAP] = {}, stop[CAP] = {};
+};
+
 struct pawfd_ctx {
+  KernelTimer ktimer;
   int n[3];
   double cell[3], h[3], k[3], dV;
   int dtype;
@@ -259,6 +269,9 @@ int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void*
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout = -1);
+// bracket one timed kernel launch on the context's stream (no-ops unless timing is on)
+void ktimer_begin(pawfd_ctx* c);
+void ktimer_end(pawfd_ctx* c);
 // residuals H psi - eps S psi, their norms and the preconditioned corrections (davidson.cu)
 int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
                             double* rnorm);

@@ -195,8 +195,10 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a.part = (double*)t.part;
     a.st = c->d_status;
     if (blk == 0 && ns < nsplit) nsplit = ns;
+    ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
+    ktimer_end(c);
     // psi^T psi: psi's planes and exponents on both sides (psi's planes through a map with the
     // B operand's box)
     sg::GramArgs a2 = a;
@@ -206,8 +208,10 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a2.sig_ldB = t.rowsA_alloc;
     a2.maxB = t.maxA;
     a2.part = (double*)t.part2;
+    ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapAB, a2);
+    ktimer_end(c);
     c->launches += 4;
   }
   const long long nn = (long long)nb * nb;

@@ -398,3 +398,23 @@ def test_gamma_96c_256b_full_size(dev):
         assert torch.max(torch.abs(r2["eps"] - eps0)).item() <= 1e-10
         cur = r2["psi_rot"].clone()
     ctx.close()
+
+
+def test_gram_kernel_timing(dev):
+    """pawfd_kernel_timing brackets each Gram MMA launch of pawfd_gram_hs with CUDA events: two
+    launches per call (one K block), positive device time, counters reset by every read."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=641)
+    nb = 40
+    ctx = api.Context(s, max_bands=nb, device=dev)
+    ctx.set_option("tc_scratch_mb", 1024)
+    psi = to_dev(synth.make_psi(s, nb, 642), dev)
+    hpsi, spsi, P = ctx.apply_hs(psi)
+    assert ctx.kernel_timing(True) == (0.0, 0)
+    for _ in range(3):
+        ctx.gram_hs(psi, hpsi, P)
+    ms, n = ctx.kernel_timing(False)
+    assert n == 6 and ms > 0.0
+    ctx.gram_hs(psi, hpsi, P)
+    assert ctx.kernel_timing(False) == (0.0, 0)
+    ctx.close()
