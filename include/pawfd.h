@@ -264,6 +264,19 @@ int pawfd_davidson_step(pawfd_ctx* ctx, void* X, int nb, const double* eps_in, v
 int pawfd_density(pawfd_ctx* ctx, const void* psi, int nb, const double* f, double* rho);
 int pawfd_atomic_density(pawfd_ctx* ctx, const void* P, int nb, const double* f, void* D);
 
+/* The Hartree potential of a density (the Poisson solve of the potential update in the
+ * Kohn-Sham section; the paper's solvers are Fourier-based or multigrid, this one iterates):
+ * v solves lap_FD v = -4 pi (rho - <rho>) on the periodic grid with the order-6 Laplacian of
+ * the kinetic stencil, i.e. T v = 2 pi (rho - <rho>) with T = -1/2 lap_FD, and has zero mean.
+ * Conjugate gradients in FP64 (T applied by the stencil kernel of the context), stopped when
+ * ||r|| <= tol ||b|| or after maxiter iterations (the residual is read every 25 iterations).
+ *   ctx: a PAWFD_R64 context of a system with v = 0 and no atoms (the operator T alone);
+ *   rho, v: device [K] doubles; work: device scratch of 4 K + 304 doubles;
+ *   iters, resid (host, optional): iterations done and the final ||r|| / ||b||.
+ * Returns PAWFD_EINVAL for another context, null arrays, tol <= 0 or maxiter < 1. */
+int pawfd_poisson(pawfd_ctx* ctx, const double* rho, double* v, double tol, int maxiter, double* work, int* iters,
+                  double* resid);
+
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
  * PAWFD_C128) of the same system as the mixed context whose rotated bands psi_lo (PAWFD_R32

@@ -292,6 +292,32 @@ def atomic_density(system, P: np.ndarray, f: np.ndarray) -> np.ndarray:
     return D
 
 
+def laplacian_symbol(system) -> np.ndarray:
+    """The eigenvalues of the order-6 FD Laplacian on the periodic grid, [N3][N2][N1]:
+    L(G) = sum_c (1/h_c^2) (c0 + 2 sum_m c_m cos(m G_c h_c)) for the grid's wave vectors G."""
+    c = fd6_coefficients()
+    h = system.h
+    parts = []
+    for ax in range(3):
+        G = 2.0 * np.pi * np.fft.fftfreq(system.n[ax], d=h[ax])
+        parts.append((c[0] + 2.0 * sum(c[m] * np.cos(m * G * h[ax]) for m in (1, 2, 3))) / (h[ax] * h[ax]))
+    return parts[2][:, None, None] + parts[1][None, :, None] + parts[0][None, None, :]
+
+
+def poisson(system, rho: np.ndarray) -> np.ndarray:
+    """The zero-mean solution of lap_FD v = -4 pi (rho - <rho>) on the periodic grid with the
+    order-6 Laplacian (the Poisson solve of the Kohn-Sham section's potential update, by its
+    direct Fourier-transform route): v(G) = -4 pi rho(G) / L(G) for G != 0, v(0) = 0."""
+    rho = np.asarray(rho, np.float64).reshape(system.n[2], system.n[1], system.n[0])
+    L = laplacian_symbol(system)
+    rg = np.fft.fftn(rho)
+    vg = np.zeros_like(rg)
+    nz = np.ones(L.shape, bool)
+    nz[0, 0, 0] = False
+    vg[nz] = -4.0 * np.pi * rg[nz] / L[nz]
+    return np.real(np.fft.ifftn(vg))
+
+
 def davidson_weights(system, eps: np.ndarray) -> np.ndarray:
     """Jacobi preconditioner weights w_n(r) = -1 / max(d(r) - eps_n, d0 / 10) of the block-Davidson
     step (a reading: the paper names the Davidson eigensolver of the Kohn-Sham and

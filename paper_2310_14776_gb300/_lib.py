@@ -57,6 +57,7 @@ SIGNATURES = {
     "pawfd_davidson_step": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
     "pawfd_density": ([VP, VP, I, VP, VP], I),
     "pawfd_kernel_timing": ([VP, I, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)], I),
+    "pawfd_poisson": ([VP, VP, VP, D, I, VP, ctypes.POINTER(I), ctypes.POINTER(D)], I),
     "pawfd_atomic_density": ([VP, VP, I, VP, VP], I),
     "pawfd_batch_create": ([ctypes.POINTER(VP), ctypes.POINTER(RrJob), I, I], I),
     "pawfd_batch_launch": ([VP, VP], I),

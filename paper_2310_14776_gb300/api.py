@@ -246,6 +246,20 @@ class Context:
         self._call(self.lib.pawfd_kernel_timing, int(bool(enable)), ctypes.byref(ms), ctypes.byref(n))
         return ms.value, n.value
 
+    def poisson(self, rho, v=None, tol: float = 1e-11, maxiter: int = 5000):
+        """The zero-mean Hartree potential of rho (pawfd_poisson); this context must be the
+        free operator of its grid (see ``poisson_context``).  Returns (v, iterations, relative
+        residual)."""
+        if rho.numel() != self.K or rho.dtype != torch.float64 or rho.device != self.device:
+            raise ValueError("rho must hold K float64 values on the device")
+        v = torch.empty(self.K, dtype=torch.float64, device=self.device) if v is None else v
+        work = torch.empty(4 * self.K + 304, dtype=torch.float64, device=self.device)
+        it = ctypes.c_int(0)
+        res = ctypes.c_double(0.0)
+        self._call(self.lib.pawfd_poisson, ctypes.c_void_p(rho.contiguous().data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                   float(tol), int(maxiter), ctypes.c_void_p(work.data_ptr()), ctypes.byref(it), ctypes.byref(res))
+        return v, it.value, res.value
+
     def density(self, psi, f, rho=None):
         """rho(r) = sum_n f_n |psi_n(r)|^2 (pawfd_density); f: device float64 [nb]."""
         nb = self._bands(psi, "psi")
@@ -451,3 +465,10 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def poisson_context(system, device=None) -> Context:
+    """An FP64 context of the free operator T on ``system``'s grid (v = 0, no atoms): the
+    operator of the Poisson solve."""
+    from . import synth
+    return Context(synth.free_grid(system), max_bands=1, device=device, precision="fp64")

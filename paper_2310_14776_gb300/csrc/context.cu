@@ -332,7 +332,12 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     std::vector<double> vs(c->K);
     const double centre = -0.5 * FD6_W0 * (1.0 / (c->h[0] * c->h[0]) + 1.0 / (c->h[1] * c->h[1]) +
                                            1.0 / (c->h[2] * c->h[2]));
-    for (size_t r = 0; r < c->K; ++r) vs[r] = d->vloc[r] + centre;
+    bool vzero = true;
+    for (size_t r = 0; r < c->K; ++r) {
+      vs[r] = d->vloc[r] + centre;
+      vzero = vzero && d->vloc[r] == 0.0;
+    }
+    c->free_operator = vzero && d->natoms == 0;
     if (is_fp32(c)) {
       std::vector<float> vf(vs.begin(), vs.end());
       float* p = dev_alloc<float>(c, c->K, &rc);

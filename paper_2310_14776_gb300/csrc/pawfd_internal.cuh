@@ -226,6 +226,7 @@ struct pawfd_ctx {
   int tc_scratch_mb = 0;                      // digit-plane scratch per operand set in MB (0: default sizes)
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
+  bool free_operator = false;                 // v = 0 and no atoms: kinetic_local is T alone (Poisson)
   bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic
   pawfd::TcScratch tc;
   std::string err;

@@ -273,6 +273,13 @@ def without_atoms(system: System) -> System:
                                dmat_off=np.zeros(1, np.int64))
 
 
+def free_grid(system: System) -> System:
+    """The same cell and grid with v = 0, no atoms and k = 0: the operator T alone (the
+    Laplacian of the Poisson solve)."""
+    s = without_atoms(system)
+    return dataclasses.replace(s, vloc=np.zeros_like(system.vloc), k=(0.0, 0.0, 0.0), complex_wf=False, wells=None)
+
+
 # ----------------------------------------------------------------------------------------------
 # named workloads
 # ----------------------------------------------------------------------------------------------

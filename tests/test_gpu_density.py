@@ -46,3 +46,21 @@ def test_density_and_atomic_density_match_oracle(dev, precision, cplx):
     assert np.max(np.abs(rho - ref_rho)) <= rel * np.max(ref_rho), np.max(np.abs(rho - ref_rho)) / np.max(ref_rho)
     assert np.max(np.abs(D - ref_D)) <= rel * np.max(np.abs(ref_D))
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [(30, 28, 26), (48, 40, 36)])
+def test_poisson_matches_oracle(dev, n):
+    """pawfd_poisson (conjugate gradients with the stencil kernel: the general FP64 kernel on
+    the smaller grid, the double-float kernel on the larger) against the oracle's Fourier
+    solve of the same FD equation."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system(n, (7.0, 6.5, 6.0), 3, synth.PSET_SP, seed=651)
+    f = synth.free_grid(s)
+    rho_np = np.abs(synth.make_psi(s, 1, 652)).reshape(-1) ** 2
+    ctx = api.poisson_context(s, device=dev)
+    v, iters, res = ctx.poisson(torch.from_numpy(rho_np).to(dev), tol=1e-12, maxiter=4000)
+    ctx.sync()
+    ref = O.poisson(f, rho_np).reshape(-1)
+    assert res <= 1e-12 and 0 < iters < 4000
+    assert np.max(np.abs(v.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
+    ctx.close()

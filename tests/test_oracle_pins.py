@@ -638,3 +638,33 @@ def test_density_of_plane_waves_is_uniform():
     f = np.array([2.0, 2.0, 1.0, 0.5])
     rho = O.density(s, psi, f)
     assert np.allclose(rho, np.sum(f) / V, rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------------------------------------------
+# f-3: the Poisson solve for the Hartree potential
+# ------------------------------------------------------------------------------------------
+
+def test_poisson_solution_satisfies_the_fd_equation():
+    # the Fourier-route solution, put through the real-space stencil of the oracle (a route
+    # that shares nothing with the FFT), gives back 2 pi (rho - <rho>); its mean is zero
+    s = small_system(n=(14, 12, 10), natoms=2)
+    f = synth.free_grid(s)
+    rho = np.abs(rand_psi(s, 1, 51)).reshape(s.n[::-1]) ** 2
+    v = O.poisson(f, rho)
+    Tv = O.kinetic_local(f, v.reshape((1,) + v.shape)).reshape(v.shape)
+    b = 2 * math.pi * (rho - rho.mean())
+    assert np.max(np.abs(Tv - b)) < 1e-12 * np.max(np.abs(b))
+    assert abs(v.mean()) < 1e-14 * np.max(np.abs(v))
+
+
+def test_poisson_plane_wave_closed_form():
+    # rho = cos(G.r) has v = -4 pi cos(G.r) / L(G) with the FD symbol written out by hand
+    s = free_system((12, 10, 9), (6.0, 5.0, 4.5))
+    x, y, z = grid_coords(s)
+    q = (2, -1, 1)
+    G = [2 * math.pi * q[c] / s.cell[c] for c in range(3)]
+    rho = np.cos(G[0] * x + G[1] * y + G[2] * z)
+    w = golden_weights()
+    L = sum((w[0] + 2 * sum(w[m] * math.cos(m * G[c] * s.h[c]) for m in (1, 2, 3))) / s.h[c] ** 2 for c in range(3))
+    v = O.poisson(s, rho)
+    assert np.allclose(v, -4 * math.pi * rho / L, rtol=0, atol=1e-13 * np.max(np.abs(4 * math.pi * rho / L)))
