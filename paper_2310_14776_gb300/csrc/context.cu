@@ -288,6 +288,9 @@ void free_ctx(pawfd_ctx* c) {
                   c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->aux_fork) cudaEventDestroy(c->aux_fork);
+  if (c->aux_join) cudaEventDestroy(c->aux_join);
   for (int i = 0; i < KernelTimer::CAP; ++i) {
     if (c->ktimer.start[i]) cudaEventDestroy(c->ktimer.start[i]);
     if (c->ktimer.stop[i]) cudaEventDestroy(c->ktimer.stop[i]);

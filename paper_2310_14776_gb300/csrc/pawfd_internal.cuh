@@ -227,6 +227,8 @@ struct pawfd_ctx {
   bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
   bool free_operator = false;                 // v = 0 and no atoms: kinetic_local is T alone (Poisson)
+  cudaStream_t aux_stream = nullptr;          // non-blocking stream for captured work (created on use)
+  cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic
   pawfd::TcScratch tc;
   std::string err;

@@ -6,7 +6,8 @@
 // the kinetic stencil (T = -1/2 lap_FD, so the system is T v = 2 pi (rho - <rho>)), and
 // returns the solution of zero mean.  T is symmetric positive definite on zero-mean grid
 // functions, so conjugate gradients apply.  All scalars of the iteration stay on the device;
-// the host reads the residual every CHECK iterations.
+// the host reads the residual every CHECK iterations, and each batch of CHECK iterations is
+// one CUDA graph launch.
 #include <cmath>
 
 #include "pawfd_internal.cuh"
@@ -114,6 +115,11 @@ __global__ void shift_kernel(const double* __restrict__ x, long long K, const do
 
 }  // namespace
 
+namespace {
+int solve(pawfd_ctx* c, const double* rho, double* v, double tol, int maxiter, double* work, int* iters,
+          double* resid);
+}  // namespace
+
 extern "C" int pawfd_poisson(pawfd_ctx* c, const double* rho, double* v, double tol, int maxiter, double* work,
                              int* iters, double* resid) {
   if (!c) return PAWFD_EINVAL;
@@ -121,6 +127,30 @@ extern "C" int pawfd_poisson(pawfd_ctx* c, const double* rho, double* v, double 
   if (!c->free_operator) return fail(c, PAWFD_EINVAL, "pawfd_poisson needs a context with v = 0 and no atoms");
   if (!rho || !v || !work) return fail(c, PAWFD_EINVAL, "null array");
   if (!(tol > 0.0) || maxiter < 1) return fail(c, PAWFD_EINVAL, "tol must be > 0 and maxiter >= 1");
+  // the solve runs on the context's auxiliary non-blocking stream (graph capture is not
+  // possible on the legacy default stream), ordered after the work already on c->stream and
+  // joined back to it at the end
+  if (!c->aux_stream) {
+    int e = check_cuda(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking), "aux stream");
+    if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming), "event");
+    if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming), "event");
+    if (e != PAWFD_OK) return e;
+  }
+  cudaStream_t caller = c->stream;
+  int rc0 = check_cuda(c, cudaEventRecord(c->aux_fork, caller), "event record");
+  if (rc0 == PAWFD_OK) rc0 = check_cuda(c, cudaStreamWaitEvent(c->aux_stream, c->aux_fork, 0), "stream wait");
+  if (rc0 != PAWFD_OK) return rc0;
+  c->stream = c->aux_stream;
+  const int rcs = solve(c, rho, v, tol, maxiter, work, iters, resid);
+  c->stream = caller;
+  int rc1 = check_cuda(c, cudaEventRecord(c->aux_join, c->aux_stream), "event record");
+  if (rc1 == PAWFD_OK) rc1 = check_cuda(c, cudaStreamWaitEvent(caller, c->aux_join, 0), "stream wait");
+  return rcs != PAWFD_OK ? rcs : rc1;
+}
+
+namespace {
+int solve(pawfd_ctx* c, const double* rho, double* v, double tol, int maxiter, double* work, int* iters,
+          double* resid) {
   const long long K = (long long)c->K;
   double* x = work;
   double* r = work + K;
@@ -144,24 +174,50 @@ extern "C" int pawfd_poisson(pawfd_ctx* c, const double* rho, double* v, double 
   const double bnorm = std::sqrt(h[S_BB]);
   double rnorm = bnorm;
   int k = 0;
+  // one iteration: Ap = T p, alpha, x and r, r.r and beta, p
+  auto iteration = [&]() {
+    int e = launch_kinetic_local(c, p, 1, Ap);
+    dot_partial_kernel<<<PG, PT, 0, s>>>(p, Ap, K, part);
+    finish_kernel<<<1, 32, 0, s>>>(part, PG, K, 2, scal);
+    cg_xr_kernel<<<PG, PT, 0, s>>>(x, r, p, Ap, K, scal, part);
+    finish_kernel<<<1, 32, 0, s>>>(part, PG, K, 3, scal);
+    cg_p_kernel<<<PG, PT, 0, s>>>(p, r, K, scal);
+    c->launches += 5;
+    return e;
+  };
+  // CHECK iterations captured once into a CUDA graph (the pointers do not change between
+  // iterations), so that a batch is one launch; eager launches if capture is not available
+  cudaGraphExec_t exec = nullptr;
+  {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      int e = PAWFD_OK;
+      for (int j = 0; j < CHECK && e == PAWFD_OK; ++j) e = iteration();
+      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (e != PAWFD_OK || ce != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();   // a failed capture leaves no error behind for the eager path
+  }
   while (k < maxiter && rnorm > tol * bnorm && bnorm > 0.0) {
     const int batch = std::min(CHECK, maxiter - k);
-    for (int j = 0; j < batch && rc == PAWFD_OK; ++j) {
-      rc = launch_kinetic_local(c, p, 1, Ap);                    // Ap = T p
-      dot_partial_kernel<<<PG, PT, 0, s>>>(p, Ap, K, part);
-      finish_kernel<<<1, 32, 0, s>>>(part, PG, K, 2, scal);      // alpha
-      cg_xr_kernel<<<PG, PT, 0, s>>>(x, r, p, Ap, K, scal, part);
-      finish_kernel<<<1, 32, 0, s>>>(part, PG, K, 3, scal);      // r.r, beta
-      cg_p_kernel<<<PG, PT, 0, s>>>(p, r, K, scal);
-      c->launches += 5;
+    if (exec && batch == CHECK) {
+      rc = check_cuda(c, cudaGraphLaunch(exec, s), "poisson graph launch");
+    } else {
+      for (int j = 0; j < batch && rc == PAWFD_OK; ++j) rc = iteration();
     }
     k += batch;
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaGetLastError(), "poisson launch");
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemcpyAsync(h, scal, sizeof(h), cudaMemcpyDeviceToHost, s), "copy");
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamSynchronize(s), "sync");
-    if (rc != PAWFD_OK) return rc;
+    if (rc != PAWFD_OK) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return rc;
+    }
     rnorm = std::sqrt(h[S_RRNEW]);
   }
+  if (exec) cudaGraphExecDestroy(exec);
   // the zero-mean solution
   dot_partial_kernel<<<PG, PT, 0, s>>>(x, nullptr, K, part);
   finish_kernel<<<1, 32, 0, s>>>(part, PG, K, 0, scal);
@@ -171,3 +227,4 @@ extern "C" int pawfd_poisson(pawfd_ctx* c, const double* rho, double* v, double 
   if (resid) *resid = bnorm > 0.0 ? rnorm / bnorm : 0.0;
   return check_cuda(c, cudaGetLastError(), "poisson launch");
 }
+}  // namespace
