@@ -46,7 +46,7 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
 _GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "9fbba2e9424e4e6498471fb2c73f3e6161a9c0a4",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "67b8b680e74ff194fe1827d5b5f1c9146aa063b9",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "356308f2280e7a65b41efb150367ecc5d5fa8b5f",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
                  "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
@@ -319,7 +319,8 @@ def run_gpu(args):
     gram_launch_flops = 2.0 * products * cfac * nb * (nb + 1) / 2 * K
     kernel_roof = None
     if mma_avg_ms:
-        ach = gram_launch_flops / (mma_avg_ms * 1e-3)
+        # two Hermitian Grams per step, over however many K-block launches they took
+        ach = 2 * args.steps * gram_launch_flops / (mma_ms * 1e-3)
         kernel_roof = {"kernel": "sliced_gram_kernel (Gram mode; %d launches timed)" % mma_launches,
                        "bound": "tensor", "achieved": ach / 1e12, "peak": bf16, "unit": "TFLOP/s",
                        "frac": ach / (bf16 * 1e12), "avg_launch_ms": mma_avg_ms,
@@ -327,8 +328,10 @@ def run_gpu(args):
                        "traffic_unit": "DRAM bytes per launch (ncu at 64^3 x 256 bands, mean of the pair's two "
                                        "launches, scaled by grid points)",
                        "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)",
-                       "work": "useful (Hermitian upper-triangle) BF16 digit products; the kernel executes "
-                               "%.2fx that in 128 x 96 tiles" % (sg_tiles_area(nb) / (nb * (nb + 1) / 2))}
+                       "work": "useful (Hermitian upper-triangle) BF16 digit products of the step's two Grams "
+                               "over the summed launch times" + (
+                                   "" if cplx else "; the kernel executes %.2fx that in 128 x 96 tiles"
+                                   % (sg_tiles_area(nb) / (nb * (nb + 1) / 2)))}
 
     result = {
         "metric": METRIC, "value_definition": VALUE_DEF,

@@ -103,11 +103,12 @@ int pawfd_nproj_total(const pawfd_ctx* ctx);
 /* number of CUDA kernels this context has launched so far (host-side counter) */
 long long pawfd_launch_count(const pawfd_ctx* ctx);
 
-/* CUDA-event timing of the tensor-core Gram MMA kernel launches of pawfd_gram_hs (each of its
- * two MMA kernels per K block is bracketed by a pair of events on the context's stream, up to
- * 256 launches between two calls).  Returns, through total_ms and launches, the summed device
- * time and the number of timed launches since the previous call (launches = -1 if more than
- * 256 were made), waiting for the last one; then turns timing on (enable = 1) or off. */
+/* CUDA-event timing of the tensor-core Gram MMA kernel launches (pawfd_gram_hs, pawfd_gram,
+ * pawfd_gram_hermitian and the steps built on them: each MMA kernel launch of a K block is
+ * bracketed by a pair of events on the context's stream, up to 1024 launches between two
+ * calls).  Returns, through total_ms and launches, the summed device time and the number of
+ * timed launches since the previous call (launches = -1 if more than 1024 were made),
+ * waiting for the last one; then turns timing on (enable = 1) or off. */
 int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long* launches);
 
 /* Select among equivalent implementations (for tests and measurements):

@@ -180,7 +180,7 @@ struct TcScratch {
 
 // CUDA-event timing of the Gram MMA kernel launches (off by default; pawfd_kernel_timing)
 struct KernelTimer {
-  static constexpr int CAP = 256;     // launches timed between two reads
+  static constexpr int CAP = 1024;    // launches timed between two reads
   bool on = false;
   int used = 0;
   bool overflow = false;

@@ -128,8 +128,10 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     a.st = c->d_status;
     // slots written by the first block must cover every split later blocks add into
     if (blk == 0 && ns < nsplit) nsplit = ns;
+    ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapB, a);
+    ktimer_end(c);
     c->launches += 1;
   }
   const long long nn = (long long)nb * nb;
