@@ -492,6 +492,14 @@ namespace pawfd {
 void ktimer_begin(pawfd_ctx* c) {
   KernelTimer& t = c->ktimer;
   if (!t.on) return;
+  // launches captured into a CUDA graph are not timed (their events would only be recorded
+  // when the graph runs); ktimer_end sees the same answer
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(c->stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    t.capturing = true;
+    return;
+  }
+  t.capturing = false;
   if (t.used >= KernelTimer::CAP) {
     t.overflow = true;
     return;
@@ -504,7 +512,7 @@ void ktimer_begin(pawfd_ctx* c) {
 }
 void ktimer_end(pawfd_ctx* c) {
   KernelTimer& t = c->ktimer;
-  if (!t.on || t.used >= KernelTimer::CAP) return;
+  if (!t.on || t.capturing || t.used >= KernelTimer::CAP) return;
   cudaEventRecord(t.stop[t.used], c->stream);
   ++t.used;
 }

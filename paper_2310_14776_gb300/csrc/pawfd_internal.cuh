@@ -184,6 +184,7 @@ struct KernelTimer {
   bool on = false;
   int used = 0;
   bool overflow = false;
+  bool capturing = false;             // the bracketed launch is being captured into a graph
   cudaEvent_t start[CAP] = {}, stop[CAP] = {};
 };
 
