@@ -901,6 +901,134 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         }
       }
     }
+    } else if constexpr (BULK && S == 4) {
+    // The rotation of FP32 bands with several chunks per tile (complex bands, or more than KC
+    // bands): one tile per CTA, the chunks' five orders summed into double-float accumulators,
+    // then one write-out with FP32 values rounded once from the double-float sums.  TMEM is
+    // read in the 16 x 256-bit shape (as in the one-chunk form): thread t holds rows t/4 and
+    // t/4 + 8 of each 16-lane half and columns 2 (t%4), 2 (t%4) + 1 of each 8-column group, so
+    // that four threads store four consecutive values of one row.  (For FP64 bands the
+    // general epilogue below measured faster: its wider TMEM loads drain each chunk in half
+    // the load instructions, and the FP64 stores gain nothing from this layout.)
+    constexpr int NG = EPI_COLS / 8;
+    const int quarter = warp & 3, chalf = warp >> 2;
+    int row0, col0, tcol;
+    tile_at(0, row0, col0, tcol);
+    const int cbase = chalf * EPI_COLS;
+    const int trow = lane >> 2, tcol2 = (lane & 3) * 2;
+    float ahi[2][NG][4], alo[2][NG][4];   // [h][group][2 p + c]
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ahi[h][g][e] = 0.0f;
+          alo[h][g][e] = 0.0f;
+        }
+    // this thread's rows: r = 2 h + p  ->  row0 + 32 quarter + 16 h + 8 p + trow
+    int rws[4], ra[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      rws[r] = row0 + quarter * 32 + (r >> 1) * 16 + (r & 1) * 8 + trow;
+      ra[r] = rws[r] < a.rowsA ? __ldg(a.maxA + rws[r]) : 0;
+    }
+    // column exponents: two registers per lane (columns cbase + lane, cbase + 32 + lane), handed
+    // to the column's threads by shuffles
+    const int cl0 = col0 + cbase + lane, cl1 = cl0 + 32;
+    const bool cv0 = cl0 < a.rowsB, cv1 = lane + 32 < EPI_COLS && cl1 < a.rowsB;
+    const int mb0 = cv0 ? __ldg(a.maxB + cl0) : 0, mb1 = cv1 ? __ldg(a.maxB + cl1) : 0;
+    for (int c = 0; c < nch; ++c) {
+      const int chunk = c_begin + c;
+      int sa[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        sa[r] = rws[r] < a.rowsA ? __ldg(a.sigA + (long long)chunk * a.sig_ldA + rws[r]) - ra[r] : 0;
+      const int sb0 = cv0 ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + cl0) - mb0 : 0;
+      const int sb1 = cv1 ? __ldg(a.sigB + (long long)chunk * a.sig_ldB + cl1) - mb1 : 0;
+      bool ok = tc::mbar_wait(&dfull, c & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) {
+          abort_flag = 1;
+          set_status(a.st, PAWFD_ETIMEDOUT, 1004);
+        }
+        break;
+      }
+      tc::fence_after_sync();
+      int sbv[NG][2];
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int c2 = 0; c2 < 2; ++c2)
+          sbv[g][c2] = __shfl_sync(0xffffffffu, g * 8 < 32 ? sb0 : sb1, (g * 8 + tcol2 + c2) & 31);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          uint32_t d[NACC][4];
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32 + h * 16) << 16) + (uint32_t)(cbase + g * 8);
+#pragma unroll
+          for (int o = 0; o < NACC; ++o) tc::tmem_ld_16x256b(taddr + o * BN, d[o]);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float scale = pow2f_nonpos(sa[2 * h + (e >> 1)] + sbv[g][e & 1]);
+            float s1, e1, s2, e2, s3, e3, vh, vl;
+            two_sum(__uint_as_float(d[0][e]), __uint_as_float(d[1][e]), s1, e1);
+            two_sum(s1, __uint_as_float(d[2][e]), s2, e2);
+            two_sum(s2, __uint_as_float(d[3][e]), s3, e3);
+            two_sum(s3, ((e1 + e2) + e3) + __uint_as_float(d[4][e]), vh, vl);
+            df_add(ahi[h][g][e], alo[h][g][e], vh * scale, vl * scale);
+          }
+        }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&dempty);
+    }
+    // the columns' largest exponents, then the write-out (FP32 values rounded once from the
+    // double-float sum, FP64 values assembled with integer operations)
+    int mbv[NG][2];
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+      for (int c2 = 0; c2 < 2; ++c2)
+        mbv[g][c2] = __shfl_sync(0xffffffffu, g * 8 < 32 ? mb0 : mb1, (g * 8 + tcol2 + c2) & 31);
+    if (!abort_flag) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int h = r >> 1, p = r & 1;
+        if (rws[r] >= a.rowsA) continue;
+        const int band = rws[r] % a.rot_nb, part = rws[r] / a.rot_nb;
+        const long long base = (long long)band * a.rot_K;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const int col = col0 + cbase + g * 8 + tcol2;
+          const bool vec = a.rot_vec && col + 1 < a.rowsB;
+          if (a.rot_fp32) {
+            const float v0 = f2f_scaled(ahi[h][g][2 * p] + alo[h][g][2 * p], ra[r] + mbv[g][0]);
+            const float v1 = f2f_scaled(ahi[h][g][2 * p + 1] + alo[h][g][2 * p + 1], ra[r] + mbv[g][1]);
+            if (vec) {
+              *(float2*)((float*)a.rot_out + base + col) = make_float2(v0, v1);
+            } else {
+              if (col < a.rowsB) ((float*)a.rot_out)[a.rot_cplx ? 2 * (base + col) + part : base + col] = v0;
+              if (col + 1 < a.rowsB)
+                ((float*)a.rot_out)[a.rot_cplx ? 2 * (base + col + 1) + part : base + col + 1] = v1;
+            }
+          } else {
+            const double v0 = df_to_double(ahi[h][g][2 * p], alo[h][g][2 * p], ra[r] + mbv[g][0]);
+            const double v1 = df_to_double(ahi[h][g][2 * p + 1], alo[h][g][2 * p + 1], ra[r] + mbv[g][1]);
+            if (vec) {
+              *(double2*)((double*)a.rot_out + base + col) = make_double2(v0, v1);
+            } else {
+              if (col < a.rowsB) ((double*)a.rot_out)[a.rot_cplx ? 2 * (base + col) + part : base + col] = v0;
+              if (col + 1 < a.rowsB)
+                ((double*)a.rot_out)[a.rot_cplx ? 2 * (base + col + 1) + part : base + col + 1] = v1;
+            }
+          }
+        }
+      }
+    }
     } else {
     // epilogue warps: lane quarter (warp % 4), column half (warp / 4)
     const int quarter = warp & 3, chalf = warp >> 2;
