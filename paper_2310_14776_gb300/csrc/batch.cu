@@ -39,8 +39,30 @@ int enqueue_rr_step(pawfd_ctx* c, const pawfd_rr_job& j) {
     return fail(c, PAWFD_EINVAL, "arrays may not alias");
   int rc = launch_apply_hs(c, j.psi, nb, j.hpsi, j.spsi, c->d_P);
   if (rc == PAWFD_OK) rc = launch_gram_hs(c, j.psi, j.hpsi, nb, c->d_P, j.Hnm, j.Snm);
-  if (rc == PAWFD_OK) rc = launch_subspace_diag(c, nb, j.Hnm, j.Snm, j.eps, j.C);
+  // The rotation's digits of psi depend on psi alone: outside graph capture they are made on
+  // the auxiliary stream while the latency-bound subspace solve runs, and the rotation then
+  // only slices C and multiplies.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  const bool overlap = rc == PAWFD_OK && c->use_tc && c->tc.ready && c->tc.rot_rblk >= (long long)c->K &&
+                       cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone &&
+                       ensure_aux_stream(c) == PAWFD_OK;
+  if (overlap) {
+    cudaStream_t main = c->stream;
+    rc = check_cuda(c, cudaEventRecord(c->aux_fork, main), "event record");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamWaitEvent(c->aux_stream, c->aux_fork, 0), "stream wait");
+    if (rc == PAWFD_OK) {
+      c->stream = c->aux_stream;
+      rotate_slice_psi(c, j.psi, nb);
+      c->stream = main;
+      rc = check_cuda(c, cudaEventRecord(c->aux_join, c->aux_stream), "event record");
+    }
+    if (rc == PAWFD_OK) rc = launch_subspace_diag(c, nb, j.Hnm, j.Snm, j.eps, j.C);
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamWaitEvent(main, c->aux_join, 0), "stream wait");
+  } else if (rc == PAWFD_OK) {
+    rc = launch_subspace_diag(c, nb, j.Hnm, j.Snm, j.eps, j.C);
+  }
   if (rc == PAWFD_OK) rc = launch_rotate(c, j.psi, nb, j.C, j.psi_out);
+  c->tc.presliced_psi = nullptr;   // consumed by the rotation, or void after an error
   return rc;
 }
 

@@ -489,6 +489,14 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
 }
 
 namespace pawfd {
+int ensure_aux_stream(pawfd_ctx* c) {
+  if (c->aux_stream) return PAWFD_OK;
+  int e = check_cuda(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking), "aux stream");
+  if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming), "event");
+  if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming), "event");
+  return e;
+}
+
 void ktimer_begin(pawfd_ctx* c) {
   KernelTimer& t = c->ktimer;
   if (!t.on) return;

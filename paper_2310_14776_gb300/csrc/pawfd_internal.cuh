@@ -168,6 +168,8 @@ struct TcScratch {
   int* rotMaxA = nullptr;
   int* rotMaxB = nullptr;
   int slice_t_ctas = 0;        // CTAs of the persistent transposing slicer
+  const void* presliced_psi = nullptr;   // psi whose rotation digits are already in rotSlicesB
+  int presliced_nb = 0;
   // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
   long long fnch = 0;          // chunks per row
   int* fsigA = nullptr;        // [fnch][max_bands]
@@ -270,6 +272,9 @@ int launch_nonlocal_add2(pawfd_ctx* c, const void* P, int nb, const void* dmat1,
 int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout);
+bool rotate_slice_psi(pawfd_ctx* c, const void* psi, int nb);
+// the context's auxiliary non-blocking stream and its fork / join events (created on first use)
+int ensure_aux_stream(pawfd_ctx* c);
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout = -1);

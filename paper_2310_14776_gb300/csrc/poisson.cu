@@ -130,10 +130,8 @@ extern "C" int pawfd_poisson(pawfd_ctx* c, const double* rho, double* v, double 
   // the solve runs on the context's auxiliary non-blocking stream (graph capture is not
   // possible on the legacy default stream), ordered after the work already on c->stream and
   // joined back to it at the end
-  if (!c->aux_stream) {
-    int e = check_cuda(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking), "aux stream");
-    if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_fork, cudaEventDisableTiming), "event");
-    if (e == PAWFD_OK) e = check_cuda(c, cudaEventCreateWithFlags(&c->aux_join, cudaEventDisableTiming), "event");
+  {
+    const int e = ensure_aux_stream(c);
     if (e != PAWFD_OK) return e;
   }
   cudaStream_t caller = c->stream;

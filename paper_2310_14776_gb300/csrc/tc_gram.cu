@@ -247,6 +247,23 @@ __global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int nou
   A[e] = v;
 }
 
+// the transposed digits of psi for the rotation, one block of grid points r0 .. r0 + rcount
+template <class R, int S>
+void rc_slice_psi(pawfd_ctx* c, const R* psi, int nb, long long r0, int rcount, int nch) {
+  TcScratch& t = c->tc;
+  const bool cplx = is_complex(c);
+  const long long K = (long long)c->K;
+  cudaMemsetAsync(t.rotMaxB, 0x80, sizeof(int) * t.rot_rblk, c->stream);
+  const int stiles = (rcount + sg::RT - 1) / sg::RT * nch;
+  // 16-byte staging copies: band rows and the block start on 16-byte boundaries
+  constexpr int v16 = 16 / (int)sizeof(R);
+  const int per = cplx ? 2 : 1;
+  const int vec16 = (per * K) % v16 == 0 && (per * r0) % v16 == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
+  sg::slice_t_kernel<R, S><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R>(), c->stream>>>(
+      psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
+      (int)t.rot_rblk, t.rotMaxB, nch, vec16);
+}
+
 template <class R, int S, int ORD>
 int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, R* out) {
   TcScratch& t = c->tc;
@@ -268,17 +285,15 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
   }
   c->launches += 2;
   const int tilesM = (rowsA + sg::BM - 1) / sg::BM;
+  // psi's digits of a single-block rotation may already be in place (rotate_slice_psi)
+  const bool presliced = t.presliced_psi == (const void*)psi && t.presliced_nb == nb && t.rot_rblk >= K;
+  t.presliced_psi = nullptr;
   for (long long r0 = 0; r0 < K; r0 += t.rot_rblk) {
     const int rcount = (int)std::min<long long>(t.rot_rblk, K - r0);
-    cudaMemsetAsync(t.rotMaxB, 0x80, sizeof(int) * t.rot_rblk, c->stream);
-    const int stiles = (rcount + sg::RT - 1) / sg::RT * nch;
-    // 16-byte staging copies: band rows and the block start on 16-byte boundaries
-    constexpr int v16 = 16 / (int)sizeof(R);
-    const int per = cplx ? 2 : 1;
-    const int vec16 = (per * K) % v16 == 0 && (per * r0) % v16 == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
-    sg::slice_t_kernel<R, S><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R>(), c->stream>>>(
-        psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
-        (int)t.rot_rblk, t.rotMaxB, nch, vec16);
+    if (!presliced) {
+      rc_slice_psi<R, S>(c, psi, nb, r0, rcount, nch);
+      c->launches += 1;
+    }
     sg::GramArgs a = {};
     a.gA = (const __nv_bfloat16*)t.rotSlicesA;
     a.gB = (const __nv_bfloat16*)t.rotSlicesB;
@@ -318,12 +333,30 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
     else
       sg::sliced_gram_kernel<S, ORD, false, true, sg::KC>
           <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, a);
-    c->launches += 2;
+    c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
 }
 
 }  // namespace
+
+// The digits of psi for a following rotation of the same psi and nb, when the rotation is one
+// block of grid points: enqueued early (on any stream ordered after psi is final) so that the
+// rotation skips them.  Returns false when the rotation would not use them.
+bool rotate_slice_psi(pawfd_ctx* c, const void* psi, int nb) {
+  TcScratch& t = c->tc;
+  if (!c->use_tc || !t.ready || t.rot_rblk < (long long)c->K) return false;
+  const long long Lk = (long long)nb * (is_complex(c) ? 2 : 1);
+  const long long Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
+  if (Lc > t.rot_Lc) return false;
+  const int nch = (int)(Lc / sg::KC);
+  if (is_fp32(c)) rc_slice_psi<float, 4>(c, (const float*)psi, nb, 0, (int)c->K, nch);
+  else rc_slice_psi<double, 7>(c, (const double*)psi, nb, 0, (int)c->K, nch);
+  c->launches += 1;
+  t.presliced_psi = psi;
+  t.presliced_nb = nb;
+  return cudaGetLastError() == cudaSuccess;
+}
 
 int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout) {
   if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core scratch not set up");

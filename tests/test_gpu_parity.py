@@ -418,3 +418,24 @@ def test_gram_kernel_timing(dev):
     ctx.gram_hs(psi, hpsi, P)
     assert ctx.kernel_timing(False) == (0.0, 0)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_rr_step_equals_staged_calls(dev, precision):
+    """pawfd_rr_step makes the rotation's digits of psi on an auxiliary stream during the
+    subspace solve; its results are bitwise those of the four staged calls."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((48, 40, 36), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=661)
+    nb = 96
+    ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+    ctx.set_option("tc_scratch_mb", 2048)
+    psi = to_dev(synth.make_psi(s, nb, 662), dev).to(ctx.dtype)
+    for _ in range(2):                      # near-Ritz bands, as in the iterated step
+        psi = ctx.rr_step(psi)["psi_rot"].clone()
+    res = ctx.rr_step(psi)
+    out_fused, eps_fused = res["psi_rot"].clone(), res["eps"].clone()
+    staged = ctx.rayleigh_ritz(psi)
+    ctx.sync()
+    assert torch.equal(eps_fused, staged["eps"])
+    assert torch.equal(out_fused, staged["psi_rot"])
+    ctx.close()
