@@ -37,15 +37,31 @@ int enqueue_rr_step(pawfd_ctx* c, const pawfd_rr_job& j) {
     return fail(c, PAWFD_EINVAL, "null array");
   if (j.psi == j.psi_out || j.psi == j.hpsi || j.psi == j.spsi || j.hpsi == j.spsi || j.Hnm == j.Snm)
     return fail(c, PAWFD_EINVAL, "arrays may not alias");
-  int rc = launch_apply_hs(c, j.psi, nb, j.hpsi, j.spsi, c->d_P);
-  if (rc == PAWFD_OK) rc = launch_gram_hs(c, j.psi, j.hpsi, nb, c->d_P, j.Hnm, j.Snm);
-  // The rotation's digits of psi depend on psi alone: outside graph capture they are made on
-  // the auxiliary stream while the latency-bound subspace solve runs, and the rotation then
-  // only slices C and multiplies.
+  // The Gram digits of psi and the rotation's digits of psi depend on psi alone: outside graph
+  // capture the first are made on the auxiliary stream while H psi and S psi are applied, the
+  // second while the latency-bound subspace solve runs.
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  const bool overlap = rc == PAWFD_OK && c->use_tc && c->tc.ready && c->tc.rot_rblk >= (long long)c->K &&
-                       cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone &&
-                       ensure_aux_stream(c) == PAWFD_OK;
+  const bool aux_ok = c->use_tc && c->tc.ready && cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess &&
+                      cap == cudaStreamCaptureStatusNone && ensure_aux_stream(c) == PAWFD_OK;
+  int rc = PAWFD_OK;
+  if (aux_ok) {
+    cudaStream_t main = c->stream;
+    rc = check_cuda(c, cudaEventRecord(c->aux_fork, main), "event record");
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamWaitEvent(c->aux_stream, c->aux_fork, 0), "stream wait");
+    if (rc == PAWFD_OK) {
+      c->stream = c->aux_stream;
+      gram_slice_psi(c, j.psi, nb);
+      c->stream = main;
+      rc = check_cuda(c, cudaEventRecord(c->aux_join, c->aux_stream), "event record");
+    }
+    if (rc == PAWFD_OK) rc = launch_apply_hs(c, j.psi, nb, j.hpsi, j.spsi, c->d_P);
+    if (rc == PAWFD_OK) rc = check_cuda(c, cudaStreamWaitEvent(main, c->aux_join, 0), "stream wait");
+  } else {
+    rc = launch_apply_hs(c, j.psi, nb, j.hpsi, j.spsi, c->d_P);
+  }
+  if (rc == PAWFD_OK) rc = launch_gram_hs(c, j.psi, j.hpsi, nb, c->d_P, j.Hnm, j.Snm);
+  c->tc.presliced_gram = nullptr;   // consumed by the Gram pair, or void after an error
+  const bool overlap = rc == PAWFD_OK && aux_ok && c->tc.rot_rblk >= (long long)c->K;
   if (overlap) {
     cudaStream_t main = c->stream;
     rc = check_cuda(c, cudaEventRecord(c->aux_fork, main), "event record");

@@ -170,6 +170,8 @@ struct TcScratch {
   int slice_t_ctas = 0;        // CTAs of the persistent transposing slicer
   const void* presliced_psi = nullptr;   // psi whose rotation digits are already in rotSlicesB
   int presliced_nb = 0;
+  const void* presliced_gram = nullptr;  // psi whose Gram digits are already in slicesA
+  int presliced_gram_nb = 0;
   // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
   long long fnch = 0;          // chunks per row
   int* fsigA = nullptr;        // [fnch][max_bands]
@@ -273,6 +275,7 @@ int launch_gram(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, boo
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian);
 int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout);
 bool rotate_slice_psi(pawfd_ctx* c, const void* psi, int nb);
+bool gram_slice_psi(pawfd_ctx* c, const void* psi, int nb);
 // the context's auxiliary non-blocking stream and its fork / join events (created on first use)
 int ensure_aux_stream(pawfd_ctx* c);
 int setup_tc(pawfd_ctx* c);

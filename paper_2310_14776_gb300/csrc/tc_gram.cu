@@ -160,16 +160,21 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
   while (nsplit > 1 && (size_t)nsplit * nb * nb * sizeof(double) > t.part_bytes) --nsplit;
   __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
   __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
+  // psi's digits of a single-block Gram may already be in place (gram_slice_psi)
+  const bool presliced = t.presliced_gram == (const void*)A && t.presliced_gram_nb == nb && Kblk >= L;
+  t.presliced_gram = nullptr;
   int blk = 0;
   for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
     const long long len = std::min(Kblk, L - k0);
     const int nch = (int)((len + sg::KCG - 1) / sg::KCG);
     const int cpc = (nch + nsplit - 1) / nsplit;
     const int ns = (nch + cpc - 1) / cpc;
-    cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+    if (!presliced) {
+      cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+      sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+          A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
+    }
     cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
-    sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
-        A + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
     sg::slice_kernel<R, S, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
         B + k0, nb, L, len, nch, t.kblk, false, 0, t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
     sg::GramArgs a = {};
@@ -214,7 +219,7 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
         t.mapA, t.mapAB, a2);
     ktimer_end(c);
-    c->launches += 4;
+    c->launches += presliced ? 3 : 4;
   }
   const long long nn = (long long)nb * nb;
   tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, nb, nb,
@@ -339,6 +344,30 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
 }
 
 }  // namespace
+
+// The Gram digits of psi (the A operand of pawfd_gram_hs) for a following Gram pair of the
+// same psi and nb, when the whole grid is one K block: enqueued early (on a stream ordered
+// after psi is final) so that the Gram pair slices only H psi.  Returns false when the Gram
+// would not use them.
+bool gram_slice_psi(pawfd_ctx* c, const void* psi, int nb) {
+  TcScratch& t = c->tc;
+  const long long L = (long long)c->K;
+  if (!c->use_tc || !t.ready || is_complex(c) || c->tc_fused || c->tc_kblk_chunks > 0 || t.kblk < L) return false;
+  const int nch = (int)((L + sg::KCG - 1) / sg::KCG);
+  cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+  if (is_fp32(c))
+    sg::slice_kernel<float, 4, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+        (const float*)psi, nb, L, L, nch, t.kblk, false, 0, t.rowsA_alloc, (__nv_bfloat16*)t.slicesA, t.sigA,
+        t.rowsA_alloc, t.maxA);
+  else
+    sg::slice_kernel<double, 7, sg::KCG><<<(unsigned)(((long long)nb * nch + 7) / 8), 256, 0, c->stream>>>(
+        (const double*)psi, nb, L, L, nch, t.kblk, false, 0, t.rowsA_alloc, (__nv_bfloat16*)t.slicesA, t.sigA,
+        t.rowsA_alloc, t.maxA);
+  c->launches += 1;
+  t.presliced_gram = psi;
+  t.presliced_gram_nb = nb;
+  return cudaGetLastError() == cudaSuccess;
+}
 
 // The digits of psi for a following rotation of the same psi and nb, when the rotation is one
 // block of grid points: enqueued early (on any stream ordered after psi is final) so that the
