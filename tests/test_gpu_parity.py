@@ -362,15 +362,21 @@ def test_subspace_near_ritz_basis(dev, cplx):
 
 @pytest.mark.slow
 def test_gamma_96c_256b_full_size(dev):
-    """The benchmark workload at full size, in the benchmark's launch configuration."""
+    """The benchmark workload at full size, in the benchmark's launch configuration: the
+    8192 MB digit-plane scratch (one K block per Gram, one rotation block) and the step as one
+    pawfd_rr_step call."""
     w = synth.WORKLOADS["gamma-96c-256b"]
     s = w.system()
     psi = w.psi(s)
     nb = w.nbands
     ctx = ctx_for(s, nb, dev)
+    ctx.set_option("tc_scratch_mb", 8192)
     psi_d = to_dev(psi, dev)
-    res = ctx.rayleigh_ritz(psi_d, keep_matrices=True)
+    res = dict(ctx.rr_step(psi_d))
+    hpsi, spsi, P_d = ctx.apply_hs(psi_d)
+    res["Hnm"], res["Snm"] = ctx.gram_hs(psi_d, hpsi, P_d)
     torch.cuda.synchronize(dev)
+    assert torch.equal(hpsi, res["Hpsi"]) and torch.equal(spsi, res["Spsi"])
     # sampled bands for the grid operators (bands are independent)
     idx = [0, 1, 77, 128, 255]
     ref_H, ref_P = O.apply_H(s, psi[idx])
@@ -392,9 +398,9 @@ def test_gamma_96c_256b_full_size(dev):
     assert_close_bands(rot, ref_rot, len(idx))
     # the ten repeated iterations of the workload reproduce the first eigenvalues
     eps0 = res["eps"].clone()
-    cur = res["psi_rot"]
+    cur = res["psi_rot"].clone()
     for _ in range(2):
-        r2 = ctx.rayleigh_ritz(cur)
+        r2 = ctx.rr_step(cur)
         assert torch.max(torch.abs(r2["eps"] - eps0)).item() <= 1e-10
         cur = r2["psi_rot"].clone()
     ctx.close()
