@@ -83,3 +83,24 @@ def test_array_bytes():
     inst = synth.Instance((10, 11, 12), 7, 2, 0, True, (0.0, 0.0, 0.0))
     assert serve.array_bytes(inst, "mixed") == 4 * 1320 * 7 * 8 + 3 * 49 * 16 + 56
     assert serve.array_bytes(inst, "fp64") == 4 * 1320 * 7 * 16 + 3 * 49 * 16 + 56
+
+
+def test_bench_tile_area_counts_upper_triangle_tiles():
+    # the bench's count of the entries the Hermitian Gram kernel computes (128 x 96 tiles that
+    # hold an element with row <= column) against a brute-force enumeration
+    import bench
+    for nb in (1, 17, 96, 128, 150, 256, 300, 1024):
+        tiles = 0
+        for r0 in range(0, nb, 128):
+            for c0 in range(0, nb, 96):
+                if any(r <= c for r in range(r0, min(nb, r0 + 128)) for c in range(c0, min(nb, c0 + 96))):
+                    tiles += 1
+        assert bench.sg_tiles_area(nb) == tiles * 128 * 96, nb
+
+
+def test_free_grid_is_the_bare_operator():
+    s = synth.make_system((12, 10, 8), (6.0, 5.0, 4.0), 3, synth.PSET_SP, seed=5, k=(0.1, 0.0, 0.2), complex_wf=True)
+    f = synth.free_grid(s)
+    assert f.natoms == 0 and f.nproj_total == 0 and not f.complex_wf and tuple(f.k) == (0.0, 0.0, 0.0)
+    assert np.all(f.vloc == 0) and f.vloc.shape == s.vloc.shape and tuple(f.n) == tuple(s.n)
+    assert tuple(f.cell) == tuple(s.cell)
