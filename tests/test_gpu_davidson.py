@@ -103,3 +103,25 @@ def test_davidson_iteration_against_dense_spectrum(dev, case):
     ctx.sync()
     assert np.sum(eps.cpu().numpy() - exact[:nb]) < first / 50
     ctx.close()
+
+
+def test_davidson_step_mixed_form(dev):
+    """The step on FP32 bands (mixed context): residual norms, the 2n Ritz values and the
+    S-orthonormal output against the FP64 oracle step on the same FP32-rounded input, to the
+    FP32 level (the corrections are formed from FP32 H psi and S psi)."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=671)
+    nb = 24
+    rr = O.rayleigh_ritz(s, synth.make_psi(s, nb, 672))
+    psi32 = rr["psi_rot"].astype(np.float32)
+    ref = O.davidson_step(s, psi32.astype(np.float64), rr["eps"])
+    ctx = api.Context(s, max_bands=2 * nb, device=dev, precision="mixed")
+    w = gpu_step(ctx, psi32, rr["eps"], nb, dev)
+    assert np.allclose(w["rnorm"].cpu().numpy(), ref["rnorm"], rtol=1e-5, atol=0)
+    eps = w["eps"].cpu().numpy()
+    scale = max(1.0, np.max(np.abs(ref["eps"])))
+    assert np.max(np.abs(eps - ref["eps"])) <= 1e-5 * scale, np.max(np.abs(eps - ref["eps"]))
+    out = w["psi_out"].cpu().numpy().astype(np.float64)
+    check = O.rayleigh_ritz(s, out)
+    assert np.max(np.abs(check["Snm"] - np.eye(nb))) <= 1e-5
+    ctx.close()
