@@ -587,6 +587,25 @@ def test_davidson_iteration_converges_from_above(case):
     assert st["rnorm"].max() < r0 / 15
 
 
+def test_davidson_weights_from_the_dense_diagonal():
+    # d(r) is the diagonal of the dense T + v (Kronecker sums of the published weights, no
+    # atoms), the floor a tenth of the diagonal of T alone; eps values on both sides of the
+    # floor, and the float32 arithmetic of the reading (so a float32-level tolerance)
+    s = small_system(**TINY["bloch"])
+    Tv, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=True, vloc=s.vloc))
+    T0, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=True, vloc=np.zeros_like(s.vloc)))
+    d = np.real(np.diag(Tv))
+    t0 = np.real(np.diag(T0))
+    assert np.allclose(t0, t0[0], rtol=1e-15, atol=0) and t0[0] > 0
+    floor = t0[0] / 10
+    eps = np.array([d.min() - 7.0, np.median(d) - floor, d.max() - 0.5 * floor, d.max() + 3.0])
+    w = O.davidson_weights(s, eps)
+    den = d[None, :] - eps[:, None]
+    expect = -1.0 / np.maximum(den, floor)
+    assert np.any(den > floor) and np.any(den < floor)
+    assert np.allclose(w, expect, rtol=2e-6, atol=0)
+
+
 def test_davidson_fixed_point_is_exact_eigenvectors():
     s = small_system(**TINY["bloch"])
     H, S = dense_operators(s)
