@@ -132,6 +132,35 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(seconds, world, dev):
+    """The job's timed region: the longest of the ranks' own timed regions (an all-reduce MAX
+    over the process group in float64; the identity for one rank)."""
+    if world == 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput in 1e9 units per second: the units all ranks processed (each rank
+    the same, weak scaling) over the job's time."""
+    return units_per_rank * world / seconds / 1e9
+
+
+def single_gpu_arm(name):
+    """Workloads measured on one GPU only: under a multi-rank launch, rank 0 runs them and the
+    other ranks return at once (True when this rank should run)."""
+    world, rank, _ = dist_env()
+    if world > 1 and rank != 0:
+        return False
+    if world > 1:
+        print("%s: a single-GPU workload; rank 0 runs it alone" % name, file=sys.stderr, flush=True)
+    return True
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -293,15 +322,11 @@ def run_gpu(args):
     ctx.sync()
     latest_idx = (args.warmup + 2 * args.steps) % 2   # the newest rotated bands, and their eps
     eps_latest = work["eps"].clone()
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = tt.item()
+    elapsed = max_over_ranks(elapsed, world, dev)
     names = ["apply_HS", "gram_HS", "subspace_diag", "rotate"]
     stages = {nm: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks) for i, nm in enumerate(names)}
 
-    units = float(nb) * K * args.steps * world
-    value = units / elapsed / 1e9
+    value = job_throughput(float(nb) * K * args.steps, world, elapsed)
     mixed = args.precision == "mixed"
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -568,13 +593,10 @@ def run_batch(args):
     for b in batches:
         b.sync()
     elapsed = evs[0].elapsed_time(evs[-1]) * 1e-3
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = tt.item()
+    elapsed = max_over_ranks(elapsed, world, dev)
     per_launch = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     units = sum(inst.npoints * inst.nbands for inst in insts)
-    value = units * args.steps * world / elapsed / 1e9
+    value = job_throughput(units * args.steps, world, elapsed)
     rr = len(insts) * args.steps * world / elapsed
     flops = sum(contraction_bf16_flops(inst, args.precision) for inst in insts)
     peaks = load_peaks()
@@ -995,14 +1017,10 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
-    elif args.workload == "served":
-        run_served(args)
-    elif args.workload == "davidson":
-        run_davidson(args)
-    elif args.workload == "density":
-        run_density(args)
-    elif args.workload == "poisson":
-        run_poisson(args)
+    elif args.workload in ("served", "davidson", "density", "poisson"):
+        if single_gpu_arm(args.workload):
+            {"served": run_served, "davidson": run_davidson, "density": run_density,
+             "poisson": run_poisson}[args.workload](args)
     else:
         run_gpu(args)
 
