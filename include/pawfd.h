@@ -26,6 +26,10 @@
  *     failure (Cholesky pivot, eigensolver sweep cap, bounded wait) is recorded in the
  *     context and returned by pawfd_sync() (and by the next call that synchronizes).
  *   - Inputs and outputs may not alias unless stated.
+ *   - A NULL context (or batch) is checked before anything else and touches no device:
+ *     calls returning int give PAWFD_EINVAL, pawfd_nproj_total and pawfd_launch_count give
+ *     PAWFD_EINVAL, pawfd_batch_is_graph and pawfd_batch_kernel_count give 0, and
+ *     pawfd_last_error / pawfd_batch_last_error give a fixed text.
  */
 #ifndef PAWFD_H
 #define PAWFD_H
@@ -87,7 +91,12 @@ typedef struct {
 } pawfd_system_desc;
 
 /* Create a context for one system; stream is a cudaStream_t (NULL = legacy default stream).
- * On success *out owns device tables sized for max_bands bands. */
+ * On success *out owns device tables sized for max_bands bands.  The description is checked
+ * on the host before any CUDA call; PAWFD_EINVAL (with *out = NULL and the reason on stderr)
+ * for a NULL out or desc, a grid size < 1 or above 2^31 - 1 points, a cell length <= 0, an
+ * unknown dtype, a real dtype with k != 0, max_bands < 1, a NULL vloc, natoms < 0, missing
+ * atom arrays, nproj outside 1..32, a box size < 1, or proj_off / dmat_off offsets that do
+ * not match the box sizes and nproj.  PAWFD_ENOMEM or PAWFD_EDEVICE for device failures. */
 int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* desc, void* stream);
 int pawfd_destroy(pawfd_ctx* ctx);
 int pawfd_set_stream(pawfd_ctx* ctx, void* stream);
