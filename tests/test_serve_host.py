@@ -43,10 +43,16 @@ def test_scheduler_never_exceeds_budget_and_admits_first_fit():
     for job in jobs:
         sch.arrive(job)
         while True:
+            window, free, full = list(sch.queue)[: sch.lookahead], sch.free_bytes(), len(sch.active) >= 6
             pick = sch.pick(need, no_reclaim)
             if pick is None:
+                # nothing in the window fits (or every slot is taken)
+                assert full or all(need(j) > free for j in window)
                 break
             # first fit: no earlier waiting job within the lookahead would have fit
+            pos = window.index(pick)
+            assert need(pick) <= free and all(need(j) > free for j in window[:pos])
+            assert pick not in sch.queue
             sch.admit(pick, need(pick))
             running.append(pick)
             assert sch.used <= sch.budget and len(sch.active) <= 6
@@ -104,3 +110,14 @@ def test_free_grid_is_the_bare_operator():
     assert f.natoms == 0 and f.nproj_total == 0 and not f.complex_wf and tuple(f.k) == (0.0, 0.0, 0.0)
     assert np.all(f.vloc == 0) and f.vloc.shape == s.vloc.shape and tuple(f.n) == tuple(s.n)
     assert tuple(f.cell) == tuple(s.cell)
+
+
+def test_latency_stats_over_the_jobs_after_the_warmup():
+    finished = [1.5, 2.0, 4.0, 3.5, 9.0]
+    recs = [serve.JobRecord(serve.Job(i, float(i), 0, i), admitted=float(i), finished=f) for i, f in enumerate(finished)]
+    st = serve.latency_stats(recs, warmup=1.0)
+    lat = np.array(finished[1:]) - np.arange(1, 5)      # finished - arrival of jobs 1..4
+    assert st["jobs"] == 4
+    assert abs(st["p50_ms"] - 1e3 * np.median(lat)) < 1e-9
+    assert abs(st["mean_ms"] - 1e3 * lat.mean()) < 1e-9
+    assert serve.latency_stats(recs, warmup=10.0) == {"jobs": 0}
