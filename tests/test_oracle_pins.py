@@ -492,6 +492,9 @@ def test_refine_exact_eigenvectors_have_zero_residual():
     assert np.allclose(res["eps"], lams, rtol=0, atol=1e-11)
     assert np.allclose(res["theta"], lams, rtol=0, atol=1e-11)
     assert np.all(res["resid"] <= 1e-11 * lams.max())
+    # the Rayleigh quotient does not depend on a band's norm (<psi|H|psi> / <psi|S|psi>)
+    scaled = O.refine(s, psi * np.array([0.5, 2.0, 3.0, 0.25]).reshape((-1,) + (1,) * (psi.ndim - 1)))
+    assert np.allclose(scaled["theta"], lams, rtol=0, atol=1e-11)
 
 
 def test_refine_residual_of_mixed_plane_waves():
