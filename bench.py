@@ -944,11 +944,40 @@ def run_poisson(args):
 # ------------------------------------------------------------------------------------------
 # CPU oracle baseline / reference arm
 # ------------------------------------------------------------------------------------------
-def oracle_step_time(system, psi):
+def oracle_step_time(system, psi, stages=None):
+    """Seconds of one full oracle Rayleigh-Ritz step.  The step is made of the oracle's own
+    calls in the order of its Rayleigh-Ritz step (H psi, S psi, the two Gram matrices, the
+    subspace diagonalization, the rotation), each timed; `stages` (a dict) collects them."""
     from oracle import oracle as O
-    t = time.perf_counter()
-    O.rayleigh_ritz(system, psi)
-    return time.perf_counter() - t
+    t = {} if stages is None else stages
+
+    def timed(name, f, *a):
+        t0 = time.perf_counter()
+        r = f(*a)
+        t[name] = t.get(name, 0.0) + time.perf_counter() - t0
+        return r
+    nb = psi.shape[0]
+    Hpsi, _ = timed("apply_H", O.apply_H, system, psi)
+    Spsi, _ = timed("apply_S", O.apply_S, system, psi)
+    Hnm = timed("gram_HS", O.gram, psi, Hpsi, system.dV, nb)
+    Snm = timed("gram_HS", O.gram, psi, Spsi, system.dV, nb)
+    _, C, _ = timed("subspace_diag", O.subspace_diag, Hnm, Snm)
+    timed("rotate", O.rotate, psi, C)
+    return sum(t[k] for k in ("apply_H", "apply_S", "gram_HS", "subspace_diag", "rotate"))
+
+
+def oracle_small_one_thread():
+    """Seconds of one oracle Rayleigh-Ritz step of the 24^3 x 16 workload on one host thread
+    (OMP_NUM_THREADS=1 in a child process), or None if that run fails."""
+    code = ("import sys, time; sys.path.insert(0, %r); import bench; from paper_2310_14776_gb300 import synth; "
+            "w = synth.WORKLOADS['gamma-24c-16b']; s = w.system(); p = w.psi(s); bench.oracle_step_time(s, p); "
+            "print(min(bench.oracle_step_time(s, p) for _ in range(3)))" % ROOT)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=dict(os.environ, OMP_NUM_THREADS="1"),
+                           capture_output=True, text=True, timeout=120)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
 
 
 def oracle_sample(system, w, precision, budget=2.3e8):
@@ -967,9 +996,13 @@ def cpu_baseline(system, w, precision):
     from oracle import oracle as O
     O.build()
     nb_s, psi = oracle_sample(system, w, precision)
-    t = oracle_step_time(system, psi)
+    stages = {}
+    t = oracle_step_time(system, psi, stages)
+    t1 = oracle_small_one_thread()
     return {"value": system.npoints * nb_s / t / 1e9, "unit": UNIT, "cores": O.num_threads(),
-            "kind": "oracle", "seconds": t,
+            "kind": "oracle", "seconds": t, "stages_s": stages,
+            "one_thread_24c_16b": {"seconds": t1, "value": 24 ** 3 * 16 / t1 / 1e9 if t1 else None,
+                                   "how": "best of 3 oracle RR steps of the 24^3 x 16 workload, OMP_NUM_THREADS=1"},
             "sample": "one full FP64 Rayleigh-Ritz step (apply_H, apply_S, two Gram matrices, subspace diag, "
                       "rotation) of the %s workload on %d of its %d bands, on the host cores"
                       % (w.name, nb_s, w.nbands)}
