@@ -121,3 +121,15 @@ def test_latency_stats_over_the_jobs_after_the_warmup():
     assert abs(st["p50_ms"] - 1e3 * np.median(lat)) < 1e-9
     assert abs(st["mean_ms"] - 1e3 * lat.mean()) < 1e-9
     assert serve.latency_stats(recs, warmup=10.0) == {"jobs": 0}
+
+
+def test_bench_oracle_stage_timing():
+    # the CPU baseline's step is the oracle's own calls, each timed; the total is their sum
+    import bench
+    w = synth.WORKLOADS["gamma-24c-16b"]
+    s = w.system()
+    stages = {}
+    total = bench.oracle_step_time(s, w.psi(s, nb=4), stages)
+    assert set(stages) == {"apply_H", "apply_S", "gram_HS", "subspace_diag", "rotate"}
+    assert all(v > 0 for v in stages.values())
+    assert abs(total - sum(stages.values())) < 1e-12
