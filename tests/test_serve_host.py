@@ -133,3 +133,17 @@ def test_bench_oracle_stage_timing():
     assert set(stages) == {"apply_H", "apply_S", "gram_HS", "subspace_diag", "rotate"}
     assert all(v > 0 for v in stages.values())
     assert abs(total - sum(stages.values())) < 1e-12
+
+
+def test_splitmix64_matches_the_published_sequence():
+    # the generator's mixing function is SplitMix64's output function: with the state advanced
+    # by the golden-ratio increment from seed 0, the first outputs of the published generator
+    # (Steele, Lea & Flood, OOPSLA 2014; the widely used splitmix64.c) are these
+    g = np.uint64(0x9E3779B97F4A7C15)
+    with np.errstate(over="ignore"):
+        z = synth._mix64(np.array([g * np.uint64(i) for i in (1, 2, 3)], dtype=np.uint64))
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    # element i of a stream does not depend on where the draw starts
+    a = synth.uniform01(7, synth.STREAM_PSI_RE, 0, 100)
+    b = synth.uniform01(7, synth.STREAM_PSI_RE, 40, 60)
+    assert np.array_equal(a[40:], b) and np.all((a >= 0) & (a < 1))
