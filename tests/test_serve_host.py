@@ -147,3 +147,13 @@ def test_splitmix64_matches_the_published_sequence():
     a = synth.uniform01(7, synth.STREAM_PSI_RE, 0, 100)
     b = synth.uniform01(7, synth.STREAM_PSI_RE, 40, 60)
     assert np.array_equal(a[40:], b) and np.all((a >= 0) & (a < 1))
+
+
+def test_projector_radial_normalisation_by_quadrature():
+    # N^2 int_0^inf r^(2l+2) exp(-r^2 / sigma^2) dr = 1 (the untruncated projector has unit norm)
+    from scipy.integrate import quad
+    for l in (0, 1, 2):
+        for sigma in (0.5, 0.8):
+            N = synth.radial_norm(l, sigma)
+            val, err = quad(lambda r: N * N * r ** (2 * l + 2) * np.exp(-r * r / sigma ** 2), 0, np.inf)
+            assert abs(val - 1.0) < 1e-10, (l, sigma, val)
