@@ -157,3 +157,16 @@ def test_projector_radial_normalisation_by_quadrature():
             N = synth.radial_norm(l, sigma)
             val, err = quad(lambda r: N * N * r ** (2 * l + 2) * np.exp(-r * r / sigma ** 2), 0, np.inf)
             assert abs(val - 1.0) < 1e-10, (l, sigma, val)
+
+
+def test_real_harmonics_are_orthonormal_on_the_sphere():
+    # Gauss-Legendre in cos(theta) x uniform phi integrates these polynomials exactly
+    mu, wmu = np.polynomial.legendre.leggauss(12)
+    phi = np.arange(24) * (2 * np.pi / 24)
+    M, P = np.meshgrid(mu, phi, indexing="ij")
+    W = np.outer(wmu, np.full(24, 2 * np.pi / 24))
+    st = np.sqrt(1 - M * M)
+    x, y, z = st * np.cos(P), st * np.sin(P), M
+    Y = [f for l in (0, 1, 2) for f in synth.solid_harmonics(l, x, y, z)]
+    G = np.array([[np.sum(W * a * b) for b in Y] for a in Y])
+    assert np.allclose(G, np.eye(9), rtol=0, atol=1e-13)
