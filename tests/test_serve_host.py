@@ -1,5 +1,7 @@
-"""Host-side logic of the batched and served forms (no GPU): seeded instance sizes, the
-Poisson job stream, and the scheduler's HBM budget and admission rules."""
+"""Host-side logic (no GPU): the batched and served forms (seeded instance sizes, the Poisson
+job stream, the scheduler's HBM budget and admission rules, latency statistics), the bench's
+helpers (tile count, oracle stage timing), and the seeded input generator (SplitMix64,
+projector normalisation, real harmonics, the free grid of the Poisson solve)."""
 import numpy as np
 
 from paper_2310_14776_gb300 import serve, synth
