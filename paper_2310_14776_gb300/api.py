@@ -125,6 +125,8 @@ class Context:
     def project(self, psi, P=None):
         nb = self._bands(psi, "psi")
         P = torch.empty((self.Ip, nb), dtype=self.dtype, device=self.device) if P is None else P
+        if P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous() or P.device != self.device:
+            raise ValueError("P must be a contiguous [Ip, nb] tensor of the band dtype on the device")
         self._call(self.lib.pawfd_project, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(P.data_ptr()))
         return P
 
@@ -252,11 +254,14 @@ class Context:
         residual)."""
         if rho.numel() != self.K or rho.dtype != torch.float64 or rho.device != self.device:
             raise ValueError("rho must hold K float64 values on the device")
+        rho = rho.contiguous()          # held until the call returns
         v = torch.empty(self.K, dtype=torch.float64, device=self.device) if v is None else v
+        if v.numel() != self.K or v.dtype != torch.float64 or v.device != self.device or not v.is_contiguous():
+            raise ValueError("v must be a contiguous float64 tensor of K values on the device")
         work = torch.empty(4 * self.K + 304, dtype=torch.float64, device=self.device)
         it = ctypes.c_int(0)
         res = ctypes.c_double(0.0)
-        self._call(self.lib.pawfd_poisson, ctypes.c_void_p(rho.contiguous().data_ptr()), ctypes.c_void_p(v.data_ptr()),
+        self._call(self.lib.pawfd_poisson, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(v.data_ptr()),
                    float(tol), int(maxiter), ctypes.c_void_p(work.data_ptr()), ctypes.byref(it), ctypes.byref(res))
         return v, it.value, res.value
 
@@ -266,8 +271,8 @@ class Context:
         if f.numel() != nb or f.dtype != torch.float64 or f.device != self.device:
             raise ValueError("f must hold nb float64 values on the device")
         rho = torch.empty(self.K, dtype=torch.float64, device=self.device) if rho is None else rho
-        if rho.numel() != self.K or rho.dtype != torch.float64 or not rho.is_contiguous():
-            raise ValueError("rho must be a contiguous float64 tensor of K values")
+        if rho.numel() != self.K or rho.dtype != torch.float64 or not rho.is_contiguous() or rho.device != self.device:
+            raise ValueError("rho must be a contiguous float64 tensor of K values on the device")
         self._call(self.lib.pawfd_density, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(f.data_ptr()),
                    ctypes.c_void_p(rho.data_ptr()))
         return rho
@@ -275,10 +280,15 @@ class Context:
     def atomic_density(self, P, f, D=None):
         """D^a = sum_n f_n conj(P_an) P_an^T per atom, packed like dH / dS (pawfd_atomic_density)."""
         nb = f.numel()
-        if P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous():
-            raise ValueError("P must be a contiguous [Ip, nb] tensor of the band dtype")
+        if f.dtype != torch.float64 or f.device != self.device or not f.is_contiguous():
+            raise ValueError("f must hold nb float64 values on the device")
+        if P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous() or P.device != self.device:
+            raise ValueError("P must be a contiguous [Ip, nb] tensor of the band dtype on the device")
         total = int(self._dmat_total)
         D = torch.empty(max(total, 1), dtype=self.mat_dtype, device=self.device) if D is None else D
+        if D.numel() < total or D.dtype != self.mat_dtype or not D.is_contiguous() or D.device != self.device:
+            raise ValueError("D must be a contiguous %s tensor of at least %d values on the device"
+                             % (self.mat_dtype, total))
         self._call(self.lib.pawfd_atomic_density, ctypes.c_void_p(P.data_ptr()), nb, ctypes.c_void_p(f.data_ptr()),
                    ctypes.c_void_p(D.data_ptr()))
         return D[:total]
