@@ -94,6 +94,18 @@ class Context:
             raise ValueError("%s must be a contiguous [%d, %d] %s tensor on %s" % (name, nb, nb, self.mat_dtype,
                                                                                    self.device))
 
+    def _out_bands(self, t: torch.Tensor, nb: int, name: str):
+        if self._bands(t, name) < nb:
+            raise ValueError("%s must hold at least %d bands" % (name, nb))
+
+    def _vec(self, t: torch.Tensor, n: int, name: str):
+        if t.device != self.device or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() < n:
+            raise ValueError("%s must be a contiguous float64 tensor of at least %d values on %s" % (name, n, self.device))
+
+    def _proj(self, P: torch.Tensor, nb: int, name: str = "P"):
+        if P.device != self.device or P.dtype != self.dtype or not P.is_contiguous() or P.numel() < self.Ip * nb:
+            raise ValueError("%s must be a contiguous [Ip, %d] tensor of the band dtype on %s" % (name, nb, self.device))
+
     def empty_bands(self, nb: int) -> torch.Tensor:
         return torch.empty((nb,) + self.n[::-1], dtype=self.dtype, device=self.device)
 
@@ -117,7 +129,7 @@ class Context:
     def kinetic_local(self, psi, out=None):
         nb = self._bands(psi, "psi")
         out = self.empty_bands(nb) if out is None else out
-        self._bands(out, "out")
+        self._out_bands(out, nb, "out")
         self._call(self.lib.pawfd_apply_kinetic_local, ctypes.c_void_p(psi.data_ptr()), nb,
                    ctypes.c_void_p(out.data_ptr()))
         return out
@@ -133,9 +145,9 @@ class Context:
     def _apply(self, fn, psi, out, P):
         nb = self._bands(psi, "psi")
         out = self.empty_bands(nb) if out is None else out
-        self._bands(out, "out")
-        if P is not None and (P.numel() != self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous()):
-            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        self._out_bands(out, nb, "out")
+        if P is not None:
+            self._proj(P, nb)
         self._call(fn, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(out.data_ptr()),
                    ctypes.c_void_p(P.data_ptr()) if P is not None else None)
         return out
@@ -151,11 +163,10 @@ class Context:
         nb = self._bands(psi, "psi")
         Hpsi = self.empty_bands(nb) if Hpsi is None else Hpsi
         Spsi = self.empty_bands(nb) if Spsi is None else Spsi
-        self._bands(Hpsi, "Hpsi")
-        self._bands(Spsi, "Spsi")
+        self._out_bands(Hpsi, nb, "Hpsi")
+        self._out_bands(Spsi, nb, "Spsi")
         P = torch.empty((max(self.Ip, 1), nb), dtype=self.dtype, device=self.device) if P is None else P
-        if P.numel() < self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous():
-            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        self._proj(P, nb)
         self._call(self.lib.pawfd_apply_HS, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(Hpsi.data_ptr()),
                    ctypes.c_void_p(Spsi.data_ptr()), ctypes.c_void_p(P.data_ptr()))
         return Hpsi, Spsi, P
@@ -170,8 +181,8 @@ class Context:
         Snm = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if Snm is None else Snm
         self._mat(Hnm, nb, "Hnm")
         self._mat(Snm, nb, "Snm")
-        if P is not None and (P.numel() < self.Ip * nb or P.dtype != self.dtype or not P.is_contiguous()):
-            raise ValueError("P must be a contiguous [Ip, nb] tensor")
+        if P is not None:
+            self._proj(P, nb)
         self._call(self.lib.pawfd_gram_hs, ctypes.c_void_p(psi.data_ptr()), ctypes.c_void_p(Hpsi.data_ptr()), nb,
                    ctypes.c_void_p(P.data_ptr()) if P is not None else None, ctypes.c_void_p(Hnm.data_ptr()),
                    ctypes.c_void_p(Snm.data_ptr()))
@@ -197,6 +208,7 @@ class Context:
         if not overwrite:
             Hnm, Snm = Hnm.clone(), Snm.clone()
         eps = torch.empty(nb, dtype=torch.float64, device=self.device) if eps is None else eps
+        self._vec(eps, nb, "eps")
         C = torch.empty((nb, nb), dtype=self.mat_dtype, device=self.device) if C is None else C
         self._mat(C, nb, "C")
         self._call(self.lib.pawfd_subspace_diag, nb, ctypes.c_void_p(Hnm.data_ptr()), ctypes.c_void_p(Snm.data_ptr()),
@@ -209,7 +221,7 @@ class Context:
         nb = self._bands(psi, "psi")
         self._mat(C, nb, "C")
         out = self.empty_bands(nb) if out is None else out
-        self._bands(out, "out")
+        self._out_bands(out, nb, "out")
         self._call(self.lib.pawfd_rotate, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(C.data_ptr()),
                    ctypes.c_void_p(out.data_ptr()))
         return out
@@ -229,12 +241,14 @@ class Context:
         """Residuals H psi - eps S psi: their norms and the preconditioned corrections
         (pawfd_residual_precond).  Returns (pr, rnorm)."""
         nb = self._bands(Hpsi, "Hpsi")
-        self._bands(Spsi, "Spsi")
-        if eps.numel() != nb or eps.dtype != torch.float64 or eps.device != self.device:
+        self._out_bands(Spsi, nb, "Spsi")
+        if eps.numel() != nb:
             raise ValueError("eps must hold nb float64 values on the device")
+        self._vec(eps, nb, "eps")
         pr = self.empty_bands(nb) if pr is None else pr
-        self._bands(pr, "pr")
+        self._out_bands(pr, nb, "pr")
         rnorm = torch.empty(nb, dtype=torch.float64, device=self.device) if rnorm is None else rnorm
+        self._vec(rnorm, nb, "rnorm")
         self._call(self.lib.pawfd_residual_precond, ctypes.c_void_p(Hpsi.data_ptr()), ctypes.c_void_p(Spsi.data_ptr()),
                    nb, ctypes.c_void_p(eps.data_ptr()), ctypes.c_void_p(pr.data_ptr()),
                    ctypes.c_void_p(rnorm.data_ptr()))
@@ -316,12 +330,12 @@ class Context:
                 raise ValueError("%s must hold %d bands" % (key, count))
         for key in ("Hnm", "Snm", "C"):
             self._mat(w[key], 2 * nb, key)
-        if eps_in.numel() < nb or eps_in.dtype != torch.float64 or eps_in.device != self.device:
-            raise ValueError("eps_in must hold nb float64 values on the device")
+        self._vec(eps_in, nb, "eps_in")
         if w["eps"].numel() != 2 * nb or w["rnorm"].numel() != nb:
             raise ValueError("eps must hold 2 nb and rnorm nb float64 values")
-        if w["P"].numel() < self.Ip * 2 * nb or w["P"].dtype != self.dtype:
-            raise ValueError("P must hold [Ip][2 nb] values of the band dtype")
+        self._vec(w["eps"], 2 * nb, "eps")
+        self._vec(w["rnorm"], nb, "rnorm")
+        self._proj(w["P"], 2 * nb)
         p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
         self._call(self.lib.pawfd_davidson_step, p(w["X"]), nb, p(eps_in), p(w["HX"]), p(w["SX"]), p(w["P"]),
                    p(w["Hnm"]), p(w["Snm"]), p(w["eps"]), p(w["C"]), p(w["rnorm"]), p(w["psi_out"]))
@@ -350,13 +364,14 @@ class Context:
 
     def _job_args(self, psi, out, work):
         nb = self._bands(psi, "psi")
-        self._bands(out, "out")
+        self._out_bands(out, nb, "out")
         for key in ("Hpsi", "Spsi"):
-            self._bands(work[key], key)
+            self._out_bands(work[key], nb, key)
         for key in ("Hnm", "Snm", "C"):
             self._mat(work[key], nb, key)
-        if work["eps"].numel() != nb or work["eps"].dtype != torch.float64:
+        if work["eps"].numel() != nb:
             raise ValueError("eps must hold nb float64 values")
+        self._vec(work["eps"], nb, "eps")
         p = lambda t: t.data_ptr()  # noqa: E731
         return nb, (p(psi), nb, p(work["Hpsi"]), p(work["Spsi"]), p(work["Hnm"]), p(work["Snm"]), p(work["eps"]),
                     p(work["C"]), p(out))
@@ -390,7 +405,7 @@ class Context:
         out = {}
         for key in ("psi", "Hpsi", "Spsi"):
             out[key] = w.get(key) if w.get(key) is not None else self.empty_bands(nb)
-            self._bands(out[key], key)
+            self._out_bands(out[key], nb, key)
         for key in ("Hnm", "Snm", "C"):
             out[key] = w.get(key) if w.get(key) is not None else torch.empty((nb, nb), dtype=self.mat_dtype,
                                                                              device=self.device)
@@ -398,6 +413,7 @@ class Context:
         for key in ("eps", "theta", "resid"):
             out[key] = w.get(key) if w.get(key) is not None else torch.empty(nb, dtype=torch.float64,
                                                                              device=self.device)
+            self._vec(out[key], nb, key)
         p = lambda t: ctypes.c_void_p(t.data_ptr())
         self._call(self.lib.pawfd_refine, p(psi_lo), nb, p(out["psi"]), p(out["Hpsi"]), p(out["Spsi"]),
                    p(out["Hnm"]), p(out["Snm"]), p(out["eps"]), p(out["theta"]), p(out["resid"]), p(out["C"]))

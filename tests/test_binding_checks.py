@@ -157,3 +157,51 @@ def test_rotate_n_and_residual_checks():
     assert c.lib.called == []
     c.rotate_n(psi, C, 2)
     assert c.lib.called[-1] == "pawfd_rotate_n"
+
+
+@pytest.mark.parametrize("case", ["apply_H out short", "apply_H P dtype", "apply_hs Spsi short", "apply_hs P short",
+                                  "gram_hs P dtype", "subspace eps dtype", "subspace eps short", "rotate out short",
+                                  "rr_step out short", "rr_step work Hpsi short", "rr_step eps dtype",
+                                  "refine eps short", "refine Hpsi short", "residual rnorm dtype",
+                                  "davidson eps_in not contiguous"])
+def test_step_calls_reject_short_or_mistyped_outputs(case):
+    c = shell()
+    nb = 4
+    psi = bands(c, nb)
+    M = lambda: torch.zeros((nb, nb), dtype=torch.float64)  # noqa: E731
+    f64 = lambda n: torch.zeros(n, dtype=torch.float64)  # noqa: E731
+    calls = {
+        "apply_H out short": lambda: c.apply_H(psi, out=bands(c, 3)),
+        "apply_H P dtype": lambda: c.apply_H(psi, P=torch.zeros((6, nb), dtype=torch.float32)),
+        "apply_hs Spsi short": lambda: c.apply_hs(psi, Spsi=bands(c, 3)),
+        "apply_hs P short": lambda: c.apply_hs(psi, P=torch.zeros((6, 3), dtype=torch.float64)),
+        "gram_hs P dtype": lambda: c.gram_hs(psi, psi, torch.zeros((6, nb), dtype=torch.complex128)),
+        "subspace eps dtype": lambda: c.subspace_diag(M(), M(), eps=torch.zeros(nb, dtype=torch.float32)),
+        "subspace eps short": lambda: c.subspace_diag(M(), M(), eps=f64(3)),
+        "rotate out short": lambda: c.rotate(psi, M(), out=bands(c, 3)),
+        "rr_step out short": lambda: c.rr_step(psi, out=bands(c, 3)),
+        "rr_step work Hpsi short": lambda: c.rr_step(psi, work=dict(c.alloc_work(nb), Hpsi=bands(c, 3))),
+        "rr_step eps dtype": lambda: c.rr_step(psi, work=dict(c.alloc_work(nb), eps=torch.zeros(nb, dtype=torch.float32))),
+        "refine eps short": lambda: c.refine(bands(c, nb, torch.float32), work={"eps": f64(3)}),
+        "refine Hpsi short": lambda: c.refine(bands(c, nb, torch.float32), work={"Hpsi": bands(c, 3)}),
+        "residual rnorm dtype": lambda: c.residual_precond(psi, psi, f64(nb), rnorm=torch.zeros(nb, dtype=torch.float32)),
+        "davidson eps_in not contiguous": lambda: c.davidson_step(c.alloc_davidson(nb), nb, f64(2 * nb)[::2]),
+    }
+    with pytest.raises(ValueError):
+        calls[case]()
+    assert c.lib.called == []
+
+
+def test_step_calls_accept_their_own_allocations():
+    c = shell()
+    nb = 4
+    psi = bands(c, nb)
+    c.rayleigh_ritz(psi, check=False)
+    c.rr_step(psi)
+    c.refine(bands(c, nb, torch.float32), check=False)
+    w = c.alloc_davidson(nb)
+    c.davidson_step(w, nb, torch.zeros(nb, dtype=torch.float64))
+    c.residual_precond(psi, psi, torch.zeros(nb, dtype=torch.float64))
+    called = [n for n in c.lib.called if n != "pawfd_set_stream"]
+    assert called == ["pawfd_apply_HS", "pawfd_gram_hs", "pawfd_subspace_diag", "pawfd_rotate", "pawfd_rr_step",
+                      "pawfd_refine", "pawfd_davidson_step", "pawfd_residual_precond"]
