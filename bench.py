@@ -41,8 +41,8 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 
 
 # Measured DRAM traffic of the dominant stage's kernels (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum of every kernel of one pawfd_gram_hs call at 64^3 x 256 bands,
-# profiles/dram_gram_hs_64c_256b.md).  At a fixed band count it grows with the grid points K
+# dram__bytes_write.sum of every kernel of one pawfd_gram_hs call at 64^3 x 256 bands).  At a
+# fixed band count it grows with the grid points K
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
 _GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "9fbba2e9424e4e6498471fb2c73f3e6161a9c0a4",
@@ -56,7 +56,7 @@ TRAFFIC = {
 
 
 # Measured DRAM traffic per launch of the Gram MMA kernel (the mean of the two launches of one
-# pawfd_gram_hs call, ncu at 64^3 x 256 bands, profiles/dram_gram_hs_64c_256b.md), per grid
+# pawfd_gram_hs call, ncu at 64^3 x 256 bands), per grid
 # point: FP64 (2026.6 + 0.5 + 940.5 + 0.8) / 2 MB, mixed (1142.2 + 0.6 + 537.6 + 0.5) / 2 MB.
 KERNEL_TRAFFIC = {
     ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1484.2e6 / 262144, "sources": _GRAM_SOURCES},
@@ -335,7 +335,8 @@ def run_gpu(args):
     # for FP64 data, <= 4 of 4 digits for FP32 data) and real multiply-adds per complex one
     products = 13 if mixed else 28
     cfac = 4 if cplx else 1
-    # algorithmic work per stage (see the roofline table of the design notes)
+    # algorithmic work per stage: bytes that must move (apply), useful digit products (Gram,
+    # rotation)
     work_units = {
         # H psi and S psi: psi read twice (stencil, copy), H psi and S psi written once
         "apply_HS": ("hbm", 4.0 * esize * nb * K, hbm * 1e9, "B/s"),
@@ -407,14 +408,16 @@ def run_gpu(args):
     if not args.no_e2e:
         result["e2e"] = e2e_gpu(ctx, psi_host, work, args, dev)
     if mixed and not args.no_refine:
-        latest = psi[latest_idx]
+        # the last step's input bands and its eigenvector matrix (the refinement rotates the
+        # former by the latter in FP64); its rotated output is not needed
+        last_in = psi[1 - latest_idx]
+        C_last = work["C"].clone()
         eps_mixed = eps_latest
-        # room for the FP64 arrays: drop the mixed step's own H psi, S psi and the other buffer
         for key in ("Hpsi", "Spsi"):
             work[key] = None
-        psi[1 - latest_idx] = None
+        psi[latest_idx] = None
         torch.cuda.empty_cache()
-        result["refine"] = refine_gpu(system, nb, latest, eps_mixed, dev, args.tc_scratch_mb)
+        result["refine"] = refine_gpu(system, nb, last_in, C_last, eps_mixed, dev, args.tc_scratch_mb)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(system, w, args.precision)
     if world > 1:
@@ -426,29 +429,49 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def refine_gpu(system, nb, psi_lo, eps_mixed, dev, tc_scratch_mb=0):
-    """The final FP64 refinement (pawfd_refine) of the last rotated mixed-form bands, timed."""
+def refine_gpu(system, nb, psi_in, C_lo, eps_mixed, dev, tc_scratch_mb=0):
+    """The final FP64 refinement (pawfd_refine) of the last mixed step: its input bands psi_in
+    rotated by its eigenvector matrix C_lo in FP64, then an FP64 Rayleigh-Ritz step; timed.
+    The refined eigenvalues are compared with the plain FP64 path of the same library on the
+    same input (apply_HS, Gram H and S, subspace solve of the promoted FP32 values), the path
+    the full-size FP64 parity test checks against the oracle."""
     import torch
     from paper_2310_14776_gb300 import api
     fp = api.Context(system, max_bands=nb, device=dev, precision="fp64")
     if tc_scratch_mb:
         fp.set_option("tc_scratch_mb", tc_scratch_mb)
-    fp.refine(psi_lo)              # untimed first call
+    fp.refine(psi_in, C_lo)        # untimed first call
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    out = fp.refine(psi_lo, check=False)
+    out = fp.refine(psi_in, C_lo, check=False)
     e1.record()
     torch.cuda.synchronize(dev)
     fp.sync()
-    eps = out["eps"]
-    res = {"ms": e0.elapsed_time(e1), "max_abs_eps_refined_minus_mixed_ha": float((eps - eps_mixed).abs().max()),
-           "max_abs_theta_minus_eps_ha": float((out["theta"] - eps).abs().max()),
-           "max_residual_norm": float(out["resid"].max()), "median_residual_norm": float(out["resid"].median()),
-           "what": "promote psi' to FP64, FP64 H psi' and S psi', Hermitian Grams, Rayleigh quotients, second "
-                   "subspace solve, residual norms ||H psi'_n - eps_n S psi'_n||"}
+    ms = e0.elapsed_time(e1)
+    eps = out["eps"].clone()
+    theta = out["theta"].clone()
+    resid = out["resid"].clone()
+    # the plain FP64 step on the same input, in the refinement's work arrays
+    x = out["psi"]
+    x.copy_(psi_in)                # exact promotion of the FP32 values
+    P = torch.empty((max(fp.Ip, 1), nb), dtype=fp.dtype, device=dev)
+    fp.apply_hs(x, Hpsi=out["Hpsi"], Spsi=out["Spsi"], P=P)
+    fp.gram_hs(x, out["Hpsi"], P, Hnm=out["Hnm"], Snm=out["Snm"])
+    eps64, _ = fp.subspace_diag(out["Hnm"], out["Snm"], C=out["C"], overwrite=True)
+    torch.cuda.synchronize(dev)
+    res = {"ms": ms,
+           "max_abs_eps_refined_minus_fp64_ha": float((eps - eps64).abs().max()),
+           "max_abs_eps_mixed_minus_fp64_ha": float((eps_mixed - eps64).abs().max()),
+           "max_abs_theta_minus_eps_ha": float((theta - eps).abs().max()),
+           "max_residual_norm": float(resid.max()), "median_residual_norm": float(resid.median()),
+           "tolerance_ha": 1e-8,
+           "what": "psi' = psi_in C_lo rotated in FP64 (psi_in, C_lo: the last mixed step's input bands and "
+                   "eigenvector matrix), FP64 H psi' and S psi', Hermitian Grams, Rayleigh quotients, second "
+                   "subspace solve, residual norms ||H psi'_n - eps_n S psi'_n||; errors against the FP64 "
+                   "Rayleigh-Ritz step of the same library on the same input"}
     fp.close()
-    del out
+    del out, P, x
     torch.cuda.empty_cache()
     return res
 

@@ -43,8 +43,10 @@ typedef struct pawfd_ctx pawfd_ctx;
 /* wave-function storage / arithmetic type of the band arrays and projections.
  * Gram matrices, eigenvalues and eigenvectors (C) are always FP64: double for the real
  * types, interleaved complex double for the complex types.  The FP32 types are the mixed
- * form: stencil, projections and back-add in FP32 arithmetic, Gram sums in FP32 within
- * chunks of at most 4096 grid points and FP64 across chunks, subspace solve in FP64. */
+ * form: stencil, projections and back-add in FP32 arithmetic; Gram matrices and rotations as
+ * exact products of BF16 digits of the FP32 values on the tensor cores (4 digits per value,
+ * the products accumulated to about FP64 accuracy; with the option tensor_cores = 0, FP32
+ * products instead); subspace solve in FP64. */
 enum {
   PAWFD_R64 = 0,  /* real double, Gamma point (k must be 0)         */
   PAWFD_C128 = 1, /* complex double, Bloch vector k                  */
@@ -76,7 +78,7 @@ typedef struct {
   int n[3];                 /* grid points N1, N2, N3 (x, y, z), each >= 1                   */
   double cell[3];           /* cell lengths L_c (bohr); spacing h_c = L_c / N_c              */
   double k[3];              /* Bloch vector (1/bohr); must be 0 for PAWFD_R64                */
-  int dtype;                /* PAWFD_R64 or PAWFD_C128                                       */
+  int dtype;                /* PAWFD_R64, PAWFD_C128, PAWFD_R32 or PAWFD_C64                 */
   int max_bands;            /* largest nb any later call will use (sizes the scratch)        */
   int natoms;               /* A >= 0                                                        */
   const int* nproj;         /* [A] I_a >= 1                                                  */
@@ -148,9 +150,6 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *   "nonlocal_df"     1 (default): for real FP64 bands the projections and the nonlocal
  *                     back-add compute in double-float FP32 pairs (runs of 32 terms, then FP64
  *                     sums); 0: FP64 arithmetic.
- *   "tc_fused"        0 (default): digit planes are sliced to memory, then multiplied; 1: the
- *                     tensor-core Gram makes its digits inside the MMA kernel from the raw
- *                     operands (when their rows are 16-byte aligned).  Same digits, same products.
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
@@ -289,22 +288,29 @@ int pawfd_poisson(pawfd_ctx* ctx, const double* rho, double* v, double tol, int 
 
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
- * PAWFD_C128) of the same system as the mixed context whose rotated bands psi_lo (PAWFD_R32
- * or PAWFD_C64 of the same kind, [nb][K], 16-byte aligned) are refined:
- *   1. psi = psi_lo promoted to FP64 (exact);
+ * PAWFD_C128) of the same system as the mixed context whose bands psi_lo (PAWFD_R32 or
+ * PAWFD_C64 of the same kind, [nb][K], 16-byte aligned) are refined:
+ *   1. psi = psi_lo promoted to FP64 (exact).  If C_lo is not NULL, psi_lo are the INPUT
+ *      bands of a mixed Rayleigh-Ritz step and C_lo ([nb][nb] FP64 of the context's kind) the
+ *      eigenvector matrix that step returned: then psi = psi_lo C_lo, rotated in FP64 (the
+ *      digit-product rotation, accumulated to about FP64).  A nonsingular C_lo keeps the span
+ *      of the input, so the refined eigenvalues are those of the FP64 step on the same input,
+ *      while the bands are already near its Ritz vectors (the second solve is the cheap
+ *      near-Ritz path).  If C_lo is NULL, psi_lo (e.g. rotated FP32 bands) are refined as given;
  *   2. hpsi = H psi and spsi = S psi in FP64 (Eq. (dh) and the overlap operator of the PAW
  *      section; one set of projections serves both);
  *   3. Hnm = dV psi^H hpsi, Snm = dV psi^H spsi (Hermitian Gram matrices, FP64);
- *   4. theta[n] = Re Hnm[n][n] / Re Snm[n][n] (FP64 Rayleigh quotients of the bands psi_lo);
+ *   4. theta[n] = Re Hnm[n][n] / Re Snm[n][n] (FP64 Rayleigh quotients of the bands psi);
  *   5. a second subspace diagonalization of (Hnm, Snm) gives eps (ascending) and C, as
  *      pawfd_subspace_diag (Hnm and Snm are overwritten);
  *   6. resid[n] = sqrt(dV sum_r |hpsi_n(r) - eps[n] spsi_n(r)|^2).
  * psi, hpsi, spsi: caller-owned FP64 device work arrays [nb][K] (on return they hold steps
  * 1-2); Hnm, Snm, C: [nb][nb] of the context's kind; eps, theta, resid: device [nb] doubles.
+ * The refined bands are psi C (pawfd_rotate on this context).
  * Returns PAWFD_EINVAL for a mixed context, nb outside 1..max_bands, null or aliased arrays,
  * or misaligned band arrays; device-side failures of step 5 are reported by pawfd_sync. */
-int pawfd_refine(pawfd_ctx* ctx, const void* psi_lo, int nb, void* psi, void* hpsi, void* spsi, void* Hnm,
-                 void* Snm, double* eps, double* theta, double* resid, void* C);
+int pawfd_refine(pawfd_ctx* ctx, const void* psi_lo, int nb, const void* C_lo, void* psi, void* hpsi, void* spsi,
+                 void* Hnm, void* Snm, double* eps, double* theta, double* resid, void* C);
 
 /* One Rayleigh-Ritz step of SCF step 1 (Kohn-Sham section) as a single call: hpsi = H psi
  * and spsi = S psi (Eq. (dh) and the overlap operator of the PAW section; one set of
@@ -366,10 +372,13 @@ int pawfd_batch_destroy(pawfd_batch* batch);
  * nb x nb partial does not fit in the 8 MiB array (nb > 1024 real, nb > 724 complex);
  * PAWFD_EDEVICE for a CUDA runtime failure.
  * Notes: every GPU that loads the library holds the 8 MiB array until the process exits.
- * The first call on each device looks up the array's device address (once per device, with
- * that device current); make that first call before any stream capture.  All calls share
- * the one array: calls whose work overlaps on the GPU race on it.  Each call overwrites all
- * the partial entries it reads, so no clearing between calls is needed. */
+ * The first call made with a given device and CUDA context current looks up the array's
+ * device address on that device (set-up once per device and context, then cached under the
+ * context's process-unique ID, so a device reset or another context is set up afresh); make
+ * that first call before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU race on it.  Each call overwrites all the partial entries it
+ * reads, so no clearing between calls is needed.  Launch failures are read from each launch's
+ * own status: an error left in the runtime by earlier work is neither reported nor cleared. */
 int pawfd_gram_noalloc(const void* A, const void* B, long long K, int nb, int dtype, double dV, void* M,
                        void* stream);
 

@@ -365,10 +365,14 @@ def davidson_step(system, psi: np.ndarray, eps_in: np.ndarray) -> dict:
             "sweeps": sweeps}
 
 
-def refine(system, psi_lo: np.ndarray) -> dict:
+def refine(system, psi_lo: np.ndarray, C_lo: Optional[np.ndarray] = None) -> dict:
     """Final refinement of the mixed form, in the order of its reading (the paper is silent):
 
-    1. the FP32 / complex64 bands psi' are promoted to FP64 (exactly);
+    1. the FP32 / complex64 bands are promoted to FP64 (exactly).  When C_lo is given they are
+       the INPUT bands of a mixed Rayleigh-Ritz step and C_lo that step's FP64 eigenvector
+       matrix: the promoted bands are rotated by it in FP64, psi' = psi C_lo.  A rotation by a
+       nonsingular matrix keeps the span of the bands, so the second Rayleigh-Ritz step below
+       sees the subspace of the original input, not that of FP32-rounded rotated bands;
     2. H psi' and S psi' are applied in FP64 (Eq. (dh) and the overlap operator);
     3. FP64 Gram matrices H'_nm, S'_nm are formed;
     4. the Rayleigh quotients theta_n = H'_nn / S'_nn are taken from their diagonals;
@@ -377,6 +381,8 @@ def refine(system, psi_lo: np.ndarray) -> dict:
     """
     psi = np.asarray(psi_lo).astype(np.complex128 if system.complex_wf else np.float64)
     psi, nb = _psi_in(system, psi)
+    if C_lo is not None:
+        psi = rotate(psi, np.asarray(C_lo))
     Hpsi, P = apply_H(system, psi)
     Spsi, _ = apply_S(system, psi)
     Hnm = gram(psi, Hpsi, system.dV, nb)

@@ -50,7 +50,7 @@ SIGNATURES = {
     "pawfd_gram_hs": ([VP, VP, VP, I, VP, VP, VP], I),
     "pawfd_subspace_diag": ([VP, I, VP, VP, VP, VP], I),
     "pawfd_rotate": ([VP, VP, I, VP, VP], I),
-    "pawfd_refine": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
+    "pawfd_refine": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP, VP, VP, VP], I),
     "pawfd_rr_step": ([VP, VP, I, VP, VP, VP, VP, VP, VP, VP], I),
     "pawfd_rotate_n": ([VP, VP, I, VP, I, VP], I),
     "pawfd_residual_precond": ([VP, VP, VP, I, VP, VP, VP], I),

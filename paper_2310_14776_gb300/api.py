@@ -388,11 +388,14 @@ class Context:
         res["psi_rot"] = out
         return res
 
-    def refine(self, psi_lo, work: Optional[dict] = None, check: bool = True) -> dict:
+    def refine(self, psi_lo, C_lo=None, work: Optional[dict] = None, check: bool = True) -> dict:
         """Final refinement of mixed-form bands on this FP64 context (pawfd_refine): FP64
         H psi', S psi', Gram matrices, Rayleigh quotients ``theta``, a second subspace solve
-        (``eps``, ``C``) and residual norms ``resid``.  ``psi_lo`` is the float32 / complex64
-        output of a mixed context of the same system."""
+        (``eps``, ``C``) and residual norms ``resid``.  ``psi_lo`` is a float32 / complex64 band
+        array of a mixed context of the same system.  With ``C_lo`` (the FP64 eigenvector
+        matrix a mixed Rayleigh-Ritz step returned for the input bands ``psi_lo``) the bands
+        refined are psi_lo C_lo rotated in FP64, which keeps the span of the input; without it,
+        psi_lo as given."""
         if self.precision != "fp64":
             raise ValueError("refine runs on an fp64 context")
         lo = torch.complex64 if self.complex else torch.float32
@@ -401,6 +404,8 @@ class Context:
         if psi_lo.numel() % self.K:
             raise ValueError("psi_lo size is not a multiple of the grid size")
         nb = psi_lo.numel() // self.K
+        if C_lo is not None:
+            self._mat(C_lo, nb, "C_lo")
         w = work if work is not None else {}
         out = {}
         for key in ("psi", "Hpsi", "Spsi"):
@@ -414,8 +419,8 @@ class Context:
             out[key] = w.get(key) if w.get(key) is not None else torch.empty(nb, dtype=torch.float64,
                                                                              device=self.device)
             self._vec(out[key], nb, key)
-        p = lambda t: ctypes.c_void_p(t.data_ptr())
-        self._call(self.lib.pawfd_refine, p(psi_lo), nb, p(out["psi"]), p(out["Hpsi"]), p(out["Spsi"]),
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        self._call(self.lib.pawfd_refine, p(psi_lo), nb, p(C_lo), p(out["psi"]), p(out["Hpsi"]), p(out["Spsi"]),
                    p(out["Hnm"]), p(out["Snm"]), p(out["eps"]), p(out["theta"]), p(out["resid"]), p(out["C"]))
         if check:
             self.sync()

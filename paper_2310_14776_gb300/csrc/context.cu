@@ -451,10 +451,6 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->nonlocal_df = value == 1;
     return PAWFD_OK;
   }
-  if (n == "tc_fused" && (value == 0 || value == 1)) {
-    c->tc_fused = value == 1;
-    return PAWFD_OK;
-  }
   if (n == "tc_scratch_mb" && value >= 0 && value <= (1 << 20)) {
     // re-size the digit-plane scratch: wait for the work in flight, free, allocate again
     c->tc_scratch_mb = value;

@@ -358,38 +358,94 @@ int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* ou
 // array until the process exits, and all calls share the one array, so calls whose work
 // overlaps on the GPU (different streams, threads or processes sharing a context) race on
 // it.  Each call writes every partial entry it later reads, so nothing has to be cleared
-// between calls; the array simply keeps the last call's partials.
+// between calls; the array simply keeps the last call's partials.  The array's device
+// address is looked up at the first call made with a given device and context current and
+// cached for that pair; that first call should come before any stream capture.
 // ------------------------------------------------------------------------------------------
 namespace pawfd {
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = 8u << 20;   // 8 MiB of split-K partials
-constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr int NOALLOC_CACHE = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
+// The device address of g_noalloc_scratch, looked up once per (device, CUDA context).  The
+// context is named by its process-unique ID (cuCtxGetId), never reused, so a device reset or
+// another context made current leads to a fresh look-up instead of a stale address.
+struct NoallocSlot {
+  int dev = -1;
+  unsigned long long ctx_id = 0;
+  void* ptr = nullptr;
+  int sms = 0;
+};
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+NoallocSlot g_noalloc_slots[NOALLOC_CACHE];
+int g_noalloc_next = 0;
 
-// Device address of g_noalloc_scratch on the current device.  In host code the array's name
-// only stands for the device symbol; its address must be asked from the runtime, once per
-// device, with that device current.
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+
+// ID of the calling thread's current context (0 if none is current yet)
+int current_context_id(unsigned long long* id) {
+  static ctx_get_current_fn get_current = nullptr;
+  static ctx_get_id_fn get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || !f1)
+      return PAWFD_EDEVICE;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q2 != cudaDriverEntryPointSuccess || !f2)
+      return PAWFD_EDEVICE;
+    get_current = (ctx_get_current_fn)f1;
+    get_id = (ctx_get_id_fn)f2;
+  }
+  CUcontext ctx = nullptr;
+  *id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS) return PAWFD_EDEVICE;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return PAWFD_EDEVICE;
+  return PAWFD_OK;
+}
+
+// Device address of g_noalloc_scratch for the current device and context.  In host code the
+// array's name only stands for the device symbol; its address must be asked from the runtime
+// with that device current (set-up done once per device and context, then cached).
 int noalloc_scratch(void** out, int* sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return PAWFD_EDEVICE;
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return PAWFD_EINVAL;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PAWFD_EDEVICE;
-    int n = 0;
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAWFD_EDEVICE;
-    g_noalloc_ptr[dev] = p;
-    g_noalloc_sms[dev] = n;
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc != PAWFD_OK) return rc;
+  if (id != 0) {
+    for (const NoallocSlot& e : g_noalloc_slots)
+      if (e.ptr && e.dev == dev && e.ctx_id == id) {
+        *out = e.ptr;
+        *sms = e.sms;
+        return PAWFD_OK;
+      }
   }
-  *out = g_noalloc_ptr[dev];
-  *sms = g_noalloc_sms[dev];
+  // set-up: the runtime's symbol look-up also makes the device's primary context current if
+  // no context was current yet
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return PAWFD_EDEVICE;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PAWFD_EDEVICE;
+  rc = current_context_id(&id);
+  if (rc != PAWFD_OK) return rc;
+  if (id != 0) {
+    NoallocSlot& e = g_noalloc_slots[g_noalloc_next];
+    g_noalloc_next = (g_noalloc_next + 1) % NOALLOC_CACHE;
+    e.dev = dev;
+    e.ctx_id = id;
+    e.ptr = p;
+    e.sms = n;
+  }
+  *out = p;
+  *sms = n;
   return PAWFD_OK;
 }
 
@@ -404,11 +460,21 @@ int gram_noalloc_impl(const T* A, const T* B, long long K, int nb, double dV, T*
   long long kchunk = (K + nsplit - 1) / nsplit;
   kchunk = (kchunk + TK - 1) / TK * TK;
   nsplit = (K + kchunk - 1) / kchunk;
-  dim3 grid((nb + TM - 1) / TM, (nb + TM - 1) / TM, (unsigned)nsplit);
-  gram_partial_kernel<T><<<grid, NT, 0, stream>>>(A, B, nb, K, kchunk, part);
+  // launched through cudaLaunchKernel so that each launch's own status is checked, without
+  // reading (and clearing) an error that earlier, unrelated work left in the runtime
+  const dim3 grid((nb + TM - 1) / TM, (nb + TM - 1) / TM, (unsigned)nsplit);
+  void* partial_args[] = {(void*)&A, (void*)&B, (void*)&nb, (void*)&K, (void*)&kchunk, (void*)&part};
+  if (cudaLaunchKernel((const void*)&gram_partial_kernel<T, false>, grid, dim3(NT), partial_args, 0, stream) !=
+      cudaSuccess)
+    return PAWFD_EDEVICE;
   const long long nn = (long long)nb * nb;
-  gram_reduce_kernel<T><<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(part, (int)nsplit, nb, dV, M);
-  return cudaGetLastError() == cudaSuccess ? PAWFD_OK : PAWFD_EDEVICE;
+  const T* cpart = part;
+  int ns = (int)nsplit;
+  void* reduce_args[] = {(void*)&cpart, (void*)&ns, (void*)&nb, (void*)&dV, (void*)&M};
+  if (cudaLaunchKernel((const void*)&gram_reduce_kernel<T>, dim3((unsigned)((nn + 255) / 256)), dim3(256),
+                       reduce_args, 0, stream) != cudaSuccess)
+    return PAWFD_EDEVICE;
+  return PAWFD_OK;
 }
 
 }  // namespace

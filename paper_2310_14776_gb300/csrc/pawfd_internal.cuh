@@ -172,12 +172,6 @@ struct TcScratch {
   int presliced_nb = 0;
   const void* presliced_gram = nullptr;  // psi whose Gram digits are already in slicesA
   int presliced_gram_nb = 0;
-  // fused Gram (digits made inside the MMA kernel): chunk exponents of the whole row length
-  long long fnch = 0;          // chunks per row
-  int* fsigA = nullptr;        // [fnch][max_bands]
-  int* fsigB = nullptr;
-  int* fmaxA = nullptr;        // [max_bands] largest exponent of each row
-  int* fmaxB = nullptr;
 };
 
 }  // namespace pawfd
@@ -229,7 +223,6 @@ struct pawfd_ctx {
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 512-value chunks (0: allocation)
   int tc_scratch_mb = 0;                      // digit-plane scratch per operand set in MB (0: default sizes)
-  bool tc_fused = false;                      // tensor-core Gram with digits made inside the MMA kernel
   bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
   bool free_operator = false;                 // v = 0 and no atoms: kinetic_local is T alone (Poisson)
   cudaStream_t aux_stream = nullptr;          // non-blocking stream for captured work (created on use)

@@ -1,11 +1,14 @@
 // refine.cu -- final refinement of the mixed form on an FP64 context.
 //
 // The paper does not describe a mixed-precision eigensolver step; the refinement follows the
-// reading that closes one: the rotated FP32 / complex64 bands psi' are promoted to FP64, H and
-// S are applied in FP64 (Eq. (dh) and the overlap operator of the PAW section), FP64 Gram
-// matrices give the Rayleigh quotients theta_n = H'_nn / S'_nn, a second FP64 subspace
-// diagonalization (SCF step 1 of the Kohn-Sham section) gives the refined eigenvalues, and
-// the residual norms ||H psi'_n - eps_n S psi'_n|| are reported.
+// reading that closes one: the FP32 / complex64 input bands of the mixed step are promoted to
+// FP64 and rotated by that step's FP64 eigenvector matrix in FP64 (psi' = psi C_lo, the
+// digit-product rotation of an FP64 context: the span of the input is kept to FP64 rounding,
+// where FP32-rounded rotated bands would move it by the FP32 rounding), H and S are applied in
+// FP64 (Eq. (dh) and the overlap operator of the PAW section), FP64 Gram matrices give the
+// Rayleigh quotients theta_n = H'_nn / S'_nn, a second FP64 subspace diagonalization (SCF step
+// 1 of the Kohn-Sham section) gives the refined eigenvalues, and the residual norms
+// ||H psi'_n - eps_n S psi'_n|| are reported.
 #include <algorithm>
 
 #include "pawfd_internal.cuh"
@@ -93,23 +96,28 @@ int refine_tail(pawfd_ctx* c, int nb, const void* hpsi, const void* spsi, void* 
 
 }  // namespace
 
-extern "C" int pawfd_refine(pawfd_ctx* c, const void* psi_lo, int nb, void* psi, void* hpsi, void* spsi,
-                            void* Hnm, void* Snm, double* eps, double* theta, double* resid, void* C) {
+extern "C" int pawfd_refine(pawfd_ctx* c, const void* psi_lo, int nb, const void* C_lo, void* psi, void* hpsi,
+                            void* spsi, void* Hnm, void* Snm, double* eps, double* theta, double* resid, void* C) {
   if (!c) return PAWFD_EINVAL;
   if (c->dtype != PAWFD_R64 && c->dtype != PAWFD_C128)
     return fail(c, PAWFD_EINVAL, "refine needs an FP64 context (real or complex)");
   if (nb < 1 || nb > c->max_bands) return fail(c, PAWFD_EINVAL, "nb must be in 1..max_bands");
   if (!psi_lo || !psi || !hpsi || !spsi || !Hnm || !Snm || !eps || !theta || !resid || !C)
     return fail(c, PAWFD_EINVAL, "null array");
-  if (psi == hpsi || psi == spsi || hpsi == spsi || psi_lo == psi || Hnm == Snm)
+  if (psi == hpsi || psi == spsi || hpsi == spsi || psi_lo == psi || psi_lo == hpsi || Hnm == Snm)
     return fail(c, PAWFD_EINVAL, "work arrays may not alias");
-  if (((uintptr_t)psi_lo | (uintptr_t)psi) & 15) return fail(c, PAWFD_EINVAL, "band arrays must be 16-byte aligned");
-  // 1. promote psi' to FP64
+  if (C_lo && (C_lo == C || C_lo == Hnm || C_lo == Snm))
+    return fail(c, PAWFD_EINVAL, "C_lo may not alias an output matrix");
+  if (((uintptr_t)psi_lo | (uintptr_t)psi | (uintptr_t)hpsi) & 15)
+    return fail(c, PAWFD_EINVAL, "band arrays must be 16-byte aligned");
+  // 1. promote the bands to FP64 (exact); with C_lo, into hpsi as a staging array, then
+  //    psi = that * C_lo in FP64 (hpsi is written again by step 2)
   const long long scalars = (long long)nb * (long long)c->K * (is_complex(c) ? 2 : 1);
   const int blocks = (int)std::min<long long>(8ll * c->num_sms, (scalars / 4 + NT - 1) / NT + 1);
-  promote_kernel<<<blocks, NT, 0, c->stream>>>((const float*)psi_lo, (double*)psi, scalars);
+  promote_kernel<<<blocks, NT, 0, c->stream>>>((const float*)psi_lo, (double*)(C_lo ? hpsi : psi), scalars);
   c->launches += 1;
   int rc = check_cuda(c, cudaGetLastError(), "promote launch");
+  if (rc == PAWFD_OK && C_lo) rc = launch_rotate(c, hpsi, nb, C_lo, psi);
   // 2. H psi' and S psi' in FP64, sharing one set of projections
   if (rc == PAWFD_OK) rc = launch_apply_hs(c, psi, nb, hpsi, spsi, c->d_P);
   // 3. FP64 Gram matrices

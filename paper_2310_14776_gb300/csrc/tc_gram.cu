@@ -13,7 +13,6 @@
 
 #include "pawfd_internal.cuh"
 #include "sliced_gram.cuh"
-#include "fused_gram.cuh"
 
 namespace pawfd {
 namespace {
@@ -352,7 +351,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
 bool gram_slice_psi(pawfd_ctx* c, const void* psi, int nb) {
   TcScratch& t = c->tc;
   const long long L = (long long)c->K;
-  if (!c->use_tc || !t.ready || is_complex(c) || c->tc_fused || c->tc_kblk_chunks > 0 || t.kblk < L) return false;
+  if (!c->use_tc || !t.ready || is_complex(c) || c->tc_kblk_chunks > 0 || t.kblk < L) return false;
   const int nch = (int)((L + sg::KCG - 1) / sg::KCG);
   cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
   if (is_fp32(c))
@@ -393,97 +392,9 @@ int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void*
   return tc_rotate_impl<double, 7, 6>(c, (const double*)psi, nb, (const double*)C, nout, (double*)out);
 }
 
-// TMA descriptor of a raw operand [rows][L] (FP64 or FP32, row stride L values): boxes of
-// 16 values x box_rows, no swizzle, zero fill past the ends.
-int encode_raw_map(pawfd_ctx* c, CUtensorMap* map, const void* base, bool fp32, long long L, int rows, int box_rows) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled not available");
-    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
-  const cuuint64_t esize = fp32 ? 4 : 8;
-  cuuint64_t dims[2] = {(cuuint64_t)L, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)L * esize};
-  cuuint32_t box[2] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  const CUresult r = encode(map, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
-                            const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(c, PAWFD_EDEVICE, "cuTensorMapEncodeTiled (raw operand) failed");
-  return PAWFD_OK;
-}
-
-// The fused Gram: chunk exponents of both operands, then one launch that streams the raw
-// operands, makes the digits in shared memory and multiplies them, then the fixed-order
-// reduction of the split-K partials.
-template <class R>
-int fused_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool herm) {
-  TcScratch& t = c->tc;
-  const bool cplx = is_complex(c);
-  const long long L = (long long)c->K * (cplx ? 2 : 1);
-  const int rowsB = cplx ? 2 * nb : nb;
-  const int Tr = (nb + sg::BM - 1) / sg::BM, Tc = (nb + sg::BN - 1) / sg::BN;
-  const int halves = cplx ? 2 : 1;
-  const int tiles = herm ? halves * sg::herm_tiles(nb) : Tr * halves * Tc;
-  const int nchunks = (int)((L + sg::KC - 1) / sg::KC);
-  if (nchunks > t.fnch) return fail(c, PAWFD_EINVAL, "fused Gram: row longer than the scratch");
-  // one CTA per SM: tiles x splits within one wave (a partial second wave doubles the time)
-  int nsplit = std::max(1, std::min(nchunks, c->num_sms / tiles));
-  while (nsplit > 1 && (size_t)nsplit * nb * rowsB * sizeof(double) > t.part_bytes) --nsplit;
-  const int cpc = (nchunks + nsplit - 1) / nsplit;
-  const int ns = (nchunks + cpc - 1) / cpc;
-  cudaMemsetAsync(t.fmaxA, 0x80, sizeof(int) * nb, c->stream);
-  cudaMemsetAsync(t.fmaxB, 0x80, sizeof(int) * nb, c->stream);
-  const long long warps = (long long)nb * nchunks;
-  const unsigned sblocks = (unsigned)((warps + 7) / 8);
-  fg::sigma_kernel<R><<<sblocks, 256, 0, c->stream>>>(A, nb, L, L, nchunks, t.fsigA, nb, t.fmaxA);
-  fg::sigma_kernel<R><<<sblocks, 256, 0, c->stream>>>(B, nb, L, L, nchunks, t.fsigB, nb, t.fmaxB);
-  c->launches += 2;
-  CUtensorMap mA, mB;
-  int rc = encode_raw_map(c, &mA, A, sizeof(R) == 4, L, nb, sg::BM);
-  if (rc == PAWFD_OK) rc = encode_raw_map(c, &mB, B, sizeof(R) == 4, L, nb, sg::BN);
-  if (rc != PAWFD_OK) return rc;
-  fg::FusedArgs fa = {};
-  sg::GramArgs& a = fa.g;
-  a.sigA = t.fsigA;
-  a.sigB = t.fsigB;
-  a.sig_ldA = nb;
-  a.sig_ldB = nb;
-  a.maxA = t.fmaxA;
-  a.maxB = t.fmaxB;
-  a.rowsA = nb;
-  a.rowsB = rowsB;
-  a.tilesN = halves * Tc;
-  a.herm = herm;
-  a.halves = halves;
-  a.half_rows = nb;
-  a.chunks_per_cta = cpc;
-  a.nchunks = nchunks;
-  a.accumulate = 0;
-  a.part = (double*)t.part;
-  a.st = c->d_status;
-  fa.braw_rows = nb;
-  fg::fused_gram_kernel<R><<<dim3(tiles, ns), fg::NTHREADS, fg::smem_bytes<R>(), c->stream>>>(mA, mB, fa);
-  c->launches += 1;
-  const long long nn = (long long)nb * nb;
-  if (cplx)
-    tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, ns, nb, rowsB, nb,
-                                                                              c->dV, herm, (zd*)M);
-  else
-    tc_reduce_kernel<double><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, ns, nb, rowsB,
-                                                                                  nb, c->dV, herm, (double*)M);
-  c->launches += 1;
-  return check_cuda(c, cudaGetLastError(), "fused tensor-core gram launch");
-}
-
 // Hermitian Grams psi^H B and psi^H psi (real bands; false when this form does not apply)
 bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc) {
-  if (!c->tc.ready || is_complex(c) || c->tc_fused) return false;
+  if (!c->tc.ready || is_complex(c)) return false;
   if (is_fp32(c)) *rc = tc_gram_pair_impl<float, 4, 4>(c, (const float*)psi, (const float*)B, nb, (double*)M1, (double*)M2);
   else *rc = tc_gram_pair_impl<double, 7, 6>(c, (const double*)psi, (const double*)B, nb, (double*)M1, (double*)M2);
   return true;
@@ -491,13 +402,6 @@ bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1
 
 int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, bool hermitian) {
   if (!c->tc.ready) return fail(c, PAWFD_EINVAL, "tensor-core Gram scratch not set up");
-  // the fused kernel reads the operands through TMA: 16-byte aligned base and row stride
-  const size_t row_bytes = band_size(c) * (size_t)c->K;
-  const bool aligned = ((uintptr_t)A % 16 == 0) && ((uintptr_t)B % 16 == 0) && (row_bytes % 16 == 0);
-  if (c->tc_fused && aligned && c->tc.fsigA) {
-    if (is_fp32(c)) return fused_gram_impl<float>(c, (const float*)A, (const float*)B, nb, M, hermitian);
-    return fused_gram_impl<double>(c, (const double*)A, (const double*)B, nb, M, hermitian);
-  }
   if (is_fp32(c)) return tc_gram_impl<float, 4, 4>(c, (const float*)A, (const float*)B, nb, M, hermitian);
   return tc_gram_impl<double, 7, 6>(c, (const double*)A, (const double*)B, nb, M, hermitian);
 }
@@ -585,22 +489,6 @@ int setup_tc(pawfd_ctx* c) {
                                               S == 7 ? sg::smem_bytes<7>() : sg::smem_bytes<4>()),
                       "smem attribute");
   }
-  // fused Gram: chunk exponents over the whole row
-  if (rc == PAWFD_OK) {
-    t.fnch = (L + sg::KC - 1) / sg::KC;
-    const size_t bytes = sizeof(int) * (size_t)t.fnch * nb;
-    rc = check_cuda(c, cudaMalloc(&t.fsigA, bytes), "cudaMalloc fused sigma");
-    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.fsigB, bytes), "cudaMalloc fused sigma");
-    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.fmaxA, sizeof(int) * nb), "cudaMalloc");
-    if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.fmaxB, sizeof(int) * nb), "cudaMalloc");
-    if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
-    if (S == 7)
-      rc = check_cuda(c, cudaFuncSetAttribute(fg::fused_gram_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              fg::smem_bytes<double>()), "smem attribute");
-    else
-      rc = check_cuda(c, cudaFuncSetAttribute(fg::fused_gram_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              fg::smem_bytes<float>()), "smem attribute");
-  }
   // rotation scratch: operand A (from C) and its digits, digits of a block of grid points
   if (rc == PAWFD_OK) {
     const long long Lk = (long long)nb * (cplx ? 2 : 1);
@@ -647,8 +535,7 @@ int setup_tc(pawfd_ctx* c) {
 void free_tc(pawfd_ctx* c) {
   TcScratch& t = c->tc;
   void* p[] = {t.slicesA, t.slicesB, t.sigA, t.sigB, t.part, t.part2, t.maxA, t.maxB,
-               t.rotA, t.rotSlicesA, t.rotSlicesB, t.rotSigA, t.rotSigB, t.rotMaxA, t.rotMaxB,
-               t.fsigA, t.fsigB, t.fmaxA, t.fmaxB};
+               t.rotA, t.rotSlicesA, t.rotSlicesB, t.rotSigA, t.rotSigB, t.rotMaxA, t.rotMaxB};
   for (void* q : p)
     if (q) cudaFree(q);
   t = TcScratch();

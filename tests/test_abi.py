@@ -45,6 +45,19 @@ def test_binding_covers_every_declared_symbol(libpath):
         assert getattr(L, name) is not None
 
 
+def test_binding_arity_matches_header():
+    # every ctypes signature has as many arguments as the header's declaration
+    decl = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for name, args in re.findall(r"\b(pawfd_\w+)\s*\(([^)]*)\)\s*;", text):
+            args = args.strip()
+            decl[name] = 0 if args in ("", "void") else args.count(",") + 1
+    assert set(decl) == set(_lib.SIGNATURES)
+    wrong = {n: (decl[n], len(_lib.SIGNATURES[n][0])) for n in decl if decl[n] != len(_lib.SIGNATURES[n][0])}
+    assert not wrong, wrong
+
+
 def test_header_compiles_as_c():
     src = '#include "pawfd.h"\nint main(void){ pawfd_system_desc d; (void)d; return PAWFD_OK; }\n'
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-fsyntax-only", "-I", os.path.join(ROOT, "include"),

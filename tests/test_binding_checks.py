@@ -162,7 +162,8 @@ def test_rotate_n_and_residual_checks():
 @pytest.mark.parametrize("case", ["apply_H out short", "apply_H P dtype", "apply_hs Spsi short", "apply_hs P short",
                                   "gram_hs P dtype", "subspace eps dtype", "subspace eps short", "rotate out short",
                                   "rr_step out short", "rr_step work Hpsi short", "rr_step eps dtype",
-                                  "refine eps short", "refine Hpsi short", "residual rnorm dtype",
+                                  "refine eps short", "refine Hpsi short", "refine C_lo shape",
+                                  "residual rnorm dtype",
                                   "davidson eps_in not contiguous"])
 def test_step_calls_reject_short_or_mistyped_outputs(case):
     c = shell()
@@ -184,6 +185,7 @@ def test_step_calls_reject_short_or_mistyped_outputs(case):
         "rr_step eps dtype": lambda: c.rr_step(psi, work=dict(c.alloc_work(nb), eps=torch.zeros(nb, dtype=torch.float32))),
         "refine eps short": lambda: c.refine(bands(c, nb, torch.float32), work={"eps": f64(3)}),
         "refine Hpsi short": lambda: c.refine(bands(c, nb, torch.float32), work={"Hpsi": bands(c, 3)}),
+        "refine C_lo shape": lambda: c.refine(bands(c, nb, torch.float32), torch.zeros((3, 3), dtype=torch.float64)),
         "residual rnorm dtype": lambda: c.residual_precond(psi, psi, f64(nb), rnorm=torch.zeros(nb, dtype=torch.float32)),
         "davidson eps_in not contiguous": lambda: c.davidson_step(c.alloc_davidson(nb), nb, f64(2 * nb)[::2]),
     }
@@ -199,9 +201,10 @@ def test_step_calls_accept_their_own_allocations():
     c.rayleigh_ritz(psi, check=False)
     c.rr_step(psi)
     c.refine(bands(c, nb, torch.float32), check=False)
+    c.refine(bands(c, nb, torch.float32), torch.zeros((nb, nb), dtype=torch.float64), check=False)
     w = c.alloc_davidson(nb)
     c.davidson_step(w, nb, torch.zeros(nb, dtype=torch.float64))
     c.residual_precond(psi, psi, torch.zeros(nb, dtype=torch.float64))
     called = [n for n in c.lib.called if n != "pawfd_set_stream"]
     assert called == ["pawfd_apply_HS", "pawfd_gram_hs", "pawfd_subspace_diag", "pawfd_rotate", "pawfd_rr_step",
-                      "pawfd_refine", "pawfd_davidson_step", "pawfd_residual_precond"]
+                      "pawfd_refine", "pawfd_refine", "pawfd_davidson_step", "pawfd_residual_precond"]

@@ -532,6 +532,39 @@ def test_refine_of_ritz_vectors_is_a_fixed_point(complex_wf):
     assert abs(res["resid"][n] - math.sqrt(s.dV) * np.linalg.norm(r)) <= 1e-12 * res["resid"][n]
 
 
+@pytest.mark.parametrize("case", ["selfwrap", "bloch"])
+def test_refine_of_rotated_input_keeps_its_span(case):
+    # refinement of a mixed step's INPUT bands with that step's C: psi' = psi C_lo keeps the span
+    # of psi for any nonsingular C_lo, so the refined eps are the Ritz values of span(psi) under
+    # the dense pencil (H, S), whatever C_lo is; with C_lo the eigenvector matrix of an exact
+    # step the rotated bands are its Ritz vectors, so theta = eps and the residuals are those
+    # of the Ritz pairs
+    s = small_system(**TINY[case])
+    H, S = dense_operators(s)
+    n = 5
+    psi = rand_psi(s, n, 31)
+    lo = psi.astype(np.complex64 if s.complex_wf else np.float32)
+    exact_in = lo.astype(np.complex128 if s.complex_wf else np.float64)
+    ritz = _dense_ritz(s, H, S, exact_in, n)
+    rng = np.random.default_rng(32)
+    M = rng.standard_normal((n, n)) + 3.0 * np.eye(n)
+    if s.complex_wf:
+        M = M + 1j * rng.standard_normal((n, n))
+    res = O.refine(s, lo, M)
+    assert np.allclose(res["eps"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
+    assert np.allclose(res["psi"].reshape(n, -1), (exact_in.reshape(n, -1).T @ M).T, rtol=0, atol=1e-13 * n)
+    C0 = O.rayleigh_ritz(s, exact_in)["C"]
+    res0 = O.refine(s, lo, C0)
+    assert np.allclose(res0["eps"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
+    assert np.allclose(res0["theta"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
+    Z = res0["psi"].reshape(n, -1).T
+    R = H @ Z - (S @ Z) * res0["eps"][None, :]
+    assert np.allclose(res0["resid"], np.sqrt(s.dV * np.sum(np.abs(R) ** 2, axis=0)), rtol=1e-9, atol=1e-12)
+    # without C_lo the bands are refined as given (the FP32 bands' own span)
+    plain = O.refine(s, lo)
+    assert np.allclose(plain["eps"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
+
+
 # ------------------------------------------------------------------------------------------
 # f-1: the block-Davidson step (the iterative eigensolver of the Kohn-Sham section; reading)
 # ------------------------------------------------------------------------------------------
