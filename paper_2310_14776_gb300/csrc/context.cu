@@ -284,8 +284,8 @@ void free_ctx(pawfd_ctx* c) {
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_dscale, c->d_barrier, c->d_status, c->d_reduce,
-                  c->d_vshift_df, c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
-                  c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df};
+                  c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
+                  c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df, c->d_vloc64};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
@@ -351,15 +351,10 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
       upload(c, p, vs.data(), c->K, &rc);
       c->d_vshift = p;
       if (c->dtype == PAWFD_R64) {
-        // the same values as (hi, lo) FP32 pairs for the double-float stencil
-        std::vector<float> df(2 * c->K);
-        for (size_t r = 0; r < c->K; ++r) {
-          df[2 * r] = (float)vs[r];
-          df[2 * r + 1] = (float)(vs[r] - (double)df[2 * r]);
-        }
-        float* q = dev_alloc<float>(c, 2 * c->K, &rc);
-        upload(c, q, df.data(), 2 * c->K, &rc);
-        c->d_vshift_df = q;
+        // v itself for the fixed-point stencil (its centre weight is an exact integer)
+        double* v = dev_alloc<double>(c, c->K, &rc);
+        upload(c, v, d->vloc, c->K, &rc);
+        c->d_vloc64 = v;
       }
     }
   }
@@ -443,8 +438,8 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
-  if (n == "stencil_df" && (value == 0 || value == 1)) {
-    c->stencil_df = value == 1;
+  if (n == "stencil_fx" && (value == 0 || value == 1)) {
+    c->stencil_fx = value == 1;
     return PAWFD_OK;
   }
   if (n == "nonlocal_df" && (value == 0 || value == 1)) {

@@ -195,7 +195,7 @@ struct pawfd_ctx {
   size_t K;
   cudaStream_t stream;
   void* d_vshift = nullptr;                   // v(r) - 1/2 c0 sum_c 1/h_c^2 (double or float)
-  void* d_vshift_df = nullptr;                // real FP64: the same as (hi, lo) FP32 pairs
+  void* d_vloc64 = nullptr;                   // real FP64: v(r) itself (fixed-point stencil)
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_Q = nullptr;                        // [Ip][max_bands] FP64 dS P of the overlap correction
@@ -223,7 +223,7 @@ struct pawfd_ctx {
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 512-value chunks (0: allocation)
   int tc_scratch_mb = 0;                      // digit-plane scratch per operand set in MB (0: default sizes)
-  bool stencil_df = true;                     // real FP64 stencil in double-float FP32 arithmetic
+  bool stencil_fx = true;                     // real FP64 stencil in exact fixed-point arithmetic
   bool free_operator = false;                 // v = 0 and no atoms: kinetic_local is T alone (Poisson)
   cudaStream_t aux_stream = nullptr;          // non-blocking stream for captured work (created on use)
   cudaEvent_t aux_fork = nullptr, aux_join = nullptr;

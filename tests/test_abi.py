@@ -110,7 +110,7 @@ def _null_args(argtypes):
         elif t is ctypes.c_double:
             out.append(1.0)
         elif t is ctypes.c_char_p:
-            out.append(b"stencil_df")
+            out.append(b"stencil_fx")
         else:
             out.append(None)
     return out

@@ -212,17 +212,17 @@ def test_hermitian_gram_equals_full_gram(dev, cplx):
 
 
 @pytest.mark.parametrize("n", [(45, 19, 13), (96, 40, 10), (40, 14, 3)])
-def test_double_float_stencil_matches_fp64_arithmetic(dev, n):
-    # the real FP64 stencil in double-float FP32 pairs against the FP64-pipe kernel: per band
-    # within 1e-13 of the band norm (the pairs carry about 48 bits)
+def test_fixed_point_stencil_matches_fp64_arithmetic(dev, n):
+    # the real FP64 stencil in exact fixed point against the FP64-pipe kernel and the oracle:
+    # per band within 1e-13 of the band norm
     from paper_2310_14776_gb300 import api
     s = synth.make_system(n, tuple(0.21 * v for v in n), 2, synth.PSET_SP, seed=330)
     nb = 6
     ctx = api.Context(s, max_bands=nb, device=dev, precision="fp64")
     psi = to_dev(synth.make_psi(s, nb, 331), dev)
-    ctx.set_option("stencil_df", 1)
+    ctx.set_option("stencil_fx", 1)
     a = ctx.kinetic_local(psi).clone()
-    ctx.set_option("stencil_df", 0)
+    ctx.set_option("stencil_fx", 0)
     b = ctx.kinetic_local(psi).clone()
     ctx.sync()
     d = (a - b).reshape(nb, -1).norm(dim=1) / b.reshape(nb, -1).norm(dim=1)
@@ -231,6 +231,37 @@ def test_double_float_stencil_matches_fp64_arithmetic(dev, n):
     e = np.linalg.norm((a.cpu().numpy() - ref).reshape(nb, -1), axis=1) / np.linalg.norm(ref.reshape(nb, -1), axis=1)
     assert e.max() <= 1e-13
     ctx.close()
+
+
+def test_fixed_point_stencil_special_values(dev):
+    # bands the fixed-point scale must handle: all zeros, subnormal values only, values near
+    # the top of the FP64 range, one spike in a zero band (a band whose slabs have different
+    # scales), and a band holding an infinity and a NaN (its slab is computed in plain FP64, so
+    # they propagate as in the oracle)
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((44, 16, 9), (9.2, 3.4, 1.9), 2, synth.PSET_SP, seed=332)
+    base = synth.make_psi(s, 5, 333)
+    psi = np.zeros_like(base)
+    psi[1] = base[1] * 1e-310
+    psi[2] = base[2] * 1e300
+    psi[3, 4, 7, 20] = 3.5
+    psi[4] = base[4]
+    psi[4, 2, 3, 5] = np.inf
+    psi[4, 6, 12, 30] = np.nan
+    ctx = api.Context(s, max_bands=5, device=dev, precision="fp64")
+    got = ctx.kinetic_local(to_dev(psi, dev)).cpu().numpy()
+    ctx.close()
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = O.kinetic_local(s, psi)
+    assert np.array_equal(got[0], np.zeros_like(got[0]))
+    for n in (1, 2, 3):
+        err = np.linalg.norm(got[n] - ref[n]) / np.linalg.norm(ref[n])
+        assert err <= 1e-13, (n, err)
+    # the non-finite band: the same non-finite pattern, finite values to the FP64 bar
+    fin = np.isfinite(ref[4])
+    assert np.array_equal(np.isfinite(got[4]), fin)
+    assert np.array_equal(np.isnan(got[4]), np.isnan(ref[4]))
+    assert np.max(np.abs(got[4][fin] - ref[4][fin])) <= 1e-12 * np.max(np.abs(ref[4][fin]))
 
 
 @pytest.mark.parametrize("case", [((45, 19, 13), 6, 5), ((30, 28, 26), 9, 40)])
