@@ -721,7 +721,11 @@ def run_served(args):
                        "over": lat_note, "warmup_s": args.serve_warmup},
         "jobs": {"arrived": len(arrived), "completed": len(recs), "unfinished_at_stop": out["unfinished"],
                  "max_queue": out["max_queue"], "peak_hbm_gb": out["peak_used"] / 1e9,
-                 "budget_overruns": out["overruns"]},
+                 "device_peak_hbm_gb": out["device_peak_used"] / 1e9, "arena_gb": out["arena_bytes"] / 1e9,
+                 "arena_peak_gb": out["arena_peak"] / 1e9, "contexts_gb": out["context_bytes"] / 1e9,
+                 "budget_overruns": out["overruns"],
+                 "device_peak_note": "free device memory at the server's start less the smallest free memory "
+                                     "sampled during the run (every loop pass)"},
         "saturated": saturated,
         "max_sustainable_jobs_per_s": len(recs) / out["elapsed"] if saturated else ">= %.0f" % args.rate,
         "fp64_sequential": {"rr_steps_per_s": 5.0 / t_job if t_job else None, "seconds_per_job": t_job,

@@ -155,6 +155,11 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
+ *   "test_barrier_missing"  0 (default); 1 (for tests of the error path only): the grid
+ *                     barriers of the subspace solve wait for one CTA more than the launch has
+ *                     and give up after 20 ms, so every such wait runs out: the kernels record
+ *                     PAWFD_ETIMEDOUT, later kernels of the context return without work, and
+ *                     pawfd_sync reports it.  Waits for the context's stream first.
  * Returns PAWFD_EINVAL for an unknown name or value. */
 int pawfd_set_option(pawfd_ctx* ctx, const char* name, int value);
 

@@ -438,6 +438,15 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
+  if (n == "test_barrier_missing" && (value == 0 || value == 1)) {
+    // test setting: grid barriers wait for one CTA more than the launch has, for 20 ms, so
+    // that every grid-barrier wait runs out and reports PAWFD_ETIMEDOUT
+    const unsigned f[2] = {(unsigned)value, value ? 20u : 0u};
+    int rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
+    if (rc == PAWFD_OK)
+      rc = check_cuda(c, cudaMemcpy(&c->d_status->barrier_extra, f, sizeof f, cudaMemcpyHostToDevice), "memcpy");
+    return rc;
+  }
   if (n == "stencil_fx" && (value == 0 || value == 1)) {
     c->stencil_fx = value == 1;
     return PAWFD_OK;
@@ -546,7 +555,7 @@ extern "C" int pawfd_sync(pawfd_ctx* c) {
   if (rc != PAWFD_OK) return rc;
   const DeviceStatus st = *c->h_status;
   if (st.code == 0) return PAWFD_OK;
-  cudaMemsetAsync(c->d_status, 0, sizeof(DeviceStatus), c->stream);
+  cudaMemsetAsync(c->d_status, 0, 2 * sizeof(int), c->stream);   // code and detail only
   cudaStreamSynchronize(c->stream);
   char buf[160];
   switch (st.code) {

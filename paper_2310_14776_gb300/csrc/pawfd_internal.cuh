@@ -96,6 +96,10 @@ template <class R> __host__ __device__ inline void fma_real(cplx<R>& acc, R s, c
 struct DeviceStatus {
   int code;    // 0 or a negative PAWFD_E* code
   int detail;  // e.g. failing Cholesky column, or the barrier that timed out
+  // test setting ("test_barrier_missing"): grid barriers wait for this many CTAs more than
+  // the launch has, and give up after barrier_limit_ms (0: the default limit)
+  unsigned barrier_extra;
+  unsigned barrier_limit_ms;
 };
 
 __device__ inline void set_status(DeviceStatus* st, int code, int detail) {

@@ -40,16 +40,19 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, DeviceStatus* st, 
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned gen = ld_volatile(&bar[1]);
+    const unsigned need = nblocks + ld_volatile(&st->barrier_extra);
+    const unsigned lim_ms = ld_volatile(&st->barrier_limit_ms);
+    const unsigned long long limit = lim_ms ? 1000000ull * lim_ms : (unsigned long long)BARRIER_TIMEOUT_NS;
     __threadfence();
     const unsigned arrived = atomicAdd(&bar[0], 1u);
-    if (arrived == nblocks - 1) {
+    if (arrived == need - 1) {
       atomicExch(&bar[0], 0u);
       __threadfence();
       atomicAdd(&bar[1], 1u);
     } else {
       const unsigned long long t0 = global_ns();
       while (ld_volatile(&bar[1]) == gen) {
-        if (global_ns() - t0 > (unsigned long long)BARRIER_TIMEOUT_NS) {
+        if (global_ns() - t0 > limit) {
           set_status(st, PAWFD_ETIMEDOUT, id);
           ok = 0;
           break;

@@ -9,8 +9,17 @@ so its kernels overlap with those of all other jobs on the GPU.  A finished job'
 return to the budget at once, and its context goes back to a pool for the next job of the
 same system; idle contexts are evicted when memory is short.
 
+Memory is held to the budget by construction.  The budget is split in two:
+  * an arena: one device allocation made once, from which every job's arrays are carved by
+    a host-side first-fit allocator (``Arena``) and returned when the job ends, so the loop
+    makes no device allocation per job and the caching allocator's blocks do not pile up;
+  * the contexts (the library allocates their tables and scratch itself): each is charged at
+    its measured size (the drop in free device memory when it was created, known for every
+    system after its first context) before a job that needs a new one is admitted, and idle
+    pooled contexts are evicted, least recently used first, to make room.
+
 ``Scheduler`` is the host-side bookkeeping (queue, budget, admission, retirement) and needs
-no GPU.  ``Server`` drives it with the library's contexts.
+no GPU, nor does ``Arena``.  ``Server`` drives them with the library's contexts.
 """
 from __future__ import annotations
 
@@ -122,6 +131,19 @@ class Scheduler:
                 return job
         return None
 
+    def pick_with(self, try_start: Callable[[Job], object]) -> Optional[Tuple[Job, object]]:
+        """First fit with a caller-side test: the first of the first `lookahead` waiting jobs
+        for which `try_start(job)` returns something other than None (it reserves whatever
+        the job needs), removed from the queue; None if no slot is free or nothing fits."""
+        if len(self.active) >= self.max_active:
+            return None
+        for i, job in enumerate(list(self.queue)[: self.lookahead]):
+            r = try_start(job)
+            if r is not None:
+                del self.queue[i]
+                return job, r
+        return None
+
     def admit(self, job: Job, nbytes: int):
         self.active[job.job_id] = nbytes
         self.used += nbytes
@@ -139,6 +161,62 @@ class Scheduler:
         self.used -= nbytes
 
 
+class Arena:
+    """First-fit allocation of byte ranges of [0, size), each starting at a multiple of
+    `align`; a freed range merges with free neighbours.  Host bookkeeping only: the device
+    memory is one buffer that the server allocates once."""
+
+    def __init__(self, size: int, align: int = 256):
+        self.align = int(align)
+        self.size = int(size) // self.align * self.align
+        self.free_ranges: List[Tuple[int, int]] = [(0, self.size)] if self.size > 0 else []   # sorted (offset, length)
+        self.used = 0
+        self.peak = 0
+
+    def _round(self, nbytes: int) -> int:
+        return max(self.align, (int(nbytes) + self.align - 1) // self.align * self.align)
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        n = self._round(nbytes)
+        for i, (off, ln) in enumerate(self.free_ranges):
+            if ln >= n:
+                if ln == n:
+                    del self.free_ranges[i]
+                else:
+                    self.free_ranges[i] = (off + n, ln - n)
+                self.used += n
+                self.peak = max(self.peak, self.used)
+                return off
+        return None
+
+    def free(self, off: int, nbytes: int):
+        n = self._round(nbytes)
+        i = 0
+        while i < len(self.free_ranges) and self.free_ranges[i][0] < off:
+            i += 1
+        self.free_ranges.insert(i, (off, n))
+        # merge with the following range, then with the preceding one
+        if i + 1 < len(self.free_ranges) and off + n == self.free_ranges[i + 1][0]:
+            self.free_ranges[i] = (off, n + self.free_ranges[i + 1][1])
+            del self.free_ranges[i + 1]
+        if i > 0 and self.free_ranges[i - 1][0] + self.free_ranges[i - 1][1] == off:
+            self.free_ranges[i - 1] = (self.free_ranges[i - 1][0], self.free_ranges[i - 1][1] + self.free_ranges[i][1])
+            del self.free_ranges[i]
+        self.used -= n
+
+    def alloc_all(self, sizes: Sequence[int]) -> Optional[List[int]]:
+        """Offsets for every size, or None (and nothing held) if one does not fit."""
+        offs: List[int] = []
+        for nb in sizes:
+            off = self.alloc(nb)
+            if off is None:
+                for o, n in zip(offs, sizes):
+                    self.free(o, n)
+                return None
+            offs.append(off)
+        return offs
+
+
 # ------------------------------------------------------------------------------------------
 # GPU executor
 # ------------------------------------------------------------------------------------------
@@ -151,12 +229,29 @@ class JobRecord:
     eps: Optional[np.ndarray] = None
 
 
+def job_array_sizes(inst: synth.Instance, precision: str) -> List[int]:
+    """Byte sizes of one job's arrays, in the order the server carves them: the two band
+    blocks (ping-pong), H psi, S psi, then Hnm, Snm, C and eps (their sum is array_bytes)."""
+    esize = {("mixed", False): 4, ("mixed", True): 8, ("fp64", False): 8, ("fp64", True): 16}[
+        (precision, inst.complex_wf)]
+    msize = 16 if inst.complex_wf else 8
+    nb = inst.nbands
+    band = inst.npoints * nb * esize
+    return [band] * 4 + [nb * nb * msize] * 3 + [nb * 8]
+
+
 class Server:
-    """Runs a job stream on one GPU with the library's contexts (see the module docstring)."""
+    """Runs a job stream on one GPU with the library's contexts (see the module docstring).
+
+    budget: `budget_bytes`, or `budget_fraction` of the free device memory at construction.
+    After ``prepare`` (contexts of the stream's systems made ahead) the arena takes what the
+    contexts leave, less `ctx_reserve_fraction` of the budget kept for contexts made during
+    the run; without it, the arena takes `arena_fraction` of the budget at the first run."""
 
     def __init__(self, systems: Sequence[synth.Instance], device, precision: str = "mixed",
                  iterations: int = 5, budget_fraction: float = 0.8, budget_bytes: Optional[int] = None,
-                 max_active: int = 48, tune: bool = True):
+                 max_active: int = 48, tune: bool = True, arena_fraction: float = 0.5,
+                 ctx_reserve_fraction: float = 0.1):
         import torch
         self.torch = torch
         self.device = torch.device(device)
@@ -165,12 +260,54 @@ class Server:
         self.iterations = iterations
         self.tune = tune
         free, _ = torch.cuda.mem_get_info(self.device)
+        self.free_at_start = free
+        self.min_free = free
         budget = int(budget_fraction * free) if budget_bytes is None else int(budget_bytes)
         self.sched = Scheduler(budget, max_active)
+        self.arena_fraction = arena_fraction
+        self.ctx_reserve_fraction = ctx_reserve_fraction
+        self.arena: Optional[Arena] = None
+        self.mem = None                                          # the arena's device buffer
+        self.ctx_used = 0                                        # measured bytes of live contexts
         self._sys_cache: Dict[int, object] = {}
         self.pool: Dict[int, List[Tuple[object, int]]] = collections.defaultdict(list)   # idle (ctx, bytes)
         self.ctx_bytes: Dict[int, int] = {}                     # measured per system
         self.idle_lru: collections.OrderedDict = collections.OrderedDict()
+        # one CUDA stream per slot, made once (a stream per job would leave device resources
+        # behind for every job served)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(max_active)]
+        self.free_streams = list(range(max_active))
+
+    # -- budget ---------------------------------------------------------------------------
+    def margin(self) -> int:
+        """Device bytes of the budget left out of the arena and the contexts' share: what the
+        library and the runtime allocate outside them (the contexts' auxiliary streams and
+        events, allocations a context makes on first use, torch's small buffers)."""
+        return int(0.02 * self.sched.budget)
+
+    def ctx_cap(self) -> int:
+        """Bytes the contexts may hold: the budget less the arena and the margin."""
+        return self.sched.budget - (self.arena.size if self.arena is not None else 0) - self.margin()
+
+    def _account(self):
+        used = self.ctx_used + (self.arena.used if self.arena is not None else 0)
+        self.sched.used = used
+        self.sched.peak_used = max(self.sched.peak_used, used)
+
+    def _sample_device(self):
+        f, _ = self.torch.cuda.mem_get_info(self.device)
+        self.min_free = min(self.min_free, f)
+
+    def _make_arena(self, size: int):
+        torch = self.torch
+        torch.cuda.synchronize(self.device)
+        torch.cuda.empty_cache()
+        self.arena = Arena(max(0, int(size)))
+        self.mem = torch.empty(max(self.arena.size, 256), dtype=torch.uint8, device=self.device)
+        self._sample_device()
+
+    def _view(self, off: int, nbytes: int, dtype, shape):
+        return self.mem[off:off + nbytes].view(dtype).view(shape)
 
     # -- systems and contexts ----------------------------------------------------------
     def system(self, sysid: int):
@@ -179,47 +316,47 @@ class Server:
         return self._sys_cache[sysid]
 
     def prepare(self, sysids: Sequence[int], contexts: bool = True):
-        """Ahead of the stream (not part of any job's latency): build the host-side systems
-        and, with `contexts`, one pooled context per system, tuned for its shape, while the
-        budget allows (smallest first)."""
+        """Ahead of the stream (not part of any job's latency): build the host-side systems,
+        and with `contexts` one pooled context per system, tuned for its shape, smallest first
+        while they leave half the budget; then the arena from what remains."""
         torch = self.torch
         for s in sysids:
             self.system(s)
-        if not contexts:
-            return
-        for s in sorted(sysids, key=lambda i: array_bytes(self.systems[i], self.precision)):
-            inst = self.systems[s]
-            if self._ctx_estimate(s) + array_bytes(inst, self.precision) > self.sched.free_bytes():
-                continue
-            ctx, cbytes, _ = self._get_ctx(s)
-            if self.tune:
-                from . import autotune
-                psi = self._bands(inst, inst.seed, torch.cuda.current_stream(self.device))
-                work = ctx.alloc_work(inst.nbands)
-                work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=self.device))
-                autotune.tune(ctx, psi, work)
-                del psi, work
-            self.pool[s].append((ctx, cbytes))
-            self.idle_lru[(s, id(ctx))] = True
-            self.sched.used += cbytes
-        torch.cuda.synchronize(self.device)
-        torch.cuda.empty_cache()
+        if contexts:
+            limit = int((1.0 - max(self.arena_fraction, 0.0)) * self.sched.budget)
+            for s in sorted(sysids, key=lambda i: array_bytes(self.systems[i], self.precision)):
+                inst = self.systems[s]
+                if self.ctx_used + self._ctx_estimate(s) > limit:
+                    continue
+                ctx, cbytes = self._new_ctx(s)
+                self.ctx_used += cbytes
+                if self.tune:
+                    from . import autotune
+                    psi = self._bands_alloc(inst, inst.seed)
+                    work = ctx.alloc_work(inst.nbands)
+                    work["C"].zero_()
+                    work["C"].diagonal().fill_(1.0)
+                    autotune.tune(ctx, psi, work)
+                    del psi, work
+                self.pool[s].append((ctx, cbytes))
+                self.idle_lru[(s, id(ctx))] = True
+        reserve = int(self.ctx_reserve_fraction * self.sched.budget)
+        self._make_arena(self.sched.budget - self.ctx_used - reserve - self.margin())
+        self._account()
 
     def _ctx_estimate(self, sysid: int) -> int:
+        """Bytes of a new context of the system: measured if one was made before, else an
+        upper estimate of its scratch (projections, Gram partials, subspace workspace, digit
+        planes of the tensor-core Gram and rotation, potential tables)."""
         if sysid in self.ctx_bytes:
             return self.ctx_bytes[sysid]
         inst = self.systems[sysid]
         nb = inst.nbands
-        return (320 << 20) + 24 * nb * nb * 16 + 2 * inst.npoints * 8
-
-    def need(self, job: Job) -> int:
-        inst = self.systems[job.system]
-        b = array_bytes(inst, self.precision)
-        if not self.pool[job.system]:
-            b += self._ctx_estimate(job.system)
-        return b
+        return (1536 << 20) + 24 * nb * nb * 16 + 4 * inst.npoints * 8
 
     def reclaim(self, short: int) -> int:
+        """Evict idle pooled contexts, least recently used first, until `short` bytes are
+        freed (or none is left); returns the bytes freed."""
         freed = 0
         while freed < short and self.idle_lru:
             key, _ = self.idle_lru.popitem(last=False)
@@ -233,64 +370,116 @@ class Server:
                     break
         return freed
 
-    def _get_ctx(self, sysid: int):
+    def _new_ctx(self, sysid: int):
+        """A new context of the system and its measured device bytes."""
         from . import api
         torch = self.torch
-        if self.pool[sysid]:
-            ctx, nbytes = self.pool[sysid].pop()
-            self.idle_lru.pop((sysid, id(ctx)), None)
-            return ctx, nbytes, False
         inst = self.systems[sysid]
+        torch.cuda.synchronize(self.device)
         f0, _ = torch.cuda.mem_get_info(self.device)
-        try:
-            ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
-        except api.PawFDError:
-            # the library allocates with cudaMalloc: give back what torch's cache holds, once
-            torch.cuda.empty_cache()
-            f0, _ = torch.cuda.mem_get_info(self.device)
-            ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
+        ctx = api.Context(self.system(sysid), max_bands=inst.nbands, device=self.device, precision=self.precision)
         f1, _ = torch.cuda.mem_get_info(self.device)
         nbytes = max(0, f0 - f1)
         self.ctx_bytes[sysid] = max(nbytes, self.ctx_bytes.get(sysid, 0))
-        return ctx, nbytes, True
+        self.min_free = min(self.min_free, f1)
+        return ctx, nbytes
 
     # -- one job ------------------------------------------------------------------------
-    def _bands(self, inst, seed, gen_stream):
+    def _bands_alloc(self, inst, seed):
+        """uniform(-1, 1) bands of the instance from a seeded generator (newly allocated)."""
         torch = self.torch
         g = torch.Generator(device=self.device)
         g.manual_seed(int(seed))
         shape = (inst.nbands,) + tuple(inst.n[::-1])
         rdt = torch.float32 if self.precision == "mixed" else torch.float64
-        with torch.cuda.stream(gen_stream):
-            re = torch.rand(shape, generator=g, device=self.device, dtype=rdt) * 2 - 1
-            if inst.complex_wf:
-                im = torch.rand(shape, generator=g, device=self.device, dtype=rdt) * 2 - 1
-                return torch.complex(re, im)
-            return re
+        re = torch.rand(shape, generator=g, device=self.device, dtype=rdt) * 2 - 1
+        if inst.complex_wf:
+            im = torch.rand(shape, generator=g, device=self.device, dtype=rdt) * 2 - 1
+            return torch.complex(re, im)
+        return re
 
-    def start(self, job: Job, now: float):
+    def _bands_into(self, inst, seed, psi, scratch):
+        """The same values as _bands_alloc, written into psi; `scratch` (a band array of the
+        same size) holds the real and imaginary parts of complex bands on the way."""
         torch = self.torch
+        g = torch.Generator(device=self.device)
+        g.manual_seed(int(seed))
+        shape = (inst.nbands,) + tuple(inst.n[::-1])
+        if not inst.complex_wf:
+            torch.rand(shape, generator=g, out=psi)
+            psi.mul_(2).sub_(1)
+            return
+        parts = scratch.view(psi.real.dtype).view((2,) + shape)
+        re, im = parts[0], parts[1]
+        torch.rand(shape, generator=g, out=re)
+        re.mul_(2).sub_(1)
+        torch.rand(shape, generator=g, out=im)
+        im.mul_(2).sub_(1)
+        torch.complex(re, im, out=psi)
+
+    def try_start(self, job: Job):
+        """Reserve what the job needs now, or None: its arrays in the arena, and a context
+        (an idle pooled one of its system, or a new one charged at its measured size, made
+        only when its measured or estimated size fits the contexts' share of the budget after
+        evicting idle contexts)."""
         inst = self.systems[job.system]
-        ctx, cbytes, fresh = self._get_ctx(job.system)
-        stream = torch.cuda.Stream(self.device)
+        sizes = job_array_sizes(inst, self.precision)
+        offs = self.arena.alloc_all(sizes)
+        if offs is None:
+            return None
+        if self.pool[job.system]:
+            ctx, cbytes = self.pool[job.system].pop()
+            self.idle_lru.pop((job.system, id(ctx)), None)
+            return offs, ctx, cbytes
+        cap = self.ctx_cap()
+        est = self._ctx_estimate(job.system)
+        if self.ctx_used + est > cap:
+            self.ctx_used -= self.reclaim(self.ctx_used + est - cap)
+        if self.ctx_used + est > cap:
+            for o, n in zip(offs, sizes):
+                self.arena.free(o, n)
+            return None
+        ctx, cbytes = self._new_ctx(job.system)
+        self.ctx_used += cbytes
+        if self.ctx_used > cap:
+            self.ctx_used -= self.reclaim(self.ctx_used - cap)
+            if self.ctx_used > cap:
+                self.sched.overruns += 1
+        return offs, ctx, cbytes
+
+    def start(self, job: Job, reservation, now: float):
+        torch = self.torch
+        offs, ctx, cbytes = reservation
+        inst = self.systems[job.system]
+        sizes = job_array_sizes(inst, self.precision)
+        nb, shape = inst.nbands, (inst.nbands,) + tuple(inst.n[::-1])
+        bufs = [self._view(offs[i], sizes[i], ctx.dtype, shape) for i in range(4)]
+        work = {"Hpsi": bufs[2], "Spsi": bufs[3],
+                "Hnm": self._view(offs[4], sizes[4], ctx.mat_dtype, (nb, nb)),
+                "Snm": self._view(offs[5], sizes[5], ctx.mat_dtype, (nb, nb)),
+                "C": self._view(offs[6], sizes[6], ctx.mat_dtype, (nb, nb)),
+                "eps": self._view(offs[7], sizes[7], torch.float64, (nb,))}
+        sidx = self.free_streams.pop()
+        stream = self.streams[sidx]
+        # the arena's ranges were last used on other streams: order after the work enqueued so far
+        stream.wait_stream(torch.cuda.current_stream(self.device))
         with torch.cuda.stream(stream):
-            psi = self._bands(inst, job.psi_seed, stream)
-            out = torch.empty_like(psi)
-            work = ctx.alloc_work(inst.nbands)
+            psi, out = bufs[0], bufs[1]
+            self._bands_into(inst, job.psi_seed, psi, out)
             if self.tune:
                 from . import autotune
-                if autotune.shape_key(ctx, inst.nbands) not in autotune._CACHE:
-                    work["C"].copy_(torch.eye(inst.nbands, dtype=work["C"].dtype, device=self.device))
+                if autotune.shape_key(ctx, nb) not in autotune._CACHE:
+                    work["C"].zero_()
+                    work["C"].diagonal().fill_(1.0)
                 autotune.tune(ctx, psi, work)
-            bufs = [psi, out]
+                self._bands_into(inst, job.psi_seed, psi, out)   # tuning may have written into the work arrays
+            pair = [psi, out]
             for it in range(self.iterations):
-                ctx.rr_step(bufs[it % 2], out=bufs[(it + 1) % 2], work=work)
+                ctx.rr_step(pair[it % 2], out=pair[(it + 1) % 2], work=work)
             done = torch.cuda.Event()
             done.record(stream)
-        nbytes = array_bytes(inst, self.precision) + (cbytes if fresh else 0)
-        state = dict(job=job, ctx=ctx, cbytes=cbytes, fresh=fresh, stream=stream, done=done, bufs=bufs, work=work,
-                     rec=JobRecord(job, admitted=now), nbytes=nbytes)
-        return state, nbytes
+        return dict(job=job, ctx=ctx, cbytes=cbytes, stream=stream, sidx=sidx, done=done, offs=offs, sizes=sizes,
+                    work=work, rec=JobRecord(job, admitted=now))
 
     def finish(self, state, now: float) -> JobRecord:
         rec = state["rec"]
@@ -298,6 +487,9 @@ class Server:
             rec.eps = state["work"]["eps"].cpu().numpy()
         state["ctx"].sync()
         rec.finished = now
+        for o, n in zip(state["offs"], state["sizes"]):
+            self.arena.free(o, n)
+        self.free_streams.append(state["sidx"])
         sysid = state["job"].system
         self.pool[sysid].append((state["ctx"], state["cbytes"]))
         self.idle_lru[(sysid, id(state["ctx"]))] = True
@@ -308,6 +500,8 @@ class Server:
             clock: Callable[[], float] = time.perf_counter) -> Dict:
         """Serve `jobs` (sorted by arrival) in real time.  Stops when every job has finished,
         or at `duration` seconds (unfinished jobs are counted, not waited for)."""
+        if self.arena is None:
+            self._make_arena(int(self.arena_fraction * self.sched.budget) - self.ctx_used - self.margin())
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         active: Dict[int, dict] = {}
         done: List[JobRecord] = []
@@ -324,25 +518,30 @@ class Server:
                 if st["done"].query():
                     rec = self.finish(st, clock() - t0)
                     done.append(rec)
-                    # the job's arrays are released; a context it created stays charged while pooled
-                    self.sched.retire(st["job"], keep=st["cbytes"] if st["fresh"] else 0)
+                    self.sched.retire(st["job"])
                     del active[jid]
                     progressed = True
             while True:
-                job = self.sched.pick(self.need, self.reclaim)
-                if job is None:
+                got = self.sched.pick_with(self.try_start)
+                if got is None:
                     break
-                st, nbytes = self.start(job, clock() - t0)
-                self.sched.admit(job, nbytes)
+                job, reservation = got
+                st = self.start(job, reservation, clock() - t0)
+                self.sched.active[job.job_id] = 0          # a slot; bytes are accounted below
                 active[job.job_id] = st
                 progressed = True
+            self._account()
+            self._sample_device()
             if not progressed:
                 nxt = pending[0].arrival - (clock() - t0) if pending else poll_s
                 time.sleep(max(0.0, min(poll_s, nxt)))
         elapsed = clock() - t0
+        self._sample_device()
         return {"records": done, "elapsed": elapsed, "unfinished": len(active) + len(self.sched.queue) + len(pending),
                 "active_at_end": len(active), "queued_at_end": len(self.sched.queue), "peak_used": self.sched.peak_used,
-                "budget": self.sched.budget, "max_queue": self.sched.max_queue, "overruns": self.sched.overruns}
+                "budget": self.sched.budget, "max_queue": self.sched.max_queue, "overruns": self.sched.overruns,
+                "device_peak_used": self.free_at_start - self.min_free, "arena_bytes": self.arena.size,
+                "arena_peak": self.arena.peak, "context_bytes": self.ctx_used}
 
     def close(self):
         for lst in self.pool.values():
@@ -350,6 +549,8 @@ class Server:
                 ctx.close()
         self.pool.clear()
         self.idle_lru.clear()
+        self.mem = None
+        self.arena = None
 
 
 def latency_stats(records: Sequence[JobRecord], warmup: float = 0.0) -> Dict:

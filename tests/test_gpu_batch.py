@@ -121,6 +121,8 @@ def test_served_results_same_alone_and_in_mix(dev):
     mixed = srv.run(jobs)
     assert mixed["unfinished"] == 0 and len(mixed["records"]) == len(jobs)
     assert mixed["peak_used"] <= budget and mixed["overruns"] == 0
+    # the device itself (free memory sampled through the run) stayed within the budget
+    assert mixed["device_peak_used"] <= budget
     got = {r.job.job_id: r.eps for r in mixed["records"]}
     srv.close()
     for job in jobs:

@@ -87,6 +87,74 @@ def test_scheduler_reclaims_idle_memory_and_skips_impossible_jobs():
     assert [j.job_id for j in sch.queue] == [0]
 
 
+def test_arena_first_fit_alignment_and_coalescing():
+    a = serve.Arena(10000, align=256)
+    assert a.size == 9984
+    offs = [a.alloc(n) for n in (100, 300, 256, 1000)]
+    assert offs == [0, 256, 768, 1024]                      # first fit, 256-byte aligned
+    assert a.used == 256 + 512 + 256 + 1024
+    a.free(256, 300)                                        # a hole of 512 bytes
+    assert a.alloc(600) == 2048                             # does not fit the hole
+    assert a.alloc(500) == 256                              # the first range that fits
+    a.free(0, 100)
+    a.free(256, 500)
+    a.free(768, 256)
+    # the three freed neighbours merged into one range at 0
+    assert a.free_ranges[0] == (0, 1024)
+    a.free(1024, 1000)
+    a.free(2048, 600)
+    assert a.free_ranges == [(0, 9984)] and a.used == 0
+    assert a.peak == 256 + 512 + 256 + 1024 + 768
+
+
+def test_arena_alloc_all_is_all_or_nothing():
+    a = serve.Arena(4096, align=256)
+    held = a.alloc(2048)
+    assert a.alloc_all([1024, 1024, 256]) is None
+    assert a.used == 2048 and a.free_ranges == [(2048, 2048)]
+    offs = a.alloc_all([1024, 1024])
+    assert offs == [2048, 3072] and a.used == 4096
+    for o in offs:
+        a.free(o, 1024)
+    a.free(held, 2048)
+    assert a.free_ranges == [(0, 4096)]
+
+
+def test_arena_random_alloc_free_never_overlaps():
+    rng = np.random.default_rng(3)
+    a = serve.Arena(1 << 20, align=256)
+    live = {}
+    for step in range(3000):
+        if live and (rng.random() < 0.45 or len(live) > 60):
+            off = list(live)[int(rng.integers(len(live)))]
+            a.free(off, live.pop(off))
+        else:
+            n = int(rng.integers(1, 40000))
+            off = a.alloc(n)
+            if off is not None:
+                assert off % 256 == 0 and off + n <= a.size
+                live[off] = n
+        spans = sorted((o, o + ((n + 255) // 256) * 256) for o, n in live.items())
+        assert all(spans[i][1] <= spans[i + 1][0] for i in range(len(spans) - 1))
+        assert a.used == sum(e - o for o, e in spans)
+        free = sum(ln for _, ln in a.free_ranges)
+        assert free + a.used == a.size
+        assert all(a.free_ranges[i][0] + a.free_ranges[i][1] < a.free_ranges[i + 1][0]
+                   for i in range(len(a.free_ranges) - 1))    # no two free ranges left unmerged
+
+
+def test_scheduler_pick_with_first_fit_and_slots():
+    sch = serve.Scheduler(budget=100, max_active=2)
+    for j in range(5):
+        sch.arrive(serve.Job(j, 0.0, 0, j))
+    fits = {0: None, 1: None, 2: "r2", 3: "r3", 4: "r4"}
+    job, r = sch.pick_with(lambda job: fits[job.job_id])
+    assert job.job_id == 2 and r == "r2" and [j.job_id for j in sch.queue] == [0, 1, 3, 4]
+    sch.active[2] = 0
+    sch.active[9] = 0
+    assert sch.pick_with(lambda job: "any") is None         # no free slot
+
+
 def test_array_bytes():
     inst = synth.Instance((10, 11, 12), 7, 2, 0, True, (0.0, 0.0, 0.0))
     assert serve.array_bytes(inst, "mixed") == 4 * 1320 * 7 * 8 + 3 * 49 * 16 + 56
