@@ -167,6 +167,22 @@ def apply_S(system, psi: np.ndarray):
     return _apply(1, system, psi)
 
 
+def nonlocal_term(system, psi: np.ndarray, which: str = "H") -> np.ndarray:
+    """sum_a sum_ii' |p_i^a> X^a_ii' <p_i'^a|psi> for X = dH ("H") or dS ("S"): the nonlocal
+    term of Eq. (dh) and of the overlap operator, without the kinetic, local and identity
+    terms."""
+    g = _Geometry(system)
+    psi, nb = _psi_in(system, psi)
+    out = np.empty_like(psi)
+    P = np.zeros((g.Ip, nb), dtype=psi.dtype)
+    dmat = g.dH if which == "H" else g.dS
+    rc = lib().oracle_apply(2, _ptr(g.n), _ptr(g.L), _ptr(g.k), int(g.cplx), _ptr(g.v), g.natoms, _ptr(g.nproj),
+                            _ptr(g.box_lo), _ptr(g.box_n), _ptr(g.proj), _ptr(g.proj_off), _ptr(dmat),
+                            _ptr(g.dmat_off), _ptr(psi), nb, _ptr(out), _ptr(P))
+    assert rc == 0
+    return out
+
+
 def gram(A: np.ndarray, B: np.ndarray, dV: float, nb: int) -> np.ndarray:
     """M[n][m] = dV sum_r conj(A_n(r)) B_m(r)."""
     cplx = np.iscomplexobj(A) or np.iscomplexobj(B)
@@ -392,3 +408,65 @@ def refine(system, psi_lo: np.ndarray, C_lo: Optional[np.ndarray] = None) -> dic
     resid = residual_norms(Hpsi, Spsi, eps, system.dV)
     return {"psi": psi, "Hpsi": Hpsi, "Spsi": Spsi, "Hnm": Hnm, "Snm": Snm, "theta": theta, "eps": eps, "C": C,
             "resid": resid}
+
+
+# ------------------------------------------------------------------------------------------
+# Plane-wave representation (the wave-function section: psi_kn(r) = sum_G C_nG e^{i(k+G).r})
+# ------------------------------------------------------------------------------------------
+
+def pw_wavevectors(system):
+    """The components (k + G)_c on the FFT grid of the cell, each [N3][N2][N1]: G_c runs over
+    2 pi j / L_c for the FFT frequencies j of N_c points (0, 1, ..., -1)."""
+    q = []
+    for c in range(3):
+        g1 = system.k[c] + 2.0 * np.pi * np.fft.fftfreq(system.n[c], d=1.0 / system.n[c]) / system.cell[c]
+        shape = [1, 1, 1]
+        shape[2 - c] = system.n[c]
+        q.append(np.broadcast_to(g1.reshape(shape), (system.n[2], system.n[1], system.n[0])))
+    return q
+
+
+def pw_kinetic(system) -> np.ndarray:
+    """The plane-wave kinetic energies |k + G|^2 / 2 (Hartree), [N3][N2][N1]."""
+    qx, qy, qz = pw_wavevectors(system)
+    return 0.5 * (qx * qx + qy * qy + qz * qz)
+
+
+def bloch_phase(system) -> np.ndarray:
+    """e^{i k.r} at the grid points r = (i1 h1, i2 h2, i3 h3), [N3][N2][N1]."""
+    z, y, x = np.meshgrid(*[np.arange(system.n[c]) * system.h[c] for c in (2, 1, 0)], indexing="ij")
+    return np.exp(1j * (system.k[0] * x + system.k[1] * y + system.k[2] * z))
+
+
+def pw_to_grid(system, C: np.ndarray) -> np.ndarray:
+    """psi(r) = sum_G C_G e^{i(k+G).r} at the grid points, for every band of C [nb][N3][N2][N1]
+    (G in FFT order): e^{ik.r} times the inverse discrete Fourier transform times K."""
+    C = np.asarray(C, np.complex128)
+    K = system.npoints
+    return bloch_phase(system)[None] * np.fft.ifftn(C, axes=(1, 2, 3)) * K
+
+
+def grid_to_pw(system, psi: np.ndarray) -> np.ndarray:
+    """C_G = (1/K) sum_r e^{-i(k+G).r} psi(r), the inverse of pw_to_grid."""
+    psi = np.asarray(psi, np.complex128)
+    return np.fft.fftn(np.conj(bloch_phase(system))[None] * psi, axes=(1, 2, 3)) / system.npoints
+
+
+def pw_apply(system, C: np.ndarray, which: str = "H", ecut: float = 0.0) -> np.ndarray:
+    """H C or S C in the plane-wave representation (a reading of the PW mode: the
+    generalized eigenproblem of Eq. (dh) in the basis e^{i(k+G).r} of the cell's FFT grid):
+      (H C)_G = |k+G|^2 / 2 C_G + [v psi + sum_a |p^a> dH^a <p^a|psi>]_G,
+      (S C)_G = C_G + [sum_a |p^a> dS^a <p^a|psi>]_G,
+    with psi = pw_to_grid(C), [f]_G = grid_to_pw(f), and the projectors sampled on the grid
+    (the same projector boxes as the finite-difference operator).  With ecut > 0 the basis is
+    the sphere |k+G|^2 / 2 <= ecut: the output is zero outside it (C is taken as given)."""
+    C = np.asarray(C, np.complex128)
+    psi = pw_to_grid(system, C)
+    if which == "H":
+        v = np.asarray(system.vloc, np.float64).reshape(system.n[2], system.n[1], system.n[0])
+        out = pw_kinetic(system)[None] * C + grid_to_pw(system, v[None] * psi + nonlocal_term(system, psi, "H"))
+    else:
+        out = C + grid_to_pw(system, nonlocal_term(system, psi, "S"))
+    if ecut > 0:
+        out = out * (pw_kinetic(system) <= ecut)[None]
+    return out

@@ -270,7 +270,8 @@ int oracle_project(const int* n, const double* L, const double* k, int is_comple
   return 0;
 }
 
-/* which = 0: H psi (kinetic + local + dH nonlocal);  which = 1: S psi (psi + dS nonlocal).
+/* which = 0: H psi (kinetic + local + dH nonlocal);  which = 1: S psi (psi + dS nonlocal);
+   which = 2: the nonlocal term alone, sum_a sum_ii' p_i^a dmat^a_ii' <p_i'^a|psi>.
    dmat holds dH or dS accordingly.  If P_out != NULL the projections are returned too. */
 int oracle_apply(int which, const int* n, const double* L, const double* k, int is_complex, const double* v,
                  int natoms, const int* nproj, const int* box_lo, const int* box_n, const double* proj,
@@ -292,8 +293,10 @@ int oracle_apply(int which, const int* n, const double* L, const double* k, int 
     free(zout);
     zout = to_complex(tmp, K * nb, is_complex);
     free(tmp);
-  } else {
+  } else if (which == 1) {
     memcpy(zout, zpsi, sizeof(zdouble) * (size_t)(K * nb));
+  } else {
+    memset(zout, 0, sizeof(zdouble) * (size_t)(K * nb));
   }
   zdouble* zP = (zdouble*)calloc((size_t)(Ip * nb > 0 ? Ip * nb : 1), sizeof(zdouble));
   project_all(&g, &at, zpsi, nb, zP);

@@ -723,3 +723,100 @@ def test_poisson_plane_wave_closed_form():
     L = sum((w[0] + 2 * sum(w[m] * math.cos(m * G[c] * s.h[c]) for m in (1, 2, 3))) / s.h[c] ** 2 for c in range(3))
     v = O.poisson(s, rho)
     assert np.allclose(v, -4 * math.pi * rho / L, rtol=0, atol=1e-13 * np.max(np.abs(4 * math.pi * rho / L)))
+
+
+# ------------------------------------------------------------------------------------------
+# f-4: H and S in the plane-wave representation (wave-function section; reading)
+# ------------------------------------------------------------------------------------------
+
+def pw_unit_vectors(system, js):
+    """Coefficient arrays [len(js)][N3][N2][N1] with a single 1 at the FFT index of G = 2 pi j / L."""
+    C = np.zeros((len(js), system.n[2], system.n[1], system.n[0]), complex)
+    for b, j in enumerate(js):
+        C[b, j[2] % system.n[2], j[1] % system.n[1], j[0] % system.n[0]] = 1.0
+    return C
+
+
+def test_pw_free_plane_waves_closed_form():
+    # no potential, no atoms: every basis vector is an eigenvector of H with |k + G|^2 / 2 (the
+    # exact kinetic energy, not the finite-difference symbol) and of S with 1
+    k = (0.37, -0.21, 0.55)
+    s = free_system((10, 9, 8), (5.0, 4.6, 4.1), k=k, complex_wf=True)
+    js = [(0, 0, 0), (1, 0, 0), (0, 2, -1), (3, -4, 2), (-5, 4, 3), (4, -4, -4)]
+    C = pw_unit_vectors(s, js)
+    HC = O.pw_apply(s, C, "H")
+    SC = O.pw_apply(s, C, "S")
+    for b, j in enumerate(js):
+        q = [k[c] + 2 * math.pi * j[c] / s.cell[c] for c in range(3)]
+        lam = 0.5 * sum(v * v for v in q)
+        assert np.allclose(HC[b], lam * C[b], rtol=0, atol=1e-13 * max(lam, 1.0))
+        assert np.allclose(SC[b], C[b], rtol=0, atol=1e-14)
+
+
+def test_pw_constant_potential_shifts_the_spectrum():
+    k = (0.1, 0.2, -0.3)
+    v0 = -0.7
+    s = free_system((8, 6, 5), (4.0, 3.0, 2.5), k=k, complex_wf=True, vloc=np.full((5, 6, 8), v0))
+    C = rand_psi(s, 4, 90)
+    HC = O.pw_apply(s, C, "H")
+    assert np.allclose(HC, (O.pw_kinetic(s)[None] + v0) * C, rtol=0, atol=1e-13 * np.max(np.abs(HC)))
+
+
+def test_pw_grid_transforms_are_inverse_and_keep_the_norm():
+    s = small_system(complex_wf=True)
+    C = rand_psi(s, 3, 91)
+    psi = O.pw_to_grid(s, C)
+    assert np.allclose(O.grid_to_pw(s, psi), C, rtol=0, atol=1e-14 * np.max(np.abs(C)))
+    # Parseval: dV sum_r |psi|^2 = Omega sum_G |C_G|^2
+    omega = s.cell[0] * s.cell[1] * s.cell[2]
+    assert np.allclose(s.dV * np.sum(np.abs(psi) ** 2, axis=(1, 2, 3)), omega * np.sum(np.abs(C) ** 2, axis=(1, 2, 3)),
+                       rtol=1e-13)
+    # a single coefficient is the plane wave e^{i(k+G).r} at the grid points
+    j = (2, -1, 1)
+    x, y, z = grid_coords(s)
+    q = [s.k[c] + 2 * math.pi * j[c] / s.cell[c] for c in range(3)]
+    wave = O.pw_to_grid(s, pw_unit_vectors(s, [j]))[0]
+    assert np.allclose(wave, np.exp(1j * (q[0] * x + q[1] * y + q[2] * z)), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("case", ["bloch", "selfwrap-bloch"])
+def test_pw_dense_bruteforce(case):
+    # the plane-wave operators as explicit K x K matrices in the coefficient basis:
+    # A_H = diag(|k+G|^2 / 2) + U^-1 (H - T) U and A_S = U^-1 S U, with U[r, G] = e^{i(k+G).r},
+    # U^-1 = U^H / K, and H, S, T (the finite-difference kinetic) the dense real-space operators;
+    # applied to random coefficients and diagonalized over the full basis
+    s = small_system(**TINY[case])
+    H, S = dense_operators(s)
+    T, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=True))
+    K = s.npoints
+    qx, qy, qz = (q.reshape(-1) for q in O.pw_wavevectors(s))
+    x, y, z = (a.reshape(-1) for a in grid_coords(s))
+    U = np.exp(1j * (np.outer(x, qx) + np.outer(y, qy) + np.outer(z, qz)))
+    A_H = np.diag(0.5 * (qx * qx + qy * qy + qz * qz)) + U.conj().T @ (H - T) @ U / K
+    A_S = U.conj().T @ S @ U / K
+    C = rand_psi(s, 5, 92)
+    Cm = C.reshape(5, K).T
+    HC = O.pw_apply(s, C, "H").reshape(5, K).T
+    SC = O.pw_apply(s, C, "S").reshape(5, K).T
+    assert np.allclose(HC, A_H @ Cm, rtol=0, atol=1e-12 * np.max(np.abs(HC)))
+    assert np.allclose(SC, A_S @ Cm, rtol=0, atol=1e-12 * np.max(np.abs(SC)))
+    # the full basis: Rayleigh-Ritz with the oracle's Gram and subspace solve gives the dense
+    # generalized spectrum
+    E = np.eye(K, dtype=complex).reshape(K, s.n[2], s.n[1], s.n[0])
+    Hnm = O.gram(E, O.pw_apply(s, E, "H"), 1.0, K)
+    Snm = O.gram(E, O.pw_apply(s, E, "S"), 1.0, K)
+    eps, _, _ = O.subspace_diag(Hnm, Snm)
+    exact = scipy.linalg.eigh(A_H, A_S, eigvals_only=True)
+    assert np.allclose(eps, exact, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(exact))))
+
+
+def test_pw_energy_cutoff_masks_the_output():
+    s = small_system(complex_wf=True)
+    C = rand_psi(s, 2, 93)
+    ecut = 0.4 * np.max(O.pw_kinetic(s))
+    mask = O.pw_kinetic(s) <= ecut
+    Cm = C * mask[None]
+    HC = O.pw_apply(s, Cm, "H", ecut=ecut)
+    full = O.pw_apply(s, Cm, "H")
+    assert np.all(HC[:, ~mask] == 0)
+    assert np.array_equal(HC[:, mask], full[:, mask])
