@@ -293,6 +293,40 @@ int pawfd_atomic_density(pawfd_ctx* ctx, const void* P, int nb, const double* f,
 int pawfd_poisson(pawfd_ctx* ctx, const double* rho, double* v, double tol, int maxiter, double* work, int* iters,
                   double* resid);
 
+/* H and S in the plane-wave representation (the wave-function section writes a Bloch state
+ * as psi_kn(r) = sum_G C_nG e^{i(k+G).r}; the paper's GPU port works in this representation).
+ * This is a reading of the PW mode on the cell's FFT grid: G runs over the N1 x N2 x N3
+ * frequencies of the grid, stored [nb][N3][N2][N1] in FFT order (index j_c for G_c = 2 pi f_c /
+ * L_c, f_c = j_c for j_c < (N_c + 1) / 2, else j_c - N_c), and
+ *   (H C)_G = |k+G|^2 / 2 C_G + [v psi + sum_a |p^a> dH^a <p^a|psi>]_G,
+ *   (S C)_G = C_G + [sum_a |p^a> dS^a <p^a|psi>]_G,
+ * with psi(r) = sum_G C_G e^{i(k+G).r} at the grid points and [f]_G = (1/K) sum_r
+ * e^{-i(k+G).r} f(r): the kinetic operator is exact in this basis (not the finite-difference
+ * stencil), v and the projector boxes are those of the context (Eq. (dh)).  ecut > 0 restricts
+ * the basis to the sphere |k+G|^2 / 2 <= ecut (Hartree): the output is zero outside it (the
+ * caller's C should be zero there too); ecut <= 0 keeps every G.
+ *   ctx: a complex context (PAWFD_C128, or PAWFD_C64 for FP32 arithmetic), grid sizes with no
+ *        prime factor other than 2, 3 and 5; the FFT tables (twiddles, e^{ik.r}, |k+G|^2 / 2) are
+ *        allocated by the first plane-wave call on the context (it waits for the context's
+ *        stream; make it before any stream capture);
+ *   C, HC / SC: [nb][K] complex coefficients of the context's dtype; work: [2][nb][K] of the
+ *        same dtype (psi on the grid and the local and nonlocal terms), all caller-owned and
+ *        pairwise distinct.  The projections of psi are left in the context's scratch.
+ * The Gram matrices of a plane-wave Rayleigh-Ritz step are those of pawfd_gram on the
+ * coefficient arrays (they carry dV instead of the cell volume, a common factor K that leaves
+ * the eigenvalues unchanged).  Returns PAWFD_EINVAL for a real context, another grid factor,
+ * nb outside 1..max_bands, null or aliased arrays; PAWFD_ENOMEM if the tables cannot be
+ * allocated.  Asynchronous like the calls above. */
+int pawfd_pw_apply_H(pawfd_ctx* ctx, const void* C, int nb, double ecut, void* HC, void* work);
+int pawfd_pw_apply_S(pawfd_ctx* ctx, const void* C, int nb, double ecut, void* SC, void* work);
+
+/* The two representations of the same bands: psi(r) = sum_G C_G e^{i(k+G).r} at the grid
+ * points (pawfd_pw_to_grid; C and psi [nb][K], distinct) and its inverse C_G = (1/K) sum_r
+ * e^{-i(k+G).r} psi(r) (pawfd_pw_from_grid; work: [nb][K], a copy of psi that the transform
+ * overwrites).  Arguments and errors as pawfd_pw_apply_H. */
+int pawfd_pw_to_grid(pawfd_ctx* ctx, const void* C, int nb, void* psi);
+int pawfd_pw_from_grid(pawfd_ctx* ctx, const void* psi, int nb, void* C, void* work);
+
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
  * PAWFD_C128) of the same system as the mixed context whose bands psi_lo (PAWFD_R32 or

@@ -66,6 +66,10 @@ SIGNATURES = {
     "pawfd_batch_last_error": ([VP], ctypes.c_char_p),
     "pawfd_batch_destroy": ([VP], I),
     "pawfd_gram_noalloc": ([VP, VP, ctypes.c_longlong, I, I, D, VP, VP], I),
+    "pawfd_pw_apply_H": ([VP, VP, I, D, VP, VP], I),
+    "pawfd_pw_apply_S": ([VP, VP, I, D, VP, VP], I),
+    "pawfd_pw_to_grid": ([VP, VP, I, VP], I),
+    "pawfd_pw_from_grid": ([VP, VP, I, VP, VP], I),
 }
 
 _lock = threading.Lock()

@@ -426,6 +426,44 @@ class Context:
             self.sync()
         return out
 
+    # -- plane-wave representation (pawfd_pw_*) ------------------------------------------
+    def _pw_check(self, C, name):
+        if not self.complex:
+            raise ValueError("the plane-wave representation needs a complex context")
+        return self._bands(C, name)
+
+    def pw_apply(self, C, which: str = "H", ecut: float = 0.0, out=None, work=None):
+        """H C or S C in the plane-wave representation (pawfd_pw_apply_H / _S): C holds the
+        coefficients of nb bands on the cell's FFT grid, [nb, N3, N2, N1] in FFT order."""
+        nb = self._pw_check(C, "C")
+        out = self.empty_bands(nb) if out is None else out
+        self._out_bands(out, nb, "out")
+        work = self.empty_bands(2 * nb) if work is None else work
+        self._out_bands(work, 2 * nb, "work")
+        fn = {"H": self.lib.pawfd_pw_apply_H, "S": self.lib.pawfd_pw_apply_S}[which]
+        self._call(fn, ctypes.c_void_p(C.data_ptr()), nb, float(ecut), ctypes.c_void_p(out.data_ptr()),
+                   ctypes.c_void_p(work.data_ptr()))
+        return out
+
+    def pw_to_grid(self, C, out=None):
+        """psi(r) = sum_G C_G e^{i(k+G).r} at the grid points (pawfd_pw_to_grid)."""
+        nb = self._pw_check(C, "C")
+        out = self.empty_bands(nb) if out is None else out
+        self._out_bands(out, nb, "out")
+        self._call(self.lib.pawfd_pw_to_grid, ctypes.c_void_p(C.data_ptr()), nb, ctypes.c_void_p(out.data_ptr()))
+        return out
+
+    def pw_from_grid(self, psi, out=None, work=None):
+        """C_G = (1/K) sum_r e^{-i(k+G).r} psi(r) (pawfd_pw_from_grid)."""
+        nb = self._pw_check(psi, "psi")
+        out = self.empty_bands(nb) if out is None else out
+        self._out_bands(out, nb, "out")
+        work = self.empty_bands(nb) if work is None else work
+        self._out_bands(work, nb, "work")
+        self._call(self.lib.pawfd_pw_from_grid, ctypes.c_void_p(psi.data_ptr()), nb, ctypes.c_void_p(out.data_ptr()),
+                   ctypes.c_void_p(work.data_ptr()))
+        return out
+
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             self.lib.pawfd_destroy(self._h)

@@ -285,7 +285,8 @@ void free_ctx(pawfd_ctx* c) {
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_dscale, c->d_barrier, c->d_status, c->d_reduce,
                   c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
-                  c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df, c->d_vloc64};
+                  c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df, c->d_vloc};
+  free_pw(c);
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
@@ -341,21 +342,24 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
       vzero = vzero && d->vloc[r] == 0.0;
     }
     c->free_operator = vzero && d->natoms == 0;
+    // and v itself (the fixed-point stencil, whose centre weight is an exact integer, and the
+    // plane-wave representation, whose kinetic term is separate)
     if (is_fp32(c)) {
       std::vector<float> vf(vs.begin(), vs.end());
       float* p = dev_alloc<float>(c, c->K, &rc);
       upload(c, p, vf.data(), c->K, &rc);
       c->d_vshift = p;
+      std::vector<float> v0(d->vloc, d->vloc + c->K);
+      float* q = dev_alloc<float>(c, c->K, &rc);
+      upload(c, q, v0.data(), c->K, &rc);
+      c->d_vloc = q;
     } else {
       double* p = dev_alloc<double>(c, c->K, &rc);
       upload(c, p, vs.data(), c->K, &rc);
       c->d_vshift = p;
-      if (c->dtype == PAWFD_R64) {
-        // v itself for the fixed-point stencil (its centre weight is an exact integer)
-        double* v = dev_alloc<double>(c, c->K, &rc);
-        upload(c, v, d->vloc, c->K, &rc);
-        c->d_vloc64 = v;
-      }
+      double* q = dev_alloc<double>(c, c->K, &rc);
+      upload(c, q, d->vloc, c->K, &rc);
+      c->d_vloc = q;
     }
   }
   if (rc == PAWFD_OK) rc = build_tables(c, d);

@@ -190,6 +190,18 @@ struct KernelTimer {
   cudaEvent_t start[CAP] = {}, stop[CAP] = {};
 };
 
+namespace pawfd {
+// Plane-wave representation (pw.cu): FFT tables of the cell's grid, made on first use.
+struct PwPlan {
+  bool ready = false;
+  int nf[3] = {0, 0, 0};          // radix stages per axis
+  int fac[3][16] = {};            // radices per axis
+  void* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i j / N_c}, complex of the band precision
+  void* phase = nullptr;          // e^{i k.r} at the grid points [K]
+  void* kin = nullptr;            // |k+G|^2 / 2 [K], real of the band precision
+};
+}  // namespace pawfd
+
 struct pawfd_ctx {
   KernelTimer ktimer;
   int n[3];
@@ -199,7 +211,7 @@ struct pawfd_ctx {
   size_t K;
   cudaStream_t stream;
   void* d_vshift = nullptr;                   // v(r) - 1/2 c0 sum_c 1/h_c^2 (double or float)
-  void* d_vloc64 = nullptr;                   // real FP64: v(r) itself (fixed-point stencil)
+  void* d_vloc = nullptr;                     // v(r) itself in the band precision (double or float)
   pawfd::AtomTables at;
   void* d_P = nullptr;                        // [Ip][max_bands] projection scratch
   void* d_Q = nullptr;                        // [Ip][max_bands] FP64 dS P of the overlap correction
@@ -233,6 +245,7 @@ struct pawfd_ctx {
   cudaEvent_t aux_fork = nullptr, aux_join = nullptr;
   bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic
   pawfd::TcScratch tc;
+  pawfd::PwPlan pw;
   std::string err;
 };
 
@@ -277,6 +290,7 @@ bool gram_slice_psi(pawfd_ctx* c, const void* psi, int nb);
 int ensure_aux_stream(pawfd_ctx* c);
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
+void free_pw(pawfd_ctx* c);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout = -1);
 // bracket one timed kernel launch on the context's stream (no-ops unless timing is on)
 void ktimer_begin(pawfd_ctx* c);

@@ -1,0 +1,428 @@
+// pw.cu -- H and S in the plane-wave representation, on the library's own FFT kernels.
+//
+// The wave-function section writes a Bloch state in plane waves,
+//     psi_kn(r) = sum_G C_nG e^{i (k + G).r},
+// the representation of the paper's GPU port.  On the cell's FFT grid (the grid of the
+// finite-difference operator, G over the N1 x N2 x N3 frequencies in FFT order) the
+// generalized eigenproblem of Eq. (dh) reads H C = eps S C with
+//     (H C)_G = |k+G|^2 / 2 C_G + [v psi + sum_a |p^a> dH^a <p^a|psi>]_G,
+//     (S C)_G = C_G + [sum_a |p^a> dS^a <p^a|psi>]_G,
+// psi(r) = e^{ik.r} sum_G C_G e^{iG.r} at the grid points and [f]_G = (1/K) sum_r
+// e^{-i(k+G).r} f(r): the kinetic operator is exact in this basis, the local potential and the
+// projectors (the same grid-sampled boxes as the finite-difference operator) act on the grid.
+// With an energy cutoff the basis is the sphere |k+G|^2 / 2 <= ecut and the output is zero
+// outside it.
+//
+// FFTs: three passes, one per axis, each a batch of 1-D transforms of the lines along that
+// axis.  A CTA stages a group of lines in shared memory and runs a mixed-radix Stockham
+// transform (radices 4, 2, 3, 5; autosorting, so no bit reversal), ping-ponging between two
+// buffers, with twiddles from a table e^{-2 pi i j / N} in shared memory.  Lines along x are
+// contiguous; lines along y and z are gathered as tiles of consecutive x, so that both the
+// loads and the stores of every pass are coalesced.  The Bloch phase, the local potential, the
+// 1/K normalisation, the kinetic (or identity) term and the cutoff are applied in the first
+// or last pass of each transform.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pawfd_internal.cuh"
+
+namespace pawfd {
+namespace {
+
+constexpr int FFT_NT = 256;
+constexpr int MAX_FAC = 16;
+
+template <class R>
+struct FftArgs {
+  int N;                       // transform length (the axis' grid size)
+  int nf;                      // number of radix stages
+  int fac[MAX_FAC];            // radices, in order
+  const cplx<R>* tw;           // e^{-2 pi i j / N}, j < N
+  int inverse;                 // 1: e^{+i ...}, no normalisation
+  int axis;                    // 0 (x), 1 (y), 2 (z)
+  int n1, n2, n3;
+  long long K;
+  int nl;                      // lines per CTA
+  int tiles;                   // axes 1, 2: tiles of nl consecutive x per row (ceil(n1 / nl))
+  long long nlines;            // axis 0: nb n2 n3 lines
+  const cplx<R>* in;
+  cplx<R>* out;
+  // prologue: 1 = multiply every input value by conj(phase[r])
+  int pre;
+  const cplx<R>* phase;
+  // epilogue: 0 = store; 1 = store y phase[r] (psi), and v[r] psi into out2 (0 if v is null);
+  // 2 = store y scale, plus kin[r] Cin (add_kin) or Cin (otherwise) when Cin is set, where
+  // kin[r] <= ecut (or ecut <= 0), else 0
+  int post;
+  cplx<R>* out2;
+  const R* v;
+  const R* kin;
+  const cplx<R>* Cin;
+  R scale;
+  double ecut;
+  int add_kin;
+  // butterfly constants: sqrt(3)/2, cos(2 pi/5), cos(4 pi/5), sin(2 pi/5), sin(4 pi/5)
+  R s3, c51, c52, s51, s52;
+};
+
+// i s z
+template <class R>
+__device__ __forceinline__ cplx<R> imul(R s, cplx<R> z) {
+  return cplx<R>{-s * z.im, s * z.re};
+}
+
+// One line element: global index (band offset included) and grid point r within the band of
+// element i of line l of this CTA; false past the grid.
+template <class R>
+__device__ __forceinline__ bool element(const FftArgs<R>& a, int l, int i, long long& g, long long& r) {
+  if (a.axis == 0) {
+    const long long L = (long long)blockIdx.x * a.nl + l;
+    if (L >= a.nlines) return false;
+    g = L * a.n1 + i;
+    r = g % a.K;
+    return true;
+  }
+  const int xt = blockIdx.x % a.tiles;
+  const long long row = blockIdx.x / a.tiles;   // (band, z) for axis 1, (band, y) for axis 2
+  const int x = xt * a.nl + l;
+  if (x >= a.n1) return false;
+  if (a.axis == 1) {
+    const long long band = row / a.n3;
+    const int z = (int)(row % a.n3);
+    r = ((long long)z * a.n2 + i) * a.n1 + x;
+    g = band * a.K + r;
+  } else {
+    const long long band = row / a.n2;
+    const int y = (int)(row % a.n2);
+    r = ((long long)i * a.n2 + y) * a.n1 + x;
+    g = band * a.K + r;
+  }
+  return true;
+}
+
+template <class R>
+__global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* W = (cplx<R>*)smem_raw;
+  cplx<R>* X = W + a.N;
+  cplx<R>* Y = X + (size_t)a.nl * a.N;
+  const int N = a.N, nl = a.nl, tid = threadIdx.x;
+  for (int j = tid; j < N; j += FFT_NT) {
+    const cplx<R> w = a.tw[j];
+    W[j] = a.inverse ? cplx<R>{w.re, -w.im} : w;
+  }
+  // load: x lines along the line (contiguous), y / z lines across the tile (consecutive x)
+  for (int e = tid; e < nl * N; e += FFT_NT) {
+    const int l = a.axis == 0 ? e / N : e % nl;
+    const int i = a.axis == 0 ? e % N : e / nl;
+    long long g, r;
+    cplx<R> v = {R(0), R(0)};
+    if (element(a, l, i, g, r)) {
+      v = a.in[g];
+      if (a.pre) {
+        const cplx<R> p = a.phase[r];
+        v = v * cplx<R>{p.re, -p.im};
+      }
+    }
+    X[l * N + i] = v;
+  }
+  __syncthreads();
+  // Stockham stages: after the stages with radices r_0 .. r_{s-1} (product Ns), transforms of
+  // length Ns R are formed from R of length Ns
+  const R sg = a.inverse ? R(1) : R(-1);
+  int Ns = 1;
+  for (int s = 0; s < a.nf; ++s) {
+    const int Rd = a.fac[s], M = N / Rd, step = N / (Ns * Rd);
+    for (int e = tid; e < nl * M; e += FFT_NT) {
+      const int l = e / M, j = e - l * M, k = j % Ns;
+      const cplx<R>* x = X + l * N + j;
+      cplx<R>* y = Y + l * N + (j / Ns) * Ns * Rd + k;
+      if (Rd == 4) {
+        cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step], v3 = x[3 * M] * W[3 * k * step];
+        const cplx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = imul(sg, v1 - v3);
+        y[0] = t0 + t2;
+        y[Ns] = t1 + t3;
+        y[2 * Ns] = t0 - t2;
+        y[3 * Ns] = t1 - t3;
+      } else if (Rd == 2) {
+        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step];
+        y[0] = v0 + v1;
+        y[Ns] = v0 - v1;
+      } else if (Rd == 3) {
+        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step];
+        const cplx<R> b = v1 + v2;
+        const cplx<R> c = v0 - R(0.5) * b;
+        const cplx<R> d = imul(sg * a.s3, v1 - v2);
+        y[0] = v0 + b;
+        y[Ns] = c + d;
+        y[2 * Ns] = c - d;
+      } else {   // 5
+        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step],
+                      v3 = x[3 * M] * W[3 * k * step], v4 = x[4 * M] * W[4 * k * step];
+        const cplx<R> A = v1 + v4, B = v2 + v3, D = v1 - v4, E = v2 - v3;
+        const cplx<R> t1 = v0 + a.c51 * A + a.c52 * B, t2 = v0 + a.c52 * A + a.c51 * B;
+        const cplx<R> u1 = imul(sg, a.s51 * D + a.s52 * E), u2 = imul(sg, a.s52 * D - a.s51 * E);
+        y[0] = v0 + A + B;
+        y[Ns] = t1 + u1;
+        y[4 * Ns] = t1 - u1;
+        y[2 * Ns] = t2 + u2;
+        y[3 * Ns] = t2 - u2;
+      }
+    }
+    __syncthreads();
+    cplx<R>* t = X;
+    X = Y;
+    Y = t;
+    Ns *= Rd;
+  }
+  // store, with the epilogue
+  for (int e = tid; e < nl * N; e += FFT_NT) {
+    const int l = a.axis == 0 ? e / N : e % nl;
+    const int i = a.axis == 0 ? e % N : e / nl;
+    long long g, r;
+    if (!element(a, l, i, g, r)) continue;
+    const cplx<R> y = X[l * N + i];
+    if (a.post == 0) {
+      a.out[g] = y;
+    } else if (a.post == 1) {
+      const cplx<R> psi = y * a.phase[r];
+      a.out[g] = psi;
+      if (a.out2) a.out2[g] = a.v ? a.v[r] * psi : cplx<R>{R(0), R(0)};
+    } else {
+      const R kn = a.kin[r];
+      cplx<R> o = {R(0), R(0)};
+      if (a.ecut <= 0.0 || (double)kn <= a.ecut) {
+        o = y * a.scale;
+        if (a.Cin) {
+          const cplx<R> cg = a.Cin[g];
+          o += a.add_kin ? kn * cg : cg;
+        }
+      }
+      a.out[g] = o;
+    }
+  }
+}
+
+// radices of n from {4, 2, 3, 5} (fours first); false for other prime factors
+bool factorize(int n, int* fac, int* nf) {
+  *nf = 0;
+  while (n % 4 == 0 && *nf < MAX_FAC) {
+    fac[(*nf)++] = 4;
+    n /= 4;
+  }
+  for (int r : {2, 3, 5})
+    while (n % r == 0 && *nf < MAX_FAC) {
+      fac[(*nf)++] = r;
+      n /= r;
+    }
+  return n == 1;
+}
+
+template <class R>
+int setup_pw_impl(pawfd_ctx* c) {
+  PwPlan& p = c->pw;
+  int rc = PAWFD_OK;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (!factorize(c->n[ax], p.fac[ax], &p.nf[ax]))
+      return fail(c, PAWFD_EINVAL, "plane-wave mode: grid sizes must have no prime factor other than 2, 3 and 5");
+    const int N = c->n[ax];
+    std::vector<cplx<R>> tw(N);
+    for (int j = 0; j < N; ++j) {
+      const double t = 2.0 * M_PI * (double)j / (double)N;
+      tw[j] = cplx<R>{(R)std::cos(t), (R)-std::sin(t)};
+    }
+    rc = check_cuda(c, cudaMalloc(&p.tw[ax], sizeof(cplx<R>) * N), "cudaMalloc pw twiddles");
+    if (rc == PAWFD_OK)
+      rc = check_cuda(c, cudaMemcpy(p.tw[ax], tw.data(), sizeof(cplx<R>) * N, cudaMemcpyHostToDevice), "memcpy");
+    if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  }
+  const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2];
+  std::vector<cplx<R>> ph(c->K);
+  std::vector<R> kin(c->K);
+  std::vector<double> qx(n1), qy(n2), qz(n3);
+  auto freq = [](int i, int n) { return (double)(i < (n + 1) / 2 ? i : i - n); };
+  for (int i = 0; i < n1; ++i) qx[i] = c->k[0] + 2.0 * M_PI * freq(i, n1) / c->cell[0];
+  for (int i = 0; i < n2; ++i) qy[i] = c->k[1] + 2.0 * M_PI * freq(i, n2) / c->cell[1];
+  for (int i = 0; i < n3; ++i) qz[i] = c->k[2] + 2.0 * M_PI * freq(i, n3) / c->cell[2];
+  for (int i3 = 0; i3 < n3; ++i3)
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const size_t r = ((size_t)i3 * n2 + i2) * n1 + i1;
+        const double kr = c->k[0] * i1 * c->h[0] + c->k[1] * i2 * c->h[1] + c->k[2] * i3 * c->h[2];
+        ph[r] = cplx<R>{(R)std::cos(kr), (R)std::sin(kr)};
+        kin[r] = (R)(0.5 * (qx[i1] * qx[i1] + qy[i2] * qy[i2] + qz[i3] * qz[i3]));
+      }
+  rc = check_cuda(c, cudaMalloc(&p.phase, sizeof(cplx<R>) * c->K), "cudaMalloc pw phase");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&p.kin, sizeof(R) * c->K), "cudaMalloc pw kinetic");
+  if (rc == PAWFD_OK)
+    rc = check_cuda(c, cudaMemcpy(p.phase, ph.data(), sizeof(cplx<R>) * c->K, cudaMemcpyHostToDevice), "memcpy");
+  if (rc == PAWFD_OK)
+    rc = check_cuda(c, cudaMemcpy(p.kin, kin.data(), sizeof(R) * c->K, cudaMemcpyHostToDevice), "memcpy");
+  if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  p.ready = true;
+  return PAWFD_OK;
+}
+
+// Tables on first use: twiddles per axis, the Bloch phase and the kinetic energies.
+int ensure_pw(pawfd_ctx* c) {
+  if (c->pw.ready) return PAWFD_OK;
+  if (!is_complex(c)) return fail(c, PAWFD_EINVAL, "plane-wave mode needs a complex context (PAWFD_C128 or PAWFD_C64)");
+  int rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
+  if (rc != PAWFD_OK) return rc;
+  rc = is_fp32(c) ? setup_pw_impl<float>(c) : setup_pw_impl<double>(c);
+  if (rc != PAWFD_OK) free_pw(c);
+  return rc;
+}
+
+template <class R>
+int fft_pass(pawfd_ctx* c, int axis, const cplx<R>* in, cplx<R>* out, int nb, bool inverse, FftArgs<R> a) {
+  const PwPlan& p = c->pw;
+  a.N = c->n[axis];
+  a.nf = p.nf[axis];
+  for (int s = 0; s < p.nf[axis]; ++s) a.fac[s] = p.fac[axis][s];
+  a.tw = (const cplx<R>*)p.tw[axis];
+  a.inverse = inverse ? 1 : 0;
+  a.axis = axis;
+  a.n1 = c->n[0];
+  a.n2 = c->n[1];
+  a.n3 = c->n[2];
+  a.K = (long long)c->K;
+  a.in = in;
+  a.out = out;
+  a.s3 = (R)(0.5 * std::sqrt(3.0));
+  a.c51 = (R)std::cos(2.0 * M_PI / 5.0);
+  a.c52 = (R)std::cos(4.0 * M_PI / 5.0);
+  a.s51 = (R)std::sin(2.0 * M_PI / 5.0);
+  a.s52 = (R)std::sin(4.0 * M_PI / 5.0);
+  // lines per CTA: about 2048 (FP64) or 4096 (FP32) complex values per buffer
+  const int cap = sizeof(R) == 8 ? 2048 : 4096;
+  long long grid;
+  if (axis == 0) {
+    a.nl = std::max(1, std::min(64, cap / a.N));
+    a.nlines = (long long)nb * a.n2 * a.n3;
+    a.tiles = 1;
+    grid = (a.nlines + a.nl - 1) / a.nl;
+  } else {
+    a.nl = std::max(1, std::min(std::min(32, a.n1), cap / a.N));
+    a.tiles = (a.n1 + a.nl - 1) / a.nl;
+    a.nlines = 0;
+    grid = (long long)nb * (axis == 1 ? a.n3 : a.n2) * a.tiles;
+  }
+  const size_t smem = sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * a.N);
+  if (smem > 48 * 1024) {
+    const int rc = check_cuda(
+        c, cudaFuncSetAttribute(fft_pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        "fft smem attribute");
+    if (rc != PAWFD_OK) return rc;
+  }
+  if (grid > 2147483647ll) return fail(c, PAWFD_EINVAL, "plane-wave mode: too many lines for one launch");
+  fft_pass_kernel<R><<<(unsigned)grid, FFT_NT, smem, c->stream>>>(a);
+  c->launches += 1;
+  return check_cuda(c, cudaGetLastError(), "fft launch");
+}
+
+// psi(r) = e^{ik.r} sum_G C_G e^{iG.r}: the inverse transform (unnormalised), the phase in the
+// last pass; with loc != null also loc = v psi (v != null) or 0
+template <class R>
+int pw_inverse(pawfd_ctx* c, const cplx<R>* C, int nb, cplx<R>* psi, cplx<R>* loc, const R* v) {
+  FftArgs<R> a = {};
+  int rc = fft_pass<R>(c, 0, C, psi, nb, true, a);
+  if (rc == PAWFD_OK) rc = fft_pass<R>(c, 1, psi, psi, nb, true, a);
+  a.post = 1;
+  a.phase = (const cplx<R>*)c->pw.phase;
+  a.out2 = loc;
+  a.v = v;
+  if (rc == PAWFD_OK) rc = fft_pass<R>(c, 2, psi, psi, nb, true, a);
+  return rc;
+}
+
+// out_G = (1/K) sum_r e^{-i(k+G).r} f(r) (+ kin_G Cin_G or + Cin_G, masked by the cutoff)
+template <class R>
+int pw_forward(pawfd_ctx* c, cplx<R>* f, int nb, cplx<R>* out, const cplx<R>* Cin, bool add_kin, double ecut) {
+  FftArgs<R> a = {};
+  a.pre = 1;
+  a.phase = (const cplx<R>*)c->pw.phase;
+  int rc = fft_pass<R>(c, 0, f, f, nb, false, a);
+  a.pre = 0;
+  if (rc == PAWFD_OK) rc = fft_pass<R>(c, 1, f, f, nb, false, a);
+  a.post = 2;
+  a.kin = (const R*)c->pw.kin;
+  a.Cin = Cin;
+  a.add_kin = add_kin ? 1 : 0;
+  a.ecut = ecut;
+  a.scale = (R)(1.0 / (double)c->K);
+  if (rc == PAWFD_OK) rc = fft_pass<R>(c, 2, f, out, nb, false, a);
+  return rc;
+}
+
+template <class R>
+int pw_apply_impl(pawfd_ctx* c, int which, const cplx<R>* C, int nb, double ecut, cplx<R>* out, cplx<R>* work) {
+  cplx<R>* psi = work;
+  cplx<R>* loc = work + (size_t)nb * c->K;
+  int rc = pw_inverse<R>(c, C, nb, psi, loc, which == 0 ? (const R*)c->d_vloc : nullptr);
+  if (rc == PAWFD_OK && c->at.natoms > 0) {
+    rc = launch_project(c, psi, nb, c->d_P);
+    if (rc == PAWFD_OK) rc = launch_nonlocal_add(c, c->d_P, nb, which == 0 ? c->at.d_dH : c->at.d_dS, loc);
+  }
+  if (rc == PAWFD_OK) rc = pw_forward<R>(c, loc, nb, out, C, which == 0, ecut);
+  return rc;
+}
+
+int check_pw_call(pawfd_ctx* c, const void* a, const void* b, int nb) {
+  if (!c) return PAWFD_EINVAL;
+  if (!a || !b) return fail(c, PAWFD_EINVAL, "null array");
+  if (nb < 1 || nb > c->max_bands) return fail(c, PAWFD_EINVAL, "nb must be in 1..max_bands");
+  return ensure_pw(c);
+}
+
+}  // namespace
+
+void free_pw(pawfd_ctx* c) {
+  PwPlan& p = c->pw;
+  void* ptrs[] = {p.tw[0], p.tw[1], p.tw[2], p.phase, p.kin};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p = PwPlan();
+}
+
+}  // namespace pawfd
+
+using namespace pawfd;
+
+static int pw_apply(pawfd_ctx* c, int which, const void* C, int nb, double ecut, void* out, void* work) {
+  int rc = check_pw_call(c, C, out, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (!work) return fail(c, PAWFD_EINVAL, "null work array");
+  if (C == out || C == work || out == work) return fail(c, PAWFD_EINVAL, "C, out and work may not alias");
+  if (is_fp32(c)) return pw_apply_impl<float>(c, which, (const zf*)C, nb, ecut, (zf*)out, (zf*)work);
+  return pw_apply_impl<double>(c, which, (const zd*)C, nb, ecut, (zd*)out, (zd*)work);
+}
+
+extern "C" int pawfd_pw_apply_H(pawfd_ctx* c, const void* C, int nb, double ecut, void* HC, void* work) {
+  return pw_apply(c, 0, C, nb, ecut, HC, work);
+}
+
+extern "C" int pawfd_pw_apply_S(pawfd_ctx* c, const void* C, int nb, double ecut, void* SC, void* work) {
+  return pw_apply(c, 1, C, nb, ecut, SC, work);
+}
+
+extern "C" int pawfd_pw_to_grid(pawfd_ctx* c, const void* C, int nb, void* psi) {
+  int rc = check_pw_call(c, C, psi, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (C == psi) return fail(c, PAWFD_EINVAL, "C and psi may not alias");
+  if (is_fp32(c)) return pw_inverse<float>(c, (const zf*)C, nb, (zf*)psi, nullptr, nullptr);
+  return pw_inverse<double>(c, (const zd*)C, nb, (zd*)psi, nullptr, nullptr);
+}
+
+extern "C" int pawfd_pw_from_grid(pawfd_ctx* c, const void* psi, int nb, void* C, void* work) {
+  int rc = check_pw_call(c, psi, C, nb);
+  if (rc != PAWFD_OK) return rc;
+  if (!work) return fail(c, PAWFD_EINVAL, "null work array");
+  if (psi == C || psi == work || C == work) return fail(c, PAWFD_EINVAL, "psi, C and work may not alias");
+  const size_t bytes = (is_fp32(c) ? sizeof(zf) : sizeof(zd)) * (size_t)nb * c->K;
+  rc = check_cuda(c, cudaMemcpyAsync(work, psi, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  if (rc != PAWFD_OK) return rc;
+  if (is_fp32(c)) return pw_forward<float>(c, (zf*)work, nb, (zf*)C, nullptr, false, 0.0);
+  return pw_forward<double>(c, (zd*)work, nb, (zd*)C, nullptr, false, 0.0);
+}

@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(NTHR) kinetic_local_fx_kernel(const double* __
 
 // Real FP64 contexts on grids the tile fits (one wrap per index); EINVAL otherwise.
 int launch_kinetic_local_fx(pawfd_ctx* c, const double* psi, int nb, double* out, double* cpy) {
-  if (c->dtype != PAWFD_R64 || !c->d_vloc64) return PAWFD_EINVAL;
+  if (c->dtype != PAWFD_R64 || !c->d_vloc) return PAWFD_EINVAL;
   if (c->n[0] < TX + 2 * HALO + 2 || c->n[1] < TY + 2 * HALO || c->n[2] < HALO) return PAWFD_EINVAL;
   FXArgs a;
   a.n1 = c->n[0];
@@ -264,7 +264,7 @@ int launch_kinetic_local_fx(pawfd_ctx* c, const double* psi, int nb, double* out
     a.ih2[cc] = 1.0 / (c->h[cc] * c->h[cc]);
     a.cs[cc] = -1.0 / (360.0 * c->h[cc] * c->h[cc]);
   }
-  a.v = (const double*)c->d_vloc64;
+  a.v = (const double*)c->d_vloc;
   const bool cubic = c->h[0] == c->h[1] && c->h[1] == c->h[2];
   const int gx = (a.n1 + TX - 1) / TX, gy = (a.n2 + TY - 1) / TY;
   const long long tiles = (long long)gx * gy;
