@@ -103,7 +103,7 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="pawfd", choices=["pawfd", "reference"])
-    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS) + ["batch64", "served", "davidson", "density", "poisson"])
+    p.add_argument("--workload", default="gamma-96c-256b", choices=sorted(synth.WORKLOADS) + ["batch64", "served", "davidson", "density", "poisson", "pw"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -969,6 +969,83 @@ def run_poisson(args):
 
 
 # ------------------------------------------------------------------------------------------
+# H and S in the plane-wave representation
+# ------------------------------------------------------------------------------------------
+def run_pw(args):
+    """pawfd_pw_apply_H + pawfd_pw_apply_S on the 96^3 grid (0.2 Angstrom spacing, 32 atoms x
+    18 projectors) with 256 bands of complex coefficients at a Bloch vector, all G of the FFT
+    grid (complex128, or complex64 with --precision mixed)."""
+    import torch
+
+    from paper_2310_14776_gb300 import api
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.WORKLOADS["gamma-96c-256b"]
+    base = w.system()
+    L = base.cell
+    kvec = (2 * np.pi * 0.25 / L[0], 2 * np.pi * 0.125 / L[1], 2 * np.pi * 0.375 / L[2])
+    system = synth.build_system(base.n, base.cell, base.pos, base.wells, base.pset,
+                                [base.dH[int(base.dmat_off[a]):int(base.dmat_off[a + 1])].reshape(18, 18)
+                                 for a in range(base.natoms)],
+                                [base.dS[int(base.dmat_off[a]):int(base.dmat_off[a + 1])].reshape(18, 18)
+                                 for a in range(base.natoms)], k=kvec, complex_wf=True)
+    nb, K = (args.bands or w.nbands), system.npoints
+    ctx = api.Context(system, max_bands=nb, device=dev, precision=args.precision)
+    C = device_bands(ctx, nb, w.seed)
+    HC, SC = ctx.empty_bands(nb), ctx.empty_bands(nb)
+    work = ctx.empty_bands(2 * nb)
+    for _ in range(args.warmup):
+        ctx.pw_apply(C, "H", out=HC, work=work)
+        ctx.pw_apply(C, "S", out=SC, work=work)
+    ctx.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    l0 = ctx.launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps + 1)]
+    evs[0].record()
+    for i in range(args.steps):
+        ctx.pw_apply(C, "H", out=HC, work=work)
+        evs[2 * i + 1].record()
+        ctx.pw_apply(C, "S", out=SC, work=work)
+        evs[2 * i + 2].record()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ctx.sync()
+    launches = ctx.launch_count() - l0
+    elapsed = evs[0].elapsed_time(evs[-1]) * 1e-3
+    h_ms = [evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(args.steps)]
+    s_ms = [evs[2 * i + 1].elapsed_time(evs[2 * i + 2]) for i in range(args.steps)]
+    esize = C.element_size()
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # six FFT passes per apply (three each way), each reading and writing every value once
+    fft_bytes = 6 * 2 * esize * nb * K
+    ach = fft_bytes / (np.mean(h_ms) * 1e-3) / 1e9
+    result = {
+        "metric": METRIC, "value_definition": "grid points x bands of plane-wave H C and S C per second / 1e9 "
+                                              "(one H application and one S application per step)",
+        "value": K * nb * args.steps / elapsed / 1e9, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if esize == 8 else "c128",
+        "data": "synthetic (coefficients from a seeded torch generator on the device)",
+        "config": {"workload": "pw: plane-wave H and S, 96^3 grid, 256 bands, Bloch k, all G",
+                   "grid": list(system.n), "bands": nb, "precision": args.precision, "parallelism": "single-gpu",
+                   "l2": "inputs larger than L2 (%.2f GB of coefficients)" % (nb * K * esize / 1e9)},
+        "apply_H_ms": float(np.mean(h_ms)), "apply_S_ms": float(np.mean(s_ms)),
+        "roofline": {"stage": "pawfd_pw_apply_H", "kernel": "fft_pass_kernel (6 passes) + project + back-add",
+                     "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                     "traffic": None, "bytes_per_apply": fft_bytes,
+                     "note": "bytes of the six FFT passes (each reads and writes every value once) over the whole "
+                             "H application time; FP64 butterflies run on the FP64 pipe"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(result), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
 # CPU oracle baseline / reference arm
 # ------------------------------------------------------------------------------------------
 def oracle_step_time(system, psi, stages=None):
@@ -1077,10 +1154,10 @@ def main():
         run_reference(args)
     elif args.workload == "batch64":
         run_batch(args)
-    elif args.workload in ("served", "davidson", "density", "poisson"):
+    elif args.workload in ("served", "davidson", "density", "poisson", "pw"):
         if single_gpu_arm(args.workload):
             {"served": run_served, "davidson": run_davidson, "density": run_density,
-             "poisson": run_poisson}[args.workload](args)
+             "poisson": run_poisson, "pw": run_pw}[args.workload](args)
     else:
         run_gpu(args)
 
