@@ -313,6 +313,10 @@ def dense_operators(system):
 
 
 TINY = {
+    # the 8^3 grid of the dense brute-force check (512 x 512 pencils), s + p + d projectors
+    "cube8": dict(n=(8, 8, 8), cell=(4.2, 4.2, 4.2), natoms=2, pset=synth.PSET_SPD2, seed=74, complex_wf=False),
+    "cube8-bloch": dict(n=(8, 8, 8), cell=(4.2, 4.2, 4.2), natoms=2, pset=synth.PSET_SPD2, seed=75,
+                        complex_wf=True, k=(0.33, -0.41, 0.27)),
     # boxes smaller than the cell, Bloch phases, s + p + d projectors
     "bloch": dict(n=(8, 7, 6), cell=(6.0, 5.6, 5.1), natoms=2, pset=synth.PSET_SPD2, seed=71, complex_wf=True,
                   k=(0.41, -0.29, 0.13)),
@@ -338,7 +342,7 @@ def test_dense_bruteforce_apply(case):
     assert np.allclose(Spsi.reshape(4, K), ref_S, rtol=0, atol=1e-12 * np.max(np.abs(ref_S)))
 
 
-@pytest.mark.parametrize("case", ["selfwrap", "selfwrap-bloch"])
+@pytest.mark.parametrize("case", ["selfwrap", "selfwrap-bloch", "cube8", "cube8-bloch"])
 def test_dense_bruteforce_full_spectrum(case):
     # RR over the full grid basis (every band a unit vector) is the full generalized eigenproblem
     s = small_system(**TINY[case])
