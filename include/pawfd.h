@@ -327,6 +327,20 @@ int pawfd_pw_apply_S(pawfd_ctx* ctx, const void* C, int nb, double ecut, void* S
 int pawfd_pw_to_grid(pawfd_ctx* ctx, const void* C, int nb, void* psi);
 int pawfd_pw_from_grid(pawfd_ctx* ctx, const void* psi, int nb, void* C, void* work);
 
+/* The Hartree potential by the direct Fourier-transform route (the Kohn-Sham section names
+ * direct solvers based on Fourier transforms as the default): the zero-mean v with
+ * lap_FD v = -4 pi (rho - <rho>) for the order-6 Laplacian of the kinetic stencil, computed
+ * as v(G) = -4 pi rho(G) / L(G) (G != 0; v(0) = 0) with L(G) the Laplacian's symbol
+ * sum_c (w0 + 2 sum_m w_m cos(m G_c h_c)) / h_c^2 on the grid's FFT frequencies, on the
+ * library's own FFT kernels (pawfd_pw_apply_H's); the same equation as pawfd_poisson solves
+ * iteratively.
+ *   ctx: a PAWFD_R64 context with v = 0 and no atoms, grid sizes with no prime factor other than
+ *   2, 3 and 5 (the FFT tables and the K-point table of -4 pi / (K L(G)) are allocated by the
+ *   first call; make it before any stream capture); rho, v: device [K] doubles; work: device
+ *   scratch of K complex doubles (16 K bytes).  Returns PAWFD_EINVAL for another context, null
+ *   or aliased arrays, another grid factor; PAWFD_ENOMEM if the tables cannot be allocated. */
+int pawfd_poisson_fft(pawfd_ctx* ctx, const double* rho, double* v, void* work);
+
 /* Final refinement of the mixed form (the paper is silent on it; this is the reading that
  * closes a mixed-precision eigensolver step).  ctx is an FP64 context (PAWFD_R64 or
  * PAWFD_C128) of the same system as the mixed context whose bands psi_lo (PAWFD_R32 or

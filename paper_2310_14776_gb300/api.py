@@ -279,6 +279,24 @@ class Context:
                    float(tol), int(maxiter), ctypes.c_void_p(work.data_ptr()), ctypes.byref(it), ctypes.byref(res))
         return v, it.value, res.value
 
+    def poisson_fft(self, rho, v=None, work=None):
+        """The zero-mean Hartree potential of rho by the direct Fourier route
+        (pawfd_poisson_fft); this context must be the free operator of its grid (see
+        ``poisson_context``).  Returns v."""
+        if rho.numel() != self.K or rho.dtype != torch.float64 or rho.device != self.device:
+            raise ValueError("rho must hold K float64 values on the device")
+        rho = rho.contiguous()          # held until the call returns
+        v = torch.empty(self.K, dtype=torch.float64, device=self.device) if v is None else v
+        if v.numel() != self.K or v.dtype != torch.float64 or v.device != self.device or not v.is_contiguous():
+            raise ValueError("v must be a contiguous float64 tensor of K values on the device")
+        work = torch.empty(self.K, dtype=torch.complex128, device=self.device) if work is None else work
+        if (work.numel() < self.K or work.dtype != torch.complex128 or work.device != self.device
+                or not work.is_contiguous()):
+            raise ValueError("work must be a contiguous complex128 tensor of at least K values on the device")
+        self._call(self.lib.pawfd_poisson_fft, ctypes.c_void_p(rho.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                   ctypes.c_void_p(work.data_ptr()))
+        return v
+
     def density(self, psi, f, rho=None):
         """rho(r) = sum_n f_n |psi_n(r)|^2 (pawfd_density); f: device float64 [nb]."""
         nb = self._bands(psi, "psi")

@@ -199,6 +199,7 @@ struct PwPlan {
   void* tw[3] = {nullptr, nullptr, nullptr};   // e^{-2 pi i j / N_c}, complex of the band precision
   void* phase = nullptr;          // e^{i k.r} at the grid points [K]
   void* kin = nullptr;            // |k+G|^2 / 2 [K], real of the band precision
+  void* pois = nullptr;           // real FP64 contexts: -4 pi / (K L(G)) of the Poisson solve [K]
 };
 }  // namespace pawfd
 

@@ -48,13 +48,17 @@ struct FftArgs {
   long long nlines;            // axis 0: nb n2 n3 lines
   const cplx<R>* in;
   cplx<R>* out;
-  // prologue: 1 = multiply every input value by conj(phase[r])
+  // prologue: 1 = multiply every input value by conj(phase[r]); 2 = the input is the real
+  // array rin (imaginary part 0)
   int pre;
   const cplx<R>* phase;
+  const R* rin;
   // epilogue: 0 = store; 1 = store y phase[r] (psi), and v[r] psi into out2 (0 if v is null);
   // 2 = store y scale, plus kin[r] Cin (add_kin) or Cin (otherwise) when Cin is set, where
-  // kin[r] <= ecut (or ecut <= 0), else 0
+  // kin[r] <= ecut (or ecut <= 0), else 0; 3 = store y tab[r]; 4 = store Re(y) into rout
   int post;
+  const R* tab;
+  R* rout;
   cplx<R>* out2;
   const R* v;
   const R* kin;
@@ -119,10 +123,14 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     long long g, r;
     cplx<R> v = {R(0), R(0)};
     if (element(a, l, i, g, r)) {
-      v = a.in[g];
-      if (a.pre) {
-        const cplx<R> p = a.phase[r];
-        v = v * cplx<R>{p.re, -p.im};
+      if (a.pre == 2) {
+        v = cplx<R>{a.rin[g], R(0)};
+      } else {
+        v = a.in[g];
+        if (a.pre == 1) {
+          const cplx<R> p = a.phase[r];
+          v = v * cplx<R>{p.re, -p.im};
+        }
       }
     }
     X[l * N + i] = v;
@@ -185,6 +193,10 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     const cplx<R> y = X[l * N + i];
     if (a.post == 0) {
       a.out[g] = y;
+    } else if (a.post == 3) {
+      a.out[g] = y * a.tab[r];
+    } else if (a.post == 4) {
+      a.rout[g] = y.re;
     } else if (a.post == 1) {
       const cplx<R> psi = y * a.phase[r];
       a.out[g] = psi;
@@ -253,6 +265,36 @@ int setup_pw_impl(pawfd_ctx* c) {
         ph[r] = cplx<R>{(R)std::cos(kr), (R)std::sin(kr)};
         kin[r] = (R)(0.5 * (qx[i1] * qx[i1] + qy[i2] * qy[i2] + qz[i3] * qz[i3]));
       }
+  // the Poisson solve's multiplier -4 pi / (K L(G)) (0 at G = 0), L(G) the symbol of the order-6
+  // FD Laplacian, sum_c (w0 + 2 sum_m w_m cos(m G_c h_c)) / h_c^2 (real FP64 contexts)
+  std::vector<double> pois;
+  if (c->dtype == PAWFD_R64) {
+    const double w[4] = {FD6_W0, FD6_W1, FD6_W2, FD6_W3};
+    std::vector<double> lx(n1), ly(n2), lz(n3);
+    auto sym = [&](std::vector<double>& out, int n, double L, double h) {
+      for (int i = 0; i < n; ++i) {
+        const double g = 2.0 * M_PI * freq(i, n) / L;
+        double acc = w[0];
+        for (int m = 1; m <= 3; ++m) acc += 2.0 * w[m] * std::cos(m * g * h);
+        out[i] = acc / (h * h);
+      }
+    };
+    sym(lx, n1, c->cell[0], c->h[0]);
+    sym(ly, n2, c->cell[1], c->h[1]);
+    sym(lz, n3, c->cell[2], c->h[2]);
+    pois.resize(c->K);
+    for (int i3 = 0; i3 < n3; ++i3)
+      for (int i2 = 0; i2 < n2; ++i2)
+        for (int i1 = 0; i1 < n1; ++i1) {
+          const size_t r = ((size_t)i3 * n2 + i2) * n1 + i1;
+          const double L = lx[i1] + ly[i2] + lz[i3];
+          pois[r] = (r == 0) ? 0.0 : -4.0 * M_PI / ((double)c->K * L);
+        }
+    rc = check_cuda(c, cudaMalloc(&p.pois, sizeof(double) * c->K), "cudaMalloc poisson table");
+    if (rc == PAWFD_OK)
+      rc = check_cuda(c, cudaMemcpy(p.pois, pois.data(), sizeof(double) * c->K, cudaMemcpyHostToDevice), "memcpy");
+    if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  }
   rc = check_cuda(c, cudaMalloc(&p.phase, sizeof(cplx<R>) * c->K), "cudaMalloc pw phase");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&p.kin, sizeof(R) * c->K), "cudaMalloc pw kinetic");
   if (rc == PAWFD_OK)
@@ -265,9 +307,10 @@ int setup_pw_impl(pawfd_ctx* c) {
 }
 
 // Tables on first use: twiddles per axis, the Bloch phase and the kinetic energies.
-int ensure_pw(pawfd_ctx* c) {
+int ensure_pw(pawfd_ctx* c, bool need_complex = true) {
+  if (need_complex && !is_complex(c))
+    return fail(c, PAWFD_EINVAL, "plane-wave mode needs a complex context (PAWFD_C128 or PAWFD_C64)");
   if (c->pw.ready) return PAWFD_OK;
-  if (!is_complex(c)) return fail(c, PAWFD_EINVAL, "plane-wave mode needs a complex context (PAWFD_C128 or PAWFD_C64)");
   int rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
   if (rc != PAWFD_OK) return rc;
   rc = is_fp32(c) ? setup_pw_impl<float>(c) : setup_pw_impl<double>(c);
@@ -369,6 +412,30 @@ int pw_apply_impl(pawfd_ctx* c, int which, const cplx<R>* C, int nb, double ecut
   return rc;
 }
 
+// v = the zero-mean solution of lap_FD v = -4 pi rho on the periodic grid: rho's transform
+// times -4 pi / (K L(G)) (0 at G = 0), transformed back; the imaginary part of the result is
+// rounding only and is dropped.
+int poisson_fft_impl(pawfd_ctx* c, const double* rho, double* v, zd* work) {
+  FftArgs<double> a = {};
+  a.pre = 2;
+  a.rin = rho;
+  int rc = fft_pass<double>(c, 0, nullptr, work, 1, false, a);
+  a.pre = 0;
+  a.rin = nullptr;
+  if (rc == PAWFD_OK) rc = fft_pass<double>(c, 1, work, work, 1, false, a);
+  a.post = 3;
+  a.tab = (const double*)c->pw.pois;
+  if (rc == PAWFD_OK) rc = fft_pass<double>(c, 2, work, work, 1, false, a);
+  a.post = 0;
+  a.tab = nullptr;
+  if (rc == PAWFD_OK) rc = fft_pass<double>(c, 0, work, work, 1, true, a);
+  if (rc == PAWFD_OK) rc = fft_pass<double>(c, 1, work, work, 1, true, a);
+  a.post = 4;
+  a.rout = v;
+  if (rc == PAWFD_OK) rc = fft_pass<double>(c, 2, work, work, 1, true, a);
+  return rc;
+}
+
 int check_pw_call(pawfd_ctx* c, const void* a, const void* b, int nb) {
   if (!c) return PAWFD_EINVAL;
   if (!a || !b) return fail(c, PAWFD_EINVAL, "null array");
@@ -380,7 +447,7 @@ int check_pw_call(pawfd_ctx* c, const void* a, const void* b, int nb) {
 
 void free_pw(pawfd_ctx* c) {
   PwPlan& p = c->pw;
-  void* ptrs[] = {p.tw[0], p.tw[1], p.tw[2], p.phase, p.kin};
+  void* ptrs[] = {p.tw[0], p.tw[1], p.tw[2], p.phase, p.kin, p.pois};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   p = PwPlan();
@@ -405,6 +472,17 @@ extern "C" int pawfd_pw_apply_H(pawfd_ctx* c, const void* C, int nb, double ecut
 
 extern "C" int pawfd_pw_apply_S(pawfd_ctx* c, const void* C, int nb, double ecut, void* SC, void* work) {
   return pw_apply(c, 1, C, nb, ecut, SC, work);
+}
+
+extern "C" int pawfd_poisson_fft(pawfd_ctx* c, const double* rho, double* v, void* work) {
+  if (!c) return PAWFD_EINVAL;
+  if (c->dtype != PAWFD_R64) return fail(c, PAWFD_EINVAL, "pawfd_poisson_fft needs a real FP64 context");
+  if (!c->free_operator) return fail(c, PAWFD_EINVAL, "pawfd_poisson_fft needs a context with v = 0 and no atoms");
+  if (!rho || !v || !work) return fail(c, PAWFD_EINVAL, "null array");
+  if ((const void*)rho == work || (void*)v == work) return fail(c, PAWFD_EINVAL, "work may not alias rho or v");
+  const int rc = ensure_pw(c, false);
+  if (rc != PAWFD_OK) return rc;
+  return poisson_fft_impl(c, rho, v, (zd*)work);
 }
 
 extern "C" int pawfd_pw_to_grid(pawfd_ctx* c, const void* C, int nb, void* psi) {

@@ -64,3 +64,59 @@ def test_poisson_matches_oracle(dev, n):
     assert res <= 1e-12 and 0 < iters < 4000
     assert np.max(np.abs(v.cpu().numpy() - ref)) <= 1e-9 * np.max(np.abs(ref))
     ctx.close()
+
+
+@pytest.mark.parametrize("n", [(30, 24, 20), (48, 40, 36), (60, 45, 32), (96, 96, 96)])
+def test_poisson_fft_matches_oracle(dev, n):
+    """pawfd_poisson_fft (the direct Fourier route on the library's FFT kernels: radices 4, 2, 3
+    and 5, ragged line tiles) against the oracle's numpy solve of the same FD equation, and
+    against the CG route (pawfd_poisson) on the same density."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system(n, (7.0, 6.5, 6.0), 3, synth.PSET_SP, seed=653)
+    f = synth.free_grid(s)
+    rho_np = np.abs(synth.make_psi(s, 1, 654)).reshape(-1) ** 2
+    ctx = api.poisson_context(s, device=dev)
+    rho = torch.from_numpy(rho_np).to(dev)
+    v = ctx.poisson_fft(rho).cpu().numpy()
+    ref = O.poisson(f, rho_np).reshape(-1)
+    assert np.max(np.abs(v - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert abs(v.mean()) <= 1e-13 * np.max(np.abs(ref))
+    if n[0] <= 48:
+        vcg, _, _ = ctx.poisson(rho, tol=1e-12, maxiter=4000)
+        assert np.max(np.abs(vcg.cpu().numpy() - v)) <= 1e-9 * np.max(np.abs(ref))
+    ctx.close()
+
+
+def test_poisson_fft_closed_form(dev):
+    """A single cosine density: v = -4 pi rho / L(G) at its one wavevector, the Laplacian's
+    symbol written out from the order-6 weights."""
+    from paper_2310_14776_gb300 import api
+    n, cell = (24, 20, 18), (9.0, 7.5, 6.75)
+    s = synth.make_system(n, cell, 1, synth.PSET_SP, seed=655)
+    j = (3, -2, 1)
+    x = [np.arange(n[c]) * cell[c] / n[c] for c in range(3)]
+    Z, Y, X = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    g = [2 * np.pi * j[c] / cell[c] for c in range(3)]
+    rho = np.cos(g[0] * X + g[1] * Y + g[2] * Z)
+    w = (-49 / 18, 3 / 2, -3 / 20, 1 / 90)
+    L = sum((w[0] + 2 * sum(w[m] * np.cos(m * g[c] * cell[c] / n[c]) for m in (1, 2, 3))) / (cell[c] / n[c]) ** 2
+            for c in range(3))
+    ctx = api.poisson_context(s, device=dev)
+    v = ctx.poisson_fft(torch.from_numpy(rho.reshape(-1)).to(dev)).cpu().numpy()
+    ctx.close()
+    assert np.max(np.abs(v - (-4 * np.pi / L) * rho.reshape(-1))) <= 1e-12 * abs(4 * np.pi / L)
+
+
+def test_poisson_fft_rejects_other_contexts(dev):
+    from paper_2310_14776_gb300 import api, _lib
+    s = synth.make_system((12, 10, 8), (5.0, 4.0, 3.5), 1, synth.PSET_SP, seed=656)
+    ctx = api.Context(s, max_bands=1, device=dev)   # has atoms and a potential
+    rho = torch.zeros(s.npoints, dtype=torch.float64, device=dev)
+    with pytest.raises(_lib.PawFDError):
+        ctx.poisson_fft(rho)
+    ctx.close()
+    s7 = synth.make_system((14, 10, 8), (5.0, 4.0, 3.5), 1, synth.PSET_SP, seed=657)
+    ctx = api.poisson_context(s7, device=dev)
+    with pytest.raises(_lib.PawFDError):
+        ctx.poisson_fft(torch.zeros(s7.npoints, dtype=torch.float64, device=dev))
+    ctx.close()
