@@ -155,6 +155,10 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
+ *   "tridiag_dsm"     1 (default): the FP32 tridiagonal reduction of the subspace solve's far
+ *                     path keeps the matrix in the distributed shared memory of one 16-CTA
+ *                     cluster when it fits (n <= 512 complex, n <= 724 real); 0: in global
+ *                     memory (L2), the form used for larger n.
  *   "test_barrier_missing"  0 (default); 1 (for tests of the error path only): the grid
  *                     barriers of the subspace solve wait for one CTA more than the launch has
  *                     and give up after 20 ms, so every such wait runs out: the kernels record

@@ -284,7 +284,7 @@ void free_ctx(pawfd_ctx* c) {
   void* ptrs[] = {c->d_vshift, c->at.d_nproj, c->at.d_row_off, c->at.d_npts, c->at.d_pt_off, c->at.d_pts,
                   c->at.d_g_off, c->at.d_g, c->at.d_dmat_off, c->at.d_dH, c->at.d_dS, c->at.d_color_atoms,
                   c->d_P, c->d_gram_part, c->d_work, c->d_evals, c->d_dscale, c->d_barrier, c->d_status, c->d_reduce,
-                  c->d_flags, c->d_oa, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
+                  c->d_flags, c->d_oa, c->d_eig, c->d_Q, c->d_Ppart, c->at.d_items, c->at.d_item_row,
                   c->at.d_atom_items, c->at.d_color_items, c->at.d_g_df, c->d_vloc};
   free_pw(c);
   for (void* p : ptrs)
@@ -384,6 +384,7 @@ extern "C" int pawfd_create(pawfd_ctx** out, const pawfd_system_desc* d, void* s
     c->d_reduce = dev_alloc<double>(c, 8192, &rc);   // [0, 2048): partial sums; then Jacobi round flags
     c->d_flags = dev_alloc<int>(c, 16, &rc);
     c->d_oa = dev_alloc<double>(c, oa_scratch_doubles(nb), &rc);
+    c->d_eig = dev_alloc<char>(c, eig32_scratch_bytes((int)nb, is_complex(c)), &rc);
   }
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMallocHost(&c->h_status, sizeof(DeviceStatus)), "cudaMallocHost");
   if (rc == PAWFD_OK && c->use_tc) rc = setup_tc(c);
@@ -440,6 +441,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
   }
   if (n == "jacobi_cluster" && (value == 0 || value == 1)) {
     c->jacobi_cluster = value == 1;
+    return PAWFD_OK;
+  }
+  if (n == "tridiag_dsm" && (value == 0 || value == 1)) {
+    c->tridiag_dsm = value == 1;
     return PAWFD_OK;
   }
   if (n == "test_barrier_missing" && (value == 0 || value == 1)) {

@@ -222,6 +222,7 @@ struct pawfd_ctx {
   void* d_work = nullptr;                     // subspace workspace (7 matrices of max_bands^2)
   int* d_flags = nullptr;                     // [16] subspace-solve path decisions (device-side gates)
   double* d_oa = nullptr;                     // Ogita-Aishima partial sums and eigenvalue estimates
+  void* d_eig = nullptr;                      // FP32 eigendecomposition scratch (eig32_scratch_bytes)
   double* d_evals = nullptr;                  // [max_bands] unsorted eigenvalues
   double* d_dscale = nullptr;                 // [max_bands] column scaling of a Davidson subspace
   unsigned* d_barrier = nullptr;              // grid-barrier counters
@@ -238,6 +239,7 @@ struct pawfd_ctx {
   int stencil_zsplit = 0;                     // general stencil: target CTAs per SM of a launch (0: 4)
   int stencil_ring = 0;                       // ring stencil: planes in the ring (0: 8; 8, 10 or 12)
   bool jacobi_cluster = false;                // Cholesky / Jacobi on one thread-block cluster where they fit
+  bool tridiag_dsm = true;                    // FP32 tridiagonal reduction in the cluster's shared memory where it fits
   int tc_kblk_chunks = 0;                     // tensor-core Gram: K block in 512-value chunks (0: allocation)
   int tc_scratch_mb = 0;                      // digit-plane scratch per operand set in MB (0: default sizes)
   bool stencil_fx = true;                     // real FP64 stencil in exact fixed-point arithmetic
@@ -300,6 +302,10 @@ void ktimer_end(pawfd_ctx* c);
 int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
                             double* rnorm);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
+// FP32 eigendecomposition of a Hermitian n x n FP64 matrix A (full storage): Z (FP64 storage)
+// the eigenvectors, ascending eigenvalues; nothing happens when *gate != 0 (tridiag.cu)
+int launch_eig32(pawfd_ctx* c, int n, const double* A, double* Z, const int* gate);
+int launch_eig32(pawfd_ctx* c, int n, const zd* A, zd* Z, const int* gate);
 int launch_overlap_correction(pawfd_ctx* c, const void* P, int nb, void* M);
 bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc);
 // H psi and S psi with one set of projections P of psi (written to P)
@@ -309,6 +315,13 @@ int launch_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, cons
 // CTAs of the Ogita-Aishima element kernels and the doubles of their scratch for nb bands
 constexpr int OA_G = 64;
 inline size_t oa_scratch_doubles(int nb) { return 5 * (size_t)OA_G + (size_t)nb; }
+// the working matrix (FP32 of the band kind), the eigenvectors of T (float) and five vectors,
+// each rounded up to 256 bytes
+inline size_t eig32_scratch_bytes(int nb, bool complex) {
+  const size_t f = complex ? 8 : 4, n = (size_t)nb;
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  return r(n * n * f) + r(n * n * 4) + 2 * r(n * f) + 3 * r(n * 4);
+}
 
 // order-6 central second-difference weights: f'' ~ (1/h^2) sum_m w_|m| f(x + m h)
 constexpr double FD6_W0 = -49.0 / 18.0;

@@ -7,92 +7,23 @@
 //   2. Cholesky S = L L^H (one CTA, right-looking, pivot <= 0 -> PAWFD_ENOTPD + column);
 //   3. L^-1 by column-wise forward substitution (one CTA per column);
 //   4. A = L^-1 H L^-H with two small GEMMs;
-//   5. parallel cyclic Jacobi on A (round-robin pair ordering: in each round n/2 disjoint
-//      rotations are applied at once, so every 2x2 block of A and every row pair of V is
-//      updated independently; one grid-wide barrier per round, bounded in time);
+//   5. an FP32 eigendecomposition A ~= Z diag Z^H (tridiag.cu) refined in FP64 by two
+//      Ogita-Aishima steps from X = Z; pairs of close eigenvalues the steps leave coupled go
+//      to a parallel cyclic Jacobi on X^H A X (round-robin pair ordering: in each round n/2
+//      disjoint rotations are applied at once, so every 2x2 block of A and every row pair of
+//      V is updated independently; one grid-wide barrier per round, bounded in time; rounds
+//      with no pair above the threshold are skipped);
 //   6. stable ascending sort, C = L^-H U, phase fixing of each column.
+// Bands that are already near the Ritz vectors (S_nm ~ I) skip steps 2-5: the Ogita-Aishima
+// steps run on (H_nm, S_nm) from X = I.
 #include <algorithm>
 #include <cmath>
 
+#include "device_sync.cuh"
 #include "pawfd_internal.cuh"
 
 namespace pawfd {
 namespace {
-
-constexpr long long BARRIER_TIMEOUT_NS = 2000000000ll;   // a grid barrier gives up after 2 s
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(const volatile unsigned*)p; }
-__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
-
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  bar[0] counts
-// arrivals, bar[1] is the generation.  The wait is bounded: after BARRIER_TIMEOUT_NS the
-// CTA records PAWFD_ETIMEDOUT and every CTA stops at its next barrier.  Returns false if
-// the kernel must stop.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, DeviceStatus* st, int id) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned gen = ld_volatile(&bar[1]);
-    const unsigned need = nblocks + ld_volatile(&st->barrier_extra);
-    const unsigned lim_ms = ld_volatile(&st->barrier_limit_ms);
-    const unsigned long long limit = lim_ms ? 1000000ull * lim_ms : (unsigned long long)BARRIER_TIMEOUT_NS;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&bar[0], 1u);
-    if (arrived == need - 1) {
-      atomicExch(&bar[0], 0u);
-      __threadfence();
-      atomicAdd(&bar[1], 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      while (ld_volatile(&bar[1]) == gen) {
-        if (global_ns() - t0 > limit) {
-          set_status(st, PAWFD_ETIMEDOUT, id);
-          ok = 0;
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    if (ld_volatile(&st->code) != 0) ok = 0;
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// Cluster-wide barrier (hardware).  Every CTA of the cluster reaches every call: the callers'
-// control flow depends only on values that all CTAs compute identically.  The fence makes
-// this CTA's global-memory writes visible before the arrive; readers use L2-only loads.
-__device__ __forceinline__ void cluster_barrier() {
-  __threadfence();
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// MODE 0: cooperative grid launch, software grid barrier (bounded); MODE 1: one thread-block
-// cluster, hardware cluster barrier.  Returns false if the kernel must stop.
-template <int MODE>
-__device__ __forceinline__ bool all_barrier(unsigned* bar, unsigned nblocks, DeviceStatus* st, int id) {
-  if (MODE == 1) {
-    cluster_barrier();
-    return true;
-  }
-  return grid_barrier(bar, nblocks, st, id);
-}
-
-// L2-only loads: data written by other CTAs of the same launch must not come from a stale L1
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ zd ldcg(const zd* p) {
-  const double2 v = __ldcg((const double2*)p);
-  return zd{v.x, v.y};
-}
 
 template <class T>
 __global__ void symmetrize_kernel(const T* __restrict__ H, const T* __restrict__ S, int n, T* __restrict__ Hs,
@@ -122,10 +53,6 @@ __device__ __forceinline__ double shfl_x(double v, int src) { return __shfl_sync
 __device__ __forceinline__ zd shfl_x(zd v, int src) {
   return zd{__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
 }
-
-// A kernel given a gate does nothing when the gate word is nonzero (a path of the subspace solve
-// that the device decided against; the word is the same for every CTA of a launch).
-__device__ __forceinline__ bool gated(const int* gate) { return gate && ld_volatile(gate) != 0; }
 
 template <class T, int MODE>
 __global__ void __launch_bounds__(CH_NT) cholesky_kernel(T* __restrict__ S, int n, unsigned* bar, DeviceStatus* st,
@@ -351,82 +278,6 @@ __device__ double block_reduce_sum(double v, double* s_red) {
   return s;   // valid in thread 0
 }
 
-// One step of the Ogita-Aishima refinement of an approximate eigenvector basis X of the
-// Hermitian A (Ogita & Aishima, "Iterative refinement for symmetric eigenvalue decomposition",
-// 2018): with S = X^H A X, R = I - X^H X, lambda_i = Re s_ii / (1 - Re r_ii),
-//   e_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i)  for |lambda_j - lambda_i| > delta,
-//   e_ij = r_ij / 2                                          otherwise (and e_ii = r_ii / 2),
-// X' = X + X E is orthonormal and diagonalizes A to second order in the error of X.  delta =
-// 2 (||S - diag S||_F + ||S||_F ||R||_F) separates clusters; their coupling is left to the
-// Jacobi sweeps, and so is every pair whose |e_ij| would exceed 1e-4 in the first step or
-// 1e-7 in a later one (a first-order correction made only in the second step would leave a
-// non-orthogonality of its square).  XtX = null means X = I (R = 0, S = A).  In the first step (XtX = null) *skip is
-// set when S is already diagonal to tol or when more than 2n coupled pairs would be left (far
-// from diagonal); every later step and product then copies instead.  One CTA.
-template <class T>
-__global__ void __launch_bounds__(1024) refine_step_kernel(const T* __restrict__ S, const T* __restrict__ XtX, int n,
-                                                          T* __restrict__ E, int* skip, double tol,
-                                                          const DeviceStatus* st, const int* gate) {
-  __shared__ double s_red[32];
-  __shared__ double s_v[3];
-  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
-  if (XtX && ld_volatile(skip)) return;
-  const int tid = threadIdx.x;
-  const int nn = n * n;
-  auto r_of = [&](int e) -> T {   // R = I - X^H X
-    if (!XtX) return zero<T>();
-    return from_real<T>(e / n == e % n ? 1.0 : 0.0) - XtX[e];
-  };
-  double off2 = 0.0, fro2 = 0.0, r2 = 0.0;
-  for (int e = tid; e < nn; e += blockDim.x) {
-    const double a2 = absx2(S[e]);
-    fro2 += a2;
-    if (e / n != e % n) off2 += a2;
-    r2 += absx2(r_of(e));
-  }
-  off2 = block_reduce_sum(off2, s_red);
-  if (tid == 0) s_v[0] = off2;
-  fro2 = block_reduce_sum(fro2, s_red);
-  if (tid == 0) s_v[1] = fro2;
-  r2 = block_reduce_sum(r2, s_red);
-  if (tid == 0) s_v[2] = r2;
-  __syncthreads();
-  off2 = s_v[0];
-  fro2 = s_v[1];
-  r2 = s_v[2];
-  if (!XtX && off2 <= tol * tol * fro2) {
-    if (tid == 0) *skip = 1;
-    return;
-  }
-  const double delta = fmax(2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
-  const double thr2 = tol * tol * fro2 / ((double)n * n);   // a coupling the Jacobi would rotate
-  auto lam = [&](int i) -> double {
-    const int d = i * n + i;
-    return realx(S[d]) / (1.0 - realx(r_of(d)));
-  };
-  double coupled = 0.0;   // pairs left to the Jacobi sweeps with a coupling above threshold
-  for (int e = tid; e < nn; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    T v = 0.5 * r_of(e);
-    if (i != j) {
-      const double li = lam(i), lj = lam(j);
-      bool cluster = fabs(lj - li) <= delta;
-      if (!cluster) {
-        const T w = (1.0 / (lj - li)) * (S[e] + lj * r_of(e));
-        // first step: |e_ij| <= 1e-4; later steps take only corrections that are already of
-        // second order (<= 1e-7), so that the orthogonality error they leave is O(1e-14)
-        if (absx2(w) <= (XtX ? 1e-14 : 1e-8)) v = w;
-        else cluster = true;
-      }
-      if (cluster && absx2(S[e]) > thr2) coupled += 1.0;
-    }
-    E[e] = v;
-  }
-  coupled = block_reduce_sum(coupled, s_red);
-  // too many coupled pairs: the matrix is far from diagonal, leave it all to the Jacobi sweeps
-  if (tid == 0 && !XtX) *skip = coupled > 2.0 * n ? 1 : 0;
-}
-
 template <class T>
 __global__ void identity_kernel(T* __restrict__ X, int n, const int* gate = nullptr) {
   if (gated(gate)) return;
@@ -444,7 +295,13 @@ __global__ void identity_kernel(T* __restrict__ X, int n, const int* gate = null
 
 // Gate words of one subspace solve (oa_decide_kernel): a kernel given gate word g does nothing
 // when flags[g] != 0.
-enum { GATE_NEAR = 0, GATE_FAR = 1, GATE_STEP2 = 2, GATE_AM = 3, GATE_JACOBI = 4, GATE_LAMBDA = 5 };
+// The far path's words: ZSKIP (the refinement from the FP32 basis Z), ZFAIL (its fallback, the
+// Jacobi sweeps from V = I), FAR_AM (X^H A X for the sweeps over coupled pairs), JACOBI_Z
+// (those sweeps).
+enum {
+  GATE_NEAR = 0, GATE_FAR = 1, GATE_STEP2 = 2, GATE_AM = 3, GATE_JACOBI = 4, GATE_LAMBDA = 5,
+  GATE_ZSKIP = 6, GATE_ZFAIL = 7, GATE_FAR_AM = 8, GATE_JACOBI_Z = 9
+};
 
 __device__ double block_reduce_max(double v, double* s_red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -487,13 +344,17 @@ __global__ void __launch_bounds__(256) oa_stats_kernel(const T* __restrict__ A, 
   }
 }
 
-// E of one step (see above).  delta = 2 (||A - diag A|| + ||A|| ||R||) separates clusters;
-// a pair is also left to the Jacobi sweeps when |e_ij|^2 would exceed ebound2.  Partials:
+// E of one step (see above).  delta = dscale 2 (||A - diag A|| + ||A|| ||R||) separates
+// clusters (at least 1e-13 ||A||_F); a pair is also left to the Jacobi sweeps when |e_ij|^2
+// would exceed ebound2.  Started from an FP32 eigenbasis the Frobenius bound counts the FP32
+// error of all n^2 entries and would call most pairs a cluster, so that path passes dscale =
+// 0 and relies on the bound on |e_ij| alone.  Partials:
 // part2[2 g] = pairs left coupled above the Jacobi threshold, part2[2 g + 1] = max |e_ij|^2.
 template <class T>
 __global__ void __launch_bounds__(256) oa_update_kernel(const T* __restrict__ A, const T* __restrict__ B, int n,
                                                         const double* __restrict__ lam, const double* __restrict__ part,
-                                                        double tol, double ebound2, T* __restrict__ E,
+                                                        double tol, double ebound2, double dscale,
+                                                        T* __restrict__ E,
                                                         double* __restrict__ part2, const int* gate,
                                                         const DeviceStatus* st) {
   __shared__ double s_red[32];
@@ -506,23 +367,30 @@ __global__ void __launch_bounds__(256) oa_update_kernel(const T* __restrict__ A,
   }
   __syncthreads();
   const double off2 = s_v[0], fro2 = s_v[1], r2 = s_v[2];
-  const double delta = fmax(2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
+  const double delta = fmax(dscale * 2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
   const double thr2 = tol * tol * fro2 / ((double)n * n);
   const long long nn = (long long)n * n;
   double coupled = 0.0, emax2 = 0.0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / n), j = (int)(e % n);
-    const T r = B ? from_real<T>(i == j ? 1.0 : 0.0) - B[e] : zero<T>();
+    const long long et = (long long)j * n + i;
+    // the Hermitian parts of A and B (products X^H A X are Hermitian only up to rounding, and
+    // e_ij + conj(e_ji) = r_ij holds exactly only for Hermitian inputs; otherwise the rounding
+    // asymmetry, divided by a small gap, would spoil the orthogonality of X')
+    const T a = 0.5 * (A[e] + conjx(A[et]));
+    const T r = B ? from_real<T>(i == j ? 1.0 : 0.0) - 0.5 * (B[e] + conjx(B[et])) : zero<T>();
     T v = 0.5 * r;
     if (i != j) {
       const double li = lam[i], lj = lam[j];
       bool cluster = fabs(lj - li) <= delta;
       if (!cluster) {
-        const T w = (1.0 / (lj - li)) * (A[e] + lj * r);
-        if (absx2(w) <= ebound2) v = w;
+        const T w = (1.0 / (lj - li)) * (a + lj * r);
+        // the pair (j, i) makes the same decision: both corrections within the bound
+        const T wt = (1.0 / (li - lj)) * (conjx(a) + li * conjx(r));
+        if (absx2(w) <= ebound2 && absx2(wt) <= ebound2) v = w;
         else cluster = true;
       }
-      if (cluster && absx2(A[e]) > thr2) coupled += 1.0;
+      if (cluster && absx2(a) > thr2) coupled += 1.0;
     }
     emax2 = fmax(emax2, absx2(v));
     E[e] = v;
@@ -555,6 +423,45 @@ __global__ void oa_decide_kernel(const double* __restrict__ part, const double* 
   flags[GATE_AM] = !near || nojac;
   flags[GATE_JACOBI] = near && nojac;
   flags[GATE_LAMBDA] = !(near && nojac);
+  flags[GATE_ZSKIP] = near;
+  flags[GATE_ZFAIL] = 1;
+  flags[GATE_FAR_AM] = 1;
+  flags[GATE_JACOBI_Z] = 1;
+}
+
+// Far path, after the first Ogita-Aishima step from the FP32 basis Z: Z is taken when the
+// norms are finite and ||I - Z^H Z||_F <= 1e-2; otherwise the Jacobi sweeps diagonalize A
+// from V = I.
+__global__ void far_decide1_kernel(const double* __restrict__ part, int* __restrict__ flags, const int* gate) {
+  if (threadIdx.x != 0 || gated(gate)) return;
+  double r2 = 0.0, fro2 = 0.0;
+  for (int g = 0; g < OA_G; ++g) {
+    fro2 += part[3 * g + 1];
+    r2 += part[3 * g + 2];
+  }
+  const bool ok = isfinite(r2) && isfinite(fro2) && r2 <= 1e-4;
+  flags[GATE_ZSKIP] = !ok;
+  flags[GATE_ZFAIL] = ok;
+  flags[GATE_JACOBI] = ok;
+  flags[GATE_JACOBI_Z] = 1;
+  flags[GATE_LAMBDA] = 1;
+  flags[GATE_FAR_AM] = 1;
+}
+
+// Far path, after the second step: with every |e_ij| <= 1e-8 and no pair coupled, X2 is the
+// eigenbasis to FP64 precision and the eigenvalues are the step's lambda_i; otherwise the
+// Jacobi sweeps run on X2^H A X2.
+__global__ void far_decide2_kernel(const double* __restrict__ part2, int* __restrict__ flags, const int* gate) {
+  if (threadIdx.x != 0 || gated(gate)) return;
+  double coupled = 0.0, emax2 = 0.0;
+  for (int g = 0; g < OA_G; ++g) {
+    coupled += part2[2 * g];
+    emax2 = fmax(emax2, part2[2 * g + 1]);
+  }
+  const bool nojac = emax2 <= 1e-16 && coupled == 0.0;
+  flags[GATE_JACOBI_Z] = nojac;
+  flags[GATE_LAMBDA] = !nojac;
+  flags[GATE_FAR_AM] = nojac;
 }
 
 // After the second step of the near path: when it left every |e_ij| <= 1e-8 and no pair
@@ -791,11 +698,10 @@ __global__ void phase_fix_kernel(T* __restrict__ C, int n, const DeviceStatus* s
 // of one thread-block cluster, the kernel runs as a single cluster and every round ends on a
 // hardware cluster barrier; otherwise as a cooperative grid with a software grid barrier.
 template <class T>
-int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm, const int* gate) {
+int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm, const int* gate, double tol) {
   cudaStream_t s = c->stream;
   const int npad = n + (n & 1), np = npad / 2;
   const size_t rot_bytes = sizeof(Rot) * np;
-  double tol = 1e-14;
   int max_sweeps = 60;
   unsigned* bar = c->d_barrier;
   DeviceStatus* st = c->d_status;
@@ -868,58 +774,6 @@ int launch_jacobi(pawfd_ctx* c, int n, T* Am, T* A2, T* Vm, const int* gate) {
   return rc;
 }
 
-// Launch a kernel of the MODE 1 / MODE 0 pair: one thread-block cluster of up to `want` CTAs
-// (non-portable sizes above 8 when allowed) when `cluster` is set and a cluster fits, else a
-// cooperative grid of up to `want` co-resident CTAs.
-template <class K1, class K0, class... Args>
-int launch_cluster_or_grid(pawfd_ctx* c, K1 kernel1, K0 kernel0, int nthreads, size_t smem, int want, bool cluster,
-                           const char* what, Args... args) {
-  cudaStream_t s = c->stream;
-  int rc;
-  if (cluster) {
-    int G = std::max(1, std::min(16, want));
-    if (G > 8 && cudaFuncSetAttribute(kernel1, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-      cudaGetLastError();
-      G = 8;
-    }
-    for (;; G = (G + 1) / 2) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(G);
-      cfg.blockDim = dim3(nthreads);
-      cfg.dynamicSmemBytes = smem;
-      cfg.stream = s;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = G;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, kernel1, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        nclusters = 0;
-      }
-      if (nclusters >= 1) {
-        rc = check_cuda(c, cudaLaunchKernelEx(&cfg, kernel1, args...), what);
-        c->launches += 1;
-        return rc;
-      }
-      if (G == 1) break;
-    }
-  }
-  int per_sm = 0;
-  rc = check_cuda(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel0, nthreads, smem), "occupancy");
-  if (rc != PAWFD_OK) return rc;
-  const int G = std::max(1, std::min(want, per_sm * c->num_sms));
-  rc = check_cuda(c, cudaMemsetAsync(c->d_barrier, 0, 2 * sizeof(unsigned), s), "barrier reset");
-  if (rc != PAWFD_OK) return rc;
-  void* argv[] = {&args...};
-  rc = check_cuda(c, cudaLaunchCooperativeKernel((const void*)kernel0, dim3(G), dim3(nthreads), argv, smem, s), what);
-  c->launches += 1;
-  return rc;
-}
-
 template <class T>
 int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   const long long nn = (long long)n * n;
@@ -945,13 +799,13 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   symmetrize_kernel<T><<<eb, 256, 0, s>>>(H, S, n, Hs, Lm);
   // the first Ogita-Aishima step from X = I on (H, S), and the path decision
   oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, part, lam, nullptr, st);
-  oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, lam, part, tol, 1e-8, Li, part2, nullptr, st);
+  oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, lam, part, tol, 1e-8, 1.0, Li, part2, nullptr, st);
   oa_decide_kernel<<<1, 32, 0, s>>>(part, part2, n, c->d_flags);
   c->launches += 4;
   int rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
 
-  // ---- far path: Cholesky S = L L^H, A = L^-1 H L^-H, Ogita-Aishima on A from X = I ----
+  // ---- far path: Cholesky S = L L^H, A = L^-1 H L^-H, its FP32 eigenbasis refined in FP64 ----
   // Cholesky: one cluster up to n = 256 (its flops fit 16 SMs), the whole GPU above
   {
     unsigned* bar = c->d_barrier;
@@ -968,26 +822,41 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   c->launches += 4;
   rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
-  // Two Ogita-Aishima steps from X = I (skipped on the device when A is already diagonal or
-  // far from it), then A <- X^H A X and the Jacobi sweeps, which accumulate onto X
+  // FP32 eigendecomposition A ~= Z diag Z^H (tridiag.cu), then two Ogita-Aishima steps in FP64
+  // from X = Z: X1 = Z (I + E1), X2 = X1 (I + E2).  Pairs of close eigenvalues that the steps
+  // leave coupled go to the Jacobi sweeps on X2^H A X2 (threshold 1e-12 ||A||_F / n: the FP64
+  // rounding of X2^H A X2 stays below it); an unusable Z sends A to the sweeps from V = I.
   {
-    identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n, near);
-    c->launches += 1;
-    int* skip = (int*)(c->d_barrier + 2);
-    // step 1: S = A, R = 0; X1 = I + E into Hs (the symmetrized H is no longer needed)
-    refine_step_kernel<T><<<1, 1024, 0, s>>>(Am, nullptr, n, T1, skip, tol, st, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, T1, false, n, Hs, st, Vm, skip, Vm, near);
-    // step 2: S = X1^H A X1 (into Lm, no longer needed), X1^H X1 (into A2), X2 = X1 + X1 E into Vm
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Hs, false, n, T1, st, nullptr, skip, Am, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, T1, false, n, Lm, st, nullptr, skip, T1, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, true, Hs, false, n, A2, st, nullptr, skip, Vm, near);
-    refine_step_kernel<T><<<1, 1024, 0, s>>>(Lm, A2, n, T1, skip, tol, st, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, T1, false, n, Vm, st, Hs, skip, Hs, near);
-    // A <- X2^H A X2
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, skip, Am, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, skip, T1, near);
-    c->launches += 9;
-    rc = check_cuda(c, cudaGetLastError(), "refinement steps");
+    const double tol_z = 1e-12;
+    const int* zskip = flags + GATE_ZSKIP;
+    const int* fam = flags + GATE_FAR_AM;
+    rc = launch_eig32(c, n, Am, Vm, near);
+    if (rc != PAWFD_OK) return rc;
+    // step 1: S1 = Z^H A Z (Lm), B1 = Z^H Z (A2), E1 (Hs)
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Lm, st, nullptr, nullptr, nullptr, near);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, Vm, false, n, A2, st, nullptr, nullptr, nullptr, near);
+    oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, near, st);
+    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, 1e-8, 0.0, Hs, part2, near, st);
+    far_decide1_kernel<<<1, 32, 0, s>>>(part, c->d_flags, near);
+    // X1 = Z + Z E1 (T1)
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Hs, false, n, T1, st, Vm, nullptr, nullptr, zskip);
+    // step 2: S2 = X1^H A X1 (Lm), B2 = X1^H X1 (A2), E2 (Hs); X2 = X1 + X1 E2 (Vm)
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, T1, false, n, Hs, st, nullptr, nullptr, nullptr, zskip);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, true, Hs, false, n, Lm, st, nullptr, nullptr, nullptr, zskip);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, true, T1, false, n, A2, st, nullptr, nullptr, nullptr, zskip);
+    oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, zskip, st);
+    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, 1e-14, 0.0, Hs, part2, zskip, st);
+    far_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, zskip);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Hs, false, n, Vm, st, T1, nullptr, nullptr, zskip);
+    // A <- X2^H A X2 for the sweeps over the coupled pairs
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, fam);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, fam);
+    hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, fam);
+    // the fallback: the sweeps on A from V = I
+    identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n, flags + GATE_ZFAIL);
+    c->launches += 20;
+    rc = check_cuda(c, cudaGetLastError(), "far-path refinement");
     if (rc != PAWFD_OK) return rc;
   }
 
@@ -1003,7 +872,7 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Lm, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2);
     oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, part, lam, step2, st);
-    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol, 1e-14, Li, part2, step2, st);
+    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol, 1e-14, 1.0, Li, part2, step2, st);
     oa_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Li, false, n, T1, st, Vm, nullptr, nullptr, step2);
     copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, step2, st);
@@ -1015,7 +884,9 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     rc = check_cuda(c, cudaGetLastError(), "near-path launch");
     if (rc != PAWFD_OK) return rc;
   }
-  rc = launch_jacobi<T>(c, n, Am, A2, Vm, flags + GATE_JACOBI);
+  rc = launch_jacobi<T>(c, n, Am, A2, Vm, flags + GATE_JACOBI, tol);
+  if (rc != PAWFD_OK) return rc;
+  rc = launch_jacobi<T>(c, n, Am, A2, Vm, flags + GATE_JACOBI_Z, 1e-12);
   if (rc != PAWFD_OK) return rc;
   sort_kernel<T><<<n, 128, 0, s>>>(Am, Vm, n, eps, T1, c->d_status);
   // C = L^-H U (far path) or U (near path: a copy)

@@ -387,6 +387,89 @@ def test_subspace_against_oracle_random(dev):
     del s, api
 
 
+@pytest.mark.parametrize("dsm", [1, 0])
+@pytest.mark.parametrize("cplx", [False, True])
+def test_subspace_far_path_n512(dev, cplx, dsm):
+    """The far path at n = 512 (the Davidson pencil of 256 bands): the FP32 tridiagonal
+    eigenbasis (reduction in the cluster's shared memory, or in global memory) refined in
+    FP64, against the oracle's Cholesky + cyclic Jacobi."""
+    from paper_2310_14776_gb300 import api
+    n = 512
+    sysm = synth.make_system((8, 8, 8), (4.0, 4.0, 4.0), 0, synth.PSET_SP, 1, k=(0.1, 0.0, 0.0) if cplx else
+                             (0.0, 0.0, 0.0), complex_wf=cplx)
+    ctx = api.Context(sysm, max_bands=n, device=dev)
+    ctx.set_option("tridiag_dsm", dsm)
+    A = synth.uniform(n, 1, n * n, -1, 1).reshape(n, n)
+    B = synth.uniform(n, 2, n * n, -1, 1).reshape(n, n)
+    if cplx:
+        A = A + 1j * synth.uniform(n, 3, n * n, -1, 1).reshape(n, n)
+        B = B + 1j * synth.uniform(n, 4, n * n, -1, 1).reshape(n, n)
+    H = 0.5 * (A + A.conj().T) * 30
+    S = B @ B.conj().T / n + np.eye(n)
+    ref_eps, _, _ = O.subspace_diag(H, S)
+    eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
+    check_subspace(eps.cpu().numpy(), C.cpu().numpy(), H, S, ref_eps)
+    ctx.close()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_subspace_far_path_clusters(dev, cplx):
+    """Far-path pencils whose spectra hold exact and near degeneracies (multiplicities 2 to 6,
+    splittings 0 to 1e-6, and a 40-fold eigenvalue): the FP32 basis cannot separate them, the
+    FP64 steps leave them coupled and the Jacobi sweeps finish them."""
+    from paper_2310_14776_gb300 import api
+    n = 200
+    sysm = synth.make_system((8, 8, 8), (4.0, 4.0, 4.0), 0, synth.PSET_SP, 1, k=(0.1, 0.0, 0.0) if cplx else
+                             (0.0, 0.0, 0.0), complex_wf=cplx)
+    ctx = api.Context(sysm, max_bands=n, device=dev)
+    rng = np.random.default_rng(31)
+    lam = []
+    while len(lam) < n - 40:
+        m = int(rng.integers(1, 7))
+        base = rng.uniform(-20.0, 20.0)
+        lam += list(base + rng.choice([0.0, 1e-9, 1e-6]) * np.arange(m))
+    lam = np.array(lam[:n - 40] + [3.25] * 40)
+    Q = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    Q, _ = np.linalg.qr(Q)
+    B = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    S = B @ B.conj().T / n + np.eye(n)
+    L = np.linalg.cholesky(S)
+    H = L @ (Q * lam) @ Q.conj().T @ L.conj().T     # eigenvalues of (H, S): lam
+    H = 0.5 * (H + H.conj().T)
+    ref_eps, _, _ = O.subspace_diag(H, S)
+    eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
+    check_subspace(eps.cpu().numpy(), C.cpu().numpy(), H, S, ref_eps)
+    assert np.max(np.abs(np.sort(lam) - eps.cpu().numpy())) <= 1e-10
+    ctx.close()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_subspace_far_path_narrow_spectrum(dev, cplx):
+    """256 eigenvalues in a band of 0.9 Ha around 28.5 Ha (the Ritz values of random bands at
+    96^3): FP32 eigenvectors couple most neighbours by more than the first refinement step
+    takes, so many pairs pass through both steps and the Jacobi sweeps.  Regression case for
+    the rounding asymmetry of X^H A X, which a small gap amplified into a loss of
+    orthogonality of the refined basis (3e-9 Ha eigenvalue errors)."""
+    from paper_2310_14776_gb300 import api
+    n = 256
+    sysm = synth.make_system((8, 8, 8), (4.0, 4.0, 4.0), 0, synth.PSET_SP, 1, k=(0.1, 0.0, 0.0) if cplx else
+                             (0.0, 0.0, 0.0), complex_wf=cplx)
+    ctx = api.Context(sysm, max_bands=n, device=dev)
+    rng = np.random.default_rng(37)
+    lam = np.sort(rng.uniform(28.1, 29.0, n))
+    Q = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    Q, _ = np.linalg.qr(Q)
+    B = rng.standard_normal((n, n)) + (1j * rng.standard_normal((n, n)) if cplx else 0)
+    S = B @ B.conj().T / n + np.eye(n)
+    L = np.linalg.cholesky(S)
+    H = L @ (Q * lam) @ Q.conj().T @ L.conj().T
+    H = 0.5 * (H + H.conj().T)
+    ref_eps, _, _ = O.subspace_diag(H, S)
+    eps, C = ctx.subspace_diag(to_dev(H, dev), to_dev(S, dev))
+    check_subspace(eps.cpu().numpy(), C.cpu().numpy(), H, S, ref_eps)
+    ctx.close()
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_subspace_near_ritz_basis(dev, cplx):
     """H_nm, S_nm of bands that are already (nearly) Ritz vectors: S close to I, H close to

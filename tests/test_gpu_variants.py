@@ -98,6 +98,7 @@ FP64_OPTIONS = [
     {"stencil_zsplit": 1},
     {"stencil_zsplit": 16},
     {"jacobi_cluster": 1},                    # Cholesky and Jacobi on one thread-block cluster
+    {"tridiag_dsm": 0},                       # FP32 tridiagonal reduction in global memory
 ]
 
 
