@@ -254,6 +254,8 @@ def run_gpu(args):
         psi_src = "seeded torch generator on the device (uniform(-1, 1))"
         args.no_e2e = True
     esize = psi0.element_size()
+    # the random start, kept for the whole-job timing below when it is small enough to copy
+    psi_start = psi0.clone() if nb * K * esize <= 4e9 else None
     psi = [psi0, torch.empty_like(psi0)]
     work = {"Hpsi": ctx.empty_bands(nb), "Spsi": ctx.empty_bands(nb),
             "P": torch.empty((max(ctx.Ip, 1), nb), dtype=ctx.dtype, device=dev),
@@ -322,6 +324,27 @@ def run_gpu(args):
     ctx.sync()
     latest_idx = (args.warmup + 2 * args.steps) % 2   # the newest rotated bands, and their eps
     eps_latest = work["eps"].clone()
+    C_latest = work["C"].clone() if args.precision == "mixed" else None
+    # a whole job of ten steps from the random start: its first step takes the far path of the
+    # subspace solve (Cholesky reduction, FP32 tridiagonal eigenbasis, FP64 refinement), which
+    # the warm-up steps absorb in the timed value; the later steps are near-Ritz steps
+    job = None
+    if psi_start is not None:
+        scratch = psi[1 - latest_idx].clone()
+        jev = [ev() for _ in range(11)]
+        jev[0].record(stream)
+        cur, nxt = psi_start, scratch
+        for i in range(10):
+            whole_step(cur, nxt)
+            jev[i + 1].record(stream)
+            cur, nxt = nxt, cur
+        torch.cuda.synchronize(dev)
+        ctx.sync()
+        jms = [jev[i].elapsed_time(jev[i + 1]) for i in range(10)]
+        job = {"steps": 10, "job_ms": float(sum(jms)), "first_step_ms": jms[0],
+               "later_steps_mean_ms": float(np.mean(jms[1:])),
+               "what": "ten pawfd_rr_step calls from the seeded random bands, CUDA events around each"}
+        del scratch, psi_start
     elapsed = max_over_ranks(elapsed, world, dev)
     names = ["apply_HS", "gram_HS", "subspace_diag", "rotate"]
     stages = {nm: statistics.mean(m[i].elapsed_time(m[i + 1]) for m in marks) for i, nm in enumerate(names)}
@@ -392,6 +415,7 @@ def run_gpu(args):
                        "of psi with the subspace solve)",
         "apply_HS_gptband_s": nb * K / (stages["apply_HS"] * 1e-3) / 1e9,
         "eig_drift_ha": drift,
+        "job": job,
         "roofline": kernel_roof,
         "stage_roofline": {"stage": dom, "kernel": kernel_of[dom], "bound": bound, "achieved": achieved / scale,
                            "peak": peak / scale, "unit": roof_unit, "frac": achieved / peak,
@@ -411,7 +435,7 @@ def run_gpu(args):
         # the last step's input bands and its eigenvector matrix (the refinement rotates the
         # former by the latter in FP64); its rotated output is not needed
         last_in = psi[1 - latest_idx]
-        C_last = work["C"].clone()
+        C_last = C_latest
         eps_mixed = eps_latest
         for key in ("Hpsi", "Spsi"):
             work[key] = None

@@ -315,12 +315,13 @@ int launch_gram_hs(pawfd_ctx* c, const void* psi, const void* hpsi, int nb, cons
 // CTAs of the Ogita-Aishima element kernels and the doubles of their scratch for nb bands
 constexpr int OA_G = 64;
 inline size_t oa_scratch_doubles(int nb) { return 5 * (size_t)OA_G + (size_t)nb; }
-// the working matrix (FP32 of the band kind), the eigenvectors of T (float) and five vectors,
+// the working matrix (FP32 of the band kind), the eigenvectors of T (two float buffers), their
+// Gram matrix and five vectors,
 // each rounded up to 256 bytes
 inline size_t eig32_scratch_bytes(int nb, bool complex) {
   const size_t f = complex ? 8 : 4, n = (size_t)nb;
   auto r = [](size_t b) { return (b + 255) / 256 * 256; };
-  return r(n * n * f) + r(n * n * 4) + 2 * r(n * f) + 3 * r(n * 4);
+  return r(n * n * f) + 3 * r(n * n * 4) + 2 * r(n * f) + 3 * r(n * 4);
 }
 
 // order-6 central second-difference weights: f'' ~ (1/h^2) sum_m w_|m| f(x + m h)

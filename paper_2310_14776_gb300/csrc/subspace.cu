@@ -295,12 +295,12 @@ __global__ void identity_kernel(T* __restrict__ X, int n, const int* gate = null
 
 // Gate words of one subspace solve (oa_decide_kernel): a kernel given gate word g does nothing
 // when flags[g] != 0.
-// The far path's words: ZSKIP (the refinement from the FP32 basis Z), ZFAIL (its fallback, the
-// Jacobi sweeps from V = I), FAR_AM (X^H A X for the sweeps over coupled pairs), JACOBI_Z
-// (those sweeps).
+// The far path's words: ZSKIP (the refinement from the FP32 basis Z), ZSTEP2 and ZSTEP3 (its
+// second and third steps), ZFAIL (its fallback, the Jacobi sweeps from V = I), FAR_AM
+// (X^H A X for the sweeps over coupled pairs), JACOBI_Z (the sweeps after refinement steps).
 enum {
   GATE_NEAR = 0, GATE_FAR = 1, GATE_STEP2 = 2, GATE_AM = 3, GATE_JACOBI = 4, GATE_LAMBDA = 5,
-  GATE_ZSKIP = 6, GATE_ZFAIL = 7, GATE_FAR_AM = 8, GATE_JACOBI_Z = 9
+  GATE_ZSKIP = 6, GATE_ZFAIL = 7, GATE_FAR_AM = 8, GATE_JACOBI_Z = 9, GATE_ZSTEP2 = 10, GATE_ZSTEP3 = 11
 };
 
 __device__ double block_reduce_max(double v, double* s_red) {
@@ -344,16 +344,17 @@ __global__ void __launch_bounds__(256) oa_stats_kernel(const T* __restrict__ A, 
   }
 }
 
-// E of one step (see above).  delta = dscale 2 (||A - diag A|| + ||A|| ||R||) separates
-// clusters (at least 1e-13 ||A||_F); a pair is also left to the Jacobi sweeps when |e_ij|^2
-// would exceed ebound2.  Started from an FP32 eigenbasis the Frobenius bound counts the FP32
-// error of all n^2 entries and would call most pairs a cluster, so that path passes dscale =
-// 0 and relies on the bound on |e_ij| alone.  Partials:
-// part2[2 g] = pairs left coupled above the Jacobi threshold, part2[2 g + 1] = max |e_ij|^2.
+// E of one step (see above).  Pairs with |lambda_j - lambda_i| <= 1e-13 ||A||_F are a
+// cluster; every other pair is corrected unless |e_ij| or |e_ji| would exceed sqrt(ebound2),
+// in which case it is left to the Jacobi sweeps as well.  (Ogita and Aishima separate clusters
+// by delta = 2 (||A - diag A|| + ||A|| ||R||); with Frobenius norms that bound sums the error of
+// all n^2 entries and calls most pairs of a dense spectrum a cluster, so the bound on the
+// corrections decides instead.)  Partials: part2[2 g] = pairs left coupled above the Jacobi
+// threshold, part2[2 g + 1] = max |e_ij|^2.
 template <class T>
 __global__ void __launch_bounds__(256) oa_update_kernel(const T* __restrict__ A, const T* __restrict__ B, int n,
                                                         const double* __restrict__ lam, const double* __restrict__ part,
-                                                        double tol, double ebound2, double dscale,
+                                                        double tol, double ebound2,
                                                         T* __restrict__ E,
                                                         double* __restrict__ part2, const int* gate,
                                                         const DeviceStatus* st) {
@@ -366,8 +367,8 @@ __global__ void __launch_bounds__(256) oa_update_kernel(const T* __restrict__ A,
     s_v[threadIdx.x] = v;
   }
   __syncthreads();
-  const double off2 = s_v[0], fro2 = s_v[1], r2 = s_v[2];
-  const double delta = fmax(dscale * 2.0 * (sqrt(off2) + sqrt(fro2 * r2)), 1e-13 * sqrt(fro2));
+  const double fro2 = s_v[1];
+  const double delta = 1e-13 * sqrt(fro2);
   const double thr2 = tol * tol * fro2 / ((double)n * n);
   const long long nn = (long long)n * n;
   double coupled = 0.0, emax2 = 0.0;
@@ -421,12 +422,14 @@ __global__ void oa_decide_kernel(const double* __restrict__ part, const double* 
   flags[GATE_FAR] = !near;
   flags[GATE_STEP2] = !near || one;
   flags[GATE_AM] = !near || nojac;
-  flags[GATE_JACOBI] = near && nojac;
+  flags[GATE_JACOBI] = 1;
   flags[GATE_LAMBDA] = !(near && nojac);
   flags[GATE_ZSKIP] = near;
   flags[GATE_ZFAIL] = 1;
   flags[GATE_FAR_AM] = 1;
-  flags[GATE_JACOBI_Z] = 1;
+  flags[GATE_JACOBI_Z] = !near || nojac;
+  flags[GATE_ZSTEP2] = 1;
+  flags[GATE_ZSTEP3] = 1;
 }
 
 // Far path, after the first Ogita-Aishima step from the FP32 basis Z: Z is taken when the
@@ -441,6 +444,8 @@ __global__ void far_decide1_kernel(const double* __restrict__ part, int* __restr
   }
   const bool ok = isfinite(r2) && isfinite(fro2) && r2 <= 1e-4;
   flags[GATE_ZSKIP] = !ok;
+  flags[GATE_ZSTEP2] = !ok;
+  flags[GATE_ZSTEP3] = 1;
   flags[GATE_ZFAIL] = ok;
   flags[GATE_JACOBI] = ok;
   flags[GATE_JACOBI_Z] = 1;
@@ -448,20 +453,26 @@ __global__ void far_decide1_kernel(const double* __restrict__ part, int* __restr
   flags[GATE_FAR_AM] = 1;
 }
 
-// Far path, after the second step: with every |e_ij| <= 1e-8 and no pair coupled, X2 is the
-// eigenbasis to FP64 precision and the eigenvalues are the step's lambda_i; otherwise the
-// Jacobi sweeps run on X2^H A X2.
-__global__ void far_decide2_kernel(const double* __restrict__ part2, int* __restrict__ flags, const int* gate) {
+// Far path, after refinement step 2 (last = 0) or 3 (last = 1): with every |e_ij| <= 1e-8
+// and no pair coupled, the step's basis is the eigenbasis to FP64 precision (the error left is
+// of the order of |e|^2) and the eigenvalues are the step's lambda_i; otherwise, after step 2
+// the third step runs, after step 3 the Jacobi sweeps run on X^H A X.
+__global__ void far_decide_kernel(const double* __restrict__ part2, int last, int* __restrict__ flags,
+                                  const int* gate) {
   if (threadIdx.x != 0 || gated(gate)) return;
   double coupled = 0.0, emax2 = 0.0;
   for (int g = 0; g < OA_G; ++g) {
     coupled += part2[2 * g];
     emax2 = fmax(emax2, part2[2 * g + 1]);
   }
-  const bool nojac = emax2 <= 1e-16 && coupled == 0.0;
-  flags[GATE_JACOBI_Z] = nojac;
-  flags[GATE_LAMBDA] = !nojac;
-  flags[GATE_FAR_AM] = nojac;
+  const bool done = emax2 <= 1e-16 && coupled == 0.0;
+  if (!last && !done) {
+    flags[GATE_ZSTEP3] = 0;
+    return;
+  }
+  flags[GATE_JACOBI_Z] = done;
+  flags[GATE_LAMBDA] = !done;
+  flags[GATE_FAR_AM] = done;
 }
 
 // After the second step of the near path: when it left every |e_ij| <= 1e-8 and no pair
@@ -477,7 +488,7 @@ __global__ void oa_decide2_kernel(const double* __restrict__ part2, int* __restr
   }
   if (emax2 <= 1e-16 && coupled == 0.0) {
     flags[GATE_AM] = 1;
-    flags[GATE_JACOBI] = 1;
+    flags[GATE_JACOBI_Z] = 1;
     flags[GATE_LAMBDA] = 0;
   }
 }
@@ -793,13 +804,16 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   double* part = c->d_oa;                   // [3 OA_G] norms
   double* part2 = c->d_oa + 3 * OA_G;       // [2 OA_G] coupled pairs, max |e|^2
   double* lam = c->d_oa + 5 * OA_G;         // [n]
-  const double tol = 1e-14;
+  const double tol = 1e-14;     // the sweeps from V = I (far-path fallback)
+  // the sweeps after Ogita-Aishima steps: threshold 1e-12 ||A||_F / n, above the FP64 rounding
+  // of the X^H A X they run on
+  const double tol_z = 1e-12;
   const unsigned eb = (unsigned)((nn + 255) / 256);
   const dim3 gg((n + 15) / 16, (n + 15) / 16);
   symmetrize_kernel<T><<<eb, 256, 0, s>>>(H, S, n, Hs, Lm);
   // the first Ogita-Aishima step from X = I on (H, S), and the path decision
   oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, part, lam, nullptr, st);
-  oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, lam, part, tol, 1e-8, 1.0, Li, part2, nullptr, st);
+  oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Hs, Lm, n, lam, part, tol_z, 1e-8, Li, part2, nullptr, st);
   oa_decide_kernel<<<1, 32, 0, s>>>(part, part2, n, c->d_flags);
   c->launches += 4;
   int rc = check_cuda(c, cudaGetLastError(), "subspace launch");
@@ -822,40 +836,45 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   c->launches += 4;
   rc = check_cuda(c, cudaGetLastError(), "subspace launch");
   if (rc != PAWFD_OK) return rc;
-  // FP32 eigendecomposition A ~= Z diag Z^H (tridiag.cu), then two Ogita-Aishima steps in FP64
-  // from X = Z: X1 = Z (I + E1), X2 = X1 (I + E2).  Pairs of close eigenvalues that the steps
-  // leave coupled go to the Jacobi sweeps on X2^H A X2 (threshold 1e-12 ||A||_F / n: the FP64
-  // rounding of X2^H A X2 stays below it); an unusable Z sends A to the sweeps from V = I.
+  // FP32 eigendecomposition A ~= Z diag Z^H (tridiag.cu), then Ogita-Aishima steps in FP64
+  // from X0 = Z: X_k = X_{k-1} (I + E_k), taking corrections up to 1e-2, 1e-4 and 1e-7 (each
+  // step squares the error of the last; the first bound is wide because the FP32 basis couples
+  // neighbours of a dense spectrum by about eps_32 ||A|| / gap); the third step runs only when
+  // the second left a correction above 1e-8 or a coupled pair.  Pairs still coupled (close
+  // eigenvalues) go to the Jacobi sweeps on X^H A X (threshold 1e-12 ||A||_F / n: the FP64
+  // rounding of X^H A X stays below it); an unusable Z sends A to the sweeps from V = I.
   {
-    const double tol_z = 1e-12;
-    const int* zskip = flags + GATE_ZSKIP;
     const int* fam = flags + GATE_FAR_AM;
     rc = launch_eig32(c, n, Am, Vm, near);
     if (rc != PAWFD_OK) return rc;
-    // step 1: S1 = Z^H A Z (Lm), B1 = Z^H Z (A2), E1 (Hs)
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Lm, st, nullptr, nullptr, nullptr, near);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, Vm, false, n, A2, st, nullptr, nullptr, nullptr, near);
-    oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, near, st);
-    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, 1e-8, 0.0, Hs, part2, near, st);
+    // one step from P: A P (Hs), S = P^H A P (Lm), B = P^H P (A2), E (Hs); then P + P E
+    auto oa_step = [&](T* P, double ebound2, const int* gate) {
+      small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, P, false, n, Hs, st, nullptr, nullptr, nullptr, gate);
+      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, Hs, false, n, Lm, st, nullptr, nullptr, nullptr, gate);
+      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, P, false, n, A2, st, nullptr, nullptr, nullptr, gate);
+      oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, gate, st);
+      oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, ebound2, Hs, part2, gate, st);
+    };
+    oa_step(Vm, 1e-4, near);
     far_decide1_kernel<<<1, 32, 0, s>>>(part, c->d_flags, near);
-    // X1 = Z + Z E1 (T1)
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Hs, false, n, T1, st, Vm, nullptr, nullptr, zskip);
-    // step 2: S2 = X1^H A X1 (Lm), B2 = X1^H X1 (A2), E2 (Hs); X2 = X1 + X1 E2 (Vm)
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, T1, false, n, Hs, st, nullptr, nullptr, nullptr, zskip);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, true, Hs, false, n, Lm, st, nullptr, nullptr, nullptr, zskip);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, true, T1, false, n, A2, st, nullptr, nullptr, nullptr, zskip);
-    oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, zskip, st);
-    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, 1e-14, 0.0, Hs, part2, zskip, st);
-    far_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, zskip);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Hs, false, n, Vm, st, T1, nullptr, nullptr, zskip);
-    // A <- X2^H A X2 for the sweeps over the coupled pairs
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Hs, false, n, T1, st, Vm, nullptr, nullptr,
+                                            flags + GATE_ZSKIP);
+    oa_step(T1, 1e-8, flags + GATE_ZSTEP2);
+    far_decide_kernel<<<1, 32, 0, s>>>(part2, 0, c->d_flags, flags + GATE_ZSTEP2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Hs, false, n, Vm, st, T1, nullptr, nullptr,
+                                            flags + GATE_ZSTEP2);
+    oa_step(Vm, 1e-14, flags + GATE_ZSTEP3);
+    far_decide_kernel<<<1, 32, 0, s>>>(part2, 1, c->d_flags, flags + GATE_ZSTEP3);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Hs, false, n, T1, st, Vm, nullptr, nullptr,
+                                            flags + GATE_ZSTEP3);
+    copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, flags + GATE_ZSTEP3, st);
+    // A <- X^H A X for the sweeps over the coupled pairs
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, fam);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, fam);
     hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, fam);
     // the fallback: the sweeps on A from V = I
     identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n, flags + GATE_ZFAIL);
-    c->launches += 20;
+    c->launches += 30;
     rc = check_cuda(c, cudaGetLastError(), "far-path refinement");
     if (rc != PAWFD_OK) return rc;
   }
@@ -872,7 +891,7 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Lm, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2);
     oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, part, lam, step2, st);
-    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol, 1e-14, 1.0, Li, part2, step2, st);
+    oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol_z, 1e-14, Li, part2, step2, st);
     oa_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Li, false, n, T1, st, Vm, nullptr, nullptr, step2);
     copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, step2, st);

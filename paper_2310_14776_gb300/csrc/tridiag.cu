@@ -11,8 +11,13 @@
 //      cluster, two cluster barriers per column;
 //   2. the eigenvalues of T by multisection on Sturm counts, one warp per eigenvalue;
 //   3. the eigenvectors of T by inverse iteration with a partial-pivoting LU of T - sigma I,
-//      the vectors of eigenvalues closer than 1e-3 ||T||_1 orthogonalized against each other
-//      (modified Gram-Schmidt within each iteration), one warp per group of close eigenvalues;
+//      the vectors of eigenvalues closer than 1e-5 ||T||_1 orthogonalized against each other
+//      (modified Gram-Schmidt within each iteration), one warp per group of such eigenvalues;
+//      then three Newton-Schulz steps Y <- Y (3 I - Y^T Y) / 2, which take the overlaps that
+//      inverse iteration leaves between vectors of close but separate eigenvalues (about
+//      eps ||T|| / gap, below 1e-2 outside the groups) down to FP32 rounding in parallel, where
+//      Gram-Schmidt over a group of close eigenvalues would be one long sequential chain (a
+//      narrow spectrum, such as the Ritz values of random bands, is one such group);
 //   4. Z = Q Y, the reflectors applied to the eigenvectors of T, one warp per vector.
 // Every step is deterministic (fixed reduction orders, a fixed pseudo-random start vector per
 // eigenvector), so repeated solves of the same matrix give bitwise the same Z.
@@ -362,7 +367,7 @@ __global__ void __launch_bounds__(256) tri_bisect_kernel(const float* __restrict
 
 // ------------------------------------------------------------------------------------------
 // 3. Eigenvectors of T by inverse iteration.  The warp of j works only if j starts a group
-//    (lambda_j - lambda_{j-1} > 1e-3 ||T||_1); it then computes the vectors of the group in
+//    (lambda_j - lambda_{j-1} > 1e-5 ||T||_1); it then computes the vectors of the group in
 //    order.  Shifts within a group are kept at least 10 eps |lambda| apart.  Per vector: one
 //    LU factorization of T - sigma I with partial pivoting (lane 0), three solves from a
 //    fixed pseudo-random start, each followed by modified Gram-Schmidt against the group's
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(32) tri_vectors_kernel(const float* __restrict
     tn = fmaxf(tn, r);
   }
   for (int o = 16; o > 0; o >>= 1) tn = fmaxf(tn, __shfl_xor_sync(0xffffffffu, tn, o));
-  const float ortol = 1e-3f * tn;
+  const float ortol = 1e-5f * tn;
   if (j0 > 0 && lam[j0] - lam[j0 - 1] <= ortol) return;
   int j1 = j0 + 1;
   while (j1 < n && lam[j1] - lam[j1 - 1] <= ortol) ++j1;
@@ -483,6 +488,78 @@ __global__ void __launch_bounds__(32) tri_vectors_kernel(const float* __restrict
 }
 
 // ------------------------------------------------------------------------------------------
+// 3b. Newton-Schulz orthonormalization of the rows of Yt (the eigenvectors of T):
+//     G = Yt Yt^T, then Yt <- (3 I - G) Yt / 2.  FP32 tiles of 64 x 64 (4 x 4 per thread),
+//     16-deep slabs staged in shared memory.  BT: C = alpha A B^T + beta D, else
+//     C = alpha A B + beta D (all n x n, row-major); the diagonal of C gets delta added.
+// ------------------------------------------------------------------------------------------
+template <bool BT>
+__global__ void __launch_bounds__(256) ns_gemm_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                                      const float* __restrict__ D, int n, float alpha, float beta,
+                                                      float delta, float* __restrict__ C, const DeviceStatus* st,
+                                                      const int* gate) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  if (ld_volatile(&st->code) != 0 || gated(gate)) return;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    // A tile: rows r0..r0+63, columns k0..k0+15 (stored transposed: As[k][r])
+    for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+      const int r = q / 16, k = q % 16;
+      const int gr = r0 + r, gk = k0 + k;
+      As[k][r] = (gr < n && gk < n) ? A[(long long)gr * n + gk] : 0.f;
+    }
+    // B tile: op(B) rows k0..k0+15, columns c0..c0+63 (Bs[k][c])
+    for (int q = threadIdx.x; q < 64 * 16; q += 256) {
+      int k, cc;
+      float v;
+      if (BT) {   // op(B)[k][c] = B[c][k]
+        cc = q / 16;
+        k = q % 16;
+        const int gc = c0 + cc, gk = k0 + k;
+        v = (gc < n && gk < n) ? B[(long long)gc * n + gk] : 0.f;
+      } else {
+        k = q / 64;
+        cc = q % 64;
+        const int gc = c0 + cc, gk = k0 + k;
+        v = (gc < n && gk < n) ? B[(long long)gk * n + gc] : 0.f;
+      }
+      Bs[k][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[k][ty + 16 * u];
+        b[u] = Bs[k][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = r0 + ty + 16 * u, cc = c0 + tx + 16 * v;
+      if (r < n && cc < n) {
+        const long long o = (long long)r * n + cc;
+        float x = alpha * acc[u][v];
+        if (D) x = fmaf(beta, D[o], x);
+        if (r == cc) x += delta;
+        C[o] = x;
+      }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // 4. Z = Q Y = H_0 H_1 ... H_{n-2} Y: one warp per eigenvector (in shared memory), the
 //    reflectors applied from the last to the first, RB of them staged in shared memory per
 //    CTA barrier.  Z is written in FP64 (row i, column j = component i of vector j).
@@ -541,6 +618,8 @@ int eig32_impl(pawfd_ctx* c, int n, const T* A, T* Z, const int* gate) {
   };
   F* W = (F*)take(nn * sizeof(F));
   float* Yt = (float*)take(nn * sizeof(float));
+  float* Y2 = (float*)take(nn * sizeof(float));
+  float* G = (float*)take(nn * sizeof(float));
   F* P = (F*)take((size_t)n * sizeof(F));
   F* tau = (F*)take((size_t)n * sizeof(F));
   float* d = (float*)take((size_t)n * sizeof(float));
@@ -609,6 +688,21 @@ int eig32_impl(pawfd_ctx* c, int n, const T* A, T* Z, const int* gate) {
     if (rc != PAWFD_OK) return rc;
   }
   tri_vectors_kernel<<<n, 32, smem3, s>>>(d, e, lam, n, Yt, c->d_status, gate);
+  // 3b. three Newton-Schulz steps: G = Yt Yt^T; Yt <- 1.5 Yt - 0.5 G Yt (ping-pong Yt, Y2)
+  {
+    const dim3 g64((n + 63) / 64, (n + 63) / 64);
+    float* cur = Yt;
+    float* nxt = Y2;
+    for (int it = 0; it < 3; ++it) {
+      ns_gemm_kernel<true><<<g64, 256, 0, s>>>(cur, cur, nullptr, n, 1.f, 0.f, 0.f, G, c->d_status, gate);
+      ns_gemm_kernel<false><<<g64, 256, 0, s>>>(G, cur, cur, n, -0.5f, 1.5f, 0.f, nxt, c->d_status, gate);
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    Yt = cur;   // three steps: the result is in Y2
+    c->launches += 6;
+  }
   // 4. back-transformation: warps per CTA and reflectors per stage within 96 KB
   const size_t row = (size_t)n * sizeof(F);
   const int nw = (int)std::max<size_t>(1, std::min<size_t>(8, (48 * 1024) / row));
