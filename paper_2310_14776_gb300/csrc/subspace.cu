@@ -154,13 +154,18 @@ __global__ void __launch_bounds__(256) tri_inverse_kernel(const T* __restrict__ 
 }
 
 // C = op(A) op(B) (+ D), n x n, op = identity or conjugate transpose.  With `skip` set on the
-// device, C is a copy of `src` instead (the product is known to be that matrix).
+// device, C is a copy of `src` instead (the product is known to be that matrix).  `shape`
+// skips the k-slabs that structure makes zero and, for a Hermitian product, half the tiles:
+// SG_ALOW: op(A)[r][k] = 0 for k > r; SG_AUP: 0 for k < r; SG_BUP: op(B)[k][c] = 0 for k > c;
+// SG_HERM: C is Hermitian, only tiles on or below the diagonal are computed and each entry
+// below the diagonal is also stored, conjugated, above it.
+enum { SG_ALOW = 1, SG_AUP = 2, SG_BUP = 4, SG_HERM = 8 };
 template <class T>
 __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A, bool ha, const T* __restrict__ B,
                                                          bool hb, int n, T* __restrict__ C, const DeviceStatus* st,
                                                          const T* __restrict__ D = nullptr,
                                                          const int* skip = nullptr, const T* __restrict__ src = nullptr,
-                                                         const int* gate = nullptr) {
+                                                         const int* gate = nullptr, int shape = 0) {
   __shared__ T As[16][17];
   __shared__ T Bs[16][17];
   if (ld_volatile(&st->code) != 0 || gated(gate)) return;
@@ -170,8 +175,13 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A
     if (row < n && col < n) C[(long long)row * n + col] = src[(long long)row * n + col];
     return;
   }
+  if ((shape & SG_HERM) && blockIdx.y < blockIdx.x) return;
+  int kbeg = 0, kend = n;
+  if (shape & SG_ALOW) kend = min(kend, (int)blockIdx.y * 16 + 16);
+  if (shape & SG_AUP) kbeg = (int)blockIdx.y * 16;
+  if (shape & SG_BUP) kend = min(kend, (int)blockIdx.x * 16 + 16);
   T acc = zero<T>();
-  for (int k0 = 0; k0 < n; k0 += 16) {
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
     {
       const int r = blockIdx.y * 16 + ty, k = k0 + tx;   // element (r, k) of op(A)
       T v = zero<T>();
@@ -187,7 +197,15 @@ __global__ void __launch_bounds__(256) small_gemm_kernel(const T* __restrict__ A
     for (int k = 0; k < 16; ++k) fma_plain(acc, As[ty][k], Bs[k][tx]);
     __syncthreads();
   }
-  if (row < n && col < n) C[(long long)row * n + col] = D ? acc + D[(long long)row * n + col] : acc;
+  if (row >= n || col >= n) return;
+  if (shape & SG_HERM) {
+    if (row < col) return;
+    if (row == col) acc = from_real<T>(realx(acc));
+    C[(long long)row * n + col] = acc;
+    if (row != col) C[(long long)col * n + row] = conjx(acc);
+    return;
+  }
+  C[(long long)row * n + col] = D ? acc + D[(long long)row * n + col] : acc;
 }
 
 template <class T>
@@ -830,8 +848,9 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     if (rc != PAWFD_OK) return rc;
   }
   tri_inverse_kernel<T><<<n, 256, sizeof(T) * n, s>>>(Lm, n, Li, st, near);
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, false, Hs, false, n, T1, st, nullptr, nullptr, nullptr, near);
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Li, true, n, Am, st, nullptr, nullptr, nullptr, near);
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, false, Hs, false, n, T1, st, nullptr, nullptr, nullptr, near, SG_ALOW);
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(T1, false, Li, true, n, Am, st, nullptr, nullptr, nullptr, near,
+                                          SG_BUP | SG_HERM);
   hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, near);
   c->launches += 4;
   rc = check_cuda(c, cudaGetLastError(), "subspace launch");
@@ -850,8 +869,8 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     // one step from P: A P (Hs), S = P^H A P (Lm), B = P^H P (A2), E (Hs); then P + P E
     auto oa_step = [&](T* P, double ebound2, const int* gate) {
       small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, P, false, n, Hs, st, nullptr, nullptr, nullptr, gate);
-      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, Hs, false, n, Lm, st, nullptr, nullptr, nullptr, gate);
-      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, P, false, n, A2, st, nullptr, nullptr, nullptr, gate);
+      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, Hs, false, n, Lm, st, nullptr, nullptr, nullptr, gate, SG_HERM);
+      small_gemm_kernel<T><<<gg, 256, 0, s>>>(P, true, P, false, n, A2, st, nullptr, nullptr, nullptr, gate, SG_HERM);
       oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, part, lam, gate, st);
       oa_update_kernel<T><<<OA_G, 256, 0, s>>>(Lm, A2, n, lam, part, tol_z, ebound2, Hs, part2, gate, st);
     };
@@ -870,7 +889,7 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, flags + GATE_ZSTEP3, st);
     // A <- X^H A X for the sweeps over the coupled pairs
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Am, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, fam);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, fam);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, fam, SG_HERM);
     hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, fam);
     // the fallback: the sweeps on A from V = I
     identity_kernel<T><<<eb, 256, 0, s>>>(Vm, n, flags + GATE_ZFAIL);
@@ -887,16 +906,16 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
     const int* amg = flags + GATE_AM;
     identity_plus_kernel<T><<<eb, 256, 0, s>>>(Li, n, Vm, far, st);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, A2, st, nullptr, nullptr, nullptr, step2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, A2, st, nullptr, nullptr, nullptr, step2, SG_HERM);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Lm, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, step2);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, step2, SG_HERM);
     oa_stats_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, part, lam, step2, st);
     oa_update_kernel<T><<<OA_G, 256, 0, s>>>(A2, Am, n, lam, part, tol_z, 1e-14, Li, part2, step2, st);
     oa_decide2_kernel<<<1, 32, 0, s>>>(part2, c->d_flags, step2);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, false, Li, false, n, T1, st, Vm, nullptr, nullptr, step2);
     copy_kernel<T><<<eb, 256, 0, s>>>(T1, nn, Vm, step2, st);
     small_gemm_kernel<T><<<gg, 256, 0, s>>>(Hs, false, Vm, false, n, T1, st, nullptr, nullptr, nullptr, amg);
-    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, amg);
+    small_gemm_kernel<T><<<gg, 256, 0, s>>>(Vm, true, T1, false, n, Am, st, nullptr, nullptr, nullptr, amg, SG_HERM);
     hermitize_kernel<T><<<eb, 256, 0, s>>>(Am, n, st, amg);
     lambda_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(lam, n, Am, flags + GATE_LAMBDA, st);
     c->launches += 14;
@@ -909,7 +928,7 @@ int subspace_impl(pawfd_ctx* c, int n, T* H, T* S, double* eps, T* C) {
   if (rc != PAWFD_OK) return rc;
   sort_kernel<T><<<n, 128, 0, s>>>(Am, Vm, n, eps, T1, c->d_status);
   // C = L^-H U (far path) or U (near path: a copy)
-  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, true, T1, false, n, C, st, nullptr, near, T1);
+  small_gemm_kernel<T><<<gg, 256, 0, s>>>(Li, true, T1, false, n, C, st, nullptr, near, T1, nullptr, SG_AUP);
   phase_fix_kernel<T><<<n, 256, 0, s>>>(C, n, c->d_status);
   c->launches += 3;
   return check_cuda(c, cudaGetLastError(), "subspace launch");
