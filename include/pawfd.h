@@ -127,11 +127,14 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *                     digit slices; 0: FMA kernels on the CUDA cores (FP64 products for the FP64
  *                     dtypes; FP32 products, about 1e-7 relative, for the FP32 dtypes).
  *   "stencil_variant" 0 (default): fastest kernel that applies to the shape; 1: skip the
- *                     bulk-copy ring kernel; 2: always the general kernel.
- *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernel, 0 (default) automatic,
+ *                     bulk-copy ring kernels (FP32 real and FP32 complex); 2: always the
+ *                     general kernel.
+ *   "stencil_rows"    y rows per CTA of the bulk-copy ring kernels, 0 (default) automatic,
  *                     at most 64 (clamped further by the kernel's thread and memory limits).
- *   "stencil_yblock"  y rows per thread of the ring kernel: 0 (default) automatic, 1, 2 or 3.
- *   "stencil_ring"    ring stencil: planes in flight + in use, 0 (default 8), 8, 10 or 12.
+ *   "stencil_yblock"  y rows per thread of the ring kernels: 0 (default) automatic, 1, 2 or 3.
+ *   "stencil_ring"    ring kernels: planes in flight + in use, 0 (default: 8 for FP32 real, 6
+ *                     for FP32 complex), 6, 8, 10 or 12 (the complex kernel takes 6 or 8, the
+ *                     real one 8, 10 or 12; other values round to the nearest it takes).
  *   "stencil_zsplit"  general stencil kernel: the z range is split so that one launch has at
  *                     least this many CTAs per SM; 0 (default) means 4, at most 64.
  *   "tc_kblk"         tensor-core Gram: grid values per K block in units of 512 (0: the whole

@@ -31,6 +31,16 @@ def stencil_candidates(ctx) -> List[Dict[str, int]]:
             for per in (2, 4, 6):
                 cands.append({"stencil_variant": 0, "stencil_yblock": yb, "stencil_rows": yb * per})
         return cands
+    if (ctx.precision == "mixed" and ctx.complex and ctx.n[0] % 2 == 0 and ctx.n[0] >= 8 and ctx.n[1] >= 3
+            and ctx.n[2] >= 3):
+        # the complex bulk-copy ring kernel (its tilings are bitwise equal) or the general one
+        cands = [{"stencil_variant": 1}]
+        for depth in (6, 8):
+            for yb in (1, 2, 3):
+                for per in (2, 4):
+                    cands.append({"stencil_variant": 0, "stencil_ring": depth, "stencil_yblock": yb,
+                                  "stencil_rows": yb * per})
+        return cands
     return [{"stencil_zsplit": z} for z in (1, 2, 4, 8, 16)]
 
 

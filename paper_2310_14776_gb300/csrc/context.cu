@@ -482,7 +482,7 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->tc_kblk_chunks = value;
     return PAWFD_OK;
   }
-  if (n == "stencil_ring" && (value == 0 || value == 8 || value == 10 || value == 12)) {
+  if (n == "stencil_ring" && (value == 0 || value == 6 || value == 8 || value == 10 || value == 12)) {
     c->stencil_ring = value;
     return PAWFD_OK;
   }

@@ -155,6 +155,7 @@ int kinetic_local_impl(pawfd_ctx* c, const T* psi, int nb, T* out, T* cpy) {
 
 int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy);
 int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy);
+int launch_kinetic_local_ring_c(pawfd_ctx* c, const zf* psi, int nb, zf* out, zf* cpy);
 int launch_kinetic_local_fx(pawfd_ctx* c, const double* psi, int nb, double* out, double* cpy);
 
 // out = (-1/2 Lap + v) psi; with cpy != null the kernels also write psi to cpy (the first term
@@ -170,6 +171,9 @@ int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out, void*
     if (launch_kinetic_local_f32x4(c, (const float*)psi, nb, (float*)out, (float*)cpy) == PAWFD_OK)
       return PAWFD_OK;
   }
+  if (c->dtype == PAWFD_C64 && c->fast_stencil && c->stencil_variant != 1 &&
+      launch_kinetic_local_ring_c(c, (const zf*)psi, nb, (zf*)out, (zf*)cpy) == PAWFD_OK)
+    return PAWFD_OK;
   return dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
     return kinetic_local_impl<T>(c, (const T*)psi, nb, (T*)out, (T*)cpy);
