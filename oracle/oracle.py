@@ -352,12 +352,48 @@ def davidson_weights(system, eps: np.ndarray) -> np.ndarray:
     return (np.float32(-1.0) / den).astype(np.float64)
 
 
-def davidson_step(system, psi: np.ndarray, eps_in: np.ndarray) -> dict:
+KINETIC_SHIFT = 0.5   # Hartree: sigma of the kinetic preconditioner (a reading)
+
+
+def kinetic_symbol(system) -> np.ndarray:
+    """t(k + G) = -1/2 L_FD(k + G), [N3][N2][N1]: the eigenvalue of the order-6 FD kinetic
+    operator T on the Bloch wave e^{i(k+G).r} of the grid (G the grid's FFT wave vectors),
+    t = -1/2 sum_c (1/h_c^2) (c0 + 2 sum_m c_m cos(m q_c h_c)) with q = k + G."""
+    c = fd6_coefficients()
+    h = system.h
+    parts = []
+    for ax in range(3):
+        q = system.k[ax] + 2.0 * np.pi * np.fft.fftfreq(system.n[ax], d=h[ax])
+        parts.append(-0.5 * (c[0] + 2.0 * sum(c[m] * np.cos(m * q * h[ax]) for m in (1, 2, 3))) / (h[ax] * h[ax]))
+    return parts[2][:, None, None] + parts[1][None, :, None] + parts[0][None, None, :]
+
+
+def kinetic_precondition(system, R: np.ndarray, sigma: float = KINETIC_SHIFT) -> np.ndarray:
+    """The kinetic preconditioner of the block-Davidson step (a reading; the paper names the
+    Davidson eigensolver without its steps): the correction -(T + sigma)^-1 R_n of each residual,
+    with T the order-6 FD kinetic operator of the grid (Bloch boundary conditions) and sigma > 0.
+    T is diagonal on the Bloch waves, so for R(r) = e^{ik.r} u(r):
+    -(T + sigma)^-1 R = -e^{ik.r} IDFT[ DFT[u] / (t(k + G) + sigma) ]."""
+    R = np.asarray(R)
+    nb = R.shape[0]
+    shape = (system.n[2], system.n[1], system.n[0])
+    u = R.reshape((nb,) + shape).astype(np.complex128)
+    ph = bloch_phase(system)
+    u = u * np.conj(ph)[None]
+    d = kinetic_symbol(system) + sigma
+    out = -ph[None] * np.fft.ifftn(np.fft.fftn(u, axes=(1, 2, 3)) / d[None], axes=(1, 2, 3))
+    if not system.complex_wf:
+        out = out.real
+    return out.reshape(R.shape)
+
+
+def davidson_step(system, psi: np.ndarray, eps_in: np.ndarray, precond: str = "kinetic") -> dict:
     """One block-Davidson step in the order of its reading:
 
     1. H psi and S psi for the n input Ritz vectors psi (Ritz values eps_in);
     2. residuals R_n = H psi_n - eps_n S psi_n and their norms sqrt(dV sum_r |R_n|^2);
-    3. corrections w_n R_n with the Jacobi weights of ``davidson_weights``;
+    3. corrections: -(T + sigma)^-1 R_n (``kinetic_precondition``, precond="kinetic") or
+       w_n R_n with the Jacobi weights of ``davidson_weights`` (precond="jacobi");
     4. Rayleigh-Ritz on the 2n columns X = [psi, corrections]: Gram matrices dV X^H H X and
        dV X^H S X, the subspace diagonalization (2n Ritz pairs, ascending), and the n lowest
        Ritz vectors X C[:, :n].
@@ -369,7 +405,10 @@ def davidson_step(system, psi: np.ndarray, eps_in: np.ndarray) -> dict:
     eps_in = np.asarray(eps_in, np.float64)[:nb]
     R = Hpsi.reshape(nb, K) - eps_in[:, None] * Spsi.reshape(nb, K)
     rnorm = np.sqrt(system.dV * np.sum(np.abs(R) ** 2, axis=1))
-    corr = R * davidson_weights(system, eps_in)
+    if precond == "kinetic":
+        corr = kinetic_precondition(system, R)
+    else:
+        corr = R * davidson_weights(system, eps_in)
     X = np.concatenate([psi.reshape(nb, K), corr.astype(psi.dtype)]).reshape((2 * nb,) + psi.shape[1:])
     HX, _ = apply_H(system, X)
     SX, _ = apply_S(system, X)

@@ -578,22 +578,30 @@ def _dense_ritz(s, H, S, X, nb):
     return scipy.linalg.eigh(s.dV * Y.conj().T @ H @ Y, s.dV * Y.conj().T @ S @ Y, eigvals_only=True)
 
 
+@pytest.mark.parametrize("precond", ["kinetic", "jacobi"])
 @pytest.mark.parametrize("case", ["selfwrap", "bloch"])
-def test_davidson_step_against_dense_operators(case):
-    # the corrections are the weights times the dense residual, and the step's 2n Ritz values
-    # are those of the dense pencil projected on X = [psi, corrections]
+def test_davidson_step_against_dense_operators(case, precond):
+    # the corrections solve (T + sigma) corr = -R with the dense kinetic operator (kinetic
+    # preconditioner) or are the weights times the dense residual (Jacobi), and the step's 2n
+    # Ritz values are those of the dense pencil projected on X = [psi, corrections]
     s = small_system(**TINY[case])
     H, S = dense_operators(s)
     n, K = 4, s.npoints
     rr = O.rayleigh_ritz(s, rand_psi(s, n, 7))
     psi, eps = rr["psi_rot"], rr["eps"]
-    st = O.davidson_step(s, psi, eps)
+    st = O.davidson_step(s, psi, eps, precond=precond)
     Y = psi.reshape(n, K)
     R = (H @ Y.T).T - eps[:, None] * (S @ Y.T).T
-    w = O.davidson_weights(s, eps)
-    assert np.all(w < 0)
     corr = st["X"].reshape(2 * n, K)[n:]
-    assert np.allclose(corr, w * R, rtol=0, atol=1e-11 * np.max(np.abs(w * R)))
+    if precond == "jacobi":
+        w = O.davidson_weights(s, eps)
+        assert np.all(w < 0)
+        assert np.allclose(corr, w * R, rtol=0, atol=1e-11 * np.max(np.abs(w * R)))
+    else:
+        T, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=s.complex_wf,
+                                           vloc=np.zeros_like(s.vloc)))
+        lhs = (T @ corr.T).T + O.KINETIC_SHIFT * corr
+        assert np.allclose(lhs, -R, rtol=0, atol=1e-11 * np.max(np.abs(R)))
     assert np.allclose(st["rnorm"], np.sqrt(s.dV * np.sum(np.abs(R) ** 2, axis=1)), rtol=1e-10, atol=0)
     ritz = _dense_ritz(s, H, S, st["X"], 2 * n)
     assert np.allclose(st["eps"], ritz, rtol=0, atol=1e-10 * max(1.0, np.max(np.abs(ritz))))
@@ -625,6 +633,27 @@ def test_davidson_iteration_converges_from_above(case):
         psi, eps = st["psi_out"], new
     assert np.sum(eps - exact[:n]) < err0 / 50
     assert st["rnorm"].max() < r0 / 15
+
+
+@pytest.mark.parametrize("complex_wf", [False, True])
+def test_kinetic_symbol_and_preconditioner_on_bloch_waves(complex_wf):
+    # T (the oracle's real-space stencil, Bloch boundary conditions) acting on a grid Bloch wave
+    # e^{i(k+G).r} multiplies it by t(k + G); the preconditioner divides it by -(t + sigma)
+    k = (0.37, -0.21, 0.55) if complex_wf else (0.0, 0.0, 0.0)
+    s = free_system((10, 9, 8), (5.0, 4.4, 3.9), k=k, complex_wf=complex_wf, vloc=None)
+    t = O.kinetic_symbol(s)
+    z, y, x = np.meshgrid(*[np.arange(s.n[c]) * s.h[c] for c in (2, 1, 0)], indexing="ij")
+    for j in [(0, 0, 0), (1, 0, 0), (3, -2, 1), (-4, 4, 3), (5, 4, -4)]:
+        q = [s.k[c] + 2 * math.pi * j[c] / s.cell[c] for c in range(3)]
+        wave = np.exp(1j * (q[0] * x + q[1] * y + q[2] * z))
+        if not complex_wf:
+            wave = wave.real
+        tj = t[j[2] % s.n[2], j[1] % s.n[1], j[0] % s.n[0]]
+        Tw = O.kinetic_local(s, wave[None])[0]
+        assert np.allclose(Tw, tj * wave, rtol=0, atol=1e-10 * max(1.0, tj))
+        P = O.kinetic_precondition(s, wave[None])[0]
+        assert np.allclose(P, -wave / (tj + O.KINETIC_SHIFT), rtol=0, atol=1e-13)
+    assert np.all(t >= -1e-12)
 
 
 def test_davidson_weights_from_the_dense_diagonal():
