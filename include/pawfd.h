@@ -158,6 +158,10 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *   "jacobi_cluster"  0 (default): the Cholesky factorization and the Jacobi eigensolver run as
  *                     cooperative grids with a bounded software grid barrier; 1: on one
  *                     thread-block cluster (hardware cluster barrier) when their work fits 16 CTAs.
+ *   "davidson_precond"  1 (default): pawfd_davidson_step forms its corrections with the kinetic
+ *                     preconditioner of pawfd_kinetic_precond when every grid size factors into
+ *                     2, 3 and 5 (the Jacobi one otherwise); 0: always the Jacobi preconditioner
+ *                     of pawfd_residual_precond.
  *   "tridiag_dsm"     1 (default): the FP32 tridiagonal reduction of the subspace solve's far
  *                     path keeps the matrix in the distributed shared memory of one 16-CTA
  *                     cluster when it fits (n <= 512 complex, n <= 724 real); 0: in global
@@ -254,12 +258,30 @@ int pawfd_rotate_n(pawfd_ctx* ctx, const void* psi, int nb, const void* C, int n
 int pawfd_residual_precond(pawfd_ctx* ctx, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
                            double* rnorm);
 
+/* The kinetic preconditioner of the Davidson step (a reading: the paper names the Davidson
+ * eigensolver without its preconditioner): out_n = -(T + sigma)^-1 R_n for every band, T the
+ * order-6 FD kinetic operator of the grid with the Bloch condition, sigma = 0.5 Ha.  T is
+ * diagonal on the grid's Bloch waves (symbol t(k+G) = -1/2 sum_c (w0 + 2 sum_m w_m cos(m q_c
+ * h_c)) / h_c^2, q = k + G), so the solve is a forward FFT, a division and an inverse FFT on the
+ * library's FFT kernels, in FP32 for every dtype (a search direction needs no more): two real
+ * bands share one complex transform.
+ *   R, out: [nb][K] band arrays of the context's dtype (out may be R); work: device scratch of
+ *   8 K bytes per transform (ceil(nb / 2) transforms for real dtypes, nb for complex ones), not
+ *   aliasing R or out.  The FFT tables are allocated by the first call (make it before any
+ *   stream capture).  Returns PAWFD_EINVAL for nb outside 1..max_bands, null or aliased work,
+ *   or a grid size with a prime factor other than 2, 3 and 5; PAWFD_ENOMEM if the tables cannot
+ *   be allocated. */
+int pawfd_kinetic_precond(pawfd_ctx* ctx, const void* R, int nb, void* out, void* work);
+
 /* One block-Davidson step (the reading of the iterative eigensolver named in the Kohn-Sham
  * and parallelization sections; needs max_bands >= 2 nb):
  *   1. HX[0 .. nb) = H psi, SX = S psi for psi = X[0 .. nb) (Ritz vectors with Ritz values
  *      eps_in, e.g. from pawfd_rr_step or a previous step);
- *   2. X[nb .. 2nb) = the preconditioned corrections of pawfd_residual_precond, rnorm their
- *      residual norms;
+ *   2. X[nb .. 2nb) = the preconditioned corrections, rnorm the residual norms: the kinetic
+ *      preconditioner of pawfd_kinetic_precond (its work in HX[nb .. 2nb), or for FP32 real
+ *      bands and odd nb a context array allocated on first need) or, with option
+ *      "davidson_precond" 0 or a grid size with another prime factor, the Jacobi corrections of
+ *      pawfd_residual_precond;
  *   3. HX[nb .. 2nb) = H of the corrections; P = the projections of all 2 nb columns of X;
  *   4. Hnm, Snm = the Hermitian Gram matrices of X (as pawfd_gram_hs), scaled to a unit S
  *      diagonal (which leaves the Ritz values unchanged and keeps the factorization well

@@ -71,6 +71,7 @@ SIGNATURES = {
     "pawfd_pw_to_grid": ([VP, VP, I, VP], I),
     "pawfd_pw_from_grid": ([VP, VP, I, VP, VP], I),
     "pawfd_poisson_fft": ([VP, VP, VP, VP], I),
+    "pawfd_kinetic_precond": ([VP, VP, I, VP, VP], I),
 }
 
 _lock = threading.Lock()

@@ -279,6 +279,20 @@ class Context:
                    float(tol), int(maxiter), ctypes.c_void_p(work.data_ptr()), ctypes.byref(it), ctypes.byref(res))
         return v, it.value, res.value
 
+    def kinetic_precond(self, R, out=None, work=None):
+        """-(T + sigma)^-1 R for every band of R (pawfd_kinetic_precond; FP32 transforms,
+        sigma = 0.5 Ha).  ``out`` may be R."""
+        nb = self._bands(R, "R")
+        out = self.empty_bands(nb) if out is None else out
+        self._out_bands(out, nb, "out")
+        nt = nb if self.complex else (nb + 1) // 2
+        work = torch.empty(nt * self.K, dtype=torch.complex64, device=self.device) if work is None else work
+        if work.numel() * work.element_size() < 8 * self.K * nt or not work.is_contiguous():
+            raise ValueError("work must be a contiguous device array of at least 8 K bytes per transform")
+        self._call(self.lib.pawfd_kinetic_precond, ctypes.c_void_p(R.data_ptr()), nb, ctypes.c_void_p(out.data_ptr()),
+                   ctypes.c_void_p(work.data_ptr()))
+        return out
+
     def poisson_fft(self, rho, v=None, work=None):
         """The zero-mean Hartree potential of rho by the direct Fourier route
         (pawfd_poisson_fft); this context must be the free operator of its grid (see

@@ -443,6 +443,10 @@ extern "C" int pawfd_set_option(pawfd_ctx* c, const char* name, int value) {
     c->jacobi_cluster = value == 1;
     return PAWFD_OK;
   }
+  if (n == "davidson_precond" && (value == 0 || value == 1)) {
+    c->davidson_precond = value;
+    return PAWFD_OK;
+  }
   if (n == "tridiag_dsm" && (value == 0 || value == 1)) {
     c->tridiag_dsm = value == 1;
     return PAWFD_OK;

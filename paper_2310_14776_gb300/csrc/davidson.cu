@@ -6,9 +6,12 @@
 //   given n Ritz vectors psi (columns of X[0 .. n)) with Ritz values eps_in,
 //   1. H psi and S psi (Eq. (dh) and the overlap operator of the PAW section);
 //   2. residuals R_n = H psi_n - eps_n S psi_n and their norms sqrt(dV sum_r |R_n(r)|^2);
-//   3. preconditioned corrections X[n + m] = -R_m / max(d(r) - eps_m, d0 / 10), with d(r) =
-//      v(r) + d0 the diagonal of the kinetic + local operator (d0 = -1/2 c0 sum_c 1/h_c^2, the
-//      stencil's centre weight): a Jacobi preconditioner, floored so that it stays positive;
+//   3. preconditioned corrections X[n + m]: by default (option "davidson_precond" 1, grids whose
+//      sizes factor into 2, 3 and 5) the kinetic preconditioner -(T + sigma)^-1 R_m, T the FD
+//      kinetic operator, sigma = 0.5 Ha, applied in Fourier space on the library's FFT kernels
+//      (pw.cu); otherwise the Jacobi one, -R_m / max(d(r) - eps_m, d0 / 10) with d(r) = v(r) + d0
+//      the diagonal of the kinetic + local operator (d0 = -1/2 c0 sum_c 1/h_c^2, the stencil's
+//      centre weight), floored so that it stays positive;
 //   4. H of the corrections, the projections of all 2n columns, the Hermitian Gram matrices
 //      of the 2n-dimensional subspace (H_nm and S_nm as pawfd_gram_hs), the subspace
 //      diagonalization (2n Ritz pairs, ascending; the pencil is scaled to a unit S diagonal
@@ -35,13 +38,15 @@ __device__ double rblock_sum(double v, double* s_red) {
 }
 
 // One band per blockIdx.y, RG blocks of grid points per band.  R = H psi - eps S psi in the
-// band's arithmetic, the correction -R / max(d - eps, d0 / 10) written to pr, and each block's
-// sum of |R|^2 (FP64) to part[band][blockIdx.x].
+// band's arithmetic, the Jacobi correction -R / max(d - eps, d0 / 10) (or R itself, for the
+// kinetic preconditioner that follows) written to pr, and each block's sum of |R|^2 (FP64) to
+// part[band][blockIdx.x].
 template <class T>
 __global__ void __launch_bounds__(RB) residual_precond_kernel(const T* __restrict__ hpsi, const T* __restrict__ spsi,
                                                               long long K, const double* __restrict__ eps,
                                                               const real_t<T>* __restrict__ dshift, double d0,
-                                                              T* __restrict__ pr, double* __restrict__ part) {
+                                                              T* __restrict__ pr, double* __restrict__ part,
+                                                              int jacobi) {
   using R = real_t<T>;
   __shared__ double s_red[RB / 32];
   const int n = blockIdx.y;
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(RB) residual_precond_kernel(const T* __restric
     // search direction; the subspace step is exact for whatever the corrections hold)
     const float d = (float)dshift[r] - ef;
     const float w = -1.0f / (d > floor_d ? d : floor_d);
-    pr[off + r] = res * (R)w;
+    pr[off + r] = jacobi ? res * (R)w : res;
   }
   const double s = rblock_sum(acc, s_red);
   if (threadIdx.x == 0) part[(long long)n * gridDim.x + blockIdx.x] = s;
@@ -112,7 +117,7 @@ int check_bands(pawfd_ctx* c, int nb) {
 namespace pawfd {
 
 int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
-                            double* rnorm) {
+                            double* rnorm, bool jacobi) {
   const double d0 = -0.5 * FD6_W0 * (1.0 / (c->h[0] * c->h[0]) + 1.0 / (c->h[1] * c->h[1]) +
                                      1.0 / (c->h[2] * c->h[2]));
   // partial sums: RG doubles per band in the subspace workspace (7 max_bands^2 matrices of at
@@ -123,7 +128,8 @@ int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, in
   int rc = dispatch_band(c, [&](auto tag) {
     using T = decltype(tag);
     residual_precond_kernel<T><<<grid, RB, 0, c->stream>>>((const T*)hpsi, (const T*)spsi, (long long)c->K, eps,
-                                                           (const real_t<T>*)c->d_vshift, d0, (T*)pr, part);
+                                                           (const real_t<T>*)c->d_vshift, d0, (T*)pr, part,
+                                                           jacobi ? 1 : 0);
     return 0;
   });
   if (rc != PAWFD_OK) return rc;
@@ -140,7 +146,7 @@ extern "C" int pawfd_residual_precond(pawfd_ctx* c, const void* hpsi, const void
   if (rc != PAWFD_OK) return rc;
   if (!hpsi || !spsi || !eps || !pr || !rnorm) return fail(c, PAWFD_EINVAL, "null array");
   if (pr == hpsi || pr == spsi) return fail(c, PAWFD_EINVAL, "pr may not alias hpsi or spsi");
-  return launch_residual_precond(c, hpsi, spsi, nb, eps, pr, rnorm);
+  return launch_residual_precond(c, hpsi, spsi, nb, eps, pr, rnorm, true);
 }
 
 extern "C" int pawfd_rotate_n(pawfd_ctx* c, const void* psi, int nb, const void* C, int nout, void* psi_out) {
@@ -165,8 +171,11 @@ extern "C" int pawfd_davidson_step(pawfd_ctx* c, void* X, int nb, const double* 
   char* HX1 = (char*)HX + band_bytes * nb;
   // 1. H psi and S psi
   int rc = launch_apply_hs(c, X, nb, HX, SX, c->d_P);
-  // 2., 3. residuals, their norms, the preconditioned corrections
-  if (rc == PAWFD_OK) rc = launch_residual_precond(c, HX, SX, nb, eps_in, X1, rnorm);
+  // 2., 3. residuals, their norms, the preconditioned corrections (the kinetic preconditioner
+  //    works through HX[nb .. 2nb), free until H of the corrections is formed)
+  const bool kinetic = c->davidson_precond == 1 && kinetic_precond_available(c);
+  if (rc == PAWFD_OK) rc = launch_residual_precond(c, HX, SX, nb, eps_in, X1, rnorm, !kinetic);
+  if (rc == PAWFD_OK && kinetic) rc = launch_kinetic_precond(c, X1, nb, X1, HX1, band_bytes * nb);
   // 4. H of the corrections (S of them enters the Gram matrix through the projections)
   if (rc == PAWFD_OK) rc = launch_kinetic_local(c, X1, nb, HX1);
   if (rc == PAWFD_OK) rc = launch_project(c, X1, nb, c->d_P);

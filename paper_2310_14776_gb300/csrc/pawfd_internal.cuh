@@ -200,6 +200,7 @@ struct PwPlan {
   void* phase = nullptr;          // e^{i k.r} at the grid points [K]
   void* kin = nullptr;            // |k+G|^2 / 2 [K], real of the band precision
   void* pois = nullptr;           // real FP64 contexts: -4 pi / (K L(G)) of the Poisson solve [K]
+  void* tab = nullptr;            // kinetic preconditioner (FP32 plan): -1 / (K (t(k+G) + sigma)) [K]
 };
 }  // namespace pawfd
 
@@ -249,6 +250,10 @@ struct pawfd_ctx {
   bool nonlocal_df = true;                    // real FP64 projector kernels in double-float arithmetic
   pawfd::TcScratch tc;
   pawfd::PwPlan pw;
+  pawfd::PwPlan pc;                           // FP32 FFT plan of the Davidson kinetic preconditioner
+  void* d_pc_work = nullptr;                  // its work array when the caller's is too small (lazy)
+  size_t pc_work_bytes = 0;
+  int davidson_precond = 1;                   // 1: kinetic (grids of 2, 3, 5 factors), 0: Jacobi
   std::string err;
 };
 
@@ -294,13 +299,17 @@ int ensure_aux_stream(pawfd_ctx* c);
 int setup_tc(pawfd_ctx* c);
 void free_tc(pawfd_ctx* c);
 void free_pw(pawfd_ctx* c);
+size_t kinetic_precond_work_bytes(const pawfd_ctx* c, int nb);
+int launch_kinetic_precond(pawfd_ctx* c, const void* R, int nb, void* out, void* work, size_t work_bytes);
 int launch_rotate(pawfd_ctx* c, const void* psi, int nb, const void* C, void* out, int nout = -1);
 // bracket one timed kernel launch on the context's stream (no-ops unless timing is on)
 void ktimer_begin(pawfd_ctx* c);
 void ktimer_end(pawfd_ctx* c);
 // residuals H psi - eps S psi, their norms and the preconditioned corrections (davidson.cu)
 int launch_residual_precond(pawfd_ctx* c, const void* hpsi, const void* spsi, int nb, const double* eps, void* pr,
-                            double* rnorm);
+                            double* rnorm, bool jacobi = true);
+// the kinetic preconditioner applies: grid sizes with no prime factor other than 2, 3 and 5
+bool kinetic_precond_available(const pawfd_ctx* c);
 int launch_subspace_diag(pawfd_ctx* c, int nb, void* Hnm, void* Snm, double* eps, void* C);
 // FP32 eigendecomposition of a Hermitian n x n FP64 matrix A (full storage): Z (FP64 storage)
 // the eigenvectors, ascending eigenvalues; nothing happens when *gate != 0 (tridiag.cu)

@@ -49,13 +49,20 @@ struct FftArgs {
   const cplx<R>* in;
   cplx<R>* out;
   // prologue: 1 = multiply every input value by conj(phase[r]); 2 = the input is the real
-  // array rin (imaginary part 0)
+  // array rin (imaginary part 0); 3 = the input is band array xin of the context's dtype
+  // (xdouble: FP64, else FP32): real (xreal) bands 2 p and 2 p + 1 (0 past xnb) as the real
+  // and imaginary parts of batch p, complex band p times conj(phase[r])
   int pre;
+  const void* xin;
+  void* xout;
+  int xdouble, xreal, xnb;
   const cplx<R>* phase;
   const R* rin;
   // epilogue: 0 = store; 1 = store y phase[r] (psi), and v[r] psi into out2 (0 if v is null);
   // 2 = store y scale, plus kin[r] Cin (add_kin) or Cin (otherwise) when Cin is set, where
-  // kin[r] <= ecut (or ecut <= 0), else 0; 3 = store y tab[r]; 4 = store Re(y) into rout
+  // kin[r] <= ecut (or ecut <= 0), else 0; 3 = store y tab[r]; 4 = store Re(y) into rout;
+  // 5 = the reverse of prologue 3 into xout: Re(y) to band 2 p and Im(y) to band 2 p + 1 (real),
+  // or y phase[r] to band p (complex)
   int post;
   const R* tab;
   R* rout;
@@ -125,6 +132,29 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     if (element(a, l, i, g, r)) {
       if (a.pre == 2) {
         v = cplx<R>{a.rin[g], R(0)};
+      } else if (a.pre == 3) {
+        const long long p = g / a.K;
+        if (a.xreal) {
+          const long long ga = 2 * p * a.K + r, gb = ga + a.K;
+          const bool hb = 2 * p + 1 < a.xnb;
+          if (a.xdouble) {
+            const double* X = (const double*)a.xin;
+            v = cplx<R>{(R)X[ga], hb ? (R)X[gb] : R(0)};
+          } else {
+            const float* X = (const float*)a.xin;
+            v = cplx<R>{(R)X[ga], hb ? (R)X[gb] : R(0)};
+          }
+        } else {
+          if (a.xdouble) {
+            const zd z = ((const zd*)a.xin)[g];
+            v = cplx<R>{(R)z.re, (R)z.im};
+          } else {
+            const zf z = ((const zf*)a.xin)[g];
+            v = cplx<R>{(R)z.re, (R)z.im};
+          }
+          const cplx<R> ph = a.phase[r];
+          v = v * cplx<R>{ph.re, -ph.im};
+        }
       } else {
         v = a.in[g];
         if (a.pre == 1) {
@@ -197,6 +227,25 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
       a.out[g] = y * a.tab[r];
     } else if (a.post == 4) {
       a.rout[g] = y.re;
+    } else if (a.post == 5) {
+      const long long p = g / a.K;
+      if (a.xreal) {
+        const long long ga = 2 * p * a.K + r, gb = ga + a.K;
+        const bool hb = 2 * p + 1 < a.xnb;
+        if (a.xdouble) {
+          double* X = (double*)a.xout;
+          X[ga] = (double)y.re;
+          if (hb) X[gb] = (double)y.im;
+        } else {
+          float* X = (float*)a.xout;
+          X[ga] = (float)y.re;
+          if (hb) X[gb] = (float)y.im;
+        }
+      } else {
+        const cplx<R> z = y * a.phase[r];
+        if (a.xdouble) ((zd*)a.xout)[g] = zd{(double)z.re, (double)z.im};
+        else ((zf*)a.xout)[g] = zf{(float)z.re, (float)z.im};
+      }
     } else if (a.post == 1) {
       const cplx<R> psi = y * a.phase[r];
       a.out[g] = psi;
@@ -319,8 +368,8 @@ int ensure_pw(pawfd_ctx* c, bool need_complex = true) {
 }
 
 template <class R>
-int fft_pass(pawfd_ctx* c, int axis, const cplx<R>* in, cplx<R>* out, int nb, bool inverse, FftArgs<R> a) {
-  const PwPlan& p = c->pw;
+int fft_pass_plan(pawfd_ctx* c, const PwPlan& p, int axis, const cplx<R>* in, cplx<R>* out, int nb, bool inverse,
+                  FftArgs<R> a) {
   a.N = c->n[axis];
   a.nf = p.nf[axis];
   for (int s = 0; s < p.nf[axis]; ++s) a.fac[s] = p.fac[axis][s];
@@ -363,6 +412,11 @@ int fft_pass(pawfd_ctx* c, int axis, const cplx<R>* in, cplx<R>* out, int nb, bo
   fft_pass_kernel<R><<<(unsigned)grid, FFT_NT, smem, c->stream>>>(a);
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "fft launch");
+}
+
+template <class R>
+int fft_pass(pawfd_ctx* c, int axis, const cplx<R>* in, cplx<R>* out, int nb, bool inverse, FftArgs<R> a) {
+  return fft_pass_plan<R>(c, c->pw, axis, in, out, nb, inverse, a);
 }
 
 // psi(r) = e^{ik.r} sum_G C_G e^{iG.r}: the inverse transform (unnormalised), the phase in the
@@ -436,6 +490,111 @@ int poisson_fft_impl(pawfd_ctx* c, const double* rho, double* v, zd* work) {
   return rc;
 }
 
+// ---- the kinetic preconditioner of the Davidson step ----
+// -(T + sigma)^-1 R for every band R: T is diagonal on the grid's Bloch waves, with the FD
+// kinetic symbol t(k + G) = -1/2 sum_c (w0 + 2 sum_m w_m cos(m q_c h_c)) / h_c^2, q = k + G.
+// A search direction needs no FP64, so the transforms are FP32 whatever the context's dtype:
+// two real bands form one complex transform (the multiplier is real and even in G, so the real
+// and imaginary parts stay apart), complex bands carry e^{-ik.r} in and e^{ik.r} out.
+constexpr double KINETIC_SHIFT = 0.5;   // sigma, Hartree
+
+int setup_pc_impl(pawfd_ctx* c) {
+  PwPlan& p = c->pc;
+  int rc = PAWFD_OK;
+  for (int ax = 0; ax < 3; ++ax) {
+    if (!factorize(c->n[ax], p.fac[ax], &p.nf[ax]))
+      return fail(c, PAWFD_EINVAL, "kinetic preconditioner: grid sizes must have no prime factor other than 2, 3 and 5");
+    const int N = c->n[ax];
+    std::vector<zf> tw(N);
+    for (int j = 0; j < N; ++j) {
+      const double t = 2.0 * M_PI * (double)j / (double)N;
+      tw[j] = zf{(float)std::cos(t), (float)-std::sin(t)};
+    }
+    rc = check_cuda(c, cudaMalloc(&p.tw[ax], sizeof(zf) * N), "cudaMalloc preconditioner twiddles");
+    if (rc == PAWFD_OK)
+      rc = check_cuda(c, cudaMemcpy(p.tw[ax], tw.data(), sizeof(zf) * N, cudaMemcpyHostToDevice), "memcpy");
+    if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  }
+  const int n1 = c->n[0], n2 = c->n[1], n3 = c->n[2];
+  const double w[4] = {FD6_W0, FD6_W1, FD6_W2, FD6_W3};
+  auto freq = [](int i, int n) { return (double)(i < (n + 1) / 2 ? i : i - n); };
+  auto sym = [&](std::vector<double>& out, int n, int ax) {
+    out.resize(n);
+    const double h = c->h[ax];
+    for (int i = 0; i < n; ++i) {
+      const double q = c->k[ax] + 2.0 * M_PI * freq(i, n) / c->cell[ax];
+      double acc = w[0];
+      for (int m = 1; m <= 3; ++m) acc += 2.0 * w[m] * std::cos(m * q * h);
+      out[i] = -0.5 * acc / (h * h);
+    }
+  };
+  std::vector<double> tx, ty, tz;
+  sym(tx, n1, 0);
+  sym(ty, n2, 1);
+  sym(tz, n3, 2);
+  std::vector<float> tab(c->K);
+  std::vector<zf> ph(c->K);
+  for (int i3 = 0; i3 < n3; ++i3)
+    for (int i2 = 0; i2 < n2; ++i2)
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const size_t r = ((size_t)i3 * n2 + i2) * n1 + i1;
+        tab[r] = (float)(-1.0 / ((double)c->K * (tx[i1] + ty[i2] + tz[i3] + KINETIC_SHIFT)));
+        const double kr = c->k[0] * i1 * c->h[0] + c->k[1] * i2 * c->h[1] + c->k[2] * i3 * c->h[2];
+        ph[r] = zf{(float)std::cos(kr), (float)std::sin(kr)};
+      }
+  rc = check_cuda(c, cudaMalloc(&p.tab, sizeof(float) * c->K), "cudaMalloc preconditioner table");
+  if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&p.phase, sizeof(zf) * c->K), "cudaMalloc preconditioner phase");
+  if (rc == PAWFD_OK)
+    rc = check_cuda(c, cudaMemcpy(p.tab, tab.data(), sizeof(float) * c->K, cudaMemcpyHostToDevice), "memcpy");
+  if (rc == PAWFD_OK)
+    rc = check_cuda(c, cudaMemcpy(p.phase, ph.data(), sizeof(zf) * c->K, cudaMemcpyHostToDevice), "memcpy");
+  if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
+  p.ready = true;
+  return PAWFD_OK;
+}
+
+void free_plan(PwPlan& p) {
+  void* ptrs[] = {p.tw[0], p.tw[1], p.tw[2], p.phase, p.kin, p.pois, p.tab};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  p = PwPlan();
+}
+
+int ensure_pc(pawfd_ctx* c) {
+  if (c->pc.ready) return PAWFD_OK;
+  int rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
+  if (rc != PAWFD_OK) return rc;
+  rc = setup_pc_impl(c);
+  if (rc != PAWFD_OK) free_plan(c->pc);
+  return rc;
+}
+
+int kinetic_precond_impl(pawfd_ctx* c, const void* R, int nb, void* out, zf* work) {
+  const int nbat = is_complex(c) ? nb : (nb + 1) / 2;
+  FftArgs<float> a = {};
+  a.xdouble = is_fp32(c) ? 0 : 1;
+  a.xreal = is_complex(c) ? 0 : 1;
+  a.xnb = nb;
+  a.phase = (const zf*)c->pc.phase;
+  a.pre = 3;
+  a.xin = R;
+  int rc = fft_pass_plan<float>(c, c->pc, 0, nullptr, work, nbat, false, a);
+  a.pre = 0;
+  a.xin = nullptr;
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 1, work, work, nbat, false, a);
+  a.post = 3;
+  a.tab = (const float*)c->pc.tab;
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 2, work, work, nbat, false, a);
+  a.post = 0;
+  a.tab = nullptr;
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 0, work, work, nbat, true, a);
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 1, work, work, nbat, true, a);
+  a.post = 5;
+  a.xout = out;
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 2, work, work, nbat, true, a);
+  return rc;
+}
+
 int check_pw_call(pawfd_ctx* c, const void* a, const void* b, int nb) {
   if (!c) return PAWFD_EINVAL;
   if (!a || !b) return fail(c, PAWFD_EINVAL, "null array");
@@ -446,11 +605,46 @@ int check_pw_call(pawfd_ctx* c, const void* a, const void* b, int nb) {
 }  // namespace
 
 void free_pw(pawfd_ctx* c) {
-  PwPlan& p = c->pw;
-  void* ptrs[] = {p.tw[0], p.tw[1], p.tw[2], p.phase, p.kin, p.pois};
-  for (void* q : ptrs)
-    if (q) cudaFree(q);
-  p = PwPlan();
+  free_plan(c->pw);
+  free_plan(c->pc);
+  if (c->d_pc_work) cudaFree(c->d_pc_work);
+  c->d_pc_work = nullptr;
+  c->pc_work_bytes = 0;
+}
+
+bool kinetic_precond_available(const pawfd_ctx* c) {
+  int fac[MAX_FAC], nf;
+  for (int ax = 0; ax < 3; ++ax)
+    if (!factorize(c->n[ax], fac, &nf)) return false;
+  return true;
+}
+
+size_t kinetic_precond_work_bytes(const pawfd_ctx* c, int nb) {
+  return sizeof(zf) * (size_t)c->K * (size_t)(is_complex(c) ? nb : (nb + 1) / 2);
+}
+
+// -(T + sigma)^-1 of nb band arrays R into out (may be R), through work (at least
+// kinetic_precond_work_bytes, or null: the context's own, allocated on first need)
+int launch_kinetic_precond(pawfd_ctx* c, const void* R, int nb, void* out, void* work, size_t work_bytes) {
+  int rc = ensure_pc(c);
+  if (rc != PAWFD_OK) return rc;
+  const size_t need = kinetic_precond_work_bytes(c, nb);
+  if (!work || work_bytes < need) {
+    if (c->pc_work_bytes < need) {
+      rc = check_cuda(c, cudaStreamSynchronize(c->stream), "stream sync");
+      if (rc != PAWFD_OK) return rc;
+      if (c->d_pc_work) cudaFree(c->d_pc_work);
+      c->d_pc_work = nullptr;
+      c->pc_work_bytes = 0;
+      if (cudaMalloc(&c->d_pc_work, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PAWFD_ENOMEM, "kinetic preconditioner work array");
+      }
+      c->pc_work_bytes = need;
+    }
+    work = c->d_pc_work;
+  }
+  return kinetic_precond_impl(c, R, nb, out, (zf*)work);
 }
 
 }  // namespace pawfd
@@ -483,6 +677,14 @@ extern "C" int pawfd_poisson_fft(pawfd_ctx* c, const double* rho, double* v, voi
   const int rc = ensure_pw(c, false);
   if (rc != PAWFD_OK) return rc;
   return poisson_fft_impl(c, rho, v, (zd*)work);
+}
+
+extern "C" int pawfd_kinetic_precond(pawfd_ctx* c, const void* R, int nb, void* out, void* work) {
+  if (!c) return PAWFD_EINVAL;
+  if (nb < 1 || nb > c->max_bands) return fail(c, PAWFD_EINVAL, "nb must be in 1..max_bands");
+  if (!R || !out || !work) return fail(c, PAWFD_EINVAL, "null array");
+  if (work == R || work == out) return fail(c, PAWFD_EINVAL, "work may not alias R or out");
+  return launch_kinetic_precond(c, R, nb, out, work, kinetic_precond_work_bytes(c, nb));
 }
 
 extern "C" int pawfd_pw_to_grid(pawfd_ctx* c, const void* C, int nb, void* psi) {

@@ -34,28 +34,53 @@ def gpu_step(ctx, psi, eps, nb, dev):
     return w
 
 
+U32 = 2.0 ** -24
+
+
+def fft32_bound(s):
+    """Per-band relative bound of an FP32 Fourier-space solve (pawfd_kinetic_precond): the
+    input rounded to FP32, three passes each way (a few roundings per radix stage), the table
+    entry: 8 u log2 K."""
+    return 8 * U32 * np.log2(s.npoints)
+
+
+@pytest.mark.parametrize("precond", ["kinetic", "jacobi"])
 @pytest.mark.parametrize("cplx", [False, True])
-def test_davidson_step_matches_oracle(dev, cplx):
+def test_davidson_step_matches_oracle(dev, cplx, precond):
     from paper_2310_14776_gb300 import api
     k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
-    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=611, k=k, complex_wf=cplx)
+    s = synth.make_system((30, 24, 20), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=611, k=k, complex_wf=cplx)
     nb = 24
     rr = O.rayleigh_ritz(s, synth.make_psi(s, nb, 612))
-    ref = O.davidson_step(s, rr["psi_rot"], rr["eps"])
+    ref = O.davidson_step(s, rr["psi_rot"], rr["eps"], precond=precond)
     ctx = api.Context(s, max_bands=2 * nb, device=dev)
+    ctx.set_option("davidson_precond", 1 if precond == "kinetic" else 0)
     w = gpu_step(ctx, rr["psi_rot"], rr["eps"], nb, dev)
     K = s.npoints
     assert np.allclose(w["rnorm"].cpu().numpy(), ref["rnorm"], rtol=1e-11, atol=0)
     corr = w["X"][nb:].cpu().numpy().reshape(nb, K)
     rcorr = ref["X"].reshape(2 * nb, K)[nb:]
-    assert np.max(np.abs(corr - rcorr)) <= 1e-12 * np.max(np.abs(rcorr))
     eps = w["eps"].cpu().numpy()
-    assert np.max(np.abs(eps - ref["eps"])) <= 1e-10, np.max(np.abs(eps - ref["eps"]))
+    if precond == "jacobi":
+        assert np.max(np.abs(corr - rcorr)) <= 1e-12 * np.max(np.abs(rcorr))
+        assert np.max(np.abs(eps - ref["eps"])) <= 1e-10, np.max(np.abs(eps - ref["eps"]))
+    else:
+        # FP32 transforms: the corrections to the FP32 bound; the Ritz values exactly those of
+        # the GPU's own subspace X (the oracle's Rayleigh-Ritz on it), and within the effect of
+        # the FP32 corrections of the oracle's FP64 step
+        err = np.linalg.norm(corr - rcorr, axis=1) / np.linalg.norm(rcorr, axis=1)
+        assert err.max() <= fft32_bound(s), err.max()
+        X = w["X"].cpu().numpy()
+        HX, _ = O.apply_H(s, X)
+        SX, _ = O.apply_S(s, X)
+        own, _, _ = O.subspace_diag(O.gram(X, HX, s.dV, 2 * nb), O.gram(X, SX, s.dV, 2 * nb))
+        assert np.max(np.abs(eps - own)) <= 1e-10, np.max(np.abs(eps - own))
+        assert np.max(np.abs(eps[:nb] - ref["eps"][:nb])) <= 1e-5 * max(1.0, np.max(np.abs(ref["eps"])))
     # the output vectors: S-orthonormal Ritz vectors with the n lowest Ritz values
     out = w["psi_out"].cpu().numpy()
     check = O.rayleigh_ritz(s, out)
     assert np.max(np.abs(check["Snm"] - np.eye(nb))) <= 1e-10
-    assert np.max(np.abs(check["Hnm"] - np.diag(ref["eps"][:nb]))) <= 1e-10 * max(1.0, np.max(np.abs(ref["eps"])))
+    assert np.max(np.abs(check["Hnm"] - np.diag(eps[:nb]))) <= 1e-10 * max(1.0, np.max(np.abs(ref["eps"])))
     ctx.close()
 
 
@@ -114,7 +139,9 @@ def test_davidson_step_mixed_form(dev):
     nb = 24
     rr = O.rayleigh_ritz(s, synth.make_psi(s, nb, 672))
     psi32 = rr["psi_rot"].astype(np.float32)
-    ref = O.davidson_step(s, psi32.astype(np.float64), rr["eps"])
+    # 28 = 4 x 7 and 26 = 2 x 13: no FFT of these sizes, so the step takes the Jacobi
+    # preconditioner (the documented rule of pawfd_davidson_step)
+    ref = O.davidson_step(s, psi32.astype(np.float64), rr["eps"], precond="jacobi")
     ctx = api.Context(s, max_bands=2 * nb, device=dev, precision="mixed")
     w = gpu_step(ctx, psi32, rr["eps"], nb, dev)
     assert np.allclose(w["rnorm"].cpu().numpy(), ref["rnorm"], rtol=1e-5, atol=0)
@@ -124,4 +151,37 @@ def test_davidson_step_mixed_form(dev):
     out = w["psi_out"].cpu().numpy().astype(np.float64)
     check = O.rayleigh_ritz(s, out)
     assert np.max(np.abs(check["Snm"] - np.eye(nb))) <= 1e-5
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision,cplx,nb", [("fp64", False, 6), ("fp64", True, 5), ("mixed", False, 7),
+                                               ("mixed", True, 4), ("fp64", False, 1)])
+def test_kinetic_precond_against_oracle(dev, precision, cplx, nb):
+    """pawfd_kinetic_precond against the oracle's -(T + sigma)^-1 on grids of radices 4, 2, 3
+    and 5, real (band pairs per transform, an odd count leaving one band alone) and Bloch, FP64
+    and FP32 bands, out aliasing R."""
+    from paper_2310_14776_gb300 import api
+    k = (0.31, -0.22, 0.17) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((30, 24, 20), (9.0, 7.5, 6.0), 3, synth.PSET_SP, seed=681, k=k, complex_wf=cplx)
+    R = synth.make_psi(s, nb, 682)
+    ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+    Rd = to_dev(R, dev).to(ctx.dtype)
+    out = ctx.kinetic_precond(Rd).cpu().numpy()
+    same = Rd.clone()
+    ctx.kinetic_precond(same, out=same)
+    ctx.close()
+    Rin = Rd.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    ref = O.kinetic_precondition(s, Rin)
+    err = np.linalg.norm((out.astype(ref.dtype) - ref).reshape(nb, -1), axis=1) / \
+        np.linalg.norm(ref.reshape(nb, -1), axis=1)
+    assert err.max() <= fft32_bound(s), err.max()
+    assert np.array_equal(same.cpu().numpy(), out)
+
+
+def test_kinetic_precond_rejects_other_grid_factors(dev):
+    from paper_2310_14776_gb300 import api, _lib
+    s = synth.make_system((14, 10, 8), (5.0, 4.0, 3.5), 1, synth.PSET_SP, seed=683)
+    ctx = api.Context(s, max_bands=2, device=dev)
+    with pytest.raises(_lib.PawFDError):
+        ctx.kinetic_precond(torch.zeros((2,) + tuple(s.n[::-1]), dtype=torch.float64, device=dev))
     ctx.close()
