@@ -338,18 +338,16 @@ def davidson_weights(system, eps: np.ndarray) -> np.ndarray:
     """Jacobi preconditioner weights w_n(r) = -1 / max(d(r) - eps_n, d0 / 10) of the block-Davidson
     step (a reading: the paper names the Davidson eigensolver of the Kohn-Sham and
     parallelization sections without its steps).  d(r) = v(r) + d0 is the diagonal of the
-    kinetic + local operator, d0 = -1/2 c0 sum_c 1/h_c^2 the stencil's centre weight.  The
-    reading fixes the weights' precision at FP32 (any positive weight gives a valid search
-    direction), so they are formed here in float32 arithmetic from the FP64 d and eps."""
+    kinetic + local operator, d0 = -1/2 c0 sum_c 1/h_c^2 the stencil's centre weight."""
     c0 = fd6_coefficients()[0]
     h = system.h
     d0 = -0.5 * c0 * (1.0 / (h[0] * h[0]) + 1.0 / (h[1] * h[1]) + 1.0 / (h[2] * h[2]))
-    d = (np.asarray(system.vloc, np.float64).reshape(-1) + d0).astype(np.float32)
-    e = np.asarray(eps, np.float64).astype(np.float32)
-    floor = np.float32(0.1 * d0)
+    d = np.asarray(system.vloc, np.float64).reshape(-1) + d0
+    e = np.asarray(eps, np.float64)
+    floor = 0.1 * d0
     den = d[None, :] - e[:, None]
     den = np.where(den > floor, den, floor)
-    return (np.float32(-1.0) / den).astype(np.float64)
+    return -1.0 / den
 
 
 KINETIC_SHIFT = 0.5   # Hartree: sigma of the kinetic preconditioner (a reading)

@@ -62,20 +62,21 @@ def test_davidson_step_matches_oracle(dev, cplx, precond):
     rcorr = ref["X"].reshape(2 * nb, K)[nb:]
     eps = w["eps"].cpu().numpy()
     if precond == "jacobi":
-        assert np.max(np.abs(corr - rcorr)) <= 1e-12 * np.max(np.abs(rcorr))
-        assert np.max(np.abs(eps - ref["eps"])) <= 1e-10, np.max(np.abs(eps - ref["eps"]))
+        # FP32 weights: d - eps in FP32 cancels at most tenfold (the floor is a tenth of d0), so
+        # each weight is within 16 u of the FP64 one
+        assert np.all(np.abs(corr - rcorr) <= 16 * U32 * np.abs(rcorr) + 1e-300)
     else:
-        # FP32 transforms: the corrections to the FP32 bound; the Ritz values exactly those of
-        # the GPU's own subspace X (the oracle's Rayleigh-Ritz on it), and within the effect of
-        # the FP32 corrections of the oracle's FP64 step
+        # FP32 transforms: the corrections to the FP32 bound
         err = np.linalg.norm(corr - rcorr, axis=1) / np.linalg.norm(rcorr, axis=1)
         assert err.max() <= fft32_bound(s), err.max()
-        X = w["X"].cpu().numpy()
-        HX, _ = O.apply_H(s, X)
-        SX, _ = O.apply_S(s, X)
-        own, _, _ = O.subspace_diag(O.gram(X, HX, s.dV, 2 * nb), O.gram(X, SX, s.dV, 2 * nb))
-        assert np.max(np.abs(eps - own)) <= 1e-10, np.max(np.abs(eps - own))
-        assert np.max(np.abs(eps[:nb] - ref["eps"][:nb])) <= 1e-5 * max(1.0, np.max(np.abs(ref["eps"])))
+    # the Ritz values exactly those of the GPU's own subspace X (the oracle's Rayleigh-Ritz on
+    # it), and within the effect of the FP32 corrections of the oracle's FP64 step
+    X = w["X"].cpu().numpy()
+    HX, _ = O.apply_H(s, X)
+    SX, _ = O.apply_S(s, X)
+    own, _, _ = O.subspace_diag(O.gram(X, HX, s.dV, 2 * nb), O.gram(X, SX, s.dV, 2 * nb))
+    assert np.max(np.abs(eps - own)) <= 1e-10, np.max(np.abs(eps - own))
+    assert np.max(np.abs(eps[:nb] - ref["eps"][:nb])) <= 1e-5 * max(1.0, np.max(np.abs(ref["eps"])))
     # the output vectors: S-orthonormal Ritz vectors with the n lowest Ritz values
     out = w["psi_out"].cpu().numpy()
     check = O.rayleigh_ritz(s, out)

@@ -659,7 +659,7 @@ def test_kinetic_symbol_and_preconditioner_on_bloch_waves(complex_wf):
 def test_davidson_weights_from_the_dense_diagonal():
     # d(r) is the diagonal of the dense T + v (Kronecker sums of the published weights, no
     # atoms), the floor a tenth of the diagonal of T alone; eps values on both sides of the
-    # floor, and the float32 arithmetic of the reading (so a float32-level tolerance)
+    # floor
     s = small_system(**TINY["bloch"])
     Tv, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=True, vloc=s.vloc))
     T0, _ = dense_operators(free_system(s.n, s.cell, k=s.k, complex_wf=True, vloc=np.zeros_like(s.vloc)))
@@ -672,7 +672,7 @@ def test_davidson_weights_from_the_dense_diagonal():
     den = d[None, :] - eps[:, None]
     expect = -1.0 / np.maximum(den, floor)
     assert np.any(den > floor) and np.any(den < floor)
-    assert np.allclose(w, expect, rtol=2e-6, atol=0)
+    assert np.allclose(w, expect, rtol=1e-13, atol=0)
 
 
 def test_davidson_fixed_point_is_exact_eigenvectors():
