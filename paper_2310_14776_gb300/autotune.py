@@ -48,10 +48,15 @@ def contraction_candidates(ctx) -> List[Dict[str, int]]:
     """Gram / rotation variants of equal accuracy.  For FP64 data both the digit-product
     tensor-core kernels and the FP64 FMA kernels meet the FP64 tolerance.  For FP32 data the FMA
     kernels form FP32 products (about 1e-7 relative), far less accurate than the exact digit
-    products, so the mixed form keeps the tensor-core path."""
+    products, so the mixed form keeps the tensor-core path.  The tensor-core Gram's K block (its
+    tiling of the grid: whole-scratch blocks, or blocks of 4, 16 or 64 exactness chunks of 512
+    values whose digit planes stay in L2 between the slicing and the MMA kernels) is a candidate
+    as well: the chunks' exact digit sums are the same for every K block, only the order in which
+    the FP64 partial sums of the blocks are added changes (results agree to FP64 rounding)."""
+    tc = [{"tensor_cores": 1, "tc_kblk": k} for k in (0, 4, 16, 64)]
     if ctx.precision == "fp64":
-        return [{"tensor_cores": 1}, {"tensor_cores": 0}]
-    return []
+        return tc + [{"tensor_cores": 0}]
+    return tc
 
 
 def _time(fn, reps: int) -> float:
