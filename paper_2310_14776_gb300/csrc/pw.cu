@@ -83,33 +83,46 @@ __device__ __forceinline__ cplx<R> imul(R s, cplx<R> z) {
   return cplx<R>{-s * z.im, s * z.re};
 }
 
-// One line element: global index (band offset included) and grid point r within the band of
-// element i of line l of this CTA; false past the grid.
+// The elements of this CTA's lines.  Line l's element i sits at grid point r = r0[l] + i s and
+// global index g = g0[l] + i s (band offset band[l] K included), with s = 1 along x, N1 along y
+// and N1 N2 along z; r0[l] < 0 marks a line past the grid.  The bases are formed once per CTA
+// (64-bit divisions there only), so the per-element index arithmetic is an add and a multiply.
+struct LineBase {
+  long long g0;
+  int r0;
+  int band;
+};
+
 template <class R>
-__device__ __forceinline__ bool element(const FftArgs<R>& a, int l, int i, long long& g, long long& r) {
-  if (a.axis == 0) {
-    const long long L = (long long)blockIdx.x * a.nl + l;
-    if (L >= a.nlines) return false;
-    g = L * a.n1 + i;
-    r = g % a.K;
-    return true;
+__device__ __forceinline__ void line_bases(const FftArgs<R>& a, LineBase* lb) {
+  for (int l = threadIdx.x; l < a.nl; l += FFT_NT) {
+    LineBase b;
+    if (a.axis == 0) {
+      const long long L = (long long)blockIdx.x * a.nl + l;
+      const long long per_band = (long long)a.n2 * a.n3;
+      if (L >= a.nlines) {
+        b = {0, -1, 0};
+      } else {
+        b.band = (int)(L / per_band);
+        b.r0 = (int)((L - (long long)b.band * per_band) * a.n1);
+        b.g0 = (long long)b.band * a.K + b.r0;
+      }
+    } else {
+      const int xt = blockIdx.x % a.tiles;
+      const long long row = blockIdx.x / a.tiles;   // (band, z) for axis 1, (band, y) for axis 2
+      const int x = xt * a.nl + l;
+      const int m = a.axis == 1 ? a.n3 : a.n2;
+      b.band = (int)(row / m);
+      const int zy = (int)(row - (long long)b.band * m);
+      if (x >= a.n1) {
+        b = {0, -1, 0};
+      } else {
+        b.r0 = a.axis == 1 ? zy * a.n2 * a.n1 + x : zy * a.n1 + x;
+        b.g0 = (long long)b.band * a.K + b.r0;
+      }
+    }
+    lb[l] = b;
   }
-  const int xt = blockIdx.x % a.tiles;
-  const long long row = blockIdx.x / a.tiles;   // (band, z) for axis 1, (band, y) for axis 2
-  const int x = xt * a.nl + l;
-  if (x >= a.n1) return false;
-  if (a.axis == 1) {
-    const long long band = row / a.n3;
-    const int z = (int)(row % a.n3);
-    r = ((long long)z * a.n2 + i) * a.n1 + x;
-    g = band * a.K + r;
-  } else {
-    const long long band = row / a.n2;
-    const int y = (int)(row % a.n2);
-    r = ((long long)i * a.n2 + y) * a.n1 + x;
-    g = band * a.K + r;
-  }
-  return true;
 }
 
 template <class R>
@@ -118,22 +131,41 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
   cplx<R>* W = (cplx<R>*)smem_raw;
   cplx<R>* X = W + a.N;
   cplx<R>* Y = X + (size_t)a.nl * a.N;
+  LineBase* lb = (LineBase*)(Y + (size_t)a.nl * a.N);
   const int N = a.N, nl = a.nl, tid = threadIdx.x;
+  const int stride = a.axis == 0 ? 1 : (a.axis == 1 ? a.n1 : a.n1 * a.n2);
+  line_bases(a, lb);
   for (int j = tid; j < N; j += FFT_NT) {
     const cplx<R> w = a.tw[j];
     W[j] = a.inverse ? cplx<R>{w.re, -w.im} : w;
   }
+  __syncthreads();   // the line bases
+  // element e of the CTA's nl N is (line l, position i): e = l N + i along x (contiguous lines),
+  // e = i nl + l along y and z (consecutive x); (l, i) advance by FFT_NT elements per iteration
+  // without a division
+  const bool xline = a.axis == 0;
+  const int inner = xline ? N : nl;                     // the fast index's range
+  const int d_fast = FFT_NT % inner, d_slow = FFT_NT / inner;
+  const int f0 = tid % inner, s0 = tid / inner;
   // load: x lines along the line (contiguous), y / z lines across the tile (consecutive x)
-  for (int e = tid; e < nl * N; e += FFT_NT) {
-    const int l = a.axis == 0 ? e / N : e % nl;
-    const int i = a.axis == 0 ? e % N : e / nl;
-    long long g, r;
+  for (int e = tid, fi = f0, si = s0; e < nl * N; e += FFT_NT) {
+    const int l = xline ? si : fi;
+    const int i = xline ? fi : si;
+    fi += d_fast;
+    si += d_slow;
+    if (fi >= inner) {
+      fi -= inner;
+      ++si;
+    }
     cplx<R> v = {R(0), R(0)};
-    if (element(a, l, i, g, r)) {
+    const LineBase b = lb[l];
+    if (b.r0 >= 0) {
+      const int r = b.r0 + i * stride;
+      const long long g = b.g0 + (long long)i * stride;
       if (a.pre == 2) {
         v = cplx<R>{a.rin[g], R(0)};
       } else if (a.pre == 3) {
-        const long long p = g / a.K;
+        const long long p = b.band;
         if (a.xreal) {
           const long long ga = 2 * p * a.K + r, gb = ga + a.K;
           const bool hb = 2 * p + 1 < a.xnb;
@@ -172,10 +204,13 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
   int Ns = 1;
   for (int s = 0; s < a.nf; ++s) {
     const int Rd = a.fac[s], M = N / Rd, step = N / (Ns * Rd);
+    // butterfly e = l M + j, j = jq Ns + k (M is a multiple of Ns); all advanced incrementally
+    const int dj = FFT_NT % M, dl = FFT_NT / M, dk = dj % Ns, djq = dj / Ns, mq = M / Ns;
+    int l = tid / M, j = tid - (tid / M) * M;
+    int jq = j / Ns, k = j - jq * Ns;
     for (int e = tid; e < nl * M; e += FFT_NT) {
-      const int l = e / M, j = e - l * M, k = j % Ns;
       const cplx<R>* x = X + l * N + j;
-      cplx<R>* y = Y + l * N + (j / Ns) * Ns * Rd + k;
+      cplx<R>* y = Y + l * N + jq * Ns * Rd + k;
       if (Rd == 4) {
         cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step], v3 = x[3 * M] * W[3 * k * step];
         const cplx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = imul(sg, v1 - v3);
@@ -207,6 +242,19 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
         y[2 * Ns] = t2 + u2;
         y[3 * Ns] = t2 - u2;
       }
+      j += dj;
+      l += dl;
+      k += dk;
+      jq += djq;
+      if (k >= Ns) {
+        k -= Ns;
+        ++jq;
+      }
+      if (j >= M) {
+        j -= M;
+        ++l;
+        jq -= mq;
+      }
     }
     __syncthreads();
     cplx<R>* t = X;
@@ -215,11 +263,19 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     Ns *= Rd;
   }
   // store, with the epilogue
-  for (int e = tid; e < nl * N; e += FFT_NT) {
-    const int l = a.axis == 0 ? e / N : e % nl;
-    const int i = a.axis == 0 ? e % N : e / nl;
-    long long g, r;
-    if (!element(a, l, i, g, r)) continue;
+  for (int e = tid, fi = f0, si = s0; e < nl * N; e += FFT_NT) {
+    const int l = xline ? si : fi;
+    const int i = xline ? fi : si;
+    fi += d_fast;
+    si += d_slow;
+    if (fi >= inner) {
+      fi -= inner;
+      ++si;
+    }
+    const LineBase b = lb[l];
+    if (b.r0 < 0) continue;
+    const int r = b.r0 + i * stride;
+    const long long g = b.g0 + (long long)i * stride;
     const cplx<R> y = X[l * N + i];
     if (a.post == 0) {
       a.out[g] = y;
@@ -228,7 +284,7 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     } else if (a.post == 4) {
       a.rout[g] = y.re;
     } else if (a.post == 5) {
-      const long long p = g / a.K;
+      const long long p = b.band;
       if (a.xreal) {
         const long long ga = 2 * p * a.K + r, gb = ga + a.K;
         const bool hb = 2 * p + 1 < a.xnb;
@@ -401,7 +457,7 @@ int fft_pass_plan(pawfd_ctx* c, const PwPlan& p, int axis, const cplx<R>* in, cp
     a.nlines = 0;
     grid = (long long)nb * (axis == 1 ? a.n3 : a.n2) * a.tiles;
   }
-  const size_t smem = sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * a.N);
+  const size_t smem = sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * a.N) + sizeof(LineBase) * (size_t)a.nl;
   if (smem > 48 * 1024) {
     const int rc = check_cuda(
         c, cudaFuncSetAttribute(fft_pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
