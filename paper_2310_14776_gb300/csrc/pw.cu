@@ -130,8 +130,12 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* W = (cplx<R>*)smem_raw;
   cplx<R>* X = W + a.N;
-  cplx<R>* Y = X + (size_t)a.nl * a.N;
-  LineBase* lb = (LineBase*)(Y + (size_t)a.nl * a.N);
+  // lines at a pitch of N + 1 values: the y and z passes fill and drain the buffer across lines
+  // (consecutive x in consecutive threads), which at a pitch of N would put a warp's accesses
+  // in one bank for every even N
+  const int pitch = a.N + 1;
+  cplx<R>* Y = X + (size_t)a.nl * pitch;
+  LineBase* lb = (LineBase*)(Y + (size_t)a.nl * pitch);
   const int N = a.N, nl = a.nl, tid = threadIdx.x;
   const int stride = a.axis == 0 ? 1 : (a.axis == 1 ? a.n1 : a.n1 * a.n2);
   line_bases(a, lb);
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
         }
       }
     }
-    X[l * N + i] = v;
+    X[l * pitch + i] = v;
   }
   __syncthreads();
   // Stockham stages: after the stages with radices r_0 .. r_{s-1} (product Ns), transforms of
@@ -209,8 +213,8 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     int l = tid / M, j = tid - (tid / M) * M;
     int jq = j / Ns, k = j - jq * Ns;
     for (int e = tid; e < nl * M; e += FFT_NT) {
-      const cplx<R>* x = X + l * N + j;
-      cplx<R>* y = Y + l * N + jq * Ns * Rd + k;
+      const cplx<R>* x = X + l * pitch + j;
+      cplx<R>* y = Y + l * pitch + jq * Ns * Rd + k;
       if (Rd == 4) {
         cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step], v3 = x[3 * M] * W[3 * k * step];
         const cplx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = imul(sg, v1 - v3);
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     if (b.r0 < 0) continue;
     const int r = b.r0 + i * stride;
     const long long g = b.g0 + (long long)i * stride;
-    const cplx<R> y = X[l * N + i];
+    const cplx<R> y = X[l * pitch + i];
     if (a.post == 0) {
       a.out[g] = y;
     } else if (a.post == 3) {
@@ -457,7 +461,8 @@ int fft_pass_plan(pawfd_ctx* c, const PwPlan& p, int axis, const cplx<R>* in, cp
     a.nlines = 0;
     grid = (long long)nb * (axis == 1 ? a.n3 : a.n2) * a.tiles;
   }
-  const size_t smem = sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * a.N) + sizeof(LineBase) * (size_t)a.nl;
+  const size_t smem =
+      sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * (a.N + 1)) + sizeof(LineBase) * (size_t)a.nl;
   if (smem > 48 * 1024) {
     const int rc = check_cuda(
         c, cudaFuncSetAttribute(fft_pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
