@@ -447,8 +447,9 @@ int fft_pass_plan(pawfd_ctx* c, const PwPlan& p, int axis, const cplx<R>* in, cp
   a.c52 = (R)std::cos(4.0 * M_PI / 5.0);
   a.s51 = (R)std::sin(2.0 * M_PI / 5.0);
   a.s52 = (R)std::sin(4.0 * M_PI / 5.0);
-  // lines per CTA: about 2048 (FP64) or 4096 (FP32) complex values per buffer
-  const int cap = sizeof(R) == 8 ? 2048 : 4096;
+  // lines per CTA: about 1024 (FP64) or 2048 (FP32) complex values per buffer (measured a
+  // little faster than twice that: more CTAs per SM)
+  const int cap = sizeof(R) == 8 ? 1024 : 2048;
   long long grid;
   if (axis == 0) {
     a.nl = std::max(1, std::min(64, cap / a.N));
