@@ -159,6 +159,7 @@ struct TcScratch {
   CUtensorMap mapA;            // row-major planes of the Gram operands (4-D TMA boxes)
   CUtensorMap mapB;
   CUtensorMap mapAB;           // slicesA with the B operand's box (the Gram of psi with itself)
+  CUtensorMap mapBA;           // slicesB with the A operand's box (complex Gram pair: psi's planes as A)
   void* part2 = nullptr;       // partials of the second Gram of a pair
   // band rotation
   long long rot_Lc = 0;        // contraction length (bands, x2 for complex) padded to chunks

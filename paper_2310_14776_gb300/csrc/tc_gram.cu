@@ -17,6 +17,28 @@
 namespace pawfd {
 namespace {
 
+// Split-K count of one K block.  The MMA kernel holds one CTA per SM (its shared memory and
+// TMEM), so tiles x splits CTAs run in ceil(tiles x splits / SMs) waves of ceil(chunks / splits)
+// chunks each.  The count with the fewest chunk-times wins, each wave's fixed cost (prologue,
+// pipeline fill, partial store) counted as one chunk; ties go to fewer splits.  Filling the SMs
+// once is not enough: 106 tiles (1024 complex bands) in one wave leave 46 of 152 SMs idle,
+// ten splits run the same work in seven waves at 98 % occupancy.
+int gram_splits(int tiles, int nch, int num_sms) {
+  int best = 1;
+  long long best_cost = -1;
+  const int cap = std::min(nch, 2 * num_sms);
+  for (int s = 1; s <= cap; ++s) {
+    const int cpc = (nch + s - 1) / s, ns = (nch + cpc - 1) / cpc;
+    const long long waves = ((long long)tiles * ns + num_sms - 1) / num_sms;
+    const long long cost = waves * (cpc + 1);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = ns;
+    }
+  }
+  return best;
+}
+
 template <class W>
 __global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, int im_off, double dV,
                                  bool herm, W* __restrict__ M);
@@ -72,10 +94,8 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
   // in L2 between the slicing kernels and the MMA kernel)
   const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
-  const int max_chunks = (int)(Kblk / sg::KCG);
-  // splits per K block: fill the SMs once (one CTA per SM), at least one chunk per CTA
-  // one CTA per SM: tiles x splits within one wave (a partial second wave doubles the time)
-  int nsplit = std::max(1, std::min(max_chunks, c->num_sms / tiles));
+  const int nch0 = (int)((std::min(Kblk, L) + sg::KCG - 1) / sg::KCG);   // chunks of the first block
+  int nsplit = gram_splits(tiles, nch0, c->num_sms);
   while (nsplit > 1 && (size_t)nsplit * nb * rowsB * sizeof(double) > t.part_bytes) --nsplit;
   __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
   __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
@@ -154,8 +174,8 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
   const int tiles = sg::herm_tiles(nb);
   const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
-  const int max_chunks = (int)(Kblk / sg::KCG);
-  int nsplit = std::max(1, std::min(max_chunks, c->num_sms / tiles));
+  const int nch0 = (int)((std::min(Kblk, L) + sg::KCG - 1) / sg::KCG);
+  int nsplit = gram_splits(tiles, nch0, c->num_sms);
   while (nsplit > 1 && (size_t)nsplit * nb * nb * sizeof(double) > t.part_bytes) --nsplit;
   __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
   __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
@@ -227,6 +247,99 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
                                                                                 c->dV, true, M2);
   c->launches += 2;
   return check_cuda(c, cudaGetLastError(), "tensor-core gram pair launch");
+}
+
+// The two Hermitian Gram matrices of the Rayleigh-Ritz step for complex bands from one slicing
+// of psi and one of B = H psi.  B_ext = [psi; psi''] (psi and its swapped rows) is the second
+// operand of both: M2 = dV psi^H psi takes psi's planes (rows [0, nb) of B_ext) as the first
+// operand as well, and M1 takes B as the first operand, M1 = dV B^H psi.  For a Hermitian
+// operator, (H psi)_n^H psi_m = conj(psi_m^H H psi_n) = H_nm, so M1 is psi^H H psi; the
+// Hermitian tiling already rests on that symmetry (only the upper triangle is formed).  Three
+// slicing passes per K block instead of the six of two separate Grams.
+template <class R, int S, int ORD>
+int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1, zd* M2) {
+  TcScratch& t = c->tc;
+  const long long L = 2LL * c->K;                                   // real-view row length
+  const int nbp = (nb + 7) / 8 * 8;
+  const int rowsB = nbp + nb;
+  const int Tc = (nb + sg::BN - 1) / sg::BN;
+  const int tiles = 2 * sg::herm_tiles(nb);
+  const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
+                                                 : t.kblk;
+  const int nch0 = (int)((std::min(Kblk, L) + sg::KCG - 1) / sg::KCG);
+  int nsplit = gram_splits(tiles, nch0, c->num_sms);
+  while (nsplit > 1 && (size_t)nsplit * nb * rowsB * sizeof(double) > t.part_bytes) --nsplit;
+  __nv_bfloat16* sA = (__nv_bfloat16*)t.slicesA;
+  __nv_bfloat16* sB = (__nv_bfloat16*)t.slicesB;
+  t.presliced_gram = nullptr;
+  int blk = 0;
+  for (long long k0 = 0; k0 < L; k0 += Kblk, ++blk) {
+    const long long len = std::min(Kblk, L - k0);
+    const int nch = (int)((len + sg::KCG - 1) / sg::KCG);
+    const int cpc = (nch + nsplit - 1) / nsplit;
+    const int ns = (nch + cpc - 1) / cpc;
+    cudaMemsetAsync(t.maxA, 0x80, sizeof(int) * t.rowsA_alloc, c->stream);
+    cudaMemsetAsync(t.maxB, 0x80, sizeof(int) * t.rowsB_alloc, c->stream);
+    const unsigned grid = (unsigned)(((long long)nb * nch + 7) / 8);
+    sg::slice_kernel<R, S, sg::KCG><<<grid, 256, 0, c->stream>>>(B + k0, nb, L, len, nch, t.kblk, false, 0,
+                                                                 t.rowsA_alloc, sA, t.sigA, t.rowsA_alloc, t.maxA);
+    sg::slice_kernel<R, S, sg::KCG><<<grid, 256, 0, c->stream>>>(A + k0, nb, L, len, nch, t.kblk, false, 0,
+                                                                 t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+    sg::slice_kernel<R, S, sg::KCG><<<grid, 256, 0, c->stream>>>(A + k0, nb, L, len, nch, t.kblk, true, nbp,
+                                                                 t.rowsB_alloc, sB, t.sigB, t.rowsB_alloc, t.maxB);
+    sg::GramArgs a = {};
+    a.gA = sA;
+    a.gB = sB;
+    a.rows_allocA = t.rowsA_alloc;
+    a.rows_allocB = t.rowsB_alloc;
+    a.ksteps = t.kblk / sg::BK;
+    a.half_stride = nbp;
+    a.sigA = t.sigA;
+    a.sigB = t.sigB;
+    a.sig_ldA = t.rowsA_alloc;
+    a.sig_ldB = t.rowsB_alloc;
+    a.maxA = t.maxA;
+    a.maxB = t.maxB;
+    a.rowsA = nb;
+    a.rowsB = rowsB;
+    a.tilesN = 2 * Tc;
+    a.herm = 1;
+    a.halves = 2;
+    a.half_rows = nb;
+    a.chunks_per_cta = cpc;
+    a.nchunks = nch;
+    a.accumulate = blk > 0;
+    a.klen = len;
+    a.part = (double*)t.part;
+    a.st = c->d_status;
+    if (blk == 0 && ns < nsplit) nsplit = ns;
+    ktimer_begin(c);
+    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.mapA, t.mapB, a);
+    ktimer_end(c);
+    // psi^H psi: psi's planes (rows [0, nb) of B_ext, read through a map with the A box) as
+    // the first operand; rows [nb, 128 Tr) of that box are zero or psi'' rows, whose output
+    // rows (>= nb) are never stored
+    sg::GramArgs a2 = a;
+    a2.gA = sB;
+    a2.rows_allocA = t.rowsB_alloc;
+    a2.sigA = t.sigB;
+    a2.sig_ldA = t.rowsB_alloc;
+    a2.maxA = t.maxB;
+    a2.part = (double*)t.part2;
+    ktimer_begin(c);
+    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
+        t.mapBA, t.mapB, a2);
+    ktimer_end(c);
+    c->launches += 5;
+  }
+  const long long nn = (long long)nb * nb;
+  tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part, nsplit, nb, rowsB, nbp,
+                                                                            c->dV, true, M1);
+  tc_reduce_kernel<zd><<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>((double*)t.part2, nsplit, nb, rowsB, nbp,
+                                                                            c->dV, true, M2);
+  c->launches += 2;
+  return check_cuda(c, cudaGetLastError(), "tensor-core complex gram pair launch");
 }
 
 // The rotation's first operand: A_ext[row][k] with k the contraction index, for the first
@@ -392,9 +505,14 @@ int launch_rotate_tc(pawfd_ctx* c, const void* psi, int nb, const void* C, void*
   return tc_rotate_impl<double, 7, 6>(c, (const double*)psi, nb, (const double*)C, nout, (double*)out);
 }
 
-// Hermitian Grams psi^H B and psi^H psi (real bands; false when this form does not apply)
+// Hermitian Grams psi^H B and psi^H psi from one slicing of psi (false when this form does not apply)
 bool gram_pair_tc(pawfd_ctx* c, const void* psi, const void* B, int nb, void* M1, void* M2, int* rc) {
-  if (!c->tc.ready || is_complex(c)) return false;
+  if (!c->tc.ready) return false;
+  if (is_complex(c)) {
+    if (is_fp32(c)) *rc = tc_gram_pair_cplx_impl<float, 4, 4>(c, (const float*)psi, (const float*)B, nb, (zd*)M1, (zd*)M2);
+    else *rc = tc_gram_pair_cplx_impl<double, 7, 6>(c, (const double*)psi, (const double*)B, nb, (zd*)M1, (zd*)M2);
+    return true;
+  }
   if (is_fp32(c)) *rc = tc_gram_pair_impl<float, 4, 4>(c, (const float*)psi, (const float*)B, nb, (double*)M1, (double*)M2);
   else *rc = tc_gram_pair_impl<double, 7, 6>(c, (const double*)psi, (const double*)B, nb, (double*)M1, (double*)M2);
   return true;
@@ -456,7 +574,7 @@ int setup_tc(pawfd_ctx* c) {
   const int nchunks = (int)(t.kblk / sg::KC);
   const int rowsB = cplx ? nbp + nb : nb;
   const int tiles_min = (cplx ? 2 : 1) * sg::herm_tiles(nb);
-  const int nsplit = std::max(1, std::min(nchunks, (c->num_sms + tiles_min - 1) / tiles_min));
+  const int nsplit = gram_splits(tiles_min, (int)(t.kblk / sg::KCG), c->num_sms);
   t.part_bytes = (size_t)nsplit * nb * rowsB * sizeof(double);
   int rc = check_cuda(c, cudaMalloc(&t.slicesA, sa), "cudaMalloc tc slices");
   if (rc == PAWFD_OK) rc = check_cuda(c, cudaMalloc(&t.slicesB, sb), "cudaMalloc tc slices");
@@ -474,6 +592,7 @@ int setup_tc(pawfd_ctx* c) {
   rc = encode_slice_map(c, &t.mapA, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BM);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapAB, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BN);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapBA, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BM);
   if (rc == PAWFD_OK) {
     const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     // the Gram (row-major planes, TMA maps) and the rotation (core-matrix planes, bulk copies;
