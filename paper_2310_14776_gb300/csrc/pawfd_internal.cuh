@@ -163,6 +163,7 @@ struct TcScratch {
   void* part2 = nullptr;       // partials of the second Gram of a pair
   // band rotation
   long long rot_Lc = 0;        // contraction length (bands, x2 for complex) padded to chunks
+  int rot_kc = 0;              // rotation chunk: 256 contraction values, or 512 beyond 256
   int rot_rowsA_alloc = 0;
   long long rot_rblk = 0;      // grid points per block
   void* rotA = nullptr;        // FP64 operand built from C

@@ -15,8 +15,11 @@
 // Five accumulators of BN = 96 columns use 480 of the 512 TMEM columns.  Chunks are KCG = 512
 // values long for the Gram matrices (D0 .. D3 stay exact: with |d| <= 65 the order-2 sums
 // reach 3 * 512 * 65^2 * 2^-14 < 2^10, inside the 2^(24-14) that keeps multiples of 2^-14
-// exact, and the others have more room) and KC = 256 for the rotation, whose contraction
-// (the bands) is usually one chunk; the FP32 drift of D4 stays small at either length.  After every chunk
+// exact, and the others have more room).  The rotation's contraction (the bands) is cut into
+// chunks of KC = 256 when it is no longer than that (one chunk) and of KCG = 512 otherwise:
+// every chunk costs the MMA warp a wait for the epilogue's TMEM drain, so fewer, longer
+// chunks keep the tensor cores busier, and complex bands up to 256 stay one chunk (the
+// persistent one-chunk form).  The FP32 drift of D4 stays small at either length.  After every chunk
 // the epilogue adds 2^(sigma_a + sigma_b) (D0 + ... + D4) to a double-float (two FP32)
 // accumulator with error-free transformations (Knuth's TwoSum), so the FP64 pipe is not
 // needed per chunk; the scale is taken relative to the row's largest sigma of the K block.
@@ -34,7 +37,7 @@
 namespace pawfd {
 namespace sg {
 
-constexpr int KC = 256;           // grid values per exactness chunk of the rotation (bands)
+constexpr int KC = 256;           // contraction values per chunk of a rotation of at most 256 of them
 constexpr int KCG = 512;          // grid values per exactness chunk of the Gram matrices
 constexpr int BM = 128;           // output rows per CTA (TMEM lanes)
 constexpr int BN = 96;            // output columns per CTA (MMA N)
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 3 : 6)
 // so that one store instruction of the warp fills two whole K-step blocks of the row group's
 // core matrices (2 x 256 contiguous bytes).  The chunk is read twice: once for its largest
 // exponent, once (from L1/L2) for the digits.
-template <class R, int S>
+template <class R, int S, int KCH>
 __global__ void __launch_bounds__(256) slice_rg_kernel(const R* __restrict__ src, int rows, long long ld, long long len,
                                                        int nchunks, long long Lp, bool swapped, int row_offset,
                                                        int out_rows, __nv_bfloat16* __restrict__ out,
@@ -243,9 +246,9 @@ __global__ void __launch_bounds__(256) slice_rg_kernel(const R* __restrict__ src
   const R* row = src + (long long)(valid ? r : 0) * ld;
   int emax = 0;
 #pragma unroll 2
-  for (int j = 0; j < KC / 32; ++j) {
+  for (int j = 0; j < KCH / 32; ++j) {
     R x[8];
-    if (valid) load8(row, c * KC + 32 * j + 8 * q, len, swapped, x);
+    if (valid) load8(row, c * KCH + 32 * j + 8 * q, len, swapped, x);
     else {
 #pragma unroll
       for (int v = 0; v < 8; ++v) x[v] = R(0);
@@ -261,8 +264,8 @@ __global__ void __launch_bounds__(256) slice_rg_kernel(const R* __restrict__ src
     atomicMax(sigmax + orow, emax - FloatBits<R>::bias - 5);
   }
 #pragma unroll 1
-  for (int j = 0; j < KC / 32; ++j) {
-    const long long k0 = c * KC + 32 * j + 8 * q;
+  for (int j = 0; j < KCH / 32; ++j) {
+    const long long k0 = c * KCH + 32 * j + 8 * q;
     R x[8];
     uint32_t o[S][4];
     if (valid) {
@@ -280,7 +283,7 @@ __global__ void __launch_bounds__(256) slice_rg_kernel(const R* __restrict__ src
 
 // Transposing slicer for the band rotation: operand rows are grid points r, the contraction
 // index k runs over the bands (real: k = n; complex: k = 2 n + c, c = 0 real / 1 imaginary
-// part).  One CTA per (16 grid points, chunk of KC contraction values): the tile is read along
+// part).  One CTA per (16 grid points, chunk of KCH contraction values): the tile is read along
 // r (coalesced), kept transposed in shared memory, the largest exponent of every grid point's
 // chunk found, and each thread turns 8 consecutive k of one grid point into S 16-byte digit
 // groups (a warp writes 512 contiguous bytes of a plane).  out: digit planes of out_rows rows (plane_offset);
@@ -350,11 +353,11 @@ __device__ __forceinline__ void digits8_t(const float (&x)[8], int emax, uint32_
 // when the band rows and the block start allow it (vec16), else one value per copy; zero
 // filled past the bands or the block's grid points.  The staged tile is dense and band-major:
 // buf[n][q] (real) or buf[n][2 q + c] (complex), RT grid points q per band row.
-template <class R>
-__host__ __device__ constexpr int slice_t_tile_values() { return KC * RT; }
-// two staged tiles of KC contraction values x RT grid points
-template <class R>
-__host__ __device__ constexpr int slice_t_smem() { return 2 * slice_t_tile_values<R>() * (int)sizeof(R); }
+template <class R, int KCH>
+__host__ __device__ constexpr int slice_t_tile_values() { return KCH * RT; }
+// two staged tiles of KCH contraction values x RT grid points
+template <class R, int KCH>
+__host__ __device__ constexpr int slice_t_smem() { return 2 * slice_t_tile_values<R, KCH>() * (int)sizeof(R); }
 
 __device__ __forceinline__ void cp_async_zfill(void* sdst, const void* gsrc, int bytes, bool valid) {
   const int src_bytes = valid ? bytes : 0;
@@ -373,19 +376,19 @@ __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int src
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-template <class R, int S>
+template <class R, int S, int KCH>
 __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi, int nb, long long K, int cplx,
                                                       long long r0, int rcount, long long Lp, int out_rows,
                                                       __nv_bfloat16* __restrict__ out, int* __restrict__ sig,
                                                       int sig_ld, int* __restrict__ sigmax, int nch, int vec16) {
   extern __shared__ __align__(16) unsigned char slice_t_smem_raw[];
-  R* bufs = (R*)slice_t_smem_raw;                    // [2][KC * RT] staged values
+  R* bufs = (R*)slice_t_smem_raw;                    // [2][KCH * RT] staged values
   __shared__ int pmax[16][RT];
   const int tid = threadIdx.x;
   const int nrt = (rcount + RT - 1) / RT;
   const int ntiles = nrt * nch;
   const int vals_per_row = cplx ? 2 * RT : RT;        // values of one band row of a tile
-  const int rows_per_chunk = cplx ? KC / 2 : KC;      // band rows of one chunk
+  const int rows_per_chunk = cplx ? KCH / 2 : KCH;    // band rows of one chunk
   constexpr int V16 = 16 / (int)sizeof(R);            // values per 16-byte copy
   // staged value (k, q) of a tile: real buf[k][q], complex buf[k / 2][2 q + k % 2]
   auto stage = [&](R* buf, int t) {
@@ -424,8 +427,8 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
   if (t < ntiles) stage(bufs, t);
   cp_async_commit();
   for (; t < ntiles; t += gridDim.x, ++it) {
-    R* cur = bufs + (it & 1) * slice_t_tile_values<R>();
-    R* nxt = bufs + ((it + 1) & 1) * slice_t_tile_values<R>();
+    R* cur = bufs + (it & 1) * slice_t_tile_values<R, KCH>();
+    R* nxt = bufs + ((it + 1) & 1) * slice_t_tile_values<R, KCH>();
     if (t + (int)gridDim.x < ntiles) stage(nxt, t + gridDim.x);
     cp_async_commit();
     cp_async_wait1();   // this tile's copies have landed
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
     {
       const int lr = tid % RT, kq = tid / RT;
       int em = 0;
-      for (int kk = kq; kk < KC; kk += 16) em = max(em, fields(val(cur, kk, lr)).exp);
+      for (int kk = kq; kk < KCH; kk += 16) em = max(em, fields(val(cur, kk, lr)).exp);
       pmax[kq][lr] = em;
     }
     __syncthreads();
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
     __syncthreads();
     // items: (K step j, half h, grid point q); the 32 threads of a warp cover the 16 grid points
     // and both halves of one K step, i.e. 512 contiguous bytes of a digit plane
-    for (int item = tid; item < RT * (KC / 8); item += 256) {
+    for (int item = tid; item < RT * (KCH / 8); item += 256) {
       const int q = item % RT, k8 = (item / (2 * RT)) * 16 + ((item / RT) & 1) * 8;
       if (rl0 + q >= rcount) continue;
       R x[8];
@@ -462,7 +465,7 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
       digits8_t<S>(x, pmax[0][q], o);
 #pragma unroll
       for (int i = 0; i < S; ++i)
-        *(uint4*)(out + plane_offset_cm(i, (long long)c * KC + k8, rl0 + q, out_rows, Lp)) =
+        *(uint4*)(out + plane_offset_cm(i, (long long)c * KCH + k8, rl0 + q, out_rows, Lp)) =
             make_uint4(o[i][0], o[i][1], o[i][2], o[i][3]);
     }
     __syncthreads();   // the buffer and pmax are reused
@@ -797,7 +800,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     }
   } else {
     if constexpr (ONE) {
-    // One chunk per tile (the rotation of real bands with nb <= KC): the value is (D0 + ... +
+    // One chunk per tile (the rotation of at most KCH contraction values): the value is (D0 + ... +
     // D4) 2^(sigma_a + sigma_b), summed exactly as a double-float and converted to the band
     // dtype.  TMEM is read in the 16 x 256-bit shape: in each 16-lane half h of the warp's
     // lane quarter, thread t holds rows t/4 and t/4 + 8 and columns 2 (t%4), 2 (t%4) + 1 of
@@ -902,8 +905,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       }
     }
     } else if constexpr (BULK && S == 4) {
-    // The rotation of FP32 bands with several chunks per tile (complex bands, or more than KC
-    // bands): one tile per CTA, the chunks' five orders summed into double-float accumulators,
+    // The rotation of FP32 bands with several chunks per tile (more than 512 contraction
+    // values: complex bands beyond 256, real bands beyond 512): one tile per CTA, the chunks' five orders summed into double-float accumulators,
     // then one write-out with FP32 values rounded once from the double-float sums.  TMEM is
     // read in the 16 x 256-bit shape (as in the one-chunk form): thread t holds rows t/4 and
     // t/4 + 8 of each 16-lane half and columns 2 (t%4), 2 (t%4) + 1 of each 8-column group, so

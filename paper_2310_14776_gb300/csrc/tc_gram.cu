@@ -365,8 +365,8 @@ __global__ void rot_operand_kernel(const double* __restrict__ C, int nb, int nou
 }
 
 // the transposed digits of psi for the rotation, one block of grid points r0 .. r0 + rcount
-template <class R, int S>
-void rc_slice_psi(pawfd_ctx* c, const R* psi, int nb, long long r0, int rcount, int nch) {
+template <class R, int S, int KCH>
+void rc_slice_psi_kc(pawfd_ctx* c, const R* psi, int nb, long long r0, int rcount, int nch) {
   TcScratch& t = c->tc;
   const bool cplx = is_complex(c);
   const long long K = (long long)c->K;
@@ -376,19 +376,25 @@ void rc_slice_psi(pawfd_ctx* c, const R* psi, int nb, long long r0, int rcount, 
   constexpr int v16 = 16 / (int)sizeof(R);
   const int per = cplx ? 2 : 1;
   const int vec16 = (per * K) % v16 == 0 && (per * r0) % v16 == 0 && (reinterpret_cast<uintptr_t>(psi) & 15) == 0;
-  sg::slice_t_kernel<R, S><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R>(), c->stream>>>(
+  sg::slice_t_kernel<R, S, KCH><<<std::min(stiles, t.slice_t_ctas), 256, sg::slice_t_smem<R, KCH>(), c->stream>>>(
       psi, nb, K, cplx, r0, rcount, t.rot_Lc, (int)t.rot_rblk, (__nv_bfloat16*)t.rotSlicesB, t.rotSigB,
       (int)t.rot_rblk, t.rotMaxB, nch, vec16);
 }
 
-template <class R, int S, int ORD>
-int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, R* out) {
+template <class R, int S>
+void rc_slice_psi(pawfd_ctx* c, const R* psi, int nb, long long r0, int rcount, int nch) {
+  if (c->tc.rot_kc == sg::KCG) rc_slice_psi_kc<R, S, sg::KCG>(c, psi, nb, r0, rcount, nch);
+  else rc_slice_psi_kc<R, S, sg::KC>(c, psi, nb, r0, rcount, nch);
+}
+
+template <class R, int S, int ORD, int KCH>
+int tc_rotate_kc(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, R* out) {
   TcScratch& t = c->tc;
   const bool cplx = is_complex(c);
   const int rowsA = cplx ? 2 * nout : nout;
   const long long Lk = (long long)nb * (cplx ? 2 : 1);
-  const long long Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
-  const int nch = (int)(Lc / sg::KC);
+  const long long Lc = (Lk + KCH - 1) / KCH * KCH;
+  const int nch = (int)(Lc / KCH);
   if (Lc > t.rot_Lc) return fail(c, PAWFD_EINVAL, "rotation scratch too small");
   const long long K = (long long)c->K;
   // operand A from C, then its digits
@@ -396,7 +402,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
       C, nb, nout, cplx, (double*)t.rotA, t.rot_Lc, t.rot_rowsA_alloc);
   cudaMemsetAsync(t.rotMaxA, 0x80, sizeof(int) * t.rot_rowsA_alloc, c->stream);
   {
-    sg::slice_rg_kernel<double, S><<<(unsigned)(((rowsA + 7) / 8 * (long long)nch + 7) / 8), 256, 0, c->stream>>>(
+    sg::slice_rg_kernel<double, S, KCH><<<(unsigned)(((rowsA + 7) / 8 * (long long)nch + 7) / 8), 256, 0, c->stream>>>(
         (const double*)t.rotA, rowsA, t.rot_Lc, Lk, nch, t.rot_Lc, false, 0, t.rot_rowsA_alloc,
         (__nv_bfloat16*)t.rotSlicesA, t.rotSigA, t.rot_rowsA_alloc, t.rotMaxA);
   }
@@ -408,7 +414,7 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
   for (long long r0 = 0; r0 < K; r0 += t.rot_rblk) {
     const int rcount = (int)std::min<long long>(t.rot_rblk, K - r0);
     if (!presliced) {
-      rc_slice_psi<R, S>(c, psi, nb, r0, rcount, nch);
+      rc_slice_psi_kc<R, S, KCH>(c, psi, nb, r0, rcount, nch);
       c->launches += 1;
     }
     sg::GramArgs a = {};
@@ -444,15 +450,21 @@ int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout
     a.klen = Lk;
     a.rot_tiles = tilesM * a.tilesN;
     if (nch == 1)   // persistent CTAs, one per SM (the kernel's shared memory admits one)
-      sg::sliced_gram_kernel<S, ORD, true, true, sg::KC>
+      sg::sliced_gram_kernel<S, ORD, true, true, KCH>
           <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB,
                                                                                                         a);
     else
-      sg::sliced_gram_kernel<S, ORD, false, true, sg::KC>
+      sg::sliced_gram_kernel<S, ORD, false, true, KCH>
           <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, a);
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
+}
+
+template <class R, int S, int ORD>
+int tc_rotate_impl(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, R* out) {
+  if (c->tc.rot_kc == sg::KCG) return tc_rotate_kc<R, S, ORD, sg::KCG>(c, psi, nb, C, nout, out);
+  return tc_rotate_kc<R, S, ORD, sg::KC>(c, psi, nb, C, nout, out);
 }
 
 }  // namespace
@@ -488,9 +500,9 @@ bool rotate_slice_psi(pawfd_ctx* c, const void* psi, int nb) {
   TcScratch& t = c->tc;
   if (!c->use_tc || !t.ready || t.rot_rblk < (long long)c->K) return false;
   const long long Lk = (long long)nb * (is_complex(c) ? 2 : 1);
-  const long long Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
+  const long long Lc = (Lk + t.rot_kc - 1) / t.rot_kc * t.rot_kc;
   if (Lc > t.rot_Lc) return false;
-  const int nch = (int)(Lc / sg::KC);
+  const int nch = (int)(Lc / t.rot_kc);
   if (is_fp32(c)) rc_slice_psi<float, 4>(c, (const float*)psi, nb, 0, (int)c->K, nch);
   else rc_slice_psi<double, 7>(c, (const double*)psi, nb, 0, (int)c->K, nch);
   c->launches += 1;
@@ -599,11 +611,15 @@ int setup_tc(pawfd_ctx* c) {
     // persistent one-chunk form and general form)
     const void* fns7[] = {(const void*)sg::sliced_gram_kernel<7, 6, false, false, sg::KCG>,
                           (const void*)sg::sliced_gram_kernel<7, 6, true, true, sg::KC>,
-                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KC>};
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KC>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, true, true, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KCG>};
     const void* fns4[] = {(const void*)sg::sliced_gram_kernel<4, 4, false, false, sg::KCG>,
                           (const void*)sg::sliced_gram_kernel<4, 4, true, true, sg::KC>,
-                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KC>};
-    for (int f = 0; f < 3 && rc == PAWFD_OK; ++f)
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KC>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, true, true, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KCG>};
+    for (int f = 0; f < 5 && rc == PAWFD_OK; ++f)
       rc = check_cuda(c, cudaFuncSetAttribute(S == 7 ? fns7[f] : fns4[f], smem_attr,
                                               S == 7 ? sg::smem_bytes<7>() : sg::smem_bytes<4>()),
                       "smem attribute");
@@ -611,14 +627,15 @@ int setup_tc(pawfd_ctx* c) {
   // rotation scratch: operand A (from C) and its digits, digits of a block of grid points
   if (rc == PAWFD_OK) {
     const long long Lk = (long long)nb * (cplx ? 2 : 1);
-    t.rot_Lc = (Lk + sg::KC - 1) / sg::KC * sg::KC;
+    t.rot_kc = Lk > sg::KC ? sg::KCG : sg::KC;
+    t.rot_Lc = (Lk + t.rot_kc - 1) / t.rot_kc * t.rot_kc;
     t.rot_rowsA_alloc = ((cplx ? 2 * nb : nb) + sg::BM - 1) / sg::BM * sg::BM;
     const long long Kpad = ((long long)c->K + sg::BN - 1) / sg::BN * sg::BN;
     // bytes of grid-point digits per block
     const long long budget = c->tc_scratch_mb > 0 ? ((long long)c->tc_scratch_mb << 20) : (512ll << 20);
     long long rblk = budget / ((long long)S * t.rot_Lc * 2) / sg::BN * sg::BN;
     t.rot_rblk = std::max<long long>(sg::BN, std::min(rblk, Kpad));
-    const int nchr = (int)(t.rot_Lc / sg::KC);
+    const int nchr = (int)(t.rot_Lc / t.rot_kc);
     const size_t a_bytes = sizeof(double) * t.rot_rowsA_alloc * t.rot_Lc;
     const size_t sa_bytes = (size_t)S * t.rot_rowsA_alloc * t.rot_Lc * 2;
     const size_t sb_bytes = (size_t)S * t.rot_rblk * t.rot_Lc * 2;
@@ -632,16 +649,17 @@ int setup_tc(pawfd_ctx* c) {
     if (rc != PAWFD_OK) return fail(c, PAWFD_ENOMEM, c->err);
     // persistent transposing slicer: as many CTAs as fit at once
     if (rc == PAWFD_OK) {
-      const void* fn = S == 7 ? (const void*)sg::slice_t_kernel<double, 7> : (const void*)sg::slice_t_kernel<float, 4>;
-      const int smem = S == 7 ? sg::slice_t_smem<double>() : sg::slice_t_smem<float>();
+      const bool lk = t.rot_kc == sg::KCG;
+      const void* fn = S == 7 ? (lk ? (const void*)sg::slice_t_kernel<double, 7, sg::KCG>
+                                    : (const void*)sg::slice_t_kernel<double, 7, sg::KC>)
+                              : (lk ? (const void*)sg::slice_t_kernel<float, 4, sg::KCG>
+                                    : (const void*)sg::slice_t_kernel<float, 4, sg::KC>);
+      const int smem = S == 7 ? (lk ? sg::slice_t_smem<double, sg::KCG>() : sg::slice_t_smem<double, sg::KC>())
+                              : (lk ? sg::slice_t_smem<float, sg::KCG>() : sg::slice_t_smem<float, sg::KC>());
       rc = check_cuda(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem), "smem attribute");
       int per_sm = 0;
       if (rc == PAWFD_OK)
-        rc = check_cuda(c, S == 7 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sg::slice_t_kernel<double, 7>,
-                                                                                  256, smem)
-                                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sg::slice_t_kernel<float, 4>,
-                                                                                  256, smem),
-                        "occupancy");
+        rc = check_cuda(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem), "occupancy");
       t.slice_t_ctas = std::max(1, per_sm) * c->num_sms;
     }
     if (rc == PAWFD_OK) rc = check_cuda(c, cudaMemset(t.rotSlicesA, 0, sa_bytes), "memset");

@@ -208,6 +208,37 @@ def test_scratch_size_changes_blocks_not_results(dev, precision, cplx):
         assert_close_bands(out[4096][2], O.rotate(psi_np, C), nb)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("cplx,nb", [(False, 200), (False, 300), (False, 600), (True, 100), (True, 200),
+                                     (True, 300)])
+def test_rotation_chunk_lengths(dev, precision, cplx, nb):
+    """The rotation cuts its contraction (nb bands, 2 nb real values for complex bands) into
+    one chunk of 256 when it is no longer than that, else into chunks of 512: one chunk of 256
+    (persistent form), one chunk of 512 (persistent form), and 600 values as a full chunk and
+    a ragged one (one tile per CTA).  Rotated bands against the oracle: FP64 to 1e-12 per
+    band; FP32 bands to the rounding bound (nb + 2) u || |psi| |C| || per band (FP32 inputs
+    rounded once, the exact digit products, one FP32 rounding of each output)."""
+    from paper_2310_14776_gb300 import api
+    k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((20, 18, 15), (6.0, 5.5, 4.6), 3, synth.PSET_SP, seed=531, k=k, complex_wf=cplx)
+    ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+    psi = to_dev(synth.make_psi(s, nb, 532), dev).to(ctx.dtype)
+    rng = np.random.default_rng(533)
+    C = np.linalg.qr(rng.standard_normal((nb, nb)))[0]
+    if cplx:
+        C = C * np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, (1, nb)))
+    rot = ctx.rotate(psi, to_dev(C, dev)).cpu().numpy()
+    psi_np = psi.cpu().numpy().astype(np.complex128 if cplx else np.float64)
+    ref = O.rotate(psi_np, C)
+    if precision == "fp64":
+        assert_close_bands(rot, ref, nb)
+    else:
+        bound = (nb + 2) * 2.0 ** -24 * np.linalg.norm(np.abs(psi_np).reshape(nb, -1).T @ np.abs(C), axis=0)
+        err = np.linalg.norm((rot.astype(ref.dtype) - ref).reshape(nb, -1), axis=1)
+        assert np.all(err <= bound), (err / bound).max()
+    ctx.close()
+
+
 @pytest.mark.parametrize("cplx", [False, True])
 def test_hermitian_gram_equals_full_gram(dev, cplx):
     k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
