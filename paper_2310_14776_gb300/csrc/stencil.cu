@@ -157,12 +157,16 @@ int launch_kinetic_local_f32x4(pawfd_ctx* c, const float* psi, int nb, float* ou
 int launch_kinetic_local_ring(pawfd_ctx* c, const float* psi, int nb, float* out, float* cpy);
 int launch_kinetic_local_ring_c(pawfd_ctx* c, const zf* psi, int nb, zf* out, zf* cpy);
 int launch_kinetic_local_fx(pawfd_ctx* c, const double* psi, int nb, double* out, double* cpy);
+int launch_kinetic_local_fx_c(pawfd_ctx* c, const zd* psi, int nb, zd* out, zd* cpy);
 
 // out = (-1/2 Lap + v) psi; with cpy != null the kernels also write psi to cpy (the first term
 // of S psi = psi + sum |p> dS <p|psi>), which saves the separate copy pass
 int launch_kinetic_local(pawfd_ctx* c, const void* psi, int nb, void* out, void* cpy) {
   if (c->dtype == PAWFD_R64 && c->stencil_fx && c->fast_stencil &&
       launch_kinetic_local_fx(c, (const double*)psi, nb, (double*)out, (double*)cpy) == PAWFD_OK)
+    return PAWFD_OK;
+  if (c->dtype == PAWFD_C128 && c->stencil_fx && c->fast_stencil &&
+      launch_kinetic_local_fx_c(c, (const zd*)psi, nb, (zd*)out, (zd*)cpy) == PAWFD_OK)
     return PAWFD_OK;
   if (c->dtype == PAWFD_R32 && c->fast_stencil) {
     if (c->stencil_variant != 1 &&

@@ -1,4 +1,5 @@
-// stencil_fx.cu -- kinetic + local kernel for real FP64 bands in exact fixed-point arithmetic.
+// stencil_fx.cu -- kinetic + local kernel for FP64 bands (real, and complex Bloch bands) in exact
+// fixed-point arithmetic.
 //
 // Same operator as stencil.cu (order-6 central second difference per axis, periodic wrap,
 // fused local potential; Eq. (dh) of the PAW section), for real FP64 band arrays.  GB300
@@ -267,6 +268,263 @@ __global__ void __launch_bounds__(NTHR) kinetic_local_fx_kernel(const double* __
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Complex (Bloch) FP64 bands: the same fixed-point scheme on the real and imaginary parts (the
+// stencil's weights are real).  A neighbour that leaves the cell across face c carries the
+// Bloch factor exp(+-i k_c L_c) (at most one crossing per index on the grids this tiling
+// admits); it is applied in FP64 before the value is rounded to the slab's grid.  A rotated
+// component can exceed the slab's largest component by up to a factor sqrt(2), so the grid
+// unit is taken one exponent step higher, 2^(ebp - 1073) with ebp = eb + 1: |q| <= 2^51
+// still holds, and every input is rounded once to within 2^(eb - 1073), twice the real
+// kernel's half unit.  Slabs holding an infinity or NaN, or values within a factor 2 of the
+// top of the FP64 range (where a rotation could overflow), are computed in plain FP64.
+
+struct FXCArgs {
+  int n1, n2, n3;
+  long long K;
+  double cs[3];        // -1 / (360 h_c^2)
+  double ih2[3];       // 1 / h_c^2 (plain FP64 path)
+  zd ph[3];            // exp(i k_c L_c)
+  const double* v;     // v(r), FP64
+  int zchunk, nzc;
+  zd* cpy;             // optional copy of psi (first band of this launch), or null
+};
+
+__device__ __forceinline__ zd ldz(const zd* p) {
+  const double2 t = __ldg((const double2*)p);
+  return zd{t.x, t.y};
+}
+__device__ __forceinline__ void stz(zd* p, zd v) { *(double2*)p = make_double2(v.re, v.im); }
+
+// -1, 0 or +1: the face an index at most one period outside [0, n) has crossed
+__device__ __forceinline__ int crossing(int i, int n) { return i < 0 ? -1 : (i >= n ? 1 : 0); }
+
+// the Bloch factor of the crossings t1, t2, t3
+__device__ __forceinline__ zd bloch(int t1, int t2, int t3, const FXCArgs& a) {
+  zd f = {1.0, 0.0};
+  if (t1) f = f * (t1 > 0 ? a.ph[0] : conjx(a.ph[0]));
+  if (t2) f = f * (t2 > 0 ? a.ph[1] : conjx(a.ph[1]));
+  if (t3) f = f * (t3 > 0 ? a.ph[2] : conjx(a.ph[2]));
+  return f;
+}
+
+__device__ void fp64_slab_c(const zd* __restrict__ src, zd* __restrict__ dst, zd* __restrict__ cp, int x, int y,
+                            int z0, int z1, const FXCArgs& a) {
+  constexpr double w1 = 270.0 / 180.0, w2 = -27.0 / 180.0, w3 = 2.0 / 180.0, w0 = -490.0 / 180.0;
+  auto at = [&](int u1, int u2, int u3) -> zd {
+    const int t1 = crossing(u1, a.n1), t2 = crossing(u2, a.n2), t3 = crossing(u3, a.n3);
+    const zd v = src[((long long)wrap1(u3, a.n3) * a.n2 + wrap1(u2, a.n2)) * a.n1 + wrap1(u1, a.n1)];
+    return (t1 | t2 | t3) ? v * bloch(t1, t2, t3, a) : v;
+  };
+  for (int z = z0; z < z1; ++z) {
+    const long long r = ((long long)z * a.n2 + y) * a.n1 + x;
+    const zd c = src[r];
+    auto axis = [&](zd p1, zd m1, zd p2, zd m2, zd p3, zd m3) -> zd {
+      return zd{w0 * c.re + w1 * (p1.re + m1.re) + w2 * (p2.re + m2.re) + w3 * (p3.re + m3.re),
+                w0 * c.im + w1 * (p1.im + m1.im) + w2 * (p2.im + m2.im) + w3 * (p3.im + m3.im)};
+    };
+    const zd lx = axis(at(x + 1, y, z), at(x - 1, y, z), at(x + 2, y, z), at(x - 2, y, z), at(x + 3, y, z),
+                       at(x - 3, y, z));
+    const zd ly = axis(at(x, y + 1, z), at(x, y - 1, z), at(x, y + 2, z), at(x, y - 2, z), at(x, y + 3, z),
+                       at(x, y - 3, z));
+    const zd lz = axis(at(x, y, z + 1), at(x, y, z - 1), at(x, y, z + 2), at(x, y, z - 2), at(x, y, z + 3),
+                       at(x, y, z - 3));
+    const double vr = a.v[r];
+    dst[r] = zd{vr * c.re - 0.5 * (a.ih2[0] * lx.re + a.ih2[1] * ly.re + a.ih2[2] * lz.re),
+                vr * c.im - 0.5 * (a.ih2[0] * lx.im + a.ih2[1] * ly.im + a.ih2[2] * lz.im)};
+    if (cp) cp[r] = c;
+  }
+}
+
+// 180 x the order-6 second differences of one part at the thread's point: the cubic-cell sum
+// over the three axes, or the per-axis sums (Sx, Sy, Sz)
+__device__ __forceinline__ long long fx_sum_cubic(const long long (*T)[SX], int ty, int tx, const long long* q) {
+  const long long* row = &T[ty + HALO][tx + HALO];
+  const long long V1 = (row[1] + row[-1]) + (T[ty + HALO + 1][tx + HALO] + T[ty + HALO - 1][tx + HALO]) + (q[4] + q[2]);
+  const long long V2 = (row[2] + row[-2]) + (T[ty + HALO + 2][tx + HALO] + T[ty + HALO - 2][tx + HALO]) + (q[5] + q[1]);
+  const long long V3 = (row[3] + row[-3]) + (T[ty + HALO + 3][tx + HALO] + T[ty + HALO - 3][tx + HALO]) + (q[6] + q[0]);
+  return 270ll * V1 - 27ll * V2 + 2ll * V3 - 1470ll * q[3];
+}
+__device__ __forceinline__ void fx_sum_axes(const long long (*T)[SX], int ty, int tx, const long long* q, long long& Sx,
+                                            long long& Sy, long long& Sz) {
+  const long long* row = &T[ty + HALO][tx + HALO];
+  const long long c490 = 490ll * q[3];
+  Sx = 270ll * (row[1] + row[-1]) - 27ll * (row[2] + row[-2]) + 2ll * (row[3] + row[-3]) - c490;
+  Sy = 270ll * (T[ty + HALO + 1][tx + HALO] + T[ty + HALO - 1][tx + HALO]) -
+       27ll * (T[ty + HALO + 2][tx + HALO] + T[ty + HALO - 2][tx + HALO]) +
+       2ll * (T[ty + HALO + 3][tx + HALO] + T[ty + HALO - 3][tx + HALO]) - c490;
+  Sz = 270ll * (q[4] + q[2]) - 27ll * (q[5] + q[1]) + 2ll * (q[6] + q[0]) - c490;
+}
+
+// Requires N1 >= TX + 2 HALO + 2, N2 >= TY + 2 HALO, N3 >= HALO (one crossing per index) and
+// 16-byte aligned band arrays.
+template <bool CUBIC>
+__global__ void __launch_bounds__(NTHR) kinetic_local_fx_c_kernel(const zd* __restrict__ psi, zd* __restrict__ out,
+                                                                    FXCArgs a) {
+  __shared__ long long tile[2][2][SY][SX];   // [buffer][real / imaginary part]
+  __shared__ int s_emax[NTHR / 32];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
+  const int band = blockIdx.z / a.nzc, zc = blockIdx.z % a.nzc;
+  const int z0 = zc * a.zchunk;
+  const int z1 = min(z0 + a.zchunk, a.n3);
+  const zd* __restrict__ src = psi + (long long)band * a.K;
+  zd* __restrict__ dst = out + (long long)band * a.K;
+  zd* __restrict__ cp = a.cpy ? a.cpy + (long long)band * a.K : nullptr;
+  const int x = X0 + tx, y = Y0 + ty;
+  const bool active = x < a.n1 && y < a.n2;
+  const long long plane = (long long)a.n1 * a.n2;
+  // this thread's column (its x, y faces crossed when it lies past the cell's edge) and halo
+  // cells, as wrapped offsets within a plane with their Bloch factors
+  const long long own = (long long)wrap1(y, a.n2) * a.n1 + wrap1(x, a.n1);
+  const int ox = crossing(x, a.n1), oy = crossing(y, a.n2);
+  const zd f0 = bloch(ox, oy, 0, a), fp = bloch(ox, oy, 1, a), fm = bloch(ox, oy, -1, a);
+  const bool oxy = (ox | oy) != 0;
+  int hy[HPER], hx[HPER];
+  long long hoff[HPER];
+  zd hph[HPER];
+  bool hwrap[HPER];
+#pragma unroll
+  for (int k = 0; k < HPER; ++k) {
+    const int h = tid + k * NTHR;
+    hph[k] = zd{1.0, 0.0};
+    hwrap[k] = false;
+    if (h < HCELLS) {
+      halo_cell(h, hy[k], hx[k]);
+      const int u1 = X0 - HALO + hx[k], u2 = Y0 - HALO + hy[k];
+      hoff[k] = (long long)wrap1(u2, a.n2) * a.n1 + wrap1(u1, a.n1);
+      const int t1 = crossing(u1, a.n1), t2 = crossing(u2, a.n2);
+      hwrap[k] = (t1 | t2) != 0;
+      if (hwrap[k]) hph[k] = bloch(t1, t2, 0, a);
+    } else {
+      hy[k] = hx[k] = -1;
+      hoff[k] = 0;
+    }
+  }
+
+  // 1. the largest exponent field of the parts the slab reads
+  int emax = 0;
+  for (int z = z0 - HALO; z < z1 + HALO; ++z) {
+    const zd* p = src + (long long)wrap1(z, a.n3) * plane;
+    const zd v = ldz(p + own);
+    emax = max(emax, max(exp_field(v.re), exp_field(v.im)));
+    if (z >= z0 && z < z1) {
+#pragma unroll
+      for (int k = 0; k < HPER; ++k)
+        if (hy[k] >= 0) {
+          const zd w = ldz(p + hoff[k]);
+          emax = max(emax, max(exp_field(w.re), exp_field(w.im)));
+        }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if ((tid & 31) == 0) s_emax[tid >> 5] = emax;
+  __syncthreads();
+  int eb = 0;
+#pragma unroll
+  for (int w = 0; w < NTHR / 32; ++w) eb = max(eb, s_emax[w]);
+  if (eb >= 0x7FE) {   // non-finite values, or a rotation could overflow: plain FP64
+    if (active) fp64_slab_c(src, dst, cp, x, y, z0, z1, a);
+    return;
+  }
+  const int ebp = max(eb, 1) + 1;
+  const bool folded = ebp >= 128;
+  const double unit = ldexp(1.0, ebp - 1073);
+  double cs[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) cs[c] = folded ? a.cs[c] * unit : a.cs[c];
+  // the own column's value of plane u3 on the grid: Bloch factor of the crossed faces, then
+  // rounded
+  auto own_fixed = [&](zd v, int u3, long long& qr, long long& qi) {
+    const int t3 = crossing(u3, a.n3);
+    if (oxy || t3) v = v * (t3 == 0 ? f0 : (t3 > 0 ? fp : fm));
+    qr = to_fixed(v.re, ebp);
+    qi = to_fixed(v.im, ebp);
+  };
+
+  // 2. the march along z: qr / qi[j] hold plane z - 3 + j of this thread's column, raw[j] the
+  //    FP64 values of planes z .. z + 3
+  long long qr[7], qi[7];
+  zd raw[4];
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    const int u3 = z0 - 3 + j;
+    const zd val = ldz(src + (long long)wrap1(u3, a.n3) * plane + own);
+    own_fixed(val, u3, qr[j + 1], qi[j + 1]);
+    if (j >= 3) raw[j - 2] = val;
+  }
+  zd hv[HPER];
+#pragma unroll
+  for (int k = 0; k < HPER; ++k)
+    if (hy[k] >= 0) hv[k] = ldz(src + (long long)z0 * plane + hoff[k]);
+
+  int buf = 0;
+  for (int z = z0; z < z1; ++z) {
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      qr[j] = qr[j + 1];
+      qi[j] = qi[j + 1];
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) raw[j] = raw[j + 1];
+    raw[3] = ldz(src + (long long)wrap1(z + 3, a.n3) * plane + own);
+    own_fixed(raw[3], z + 3, qr[6], qi[6]);
+    long long(*TR)[SX] = tile[buf][0];
+    long long(*TI)[SX] = tile[buf][1];
+    TR[ty + HALO][tx + HALO] = qr[3];
+    TI[ty + HALO][tx + HALO] = qi[3];
+#pragma unroll
+    for (int k = 0; k < HPER; ++k)
+      if (hy[k] >= 0) {
+        const zd w = hwrap[k] ? hv[k] * hph[k] : hv[k];
+        TR[hy[k]][hx[k]] = to_fixed(w.re, ebp);
+        TI[hy[k]][hx[k]] = to_fixed(w.im, ebp);
+      }
+    __syncthreads();
+    if (z + 1 < z1) {
+#pragma unroll
+      for (int k = 0; k < HPER; ++k)
+        if (hy[k] >= 0) hv[k] = ldz(src + (long long)(z + 1) * plane + hoff[k]);
+    }
+    if (active) {
+      const long long r = (long long)z * plane + (long long)y * a.n1 + x;
+      const double vv = __ldg(a.v + r);
+      const double vr = vv * raw[0].re, vi = vv * raw[0].im;
+      double rre, rim;
+      if (CUBIC) {
+        const long long Sr = fx_sum_cubic(TR, ty, tx, qr), Si = fx_sum_cubic(TI, ty, tx, qi);
+        if (folded) {
+          rre = fma(i64_to_f64(Sr), cs[0], vr);
+          rim = fma(i64_to_f64(Si), cs[0], vi);
+        } else {
+          rre = fma(i64_to_f64(Sr) * cs[0], unit, vr);
+          rim = fma(i64_to_f64(Si) * cs[0], unit, vi);
+        }
+      } else {
+        long long Sx, Sy, Sz;
+        fx_sum_axes(TR, ty, tx, qr, Sx, Sy, Sz);
+        if (folded) {
+          rre = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vr)));
+        } else {
+          const double t = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], i64_to_f64(Sz) * cs[2]));
+          rre = fma(t, unit, vr);
+        }
+        fx_sum_axes(TI, ty, tx, qi, Sx, Sy, Sz);
+        if (folded) {
+          rim = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vi)));
+        } else {
+          const double t = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], i64_to_f64(Sz) * cs[2]));
+          rim = fma(t, unit, vi);
+        }
+      }
+      stz(dst + r, zd{rre, rim});
+      if (cp) stz(cp + r, raw[0]);
+    }
+    buf ^= 1;
+  }
+}
+
 }  // namespace
 
 // Real FP64 contexts on grids the tile fits (one wrap per index); EINVAL otherwise.
@@ -307,6 +565,48 @@ int launch_kinetic_local_fx(pawfd_ctx* c, const double* psi, int nb, double* out
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "kinetic_local fixed-point launch");
+}
+
+// Complex FP64 (Bloch) contexts on grids the tile fits, with 16-byte aligned band arrays;
+// EINVAL otherwise.
+int launch_kinetic_local_fx_c(pawfd_ctx* c, const zd* psi, int nb, zd* out, zd* cpy) {
+  if (c->dtype != PAWFD_C128 || !c->d_vloc) return PAWFD_EINVAL;
+  if (c->n[0] < TX + 2 * HALO + 2 || c->n[1] < TY + 2 * HALO || c->n[2] < HALO) return PAWFD_EINVAL;
+  if (((uintptr_t)psi | (uintptr_t)out | (uintptr_t)cpy) & 15) return PAWFD_EINVAL;
+  FXCArgs a;
+  a.n1 = c->n[0];
+  a.n2 = c->n[1];
+  a.n3 = c->n[2];
+  a.K = (long long)c->K;
+  for (int cc = 0; cc < 3; ++cc) {
+    a.ih2[cc] = 1.0 / (c->h[cc] * c->h[cc]);
+    a.cs[cc] = -1.0 / (360.0 * c->h[cc] * c->h[cc]);
+    const double kl = c->k[cc] * c->cell[cc];
+    a.ph[cc] = zd{cos(kl), sin(kl)};
+  }
+  a.v = (const double*)c->d_vloc;
+  const bool cubic = c->h[0] == c->h[1] && c->h[1] == c->h[2];
+  const int gx = (a.n1 + TX - 1) / TX, gy = (a.n2 + TY - 1) / TY;
+  const long long tiles = (long long)gx * gy;
+  const long long per_sm = c->stencil_zsplit > 0 ? c->stencil_zsplit : 4;
+  const long long want = std::max<long long>((per_sm * c->num_sms + tiles * nb - 1) / (tiles * nb),
+                                             (a.n3 + ZSLAB - 1) / ZSLAB);
+  const int nzc = (int)std::max(1ll, std::min<long long>(want, (a.n3 + 3) / 4));
+  a.zchunk = (a.n3 + nzc - 1) / nzc;
+  a.nzc = (a.n3 + a.zchunk - 1) / a.zchunk;
+  const int bands_per_launch = std::max(1, 65535 / a.nzc);
+  for (int b0 = 0; b0 < nb; b0 += bands_per_launch) {
+    const int nbl = std::min(bands_per_launch, nb - b0);
+    dim3 grid(gx, gy, nbl * a.nzc), block(TX, TY);
+    a.cpy = cpy ? cpy + (size_t)b0 * c->K : nullptr;
+    if (cubic)
+      kinetic_local_fx_c_kernel<true><<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K, out + (size_t)b0 * c->K, a);
+    else
+      kinetic_local_fx_c_kernel<false><<<grid, block, 0, c->stream>>>(psi + (size_t)b0 * c->K,
+                                                                      out + (size_t)b0 * c->K, a);
+    c->launches += 1;
+  }
+  return check_cuda(c, cudaGetLastError(), "kinetic_local complex fixed-point launch");
 }
 
 }  // namespace pawfd

@@ -311,6 +311,66 @@ def test_fixed_point_stencil_special_values(dev):
     assert np.max(np.abs(got[4][fin] - ref[4][fin])) <= 1e-12 * np.max(np.abs(ref[4][fin]))
 
 
+@pytest.mark.parametrize("n,cell", [((45, 19, 13), None), ((96, 40, 10), None), ((40, 14, 3), None),
+                                    ((48, 16, 12), (9.6, 3.2, 2.4))])
+def test_fixed_point_stencil_complex_matches_fp64_arithmetic(dev, n, cell):
+    # complex Bloch bands in exact fixed point (the Bloch factor applied before rounding to the
+    # slab's grid) against the FP64-pipe kernel and the oracle: per band within 1e-13 of the
+    # band norm; the grids cover ragged x and y tiles, every z neighbour wrapping (N3 = 3) and
+    # a cubic cell (one integer sum over the three axes)
+    from paper_2310_14776_gb300 import api
+    cell = cell if cell is not None else tuple(0.21 * v for v in n)
+    s = synth.make_system(n, cell, 2, synth.PSET_SP, seed=334, k=(0.37, -0.61, 0.23), complex_wf=True)
+    nb = 5
+    ctx = api.Context(s, max_bands=nb, device=dev, precision="fp64")
+    psi_np = synth.make_psi(s, nb, 335)
+    psi = to_dev(psi_np, dev)
+    ctx.set_option("stencil_fx", 1)
+    a = ctx.kinetic_local(psi).clone()
+    ctx.set_option("stencil_fx", 0)
+    b = ctx.kinetic_local(psi).clone()
+    ctx.sync()
+    d = (a - b).reshape(nb, -1).norm(dim=1) / b.reshape(nb, -1).norm(dim=1)
+    assert d.max().item() <= 1e-13, d.max().item()
+    ref = O.kinetic_local(s, psi_np)
+    e = np.linalg.norm((a.cpu().numpy() - ref).reshape(nb, -1), axis=1) / np.linalg.norm(ref.reshape(nb, -1), axis=1)
+    assert e.max() <= 1e-13, e.max()
+    ctx.close()
+
+
+def test_fixed_point_stencil_complex_special_values(dev):
+    # complex bands: zeros, subnormal values, large values (1e300 and 1e305, whose grid unit
+    # sits one exponent step above the largest part), one spike in a zero band, and an
+    # infinity and a NaN (plain FP64, propagated as in the oracle)
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((44, 16, 9), (9.2, 3.4, 1.9), 2, synth.PSET_SP, seed=336, k=(0.3, -0.4, 0.5),
+                          complex_wf=True)
+    base = synth.make_psi(s, 6, 337)
+    psi = np.zeros_like(base)
+    psi[1] = base[1] * 1e-310
+    psi[2] = base[2] * 1e300
+    psi[3, 4, 7, 20] = 3.5 - 1.25j
+    psi[4] = base[4]
+    psi[4, 2, 3, 5] = np.inf
+    psi[4, 6, 12, 30] = complex(0.5, np.nan)
+    psi[5] = base[5] * 1e305 / np.max(np.abs(base[5]))
+    ctx = api.Context(s, max_bands=6, device=dev, precision="fp64")
+    got = ctx.kinetic_local(to_dev(psi, dev)).cpu().numpy()
+    ctx.close()
+    with np.errstate(invalid="ignore", over="ignore"):
+        ref = O.kinetic_local(s, psi)
+    assert np.array_equal(got[0], np.zeros_like(got[0]))
+    for n, bar in ((1, 1e-12), (2, 1e-13), (3, 1e-13), (5, 1e-13)):
+        err = np.max(np.abs(got[n] - ref[n])) / np.max(np.abs(ref[n]))
+        assert err <= bar, (n, err)
+    # the same non-finite pattern and the finite values to the FP64 bar; whether a non-finite
+    # part is an infinity or a NaN is not compared: the oracle multiplies every term by its
+    # Bloch factor, also by 1 + 0i inside the cell, and 0 x inf makes a NaN part there
+    fin = np.isfinite(ref[4])
+    assert np.array_equal(np.isfinite(got[4]), fin)
+    assert np.max(np.abs(got[4][fin] - ref[4][fin])) <= 1e-12 * np.max(np.abs(ref[4][fin]))
+
+
 @pytest.mark.parametrize("case", [((45, 19, 13), 6, 5), ((30, 28, 26), 9, 40)])
 def test_double_float_projectors_match_fp64_arithmetic(dev, case):
     """Real FP64 projections and nonlocal back-adds in double-float pairs (the default) against
