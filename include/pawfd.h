@@ -147,11 +147,12 @@ int pawfd_kernel_timing(pawfd_ctx* ctx, int enable, double* total_ms, long long*
  *                     Waits for the context's stream, then frees and re-allocates the scratch;
  *                     on an allocation failure returns PAWFD_ENOMEM and turns the tensor-core
  *                     path off.
- *   "stencil_fx"      1 (default): the real FP64 stencil computes the order-6 sums exactly in
- *                     64-bit integers on the band slab's FP64 grid (inputs rounded once to
- *                     that grid, the integer sum rounded once to FP64), the FP64 pipe only for
- *                     the scaling and v psi; 0: FP64 arithmetic.  "stencil_variant" 2 also
- *                     selects FP64.
+ *   "stencil_fx"      1 (default): the FP64 stencil (real bands, and complex Bloch bands in
+ *                     16-byte aligned arrays) computes the order-6 sums exactly in 64-bit
+ *                     integers on the band slab's FP64 grid (inputs rounded once to that grid,
+ *                     Bloch factors of wrapped neighbours applied before that rounding, the
+ *                     integer sum rounded once to FP64), the FP64 pipe only for the scaling
+ *                     and v psi; 0: FP64 arithmetic.  "stencil_variant" 2 also selects FP64.
  *   "nonlocal_df"     1 (default): for real FP64 bands the projections and the nonlocal
  *                     back-add compute in double-float FP32 pairs (runs of 32 terms, then FP64
  *                     sums); 0: FP64 arithmetic.
