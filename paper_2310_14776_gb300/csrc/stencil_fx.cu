@@ -308,6 +308,17 @@ __device__ __forceinline__ zd bloch(int t1, int t2, int t3, const FXCArgs& a) {
   return f;
 }
 
+// v times the Bloch factor of the crossings (t1, t2, t3).  Out of line: the wrapped case is
+// rare (boundary tiles and planes), and inlined the compiler evaluated its FP64 products under
+// a predicate for every halo and queue value (the FP64 pipe at 57 % for about 14 FP64
+// instructions per point instead of four).
+__device__ __noinline__ zd bloch_mul(zd v, int t1, int t2, int t3, zd p0, zd p1, zd p2) {
+  if (t1) v = v * (t1 > 0 ? p0 : conjx(p0));
+  if (t2) v = v * (t2 > 0 ? p1 : conjx(p1));
+  if (t3) v = v * (t3 > 0 ? p2 : conjx(p2));
+  return v;
+}
+
 __device__ void fp64_slab_c(const zd* __restrict__ src, zd* __restrict__ dst, zd* __restrict__ cp, int x, int y,
                             int z0, int z1, const FXCArgs& a) {
   constexpr double w1 = 270.0 / 180.0, w2 = -27.0 / 180.0, w3 = 2.0 / 180.0, w0 = -490.0 / 180.0;
@@ -359,8 +370,9 @@ __device__ __forceinline__ void fx_sum_axes(const long long (*T)[SX], int ty, in
 // Requires N1 >= TX + 2 HALO + 2, N2 >= TY + 2 HALO, N3 >= HALO (one crossing per index) and
 // 16-byte aligned band arrays.
 // Three CTAs per SM (80 registers, a little spilled) measured faster than two at 124 registers
-// (38.3 against 42.5 ps per point at 144^3 x 128): the march is bound by the latency of each
-// plane's loads, so more warps per SM pay more than the spilled registers cost.
+// (38.3 against 42.5 ps per point at 144^3 x 128, before the out-of-line Bloch products took it
+// to 33.0): the march is bound by the latency of each plane's loads, so more warps per SM pay
+// more than the spilled registers cost.
 template <bool CUBIC>
 __global__ void __launch_bounds__(NTHR, 3) kinetic_local_fx_c_kernel(const zd* __restrict__ psi, zd* __restrict__ out,
                                                                     FXCArgs a) {
@@ -436,7 +448,7 @@ __global__ void __launch_bounds__(NTHR, 3) kinetic_local_fx_c_kernel(const zd* _
   // rounded
   auto own_fixed = [&](zd v, int u3, long long& qr, long long& qi) {
     const int t3 = crossing(u3, a.n3);
-    if (ox | oy | t3) v = v * bloch(ox, oy, t3, a);
+    if (ox | oy | t3) v = bloch_mul(v, ox, oy, t3, a.ph[0], a.ph[1], a.ph[2]);
     qr = to_fixed(v.re, ebp);
     qi = to_fixed(v.im, ebp);
   };
@@ -471,7 +483,8 @@ __global__ void __launch_bounds__(NTHR, 3) kinetic_local_fx_c_kernel(const zd* _
 #pragma unroll
     for (int k = 0; k < HPER; ++k)
       if (hy[k] >= 0) {
-        const zd w = hcr[k] != 4 ? hv[k] * bloch(hcr[k] % 3 - 1, hcr[k] / 3 - 1, 0, a) : hv[k];
+        const zd w = hcr[k] != 4 ? bloch_mul(hv[k], hcr[k] % 3 - 1, hcr[k] / 3 - 1, 0, a.ph[0], a.ph[1], a.ph[2])
+                                 : hv[k];
         TR[hy[k]][hx[k]] = to_fixed(w.re, ebp);
         TI[hy[k]][hx[k]] = to_fixed(w.im, ebp);
       }
