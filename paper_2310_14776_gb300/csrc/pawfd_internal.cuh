@@ -160,6 +160,8 @@ struct TcScratch {
   CUtensorMap mapB;
   CUtensorMap mapAB;           // slicesA with the B operand's box (the Gram of psi with itself)
   CUtensorMap mapBA;           // slicesB with the A operand's box (complex Gram pair: psi's planes as A)
+  CUtensorMap mapB32;          // slicesB with a box of 32 rows (symmetric cover)
+  CUtensorMap mapAB32;         // slicesA with a box of 32 rows (symmetric cover, psi^T psi)
   void* part2 = nullptr;       // partials of the second Gram of a pair
   // band rotation
   long long rot_Lc = 0;        // contraction length (bands, x2 for complex) padded to chunks

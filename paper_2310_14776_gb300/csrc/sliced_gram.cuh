@@ -475,6 +475,9 @@ __global__ void __launch_bounds__(256) slice_t_kernel(const R* __restrict__ psi,
 // ------------------------------------------------------------------------------------------
 // Gram kernel
 // ------------------------------------------------------------------------------------------
+constexpr int COVER_TILES = 4;   // tiles of the symmetric cover (at most 256 rows)
+constexpr int CB = 32;           // rows per block of the symmetric cover
+
 struct GramArgs {
   const int* sigA = nullptr;      // [nchunks][sig_ldA]  (chunks of this K block)
   const int* sigB = nullptr;      // [nchunks][sig_ldB]
@@ -509,6 +512,17 @@ struct GramArgs {
   int rows_allocA = 0, rows_allocB = 0;
   long long ksteps = 0;           // K steps per plane (Lp / 16) of both buffers
   int half_stride = 0;            // B row of the second half's first row (complex; 0: half_rows)
+  // Symmetric cover of a Hermitian Gram of at most 256 rows (real operands, one half): tile t
+  // has A rows cov_row0[t] .. + 127 and B rows from three 32-row blocks cov_seg[t][0..2] (one
+  // 32-row box of all planes each; N = 32 MMAs per block).  A tile below the diagonal computes
+  // needed entries mirrored.  Each pair of 32-row blocks (lo, hi), bit 8 lo + hi, belongs to one tile
+  // (cov_own[t]); cov_tr[t] marks the pairs that tile writes from its mirrored orientation
+  // (row block hi).  Entries of a diagonal block are written for row <= column.
+  int cover = 0;
+  int cov_row0[COVER_TILES] = {};
+  int cov_seg[COVER_TILES][3] = {};
+  unsigned long long cov_own[COVER_TILES] = {};
+  unsigned long long cov_tr[COVER_TILES] = {};
 };
 
 // 2^e for the product scale; below the normal range the chunk contributes nothing (its
@@ -625,9 +639,11 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
 // BULK: the operands are core-matrix planes (plane_offset_cm), one bulk copy per plane and
 // operand per stage, read by the tensor cores without swizzle; otherwise row-major planes
 // (plane_offset_rm) through the 4-D TMA maps tA and tB with a 32-byte swizzle.
+// tB32: the B planes with a box of CB rows (the symmetric cover's B blocks).
 template <int S, int ORD, bool ONE, bool BULK, int KCH>
 __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
                                                                   const __grid_constant__ CUtensorMap tB,
+                                                                  const __grid_constant__ CUtensorMap tB32,
                                                                   const __grid_constant__ GramArgs a) {
   constexpr int STAGES = stages<S>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -645,6 +661,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   // tile run while the epilogue of the last one drains TMEM and stores).
   const int ntiles = !ONE ? 1 : ((int)blockIdx.x < a.rot_tiles ? (a.rot_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   auto tile_at = [&](int i, int& row0, int& col0, int& tcol) {
+    if (!BULK && a.cover) {
+      row0 = a.cov_row0[blockIdx.x];
+      col0 = 0;
+      tcol = 0;
+      return;
+    }
     int tr;
     gram_tile(a, (int)blockIdx.x + i * (int)gridDim.x, &tr, &tcol);
     row0 = tr * BM;
@@ -713,7 +735,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           }
         } else {
           tc::tma_load_4d(sa, &tA, &full[s], 0, row0, (int)ks, 0);
-          tc::tma_load_4d(sb, &tB, &full[s], 0, col0, (int)ks, 0);
+          if (a.cover) {
+            // B rows from three blocks, each with its S planes in one box: block g's plane j
+            // at (g S + j) KB of the stage's B area (the MMAs then take N = 32 per block)
+#pragma unroll
+            for (int g3 = 0; g3 < 3; ++g3)
+              tc::tma_load_4d(sb + g3 * (S * CB * BK * 2), &tB32, &full[s], 0, a.cov_seg[blockIdx.x][g3], (int)ks, 0);
+          } else {
+            tc::tma_load_4d(sb, &tB, &full[s], 0, col0, (int)ks, 0);
+          }
         }
         issued = g + 1;
         if (++q == steps_of(c)) {
@@ -763,7 +793,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         // field (address / 16, 14 bits) does not overflow inside the 228 KB of shared memory
         const uint64_t da0 = BULK ? tc::smem_desc_nosw(sa, 128, 256) : tc::smem_desc(sa, BK * 2);
         const uint64_t db0 = BULK ? tc::smem_desc_nosw(sb, 128, 256) : tc::smem_desc(sb, BK * 2);
-        if (leader) {
+        if (leader && a.cover) {
+          // the symmetric cover: each product as three N = 32 MMAs, one per B block, into the
+          // block's 32 columns of the accumulator; A plane i stays in the collector buffer over
+          // all of them
+          constexpr uint32_t idesc32 = tc::idesc_bf16_f32(BM, CB);
+          bool touched[NACC] = {false, false, false, false, false};
+#pragma unroll
+          for (int i = 0; i < S; ++i)
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+              if (i + j > ORD) continue;
+              const int slot = (i + j) < NACC - 1 ? (i + j) : NACC - 1;
+              const uint32_t acc = touched[slot] ? 1u : (q == 0 ? 0u : 1u);
+              touched[slot] = true;
+              const uint64_t da = da0 + (uint64_t)((i * a_slice_bytes<S>()) >> 4);
+              const int jlast = (ORD - i) < (S - 1) ? (ORD - i) : (S - 1);
+#pragma unroll
+              for (int g3 = 0; g3 < 3; ++g3) {
+                const uint32_t d = tmem + (uint32_t)(slot * BN + g3 * CB);
+                const uint64_t db = db0 + (uint64_t)(((g3 * S + j) * (CB * BK * 2)) >> 4);
+                if (j == 0 && g3 == 0)
+                  tc::mma_bf16_ca<1>(d, da, db, idesc32, acc);
+                else if (j == jlast && g3 == 2)
+                  tc::mma_bf16_ca<3>(d, da, db, idesc32, acc);
+                else
+                  tc::mma_bf16_ca<2>(d, da, db, idesc32, acc);
+              }
+            }
+          tc::mma_commit(&empty[s]);
+          consumed = g + 1;
+        } else if (leader) {
           bool touched[NACC] = {false, false, false, false, false};
 #pragma unroll
           for (int i = 0; i < S; ++i)
@@ -1046,9 +1106,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       alo[j] = 0.0f;
     }
     const int ra = (row < a.rowsA) ? __ldg(a.maxA + row) : 0;
+    // B row of tile column tc (the symmetric cover gathers three 32-row blocks)
+    auto bcol = [&](int tcn) { return (!BULK && a.cover) ? a.cov_seg[blockIdx.x][tcn / CB] + tcn % CB : col0 + tcn; };
     // column exponents: two registers per lane (columns cbase + lane, cbase + 32 + lane), handed
     // to the column's threads by shuffles; the chunk's exponents are loaded before its MMAs end
-    const int cl0 = col0 + cbase + lane, cl1 = cl0 + 32;
+    const int cl0 = bcol(cbase + lane), cl1 = lane + 32 < EPI_COLS ? bcol(cbase + lane + 32) : a.rowsB;
     const bool cv0 = cl0 < a.rowsB, cv1 = lane + 32 < EPI_COLS && cl1 < a.rowsB;
     const int mb0 = cv0 ? __ldg(a.maxB + cl0) : 0, mb1 = cv1 ? __ldg(a.maxB + cl1) : 0;
     for (int c = 0; c < nch; ++c) {
@@ -1131,6 +1193,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
               else ((double*)a.rot_out)[idx] = v;
             }
           }
+        }
+      }
+    } else if (!BULK && a.cover) {
+      // the symmetric cover: the entries of the block pairs this tile owns, at (min, max)
+      if (row < a.rowsA && !abort_flag) {
+        const unsigned long long own = a.cov_own[blockIdx.x], trm = a.cov_tr[blockIdx.x];
+        const int bi = row / CB;
+        double* base = a.part + (long long)blockIdx.y * a.rowsA * a.rowsB;
+#pragma unroll
+        for (int j = 0; j < EPI_COLS; ++j) {
+          const int col = bcol(cbase + j);
+          if (col >= a.rowsB) continue;
+          const int bj = col / CB, lo = min(bi, bj), hi = max(bi, bj);
+          const int bit = lo * 8 + hi;
+          if (!((own >> bit) & 1ull)) continue;
+          const bool write = bi == bj ? row <= col : (((trm >> bit) & 1ull) ? bi == hi : bi == lo);
+          if (!write) continue;
+          const double v = df_to_double(ahi[j], alo[j], ra + __ldg(a.maxB + col));
+          double* o = base + (long long)min(row, col) * a.rowsB + max(row, col);
+          *o = a.accumulate ? *o + v : v;
         }
       }
     } else if (row < a.rowsA && !abort_flag) {

@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(NTHR) kinetic_local_fx_kernel(const double* __
 // component can exceed the slab's largest component by up to a factor sqrt(2), so the grid
 // unit is taken one exponent step higher, 2^(ebp - 1073) with ebp = eb + 1: |q| <= 2^51
 // still holds, and every input is rounded once to within 2^(eb - 1073), twice the real
-// kernel's half unit.  Slabs holding an infinity or NaN, or values within a factor 2 of the
-// top of the FP64 range (where a rotation could overflow), are computed in plain FP64.
+// kernel's half unit.  Slabs holding an infinity or NaN, values within a factor 2 of the top
+// of the FP64 range (where a rotation could overflow), or only values below about 2^-896
+// (where the unit folded into the axis factors would leave the normal range) are computed in
+// plain FP64.
 
 struct FXCArgs {
   int n1, n2, n3;
@@ -434,16 +436,20 @@ __global__ void __launch_bounds__(NTHR, 3) kinetic_local_fx_c_kernel(const zd* _
   int eb = 0;
 #pragma unroll
   for (int w = 0; w < NTHR / 32; ++w) eb = max(eb, s_emax[w]);
-  if (eb >= 0x7FE) {   // non-finite values, or a rotation could overflow: plain FP64
+  // plain FP64 for non-finite values, parts a rotation could overflow, and slabs of values so
+  // small (below about 2^-895) that the unit folded into the axis factors would leave the
+  // normal range: the march then has one form only (a per-CTA choice between two forms of the
+  // final FMAs was evaluated under a predicate on both sides, FP64 work on every point)
+  if (eb >= 0x7FE || eb < 126) {
     if (active) fp64_slab_c(src, dst, cp, x, y, z0, z1, a);
     return;
   }
-  const int ebp = max(eb, 1) + 1;
-  const bool folded = ebp >= 128;
-  const double unit = ldexp(1.0, ebp - 1073);
+  const int ebp = eb + 1;
+  // 2^(ebp - 1073), a normal number for ebp >= 128, from its bit fields (no library call)
+  const double unit = __longlong_as_double((long long)(ebp - 1073 + 1023) << 52);
   double cs[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) cs[c] = folded ? a.cs[c] * unit : a.cs[c];
+  for (int c = 0; c < 3; ++c) cs[c] = a.cs[c] * unit;
   // the own column's value of plane u3 on the grid: Bloch factor of the crossed faces, then
   // rounded
   auto own_fixed = [&](zd v, int u3, long long& qr, long long& qi) {
@@ -501,30 +507,14 @@ __global__ void __launch_bounds__(NTHR, 3) kinetic_local_fx_c_kernel(const zd* _
       const double vr = vv * c.re, vi = vv * c.im;
       double rre, rim;
       if (CUBIC) {
-        const long long Sr = fx_sum_cubic(TR, ty, tx, qr), Si = fx_sum_cubic(TI, ty, tx, qi);
-        if (folded) {
-          rre = fma(i64_to_f64(Sr), cs[0], vr);
-          rim = fma(i64_to_f64(Si), cs[0], vi);
-        } else {
-          rre = fma(i64_to_f64(Sr) * cs[0], unit, vr);
-          rim = fma(i64_to_f64(Si) * cs[0], unit, vi);
-        }
+        rre = fma(i64_to_f64(fx_sum_cubic(TR, ty, tx, qr)), cs[0], vr);
+        rim = fma(i64_to_f64(fx_sum_cubic(TI, ty, tx, qi)), cs[0], vi);
       } else {
         long long Sx, Sy, Sz;
         fx_sum_axes(TR, ty, tx, qr, Sx, Sy, Sz);
-        if (folded) {
-          rre = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vr)));
-        } else {
-          const double t = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], i64_to_f64(Sz) * cs[2]));
-          rre = fma(t, unit, vr);
-        }
+        rre = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vr)));
         fx_sum_axes(TI, ty, tx, qi, Sx, Sy, Sz);
-        if (folded) {
-          rim = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vi)));
-        } else {
-          const double t = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], i64_to_f64(Sz) * cs[2]));
-          rim = fma(t, unit, vi);
-        }
+        rim = fma(i64_to_f64(Sx), cs[0], fma(i64_to_f64(Sy), cs[1], fma(i64_to_f64(Sz), cs[2], vi)));
       }
       stz(dst + r, zd{rre, rim});
       if (cp) stz(cp + r, c);

@@ -39,6 +39,46 @@ int gram_splits(int tiles, int nch, int num_sms) {
   return best;
 }
 
+// The symmetric cover of a real Hermitian Gram of 192 < nb <= 256 rows.  Eight blocks of 32
+// rows; a tile has A rows from block row_blk (four blocks, 128 rows) and B rows from three
+// blocks.  With each tile's mirror (a tile below the diagonal computes the transposes of needed
+// entries) the four tiles hold all 36 pairs of blocks; found by exhaustive search over the row
+// starts and block triples.  The upper-triangle tiling needs five 128 x 96 tiles for the same
+// matrix, so the cover does 20 % fewer digit products.
+constexpr int kCoverRowBlk[sg::COVER_TILES] = {0, 0, 1, 4};
+constexpr int kCoverSegBlk[sg::COVER_TILES][3] = {{0, 4, 5}, {1, 6, 7}, {2, 3, 4}, {5, 6, 7}};
+
+bool use_cover(int nb) { return nb > 2 * sg::BN && nb <= 8 * sg::CB; }
+
+// Fills the cover fields of a: each block pair goes to the first tile that holds it, written
+// from the direct orientation (row block lo) when that tile has it, else mirrored.
+void set_cover(sg::GramArgs& a) {
+  a.cover = 1;
+  unsigned long long owned = 0;
+  for (int t = 0; t < sg::COVER_TILES; ++t) {
+    a.cov_row0[t] = kCoverRowBlk[t] * sg::CB;
+    for (int g = 0; g < 3; ++g) a.cov_seg[t][g] = kCoverSegBlk[t][g] * sg::CB;
+    a.cov_own[t] = a.cov_tr[t] = 0;
+    auto in_rows = [&](int b) { return b >= kCoverRowBlk[t] && b < kCoverRowBlk[t] + sg::BM / sg::CB; };
+    auto in_cols = [&](int b) { return b == kCoverSegBlk[t][0] || b == kCoverSegBlk[t][1] || b == kCoverSegBlk[t][2]; };
+    for (int lo = 0; lo < 8; ++lo)
+      for (int hi = lo; hi < 8; ++hi) {
+        const unsigned long long bit = 1ull << (lo * 8 + hi);
+        if (owned & bit) continue;
+        const bool direct = in_rows(lo) && in_cols(hi), mirrored = in_rows(hi) && in_cols(lo);
+        if (!direct && !mirrored) continue;
+        owned |= bit;
+        a.cov_own[t] |= bit;
+        if (!direct) a.cov_tr[t] |= bit;
+      }
+  }
+}
+
+// Tiles of the Hermitian Gram pair for nb bands
+int pair_tiles(int nb, bool cplx) {
+  return cplx ? 2 * sg::herm_tiles(nb) : (use_cover(nb) ? sg::COVER_TILES : sg::herm_tiles(nb));
+}
+
 template <class W>
 __global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, int im_off, double dV,
                                  bool herm, W* __restrict__ M);
@@ -149,7 +189,7 @@ int tc_gram_impl(pawfd_ctx* c, const R* A, const R* B, int nb, void* M, bool her
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, a);
+        t.mapA, t.mapB, t.mapB, a);
     ktimer_end(c);
     c->launches += 1;
   }
@@ -171,7 +211,8 @@ template <class R, int S, int ORD>
 int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, double* M2) {
   TcScratch& t = c->tc;
   const long long L = (long long)c->K;
-  const int tiles = sg::herm_tiles(nb);
+  const bool cover = use_cover(nb);
+  const int tiles = pair_tiles(nb, false);
   const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
   const int nch0 = (int)((std::min(Kblk, L) + sg::KCG - 1) / sg::KCG);
@@ -220,10 +261,11 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a.klen = len;
     a.part = (double*)t.part;
     a.st = c->d_status;
+    if (cover) set_cover(a);
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, a);
+        t.mapA, t.mapB, t.mapB32, a);
     ktimer_end(c);
     // psi^T psi: psi's planes and exponents on both sides (psi's planes through a map with the
     // B operand's box)
@@ -236,7 +278,7 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a2.part = (double*)t.part2;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapAB, a2);
+        t.mapA, t.mapAB, t.mapAB32, a2);
     ktimer_end(c);
     c->launches += presliced ? 3 : 4;
   }
@@ -315,7 +357,7 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, a);
+        t.mapA, t.mapB, t.mapB, a);
     ktimer_end(c);
     // psi^H psi: psi's planes (rows [0, nb) of B_ext, read through a map with the A box) as
     // the first operand; rows [nb, 128 Tr) of that box are zero or psi'' rows, whose output
@@ -329,7 +371,7 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     a2.part = (double*)t.part2;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapBA, t.mapB, a2);
+        t.mapBA, t.mapB, t.mapB, a2);
     ktimer_end(c);
     c->launches += 5;
   }
@@ -452,10 +494,10 @@ int tc_rotate_kc(pawfd_ctx* c, const R* psi, int nb, const double* C, int nout, 
     if (nch == 1)   // persistent CTAs, one per SM (the kernel's shared memory admits one)
       sg::sliced_gram_kernel<S, ORD, true, true, KCH>
           <<<dim3(std::min(a.rot_tiles, c->num_sms), 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB,
-                                                                                                        a);
+                                                                                                        t.mapB, a);
     else
       sg::sliced_gram_kernel<S, ORD, false, true, KCH>
-          <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, a);
+          <<<dim3(a.rot_tiles, 1), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, t.mapB, a);
     c->launches += 1;
   }
   return check_cuda(c, cudaGetLastError(), "tensor-core rotate launch");
@@ -539,7 +581,8 @@ int launch_gram_tc(pawfd_ctx* c, const void* A, const void* B, int nb, void* M, 
 // TMA descriptor of a row-major digit-plane buffer (S planes, K steps of rows x 16 values):
 // boxes of 16 values x box_rows x S planes, 32-byte swizzle (the layout the tensor core reads
 // through smem_desc(..., 32)); rows past the allocation read as zero.
-int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S, int box_rows) {
+int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long long Lp, int S, int box_rows,
+                     int box_planes = 0) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -553,7 +596,7 @@ int encode_slice_map(pawfd_ctx* c, CUtensorMap* map, void* base, int rows, long 
   const cuuint64_t ks = (cuuint64_t)(Lp / sg::BK);
   cuuint64_t dims[4] = {(cuuint64_t)sg::BK, (cuuint64_t)rows, ks, (cuuint64_t)S};
   cuuint64_t strides[3] = {(cuuint64_t)sg::BK * 2, (cuuint64_t)rows * sg::BK * 2, ks * rows * sg::BK * 2};
-  cuuint32_t box[4] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows, 1, (cuuint32_t)S};
+  cuuint32_t box[4] = {(cuuint32_t)sg::BK, (cuuint32_t)box_rows, 1, (cuuint32_t)(box_planes > 0 ? box_planes : S)};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estr,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -585,7 +628,7 @@ int setup_tc(pawfd_ctx* c) {
   const size_t sa = (size_t)S * t.rowsA_alloc * t.kblk * 2, sb = (size_t)S * t.rowsB_alloc * t.kblk * 2;
   const int nchunks = (int)(t.kblk / sg::KC);
   const int rowsB = cplx ? nbp + nb : nb;
-  const int tiles_min = (cplx ? 2 : 1) * sg::herm_tiles(nb);
+  const int tiles_min = pair_tiles(nb, cplx);
   const int nsplit = gram_splits(tiles_min, (int)(t.kblk / sg::KCG), c->num_sms);
   t.part_bytes = (size_t)nsplit * nb * rowsB * sizeof(double);
   int rc = check_cuda(c, cudaMalloc(&t.slicesA, sa), "cudaMalloc tc slices");
@@ -605,6 +648,8 @@ int setup_tc(pawfd_ctx* c) {
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapAB, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::BN);
   if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapBA, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::BM);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapB32, t.slicesB, t.rowsB_alloc, t.kblk, S, sg::CB);
+  if (rc == PAWFD_OK) rc = encode_slice_map(c, &t.mapAB32, t.slicesA, t.rowsA_alloc, t.kblk, S, sg::CB);
   if (rc == PAWFD_OK) {
     const cudaFuncAttribute smem_attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     // the Gram (row-major planes, TMA maps) and the rotation (core-matrix planes, bulk copies;

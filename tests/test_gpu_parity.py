@@ -122,18 +122,21 @@ def test_edge_cases(dev, case):
     full_step_parity(s, case["nb"], 301, dev)
 
 
+@pytest.mark.parametrize("nb", [150, 256])
 @pytest.mark.parametrize("precision,cplx", [("fp64", False), ("fp64", True), ("mixed", False), ("mixed", True)])
-def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx):
+def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx, nb):
     """pawfd_gram_hs: H_nm from the shared slicing of psi is the same Hermitian Gram as
     pawfd_gram_hermitian(psi, H psi); S_nm = dV psi^H psi + sum_a P^H dS P agrees with the
     Gram of psi and S psi (the oracle's form) to the precision of the bands.  Complex bands
     take H_nm as (H psi)^H psi (equal for a Hermitian H): its upper triangle is that of the
     full Gram of H psi and psi, and with FP32 H psi it differs from psi^H (H psi) at the
-    FP32 level (the rounding of H psi breaks the exact symmetry)."""
+    FP32 level (the rounding of H psi breaks the exact symmetry).  Real bands with 192 < nb <= 256
+    take the symmetric cover (four tiles, some of whose entries are computed mirrored, as
+    psi_m^T H psi_n): the same tolerances."""
     from paper_2310_14776_gb300 import api
     k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
     s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=511, k=k, complex_wf=cplx)
-    nb = 150
+    mirrored = cplx or 192 < nb <= 256
     ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
     psi_np = synth.make_psi(s, nb, 512)
     psi = to_dev(psi_np, dev).to(ctx.dtype)
@@ -152,7 +155,7 @@ def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx):
         # the diagonal of a Hermitian Gram is stored real
         assert np.max(np.abs(np.diag(Hnm).real - np.diag(Hfull).real)) <= 1e-13 * scale
     if precision == "fp64":
-        if cplx:
+        if mirrored:
             assert_close_matrix(Hnm, Hsep)
         else:
             assert np.array_equal(Hnm, Hsep)
@@ -162,13 +165,46 @@ def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx):
         assert_close_matrix(Hnm, ref["Hnm"])
     else:
         # S psi in FP32 rounds each value once: the two forms differ at the FP32 level
-        assert_close_matrix(Hnm, Hsep, rel=1e-6 if cplx else 1e-12)
+        assert_close_matrix(Hnm, Hsep, rel=1e-6 if mirrored else 1e-12)
         assert_close_matrix(Snm, Ssep, rel=1e-6)
         # against the oracle's FP64 S_nm of the FP32-rounded bands (the projections are FP32)
         psi32 = psi.cpu().numpy().astype(np.complex128 if cplx else np.float64)
         ref = O.rayleigh_ritz(s, psi32)
         assert_close_matrix(Snm, ref["Snm"], rel=1e-6)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nb", [193, 256])
+def test_symmetric_cover_gram_pair(dev, precision, nb):
+    """The real Gram pair with 192 < nb <= 256 bands runs on the symmetric cover (four tiles;
+    B rows from three 32-row blocks; entries of some block pairs computed mirrored).  With 1 MB
+    of scratch the grid is cut into K blocks of one chunk, so every owned entry is also
+    accumulated over many blocks.  FP64: H_nm and S_nm against the oracle's to 1e-12 of the
+    largest entry.  FP32 bands: S_nm against the oracle on the FP32-rounded bands and H_nm
+    against the upper-triangle tiling of the same FP32 H psi, to 1e-6."""
+    from paper_2310_14776_gb300 import api
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=541)
+    psi_np = synth.make_psi(s, nb, 542)
+    for mb in (0, 1):
+        ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
+        ctx.set_option("tc_scratch_mb", mb)
+        psi = to_dev(psi_np, dev).to(ctx.dtype)
+        hpsi, spsi, P = ctx.apply_hs(psi)
+        Hnm, Snm = (t.cpu().numpy() for t in ctx.gram_hs(psi, hpsi, P))
+        psi_in = psi.cpu().numpy().astype(np.float64)
+        ref = O.rayleigh_ritz(s, psi_in)
+        if precision == "fp64":
+            assert_close_matrix(Hnm, ref["Hnm"])
+            assert_close_matrix(Snm, ref["Snm"])
+        else:
+            # H psi in FP32: against the upper-triangle tiling of the same FP32 H psi (the
+            # mirrored entries differ at the FP32 level), S_nm against the oracle
+            Hsep = ctx.gram(psi, hpsi, hermitian=True).cpu().numpy()
+            assert_close_matrix(Hnm, Hsep, rel=1e-6)
+            assert_close_matrix(Snm, ref["Snm"], rel=1e-6)
+        assert np.array_equal(Hnm, Hnm.T) and np.array_equal(Snm, Snm.T)
+        ctx.close()
 
 
 @pytest.mark.parametrize("precision,cplx", [("fp64", False), ("fp64", True), ("mixed", False)])
