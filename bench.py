@@ -45,22 +45,22 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # fixed band count it grows with the grid points K
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
-_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "ce7af29f09dcbfc6b5d7746d83fe19cb5c81801a",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "c52f68735a494d5aa6a55ba97d4570ae9bc39f79",
+_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "35d92882799e406566221d91a0be7a4c74e5ca74",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "f4c07d5624d718e074ceddb60c13629acfc98a8e",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
                  "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
-    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 22180.9, "sources": _GRAM_SOURCES},
-    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 12196.6, "sources": _GRAM_SOURCES},
+    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21753.2, "sources": _GRAM_SOURCES},
+    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11966.8, "sources": _GRAM_SOURCES},
 }
 
 
 # Measured DRAM traffic per launch of the Gram MMA kernel (the mean of the two launches of one
 # pawfd_gram_hs call, ncu at 64^3 x 256 bands), per grid
-# point: FP64 (2005.9 + 0.5 + 940.5 + 0.8) / 2 MB, mixed (1142.2 + 0.9 + 537.7 + 0.6) / 2 MB.
+# point: FP64 (1880.8 + 6.1 + 940.8 + 3.6) / 2 MB, mixed (1075.2 + 1.6 + 538.0 + 1.7) / 2 MB.
 KERNEL_TRAFFIC = {
-    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1473.85e6 / 262144, "sources": _GRAM_SOURCES},
-    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 840.7e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1415.65e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 808.25e6 / 262144, "sources": _GRAM_SOURCES},
 }
 
 
@@ -78,8 +78,11 @@ def kernel_traffic(kernel, precision, cplx, K, nb):
 
 
 def sg_tiles_area(nb):
-    """Output entries the Hermitian Gram kernel computes: 128 x 96 tiles holding an element
-    with row <= column."""
+    """Output entries the real Hermitian Gram kernel computes: for 192 < nb <= 256 the four
+    128 x 96 tiles of the symmetric cover, otherwise the 128 x 96 tiles holding an element with
+    row <= column."""
+    if 192 < nb <= 256:
+        return 4 * 128 * 96
     tr, tcn = (nb + 127) // 128, (nb + 95) // 96
     return sum(max(0, tcn - (128 * r) // 96) for r in range(tr)) * 128 * 96
 
