@@ -759,7 +759,7 @@ def run_served(args):
                             "how": "plain FP64 pawfd_rr_step, one job at a time, on 8 small and %d large systems "
                                    "of the stream, weighted by its large fraction %.3f" % (len(large), frac_large)},
         "speedup_vs_fp64_sequential": (steps_done / out["elapsed"]) / (5.0 / t_job) if t_job else None,
-        "roofline": None, "gpu_launches": None, "clocks": clk,
+        "roofline": None, "gpu_launches": int(out["kernel_launches"]), "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(result), flush=True)

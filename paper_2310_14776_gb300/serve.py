@@ -258,6 +258,7 @@ class Server:
         self.systems = list(systems)
         self.precision = precision
         self.iterations = iterations
+        self.kernel_launches = 0
         self.tune = tune
         free, _ = torch.cuda.mem_get_info(self.device)
         self.free_at_start = free
@@ -466,6 +467,7 @@ class Server:
         with torch.cuda.stream(stream):
             psi, out = bufs[0], bufs[1]
             self._bands_into(inst, job.psi_seed, psi, out)
+            launches0 = ctx.launch_count()
             if self.tune:
                 from . import autotune
                 if autotune.shape_key(ctx, nb) not in autotune._CACHE:
@@ -476,6 +478,7 @@ class Server:
             pair = [psi, out]
             for it in range(self.iterations):
                 ctx.rr_step(pair[it % 2], out=pair[(it + 1) % 2], work=work)
+            self.kernel_launches += ctx.launch_count() - launches0
             done = torch.cuda.Event()
             done.record(stream)
         return dict(job=job, ctx=ctx, cbytes=cbytes, stream=stream, sidx=sidx, done=done, offs=offs, sizes=sizes,
@@ -505,6 +508,7 @@ class Server:
         pending = collections.deque(sorted(jobs, key=lambda j: j.arrival))
         active: Dict[int, dict] = {}
         done: List[JobRecord] = []
+        self.kernel_launches = 0   # library kernels the jobs launched (tuning included)
         t0 = clock()
         while pending or self.sched.queue or active:
             now = clock() - t0
@@ -537,7 +541,8 @@ class Server:
                 time.sleep(max(0.0, min(poll_s, nxt)))
         elapsed = clock() - t0
         self._sample_device()
-        return {"records": done, "elapsed": elapsed, "unfinished": len(active) + len(self.sched.queue) + len(pending),
+        return {"records": done, "elapsed": elapsed, "kernel_launches": self.kernel_launches,
+                "unfinished": len(active) + len(self.sched.queue) + len(pending),
                 "active_at_end": len(active), "queued_at_end": len(self.sched.queue), "peak_used": self.sched.peak_used,
                 "budget": self.sched.budget, "max_queue": self.sched.max_queue, "overruns": self.sched.overruns,
                 "device_peak_used": self.free_at_start - self.min_free, "arena_bytes": self.arena.size,

@@ -162,16 +162,64 @@ def test_array_bytes():
 
 
 def test_bench_tile_area_counts_upper_triangle_tiles():
-    # the bench's count of the entries the Hermitian Gram kernel computes (128 x 96 tiles that
-    # hold an element with row <= column) against a brute-force enumeration
+    # the bench's count of the entries the real Hermitian Gram kernel computes (128 x 96 tiles
+    # that hold an element with row <= column; for 192 < nb <= 256 the four tiles of the
+    # symmetric cover) against a brute-force enumeration
     import bench
-    for nb in (1, 17, 96, 128, 150, 256, 300, 1024):
+    for nb in (1, 17, 96, 128, 150, 192, 193, 256, 257, 300, 1024):
         tiles = 0
         for r0 in range(0, nb, 128):
             for c0 in range(0, nb, 96):
                 if any(r <= c for r in range(r0, min(nb, r0 + 128)) for c in range(c0, min(nb, c0 + 96))):
                     tiles += 1
+        if 192 < nb <= 256:
+            tiles = 4
         assert bench.sg_tiles_area(nb) == tiles * 128 * 96, nb
+
+
+def test_symmetric_cover_table_holds_every_block_pair():
+    # the cover table of the tensor-core Gram (csrc/tc_gram.cu): four tiles of 128 rows (from a
+    # 32-row block) x three 32-row B blocks whose entries and mirrors hold every pair of the
+    # eight blocks of a 256-band Hermitian matrix; the kernel's write rule (first tile that
+    # holds a pair owns it, direct orientation when it has one) then writes every upper entry
+    # exactly once
+    import pathlib
+    import re
+    root = pathlib.Path(__file__).resolve().parents[1]
+    src = (root / "paper_2310_14776_gb300" / "csrc" / "tc_gram.cu").read_text()
+    rows = [int(v) for v in re.search(r"kCoverRowBlk\[sg::COVER_TILES\] = \{([^}]*)\}", src).group(1).split(",")]
+    segs = [[int(v) for v in t.split(",")] for t in re.findall(r"\{(\d+, \d+, \d+)\}",
+                                                             src[src.find("kCoverSegBlk"):src.find("bool use_cover")])]
+    assert len(rows) == 4 and len(segs) == 4
+    nb = 256
+    cnt = np.zeros((nb, nb), int)
+    owned = set()
+    for t in range(4):
+        mine = {}
+        for lo in range(8):
+            for hi in range(lo, 8):
+                if (lo, hi) in owned:
+                    continue
+                direct = rows[t] <= lo < rows[t] + 4 and hi in segs[t]
+                mirrored = rows[t] <= hi < rows[t] + 4 and lo in segs[t]
+                if direct or mirrored:
+                    owned.add((lo, hi))
+                    mine[(lo, hi)] = direct
+        for n in range(32 * rows[t], 32 * rows[t] + 128):
+            for c in range(96):
+                m = 32 * segs[t][c // 32] + c % 32
+                bi, bj = n // 32, m // 32
+                key = (min(bi, bj), max(bi, bj))
+                if key not in mine:
+                    continue
+                if bi == bj:
+                    write = n <= m
+                else:
+                    write = bi == key[0] if mine[key] else bi == key[1]
+                if write:
+                    cnt[min(n, m), max(n, m)] += 1
+    assert len(owned) == 36
+    assert np.array_equal(cnt, np.triu(np.ones((nb, nb), int)))
 
 
 def test_free_grid_is_the_bare_operator():
