@@ -77,12 +77,14 @@ def check_fp64(out, ref, nb):
     assert per_band(out["psi_rot"], O.rotate(ref["psi_in"], C), nb).max() <= REL
 
 
-# real FP64 systems on grids the fixed-point and double-float kernels serve (N1 >= 40,
-# N2 >= 14): a cubic cell (equal spacings: the fixed-point kernel sums the three axes in one
-# integer) and an orthorhombic one (per-axis sums); a complex (Bloch) system
+# FP64 systems on grids the fixed-point and double-float kernels serve (N1 >= 40, N2 >= 14):
+# a real cubic cell (equal spacings: the fixed-point kernel sums the three axes in one
+# integer), a real orthorhombic one (per-axis sums) and a complex (Bloch) one with ragged
+# tiles; a complex system below the fixed-point kernel's grid (the general kernel)
 FP64_SYSTEMS = {
     "real-cubic": dict(n=(48, 40, 36), cell=(18.0, 15.0, 13.5), natoms=4, cplx=False),
     "real-ortho": dict(n=(45, 19, 13), cell=(9.0, 7.6, 5.2), natoms=4, cplx=False),
+    "bloch-fx": dict(n=(44, 20, 14), cell=(13.2, 6.0, 4.2), natoms=4, cplx=True),
     "bloch": dict(n=(30, 28, 26), cell=(11.3, 10.6, 9.8), natoms=5, cplx=True),
 }
 
