@@ -512,10 +512,11 @@ struct GramArgs {
   int rows_allocA = 0, rows_allocB = 0;
   long long ksteps = 0;           // K steps per plane (Lp / 16) of both buffers
   int half_stride = 0;            // B row of the second half's first row (complex; 0: half_rows)
-  // Symmetric cover of a Hermitian Gram of at most 256 rows (real operands, one half): tile t
-  // has A rows cov_row0[t] .. + 127 and B rows from three 32-row blocks cov_seg[t][0..2] (one
-  // 32-row box of all planes each; N = 32 MMAs per block).  A tile below the diagonal computes
-  // needed entries mirrored.  Each pair of 32-row blocks (lo, hi), bit 8 lo + hi, belongs to one tile
+  // Symmetric cover of a Hermitian Gram of at most 256 rows: tile t has A rows cov_row0[t] ..
+  // + 127 and B rows from three 32-row blocks cov_seg[t][0..2] (one 32-row box of all planes
+  // each; N = 32 MMAs per block); complex operands run the four tiles once per half of B
+  // (CTA x = half x COVER_TILES + t).  A tile below the diagonal computes needed entries
+  // mirrored (the imaginary half negated: Im G_mn = -Im G_nm).  Each pair of 32-row blocks (lo, hi), bit 8 lo + hi, belongs to one tile
   // (cov_own[t]); cov_tr[t] marks the pairs that tile writes from its mirrored orientation
   // (row block hi).  Entries of a diagonal block are written for row <= column.
   int cover = 0;
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   const int ntiles = !ONE ? 1 : ((int)blockIdx.x < a.rot_tiles ? (a.rot_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   auto tile_at = [&](int i, int& row0, int& col0, int& tcol) {
     if (!BULK && a.cover) {
-      row0 = a.cov_row0[blockIdx.x];
+      row0 = a.cov_row0[blockIdx.x % COVER_TILES];
       col0 = 0;
       tcol = 0;
       return;
@@ -738,9 +739,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           if (a.cover) {
             // B rows from three blocks, each with its S planes in one box: block g's plane j
             // at (g S + j) KB of the stage's B area (the MMAs then take N = 32 per block)
+            const int ct = blockIdx.x % COVER_TILES, boff = (blockIdx.x / COVER_TILES) * HS;
 #pragma unroll
             for (int g3 = 0; g3 < 3; ++g3)
-              tc::tma_load_4d(sb + g3 * (S * CB * BK * 2), &tB32, &full[s], 0, a.cov_seg[blockIdx.x][g3], (int)ks, 0);
+              tc::tma_load_4d(sb + g3 * (S * CB * BK * 2), &tB32, &full[s], 0, boff + a.cov_seg[ct][g3], (int)ks, 0);
           } else {
             tc::tma_load_4d(sb, &tB, &full[s], 0, col0, (int)ks, 0);
           }
@@ -1106,8 +1108,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
       alo[j] = 0.0f;
     }
     const int ra = (row < a.rowsA) ? __ldg(a.maxA + row) : 0;
-    // B row of tile column tc (the symmetric cover gathers three 32-row blocks)
-    auto bcol = [&](int tcn) { return (!BULK && a.cover) ? a.cov_seg[blockIdx.x][tcn / CB] + tcn % CB : col0 + tcn; };
+    // B row of tile column tc (the symmetric cover gathers three 32-row blocks of its half)
+    auto bcol = [&](int tcn) -> int {
+      if (!BULK && a.cover)
+        return (int)(blockIdx.x / COVER_TILES) * HS + a.cov_seg[blockIdx.x % COVER_TILES][tcn / CB] + tcn % CB;
+      return col0 + tcn;
+    };
     // column exponents: two registers per lane (columns cbase + lane, cbase + 32 + lane), handed
     // to the column's threads by shuffles; the chunk's exponents are loaded before its MMAs end
     const int cl0 = bcol(cbase + lane), cl1 = lane + 32 < EPI_COLS ? bcol(cbase + lane + 32) : a.rowsB;
@@ -1196,22 +1202,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         }
       }
     } else if (!BULK && a.cover) {
-      // the symmetric cover: the entries of the block pairs this tile owns, at (min, max)
+      // the symmetric cover: the entries of the block pairs this tile owns, at (min, max) of
+      // its half
       if (row < a.rowsA && !abort_flag) {
-        const unsigned long long own = a.cov_own[blockIdx.x], trm = a.cov_tr[blockIdx.x];
-        const int bi = row / CB;
-        double* base = a.part + (long long)blockIdx.y * a.rowsA * a.rowsB;
+        const int cov_t = blockIdx.x % COVER_TILES, cov_h = blockIdx.x / COVER_TILES;
+        const unsigned long long own = a.cov_own[cov_t], trm = a.cov_tr[cov_t];
+        const int bi = row / CB, hoff = cov_h * HS;
+        double* base = a.part + (long long)blockIdx.y * a.rowsA * a.rowsB + hoff;
 #pragma unroll
         for (int j = 0; j < EPI_COLS; ++j) {
-          const int col = bcol(cbase + j);
-          if (col >= a.rowsB) continue;
-          const int bj = col / CB, lo = min(bi, bj), hi = max(bi, bj);
+          const int col = bcol(cbase + j);    // B row
+          const int m = col - hoff;           // band of the column
+          if (m >= a.half_rows) continue;
+          const int bj = m / CB, lo = min(bi, bj), hi = max(bi, bj);
           const int bit = lo * 8 + hi;
           if (!((own >> bit) & 1ull)) continue;
-          const bool write = bi == bj ? row <= col : (((trm >> bit) & 1ull) ? bi == hi : bi == lo);
+          const bool write = bi == bj ? row <= m : (((trm >> bit) & 1ull) ? bi == hi : bi == lo);
           if (!write) continue;
-          const double v = df_to_double(ahi[j], alo[j], ra + __ldg(a.maxB + col));
-          double* o = base + (long long)min(row, col) * a.rowsB + max(row, col);
+          double v = df_to_double(ahi[j], alo[j], ra + __ldg(a.maxB + col));
+          if (cov_h == 1 && row > m) v = -v;
+          double* o = base + (long long)min(row, m) * a.rowsB + max(row, m);
           *o = a.accumulate ? *o + v : v;
         }
       }

@@ -39,7 +39,7 @@ int gram_splits(int tiles, int nch, int num_sms) {
   return best;
 }
 
-// The symmetric cover of a real Hermitian Gram of 192 < nb <= 256 rows.  Eight blocks of 32
+// The symmetric cover of a Hermitian Gram of 192 < nb <= 256 rows (per half for complex bands).  Eight blocks of 32
 // rows; a tile has A rows from block row_blk (four blocks, 128 rows) and B rows from three
 // blocks.  With each tile's mirror (a tile below the diagonal computes the transposes of needed
 // entries) the four tiles hold all 36 pairs of blocks; found by exhaustive search over the row
@@ -75,9 +75,7 @@ void set_cover(sg::GramArgs& a) {
 }
 
 // Tiles of the Hermitian Gram pair for nb bands
-int pair_tiles(int nb, bool cplx) {
-  return cplx ? 2 * sg::herm_tiles(nb) : (use_cover(nb) ? sg::COVER_TILES : sg::herm_tiles(nb));
-}
+int pair_tiles(int nb, bool cplx) { return (cplx ? 2 : 1) * (use_cover(nb) ? sg::COVER_TILES : sg::herm_tiles(nb)); }
 
 template <class W>
 __global__ void tc_reduce_kernel(const double* __restrict__ part, int nsplit, int nb, int rowsB, int im_off, double dV,
@@ -305,7 +303,8 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
   const int nbp = (nb + 7) / 8 * 8;
   const int rowsB = nbp + nb;
   const int Tc = (nb + sg::BN - 1) / sg::BN;
-  const int tiles = 2 * sg::herm_tiles(nb);
+  const bool cover = use_cover(nb);
+  const int tiles = pair_tiles(nb, true);
   const long long Kblk = c->tc_kblk_chunks > 0 ? std::min<long long>(t.kblk, (long long)c->tc_kblk_chunks * sg::KCG)
                                                  : t.kblk;
   const int nch0 = (int)((std::min(Kblk, L) + sg::KCG - 1) / sg::KCG);
@@ -354,10 +353,11 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     a.klen = len;
     a.part = (double*)t.part;
     a.st = c->d_status;
+    if (cover) set_cover(a);
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, t.mapB, a);
+        t.mapA, t.mapB, t.mapB32, a);
     ktimer_end(c);
     // psi^H psi: psi's planes (rows [0, nb) of B_ext, read through a map with the A box) as
     // the first operand; rows [nb, 128 Tr) of that box are zero or psi'' rows, whose output
@@ -371,7 +371,7 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     a2.part = (double*)t.part2;
     ktimer_begin(c);
     sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapBA, t.mapB, t.mapB, a2);
+        t.mapBA, t.mapB, t.mapB32, a2);
     ktimer_end(c);
     c->launches += 5;
   }

@@ -151,9 +151,12 @@ def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx, nb):
         Hfull = Hfull.cpu().numpy()
         iu = np.triu_indices(nb, 1)
         scale = np.max(np.abs(Hfull))
-        assert np.max(np.abs(Hnm[iu] - Hfull[iu])) <= 1e-13 * scale
+        # the symmetric cover (192 < nb <= 256) forms some upper entries mirrored, as psi^H H psi
+        # entries: with FP32 H psi those differ from (H psi)^H psi at the FP32 level
+        tol = 1e-6 if (precision == "mixed" and 192 < nb <= 256) else 1e-13
+        assert np.max(np.abs(Hnm[iu] - Hfull[iu])) <= tol * scale
         # the diagonal of a Hermitian Gram is stored real
-        assert np.max(np.abs(np.diag(Hnm).real - np.diag(Hfull).real)) <= 1e-13 * scale
+        assert np.max(np.abs(np.diag(Hnm).real - np.diag(Hfull).real)) <= tol * scale
     if precision == "fp64":
         if mirrored:
             assert_close_matrix(Hnm, Hsep)
@@ -174,17 +177,20 @@ def test_gram_hs_against_separate_grams_and_oracle(dev, precision, cplx, nb):
     ctx.close()
 
 
+@pytest.mark.parametrize("cplx", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("nb", [193, 256])
-def test_symmetric_cover_gram_pair(dev, precision, nb):
-    """The real Gram pair with 192 < nb <= 256 bands runs on the symmetric cover (four tiles;
-    B rows from three 32-row blocks; entries of some block pairs computed mirrored).  With 1 MB
+def test_symmetric_cover_gram_pair(dev, precision, nb, cplx):
+    """The Gram pair with 192 < nb <= 256 bands runs on the symmetric cover (four tiles, per
+    half of B for complex bands; B rows from three 32-row blocks; entries of some block pairs
+    computed mirrored, the imaginary half negated).  With 1 MB
     of scratch the grid is cut into K blocks of one chunk, so every owned entry is also
     accumulated over many blocks.  FP64: H_nm and S_nm against the oracle's to 1e-12 of the
     largest entry.  FP32 bands: S_nm against the oracle on the FP32-rounded bands and H_nm
     against the upper-triangle tiling of the same FP32 H psi, to 1e-6."""
     from paper_2310_14776_gb300 import api
-    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=541)
+    k = (0.2, 0.1, -0.3) if cplx else (0.0, 0.0, 0.0)
+    s = synth.make_system((30, 28, 26), (7.0, 6.5, 6.0), 4, synth.PSET_SPD2, seed=541, k=k, complex_wf=cplx)
     psi_np = synth.make_psi(s, nb, 542)
     for mb in (0, 1):
         ctx = api.Context(s, max_bands=nb, device=dev, precision=precision)
@@ -192,7 +198,7 @@ def test_symmetric_cover_gram_pair(dev, precision, nb):
         psi = to_dev(psi_np, dev).to(ctx.dtype)
         hpsi, spsi, P = ctx.apply_hs(psi)
         Hnm, Snm = (t.cpu().numpy() for t in ctx.gram_hs(psi, hpsi, P))
-        psi_in = psi.cpu().numpy().astype(np.float64)
+        psi_in = psi.cpu().numpy().astype(np.complex128 if cplx else np.float64)
         ref = O.rayleigh_ritz(s, psi_in)
         if precision == "fp64":
             assert_close_matrix(Hnm, ref["Hnm"])
@@ -203,7 +209,7 @@ def test_symmetric_cover_gram_pair(dev, precision, nb):
             Hsep = ctx.gram(psi, hpsi, hermitian=True).cpu().numpy()
             assert_close_matrix(Hnm, Hsep, rel=1e-6)
             assert_close_matrix(Snm, ref["Snm"], rel=1e-6)
-        assert np.array_equal(Hnm, Hnm.T) and np.array_equal(Snm, Snm.T)
+        assert np.array_equal(Hnm, Hnm.conj().T) and np.array_equal(Snm, Snm.conj().T)
         ctx.close()
 
 
