@@ -45,22 +45,22 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # fixed band count it grows with the grid points K
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
-_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "35d92882799e406566221d91a0be7a4c74e5ca74",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "f4c07d5624d718e074ceddb60c13629acfc98a8e",
+_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "05eabe1a03a7cdb78122fe75a1a064ab2d7805f5",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "eced3be7a95b668779d6c3bee6eadee448766e48",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
                  "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
-    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21753.2, "sources": _GRAM_SOURCES},
-    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11966.8, "sources": _GRAM_SOURCES},
+    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21750.5, "sources": _GRAM_SOURCES},
+    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11965.2, "sources": _GRAM_SOURCES},
 }
 
 
 # Measured DRAM traffic per launch of the Gram MMA kernel (the mean of the two launches of one
 # pawfd_gram_hs call, ncu at 64^3 x 256 bands), per grid
-# point: FP64 (1880.8 + 6.1 + 940.8 + 3.6) / 2 MB, mixed (1075.2 + 1.6 + 538.0 + 1.7) / 2 MB.
+# point: FP64 (1880.8 + 5.7 + 940.8 + 3.1) / 2 MB, mixed (1075.3 + 1.5 + 538.0 + 1.5) / 2 MB.
 KERNEL_TRAFFIC = {
-    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1415.65e6 / 262144, "sources": _GRAM_SOURCES},
-    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 808.25e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1415.2e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 808.15e6 / 262144, "sources": _GRAM_SOURCES},
 }
 
 
