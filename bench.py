@@ -1129,8 +1129,13 @@ def run_pw(args):
     esize = C.element_size()
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    # six FFT passes per apply (three each way), each reading and writing every value once
-    fft_bytes = 6 * 2 * esize * nb * K
+    # FFT passes per apply, each reading and writing every value once: three each way, or two
+    # each way when x and y run as one pass per xy plane (FP32, both plane buffers within 200 KB
+    # of shared memory)
+    n1, n2 = int(system.n[0]), int(system.n[1])
+    xy = esize == 8 and 8 * (n1 + n2 + 2 * n2 * (n1 + 1)) + 16 * n2 <= 200 * 1024
+    passes = 4 if xy else 6
+    fft_bytes = passes * 2 * esize * nb * K
     ach = fft_bytes / (np.mean(h_ms) * 1e-3) / 1e9
     result = {
         "metric": METRIC, "value_definition": "grid points x bands of plane-wave H C and S C per second / 1e9 "
@@ -1143,11 +1148,11 @@ def run_pw(args):
                    "grid": list(system.n), "bands": nb, "precision": args.precision, "parallelism": "single-gpu",
                    "l2": "inputs larger than L2 (%.2f GB of coefficients)" % (nb * K * esize / 1e9)},
         "apply_H_ms": float(np.mean(h_ms)), "apply_S_ms": float(np.mean(s_ms)),
-        "roofline": {"stage": "pawfd_pw_apply_H", "kernel": "fft_pass_kernel (6 passes) + project + back-add",
+        "roofline": {"stage": "pawfd_pw_apply_H", "kernel": "fft_pass_kernel (%d passes) + project + back-add" % passes,
                      "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                      "traffic": None, "bytes_per_apply": fft_bytes,
-                     "note": "bytes of the six FFT passes (each reads and writes every value once) over the whole "
-                             "H application time; FP64 butterflies run on the FP64 pipe"},
+                     "note": "bytes of the %d FFT passes (each reads and writes every value once) over the whole "
+                             "H application time; FP64 butterflies run on the FP64 pipe" % passes},
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(result), flush=True)

@@ -75,6 +75,12 @@ struct FftArgs {
   int add_kin;
   // butterfly constants: sqrt(3)/2, cos(2 pi/5), cos(4 pi/5), sin(2 pi/5), sin(4 pi/5)
   R s3, c51, c52, s51, s52;
+  // xy = 1: an x pass whose CTA holds one whole xy plane (nl = N2 lines) and transforms its
+  // columns too (length N2, radices fac2, twiddles tw2) before the store
+  int xy;
+  int N2, nf2;
+  int fac2[MAX_FAC];
+  const cplx<R>* tw2;
 };
 
 // i s z
@@ -93,9 +99,9 @@ struct LineBase {
   int band;
 };
 
-template <class R>
+template <class R, int NT>
 __device__ __forceinline__ void line_bases(const FftArgs<R>& a, LineBase* lb) {
-  for (int l = threadIdx.x; l < a.nl; l += FFT_NT) {
+  for (int l = threadIdx.x; l < a.nl; l += NT) {
     LineBase b;
     if (a.axis == 0) {
       const long long L = (long long)blockIdx.x * a.nl + l;
@@ -125,11 +131,50 @@ __device__ __forceinline__ void line_bases(const FftArgs<R>& a, LineBase* lb) {
   }
 }
 
+// One radix-Rd butterfly of a Stockham stage: inputs x[r xs] (r < Rd), the r-th times the
+// twiddle W[r k step], outputs y[r ys]
 template <class R>
-__global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
+__device__ __forceinline__ void stockham_butterfly(const cplx<R>* x, int xs, cplx<R>* y, int ys, const cplx<R>* W,
+                                                   int k, int step, int Rd, R sg, const FftArgs<R>& a) {
+  if (Rd == 4) {
+    cplx<R> v0 = x[0], v1 = x[xs] * W[k * step], v2 = x[2 * xs] * W[2 * k * step], v3 = x[3 * xs] * W[3 * k * step];
+    const cplx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = imul(sg, v1 - v3);
+    y[0] = t0 + t2;
+    y[ys] = t1 + t3;
+    y[2 * ys] = t0 - t2;
+    y[3 * ys] = t1 - t3;
+  } else if (Rd == 2) {
+    const cplx<R> v0 = x[0], v1 = x[xs] * W[k * step];
+    y[0] = v0 + v1;
+    y[ys] = v0 - v1;
+  } else if (Rd == 3) {
+    const cplx<R> v0 = x[0], v1 = x[xs] * W[k * step], v2 = x[2 * xs] * W[2 * k * step];
+    const cplx<R> b = v1 + v2;
+    const cplx<R> c = v0 - R(0.5) * b;
+    const cplx<R> d = imul(sg * a.s3, v1 - v2);
+    y[0] = v0 + b;
+    y[ys] = c + d;
+    y[2 * ys] = c - d;
+  } else {   // 5
+    const cplx<R> v0 = x[0], v1 = x[xs] * W[k * step], v2 = x[2 * xs] * W[2 * k * step],
+                  v3 = x[3 * xs] * W[3 * k * step], v4 = x[4 * xs] * W[4 * k * step];
+    const cplx<R> A = v1 + v4, B = v2 + v3, D = v1 - v4, E = v2 - v3;
+    const cplx<R> t1 = v0 + a.c51 * A + a.c52 * B, t2 = v0 + a.c52 * A + a.c51 * B;
+    const cplx<R> u1 = imul(sg, a.s51 * D + a.s52 * E), u2 = imul(sg, a.s52 * D - a.s51 * E);
+    y[0] = v0 + A + B;
+    y[ys] = t1 + u1;
+    y[4 * ys] = t1 - u1;
+    y[2 * ys] = t2 + u2;
+    y[3 * ys] = t2 - u2;
+  }
+}
+
+template <class R, int NT>
+__global__ void __launch_bounds__(NT) fft_pass_kernel(const FftArgs<R> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<R>* W = (cplx<R>*)smem_raw;
-  cplx<R>* X = W + a.N;
+  cplx<R>* W2 = W + a.N;                          // the columns' twiddles (xy passes)
+  cplx<R>* X = W2 + (a.xy ? a.N2 : 0);
   // lines at a pitch of N + 1 values: the y and z passes fill and drain the buffer across lines
   // (consecutive x in consecutive threads), which at a pitch of N would put a warp's accesses
   // in one bank for every even N
@@ -138,21 +183,26 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
   LineBase* lb = (LineBase*)(Y + (size_t)a.nl * pitch);
   const int N = a.N, nl = a.nl, tid = threadIdx.x;
   const int stride = a.axis == 0 ? 1 : (a.axis == 1 ? a.n1 : a.n1 * a.n2);
-  line_bases(a, lb);
-  for (int j = tid; j < N; j += FFT_NT) {
+  line_bases<R, NT>(a, lb);
+  for (int j = tid; j < N; j += NT) {
     const cplx<R> w = a.tw[j];
     W[j] = a.inverse ? cplx<R>{w.re, -w.im} : w;
   }
+  if (a.xy)
+    for (int j = tid; j < a.N2; j += NT) {
+      const cplx<R> w = a.tw2[j];
+      W2[j] = a.inverse ? cplx<R>{w.re, -w.im} : w;
+    }
   __syncthreads();   // the line bases
   // element e of the CTA's nl N is (line l, position i): e = l N + i along x (contiguous lines),
-  // e = i nl + l along y and z (consecutive x); (l, i) advance by FFT_NT elements per iteration
+  // e = i nl + l along y and z (consecutive x); (l, i) advance by NT elements per iteration
   // without a division
   const bool xline = a.axis == 0;
   const int inner = xline ? N : nl;                     // the fast index's range
-  const int d_fast = FFT_NT % inner, d_slow = FFT_NT / inner;
+  const int d_fast = NT % inner, d_slow = NT / inner;
   const int f0 = tid % inner, s0 = tid / inner;
   // load: x lines along the line (contiguous), y / z lines across the tile (consecutive x)
-  for (int e = tid, fi = f0, si = s0; e < nl * N; e += FFT_NT) {
+  for (int e = tid, fi = f0, si = s0; e < nl * N; e += NT) {
     const int l = xline ? si : fi;
     const int i = xline ? fi : si;
     fi += d_fast;
@@ -209,43 +259,11 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
   for (int s = 0; s < a.nf; ++s) {
     const int Rd = a.fac[s], M = N / Rd, step = N / (Ns * Rd);
     // butterfly e = l M + j, j = jq Ns + k (M is a multiple of Ns); all advanced incrementally
-    const int dj = FFT_NT % M, dl = FFT_NT / M, dk = dj % Ns, djq = dj / Ns, mq = M / Ns;
+    const int dj = NT % M, dl = NT / M, dk = dj % Ns, djq = dj / Ns, mq = M / Ns;
     int l = tid / M, j = tid - (tid / M) * M;
     int jq = j / Ns, k = j - jq * Ns;
-    for (int e = tid; e < nl * M; e += FFT_NT) {
-      const cplx<R>* x = X + l * pitch + j;
-      cplx<R>* y = Y + l * pitch + jq * Ns * Rd + k;
-      if (Rd == 4) {
-        cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step], v3 = x[3 * M] * W[3 * k * step];
-        const cplx<R> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3, t3 = imul(sg, v1 - v3);
-        y[0] = t0 + t2;
-        y[Ns] = t1 + t3;
-        y[2 * Ns] = t0 - t2;
-        y[3 * Ns] = t1 - t3;
-      } else if (Rd == 2) {
-        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step];
-        y[0] = v0 + v1;
-        y[Ns] = v0 - v1;
-      } else if (Rd == 3) {
-        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step];
-        const cplx<R> b = v1 + v2;
-        const cplx<R> c = v0 - R(0.5) * b;
-        const cplx<R> d = imul(sg * a.s3, v1 - v2);
-        y[0] = v0 + b;
-        y[Ns] = c + d;
-        y[2 * Ns] = c - d;
-      } else {   // 5
-        const cplx<R> v0 = x[0], v1 = x[M] * W[k * step], v2 = x[2 * M] * W[2 * k * step],
-                      v3 = x[3 * M] * W[3 * k * step], v4 = x[4 * M] * W[4 * k * step];
-        const cplx<R> A = v1 + v4, B = v2 + v3, D = v1 - v4, E = v2 - v3;
-        const cplx<R> t1 = v0 + a.c51 * A + a.c52 * B, t2 = v0 + a.c52 * A + a.c51 * B;
-        const cplx<R> u1 = imul(sg, a.s51 * D + a.s52 * E), u2 = imul(sg, a.s52 * D - a.s51 * E);
-        y[0] = v0 + A + B;
-        y[Ns] = t1 + u1;
-        y[4 * Ns] = t1 - u1;
-        y[2 * Ns] = t2 + u2;
-        y[3 * Ns] = t2 - u2;
-      }
+    for (int e = tid; e < nl * M; e += NT) {
+      stockham_butterfly(X + l * pitch + j, M, Y + l * pitch + jq * Ns * Rd + k, Ns, W, k, step, Rd, sg, a);
       j += dj;
       l += dl;
       k += dk;
@@ -266,8 +284,45 @@ __global__ void __launch_bounds__(FFT_NT) fft_pass_kernel(const FftArgs<R> a) {
     Y = t;
     Ns *= Rd;
   }
+  // xy passes: the columns of the plane (element i of column x at X[i pitch + x]); butterfly
+  // e = j N + x with x fastest, so that a warp touches consecutive columns (no bank conflicts)
+  if (a.xy) {
+    const int Ny = a.N2;
+    int Ns2 = 1;
+    for (int s = 0; s < a.nf2; ++s) {
+      const int Rd = a.fac2[s], M = Ny / Rd, step = Ny / (Ns2 * Rd);
+      const int dx = NT % N, dj = NT / N, dk = dj % Ns2, djq = dj / Ns2;
+      int x = tid % N, j = tid / N;
+      int jq = j / Ns2, k = j - jq * Ns2;
+      for (int e = tid; e < M * N; e += NT) {
+        stockham_butterfly(X + j * pitch + x, M * pitch, Y + (jq * Ns2 * Rd + k) * pitch + x, Ns2 * pitch, W2, k, step,
+                           Rd, sg, a);
+        x += dx;
+        j += dj;
+        k += dk;
+        jq += djq;
+        if (k >= Ns2) {
+          k -= Ns2;
+          ++jq;
+        }
+        if (x >= N) {
+          x -= N;
+          ++j;
+          if (++k >= Ns2) {
+            k -= Ns2;
+            ++jq;
+          }
+        }
+      }
+      __syncthreads();
+      cplx<R>* t = X;
+      X = Y;
+      Y = t;
+      Ns2 *= Rd;
+    }
+  }
   // store, with the epilogue
-  for (int e = tid, fi = f0, si = s0; e < nl * N; e += FFT_NT) {
+  for (int e = tid, fi = f0, si = s0; e < nl * N; e += NT) {
     const int l = xline ? si : fi;
     const int i = xline ? fi : si;
     fi += d_fast;
@@ -466,14 +521,82 @@ int fft_pass_plan(pawfd_ctx* c, const PwPlan& p, int axis, const cplx<R>* in, cp
       sizeof(cplx<R>) * ((size_t)a.N + 2 * (size_t)a.nl * (a.N + 1)) + sizeof(LineBase) * (size_t)a.nl;
   if (smem > 48 * 1024) {
     const int rc = check_cuda(
-        c, cudaFuncSetAttribute(fft_pass_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+        c, cudaFuncSetAttribute(fft_pass_kernel<R, FFT_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
         "fft smem attribute");
     if (rc != PAWFD_OK) return rc;
   }
   if (grid > 2147483647ll) return fail(c, PAWFD_EINVAL, "plane-wave mode: too many lines for one launch");
-  fft_pass_kernel<R><<<(unsigned)grid, FFT_NT, smem, c->stream>>>(a);
+  fft_pass_kernel<R, FFT_NT><<<(unsigned)grid, FFT_NT, smem, c->stream>>>(a);
   c->launches += 1;
   return check_cuda(c, cudaGetLastError(), "fft launch");
+}
+
+// The fused xy pass: one CTA of XY_NT threads per xy plane (both buffers of the plane in
+// shared memory), x then y transforms, a's prologue on load and epilogue on store.  FP32 only,
+// and only while the plane's two buffers fit XY_SMEM_MAX bytes (96^2: 149 KB).
+constexpr int XY_NT = 1024;
+constexpr size_t XY_SMEM_MAX = 200 * 1024;
+
+template <class R>
+size_t xy_smem(const pawfd_ctx* c) {
+  const size_t n1 = (size_t)c->n[0], n2 = (size_t)c->n[1];
+  return sizeof(cplx<R>) * (n1 + n2 + 2 * n2 * (n1 + 1)) + sizeof(LineBase) * n2;
+}
+template <class R>
+bool xy_fits(const pawfd_ctx* c) { return sizeof(R) == 4 && xy_smem<R>(c) <= XY_SMEM_MAX; }
+
+template <class R>
+int fft_xy_pass_plan(pawfd_ctx* c, const PwPlan& p, const cplx<R>* in, cplx<R>* out, int nb, bool inverse,
+                     FftArgs<R> a) {
+  a.N = c->n[0];
+  a.nf = p.nf[0];
+  for (int s = 0; s < p.nf[0]; ++s) a.fac[s] = p.fac[0][s];
+  a.tw = (const cplx<R>*)p.tw[0];
+  a.xy = 1;
+  a.N2 = c->n[1];
+  a.nf2 = p.nf[1];
+  for (int s = 0; s < p.nf[1]; ++s) a.fac2[s] = p.fac[1][s];
+  a.tw2 = (const cplx<R>*)p.tw[1];
+  a.inverse = inverse ? 1 : 0;
+  a.axis = 0;
+  a.n1 = c->n[0];
+  a.n2 = c->n[1];
+  a.n3 = c->n[2];
+  a.K = (long long)c->K;
+  a.in = in;
+  a.out = out;
+  a.s3 = (R)(0.5 * std::sqrt(3.0));
+  a.c51 = (R)std::cos(2.0 * M_PI / 5.0);
+  a.c52 = (R)std::cos(4.0 * M_PI / 5.0);
+  a.s51 = (R)std::sin(2.0 * M_PI / 5.0);
+  a.s52 = (R)std::sin(4.0 * M_PI / 5.0);
+  a.nl = c->n[1];                                   // one xy plane per CTA
+  a.nlines = (long long)nb * c->n[1] * c->n[2];
+  a.tiles = 1;
+  const long long grid = (long long)nb * c->n[2];
+  const size_t smem = xy_smem<R>(c);
+  int rc = check_cuda(c, cudaFuncSetAttribute(fft_pass_kernel<R, XY_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem),
+                      "fft xy smem attribute");
+  if (rc != PAWFD_OK) return rc;
+  if (grid > 2147483647ll) return fail(c, PAWFD_EINVAL, "plane-wave mode: too many planes for one launch");
+  fft_pass_kernel<R, XY_NT><<<(unsigned)grid, XY_NT, smem, c->stream>>>(a);
+  c->launches += 1;
+  return check_cuda(c, cudaGetLastError(), "fft xy launch");
+}
+
+// The x and y transforms of every xy plane: the fused pass where it applies, else the x pass
+// (with a's prologue, in -> out) and the y pass (with a's epilogue, in place in out).
+template <class R>
+int fft_xy(pawfd_ctx* c, const PwPlan& p, const cplx<R>* in, cplx<R>* out, int nb, bool inverse, FftArgs<R> a) {
+  if (xy_fits<R>(c)) return fft_xy_pass_plan<R>(c, p, in, out, nb, inverse, a);
+  FftArgs<R> ax = a, ay = a;
+  ax.post = 0;
+  ay.pre = 0;
+  ay.xin = nullptr;
+  int rc = fft_pass_plan<R>(c, p, 0, in, out, nb, inverse, ax);
+  if (rc == PAWFD_OK) rc = fft_pass_plan<R>(c, p, 1, out, out, nb, inverse, ay);
+  return rc;
 }
 
 template <class R>
@@ -486,7 +609,18 @@ int fft_pass(pawfd_ctx* c, int axis, const cplx<R>* in, cplx<R>* out, int nb, bo
 template <class R>
 int pw_inverse(pawfd_ctx* c, const cplx<R>* C, int nb, cplx<R>* psi, cplx<R>* loc, const R* v) {
   FftArgs<R> a = {};
-  int rc = fft_pass<R>(c, 0, C, psi, nb, true, a);
+  int rc;
+  if (xy_fits<R>(c)) {
+    // z first, then x and y in one pass with the phase epilogue (the axes commute)
+    rc = fft_pass<R>(c, 2, C, psi, nb, true, a);
+    a.post = 1;
+    a.phase = (const cplx<R>*)c->pw.phase;
+    a.out2 = loc;
+    a.v = v;
+    if (rc == PAWFD_OK) rc = fft_xy_pass_plan<R>(c, c->pw, psi, psi, nb, true, a);
+    return rc;
+  }
+  rc = fft_pass<R>(c, 0, C, psi, nb, true, a);
   if (rc == PAWFD_OK) rc = fft_pass<R>(c, 1, psi, psi, nb, true, a);
   a.post = 1;
   a.phase = (const cplx<R>*)c->pw.phase;
@@ -502,9 +636,8 @@ int pw_forward(pawfd_ctx* c, cplx<R>* f, int nb, cplx<R>* out, const cplx<R>* Ci
   FftArgs<R> a = {};
   a.pre = 1;
   a.phase = (const cplx<R>*)c->pw.phase;
-  int rc = fft_pass<R>(c, 0, f, f, nb, false, a);
+  int rc = fft_xy<R>(c, c->pw, f, f, nb, false, a);
   a.pre = 0;
-  if (rc == PAWFD_OK) rc = fft_pass<R>(c, 1, f, f, nb, false, a);
   a.post = 2;
   a.kin = (const R*)c->pw.kin;
   a.Cin = Cin;
@@ -640,20 +773,20 @@ int kinetic_precond_impl(pawfd_ctx* c, const void* R, int nb, void* out, zf* wor
   a.phase = (const zf*)c->pc.phase;
   a.pre = 3;
   a.xin = R;
-  int rc = fft_pass_plan<float>(c, c->pc, 0, nullptr, work, nbat, false, a);
+  // forward: x and y (reading the bands), z (times the table); inverse: z, then x and y
+  // (writing the bands); the axes commute
+  int rc = fft_xy<float>(c, c->pc, nullptr, work, nbat, false, a);
   a.pre = 0;
   a.xin = nullptr;
-  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 1, work, work, nbat, false, a);
   a.post = 3;
   a.tab = (const float*)c->pc.tab;
   if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 2, work, work, nbat, false, a);
   a.post = 0;
   a.tab = nullptr;
-  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 0, work, work, nbat, true, a);
-  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 1, work, work, nbat, true, a);
+  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 2, work, work, nbat, true, a);
   a.post = 5;
   a.xout = out;
-  if (rc == PAWFD_OK) rc = fft_pass_plan<float>(c, c->pc, 2, work, work, nbat, true, a);
+  if (rc == PAWFD_OK) rc = fft_xy<float>(c, c->pc, work, work, nbat, true, a);
   return rc;
 }
 
