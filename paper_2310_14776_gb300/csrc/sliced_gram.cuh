@@ -640,8 +640,10 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float xh, float xl)
 // BULK: the operands are core-matrix planes (plane_offset_cm), one bulk copy per plane and
 // operand per stage, read by the tensor cores without swizzle; otherwise row-major planes
 // (plane_offset_rm) through the 4-D TMA maps tA and tB with a 32-byte swizzle.
-// tB32: the B planes with a box of CB rows (the symmetric cover's B blocks).
-template <int S, int ORD, bool ONE, bool BULK, int KCH>
+// tB32: the B planes with a box of CB rows (the symmetric cover's B blocks).  COVER: the Gram
+// on the symmetric cover (a separate instance, so that the other instances carry none of its
+// registers).
+template <int S, int ORD, bool ONE, bool BULK, int KCH, bool COVER = false>
 __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_constant__ CUtensorMap tA,
                                                                   const __grid_constant__ CUtensorMap tB,
                                                                   const __grid_constant__ CUtensorMap tB32,
@@ -662,7 +664,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
   // tile run while the epilogue of the last one drains TMEM and stores).
   const int ntiles = !ONE ? 1 : ((int)blockIdx.x < a.rot_tiles ? (a.rot_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0);
   auto tile_at = [&](int i, int& row0, int& col0, int& tcol) {
-    if (!BULK && a.cover) {
+    if (COVER) {
       row0 = a.cov_row0[blockIdx.x % COVER_TILES];
       col0 = 0;
       tcol = 0;
@@ -736,7 +738,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           }
         } else {
           tc::tma_load_4d(sa, &tA, &full[s], 0, row0, (int)ks, 0);
-          if (a.cover) {
+          if constexpr (COVER) {
             // B rows from three blocks, each with its S planes in one box: block g's plane j
             // at (g S + j) KB of the stage's B area (the MMAs then take N = 32 per block)
             const int ct = blockIdx.x % COVER_TILES, boff = (blockIdx.x / COVER_TILES) * HS;
@@ -795,7 +797,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
         // field (address / 16, 14 bits) does not overflow inside the 228 KB of shared memory
         const uint64_t da0 = BULK ? tc::smem_desc_nosw(sa, 128, 256) : tc::smem_desc(sa, BK * 2);
         const uint64_t db0 = BULK ? tc::smem_desc_nosw(sb, 128, 256) : tc::smem_desc(sb, BK * 2);
-        if (leader && a.cover) {
+        if (COVER && leader) {
           // the symmetric cover: each product as three N = 32 MMAs, one per B block, into the
           // block's 32 columns of the accumulator; A plane i stays in the collector buffer over
           // all of them
@@ -1110,7 +1112,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
     const int ra = (row < a.rowsA) ? __ldg(a.maxA + row) : 0;
     // B row of tile column tc (the symmetric cover gathers three 32-row blocks of its half)
     auto bcol = [&](int tcn) -> int {
-      if (!BULK && a.cover)
+      if (COVER)
         return (int)(blockIdx.x / COVER_TILES) * HS + a.cov_seg[blockIdx.x % COVER_TILES][tcn / CB] + tcn % CB;
       return col0 + tcn;
     };
@@ -1201,7 +1203,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gram_kernel(const __grid_c
           }
         }
       }
-    } else if (!BULK && a.cover) {
+    } else if (COVER) {
       // the symmetric cover: the entries of the block pairs this tile owns, at (min, max) of
       // its half
       if (row < a.rowsA && !abort_flag) {

@@ -262,8 +262,12 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     if (cover) set_cover(a);
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
-    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, t.mapB32, a);
+    if (cover)
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG, true>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, t.mapB32, a);
+    else
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, t.mapB32, a);
     ktimer_end(c);
     // psi^T psi: psi's planes and exponents on both sides (psi's planes through a map with the
     // B operand's box)
@@ -275,8 +279,12 @@ int tc_gram_pair_impl(pawfd_ctx* c, const R* A, const R* B, int nb, double* M1, 
     a2.maxB = t.maxA;
     a2.part = (double*)t.part2;
     ktimer_begin(c);
-    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapAB, t.mapAB32, a2);
+    if (cover)
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG, true>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapAB, t.mapAB32, a2);
+    else
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapAB, t.mapAB32, a2);
     ktimer_end(c);
     c->launches += presliced ? 3 : 4;
   }
@@ -356,8 +364,12 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     if (cover) set_cover(a);
     if (blk == 0 && ns < nsplit) nsplit = ns;
     ktimer_begin(c);
-    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapA, t.mapB, t.mapB32, a);
+    if (cover)
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG, true>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, t.mapB32, a);
+    else
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapA, t.mapB, t.mapB32, a);
     ktimer_end(c);
     // psi^H psi: psi's planes (rows [0, nb) of B_ext, read through a map with the A box) as
     // the first operand; rows [nb, 128 Tr) of that box are zero or psi'' rows, whose output
@@ -370,8 +382,12 @@ int tc_gram_pair_cplx_impl(pawfd_ctx* c, const R* A, const R* B, int nb, zd* M1,
     a2.maxA = t.maxB;
     a2.part = (double*)t.part2;
     ktimer_begin(c);
-    sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG><<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(
-        t.mapBA, t.mapB, t.mapB32, a2);
+    if (cover)
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG, true>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapBA, t.mapB, t.mapB32, a2);
+    else
+      sg::sliced_gram_kernel<S, ORD, false, false, sg::KCG>
+          <<<dim3(tiles, ns), sg::NTHREADS, sg::smem_bytes<S>(), c->stream>>>(t.mapBA, t.mapB, t.mapB32, a2);
     ktimer_end(c);
     c->launches += 5;
   }
@@ -658,13 +674,15 @@ int setup_tc(pawfd_ctx* c) {
                           (const void*)sg::sliced_gram_kernel<7, 6, true, true, sg::KC>,
                           (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KC>,
                           (const void*)sg::sliced_gram_kernel<7, 6, true, true, sg::KCG>,
-                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KCG>};
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, true, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<7, 6, false, false, sg::KCG, true>};
     const void* fns4[] = {(const void*)sg::sliced_gram_kernel<4, 4, false, false, sg::KCG>,
                           (const void*)sg::sliced_gram_kernel<4, 4, true, true, sg::KC>,
                           (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KC>,
                           (const void*)sg::sliced_gram_kernel<4, 4, true, true, sg::KCG>,
-                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KCG>};
-    for (int f = 0; f < 5 && rc == PAWFD_OK; ++f)
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, true, sg::KCG>,
+                          (const void*)sg::sliced_gram_kernel<4, 4, false, false, sg::KCG, true>};
+    for (int f = 0; f < 6 && rc == PAWFD_OK; ++f)
       rc = check_cuda(c, cudaFuncSetAttribute(S == 7 ? fns7[f] : fns4[f], smem_attr,
                                               S == 7 ? sg::smem_bytes<7>() : sg::smem_bytes<4>()),
                       "smem attribute");
