@@ -45,22 +45,22 @@ FP32_PROBE_TFLOPS = 70.1     # GB300 FP32 FMA rate measured by a DFMA/FFMA probe
 # fixed band count it grows with the grid points K
 # (slicing and digit-plane reads per K block); valid only for that band count and while the
 # kernels' sources are the ones that were measured.
-_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "05eabe1a03a7cdb78122fe75a1a064ab2d7805f5",
-                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "eced3be7a95b668779d6c3bee6eadee448766e48",
+_GRAM_SOURCES = {"paper_2310_14776_gb300/csrc/sliced_gram.cuh": "dcad82e720e6d74d785b8eceb2d43563d70a1ea4",
+                 "paper_2310_14776_gb300/csrc/tc_gram.cu": "f71758ac3494c927ade28099fe219df55efa207c",
                  "paper_2310_14776_gb300/csrc/nonlocal.cu": "375a13b3bd58e662195fcecdc233878a150e7244",
                  "paper_2310_14776_gb300/csrc/tc_common.cuh": "69b7022593a46a5fea888d3ab59abd564beb1cc9"}
 TRAFFIC = {
-    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21750.5, "sources": _GRAM_SOURCES},
-    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11965.2, "sources": _GRAM_SOURCES},
+    ("gram_HS", "fp64", False): {"nb": 256, "per_point": 21819.6, "sources": _GRAM_SOURCES},
+    ("gram_HS", "mixed", False): {"nb": 256, "per_point": 11975.8, "sources": _GRAM_SOURCES},
 }
 
 
 # Measured DRAM traffic per launch of the Gram MMA kernel (the mean of the two launches of one
 # pawfd_gram_hs call, ncu at 64^3 x 256 bands), per grid
-# point: FP64 (1880.8 + 5.7 + 940.8 + 3.1) / 2 MB, mixed (1075.3 + 1.5 + 538.0 + 1.5) / 2 MB.
+# point: FP64 (1887.1 + 15.0 + 940.7 + 5.5) / 2 MB, mixed (1075.2 + 4.6 + 537.9 + 1.3) / 2 MB.
 KERNEL_TRAFFIC = {
-    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1415.2e6 / 262144, "sources": _GRAM_SOURCES},
-    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 808.15e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "fp64", False): {"nb": 256, "per_point": 1424.15e6 / 262144, "sources": _GRAM_SOURCES},
+    ("gram_mma", "mixed", False): {"nb": 256, "per_point": 809.5e6 / 262144, "sources": _GRAM_SOURCES},
 }
 
 
