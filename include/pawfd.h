@@ -217,9 +217,12 @@ int pawfd_apply_HS(pawfd_ctx* ctx, const void* psi, int nb, void* hpsi, void* sp
  *   Snm = dV psi^H psi + sum_a P_a^H dS^a P_a      (the PAW overlap <psi_n|S|psi_m>, its
  *                                                    projector term from the projections P)
  * P: the projections of psi ([Ip][nb], as written by pawfd_project / pawfd_apply_HS; may be
- * NULL only when the context has no atoms).  With the tensor-core contraction and real bands
- * the digits of psi are made once and serve both matrices.  Hnm, Snm: [nb][nb] FP64 of the
- * context's kind, Hermitian (mirrored, real diagonal); they may not alias.  Asynchronous. */
+ * NULL only when the context has no atoms).  With the tensor-core contraction the digits of
+ * psi are made once and serve both matrices.  Since H is Hermitian, some entries of Hnm may be
+ * formed from the mirrored product ((H psi)_m^H psi_n conjugated, or psi_m^H (H psi)_n): equal
+ * in exact arithmetic, with H psi in FP32 they differ at the FP32 level.  Hnm, Snm: [nb][nb]
+ * FP64 of the context's kind, Hermitian (mirrored, real diagonal); they may not alias.
+ * Asynchronous. */
 int pawfd_gram_hs(pawfd_ctx* ctx, const void* psi, const void* hpsi, int nb, const void* P, void* Hnm, void* Snm);
 
 /* Subspace diagonalization: given Hermitian H_nm and positive definite S_nm ([nb][nb],
